@@ -1,0 +1,225 @@
+"""A second, deliberately naive evaluator of access-index programs, used only
+to pin the C oracle on tiny grids (every block, every thread).
+
+It is written independently of oracle/cufz_oracle.c: its own decoder (a
+recursive parse into nested blocks), Python integers with explicit masking,
+its own hash, classification and bucketing.  Both follow the same definition:
+serial execution of every thread (Sec. 4.1, Listings 1-2), exact bounds
+checks, AFL-style edges (Sec. 2.1).
+"""
+from __future__ import annotations
+
+import struct
+
+M32 = 0xFFFFFFFF
+M64 = (1 << 64) - 1
+
+
+def s32(v):
+    v &= M32
+    return v - (1 << 32) if v >> 31 else v
+
+
+def murmur_fmix32(h):
+    h &= M32
+    h ^= h >> 16
+    h = (h * 0x85EBCA6B) & M32
+    h ^= h >> 13
+    h = (h * 0xC2B2AE35) & M32
+    return h ^ (h >> 16)
+
+
+def afl_class(n):
+    for limit, cls in ((0, 0), (1, 1), (2, 2), (3, 4), (7, 8), (15, 16), (31, 32), (127, 64)):
+        if n <= limit:
+            return cls
+    return 128
+
+
+def parse(prog: bytes):
+    magic, ver, n_ops, n_regs, n_bufs, n_sites, _, shmask, _, seed = struct.unpack_from(
+        "<IHHBBBBHHI", prog, 0)
+    assert magic == 0x315A4643 and ver == 1
+    loc = [struct.unpack_from("<HH", prog, 32 + 4 * s) for s in range(n_sites)]
+    raw = [struct.unpack_from("<BBBBi", prog, 32 + 4 * n_sites + 8 * i) for i in range(n_ops)]
+    counters = {"b": 0, "a": 0}
+    pos = [0]
+
+    def block(terminators):
+        out = []
+        while pos[0] < len(raw):
+            opc, d, a, b, imm = raw[pos[0]]
+            if opc in terminators:
+                return out, opc
+            pos[0] += 1
+            if opc == 0x50:
+                site = counters["b"]
+                counters["b"] += 1
+                then, t = block((0x51, 0x52))
+                els = []
+                if t == 0x51:
+                    pos[0] += 1
+                    els, t = block((0x52,))
+                pos[0] += 1
+                out.append(("if", a, site, then, els))
+            elif opc == 0x53:
+                site = counters["b"]
+                counters["b"] += 1
+                body, _ = block((0x54,))
+                pos[0] += 1
+                out.append(("loop", d, a, imm, site, body))
+            elif opc in (0x40, 0x41):
+                out.append(("mem", opc == 0x41, d, a, b, imm, counters["a"]))
+                counters["a"] += 1
+            else:
+                out.append(("op", opc, d, a, b, imm))
+        return out, None
+
+    body, _ = block(())
+    return dict(n_regs=n_regs, n_bufs=n_bufs, shmask=shmask, seed=seed, loc=loc, body=body)
+
+
+def alu(opc, x, y):
+    ux, uy = x & M32, y & M32
+    sh = uy & 31
+    f = {
+        0x10: lambda: ux + uy, 0x11: lambda: ux - uy, 0x12: lambda: ux * uy,
+        0x13: lambda: ux << sh, 0x14: lambda: s32(ux) >> sh, 0x15: lambda: ux >> sh,
+        0x16: lambda: ux & uy, 0x17: lambda: ux | uy, 0x18: lambda: ux ^ uy,
+        0x19: lambda: min(s32(ux), s32(uy)), 0x1A: lambda: max(s32(ux), s32(uy)),
+        0x1B: lambda: int(s32(ux) < s32(uy)), 0x1C: lambda: int(s32(ux) <= s32(uy)),
+        0x1D: lambda: int(ux == uy), 0x1E: lambda: int(ux != uy), 0x1F: lambda: int(ux < uy),
+    }[opc]
+    return s32(f())
+
+
+def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
+    """inp: dict(grid=(x,y,z), block=(x,y,z), args=[4], lens=[...]).
+    Returns dict(status, flags, records=[tuple], counts={e: n}, digest,
+    n_accesses, n_violations, first_key, n_branch)."""
+    P = parse(prog)
+    g, b = inp["grid"], inp["block"]
+    if 0 in g or 0 in b or b[0] > 1024 or b[1] > 1024 or b[2] > 64 or b[0] * b[1] * b[2] > 1024 \
+            or g[0] > 2**31 - 1 or g[1] > 65535 or g[2] > 65535:
+        return dict(status=2, flags=0, records=[], counts={}, digest=0, n_accesses=0,
+                    n_violations=0, first_key=M64, n_branch=0)
+    lens = list(inp["lens"]) + [0] * 9
+    shm = P["shmask"]
+    base = {}
+    nxt = {0: redzone, 1: redzone}
+    for k in range(P["n_bufs"]):
+        sp = (shm >> k) & 1
+        base[k] = nxt[sp]
+        nxt[sp] = -(-(nxt[sp] + lens[k] + redzone) // 256) * 256
+    st = dict(records=[], counts={}, digest=0, n_accesses=0, n_branch=0, budget_hit=False)
+
+    def classify(buf, off, w):
+        if -redzone <= off < 0:
+            return 1
+        if 0 <= off < lens[buf] + redzone:
+            return 2
+        addr = base[buf] + off
+        for j in range(P["n_bufs"]):
+            if j != buf and ((shm >> j) & 1) == ((shm >> buf) & 1) and lens[j] > 0:
+                if addr < base[j] + lens[j] and addr + w > base[j]:
+                    return 3
+        return 4
+
+    def run_thread(bl, tl, sregs):
+        regs = [0] * max(P["n_regs"], 1)
+        t = dict(ordinal=0, prev=0, back=0, stop=False)
+        th = murmur_fmix32((bl * 0x9E3779B1 + tl) & M32)
+
+        def edge(site, out):
+            cur = P["loc"][site][out]
+            e = (cur ^ t["prev"]) & 0xFFFF
+            st["counts"][e] = st["counts"].get(e, 0) + 1
+            t["prev"] = cur >> 1
+            st["n_branch"] += 1
+
+        def mem(is_st, d, a, buf, w, site):
+            off = regs[a] * w
+            bad = off < 0 or off + w > lens[buf]
+            mix = ((t["ordinal"] * 0x85EBCA77 + site * 0xC2B2AE3D) & M32) ^ (off & M32) ^ \
+                (((off & M64) >> 32) * 0x27D4EB2F & M32)
+            st["digest"] = (st["digest"] + murmur_fmix32(th ^ mix)) & M64
+            st["n_accesses"] += 1
+            val = 0
+            if bad:
+                st["records"].append((bl, tl, t["ordinal"], site, buf, int(is_st), w,
+                                      (shm >> buf) & 1, classify(buf, off, w), off))
+            elif not is_st and not (shm >> buf) & 1:
+                word = murmur_fmix32(P["seed"] ^ ((buf * 0x9E3779B9) & M32) ^ ((off >> 2) & M32))
+                val = s32((word >> (8 * (off & 3))) & 0xFF) if w == 1 else s32(word)
+            t["ordinal"] += 1
+            if not is_st:
+                regs[d] = val
+
+        def run(stmts):
+            for s in stmts:
+                if t["stop"]:
+                    return
+                kind = s[0]
+                if kind == "op":
+                    _, opc, d, a, bb, imm = s
+                    if opc == 0x01:
+                        regs[d] = sregs[imm]
+                    elif opc == 0x02:
+                        regs[d] = imm
+                    elif opc == 0x03:
+                        regs[d] = regs[a]
+                    elif opc == 0x04:
+                        regs[d] = regs[bb] if regs[a] != 0 else regs[imm]
+                    elif 0x10 <= opc <= 0x1F:
+                        regs[d] = alu(opc, regs[a], regs[bb])
+                    elif 0x30 <= opc <= 0x3F:
+                        regs[d] = alu(opc - 0x20, regs[a], imm)
+                elif kind == "mem":
+                    _, is_st, d, a, buf, w, site = s
+                    mem(is_st, d, a, buf, w, site)
+                elif kind == "if":
+                    _, a, site, then, els = s
+                    taken = regs[a] != 0
+                    edge(site, int(taken))
+                    run(then if taken else els)
+                else:
+                    _, ctr, a, mx, site, body = s
+                    trip = min(max(regs[a], 0), mx)
+                    i = 0
+                    while True:
+                        edge(site, int(i < trip))
+                        if i >= trip:
+                            break
+                        regs[ctr] = i
+                        run(body)
+                        if t["stop"]:
+                            return
+                        t["back"] += 1
+                        if t["back"] > budget:
+                            t["stop"] = True
+                            st["budget_hit"] = True
+                            return
+                        i += 1
+
+        run(P["body"])
+
+    args = [s32(v) for v in inp["args"]]
+    for bz in range(g[2]):
+        for by in range(g[1]):
+            for bx in range(g[0]):
+                bl = bx + by * g[0] + bz * g[0] * g[1]
+                for tz in range(b[2]):
+                    for ty in range(b[1]):
+                        for tx in range(b[0]):
+                            tl = tx + ty * b[0] + tz * b[0] * b[1]
+                            sregs = [tx, ty, tz, b[0], b[1], b[2], bx, by, bz, g[0], g[1], g[2]] + args
+                            run_thread(bl, tl, [s32(v) for v in sregs])
+    recs = st["records"]
+    fk = min(((r[0] << 32) | (r[1] << 22) | min(r[2], (1 << 22) - 1) for r in recs), default=M64)
+    return dict(status=1 if recs else 0, flags=1 if st["budget_hit"] else 0, records=recs,
+                counts=st["counts"], digest=st["digest"], n_accesses=st["n_accesses"],
+                n_violations=len(recs), first_key=fk, n_branch=st["n_branch"])
+
+
+def bitmap_of(counts: dict) -> dict:
+    return {e: afl_class(n) for e, n in counts.items() if n}

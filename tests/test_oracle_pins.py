@@ -1,0 +1,458 @@
+"""Pins of the CPU oracle to facts that do not come from the oracle itself:
+published hash vectors, AFL's bucket table, the paper's worked examples,
+closed forms for affine kernels, the PREX corner theorem and brute force on
+tiny grids (an independent evaluator, tests/bruteforce.py)."""
+import numpy as np
+import pytest
+
+import bruteforce as bf
+from conftest import golden
+from paper_2601_01048_gb300 import bytecode as bc
+from paper_2601_01048_gb300 import gen
+from paper_2601_01048_gb300.bytecode import Asm, Imm
+
+
+def mk(grid=(1, 1, 1), block=(1, 1, 1), args=(), lens=(), pid=0):
+    a = gen.make_inputs(1)
+    gen.set_input(a[0], pid, grid, block, args, lens)
+    return a[0]
+
+
+def rec_tuples(recs):
+    return [(int(r["block_lin"]), int(r["thread_lin"]), int(r["ordinal"]), int(r["site"]),
+             int(r["buf"]), int(r["kind"]), int(r["width"]), int(r["space"]), int(r["cls"]),
+             int(r["byte_off"])) for r in recs]
+
+
+# ---------------------------------------------------------------- hashing / tables
+
+def test_fmix32_published_vectors(orc):
+    for seed, h in golden("murmur3_fmix32.txt"):
+        assert orc.fmix32(int(seed, 16)) == int(h, 16)
+
+
+def test_splitmix64_published_vectors():
+    for row in golden("splitmix64.txt"):
+        r = gen.SplitMix64(int(row[0]))
+        assert [r.next() for _ in range(3)] == [int(x) for x in row[1:]]
+
+
+def test_bucket_table_matches_afl(orc):
+    for lo, hi, val in golden("afl_buckets.txt"):
+        lo, hi, val = int(lo), int(hi), int(val)
+        for n in {lo, hi, (lo + hi) // 2}:
+            assert orc.bucket(n) == val, n
+    assert orc.bucket(1 << 40) == 128
+
+
+def test_loop_edge_counts_closed_form(orc):
+    """A loop of trip t: the first head decision is edge LOC1 (prev = 0), the
+    t-1 later 'continue' decisions are edge LOC1 ^ (LOC1 >> 1), the exit is
+    LOC0 ^ (LOC1 >> 1); the bitmap holds the AFL bucket of each count."""
+    A = Asm(n_bufs=1)
+    n = A.sreg(bc.ARG0)
+    A.loop(n, 65535)
+    A.endloop()
+    prog = A.build()
+    l0, l1 = bc.loc_of(prog)[0]
+    P = orc.Program(prog)
+    for t in [0, 1, 2, 3, 4, 7, 8, 31, 32, 127, 128, 300]:
+        res, _, bm = orc.run(P, mk(args=(t,)))
+        expect = {}
+        if t == 0:
+            expect[l0] = 1
+        else:
+            for e, c in ((l1, 1), (l1 ^ (l1 >> 1), t - 1), (l0 ^ (l1 >> 1), 1)):
+                expect[e] = expect.get(e, 0) + c
+        want = {e: bf.afl_class(c) for e, c in expect.items() if c}
+        got = {int(e): int(bm[e]) for e in np.nonzero(bm)[0]}
+        assert got == want, t
+        assert int(res["n_branch"]) == t + 1
+
+
+# ---------------------------------------------------------------- worked examples
+
+def test_listing3_paper_worked_example(orc):
+    for n, bs, blk, thr, off in golden("listing3_guarded.txt"):
+        n, bs, blk, thr, off = map(int, (n, bs, blk, thr, off))
+        prog = gen.guarded_plus1_program(bs)
+        grid = -(-n // bs)
+        assert blk == grid - 1 and thr == bs - 2  # the paper's statement for these rows
+        res, recs, _ = orc.run(prog, mk((grid, 1, 1), (bs, 1, 1), (n,), (4 * n,) * 3))
+        assert int(res["status"]) == orc.ST_VIOLATION
+        t = rec_tuples(recs)
+        assert {(r[0], r[1]) for r in t} == {(blk, thr)}
+        assert sorted(r[3] for r in t) == [0, 1, 2]       # all three access sites
+        assert all(r[9] == off and r[8] == orc.CLS_OVERFLOW_RZ for r in t)
+
+
+@pytest.mark.parametrize("n,bs", [(1000, 256), (1024, 256), (1, 32), (257, 128), (5000, 1024)])
+def test_listing3_general_case(orc, n, bs):
+    """For any N >= 1 exactly one thread violates, id = N - 1."""
+    prog = gen.guarded_plus1_program(bs)
+    grid = -(-n // bs)
+    res, recs, _ = orc.run(prog, mk((grid, 1, 1), (bs, 1, 1), (n,), (4 * n,) * 3))
+    t = rec_tuples(recs)
+    assert {(r[0], r[1]) for r in t} == {((n - 1) // bs, (n - 1) % bs)}
+    assert len(t) == 3 and int(res["n_violations"]) == 3
+    assert int(res["n_accesses"]) == 3 * n
+
+
+def test_listing3_zero_n_is_invalid_config(orc):
+    prog = gen.guarded_plus1_program(64)
+    res, _, _ = orc.run(prog, mk((0, 1, 1), (64, 1, 1), (0,), (0,) * 3))
+    assert int(res["status"]) == orc.ST_INVALID_CONFIG
+
+
+def test_listing1_vecadd(orc):
+    per_thread = int(golden("listing1_vecadd.txt")[0][0])
+    bs, nb = 64, 6
+    prog = gen.vecadd_shared_program(bs)
+    nel = bs * nb
+    lens = (4 * nel, 4 * nel, 4 * nel, 4 * bs, 4 * bs)
+    res, recs, _ = orc.run(prog, mk((nb, 1, 1), (bs, 1, 1), (), lens))
+    assert int(res["n_accesses"]) == per_thread * nel
+    assert int(res["n_violations"]) == 0 and int(res["status"]) == orc.ST_OK
+    for short in (0, 1):
+        l2 = list(lens)
+        l2[short] -= 4
+        res, recs, _ = orc.run(prog, mk((nb, 1, 1), (bs, 1, 1), (), l2))
+        t = rec_tuples(recs)
+        assert len(t) == 1 and (t[0][0], t[0][1]) == (nb - 1, bs - 1) and t[0][4] == short
+
+
+# ---------------------------------------------------------------- config 1 closed form
+
+def c1_expect(a0, a1, lens_bytes, threads=8192):
+    hi = min(a0 + threads, a1)
+    g = max(hi - a0, 0)
+    neg = max(min(hi, 0) - a0, 0) if g else 0
+    viol = []
+    for k in range(3):
+        L = lens_bytes[k] // 4
+        over = max(hi - max(L, a0), 0) if g else 0
+        viol.append(neg + over)
+    return g, viol
+
+
+def test_c1_closed_form(orc):
+    prog = gen.c1_program()
+    inputs = gen.c1_inputs(1000)
+    res, recs, bms = orc.run_batch([prog], inputs, rec_cap=1 << 15, bitmaps=True)
+    l0, l1 = bc.loc_of(prog)[0]
+    for k in range(len(inputs)):
+        a0, a1 = int(inputs[k]["args"][0]), int(inputs[k]["args"][1])
+        g, viol = c1_expect(a0, a1, [int(x) for x in inputs[k]["buf_len"]])
+        r = res[k]
+        assert int(r["n_accesses"]) == 3 * g
+        assert int(r["n_violations"]) == sum(viol)
+        assert int(r["n_branch"]) == 8192
+        got = recs[k][: int(r["n_records"])]
+        for site in range(3):
+            assert int((got["site"] == site).sum()) == viol[site]
+        assert np.all(got["cls"][got["byte_off"] < 0] == orc.CLS_UNDERFLOW_RZ)
+        want = {}
+        for e, c in ((l1, g), (l0, 8192 - g)):
+            if c:
+                want[e] = want.get(e, 0) + c
+        bm = bms[k]
+        assert {int(e): int(bm[e]) for e in np.nonzero(bm)[0]} == \
+            {e: bf.afl_class(c) for e, c in want.items()}
+
+
+# ---------------------------------------------------------------- hand-built cases
+
+def unguarded_1d(width=4, n_bufs=1, shared_mask=0, buf=0):
+    A = Asm(n_bufs=n_bufs, shared_mask=shared_mask)
+    i = A.alu(bc.ADD, A.sreg(bc.TID_X), A.sreg(bc.ARG0))
+    A.ld(buf, i, width)
+    return A.build()
+
+
+@pytest.mark.parametrize("k", [1, 5, 64, 100])
+def test_negative_index(orc, k):
+    prog = unguarded_1d()
+    res, recs, _ = orc.run(prog, mk((1, 1, 1), (128, 1, 1), (-k,), (4 * 128,)))
+    t = rec_tuples(recs)
+    assert [r[1] for r in t] == list(range(k))
+    assert [r[9] for r in t] == [4 * (tid - k) for tid in range(k)]
+    for r in t:
+        assert r[8] == (orc.CLS_UNDERFLOW_RZ if r[9] >= -256 else orc.CLS_WILD)
+
+
+def test_other_alloc_and_wild(orc):
+    # A (64 B) at base 256, B (64 B) at base align256(256+64+256) = 768
+    A = Asm(n_bufs=2)
+    A.ld(0, A.sreg(bc.ARG0), 4)
+    prog = A.build()
+    cases = [(128, orc.CLS_OTHER_ALLOC),   # off 512 -> address 768 = start of B
+             (143, orc.CLS_OTHER_ALLOC),   # last word of B
+             (144, orc.CLS_WILD),          # just past B
+             (16, orc.CLS_OVERFLOW_RZ),    # off 64 = len
+             (79, orc.CLS_OVERFLOW_RZ),    # off 316 < len + R = 320
+             (80, orc.CLS_WILD),           # off 320
+             (-64, orc.CLS_UNDERFLOW_RZ),  # off -256 = -R
+             (-65, orc.CLS_WILD)]
+    for idx, cls in cases:
+        _, recs, _ = orc.run(prog, mk(args=(idx,), lens=(64, 64)))
+        assert len(recs) == 1 and int(recs[0]["cls"]) == cls, idx
+
+
+def test_other_alloc_needs_same_space(orc):
+    # buffer 1 shared: an access of global buffer 0 cannot land in it
+    A = Asm(n_bufs=2, shared_mask=0b10)
+    A.ld(0, A.sreg(bc.ARG0), 4)
+    _, recs, _ = orc.run(A.build(), mk(args=(128,), lens=(64, 64)))
+    assert int(recs[0]["cls"]) == orc.CLS_WILD
+
+
+def test_shared_overflow_per_block(orc):
+    prog = unguarded_1d(n_bufs=1, shared_mask=1)
+    bs, nb = 32, 5
+    res, recs, _ = orc.run(prog, mk((nb, 1, 1), (bs, 1, 1), (0,), (4 * bs - 4,)))
+    t = rec_tuples(recs)
+    assert [(r[0], r[1]) for r in t] == [(b, bs - 1) for b in range(nb)]
+    assert all(r[7] == 1 and r[8] == orc.CLS_OVERFLOW_RZ for r in t)
+
+
+def test_zero_length_buffer(orc):
+    prog = unguarded_1d()
+    res, recs, _ = orc.run(prog, mk((2, 1, 1), (16, 1, 1), (0,), (0,)))
+    assert int(res["n_violations"]) == int(res["n_accesses"]) == 32
+
+
+def test_loaded_values_are_seeded_content(orc):
+    """A loaded value steers a branch: the IF is taken iff the loaded word's
+    low bit (fmix32 of seed ^ buf*0x9E3779B9 ^ word) is set."""
+    A = Asm(n_bufs=2, seed=1234)
+    i = A.sreg(bc.TID_X)
+    v = A.ld(1, i, 4)
+    A.if_(A.alu(bc.AND, v, Imm(1)))
+    A.endif()
+    prog = A.build()
+    l0, l1 = bc.loc_of(prog)[0]
+    res, _, bm = orc.run(prog, mk((1, 1, 1), (64, 1, 1), (), (0, 4 * 64)))
+    taken = sum(orc.fmix32(1234 ^ 0x9E3779B9 ^ j) & 1 for j in range(64))
+    assert bm[l1] == bf.afl_class(taken) and bm[l0] == bf.afl_class(64 - taken)
+
+
+INVALID = [((0, 1, 1), (1, 1, 1)), ((1, 0, 1), (1, 1, 1)), ((1, 1, 0), (1, 1, 1)),
+           ((1, 1, 1), (0, 1, 1)), ((1, 1, 1), (1025, 1, 1)), ((1, 1, 1), (1, 1, 65)),
+           ((1, 1, 1), (64, 32, 1)), ((1, 65536, 1), (1, 1, 1)), ((1, 1, 65536), (1, 1, 1)),
+           ((2 ** 31, 1, 1), (1, 1, 1))]
+
+
+@pytest.mark.parametrize("grid,block", INVALID)
+def test_invalid_launch_configs(orc, grid, block):
+    res, recs, bm = orc.run(unguarded_1d(), mk(grid, block, (0,), (4,)))
+    assert int(res["status"]) == orc.ST_INVALID_CONFIG
+    assert int(res["n_accesses"]) == 0 and not bm.any()
+
+
+def test_limit_status(orc):
+    o = orc.opts(max_threads=1000)
+    res, _, _ = orc.run(unguarded_1d(), mk((4, 1, 1), (256, 1, 1), (0,), (4,)), o)
+    assert int(res["status"]) == orc.ST_LIMIT
+    res, _, _ = orc.run(unguarded_1d(), mk((1, 1, 1), (1, 1, 1), (0,), (1 << 48,)))
+    assert int(res["status"]) == orc.ST_LIMIT
+
+
+def test_budget_closed_form(orc):
+    A = Asm(n_bufs=1)
+    a0, a1 = A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    A.loop(a0, 100)
+    j = A.loop(a1, 100)
+    A.ld(0, j, 4)
+    A.endloop()
+    A.endloop()
+    prog = A.build()
+    budget, t0, t1 = 50, 10, 7
+    res, _, _ = orc.run(prog, mk((1, 1, 1), (3, 1, 1), (t0, t1), (4 * 100,)),
+                        orc.opts(iter_budget=budget))
+    bodies = (budget + 1) - (budget + 1) // (t1 + 1)
+    assert int(res["flags"]) & orc.FL_BUDGET
+    assert int(res["n_accesses"]) == 3 * bodies
+    res, _, _ = orc.run(prog, mk((1, 1, 1), (3, 1, 1), (t0, t1), (4 * 100,)),
+                        orc.opts(iter_budget=t0 * (t1 + 1)))
+    assert not int(res["flags"]) & orc.FL_BUDGET and int(res["n_accesses"]) == 3 * t0 * t1
+
+
+def test_overflow_flag_and_exact_count(orc):
+    prog = unguarded_1d()
+    res, recs, _ = orc.run(prog, mk((4, 1, 1), (64, 1, 1), (-1000,), (4,)), rec_cap=10)
+    assert int(res["n_violations"]) == 256 and len(recs) == 10
+    assert int(res["flags"]) & orc.FL_OVERFLOW
+    assert int(res["first_key"]) == 0
+
+
+def test_first_key_packing(orc):
+    prog = gen.guarded_plus1_program(128)
+    res, recs, _ = orc.run(prog, mk((4, 1, 1), (128, 1, 1), (300,), (1200,) * 3))
+    assert int(res["first_key"]) == (2 << 32) | (299 - 256) << 22 | 0
+
+
+# ---------------------------------------------------------------- validation
+
+def _bad_programs():
+    out = {}
+    A = Asm(n_bufs=1)
+    c = A.loop(A.sreg(bc.ARG0), 4)
+    A.raw(bc.ADD | bc.IMM_FORM, c, c, 0, 1)   # writes its own loop counter
+    A.endloop()
+    out["loopctr"] = A.build()
+    good = gen.c1_program()
+    out["truncated"] = good[:-1]
+    b = bytearray(good)
+    b[0] ^= 1
+    out["magic"] = bytes(b)
+    A = Asm(n_bufs=1)
+    A.raw(bc.LD, 0, 0, 0, 3)                  # width 3
+    A.n_regs = 1
+    out["width"] = A.build()
+    A = Asm(n_bufs=1)
+    A.raw(bc.LD, 0, 0, 1, 4)                  # buffer 1 of 1
+    A.n_regs = 1
+    out["buf"] = A.build()
+    A = Asm(n_bufs=1)
+    A.raw(bc.ENDIF)
+    out["unbalanced"] = A.build()
+    A = Asm(n_bufs=1)
+    r = A.imm(1)
+    for _ in range(17):
+        A.if_(r)
+    for _ in range(17):
+        A.endif()
+    out["depth"] = A.build()
+    return out
+
+
+@pytest.mark.parametrize("name", ["loopctr", "truncated", "magic", "width", "buf", "unbalanced",
+                                  "depth"])
+def test_rejects_malformed(orc, name):
+    assert orc.validate(_bad_programs()[name]) < 0
+
+
+# ---------------------------------------------------------------- PREX theorem
+
+def affine_program(rng, dims, n_access):
+    """Unguarded accesses whose indices are sum_d M_d tid_d + N_d ctaid_d + C
+    with thread-invariant coefficients (the paper's affine-access class)."""
+    A = Asm(n_bufs=3)
+    tids = [A.sreg(bc.TID_X + d) for d in range(dims)]
+    ctas = [A.sreg(bc.CTAID_X + d) for d in range(dims)]
+    for _ in range(n_access):
+        acc = A.sreg(bc.ARG0 + rng.below(4))
+        for v in tids + ctas:
+            acc = A.alu(bc.ADD, acc, A.alu(bc.MUL, v, Imm(rng.randint(-6, 6))))
+        acc = A.alu(bc.ADD, acc, Imm(rng.randint(-8, 8)))
+        if rng.chance(0.5):
+            A.ld(rng.below(3), acc, rng.choice(bc.WIDTHS))
+        else:
+            A.st(rng.below(3), acc, acc, rng.choice(bc.WIDTHS))
+    return A.build()
+
+
+def test_prex_corner_theorem(orc):
+    """Sec. 5.1.1 Theorem: in an affine-access kernel with unguarded accesses,
+    if any thread violates at a site then one of the corner threads (each
+    block and thread coordinate first or last) violates there too."""
+    rng = gen.SplitMix64(77)
+    checked = 0
+    for trial in range(60):
+        dims = 1 + trial % 3
+        prog = affine_program(rng, dims, 4)
+        P = orc.Program(prog)
+        for _ in range(4):
+            grid = [rng.randint(1, 5) for _ in range(dims)] + [1] * (3 - dims)
+            block = [rng.randint(1, 6) for _ in range(dims)] + [1] * (3 - dims)
+            args = [rng.randint(-20, 60) for _ in range(4)]
+            lens = [rng.randint(0, 400) for _ in range(3)]
+            res, recs, _ = orc.run(P, mk(grid, block, args, lens), rec_cap=1 << 17)
+            assert int(res["n_records"]) == int(res["n_violations"])
+
+            def corner(lin, ext):
+                c = [lin % ext[0], (lin // ext[0]) % ext[1], lin // (ext[0] * ext[1])]
+                return all(v in (0, e - 1) for v, e in zip(c, ext))
+
+            sites = {int(r["site"]) for r in recs}
+            corner_sites = {int(r["site"]) for r in recs
+                            if corner(int(r["block_lin"]), grid) and corner(int(r["thread_lin"]), block)}
+            assert sites == corner_sites
+            checked += len(sites)
+    assert checked > 20
+
+
+# ---------------------------------------------------------------- brute force
+
+def _compare_bruteforce(orc, prog, inp_kwargs, budget=4096):
+    rec = mk(**inp_kwargs)
+    res, recs, bm = orc.run(prog, rec, orc.opts(iter_budget=budget), rec_cap=1 << 16)
+    ref = bf.evaluate(prog, dict(grid=inp_kwargs["grid"], block=inp_kwargs["block"],
+                                 args=list(inp_kwargs["args"]) + [0] * 4,
+                                 lens=inp_kwargs["lens"]), budget=budget)
+    assert rec_tuples(recs) == ref["records"]
+    assert int(res["digest"]) == ref["digest"]
+    assert int(res["n_accesses"]) == ref["n_accesses"]
+    assert int(res["n_branch"]) == ref["n_branch"]
+    assert int(res["first_key"]) == ref["first_key"]
+    assert int(res["flags"]) & 1 == ref["flags"]
+    assert {int(e): int(bm[e]) for e in np.nonzero(bm)[0]} == bf.bitmap_of(ref["counts"])
+
+
+@pytest.mark.parametrize("index", range(12))
+def test_bruteforce_random_programs(orc, index):
+    prog = gen.c2_program(index)
+    h = bc.decode_header(prog)
+    rng = gen.SplitMix64(1000 + index)
+    for _ in range(2):
+        lens = [rng.choice((0, 1, 4, 16, 64, 256, 1024, 4096)) + rng.randint(-1, 1) * 4
+                for _ in range(h["n_bufs"])]
+        lens = [max(x, 0) for x in lens]
+        args = [rng.choice((0, -1, 1, 3, 16, 255, -7)) for _ in range(4)]
+        _compare_bruteforce(orc, prog, dict(grid=(rng.randint(1, 3), rng.randint(1, 2), 1),
+                                            block=(rng.randint(1, 4), rng.randint(1, 4), 1),
+                                            args=args, lens=lens))
+
+
+@pytest.mark.parametrize("index", range(4))
+def test_bruteforce_branchy_programs(orc, index):
+    prog = gen.c4_program(index)
+    rng = gen.SplitMix64(2000 + index)
+    for _ in range(2):
+        args = [rng.choice((0, -1, 1, 5, 100, 1 << 20, -(1 << 30))) for _ in range(4)]
+        _compare_bruteforce(orc, prog, dict(grid=(rng.randint(1, 3), 1, 1), block=(8, 1, 1),
+                                            args=args, lens=(4 * 4096, 4 * 1024, 64)))
+
+
+def test_bruteforce_budget_and_3d(orc):
+    A = Asm(n_bufs=2, shared_mask=0b10)
+    a0, a1 = A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    tz = A.sreg(bc.TID_Z)
+    bz = A.sreg(bc.CTAID_Z)
+    i = A.loop(a0, 9)
+    A.if_(A.alu(bc.SETLT, i, tz))
+    j = A.loop(a1, 5)
+    A.st(1, A.alu(bc.ADD, j, bz), i, 8)
+    A.endloop()
+    A.else_()
+    A.ld(0, A.alu(bc.SHR, A.alu(bc.SUB, i, Imm(3)), Imm(1)), 1)
+    A.endif()
+    A.endloop()
+    prog = A.build()
+    for budget in (3, 12, 4096):
+        _compare_bruteforce(orc, prog, dict(grid=(1, 2, 2), block=(2, 1, 3), args=(7, 4),
+                                            lens=(5, 24)), budget=budget)
+
+
+def test_batch_equals_single_runs(orc):
+    progs = [gen.c1_program(), gen.c2_program(3)]
+    ins = gen.c1_inputs(6)
+    ins2 = gen.c2_inputs([progs[1]], per_program=3, max_grid=3)
+    ins2["program_id"] = 1
+    allin = np.concatenate([ins, ins2])
+    res, recs, bms = orc.run_batch(progs, allin, rec_cap=4096, bitmaps=True, threads=3)
+    for k in range(len(allin)):
+        r1, rc1, bm1 = orc.run(progs[int(allin[k]["program_id"])], allin[k], rec_cap=4096)
+        assert res[k].tobytes() == r1.tobytes()
+        assert recs[k][: int(r1["n_records"])].tobytes() == rc1.tobytes()
+        assert np.array_equal(bms[k], bm1)
