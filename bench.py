@@ -1,0 +1,408 @@
+#!/usr/bin/env python3
+"""Benchmark of the cufz checked-execution engine on GB300.
+
+Default workload (the random-program configuration): 32 seeded random access
+programs of 20-200 int32 ops, 256 inputs each, 2D grids of up to 256 x 256
+blocks of 16 x 16 threads.  A step is one pass of the whole hot path (load
+already done; admission, staging, interpretation of every test thread,
+bounds checks, record compaction, coverage, finalize) over one batch of
+inputs, run as one persistent launch in a CUDA graph.
+
+Prints one JSON line (rank 0): checked thread-accesses per second, timed with
+CUDA events on the engine's stream (value) and end to end through the C ABI
+with host input records and host result records (e2e), with the roofline of
+the interpreter kernel against the INT32 issue rate and the CPU oracle's rate
+on a bounded sample.  `--impl reference` times the CPU oracle instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "checked thread-accesses/sec"
+UNIT = "checked accesses/s"
+# INT32 issue peak derived from the unit counts: 152 SMs x 4 sub-partitions x
+# 32 lanes per clock, at the maximum SM clock (MEASURED_PEAKS sm_max_mhz).
+N_SM_GB300 = 152
+LANES_PER_SM = 128
+# algorithmic integer ops per checked access and per branch evaluation
+OPS_PER_ACCESS = 5
+OPS_PER_BRANCH = 4
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
+    ap.add_argument("--inputs-per-step", type=int, default=0, help="0: the whole workload")
+    ap.add_argument("--plain", action="store_true", help="one kernel launch per input")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--cta-threads", type=int, default=256)
+    ap.add_argument("--item-threads", type=int, default=0)
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------ workload
+
+def workload(name: str, rank: int = 0):
+    from paper_2601_01048_gb300 import gen
+
+    if name == "c1":
+        return ("c1: 1 guarded 1D program, 1000 inputs, grid 64 x 128",
+                [gen.c1_program()], gen.c1_inputs(1000), 1 << 15)
+    if name == "c2":
+        progs = gen.c2_programs()
+        return ("c2: 32 random access programs (20-200 ops) x 256 inputs, 2D grids up to "
+                "256x256 blocks of 16x16", progs, gen.c2_inputs(progs, 256), 4096)
+    if name == "c3":
+        return ("c3: 4096 inputs over 16 C1-family programs, 1-65536 blocks x 32-1024 threads",
+                gen.c3_programs(), gen.c3_inputs(4096), 4096)
+    progs = gen.c4_programs()
+    return ("c4: 16 branch-heavy programs (<=64 data-dependent sites), 16384 inputs, "
+            "1-1024 blocks x 256", progs, gen.c4_inputs(16384), 1024)
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+# ------------------------------------------------------------------ clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines: list[str] = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.device), "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], 0.0, set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                mx = max(mx, float(p[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if p[5 + k].lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ dist
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+        pg = dist
+    return rank, world, local, pg
+
+
+def barrier(pg):
+    if pg is not None:
+        pg.barrier()
+
+
+def allreduce_max(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def allreduce_sum(pg, x: float, device) -> float:
+    if pg is None:
+        return x
+    import torch
+
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ------------------------------------------------------------------ CPU oracle
+
+def oracle_rate(progs, inputs, seconds: float, seed: int = 11):
+    """Runs the CPU oracle over a seeded random order of the inputs, in chunks
+    over all host cores, until `seconds` have passed; returns (accesses/s,
+    inputs/s, cores, n_inputs, accesses)."""
+    from oracle import oracle
+
+    cores = os.cpu_count() or 1
+    P = [oracle.Program(p) for p in progs]
+    order = np.random.default_rng(seed).permutation(len(inputs))
+    done_acc = 0
+    done_in = 0
+    t0 = time.perf_counter()
+    pos = 0
+    chunk = max(cores, 1)
+    while pos < len(order) and time.perf_counter() - t0 < seconds:
+        sel = inputs[order[pos: pos + chunk]]
+        res, _, _ = oracle.run_batch(P, sel, threads=cores)
+        done_acc += int(res["n_accesses"].sum())
+        done_in += len(sel)
+        pos += chunk
+    dt = time.perf_counter() - t0
+    return done_acc / dt, done_in / dt, cores, done_in, done_acc, dt
+
+
+# ------------------------------------------------------------------ engine arm
+
+def run_engine(args, rank, world, local, pg):
+    import torch
+
+    from paper_2601_01048_gb300 import binding as B
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    wl_name, progs, inputs, cap = workload(args.workload, rank)
+    n_all = len(inputs)
+    per_step = args.inputs_per_step or n_all
+    flags = B.CF_AUTO_RELEASE | (B.CF_PLAIN_LAUNCH if args.plain else 0)
+    E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
+                 cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2)
+    for p in progs:
+        E.load(p)
+    n_batches = (n_all + per_step - 1) // per_step
+    batches = [inputs[(k * per_step) % n_all: (k * per_step) % n_all + per_step]
+               for k in range(n_batches)]
+
+    def step(k):
+        batch = batches[k % n_batches]
+        pos, got = 0, 0
+        acc = np.zeros(len(batch), B.RESULT_DTYPE)
+        lat = []
+        t_sub = time.perf_counter()
+        while got < len(batch):
+            if pos < len(batch):
+                st, n_acc, _ = B.cufz_submit_inputs(E.ctx, batch[pos:])
+                pos += n_acc
+            out = B.cufz_poll_results(E.ctx, len(batch), 2000)
+            now = time.perf_counter()
+            if len(out):
+                acc[got: got + len(out)] = out
+                lat.extend([now - t_sub] * len(out))
+                got += len(out)
+        return acc, lat
+
+    for k in range(args.warmup):
+        step(k)
+    torch.cuda.synchronize(dev)
+    barrier(pg)
+    B.cufz_reset_stats(E.ctx)
+    clocks = ClockSampler(local)
+    clocks.start()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    tot = dict(acc=0, inputs=0, ops=0, br=0, viol=0, threads=0)
+    lats = []
+    h2d = d2h = 0
+    for k in range(args.steps):
+        res, lat = step(args.warmup + k)
+        lats += lat
+        tot["acc"] += int(res["n_accesses"].sum())
+        tot["inputs"] += len(res)
+        tot["ops"] += int(res["n_ops"].sum())
+        tot["br"] += int(res["n_branch"].sum())
+        tot["viol"] += int(res["n_violations"].sum())
+        tot["threads"] += int(res["n_threads"].sum())
+        h2d += len(res) * 128
+        d2h += len(res) * 96
+    torch.cuda.synchronize(dev)
+    t1 = time.perf_counter()
+    barrier(pg)
+    clk = clocks.stop()
+    st = B.cufz_get_stats(E.ctx)
+    kernel_s = st.kernel_ms / 1e3
+    wall_s = t1 - t0
+    kernel_s_max = allreduce_max(pg, kernel_s, dev)
+    wall_s_max = allreduce_max(pg, wall_s, dev)
+    acc_all = allreduce_sum(pg, tot["acc"], dev)
+    inputs_all = allreduce_sum(pg, tot["inputs"], dev)
+    launches = int(st.kernel_launches)
+    E.close()
+
+    peaks = load_peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    n_sm = int(st.n_sms) or N_SM_GB300
+    peak_ops = n_sm * LANES_PER_SM * sm_max * 1e6
+    alg_ops = tot["ops"] + OPS_PER_ACCESS * tot["acc"] + OPS_PER_BRANCH * tot["br"]
+    achieved = alg_ops / kernel_s if kernel_s > 0 else 0.0
+    line = {
+        "metric": METRIC,
+        "value": acc_all / kernel_s_max if kernel_s_max > 0 else 0.0,
+        "unit": UNIT,
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": kernel_s_max * 1e3 / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int32",
+        "data": "synthetic (seeded programs and fuzz inputs)",
+        "config": {
+            "workload": wl_name,
+            "inputs_per_step": per_step,
+            "path": "plain one launch per input" if args.plain else "persistent kernel in a CUDA graph",
+            "cta_threads": int(st.cta_threads),
+            "ctas_per_sm": int(st.ctas_per_sm),
+            "item_threads": int(st.item_threads),
+            "record_cap": cap,
+            "l2": "no flush: every step writes one 64 KiB bitmap per input (>= 512 MiB for the "
+                  "default workload) plus edge counters and records, far above the 129 MB L2",
+            "parallelism": f"replicas x{world}",
+        },
+        "inputs_per_s": inputs_all / kernel_s_max if kernel_s_max > 0 else 0.0,
+        "test_threads_per_step": tot["threads"] // max(args.steps, 1),
+        "violations_per_step": tot["viol"] // max(args.steps, 1),
+        "roofline": {
+            "bound": "alu",
+            "achieved": achieved / 1e12,
+            "peak": peak_ops / 1e12,
+            "unit": "Tops/s (int32 lane-ops)",
+            "frac": achieved / peak_ops,
+            "traffic": None,
+            "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
+            "alg_ops_per_step": alg_ops // max(args.steps, 1),
+        },
+        "e2e": {
+            "value": acc_all / wall_s_max if wall_s_max > 0 else 0.0,
+            "unit": UNIT,
+            "h2d_bytes_per_step": h2d // max(args.steps, 1),
+            "d2h_bytes_per_step": d2h // max(args.steps, 1),
+            "latency_ms": {"p50": 1e3 * float(np.percentile(lats, 50)) if lats else None,
+                           "p99": 1e3 * float(np.percentile(lats, 99)) if lats else None,
+                           "kind": "submit-to-poll within a whole-batch step"},
+        },
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, irate, cores, n_in, n_acc, dt = oracle_rate(progs, inputs, args.cpu_seconds)
+        line["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{n_in} inputs of the same workload in seeded random order, "
+                      f"{n_acc} checked accesses in {dt:.1f} s",
+            "inputs_per_s": irate,
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    wl_name, progs, inputs, cap = workload(args.workload)
+    per = max(args.cpu_seconds / 2.0, 2.0)
+    rates, irates = [], []
+    cores = os.cpu_count() or 1
+    n_tot = acc_tot = 0
+    t_tot = 0.0
+    for k in range(args.warmup + args.steps):
+        rate, irate, cores, n_in, n_acc, dt = oracle_rate(progs, inputs, per, seed=100 + k)
+        if k >= args.warmup:
+            rates.append(rate)
+            irates.append(irate)
+            n_tot += n_in
+            acc_tot += n_acc
+            t_tot += dt
+    value = acc_tot / t_tot
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_tot / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+        "data": "synthetic (seeded programs and fuzz inputs)",
+        "config": {"workload": wl_name, "inputs_per_step": "bounded sample",
+                   "path": "CPU oracle, serial per input, pool over inputs"},
+        "inputs_per_s": n_tot / t_tot,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{args.steps} steps of ~{per:.0f} s, {n_tot} inputs in "
+                                   "seeded random order"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    rank, world, local, pg = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_engine(args, rank, world, local, pg)
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,274 @@
+/*
+ * cufz.h - C ABI of the GB300 checked-execution engine.
+ *
+ * The engine runs a kernel under test, given as an integer access-index
+ * program, over its full grid once per fuzz input; it checks every load and
+ * store against its buffer's bounds and records AFL-style edge coverage.
+ * This is the work the paper moves to the CPU through IR translation and
+ * AddressSanitizer (Sec. 4, Fig. 2: translate, instrument with ASan and AFL,
+ * run every GPU thread of every block) and then reduces with AXIPrune
+ * (Sec. 5.2, Alg. 2).  Here it runs on the GPU, in hand-written sm_103a
+ * kernels.
+ *
+ * Conventions
+ *   - Every entry point returns a cufz_status: 0 on success, a negative
+ *     CUFZ_E_* code otherwise.  Nothing aborts, throws across the ABI or
+ *     traps; all device waits are bounded and surface as CUFZ_E_TIMEOUT.
+ *   - Device memory belongs to the caller: cufz_create receives an arena
+ *     (a device pointer and its size) and the library sub-allocates from it;
+ *     it never calls cudaMalloc.  It allocates pinned host memory for its
+ *     staging and completion buffers and creates its own CUDA streams.
+ *   - The library copies program bytes and input records before a call
+ *     returns; the caller may reuse its buffers at once.
+ *   - Results (records, bitmaps) stay owned by the library until
+ *     cufz_release (or, with CUFZ_CF_AUTO_RELEASE, until polled).
+ *   - A context may be used from several host threads; calls on one
+ *     context are serialised by an internal lock.
+ *
+ * Program format: see the header comment of bytecode.py in the Python
+ * package (32-byte header, LOC table, 8-byte ops).  Input, result and
+ * violation records are the fixed-layout structs below.
+ */
+#ifndef CUFZ_H
+#define CUFZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cufz_ctx cufz_ctx;
+typedef int32_t cufz_status;
+
+/* ---------------------------------------------------------------- status */
+#define CUFZ_OK 0
+#define CUFZ_E_INVALID_ARG (-1)     /* NULL pointer, bad size, bad config field */
+#define CUFZ_E_INVALID_PROGRAM (-2) /* program bytes rejected by the validator */
+#define CUFZ_E_NOMEM (-3)           /* arena too small, or a table is full */
+#define CUFZ_E_BUSY (-4)            /* no free slot: poll, release, resubmit */
+#define CUFZ_E_TIMEOUT (-5)         /* a bounded wait gave up */
+#define CUFZ_E_CUDA (-6)            /* a CUDA runtime call failed */
+#define CUFZ_E_NOT_FOUND (-7)       /* unknown ticket or program id */
+#define CUFZ_E_NO_DEVICE (-8)       /* no usable CUDA device */
+#define CUFZ_E_DEVICE_FAULT (-9)    /* the device reported an internal error word */
+
+/* per-input status (cufz_result.status) */
+#define CUFZ_ST_OK 0
+#define CUFZ_ST_VIOLATION 1      /* at least one out-of-bounds access */
+#define CUFZ_ST_INVALID_CONFIG 2 /* CUDA would reject the launch (Sec. 3.3.1) */
+#define CUFZ_ST_LIMIT 3          /* beyond the engine's limits (max_threads, len >= 2^48) */
+#define CUFZ_ST_BAD_PROGRAM 4    /* program_id names no loaded program */
+
+/* per-input flags (cufz_result.flags) */
+#define CUFZ_FL_BUDGET 1   /* some thread exceeded the back-edge budget (hang analog) */
+#define CUFZ_FL_OVERFLOW 2 /* more violations than record_cap; counts stay exact */
+#define CUFZ_FL_NEW_COV 4  /* bitmap has a bucket bit the epoch's union lacks */
+
+/* violation classes (cufz_violation.cls) */
+#define CUFZ_CLS_UNDERFLOW_RZ 1 /* byte_off in [-R, 0) */
+#define CUFZ_CLS_OVERFLOW_RZ 2  /* access overlaps [len, len + R) */
+#define CUFZ_CLS_OTHER_ALLOC 3  /* lands in another buffer of the same space */
+#define CUFZ_CLS_WILD 4         /* anything else */
+
+/* configuration flags (cufz_config.flags) */
+#define CUFZ_CF_KEEP_BITMAPS 1 /* keep each input's 64 KiB bitmap until released */
+#define CUFZ_CF_PLAIN_LAUNCH 2 /* baseline path: one kernel launch per input */
+#define CUFZ_CF_NO_PRUNE 4     /* run programs unpruned (the pruning check) */
+#define CUFZ_CF_AUTO_RELEASE 8 /* release a slot as soon as its result is polled */
+#define CUFZ_CF_NO_GRAPH 16    /* launch batches directly, not through a CUDA graph */
+#define CUFZ_CF_NO_DIGEST 32   /* skip the per-access digest */
+
+/* Engine configuration.  cufz_config_default fills every field; a zero in
+ * max_slots, item_threads or cta_threads means "choose automatically". */
+typedef struct {
+  int32_t device;        /* CUDA device ordinal */
+  uint32_t flags;        /* CUFZ_CF_* */
+  void* stream;          /* caller's cudaStream_t: the arena is first touched on it */
+  void* arena;           /* device memory owned by the caller, 256-byte aligned */
+  uint64_t arena_bytes;  /* its size */
+  uint32_t max_slots;    /* inputs resident at once (admission limit) */
+  uint32_t record_cap;   /* violation records kept per input */
+  uint32_t redzone;      /* R, bytes, for classification (default 256) */
+  uint32_t iter_budget;  /* back-edges per test thread before it stops (default 4096) */
+  uint64_t max_threads;  /* test threads per input beyond which LIMIT (<= 2^32-1) */
+  uint32_t item_threads; /* test threads per work item (multiple of 32) */
+  uint32_t cta_threads;  /* threads per CTA of the persistent kernel (64..1024) */
+  uint32_t n_lanes;      /* batches that may overlap on the device (1..8) */
+  uint32_t ctas_per_sm;  /* persistent CTAs per SM (0 = from occupancy) */
+} cufz_config;
+
+/* One fuzz input, 128 bytes.  grid/block are the launch shape of the kernel
+ * under test; args its four scalar arguments; buf_len[k] the byte length of
+ * buffer k (for a shared buffer: its size per block). */
+typedef struct {
+  uint32_t program_id;
+  uint32_t grid[3];
+  uint32_t block[3];
+  int32_t args[4];
+  uint32_t reserved;
+  uint64_t buf_len[9];
+  uint64_t user_tag; /* returned unchanged in the result */
+} cufz_input;
+
+/* Result summary of one input, 96 bytes. */
+typedef struct {
+  uint64_t ticket;
+  uint64_t user_tag;
+  int32_t status;        /* CUFZ_ST_* */
+  uint32_t flags;        /* CUFZ_FL_* */
+  uint64_t n_accesses;   /* executed loads + stores (checked thread-accesses) */
+  uint64_t n_violations; /* exact, even when records overflowed */
+  uint64_t first_key;    /* min of block_lin<<32 | thread_lin<<22 | min(ordinal, 2^22-1) */
+  uint64_t digest;       /* sum of per-access hashes mod 2^64 (pruning check) */
+  uint64_t n_branch;     /* branch evaluations (coverage events) */
+  uint64_t n_threads;    /* test threads run */
+  uint64_t n_ops;        /* executed program ops, summed over test threads */
+  uint32_t n_records;    /* records stored (<= record_cap) */
+  uint32_t n_edges;      /* nonzero bitmap entries */
+  uint64_t reserved;
+} cufz_result;
+
+/* One violation record, 32 bytes; ids are linear:
+ * block_lin = bx + by*gx + bz*gx*gy, thread_lin = tx + ty*Bx + tz*Bx*By. */
+typedef struct {
+  uint32_t block_lin;
+  uint32_t thread_lin;
+  uint32_t ordinal; /* accesses this thread executed before this one */
+  uint16_t site;    /* access site: index of the LD/ST among the program's LD/STs */
+  uint8_t buf;
+  uint8_t kind;     /* 0 load, 1 store */
+  uint8_t width;    /* bytes */
+  uint8_t space;    /* 0 global, 1 shared */
+  uint8_t cls;      /* CUFZ_CLS_* */
+  uint8_t pad0;
+  uint32_t pad1;
+  int64_t byte_off; /* index * width */
+} cufz_violation;
+
+/* Statistics of a context since creation (or the last reset). */
+typedef struct {
+  uint64_t inputs_submitted;
+  uint64_t inputs_completed;
+  uint64_t kernel_launches;   /* engine kernels launched */
+  uint64_t graph_launches;    /* of which through CUDA graphs */
+  uint64_t batches;
+  double kernel_ms;           /* device time of engine kernels (CUDA events) */
+  uint32_t cta_threads;       /* launch shape in use */
+  uint32_t ctas_per_sm;
+  uint32_t item_threads;
+  uint32_t n_sms;
+  uint32_t max_slots;
+  uint32_t smem_bytes;
+} cufz_stats;
+
+/* Statistics of a loaded (or pruned) program. */
+typedef struct {
+  uint32_t n_ops_in;     /* ops of the program as given */
+  uint32_t n_ops_kept;   /* ops left after pruning */
+  uint32_t n_regs_in;
+  uint32_t n_regs_alloc; /* device registers after allocation */
+  uint32_t n_access_sites;
+  uint32_t n_branch_sites;
+  uint32_t n_loads_value_dead; /* loads kept as checks whose value is unused */
+  uint32_t reserved;
+} cufz_prog_stats;
+
+/* ------------------------------------------------------------ host-only
+ * These need no GPU. */
+
+/* Fills a configuration with defaults (device 0, no arena). */
+void cufz_config_default(cufz_config* cfg);
+
+/* Bytes of arena needed for n_slots resident inputs under cfg's
+ * record_cap and flags (plus the fixed tables). */
+uint64_t cufz_arena_bytes(const cufz_config* cfg, uint32_t n_slots);
+
+/* Validates program bytes (format, operands, nesting <= 16, loop counters
+ * read-only in their body).  Returns CUFZ_OK or CUFZ_E_INVALID_PROGRAM. */
+cufz_status cufz_validate_program(const void* bytes, size_t nbytes);
+
+/* AXIPrune's MathElimination (Sec. 5.2, Alg. 2) on the program format:
+ * drops every op whose result reaches no access index, branch condition or
+ * loop trip count (stored values are dropped; loads stay as checked
+ * accesses), then renumbers registers.  Writes the pruned program in the
+ * same format to out (capacity out_cap bytes; *out_bytes gets its size).
+ * Every access and branch decision of every thread is unchanged. */
+cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void* out, size_t out_cap,
+                               size_t* out_bytes, cufz_prog_stats* stats);
+
+/* Human-readable name of a status code. */
+const char* cufz_status_str(cufz_status s);
+
+/* ------------------------------------------------------------- context */
+
+/* Creates an engine on cfg->device over cfg->arena.  Clears the arena's
+ * tables on cfg->stream and waits for that.  *out is NULL on failure. */
+cufz_status cufz_create(const cufz_config* cfg, cufz_ctx** out);
+
+/* Waits (bounded) for in-flight work, then frees host-side resources.  The
+ * arena is left to the caller. */
+cufz_status cufz_destroy(cufz_ctx* ctx);
+
+/* Validates, prunes (unless CUFZ_CF_NO_PRUNE), allocates registers and
+ * uploads one program; *program_id receives its id (0, 1, ...).  Programs
+ * stay resident until the context is destroyed.  Up to 256 programs. */
+cufz_status cufz_load_program(cufz_ctx* ctx, const void* bytes, size_t nbytes,
+                              uint32_t* program_id, cufz_prog_stats* stats);
+
+/* Admits a prefix of in[0..n) while slots are free; each admitted input gets
+ * ticket first_ticket + i.  Inputs with an invalid launch configuration,
+ * beyond the limits or naming no program are admitted and complete at once
+ * with their status, without device work.  Returns CUFZ_E_BUSY (with
+ * *n_accepted < n) when it ran out of slots; the caller polls and resubmits
+ * the rest.  The admitted inputs run as one batch: one persistent launch
+ * (through a CUDA graph unless CUFZ_CF_NO_GRAPH), or one launch per input
+ * with CUFZ_CF_PLAIN_LAUNCH.  Batches of successive calls overlap on the
+ * device. */
+cufz_status cufz_submit_inputs(cufz_ctx* ctx, const cufz_input* in, uint32_t n,
+                               uint32_t* n_accepted, uint64_t* first_ticket);
+
+/* Copies up to max completed results (in completion order) to out and sets
+ * *n_out.  Waits up to timeout_us microseconds for the first one when none
+ * is ready (0: do not wait; <0: wait until all submitted inputs are done,
+ * bounded by an internal limit). */
+cufz_status cufz_poll_results(cufz_ctx* ctx, cufz_result* out, uint32_t max, uint32_t* n_out,
+                              int32_t timeout_us);
+
+/* Copies the stored violation records of a completed, unreleased ticket
+ * (in device write order; *n receives min(n_records, cap)). */
+cufz_status cufz_get_records(cufz_ctx* ctx, uint64_t ticket, cufz_violation* out, uint32_t cap,
+                             uint32_t* n);
+
+/* Copies the 64 KiB bucketed edge bitmap of a completed, unreleased ticket
+ * (needs CUFZ_CF_KEEP_BITMAPS). */
+cufz_status cufz_get_bitmap(cufz_ctx* ctx, uint64_t ticket, uint8_t* out65536);
+
+/* Copies the device union bitmap (OR of every completed input's bitmap). */
+cufz_status cufz_get_union(cufz_ctx* ctx, uint8_t* out65536);
+
+/* Waits for all in-flight inputs, then snapshots the union: NEW_COV of later
+ * inputs is measured against this snapshot, which keeps it independent of
+ * completion order.  The first epoch's snapshot is empty. */
+cufz_status cufz_new_epoch(cufz_ctx* ctx);
+
+/* Frees the slot of a completed ticket (records and bitmap go with it). */
+cufz_status cufz_release(cufz_ctx* ctx, uint64_t ticket);
+
+/* Waits until every submitted input has completed (bounded). */
+cufz_status cufz_sync(cufz_ctx* ctx, int32_t timeout_us);
+
+cufz_status cufz_get_stats(cufz_ctx* ctx, cufz_stats* out);
+cufz_status cufz_reset_stats(cufz_ctx* ctx);
+
+/* Measures the INT32 issue rate of device `device` with a kernel of
+ * independent integer add/logic chains on the caller's stream; writes lane
+ * operations per second. */
+cufz_status cufz_int32_peak(int32_t device, void* stream, double* lane_ops_per_s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CUFZ_H */

@@ -32,6 +32,10 @@
  *     trampolines after branches feed a coverage payload).  Counts are then
  *     bucketed: 0,1,2 stay; 3->4; 4-7->8; 8-15->16; 16-31->32; 32-127->64;
  *     >=128->128.
+ *   - LOOP ctr, n, max behaves as C's for (ctr = 0; ctr < trip; ctr++) with
+ *     trip = clamp(n, 0, max) taken once at entry: the counter is 0 on
+ *     entry, 1 more after each body, and equals trip after the exit.  Each
+ *     head decision (ctr < trip) is a branch evaluation.
  *   - A per-thread back-edge budget stands in for the fuzzer's hang timeout
  *     (Sec. 7.1, 10 s per execution): a thread whose back-edge count exceeds
  *     it stops, and the input is flagged BUDGET.
@@ -439,13 +443,14 @@ static void exec_range(orc_ctx* c, int pc, int end) {
         break;
       }
       case OP_LOOP: {
+        /* for (ctr = 0; ctr < trip; ctr++) body;  trip = clamp(n, 0, max) */
         int32_t n = r[o->a];
         int32_t trip = n < 0 ? 0 : (n > o->imm ? o->imm : n);
-        for (int32_t i = 0;; i++) {
-          int cont = i < trip;
+        r[o->dst] = 0;
+        for (;;) {
+          int cont = r[o->dst] < trip;
           cover(c, o->site, cont);
           if (!cont) break;
-          r[o->dst] = i;
           exec_range(c, pc + 1, o->end_pc);
           if (c->stopped) return;
           c->backedges++;
@@ -454,6 +459,7 @@ static void exec_range(orc_ctx* c, int pc, int end) {
             c->res->flags |= ORC_FL_BUDGET;
             return;
           }
+          r[o->dst]++;
         }
         pc = o->end_pc + 1;
         break;

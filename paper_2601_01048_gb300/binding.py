@@ -1,0 +1,358 @@
+"""Thin ctypes binding of the cufz C ABI (include/cufz.h).
+
+The functions named cufz_* marshal arguments to the entry points of the same
+name; every step of the checked execution runs in libcufz.so.  PyTorch only
+supplies the device arena (a uint8 tensor) and the stream.  There is no CPU
+path: if the library cannot be built or loaded, this module raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build_ext
+from .gen import INPUT_DTYPE
+
+# ---------------------------------------------------------------- constants
+OK = 0
+E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUND, \
+    E_NO_DEVICE, E_DEVICE_FAULT = range(-1, -10, -1)
+ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
+FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
+CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST = \
+    1, 2, 4, 8, 16, 32
+
+RESULT_DTYPE = np.dtype([
+    ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),
+    ("n_accesses", "<u8"), ("n_violations", "<u8"), ("first_key", "<u8"), ("digest", "<u8"),
+    ("n_branch", "<u8"), ("n_threads", "<u8"), ("n_ops", "<u8"), ("n_records", "<u4"),
+    ("n_edges", "<u4"), ("reserved", "<u8"),
+])
+assert RESULT_DTYPE.itemsize == 96
+
+VIOLATION_DTYPE = np.dtype([
+    ("block_lin", "<u4"), ("thread_lin", "<u4"), ("ordinal", "<u4"), ("site", "<u2"),
+    ("buf", "u1"), ("kind", "u1"), ("width", "u1"), ("space", "u1"), ("cls", "u1"),
+    ("pad0", "u1"), ("pad1", "<u4"), ("byte_off", "<i8"),
+])
+assert VIOLATION_DTYPE.itemsize == 32
+
+
+class cufz_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("flags", ctypes.c_uint32),
+                ("stream", ctypes.c_void_p), ("arena", ctypes.c_void_p),
+                ("arena_bytes", ctypes.c_uint64), ("max_slots", ctypes.c_uint32),
+                ("record_cap", ctypes.c_uint32), ("redzone", ctypes.c_uint32),
+                ("iter_budget", ctypes.c_uint32), ("max_threads", ctypes.c_uint64),
+                ("item_threads", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
+                ("n_lanes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+
+
+class cufz_stats(ctypes.Structure):
+    _fields_ = [("inputs_submitted", ctypes.c_uint64), ("inputs_completed", ctypes.c_uint64),
+                ("kernel_launches", ctypes.c_uint64), ("graph_launches", ctypes.c_uint64),
+                ("batches", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
+                ("cta_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("item_threads", ctypes.c_uint32), ("n_sms", ctypes.c_uint32),
+                ("max_slots", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32)]
+
+
+class cufz_prog_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint32) for n in (
+        "n_ops_in", "n_ops_kept", "n_regs_in", "n_regs_alloc", "n_access_sites",
+        "n_branch_sites", "n_loads_value_dead", "reserved")]
+
+
+class CufzError(RuntimeError):
+    def __init__(self, status: int, what: str = ""):
+        self.status = status
+        super().__init__(f"{what}: {cufz_status_str(status)} ({status})")
+
+
+_lib = None
+_lock = threading.Lock()
+
+EXPORTS = [
+    "cufz_config_default", "cufz_arena_bytes", "cufz_validate_program", "cufz_prune_program",
+    "cufz_status_str", "cufz_create", "cufz_destroy", "cufz_load_program", "cufz_submit_inputs",
+    "cufz_poll_results", "cufz_get_records", "cufz_get_bitmap", "cufz_get_union",
+    "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
+    "cufz_int32_peak",
+]
+
+
+def lib():
+    """Loads libcufz.so, building it first if the sources are newer."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = build_ext.build()
+            L = ctypes.CDLL(path)
+            vp, sz, u32, u64, i32 = (ctypes.c_void_p, ctypes.c_size_t, ctypes.c_uint32,
+                                     ctypes.c_uint64, ctypes.c_int32)
+            P = ctypes.POINTER
+            sig = {
+                "cufz_config_default": (None, [P(cufz_config)]),
+                "cufz_arena_bytes": (u64, [P(cufz_config), u32]),
+                "cufz_validate_program": (i32, [vp, sz]),
+                "cufz_prune_program": (i32, [vp, sz, vp, sz, P(sz), P(cufz_prog_stats)]),
+                "cufz_status_str": (ctypes.c_char_p, [i32]),
+                "cufz_create": (i32, [P(cufz_config), P(vp)]),
+                "cufz_destroy": (i32, [vp]),
+                "cufz_load_program": (i32, [vp, vp, sz, P(u32), P(cufz_prog_stats)]),
+                "cufz_submit_inputs": (i32, [vp, vp, u32, P(u32), P(u64)]),
+                "cufz_poll_results": (i32, [vp, vp, u32, P(u32), i32]),
+                "cufz_get_records": (i32, [vp, u64, vp, u32, P(u32)]),
+                "cufz_get_bitmap": (i32, [vp, u64, vp]),
+                "cufz_get_union": (i32, [vp, vp]),
+                "cufz_new_epoch": (i32, [vp]),
+                "cufz_release": (i32, [vp, u64]),
+                "cufz_sync": (i32, [vp, i32]),
+                "cufz_get_stats": (i32, [vp, P(cufz_stats)]),
+                "cufz_reset_stats": (i32, [vp]),
+                "cufz_int32_peak": (i32, [i32, vp, P(ctypes.c_double)]),
+            }
+            for name, (res, args) in sig.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(st: int, what: str) -> int:
+    if st < 0:
+        raise CufzError(st, what)
+    return st
+
+
+def _bytes_ptr(b: bytes):
+    return ctypes.cast(ctypes.c_char_p(b), ctypes.c_void_p)
+
+
+# ------------------------------------------------------------ ABI mirrors
+
+def cufz_status_str(st: int) -> str:
+    return lib().cufz_status_str(st).decode()
+
+
+def cufz_config_default() -> cufz_config:
+    c = cufz_config()
+    lib().cufz_config_default(ctypes.byref(c))
+    return c
+
+
+def cufz_arena_bytes(cfg: cufz_config, n_slots: int) -> int:
+    return lib().cufz_arena_bytes(ctypes.byref(cfg), n_slots)
+
+
+def cufz_validate_program(prog: bytes) -> int:
+    return lib().cufz_validate_program(_bytes_ptr(prog), len(prog))
+
+
+def cufz_prune_program(prog: bytes) -> tuple[bytes, cufz_prog_stats]:
+    cap = len(prog) + 64
+    out = ctypes.create_string_buffer(cap)
+    n = ctypes.c_size_t(0)
+    st = cufz_prog_stats()
+    _check(lib().cufz_prune_program(_bytes_ptr(prog), len(prog), out, cap, ctypes.byref(n),
+                                    ctypes.byref(st)), "cufz_prune_program")
+    return out.raw[: n.value], st
+
+
+def cufz_create(cfg: cufz_config):
+    h = ctypes.c_void_p()
+    _check(lib().cufz_create(ctypes.byref(cfg), ctypes.byref(h)), "cufz_create")
+    return h
+
+
+def cufz_destroy(ctx) -> None:
+    _check(lib().cufz_destroy(ctx), "cufz_destroy")
+
+
+def cufz_load_program(ctx, prog: bytes) -> tuple[int, cufz_prog_stats]:
+    pid = ctypes.c_uint32(0)
+    st = cufz_prog_stats()
+    _check(lib().cufz_load_program(ctx, _bytes_ptr(prog), len(prog), ctypes.byref(pid),
+                                   ctypes.byref(st)), "cufz_load_program")
+    return pid.value, st
+
+
+def cufz_submit_inputs(ctx, inputs: np.ndarray) -> tuple[int, int, int]:
+    """Returns (status, n_accepted, first_ticket); BUSY is not an error."""
+    inputs = np.ascontiguousarray(inputs, dtype=INPUT_DTYPE)
+    acc = ctypes.c_uint32(0)
+    first = ctypes.c_uint64(0)
+    st = lib().cufz_submit_inputs(ctx, inputs.ctypes.data, len(inputs), ctypes.byref(acc),
+                                  ctypes.byref(first))
+    if st < 0 and st != E_BUSY:
+        raise CufzError(st, "cufz_submit_inputs")
+    return st, acc.value, first.value
+
+
+def cufz_poll_results(ctx, max_results: int, timeout_us: int = 0) -> np.ndarray:
+    out = np.zeros(max_results, RESULT_DTYPE)
+    n = ctypes.c_uint32(0)
+    st = lib().cufz_poll_results(ctx, out.ctypes.data, max_results, ctypes.byref(n), timeout_us)
+    if st < 0:
+        raise CufzError(st, "cufz_poll_results")
+    return out[: n.value]
+
+
+def cufz_get_records(ctx, ticket: int, cap: int) -> np.ndarray:
+    out = np.zeros(max(cap, 1), VIOLATION_DTYPE)
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_get_records(ctx, ticket, out.ctypes.data, cap, ctypes.byref(n)),
+           "cufz_get_records")
+    return out[: n.value]
+
+
+def cufz_get_bitmap(ctx, ticket: int) -> np.ndarray:
+    out = np.zeros(65536, np.uint8)
+    _check(lib().cufz_get_bitmap(ctx, ticket, out.ctypes.data), "cufz_get_bitmap")
+    return out
+
+
+def cufz_get_union(ctx) -> np.ndarray:
+    out = np.zeros(65536, np.uint8)
+    _check(lib().cufz_get_union(ctx, out.ctypes.data), "cufz_get_union")
+    return out
+
+
+def cufz_new_epoch(ctx) -> None:
+    _check(lib().cufz_new_epoch(ctx), "cufz_new_epoch")
+
+
+def cufz_release(ctx, ticket: int) -> None:
+    _check(lib().cufz_release(ctx, ticket), "cufz_release")
+
+
+def cufz_sync(ctx, timeout_us: int = -1) -> None:
+    _check(lib().cufz_sync(ctx, timeout_us), "cufz_sync")
+
+
+def cufz_get_stats(ctx) -> cufz_stats:
+    s = cufz_stats()
+    _check(lib().cufz_get_stats(ctx, ctypes.byref(s)), "cufz_get_stats")
+    return s
+
+
+def cufz_reset_stats(ctx) -> None:
+    _check(lib().cufz_reset_stats(ctx), "cufz_reset_stats")
+
+
+def cufz_int32_peak(device: int = 0, stream: int = 0) -> float:
+    v = ctypes.c_double(0)
+    _check(lib().cufz_int32_peak(device, ctypes.c_void_p(stream), ctypes.byref(v)),
+           "cufz_int32_peak")
+    return v.value
+
+
+# ------------------------------------------------------------ convenience
+
+class Engine:
+    """One cufz context over a torch-allocated arena on one device."""
+
+    def __init__(self, device: int = 0, arena_bytes: int | None = None, max_slots: int = 0,
+                 record_cap: int = 4096, flags: int = CF_KEEP_BITMAPS, redzone: int = 256,
+                 iter_budget: int = 4096, max_threads: int = 1 << 31, cta_threads: int = 256,
+                 item_threads: int = 0, n_lanes: int = 4, ctas_per_sm: int = 0):
+        import torch
+
+        if not torch.cuda.is_available():
+            raise CufzError(E_NO_DEVICE, "Engine")
+        self.device = device
+        cfg = cufz_config_default()
+        cfg.device = device
+        cfg.flags = flags
+        cfg.record_cap = record_cap
+        cfg.redzone = redzone
+        cfg.iter_budget = iter_budget
+        cfg.max_threads = max_threads
+        cfg.cta_threads = cta_threads
+        cfg.item_threads = item_threads
+        cfg.n_lanes = n_lanes
+        cfg.ctas_per_sm = ctas_per_sm
+        cfg.max_slots = max_slots
+        if arena_bytes is None:
+            arena_bytes = cufz_arena_bytes(cfg, max_slots or 1024)
+        self.arena = torch.empty(int(arena_bytes), dtype=torch.uint8, device=f"cuda:{device}")
+        self.stream = torch.cuda.current_stream(device)
+        cfg.arena = self.arena.data_ptr()
+        cfg.arena_bytes = int(arena_bytes)
+        cfg.stream = self.stream.cuda_stream
+        self.cfg = cfg
+        self.record_cap = record_cap
+        self.ctx = cufz_create(cfg)
+        self.prog_stats: list[cufz_prog_stats] = []
+
+    def close(self) -> None:
+        if getattr(self, "ctx", None):
+            cufz_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def load(self, prog: bytes) -> int:
+        pid, st = cufz_load_program(self.ctx, prog)
+        self.prog_stats.append(st)
+        return pid
+
+    def run(self, inputs: np.ndarray, records: bool = True, bitmaps: bool = True,
+            release: bool = True, timeout_s: float = 600.0):
+        """Submits every input (resubmitting as slots free up), waits for all
+        results and returns (results sorted by ticket order of `inputs`,
+        list of record arrays or None, bitmaps [n, 65536] or None)."""
+        import time
+
+        inputs = np.ascontiguousarray(inputs, dtype=INPUT_DTYPE)
+        n = len(inputs)
+        res = np.zeros(n, RESULT_DTYPE)
+        recs = [None] * n if records else None
+        bms = np.zeros((n, 65536), np.uint8) if bitmaps else None
+        ticket_to_idx = {}
+        pos = 0
+        got = 0
+        t_end = time.time() + timeout_s
+        while got < n:
+            if pos < n:
+                st, acc, first = cufz_submit_inputs(self.ctx, inputs[pos:])
+                for k in range(acc):
+                    ticket_to_idx[first + k] = pos + k
+                pos += acc
+            out = cufz_poll_results(self.ctx, 4096, 200 if pos < n else 20000)
+            for r in out:
+                i = ticket_to_idx.pop(int(r["ticket"]))
+                res[i] = r
+                t = int(r["ticket"])
+                if records:
+                    recs[i] = cufz_get_records(self.ctx, t, int(r["n_records"]))
+                if bitmaps:
+                    bms[i] = cufz_get_bitmap(self.ctx, t)
+                if release:
+                    cufz_release(self.ctx, t)
+                got += 1
+            if time.time() > t_end:
+                raise CufzError(E_TIMEOUT, "Engine.run")
+        return res, recs, bms
+
+    def union(self) -> np.ndarray:
+        return cufz_get_union(self.ctx)
+
+    def new_epoch(self) -> None:
+        cufz_new_epoch(self.ctx)
+
+    def stats(self) -> cufz_stats:
+        return cufz_get_stats(self.ctx)

@@ -1,0 +1,687 @@
+// Program loader of the cufz engine: decodes and validates the program
+// format, prunes it (AXIPrune's MathElimination, Sec. 5.2, Alg. 2: an op
+// whose result reaches no memory-access index and no branch stays out),
+// allocates device registers and emits the device program blob.
+//
+// The prune is a backward slice computed by liveness over the structured
+// control-flow graph: roots are every load/store index, every IF condition
+// and every LOOP trip expression; stored values are not roots (stores are
+// checked, not performed); loads stay as checked accesses even when their
+// value is dead.  Every access of every thread therefore keeps its index,
+// site and ordinal, and every branch keeps its decision (Sec. 5.2, "all
+// memory accesses are preserved exactly as in the original GPU program").
+#include <algorithm>
+#include <cstdint>
+#include <cstdlib>
+#include <cstring>
+#include <vector>
+
+#include "engine.h"
+
+namespace cufz {
+namespace {
+
+enum : uint8_t {
+  B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04,
+  B_LD = 0x40, B_ST = 0x41, B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53,
+  B_ENDLOOP = 0x54
+};
+constexpr uint32_t kMagic = 0x315A4643u;
+
+inline bool is_alu_reg(uint8_t o) { return o >= 0x10 && o <= 0x1F; }
+inline bool is_alu_imm(uint8_t o) { return o >= 0x30 && o <= 0x3F; }
+
+// Virtual registers: 0..255 program registers, 256..271 special registers
+// (materialised at thread start), 272.. hidden loop-trip registers.
+constexpr int kSregBase = 256;
+constexpr int kTripBase = 272;
+
+struct IrOp {
+  uint8_t opc = 0;     // program-format opcode
+  int dst = -1, a = -1, b = -1, c = -1;
+  int32_t imm = 0;
+  int else_pc = -1, end_pc = -1, head_pc = -1;  // structure (head_pc: the IF/LOOP of an ELSE/ENDIF/ENDLOOP)
+  int site = -1;       // branch site (IF/LOOP) or access site (LD/ST)
+  int depth = 0;       // nesting depth of the op itself
+  int trip = -1;       // hidden trip vreg (LOOP, ENDLOOP)
+  bool kept = true;
+  bool value_dead = false;
+  int sreg = -1;       // SREG id (format level)
+  int buf = -1;
+  int width = 0;
+};
+
+struct Ir {
+  int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0;
+  uint32_t shared_mask = 0, seed = 0;
+  std::vector<uint16_t> loc0, loc1;
+  std::vector<IrOp> ops;
+  int nv = 0;  // vreg count (kTripBase + loops)
+};
+
+uint16_t get16(const uint8_t* p) { return (uint16_t)(p[0] | (p[1] << 8)); }
+uint32_t get32(const uint8_t* p) {
+  return (uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) | ((uint32_t)p[3] << 24);
+}
+
+bool width_ok(int32_t w) { return w == 1 || w == 4 || w == 8 || w == 16; }
+
+// Decodes and validates; false on any violation of the format.
+bool decode(const uint8_t* p, size_t n, Ir* ir) {
+  if (!p || n < 32) return false;
+  if (get32(p) != kMagic || get16(p + 4) != 1) return false;
+  int n_ops = get16(p + 6);
+  ir->n_regs = p[8];
+  ir->n_bufs = p[9];
+  ir->n_sites = p[10];
+  ir->shared_mask = get16(p + 12);
+  ir->seed = get32(p + 16);
+  if (p[11] || get16(p + 14) || get32(p + 20) || get32(p + 24) || get32(p + 28)) return false;
+  if (n_ops < 1 || n_ops > kMaxOps || ir->n_bufs > kMaxBufs) return false;
+  if (ir->shared_mask >> ir->n_bufs) return false;
+  if (n != 32u + 4u * (size_t)ir->n_sites + 8u * (size_t)n_ops) return false;
+  ir->loc0.resize(ir->n_sites);
+  ir->loc1.resize(ir->n_sites);
+  for (int s = 0; s < ir->n_sites; s++) {
+    ir->loc0[s] = get16(p + 32 + 4 * s);
+    ir->loc1[s] = get16(p + 34 + 4 * s);
+  }
+  const uint8_t* q = p + 32 + 4 * ir->n_sites;
+  ir->ops.resize(n_ops);
+  std::vector<int> open;
+  int bsites = 0, asites = 0, loops = 0;
+  const int R = ir->n_regs;
+  auto reg = [R](int r) { return r < R; };
+  for (int pc = 0; pc < n_ops; pc++) {
+    const uint8_t* w = q + 8 * pc;
+    IrOp& o = ir->ops[pc];
+    uint8_t opc = w[0];
+    int d = w[1], a = w[2], b = w[3];
+    int32_t imm = (int32_t)get32(w + 4);
+    o.opc = opc;
+    o.imm = imm;
+    o.depth = (int)open.size();
+    bool ok = false;
+    if (is_alu_reg(opc)) {
+      ok = reg(d) && reg(a) && reg(b) && imm == 0;
+      o.dst = d; o.a = a; o.b = b;
+    } else if (is_alu_imm(opc)) {
+      ok = reg(d) && reg(a) && b == 0;
+      o.dst = d; o.a = a;
+    } else {
+      switch (opc) {
+        case B_NOP:
+          ok = !d && !a && !b && !imm;
+          o.kept = false;
+          break;
+        case B_SREG:
+          ok = reg(d) && !a && !b && imm >= 0 && imm <= 15;
+          o.dst = d; o.sreg = imm;
+          break;
+        case B_IMM:
+          ok = reg(d) && !a && !b;
+          o.dst = d;
+          break;
+        case B_MOV:
+          ok = reg(d) && reg(a) && !b && !imm;
+          o.dst = d; o.a = a;
+          break;
+        case B_SEL:
+          ok = reg(d) && reg(a) && reg(b) && imm >= 0 && imm < R;
+          o.dst = d; o.a = a; o.b = b; o.c = imm;
+          break;
+        case B_LD:
+        case B_ST:
+          ok = reg(d) && reg(a) && b < ir->n_bufs && width_ok(imm);
+          if (opc == B_LD) o.dst = d; else o.b = d;  // ST: value register, never a root
+          o.a = a; o.buf = b; o.width = imm; o.site = asites++;
+          break;
+        case B_IF:
+          ok = !d && reg(a) && !b && !imm && (int)open.size() < kMaxDepth;
+          o.a = a; o.site = bsites++;
+          if (ok) open.push_back(pc);
+          break;
+        case B_LOOP:
+          ok = reg(d) && reg(a) && !b && imm >= 0 && imm <= 65535 && (int)open.size() < kMaxDepth;
+          o.dst = d; o.a = a; o.site = bsites++; o.trip = kTripBase + loops++;
+          if (ok) open.push_back(pc);
+          break;
+        case B_ELSE:
+          ok = !d && !a && !b && !imm && !open.empty() && ir->ops[open.back()].opc == B_IF &&
+               ir->ops[open.back()].else_pc < 0;
+          if (ok) {
+            ir->ops[open.back()].else_pc = pc;
+            o.head_pc = open.back();
+            o.depth = (int)open.size() - 1;
+          }
+          break;
+        case B_ENDIF:
+          ok = !d && !a && !b && !imm && !open.empty() && ir->ops[open.back()].opc == B_IF;
+          if (ok) {
+            o.head_pc = open.back();
+            ir->ops[open.back()].end_pc = pc;
+            open.pop_back();
+            o.depth = (int)open.size();
+          }
+          break;
+        case B_ENDLOOP:
+          ok = !d && !a && !b && !imm && !open.empty() && ir->ops[open.back()].opc == B_LOOP;
+          if (ok) {
+            o.head_pc = open.back();
+            ir->ops[open.back()].end_pc = pc;
+            open.pop_back();
+            o.depth = (int)open.size();
+          }
+          break;
+        default:
+          ok = false;
+      }
+    }
+    if (!ok) return false;
+  }
+  if (!open.empty() || bsites != ir->n_sites) return false;
+  for (auto& o : ir->ops) {
+    if (o.opc == B_ELSE) o.end_pc = ir->ops[o.head_pc].end_pc;
+    if (o.opc == B_ENDLOOP) {
+      const IrOp& h = ir->ops[o.head_pc];
+      o.dst = h.dst;
+      o.trip = h.trip;
+      o.site = h.site;
+    }
+  }
+  // a loop counter is read-only in its own body
+  for (int pc = 0; pc < n_ops; pc++) {
+    const IrOp& h = ir->ops[pc];
+    if (h.opc != B_LOOP) continue;
+    for (int j = pc + 1; j < h.end_pc; j++) {
+      const IrOp& o = ir->ops[j];
+      bool writes = (o.opc == B_SREG || o.opc == B_IMM || o.opc == B_MOV || o.opc == B_SEL ||
+                     o.opc == B_LD || o.opc == B_LOOP || is_alu_reg(o.opc) || is_alu_imm(o.opc));
+      if (writes && o.dst == h.dst) return false;
+    }
+  }
+  ir->n_access = asites;
+  ir->n_loops = loops;
+  ir->nv = kTripBase + loops;
+  return true;
+}
+
+// ------------------------------------------------------------ dataflow
+
+struct Bits {
+  std::vector<uint64_t> w;
+  explicit Bits(int n = 0) : w((n + 63) / 64, 0) {}
+  void set(int i) { w[i >> 6] |= 1ull << (i & 63); }
+  void clr(int i) { w[i >> 6] &= ~(1ull << (i & 63)); }
+  bool get(int i) const { return (w[i >> 6] >> (i & 63)) & 1; }
+  bool operator==(const Bits& o) const { return w == o.w; }
+  void or_with(const Bits& o) {
+    for (size_t k = 0; k < w.size(); k++) w[k] |= o.w[k];
+  }
+};
+
+// Uses and defs of one op.  `sreg_as_pseudo`: SREG reads its special
+// register (device IR) instead of being a constant def (format level).
+void uses_defs(const IrOp& o, bool device_ir, int* U, int* nu, int* D, int* nd) {
+  *nu = *nd = 0;
+  if (!o.kept) return;
+  uint8_t opc = o.opc;
+  if (is_alu_reg(opc)) {
+    U[(*nu)++] = o.a; U[(*nu)++] = o.b; D[(*nd)++] = o.dst;
+    return;
+  }
+  if (is_alu_imm(opc)) {
+    U[(*nu)++] = o.a; D[(*nd)++] = o.dst;
+    return;
+  }
+  switch (opc) {
+    case B_SREG:
+      if (device_ir) U[(*nu)++] = kSregBase + o.sreg;
+      D[(*nd)++] = o.dst;
+      break;
+    case B_IMM: D[(*nd)++] = o.dst; break;
+    case B_MOV: U[(*nu)++] = o.a; D[(*nd)++] = o.dst; break;
+    case B_SEL: U[(*nu)++] = o.a; U[(*nu)++] = o.b; U[(*nu)++] = o.c; D[(*nd)++] = o.dst; break;
+    case B_LD:
+      U[(*nu)++] = o.a;
+      if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
+      break;
+    case B_ST: U[(*nu)++] = o.a; break;
+    case B_IF: U[(*nu)++] = o.a; break;
+    case B_LOOP:
+      U[(*nu)++] = o.a;
+      D[(*nd)++] = o.dst;
+      if (device_ir) D[(*nd)++] = o.trip;
+      break;
+    case B_ENDLOOP:
+      U[(*nu)++] = o.dst;
+      if (device_ir) U[(*nu)++] = o.trip;
+      D[(*nd)++] = o.dst;
+      break;
+    default: break;
+  }
+}
+
+int successors(const Ir& ir, int pc, int* S) {
+  const IrOp& o = ir.ops[pc];
+  int n = 0;
+  int N = (int)ir.ops.size();
+  auto push = [&](int t) {
+    if (t < N) S[n++] = t;
+  };
+  switch (o.opc) {
+    case B_IF:
+      push(pc + 1);
+      push(o.else_pc >= 0 ? o.else_pc + 1 : o.end_pc);
+      break;
+    case B_ELSE: push(o.end_pc); break;
+    case B_LOOP: push(pc + 1); push(o.end_pc + 1); break;
+    case B_ENDLOOP: push(o.head_pc + 1); push(pc + 1); break;
+    default: push(pc + 1); break;
+  }
+  return n;
+}
+
+struct Liveness {
+  std::vector<Bits> in, out;
+};
+
+Liveness liveness(const Ir& ir, bool device_ir) {
+  int N = (int)ir.ops.size();
+  Liveness L;
+  L.in.assign(N, Bits(ir.nv));
+  L.out.assign(N, Bits(ir.nv));
+  bool changed = true;
+  int U[4], D[4], S[2], nu, nd;
+  while (changed) {
+    changed = false;
+    for (int pc = N - 1; pc >= 0; pc--) {
+      Bits out(ir.nv);
+      int ns = successors(ir, pc, S);
+      for (int k = 0; k < ns; k++) out.or_with(L.in[S[k]]);
+      uses_defs(ir.ops[pc], device_ir, U, &nu, D, &nd);
+      Bits in = out;
+      for (int k = 0; k < nd; k++) in.clr(D[k]);
+      for (int k = 0; k < nu; k++) in.set(U[k]);
+      if (!(out == L.out[pc]) || !(in == L.in[pc])) {
+        L.out[pc] = std::move(out);
+        L.in[pc] = std::move(in);
+        changed = true;
+      }
+    }
+  }
+  return L;
+}
+
+bool is_value_op(uint8_t opc) {
+  return opc == B_SREG || opc == B_IMM || opc == B_MOV || opc == B_SEL || is_alu_reg(opc) ||
+         is_alu_imm(opc);
+}
+
+// MathElimination: drop value ops whose result is dead, to a fixed point.
+void prune(Ir* ir) {
+  for (;;) {
+    Liveness L = liveness(*ir, false);
+    bool changed = false;
+    for (size_t pc = 0; pc < ir->ops.size(); pc++) {
+      IrOp& o = ir->ops[pc];
+      if (o.kept && is_value_op(o.opc) && !L.out[pc].get(o.dst)) {
+        o.kept = false;
+        changed = true;
+      }
+    }
+    if (!changed) {
+      for (size_t pc = 0; pc < ir->ops.size(); pc++) {
+        IrOp& o = ir->ops[pc];
+        if (o.opc == B_LD) o.value_dead = !L.out[pc].get(o.dst);
+      }
+      return;
+    }
+  }
+}
+
+// Replaces uses of a register defined once, at depth 0, by SREG id, with the
+// special register itself (the def dominates every later use).
+void propagate_sregs(Ir* ir) {
+  int N = (int)ir->ops.size();
+  std::vector<int> ndefs(256, 0), defpc(256, -1);
+  int U[4], D[4], nu, nd;
+  for (int pc = 0; pc < N; pc++) {
+    uses_defs(ir->ops[pc], true, U, &nu, D, &nd);
+    for (int k = 0; k < nd; k++)
+      if (D[k] < 256) {
+        ndefs[D[k]]++;
+        defpc[D[k]] = pc;
+      }
+  }
+  for (int r = 0; r < 256; r++) {
+    if (ndefs[r] != 1) continue;
+    IrOp& def = ir->ops[defpc[r]];
+    if (def.opc != B_SREG || def.depth != 0) continue;
+    int pseudo = kSregBase + def.sreg;
+    bool early_use = false;
+    for (int pc = 0; pc <= defpc[r] && !early_use; pc++) {
+      uses_defs(ir->ops[pc], true, U, &nu, D, &nd);
+      for (int k = 0; k < nu; k++) early_use |= (U[k] == r);
+    }
+    if (early_use) continue;
+    for (int pc = defpc[r] + 1; pc < N; pc++) {
+      IrOp& o = ir->ops[pc];
+      if (!o.kept) continue;
+      if (o.a == r) o.a = pseudo;
+      if (o.c == r) o.c = pseudo;
+      if (o.b == r && o.opc != B_ST) o.b = pseudo;
+      if (o.opc == B_ST && o.b == r) o.b = -1;
+    }
+    def.kept = false;
+  }
+}
+
+// Interval register allocation: each vreg's live range is the hull of the
+// pcs where it is live or defined; overlapping hulls get distinct registers.
+// Returns the register count; map[v] = register or -1.
+int allocate(const Ir& ir, bool device_ir, std::vector<int>* map, Bits* live_at_entry) {
+  int N = (int)ir.ops.size();
+  Liveness L = liveness(ir, device_ir);
+  std::vector<int> lo(ir.nv, N + 1), hi(ir.nv, -1);
+  int U[4], D[4], nu, nd;
+  auto touch = [&](int v, int pc) {
+    lo[v] = std::min(lo[v], pc);
+    hi[v] = std::max(hi[v], pc);
+  };
+  for (int pc = 0; pc < N; pc++) {
+    for (int v = 0; v < ir.nv; v++)
+      if (L.in[pc].get(v) || L.out[pc].get(v)) touch(v, pc);
+    uses_defs(ir.ops[pc], device_ir, U, &nu, D, &nd);
+    for (int k = 0; k < nu; k++) touch(U[k], pc);
+    for (int k = 0; k < nd; k++) touch(D[k], pc);
+  }
+  *live_at_entry = N ? L.in[0] : Bits(ir.nv);
+  std::vector<int> order;
+  for (int v = 0; v < ir.nv; v++)
+    if (hi[v] >= 0) {
+      if (v >= kSregBase && v < kTripBase) lo[v] = -1;  // defined by the prologue
+      order.push_back(v);
+    }
+  std::sort(order.begin(), order.end(), [&](int x, int y) {
+    return lo[x] != lo[y] ? lo[x] < lo[y] : x < y;
+  });
+  map->assign(ir.nv, -1);
+  std::vector<int> reg_end;  // last pc of the interval occupying each register
+  for (int v : order) {
+    int r = -1;
+    for (size_t k = 0; k < reg_end.size(); k++)
+      if (reg_end[k] < lo[v]) {
+        r = (int)k;
+        break;
+      }
+    if (r < 0) {
+      r = (int)reg_end.size();
+      reg_end.push_back(0);
+    }
+    reg_end[r] = hi[v];
+    (*map)[v] = r;
+  }
+  return (int)reg_end.size();
+}
+
+void put16(std::vector<uint8_t>& v, uint16_t x) {
+  v.push_back(x & 0xFF);
+  v.push_back(x >> 8);
+}
+void put32(std::vector<uint8_t>& v, uint32_t x) {
+  for (int k = 0; k < 4; k++) v.push_back((x >> (8 * k)) & 0xFF);
+}
+
+int log2w(int w) { return w == 1 ? 0 : w == 4 ? 2 : w == 8 ? 3 : 4; }
+
+void fill_stats(const Ir& ir, int n_in, int regs_alloc, cufz_prog_stats* st) {
+  if (!st) return;
+  memset(st, 0, sizeof(*st));
+  st->n_ops_in = (uint32_t)n_in;
+  uint32_t kept = 0, dead = 0;
+  for (const auto& o : ir.ops) {
+    if (o.kept && o.opc != B_NOP) kept++;
+    if (o.kept && o.opc == B_LD && o.value_dead) dead++;
+  }
+  st->n_ops_kept = kept;
+  st->n_regs_in = (uint32_t)ir.n_regs;
+  st->n_regs_alloc = (uint32_t)regs_alloc;
+  st->n_access_sites = (uint32_t)ir.n_access;
+  st->n_branch_sites = (uint32_t)ir.n_sites;
+  st->n_loads_value_dead = dead;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- public
+
+cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
+  Ir ir;
+  if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  int n_in = (int)ir.ops.size();
+  if (do_prune) {
+    prune(&ir);
+  } else {
+    Liveness L = liveness(ir, false);
+    for (size_t pc = 0; pc < ir.ops.size(); pc++)
+      if (ir.ops[pc].opc == B_LD) ir.ops[pc].value_dead = !L.out[pc].get(ir.ops[pc].dst);
+  }
+  propagate_sregs(&ir);
+  std::vector<int> map;
+  Bits entry;
+  int n_regs = allocate(ir, true, &map, &entry);
+  if (n_regs > kMaxPhysRegs) return CUFZ_E_INVALID_PROGRAM;
+
+  // device ops
+  int N = (int)ir.ops.size();
+  std::vector<int> dpc(N + 1, -1);
+  int nd = 0;
+  for (int pc = 0; pc < N; pc++) {
+    dpc[pc] = nd;
+    if (ir.ops[pc].kept) nd++;
+  }
+  dpc[N] = nd;
+  int n_dev = nd + 1;  // + END
+  if (n_dev > kMaxDevOps) return CUFZ_E_INVALID_PROGRAM;
+  std::vector<DevOp> dops;
+  dops.reserve(n_dev);
+  auto off = [&](int v) -> uint16_t { return v < 0 ? 0 : (uint16_t)(map[v] * kRegStride); };
+  uint32_t sreg_mask = 0;
+  DevProgHdr hdr;
+  memset(&hdr, 0, sizeof(hdr));
+  for (int s = 0; s < 16; s++)
+    if (map[kSregBase + s] >= 0) {
+      sreg_mask |= 1u << s;
+      hdr.sreg_reg[s] = (uint8_t)map[kSregBase + s];
+    }
+  for (int pc = 0; pc < N; pc++) {
+    const IrOp& o = ir.ops[pc];
+    if (!o.kept) continue;
+    DevOp d;
+    memset(&d, 0, sizeof(d));
+    uint8_t opc = o.opc;
+    if (is_alu_reg(opc)) {
+      d.opc = D_ALU0 + (opc - 0x10);
+      d.d = off(o.dst); d.a = off(o.a); d.b = off(o.b);
+    } else if (is_alu_imm(opc)) {
+      d.opc = D_ALUI0 + (opc - 0x30);
+      d.d = off(o.dst); d.a = off(o.a); d.imm = o.imm;
+    } else {
+      switch (opc) {
+        case B_SREG: d.opc = D_MOV; d.d = off(o.dst); d.a = off(kSregBase + o.sreg); break;
+        case B_IMM: d.opc = D_IMM; d.d = off(o.dst); d.imm = o.imm; break;
+        case B_MOV: d.opc = D_MOV; d.d = off(o.dst); d.a = off(o.a); break;
+        case B_SEL:
+          d.opc = D_SEL; d.d = off(o.dst); d.a = off(o.a); d.b = off(o.b);
+          d.imm = (int32_t)off(o.c);
+          break;
+        case B_LD:
+        case B_ST:
+          d.opc = opc == B_ST ? D_ST : (o.value_dead ? D_LDX : D_LD);
+          if (d.opc == D_LD) d.d = off(o.dst);
+          d.a = off(o.a);
+          d.b = (uint16_t)o.buf;
+          d.x = (uint8_t)log2w(o.width);
+          d.imm = o.site;
+          break;
+        case B_IF:
+          d.opc = D_IF; d.a = off(o.a); d.x = (uint8_t)o.site;
+          d.j0 = (uint16_t)(o.else_pc >= 0 ? dpc[o.else_pc] : dpc[o.end_pc]);
+          break;
+        case B_ELSE: d.opc = D_ELSE; d.j0 = (uint16_t)dpc[o.end_pc]; break;
+        case B_ENDIF: d.opc = D_ENDIF; break;
+        case B_LOOP:
+        case B_ENDLOOP: {
+          const IrOp& h = opc == B_LOOP ? o : ir.ops[o.head_pc];
+          d.opc = opc == B_LOOP ? D_LOOP : D_ENDLOOP;
+          d.d = off(h.dst);
+          d.a = opc == B_LOOP ? off(h.a) : 0;
+          d.b = off(h.trip);
+          d.imm = opc == B_LOOP ? h.imm : 0;
+          d.x = (uint8_t)h.site;
+          d.j0 = (uint16_t)(dpc[h.end_pc] + 1);
+          d.j1 = (uint16_t)(dpc[o.opc == B_LOOP ? pc : o.head_pc] + 1);
+          break;
+        }
+        default: continue;
+      }
+    }
+    dops.push_back(d);
+  }
+  DevOp end;
+  memset(&end, 0, sizeof(end));
+  end.opc = D_END;
+  dops.push_back(end);
+
+  std::vector<uint16_t> zero;
+  for (int v = 0; v < kSregBase; v++)
+    if (entry.get(v) && map[v] >= 0) zero.push_back((uint16_t)(map[v] * kRegStride));
+  for (int v = kTripBase; v < ir.nv; v++)
+    if (entry.get(v) && map[v] >= 0) zero.push_back((uint16_t)(map[v] * kRegStride));
+  std::sort(zero.begin(), zero.end());
+  zero.erase(std::unique(zero.begin(), zero.end()), zero.end());
+
+  hdr.n_ops = (uint32_t)dops.size();
+  hdr.n_regs = (uint32_t)std::max(n_regs, 1);
+  hdr.n_bufs = (uint32_t)ir.n_bufs;
+  hdr.shared_mask = ir.shared_mask;
+  hdr.seed = ir.seed;
+  hdr.n_sites = (uint32_t)ir.n_sites;
+  hdr.sreg_mask = sreg_mask;
+  hdr.n_zero = (uint32_t)zero.size();
+  hdr.n_loops = (uint32_t)ir.n_loops;
+  uint32_t ops_off = sizeof(DevProgHdr);
+  uint32_t loc_off = ops_off + (uint32_t)(dops.size() * sizeof(DevOp));
+  uint32_t zero_off = loc_off + 4u * (uint32_t)ir.n_sites;
+  uint32_t bytes_total = zero_off + 2u * (uint32_t)zero.size();
+  bytes_total = (bytes_total + 15u) & ~15u;
+  hdr.ops_off = ops_off;
+  hdr.loc_off = loc_off;
+  hdr.zero_off = zero_off;
+  hdr.bytes = bytes_total;
+
+  uint8_t* blob = (uint8_t*)calloc(1, bytes_total);
+  if (!blob) return CUFZ_E_NOMEM;
+  memcpy(blob, &hdr, sizeof(hdr));
+  memcpy(blob + ops_off, dops.data(), dops.size() * sizeof(DevOp));
+  for (int s = 0; s < ir.n_sites; s++) {
+    uint32_t w = (uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16);
+    memcpy(blob + loc_off + 4 * s, &w, 4);
+  }
+  if (!zero.empty()) memcpy(blob + zero_off, zero.data(), 2 * zero.size());
+  out->hdr = hdr;
+  out->blob = blob;
+  out->blob_bytes = bytes_total;
+  out->n_bufs = (uint32_t)ir.n_bufs;
+  out->shared_mask = ir.shared_mask;
+  fill_stats(ir, n_in, n_regs, &out->stats);
+  return CUFZ_OK;
+}
+
+void free_program(LoadedProgram* p) {
+  free(p->blob);
+  p->blob = nullptr;
+}
+
+}  // namespace cufz
+
+using namespace cufz;
+
+extern "C" cufz_status cufz_validate_program(const void* bytes, size_t nbytes) {
+  Ir ir;
+  return decode((const uint8_t*)bytes, nbytes, &ir) ? CUFZ_OK : CUFZ_E_INVALID_PROGRAM;
+}
+
+extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void* out,
+                                          size_t out_cap, size_t* out_bytes,
+                                          cufz_prog_stats* stats) {
+  if (!out || !out_bytes) return CUFZ_E_INVALID_ARG;
+  Ir ir;
+  if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  int n_in = (int)ir.ops.size();
+  prune(&ir);
+  std::vector<int> map;
+  Bits entry;
+  int n_regs = allocate(ir, false, &map, &entry);
+  if (n_regs > 255) return CUFZ_E_INVALID_PROGRAM;
+  std::vector<uint8_t> v;
+  std::vector<IrOp> kept;
+  for (const auto& o : ir.ops)
+    if (o.kept && o.opc != B_NOP) kept.push_back(o);
+  if (kept.empty()) {  // the format needs one op
+    IrOp nop;
+    nop.opc = B_NOP;
+    kept.push_back(nop);
+  }
+  put32(v, kMagic);
+  put16(v, 1);
+  put16(v, (uint16_t)kept.size());
+  v.push_back((uint8_t)std::max(n_regs, 1));
+  v.push_back((uint8_t)ir.n_bufs);
+  v.push_back((uint8_t)ir.n_sites);
+  v.push_back(0);
+  put16(v, (uint16_t)ir.shared_mask);
+  put16(v, 0);
+  put32(v, ir.seed);
+  put32(v, 0);
+  put32(v, 0);
+  put32(v, 0);
+  for (int s = 0; s < ir.n_sites; s++) {
+    put16(v, ir.loc0[s]);
+    put16(v, ir.loc1[s]);
+  }
+  auto R = [&](int r) -> uint8_t { return r < 0 ? 0 : (uint8_t)map[r]; };
+  for (const auto& o : kept) {
+    uint8_t d = 0, a = 0, b = 0;
+    int32_t imm = 0;
+    uint8_t opc = o.opc;
+    if (is_alu_reg(opc)) {
+      d = R(o.dst); a = R(o.a); b = R(o.b);
+    } else if (is_alu_imm(opc)) {
+      d = R(o.dst); a = R(o.a); imm = o.imm;
+    } else {
+      switch (opc) {
+        case B_SREG: d = R(o.dst); imm = o.sreg; break;
+        case B_IMM: d = R(o.dst); imm = o.imm; break;
+        case B_MOV: d = R(o.dst); a = R(o.a); break;
+        case B_SEL: d = R(o.dst); a = R(o.a); b = R(o.b); imm = R(o.c); break;
+        case B_LD: d = R(o.dst); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
+        case B_ST: d = R(o.a); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
+        case B_IF: a = R(o.a); break;
+        case B_LOOP: d = R(o.dst); a = R(o.a); imm = o.imm; break;
+        default: break;
+      }
+    }
+    v.push_back(opc);
+    v.push_back(d);
+    v.push_back(a);
+    v.push_back(b);
+    put32(v, (uint32_t)imm);
+  }
+  *out_bytes = v.size();
+  fill_stats(ir, n_in, n_regs, stats);
+  if (v.size() > out_cap) return CUFZ_E_NOMEM;
+  memcpy(out, v.data(), v.size());
+  return CUFZ_OK;
+}

@@ -1,0 +1,908 @@
+// Host runtime of cufz: context over a caller-owned arena, program table,
+// admission by free slots, batches on overlapping pipeline lanes (each a
+// stream with its own staging buffer and CUDA graph), completion polling
+// through pinned mapped memory, and the C ABI of include/cufz.h.
+//
+// The runtime plays the part of the paper's CPU runtime library and fuzzing
+// harness (Sec. 4: emulated cudaMalloc/cudaMemcpy and a thread pool that
+// runs blocks; Sec. 2.1: the fuzzer feeds inputs and reads the coverage
+// map), rebuilt around one GPU: inputs are admitted while earlier ones still
+// run, and each input's work is split into block ranges that persistent
+// CTAs pull from a device queue.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "engine.h"
+
+using namespace cufz;
+
+namespace {
+
+constexpr uint32_t kMaxLanes = 8;
+constexpr uint64_t kProgAreaBytes = 8ull << 20;
+constexpr uint64_t kAlign = 256;
+constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
+
+uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
+
+uint64_t now_us() {
+  return (uint64_t)std::chrono::duration_cast<std::chrono::microseconds>(
+             std::chrono::steady_clock::now().time_since_epoch())
+      .count();
+}
+
+struct SlotHost {
+  uint64_t ticket = 0;
+  uint32_t seq = 0;
+  int state = 0;  // 0 free, 1 in flight, 2 completed (held until release)
+  uint32_t lane = 0;
+  uint64_t batch = 0;
+};
+
+struct Lane {
+  cudaStream_t stream = nullptr;
+  cudaEvent_t ev_start = nullptr, ev_end = nullptr;
+  uint8_t* h_stage = nullptr;
+  uint8_t* d_batch = nullptr;
+  uint64_t cap = 0;
+  bool busy = false;
+  bool timed = false;
+  uint64_t batch_id = 0;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphNode_t copy_node = nullptr;
+  uint32_t graph_regs = 0, graph_prog = 0, graph_ctas = 0, graph_threads = 0;
+};
+
+struct HostOnlyResult {
+  cufz_result res;
+};
+
+}  // namespace
+
+struct cufz_ctx {
+  cufz_config cfg{};
+  std::mutex mu;
+  int device = 0;
+  int n_sms = 0;
+  uint8_t* arena = nullptr;
+  EngineTables T{};
+  uint8_t* d_progs = nullptr;
+  uint64_t prog_used = 0;
+  std::vector<LoadedProgram> progs;
+  std::vector<uint32_t> prog_off;
+  uint32_t max_regs = 1, max_prog_bytes = 16;
+  uint32_t max_slots = 0;
+  std::vector<SlotHost> slots;
+  std::vector<uint32_t> free_slots;
+  std::unordered_map<uint64_t, uint32_t> ticket_slot;
+  std::unordered_map<uint64_t, cufz_result> host_done;  // tickets completed without device work
+  std::deque<uint32_t> inflight;
+  std::deque<cufz_result> ready;
+  HostDone* done_h = nullptr;
+  HostDone* done_d = nullptr;
+  Lane lanes[kMaxLanes];
+  uint32_t n_lanes = 1;
+  uint32_t next_lane = 0;
+  uint64_t next_ticket = 1;
+  uint32_t next_seq = 1;
+  uint64_t next_batch = 1;
+  LaunchShape shape{};
+  uint32_t smem_set = 0;
+  uint32_t lane_max_inputs = 0, lane_max_items = 0;
+  uint32_t* d_scratch_word = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  cufz_stats stats{};
+};
+
+namespace {
+
+bool invalid_launch(const cufz_input& in) {
+  const uint32_t* g = in.grid;
+  const uint32_t* b = in.block;
+  if (!g[0] || !g[1] || !g[2] || !b[0] || !b[1] || !b[2]) return true;
+  if (b[0] > 1024 || b[1] > 1024 || b[2] > 64) return true;
+  if ((uint64_t)b[0] * b[1] * b[2] > 1024) return true;
+  if (g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535) return true;
+  return false;
+}
+
+
+uint64_t lane_bytes(uint32_t max_inputs, uint32_t max_items) {
+  return align_up(sizeof(BatchHdr) + (uint64_t)max_inputs * sizeof(DevInput) +
+                      (uint64_t)max_items * sizeof(WorkItem),
+                  kAlign);
+}
+
+uint64_t fixed_bytes(const cufz_config& c, uint32_t n_slots, uint32_t* max_inputs,
+                     uint32_t* max_items) {
+  uint32_t lanes = std::max(1u, std::min(c.n_lanes, kMaxLanes));
+  *max_inputs = std::max(1u, std::min(n_slots, 16384u));
+  *max_items = 1u << 20;
+  return kProgAreaBytes + 2ull * kBitmapBytes + lanes * lane_bytes(*max_inputs, *max_items) + 4096;
+}
+
+uint64_t total_bytes(const cufz_config& c, uint32_t n_slots) {
+  uint32_t mi, mt;
+  uint64_t f = fixed_bytes(c, n_slots, &mi, &mt);
+  // per-slot tables, each region 256-aligned
+  uint64_t b = f;
+  b += align_up((uint64_t)n_slots * sizeof(SlotState), kAlign);
+  b += align_up((uint64_t)n_slots * 4ull * kEdgeCount, kAlign);
+  b += align_up((uint64_t)n_slots * 2ull * kEdgeCount, kAlign);
+  b += align_up((uint64_t)n_slots * c.record_cap * sizeof(cufz_violation), kAlign);
+  if (c.flags & CUFZ_CF_KEEP_BITMAPS) b += align_up((uint64_t)n_slots * kBitmapBytes, kAlign);
+  return b + 8 * kAlign;
+}
+
+cufz_status cuda_err(cudaError_t e) { return e == cudaSuccess ? CUFZ_OK : CUFZ_E_CUDA; }
+
+void lane_reset_graph(Lane& L) {
+  if (L.gexec) cudaGraphExecDestroy(L.gexec);
+  L.gexec = nullptr;
+  L.copy_node = nullptr;
+}
+
+// Accounts the finished batch of a lane (timing) and marks it free.
+void lane_retire(cufz_ctx* c, Lane& L) {
+  if (!L.busy) return;
+  if (L.timed) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, L.ev_start, L.ev_end) == cudaSuccess) c->stats.kernel_ms += ms;
+  }
+  L.busy = false;
+}
+
+bool lane_done(Lane& L) {
+  if (!L.busy) return true;
+  return cudaEventQuery(L.ev_end) == cudaSuccess;
+}
+
+// Moves completed in-flight slots to the ready queue.
+void harvest(cufz_ctx* c) {
+  for (uint32_t k = 0; k < c->n_lanes; k++)
+    if (c->lanes[k].busy && lane_done(c->lanes[k])) lane_retire(c, c->lanes[k]);
+  size_t n = c->inflight.size();
+  for (size_t i = 0; i < n; i++) {
+    uint32_t s = c->inflight.front();
+    c->inflight.pop_front();
+    SlotHost& sh = c->slots[s];
+    volatile HostDone* hd = &c->done_h[s];
+    if (hd->seq == sh.seq) {
+      std::atomic_thread_fence(std::memory_order_acquire);
+      cufz_result r;
+      memcpy(&r, const_cast<const cufz_result*>(&c->done_h[s].res), sizeof(r));
+      c->ready.push_back(r);
+      c->stats.inputs_completed++;
+      if (c->cfg.flags & CUFZ_CF_AUTO_RELEASE) {
+        c->ticket_slot.erase(sh.ticket);
+        sh.state = 0;
+        c->free_slots.push_back(s);
+      } else {
+        sh.state = 2;
+      }
+    } else {
+      c->inflight.push_back(s);
+    }
+  }
+}
+
+uint32_t smem_for(const LaunchShape& s, uint32_t cta_threads) {
+  return kHashSlots * 4 + s.max_prog_bytes + 336 + (cta_threads / 32) * s.max_regs * kRegStride;
+}
+
+// Sets the kernels' dynamic shared memory limit to what the persistent shape
+// and the largest plain (one CTA per test block, up to 1024 threads) launch
+// need, and derives the persistent grid from occupancy.
+cufz_status ensure_smem(cufz_ctx* c) {
+  const LaunchShape& s = c->shape;
+  const uint32_t kSmemMax = 227u * 1024u;
+  uint32_t bytes = smem_for(s, s.cta_threads);
+  if (bytes > kSmemMax) return CUFZ_E_NOMEM;
+  uint32_t attr = std::min(std::max(bytes, smem_for(s, 1024)), kSmemMax);
+  if (attr != c->smem_set) {
+    if (set_kernel_smem(attr) != cudaSuccess) return CUFZ_E_CUDA;
+    c->smem_set = attr;
+  }
+  c->shape.smem_bytes = bytes;
+  int occ = 0;
+  if (persistent_occupancy(s.cta_threads, bytes, &occ) != cudaSuccess || occ < 1) return CUFZ_E_CUDA;
+  uint32_t per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
+  c->shape.ctas = per_sm * (uint32_t)c->n_sms;
+  c->stats.ctas_per_sm = per_sm;
+  c->stats.smem_bytes = bytes;
+  return CUFZ_OK;
+}
+
+// Captures (or re-captures) the lane's graph: batch upload + persistent kernel.
+cufz_status lane_graph(cufz_ctx* c, Lane& L) {
+  const LaunchShape& s = c->shape;
+  if (L.gexec && L.graph_regs == s.max_regs && L.graph_prog == s.max_prog_bytes &&
+      L.graph_ctas == s.ctas && L.graph_threads == s.cta_threads)
+    return CUFZ_OK;
+  lane_reset_graph(L);
+  cudaGraph_t g = nullptr;
+  if (cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+    return CUFZ_E_CUDA;
+  cudaError_t e1 = cudaMemcpyAsync(L.d_batch, L.h_stage, sizeof(BatchHdr), cudaMemcpyHostToDevice, L.stream);
+  cudaError_t e2 = launch_persistent(c->T, reinterpret_cast<const BatchHdr*>(L.d_batch), s, L.stream);
+  cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
+  if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    cudaGetLastError();
+    return CUFZ_E_CUDA;
+  }
+  size_t n = 0;
+  cudaGraphGetNodes(g, nullptr, &n);
+  std::vector<cudaGraphNode_t> nodes(n);
+  cudaGraphGetNodes(g, nodes.data(), &n);
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeMemcpy) L.copy_node = nd;
+  }
+  cudaError_t e4 = cudaGraphInstantiate(&L.gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (e4 != cudaSuccess || !L.copy_node) {
+    lane_reset_graph(L);
+    return CUFZ_E_CUDA;
+  }
+  L.graph_regs = s.max_regs;
+  L.graph_prog = s.max_prog_bytes;
+  L.graph_ctas = s.ctas;
+  L.graph_threads = s.cta_threads;
+  return CUFZ_OK;
+}
+
+void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput* d) {
+  memset(d, 0, sizeof(*d));
+  const LoadedProgram& P = c->progs[in.program_id];
+  d->slot = slot;
+  d->prog = in.program_id;
+  for (int k = 0; k < 3; k++) {
+    d->grid[k] = in.grid[k];
+    d->block[k] = in.block[k];
+  }
+  for (int k = 0; k < 4; k++) d->args[k] = in.args[k];
+  uint32_t Bx = in.block[0], By = in.block[1], Bz = in.block[2];
+  uint32_t T = Bx * By * Bz;
+  uint64_t nb = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2];
+  d->T = T;
+  d->n_threads = nb * T;
+  d->mT = div_magic(T);
+  d->Bx = Bx;
+  d->mBx = div_magic(Bx);
+  d->Bxy = Bx * By;
+  d->mBxy = div_magic(Bx * By);
+  d->gx = in.grid[0];
+  d->mGx = div_magic(in.grid[0]);
+  d->gxy = (uint32_t)((uint64_t)in.grid[0] * in.grid[1]);
+  d->mGxy = div_magic(d->gxy);
+  int64_t R = (int64_t)c->cfg.redzone;
+  int64_t next[2] = {R, R};
+  for (uint32_t k = 0; k < P.n_bufs; k++) {
+    int sp = (P.shared_mask >> k) & 1;
+    d->len[k] = (int64_t)in.buf_len[k];
+    d->base[k] = next[sp];
+    next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
+  }
+  d->prog_off = c->prog_off[in.program_id];
+  d->prog_bytes = P.blob_bytes;
+  d->user_tag = in.user_tag;
+}
+
+uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
+  if (c->cfg.item_threads) return c->cfg.item_threads;
+  uint32_t cta = c->shape.cta_threads;
+  uint64_t target = batch_threads / (8ull * std::max(c->shape.ctas, 1u));
+  uint64_t lo = 2ull * cta, hi = 256ull * cta;
+  target = std::min(std::max(target, lo), hi);
+  return (uint32_t)align_up(target, 32);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+void cufz_config_default(cufz_config* cfg) {
+  if (!cfg) return;
+  memset(cfg, 0, sizeof(*cfg));
+  cfg->device = 0;
+  cfg->flags = CUFZ_CF_KEEP_BITMAPS;
+  cfg->record_cap = 4096;
+  cfg->redzone = 256;
+  cfg->iter_budget = 4096;
+  cfg->max_threads = 1ull << 31;
+  cfg->cta_threads = 256;
+  cfg->n_lanes = 4;
+}
+
+uint64_t cufz_arena_bytes(const cufz_config* cfg, uint32_t n_slots) {
+  if (!cfg || !n_slots) return 0;
+  return total_bytes(*cfg, n_slots);
+}
+
+const char* cufz_status_str(cufz_status s) {
+  switch (s) {
+    case CUFZ_OK: return "ok";
+    case CUFZ_E_INVALID_ARG: return "invalid argument";
+    case CUFZ_E_INVALID_PROGRAM: return "invalid program";
+    case CUFZ_E_NOMEM: return "out of arena memory or table space";
+    case CUFZ_E_BUSY: return "busy: no free slot or lane";
+    case CUFZ_E_TIMEOUT: return "timeout";
+    case CUFZ_E_CUDA: return "CUDA error";
+    case CUFZ_E_NOT_FOUND: return "not found";
+    case CUFZ_E_NO_DEVICE: return "no CUDA device";
+    case CUFZ_E_DEVICE_FAULT: return "device reported an engine error";
+    default: return "unknown status";
+  }
+}
+
+cufz_status cufz_create(const cufz_config* cfg_in, cufz_ctx** out) {
+  if (!cfg_in || !out) return CUFZ_E_INVALID_ARG;
+  *out = nullptr;
+  cufz_config cfg = *cfg_in;
+  if (!cfg.arena || (reinterpret_cast<uintptr_t>(cfg.arena) & (kAlign - 1))) return CUFZ_E_INVALID_ARG;
+  if (!cfg.record_cap) cfg.record_cap = 1;
+  if (!cfg.cta_threads) cfg.cta_threads = 256;
+  if (cfg.cta_threads < 64 || cfg.cta_threads > 1024 || cfg.cta_threads % 32) return CUFZ_E_INVALID_ARG;
+  if (cfg.item_threads % 32) return CUFZ_E_INVALID_ARG;
+  if (!cfg.max_threads || cfg.max_threads > 0xFFFFFFFFull) cfg.max_threads = 0xFFFFFFFFull;
+  if (cfg.redzone > (1u << 20)) return CUFZ_E_INVALID_ARG;
+  cfg.n_lanes = std::max(1u, std::min(cfg.n_lanes, kMaxLanes));
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev <= cfg.device || cfg.device < 0) {
+    cudaGetLastError();
+    return CUFZ_E_NO_DEVICE;
+  }
+  if (cudaSetDevice(cfg.device) != cudaSuccess) return CUFZ_E_NO_DEVICE;
+  uint32_t n_slots = cfg.max_slots;
+  if (!n_slots) {
+    // as many as fit, up to 16384
+    uint32_t lo = 1, hi = 16384;
+    if (total_bytes(cfg, 1) > cfg.arena_bytes) return CUFZ_E_NOMEM;
+    while (lo < hi) {
+      uint32_t mid = lo + (hi - lo + 1) / 2;
+      if (total_bytes(cfg, mid) <= cfg.arena_bytes) lo = mid; else hi = mid - 1;
+    }
+    n_slots = lo;
+  }
+  if (total_bytes(cfg, n_slots) > cfg.arena_bytes) return CUFZ_E_NOMEM;
+  cufz_ctx* c = new cufz_ctx();
+  c->cfg = cfg;
+  c->device = cfg.device;
+  cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, cfg.device);
+  c->arena = reinterpret_cast<uint8_t*>(cfg.arena);
+  c->max_slots = n_slots;
+  c->n_lanes = cfg.n_lanes;
+  // carve the arena
+  uint64_t off = 0;
+  auto take = [&](uint64_t bytes) {
+    uint8_t* p = c->arena + off;
+    off = align_up(off + bytes, kAlign);
+    return p;
+  };
+  uint32_t max_inputs, max_items;
+  fixed_bytes(cfg, n_slots, &max_inputs, &max_items);
+  c->lane_max_inputs = max_inputs;
+  c->lane_max_items = max_items;
+  c->d_progs = take(kProgAreaBytes);
+  c->T.progs = c->d_progs;
+  c->T.union_map = reinterpret_cast<uint32_t*>(take(kBitmapBytes));
+  c->T.union_snap = reinterpret_cast<uint32_t*>(take(kBitmapBytes));
+  c->d_scratch_word = reinterpret_cast<uint32_t*>(take(4096));
+  for (uint32_t k = 0; k < c->n_lanes; k++) {
+    c->lanes[k].cap = lane_bytes(max_inputs, max_items);
+    c->lanes[k].d_batch = take(c->lanes[k].cap);
+  }
+  c->T.slots = reinterpret_cast<SlotState*>(take((uint64_t)n_slots * sizeof(SlotState)));
+  c->T.counts = reinterpret_cast<uint32_t*>(take((uint64_t)n_slots * 4ull * kEdgeCount));
+  c->T.touched = reinterpret_cast<uint16_t*>(take((uint64_t)n_slots * 2ull * kEdgeCount));
+  c->T.records = reinterpret_cast<cufz_violation*>(
+      take((uint64_t)n_slots * cfg.record_cap * sizeof(cufz_violation)));
+  c->T.bitmaps = (cfg.flags & CUFZ_CF_KEEP_BITMAPS) ? take((uint64_t)n_slots * kBitmapBytes) : nullptr;
+  c->T.record_cap = cfg.record_cap;
+  c->T.redzone = cfg.redzone;
+  c->T.iter_budget = cfg.iter_budget;
+  c->T.flags = cfg.flags;
+  if (off > cfg.arena_bytes) {
+    delete c;
+    return CUFZ_E_NOMEM;
+  }
+  cudaStream_t s0 = reinterpret_cast<cudaStream_t>(cfg.stream);
+  cudaError_t e = cudaSuccess;
+  // host structures
+  e = cudaHostAlloc(reinterpret_cast<void**>(&c->done_h), (size_t)n_slots * sizeof(HostDone),
+                    cudaHostAllocMapped);
+  if (e == cudaSuccess) {
+    memset(c->done_h, 0, (size_t)n_slots * sizeof(HostDone));
+    e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&c->done_d), c->done_h, 0);
+  }
+  c->T.done = c->done_d;
+  for (uint32_t k = 0; k < c->n_lanes && e == cudaSuccess; k++) {
+    Lane& L = c->lanes[k];
+    e = cudaStreamCreateWithFlags(&L.stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.ev_start);
+    if (e == cudaSuccess) e = cudaEventCreate(&L.ev_end);
+    if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&L.h_stage), L.cap, cudaHostAllocDefault);
+  }
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  // clear the tables on the caller's stream
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->T.union_map, 0, kBitmapBytes, s0);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->T.union_snap, 0, kBitmapBytes, s0);
+  if (e == cudaSuccess)
+    e = cudaMemsetAsync(c->T.counts, 0, (size_t)n_slots * 4ull * kEdgeCount, s0);
+  if (e == cudaSuccess) {
+    std::vector<SlotState> init(n_slots);
+    memset(init.data(), 0, init.size() * sizeof(SlotState));
+    for (auto& s : init) s.first_key = ~0ull;
+    e = cudaMemcpyAsync(c->T.slots, init.data(), init.size() * sizeof(SlotState),
+                        cudaMemcpyHostToDevice, s0);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s0);
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    cufz_destroy(c);
+    return CUFZ_E_CUDA;
+  }
+  c->slots.resize(n_slots);
+  for (uint32_t s = n_slots; s-- > 0;) c->free_slots.push_back(s);
+  c->shape.cta_threads = cfg.cta_threads;
+  c->shape.max_regs = 1;
+  c->shape.max_prog_bytes = 16;
+  c->stats.cta_threads = cfg.cta_threads;
+  c->stats.n_sms = (uint32_t)c->n_sms;
+  c->stats.max_slots = n_slots;
+  *out = c;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_destroy(cufz_ctx* c) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    uint64_t t0 = now_us();
+    for (uint32_t k = 0; k < c->n_lanes; k++) {
+      Lane& L = c->lanes[k];
+      while (L.busy && !lane_done(L) && (int64_t)(now_us() - t0) < kWaitLimitUs)
+        std::this_thread::sleep_for(std::chrono::microseconds(200));
+      lane_reset_graph(L);
+      if (L.ev_start) cudaEventDestroy(L.ev_start);
+      if (L.ev_end) cudaEventDestroy(L.ev_end);
+      if (L.stream) cudaStreamDestroy(L.stream);
+      if (L.h_stage) cudaFreeHost(L.h_stage);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->done_h) cudaFreeHost(c->done_h);
+    for (auto& p : c->progs) free_program(&p);
+  }
+  delete c;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uint32_t* program_id,
+                              cufz_prog_stats* stats) {
+  if (!c || !bytes || !program_id) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->progs.size() >= (size_t)kMaxPrograms) return CUFZ_E_NOMEM;
+  LoadedProgram P;
+  cufz_status st = load_program(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), &P);
+  if (st != CUFZ_OK) return st;
+  if (c->prog_used + P.blob_bytes > kProgAreaBytes) {
+    free_program(&P);
+    return CUFZ_E_NOMEM;
+  }
+  uint32_t off = (uint32_t)c->prog_used;
+  cudaError_t e = cudaMemcpy(c->d_progs + off, P.blob, P.blob_bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) {
+    free_program(&P);
+    return CUFZ_E_CUDA;
+  }
+  c->prog_used = align_up(c->prog_used + P.blob_bytes, 16);
+  if (stats) *stats = P.stats;
+  *program_id = (uint32_t)c->progs.size();
+  c->progs.push_back(P);
+  c->prog_off.push_back(off);
+  c->shape.max_regs = std::max(c->shape.max_regs, P.hdr.n_regs);
+  c->shape.max_prog_bytes = std::max(c->shape.max_prog_bytes, (uint32_t)align_up(P.blob_bytes, 16));
+  return ensure_smem(c);
+}
+
+cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, uint32_t* n_accepted,
+                               uint64_t* first_ticket) {
+  if (!c || (!in && n) || !n_accepted) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  *n_accepted = 0;
+  if (first_ticket) *first_ticket = c->next_ticket;
+  if (!n) return CUFZ_OK;
+  harvest(c);
+  // a free lane
+  Lane* L = nullptr;
+  uint32_t lane_idx = 0;
+  for (uint32_t k = 0; k < c->n_lanes; k++) {
+    uint32_t li = (c->next_lane + k) % c->n_lanes;
+    if (lane_done(c->lanes[li])) {
+      lane_retire(c, c->lanes[li]);
+      L = &c->lanes[li];
+      lane_idx = li;
+      break;
+    }
+  }
+  if (!L) return CUFZ_E_BUSY;
+  const bool plain = c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH;
+  // admission
+  BatchHdr* hdr = reinterpret_cast<BatchHdr*>(L->h_stage);
+  DevInput* dins = reinterpret_cast<DevInput*>(L->h_stage + sizeof(BatchHdr));
+  uint32_t n_dev = 0;
+  uint64_t batch_threads = 0;
+  std::vector<uint32_t> dev_slots;
+  uint32_t accepted = 0;
+  bool busy = false;
+  for (uint32_t i = 0; i < n; i++) {
+    const cufz_input& x = in[i];
+    int32_t status = CUFZ_ST_OK;
+    if (x.program_id >= c->progs.size()) status = CUFZ_ST_BAD_PROGRAM;
+    else if (invalid_launch(x)) status = CUFZ_ST_INVALID_CONFIG;
+    else {
+      uint64_t nt = (uint64_t)x.grid[0] * x.grid[1] * x.grid[2] * x.block[0] * x.block[1] * x.block[2];
+      if (nt > c->cfg.max_threads) status = CUFZ_ST_LIMIT;
+      const LoadedProgram& P = c->progs[x.program_id];
+      for (uint32_t k = 0; k < P.n_bufs; k++)
+        if (x.buf_len[k] >= (1ull << 48)) status = CUFZ_ST_LIMIT;
+    }
+    uint64_t ticket = c->next_ticket;
+    if (status != CUFZ_ST_OK) {
+      cufz_result r;
+      memset(&r, 0, sizeof(r));
+      r.ticket = ticket;
+      r.user_tag = x.user_tag;
+      r.status = status;
+      r.first_key = ~0ull;
+      c->host_done[ticket] = r;
+      c->ready.push_back(r);
+      c->next_ticket++;
+      accepted++;
+      c->stats.inputs_submitted++;
+      c->stats.inputs_completed++;
+      continue;
+    }
+    if (c->free_slots.empty() || n_dev >= c->lane_max_inputs) {
+      busy = true;
+      break;
+    }
+    uint32_t s = c->free_slots.back();
+    c->free_slots.pop_back();
+    DevInput* d = &dins[n_dev];
+    build_dev_input(c, x, s, d);
+    d->ticket = ticket;
+    d->seq = c->next_seq++;
+    if (c->next_seq == 0) c->next_seq = 1;
+    SlotHost& sh = c->slots[s];
+    sh.ticket = ticket;
+    sh.seq = d->seq;
+    sh.state = 1;
+    sh.lane = lane_idx;
+    c->ticket_slot[ticket] = s;
+    dev_slots.push_back(s);
+    batch_threads += d->n_threads;
+    n_dev++;
+    c->next_ticket++;
+    accepted++;
+    c->stats.inputs_submitted++;
+  }
+  *n_accepted = accepted;
+  if (n_dev) {
+    // work items
+    WorkItem* items = reinterpret_cast<WorkItem*>(reinterpret_cast<uint8_t*>(dins) +
+                                                  (uint64_t)n_dev * sizeof(DevInput));
+    uint32_t n_items = 0;
+    uint32_t item = choose_item_threads(c, batch_threads);
+    c->stats.item_threads = item;
+    bool overflow = false;
+    for (uint32_t i = 0; i < n_dev; i++) {
+      DevInput* d = &dins[i];
+      if (plain) {
+        d->n_items = (uint32_t)(d->n_threads / d->T);
+        continue;
+      }
+      uint32_t cnt = (uint32_t)((d->n_threads + item - 1) / item);
+      if (n_items + cnt > c->lane_max_items) {
+        overflow = true;
+        cnt = 0;
+      }
+      d->n_items = cnt;
+      for (uint32_t k = 0; k < cnt; k++) {
+        WorkItem& w = items[n_items++];
+        w.input = i;
+        w.g0 = k * item;
+        uint64_t rem = d->n_threads - (uint64_t)k * item;
+        w.count = (uint32_t)std::min<uint64_t>(rem, item);
+        w.pad = 0;
+      }
+    }
+    if (overflow) {
+      // roll back every device input of this call: more work items than a lane holds
+      for (uint32_t s : dev_slots) {
+        c->ticket_slot.erase(c->slots[s].ticket);
+        c->slots[s].state = 0;
+        c->free_slots.push_back(s);
+      }
+      *n_accepted = 0;
+      return CUFZ_E_NOMEM;
+    }
+    memset(hdr, 0, sizeof(*hdr));
+    hdr->n_inputs = n_dev;
+    hdr->n_items = n_items;
+    hdr->next_item = 0;
+    hdr->inputs_off = sizeof(BatchHdr);
+    hdr->items_off = sizeof(BatchHdr) + (uint64_t)n_dev * sizeof(DevInput);
+    uint64_t bytes = hdr->items_off + (uint64_t)n_items * sizeof(WorkItem);
+    cufz_status st = CUFZ_OK;
+    L->batch_id = c->next_batch++;
+    cudaError_t e = cudaEventRecord(L->ev_start, L->stream);
+    bool use_graph = !plain && !(c->cfg.flags & CUFZ_CF_NO_GRAPH);
+    if (use_graph && lane_graph(c, *L) != CUFZ_OK) use_graph = false;
+    if (e == cudaSuccess) {
+      if (use_graph) {
+        e = cudaGraphExecMemcpyNodeSetParams1D(L->gexec, L->copy_node, L->d_batch, L->h_stage,
+                                               bytes, cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+          // the graph cannot take this batch: drop it and launch directly
+          cudaGetLastError();
+          lane_reset_graph(*L);
+          use_graph = false;
+          e = cudaSuccess;
+        } else {
+          e = cudaGraphLaunch(L->gexec, L->stream);
+          if (e == cudaSuccess) {
+            c->stats.graph_launches++;
+            c->stats.kernel_launches++;
+          }
+        }
+      }
+      if (!use_graph && e == cudaSuccess) {
+        e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
+        if (e == cudaSuccess && !plain) {
+          LaunchShape s = c->shape;
+          s.ctas = std::min<uint32_t>(s.ctas, std::max<uint32_t>(n_items, 1));
+          e = launch_persistent(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), s, L->stream);
+          if (e == cudaSuccess) c->stats.kernel_launches++;
+        } else if (e == cudaSuccess) {
+          for (uint32_t i = 0; i < n_dev && e == cudaSuccess; i++) {
+            LaunchShape s = c->shape;
+            s.cta_threads = (uint32_t)align_up(dins[i].T, 32);
+            if (smem_for(s, s.cta_threads) > c->smem_set) {
+              e = cudaErrorInvalidConfiguration;
+              break;
+            }
+            e = launch_plain(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
+                             dins[i].n_items, s, L->stream);
+            if (e == cudaSuccess) c->stats.kernel_launches++;
+          }
+        }
+      }
+    }
+    if (e == cudaSuccess) e = cudaEventRecord(L->ev_end, L->stream);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      st = CUFZ_E_CUDA;
+    }
+    L->busy = true;
+    L->timed = (e == cudaSuccess);
+    c->stats.batches++;
+    c->next_lane = (lane_idx + 1) % c->n_lanes;
+    for (uint32_t s : dev_slots) c->inflight.push_back(s);
+    if (st != CUFZ_OK) return st;
+  }
+  return busy ? CUFZ_E_BUSY : CUFZ_OK;
+}
+
+cufz_status cufz_poll_results(cufz_ctx* c, cufz_result* out, uint32_t max, uint32_t* n_out,
+                              int32_t timeout_us) {
+  if (!c || !n_out || (!out && max)) return CUFZ_E_INVALID_ARG;
+  *n_out = 0;
+  uint64_t t0 = now_us();
+  int64_t limit = timeout_us < 0 ? kWaitLimitUs : (int64_t)timeout_us;
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      harvest(c);
+      bool all_done = c->inflight.empty();
+      uint32_t k = 0;
+      if (timeout_us >= 0 || all_done) {
+        while (k < max && !c->ready.empty()) {
+          out[k++] = c->ready.front();
+          c->ready.pop_front();
+        }
+      }
+      if (k) {
+        *n_out = k;
+        return CUFZ_OK;
+      }
+      if (timeout_us < 0 && all_done) return CUFZ_OK;
+      if (timeout_us == 0) return CUFZ_OK;
+    }
+    if ((int64_t)(now_us() - t0) >= limit) return timeout_us < 0 ? CUFZ_E_TIMEOUT : CUFZ_OK;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+cufz_status cufz_sync(cufz_ctx* c, int32_t timeout_us) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  uint64_t t0 = now_us();
+  int64_t limit = timeout_us < 0 ? kWaitLimitUs : (int64_t)timeout_us;
+  for (;;) {
+    {
+      std::lock_guard<std::mutex> g(c->mu);
+      harvest(c);
+      bool lanes_idle = true;
+      for (uint32_t k = 0; k < c->n_lanes; k++)
+        if (c->lanes[k].busy) lanes_idle = false;
+      if (c->inflight.empty() && lanes_idle) return CUFZ_OK;
+    }
+    if ((int64_t)(now_us() - t0) >= limit) return CUFZ_E_TIMEOUT;
+    std::this_thread::sleep_for(std::chrono::microseconds(20));
+  }
+}
+
+static cufz_status lookup_completed(cufz_ctx* c, uint64_t ticket, uint32_t* slot, bool* host_only) {
+  harvest(c);
+  *host_only = false;
+  auto it = c->ticket_slot.find(ticket);
+  if (it == c->ticket_slot.end()) {
+    if (c->host_done.count(ticket)) {
+      *host_only = true;
+      return CUFZ_OK;
+    }
+    return CUFZ_E_NOT_FOUND;
+  }
+  if (c->slots[it->second].state != 2) return CUFZ_E_BUSY;
+  *slot = it->second;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_get_records(cufz_ctx* c, uint64_t ticket, cufz_violation* out, uint32_t cap,
+                             uint32_t* n) {
+  if (!c || !n || (!out && cap)) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  uint32_t s = 0;
+  bool host_only = false;
+  cufz_status st = lookup_completed(c, ticket, &s, &host_only);
+  if (st != CUFZ_OK) return st;
+  *n = 0;
+  if (host_only) return CUFZ_OK;
+  uint32_t have = c->done_h[s].res.n_records;
+  uint32_t k = std::min(have, cap);
+  if (k) {
+    cudaError_t e = cudaMemcpyAsync(out, c->T.records + (size_t)s * c->cfg.record_cap,
+                                     (size_t)k * sizeof(cufz_violation), cudaMemcpyDeviceToHost,
+                                     c->copy_stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+    if (e != cudaSuccess) return CUFZ_E_CUDA;
+  }
+  *n = k;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_get_bitmap(cufz_ctx* c, uint64_t ticket, uint8_t* out65536) {
+  if (!c || !out65536) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (!(c->cfg.flags & CUFZ_CF_KEEP_BITMAPS)) return CUFZ_E_INVALID_ARG;
+  uint32_t s = 0;
+  bool host_only = false;
+  cufz_status st = lookup_completed(c, ticket, &s, &host_only);
+  if (st != CUFZ_OK) return st;
+  if (host_only) {
+    memset(out65536, 0, kBitmapBytes);
+    return CUFZ_OK;
+  }
+  cudaError_t e = cudaMemcpyAsync(out65536, c->T.bitmaps + (size_t)s * kBitmapBytes, kBitmapBytes,
+                                   cudaMemcpyDeviceToHost, c->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  return cuda_err(e);
+}
+
+cufz_status cufz_get_union(cufz_ctx* c, uint8_t* out65536) {
+  if (!c || !out65536) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaError_t e = cudaMemcpyAsync(out65536, c->T.union_map, kBitmapBytes, cudaMemcpyDeviceToHost,
+                                   c->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  return cuda_err(e);
+}
+
+cufz_status cufz_new_epoch(cufz_ctx* c) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  cufz_status st = cufz_sync(c, -1);
+  if (st != CUFZ_OK) return st;
+  std::lock_guard<std::mutex> g(c->mu);
+  cudaError_t e = cudaMemcpyAsync(c->T.union_snap, c->T.union_map, kBitmapBytes,
+                                   cudaMemcpyDeviceToDevice, c->copy_stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->copy_stream);
+  return cuda_err(e);
+}
+
+cufz_status cufz_release(cufz_ctx* c, uint64_t ticket) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (c->host_done.erase(ticket)) return CUFZ_OK;
+  auto it = c->ticket_slot.find(ticket);
+  if (it == c->ticket_slot.end()) return CUFZ_E_NOT_FOUND;
+  harvest(c);
+  SlotHost& sh = c->slots[it->second];
+  if (sh.state != 2) return CUFZ_E_BUSY;
+  sh.state = 0;
+  c->free_slots.push_back(it->second);
+  c->ticket_slot.erase(it);
+  return CUFZ_OK;
+}
+
+cufz_status cufz_get_stats(cufz_ctx* c, cufz_stats* out) {
+  if (!c || !out) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  harvest(c);
+  *out = c->stats;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_reset_stats(cufz_ctx* c) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  harvest(c);
+  cufz_stats keep = c->stats;
+  memset(&c->stats, 0, sizeof(c->stats));
+  c->stats.cta_threads = keep.cta_threads;
+  c->stats.ctas_per_sm = keep.ctas_per_sm;
+  c->stats.item_threads = keep.item_threads;
+  c->stats.n_sms = keep.n_sms;
+  c->stats.max_slots = keep.max_slots;
+  c->stats.smem_bytes = keep.smem_bytes;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_int32_peak(int32_t device, void* stream, double* lane_ops_per_s) {
+  if (!lane_ops_per_s) return CUFZ_E_INVALID_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) return CUFZ_E_NO_DEVICE;
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+  uint32_t* h = nullptr;
+  uint32_t* d = nullptr;
+  cudaError_t e = cudaHostAlloc(reinterpret_cast<void**>(&h), 64, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(reinterpret_cast<void**>(&d), h, 0);
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  const uint32_t threads = 256, blocks = (uint32_t)sms * 8, iters = 4096;
+  float best = 1e30f;
+  for (int rep = 0; rep < 4 && e == cudaSuccess; rep++) {
+    e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = launch_int32_peak(d, blocks, threads, iters, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e == cudaSuccess && rep > 0) best = std::min(best, ms);
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (h) cudaFreeHost(h);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return CUFZ_E_CUDA;
+  }
+  double ops = (double)blocks * threads * iters * 8.0 * 16.0;
+  *lane_ops_per_s = ops / (best * 1e-3);
+  return CUFZ_OK;
+}
+
+}  // extern "C"

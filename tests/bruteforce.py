@@ -185,12 +185,11 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 else:
                     _, ctr, a, mx, site, body = s
                     trip = min(max(regs[a], 0), mx)
-                    i = 0
+                    regs[ctr] = 0
                     while True:
-                        edge(site, int(i < trip))
-                        if i >= trip:
+                        edge(site, int(regs[ctr] < trip))
+                        if regs[ctr] >= trip:
                             break
-                        regs[ctr] = i
                         run(body)
                         if t["stop"]:
                             return
@@ -199,7 +198,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                             t["stop"] = True
                             st["budget_hit"] = True
                             return
-                        i += 1
+                        regs[ctr] += 1
 
         run(P["body"])
 

@@ -1,0 +1,149 @@
+"""Host-side tests of the engine library (no GPU): exported symbols, the
+validator, the prune pass (checked by running the CPU oracle on pruned and
+unpruned programs) and the division magic numbers."""
+import re
+
+import numpy as np
+import pytest
+
+from conftest import ROOT
+from paper_2601_01048_gb300 import binding as B
+from paper_2601_01048_gb300 import bytecode as bc
+from paper_2601_01048_gb300 import gen
+from paper_2601_01048_gb300.bytecode import Asm, Imm
+
+
+def header_functions():
+    src = open(f"{ROOT}/include/cufz.h").read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return set(re.findall(r"\b(cufz_[a-z0-9_]+)\s*\(", src))
+
+
+def test_library_exports_every_declared_function():
+    names = header_functions()
+    assert len(names) >= 19
+    L = B.lib()
+    for n in names:
+        assert hasattr(L, n), n
+    assert set(B.EXPORTS) == names
+
+
+def test_status_strings():
+    for st in range(0, -10, -1):
+        assert B.cufz_status_str(st)
+
+
+def all_programs():
+    progs = [gen.c1_program(), gen.vecadd_shared_program(64), gen.guarded_plus1_program(128)]
+    progs += gen.c3_programs() + gen.c2_programs() + gen.c4_programs()
+    return progs
+
+
+def small_inputs(prog, n, seed):
+    h = bc.decode_header(prog)
+    rng = gen.SplitMix64(seed)
+    out = gen.make_inputs(n)
+    for k in range(n):
+        grid = (rng.randint(1, 3), rng.randint(1, 2), 1)
+        block = (rng.randint(1, 40), rng.randint(1, 3), 1)
+        args = [rng.choice((0, -1, 1, 7, 33, 200, -5, 1 << 20)) for _ in range(4)]
+        lens = [rng.choice((0, 4, 60, 256, 1024, 4096, 1 << 16)) for _ in range(h["n_bufs"])]
+        gen.set_input(out[k], 0, grid, block, args, lens)
+    return out
+
+
+@pytest.mark.parametrize("which", range(67))
+def test_prune_keeps_every_access_and_branch(orc, which):
+    """Sec. 5.2: AXIPrune may change values but preserves every memory access.
+    The oracle on the pruned program must give the same records (site,
+    ordinal, byte offset), digest, counts and bitmap as on the original."""
+    prog = all_programs()[which]
+    pruned, st = B.cufz_prune_program(prog)
+    assert orc.validate(pruned) == 0
+    assert B.cufz_validate_program(pruned) == 0
+    ops0, ops1 = bc.ops_of(prog), bc.ops_of(pruned)
+    kinds = (bc.LD, bc.ST, bc.IF, bc.ELSE, bc.ENDIF, bc.LOOP, bc.ENDLOOP)
+    assert [o[0] for o in ops0 if o[0] in kinds] == [o[0] for o in ops1 if o[0] in kinds]
+    assert st.n_ops_kept <= st.n_ops_in and st.n_regs_alloc <= max(st.n_regs_in, 1)
+    ins = small_inputs(prog, 4, 77 + which)
+    for o in (orc.opts(), orc.opts(iter_budget=5)):
+        r0, c0, b0 = orc.run_batch([prog], ins, o, rec_cap=1 << 15, bitmaps=True, threads=2)
+        r1, c1, b1 = orc.run_batch([pruned], ins, o, rec_cap=1 << 15, bitmaps=True, threads=2)
+        assert r0.tobytes() == r1.tobytes()
+        assert c0.tobytes() == c1.tobytes()
+        assert np.array_equal(b0, b1)
+
+
+def test_prune_removes_dead_math():
+    pruned, st = B.cufz_prune_program(gen.c1_program())
+    assert st.n_ops_kept == st.n_ops_in - 1          # the stored sum x + y
+    assert st.n_loads_value_dead == 2                # both loads kept only as checks
+    c2 = [B.cufz_prune_program(p)[1] for p in gen.c2_programs()]
+    assert sum(s.n_ops_kept for s in c2) < 0.95 * sum(s.n_ops_in for s in c2)
+
+
+def test_prune_keeps_values_that_steer_branches_and_indices():
+    """Listing-in-Sec.-5.2 shape: an expensive value feeding a branch that
+    guards an access stays; one only stored goes."""
+    A = Asm(n_bufs=2)
+    t = A.sreg(bc.TID_X)
+    a = A.sreg(bc.ARG0)
+    dead = A.alu(bc.MUL, A.alu(bc.MUL, t, t), a)       # only stored
+    live = A.alu(bc.XOR, A.alu(bc.MUL, t, a), Imm(5))   # steers the branch
+    A.if_(A.alu(bc.SETLT, live, Imm(100)))
+    A.st(0, t, dead)
+    A.endif()
+    idx = A.alu(bc.ADD, A.ld(1, t), Imm(0))             # a loaded value used as index
+    A.ld(0, idx)
+    pruned, st = B.cufz_prune_program(A.build())
+    assert st.n_ops_kept == st.n_ops_in - 2
+    assert st.n_loads_value_dead == 1
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_validator_agrees_with_oracle(orc, seed):
+    rng = gen.SplitMix64(seed)
+    prog = bytearray(rng.choice(all_programs()))
+    for _ in range(rng.randint(1, 3)):
+        pos = rng.randint(0, len(prog) - 1)
+        prog[pos] = rng.below(256)
+    if rng.chance(0.2):
+        prog = prog[: rng.randint(0, len(prog))]
+    p = bytes(prog)
+    assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)
+
+
+def test_division_magic_identity():
+    """The device divides n < 2^32 by a launch dimension d with
+    m = ceil(2^64 / d): floor(n/d) = (m_hi*n + (m_lo*n >> 32)) >> 32."""
+    rng = gen.SplitMix64(5)
+    ds = [1, 2, 3, 5, 7, 31, 32, 33, 100, 1023, 1024, 65535, 65536, (1 << 31) - 1, 1 << 31,
+          (1 << 32) - 1] + [rng.randint(1, (1 << 32) - 1) for _ in range(200)]
+    ns = [0, 1, 2, (1 << 32) - 1, (1 << 31), (1 << 31) - 1] + [rng.next32() for _ in range(300)]
+    for d in ds:
+        m = 0 if d <= 1 else ((1 << 64) - 1) // d + 1
+        for n in ns + [d - 1, d, d + 1, 2 * d - 1, 2 * d]:
+            n &= (1 << 32) - 1
+            if m == 0:
+                q = n
+            else:
+                t = (m & 0xFFFFFFFF) * n
+                q = (((m >> 32) * n + (t >> 32)) >> 32)
+            assert q == n // d, (n, d)
+
+
+def test_arena_sizing():
+    cfg = B.cufz_config_default()
+    a = B.cufz_arena_bytes(cfg, 16)
+    b = B.cufz_arena_bytes(cfg, 32)
+    assert 0 < a < b
+    cfg.record_cap = 1 << 15
+    assert B.cufz_arena_bytes(cfg, 16) > a
+
+
+def test_engine_needs_a_gpu():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(B.CufzError):
+        B.Engine()

@@ -277,6 +277,21 @@ def test_budget_closed_form(orc):
     assert not int(res["flags"]) & orc.FL_BUDGET and int(res["n_accesses"]) == 3 * t0 * t1
 
 
+def test_loop_counter_after_exit(orc):
+    """for (i = 0; i < trip; i++) leaves i == trip (also for trip 0): the
+    counter indexes an access after the loop."""
+    A = Asm(n_bufs=1)
+    r = A.imm(5)
+    c = A.loop(A.sreg(bc.ARG0), 9)
+    A.endloop()
+    A.ld(0, A.alu(bc.ADD, c, Imm(-100)), 4)
+    prog = A.build()
+    assert r != c
+    for t, want in ((0, 0), (3, 3), (50, 9)):
+        _, recs, _ = orc.run(prog, mk(args=(t,), lens=(4,)))
+        assert int(recs[0]["byte_off"]) == 4 * (want - 100)
+
+
 def test_overflow_flag_and_exact_count(orc):
     prog = unguarded_1d()
     res, recs, _ = orc.run(prog, mk((4, 1, 1), (64, 1, 1), (-1000,), (4,)), rec_cap=10)
