@@ -225,7 +225,7 @@ def run_engine(args, rank, world, local, pg):
     wl_name, progs, inputs, cap = workload(args.workload, rank)
     n_all = len(inputs)
     per_step = args.inputs_per_step or n_all
-    flags = B.CF_AUTO_RELEASE | (B.CF_PLAIN_LAUNCH if args.plain else 0)
+    flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
                  cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2)
     for p in progs:
@@ -288,6 +288,10 @@ def run_engine(args, rank, world, local, pg):
     inputs_all = allreduce_sum(pg, tot["inputs"], dev)
     launches = int(st.kernel_launches)
     E.close()
+    try:
+        measured_peak = B.cufz_int32_peak(local, torch.cuda.current_stream(dev).cuda_stream)
+    except Exception:
+        measured_peak = None
 
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
@@ -332,6 +336,8 @@ def run_engine(args, rank, world, local, pg):
             "traffic": None,
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
             "alg_ops_per_step": alg_ops // max(args.steps, 1),
+            "measured_int32_peak": measured_peak / 1e12 if measured_peak else None,
+            "frac_of_measured": achieved / measured_peak if measured_peak else None,
         },
         "e2e": {
             "value": acc_all / wall_s_max if wall_s_max > 0 else 0.0,
