@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4"])
     ap.add_argument("--inputs-per-step", type=int, default=0, help="0: the whole workload")
     ap.add_argument("--plain", action="store_true", help="one kernel launch per input")
+    ap.add_argument("--path", default="jit", choices=["jit", "interp"],
+                    help="compiled programs (default) or the bytecode interpreter")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cta-threads", type=int, default=256)
@@ -226,6 +228,8 @@ def run_engine(args, rank, world, local, pg):
     n_all = len(inputs)
     per_step = args.inputs_per_step or n_all
     flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
+    if args.path == "jit":
+        flags |= B.CF_JIT
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
                  cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2)
     for p in progs:
@@ -315,7 +319,10 @@ def run_engine(args, rank, world, local, pg):
         "config": {
             "workload": wl_name,
             "inputs_per_step": per_step,
-            "path": "plain one launch per input" if args.plain else "persistent kernel in a CUDA graph",
+            "path": ("plain one launch per input" if args.plain else
+                     "persistent kernel in a CUDA graph"),
+            "engine": ("programs compiled to sm_103a at load" if args.path == "jit" else
+                       "bytecode interpreter"),
             "cta_threads": int(st.cta_threads),
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),

@@ -32,8 +32,10 @@
 #ifndef CUFZ_H
 #define CUFZ_H
 
+#if !defined(__CUDACC_RTC__)
 #include <stddef.h>
 #include <stdint.h>
+#endif
 
 #ifdef __cplusplus
 extern "C" {
@@ -79,6 +81,8 @@ typedef int32_t cufz_status;
 #define CUFZ_CF_AUTO_RELEASE 8 /* release a slot as soon as its result is polled */
 #define CUFZ_CF_NO_GRAPH 16    /* launch batches directly, not through a CUDA graph */
 #define CUFZ_CF_NO_DIGEST 32   /* skip the per-access digest */
+#define CUFZ_CF_JIT 64         /* run programs compiled to sm_103a code at load time
+                                  instead of through the bytecode interpreter */
 
 /* Engine configuration.  cufz_config_default fills every field; a zero in
  * max_slots, item_threads or cta_threads means "choose automatically". */
@@ -92,7 +96,7 @@ typedef struct {
   uint32_t record_cap;   /* violation records kept per input */
   uint32_t redzone;      /* R, bytes, for classification (default 256) */
   uint32_t iter_budget;  /* back-edges per test thread before it stops (default 4096) */
-  uint64_t max_threads;  /* test threads per input beyond which LIMIT (<= 2^32-1) */
+  uint64_t max_threads;  /* test threads per input beyond which LIMIT (<= 2^31) */
   uint32_t item_threads; /* test threads per work item (multiple of 32) */
   uint32_t cta_threads;  /* threads per CTA of the persistent kernel (64..1024) */
   uint32_t n_lanes;      /* batches that may overlap on the device (1..8) */
@@ -147,6 +151,7 @@ typedef struct {
   int64_t byte_off; /* index * width */
 } cufz_violation;
 
+#if !defined(__CUDACC_RTC__)
 /* Statistics of a context since creation (or the last reset). */
 typedef struct {
   uint64_t inputs_submitted;
@@ -197,6 +202,19 @@ cufz_status cufz_validate_program(const void* bytes, size_t nbytes);
  * Every access and branch decision of every thread is unchanged. */
 cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void* out, size_t out_cap,
                                size_t* out_bytes, cufz_prog_stats* stats);
+
+/* The CUDA source the compiled path (CUFZ_CF_JIT) generates for one program
+ * (pruned unless flags has CUFZ_CF_NO_PRUNE): a __device__ function running
+ * a work item of that program, NUL-terminated.  *out_bytes receives the size
+ * needed; CUFZ_E_NOMEM if out_cap is smaller. */
+cufz_status cufz_program_cuda(const void* bytes, size_t nbytes, uint32_t flags, char* out,
+                              size_t out_cap, size_t* out_bytes);
+
+/* Generates and runtime-compiles the module for n programs for sm_103a
+ * without loading it (no device needed): CUFZ_OK, or CUFZ_E_INVALID_PROGRAM
+ * with the compiler's log in log. */
+cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, uint32_t n,
+                               uint32_t flags, char* log, uint32_t log_cap, size_t* cubin_bytes);
 
 /* Human-readable name of a status code. */
 const char* cufz_status_str(cufz_status s);
@@ -259,6 +277,13 @@ cufz_status cufz_release(cufz_ctx* ctx, uint64_t ticket);
 /* Waits until every submitted input has completed (bounded). */
 cufz_status cufz_sync(cufz_ctx* ctx, int32_t timeout_us);
 
+/* Compiles every loaded program to sm_103a code with the runtime compiler
+ * (one module; programs become straight-line functions with their registers
+ * in hardware registers) and loads it.  Used by CUFZ_CF_JIT; runs by itself
+ * at the next submit when programs were loaded since the last compile.  The
+ * compiler's log is copied to log (capacity log_cap, may be NULL). */
+cufz_status cufz_compile_programs(cufz_ctx* ctx, char* log, uint32_t log_cap);
+
 cufz_status cufz_get_stats(cufz_ctx* ctx, cufz_stats* out);
 cufz_status cufz_reset_stats(cufz_ctx* ctx);
 
@@ -266,6 +291,8 @@ cufz_status cufz_reset_stats(cufz_ctx* ctx);
  * independent integer add/logic chains on the caller's stream; writes lane
  * operations per second. */
 cufz_status cufz_int32_peak(int32_t device, void* stream, double* lane_ops_per_s);
+
+#endif /* !__CUDACC_RTC__ */
 
 #ifdef __cplusplus
 }

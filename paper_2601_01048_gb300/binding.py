@@ -21,8 +21,8 @@ E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUN
     E_NO_DEVICE, E_DEVICE_FAULT = range(-1, -10, -1)
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
-CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST = \
-    1, 2, 4, 8, 16, 32
+CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \
+    CF_JIT = 1, 2, 4, 8, 16, 32, 64
 
 RESULT_DTYPE = np.dtype([
     ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),
@@ -79,7 +79,7 @@ EXPORTS = [
     "cufz_status_str", "cufz_create", "cufz_destroy", "cufz_load_program", "cufz_submit_inputs",
     "cufz_poll_results", "cufz_get_records", "cufz_get_bitmap", "cufz_get_union",
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
-    "cufz_int32_peak",
+    "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
 ]
 
 
@@ -113,6 +113,9 @@ def lib():
                 "cufz_get_stats": (i32, [vp, P(cufz_stats)]),
                 "cufz_reset_stats": (i32, [vp]),
                 "cufz_int32_peak": (i32, [i32, vp, P(ctypes.c_double)]),
+                "cufz_compile_programs": (i32, [vp, ctypes.c_char_p, u32]),
+                "cufz_program_cuda": (i32, [vp, sz, u32, ctypes.c_char_p, sz, P(sz)]),
+                "cufz_compile_check": (i32, [vp, vp, u32, u32, ctypes.c_char_p, u32, P(sz)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -241,6 +244,39 @@ def cufz_get_stats(ctx) -> cufz_stats:
 
 def cufz_reset_stats(ctx) -> None:
     _check(lib().cufz_reset_stats(ctx), "cufz_reset_stats")
+
+
+def cufz_compile_programs(ctx) -> str:
+    """Compiles the loaded programs for the compiled path; returns the log."""
+    buf = ctypes.create_string_buffer(1 << 16)
+    st = lib().cufz_compile_programs(ctx, buf, len(buf))
+    log = buf.value.decode(errors="replace")
+    if st < 0:
+        raise CufzError(st, "cufz_compile_programs: " + log[-2000:])
+    return log
+
+
+def cufz_program_cuda(prog: bytes, flags: int = 0) -> str:
+    n = ctypes.c_size_t(0)
+    lib().cufz_program_cuda(_bytes_ptr(prog), len(prog), flags, None, 0, ctypes.byref(n))
+    buf = ctypes.create_string_buffer(max(n.value, 1))
+    _check(lib().cufz_program_cuda(_bytes_ptr(prog), len(prog), flags, buf, len(buf),
+                                   ctypes.byref(n)), "cufz_program_cuda")
+    return buf.value.decode()
+
+
+def cufz_compile_check(progs: list[bytes], flags: int = 0) -> tuple[int, str, int]:
+    """Runtime-compiles the module of `progs` without a device; returns
+    (status, log, cubin bytes)."""
+    bufs = [ctypes.create_string_buffer(p, len(p)) for p in progs]
+    ptrs = (ctypes.c_void_p * max(len(progs), 1))(*[ctypes.cast(b, ctypes.c_void_p) for b in bufs])
+    sizes = (ctypes.c_size_t * max(len(progs), 1))(*[len(p) for p in progs])
+    log = ctypes.create_string_buffer(1 << 16)
+    nb = ctypes.c_size_t(0)
+    st = lib().cufz_compile_check(ctypes.cast(ptrs, ctypes.c_void_p),
+                                  ctypes.cast(sizes, ctypes.c_void_p), len(progs), flags, log,
+                                  len(log), ctypes.byref(nb))
+    return st, log.value.decode(errors="replace"), nb.value
 
 
 def cufz_int32_peak(device: int = 0, stream: int = 0) -> float:

@@ -27,43 +27,10 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "device_common.cuh"
 #include "engine.h"
 
 namespace cufz {
-
-constexpr uint32_t FULL = 0xFFFFFFFFu;
-constexpr uint32_t kFlagEngineError = 0x80000000u;
-constexpr uint32_t kHashCountMask = 0x7FFFu;
-constexpr int kHashTagShift = 15;
-constexpr uint32_t kInputSmemBytes = 336;  // DevInput rounded up to 16
-
-__device__ __forceinline__ uint32_t mix32(uint32_t h) {
-  // MurmurHash3 fmix32 finalizer
-  h ^= h >> 16;
-  h *= 0x85EBCA6Bu;
-  h ^= h >> 13;
-  h *= 0xC2B2AE35u;
-  h ^= h >> 16;
-  return h;
-}
-
-// floor(n / d) for n < 2^32 with m = ceil(2^64 / d) (m == 0 means d == 1).
-__device__ __forceinline__ uint32_t udiv(uint32_t n, uint64_t m) {
-  if (m == 0) return n;
-  uint64_t t = (uint64_t)(uint32_t)m * n;
-  uint64_t u = (uint64_t)(uint32_t)(m >> 32) * n + (t >> 32);
-  return (uint32_t)(u >> 32);
-}
-
-__device__ __forceinline__ uint32_t afl_bucket(uint32_t n) {
-  if (n <= 2) return n;
-  if (n == 3) return 4;
-  if (n < 8) return 8;
-  if (n < 16) return 16;
-  if (n < 32) return 32;
-  if (n < 128) return 64;
-  return 128;
-}
 
 __device__ __forceinline__ int32_t rf_ld(const uint8_t* rf, uint32_t off) {
   return *reinterpret_cast<const int32_t*>(rf + off);
@@ -94,68 +61,6 @@ __device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y) {
   }
 }
 
-// Adds c hits of edge e to the slot's global counters, appending e to the
-// touched list the first time it becomes nonzero.
-__device__ __forceinline__ void edge_global_add(const EngineTables& T, uint32_t slot, uint32_t e,
-                                                uint32_t c) {
-  uint32_t old = atomicAdd(&T.counts[(size_t)slot * kEdgeCount + e], c);
-  if (old == 0) {
-    uint32_t k = atomicAdd(&T.slots[slot].n_touched, 1u);
-    T.touched[(size_t)slot * kEdgeCount + k] = (uint16_t)e;
-  }
-}
-
-// Per-CTA hash table entry: (e + 1) << 15 | count (count saturates near 128;
-// at most 127 + 32 * 32 < 2^15 with every warp adding at once).
-__device__ __forceinline__ void edge_add(uint32_t* hash, const EngineTables& T, uint32_t slot,
-                                         uint32_t e, uint32_t c) {
-  uint32_t tag = (e + 1u) << kHashTagShift;
-  uint32_t h = (e * 2654435761u) >> (32 - 11);
-  static_assert(kHashSlots == 2048, "hash index uses 11 bits");
-#pragma unroll 1
-  for (int p = 0; p < kHashProbes; p++) {
-    uint32_t cur = hash[h];
-    if ((cur & ~kHashCountMask) == tag) {
-      if ((cur & kHashCountMask) < 128u) atomicAdd(&hash[h], c);
-      return;
-    }
-    if (cur == 0) {
-      uint32_t old = atomicCAS(&hash[h], 0u, tag | c);
-      if (old == 0) return;
-      if ((old & ~kHashCountMask) == tag) {
-        if ((old & kHashCountMask) < 128u) atomicAdd(&hash[h], c);
-        return;
-      }
-    }
-    h = (h + 1) & (kHashSlots - 1);
-  }
-  edge_global_add(T, slot, e, c);
-}
-
-// Violation class from the virtual layout of the input's buffers.
-__device__ __noinline__ uint32_t classify(const DevInput* in, uint32_t shared_mask, uint32_t n_bufs,
-                                          uint32_t buf, int64_t off, uint32_t w, int64_t R) {
-  int64_t len = in->len[buf];
-  if (off < 0 && off >= -R) return CUFZ_CLS_UNDERFLOW_RZ;
-  if (off >= 0 && off < len + R) return CUFZ_CLS_OVERFLOW_RZ;
-  uint32_t sp = (shared_mask >> buf) & 1u;
-  int64_t a = in->base[buf] + off;
-  for (uint32_t j = 0; j < n_bufs; j++) {
-    if (j == buf || ((shared_mask >> j) & 1u) != sp) continue;
-    int64_t lj = in->len[j];
-    if (lj > 0 && a < in->base[j] + lj && a + (int64_t)w > in->base[j]) return CUFZ_CLS_OTHER_ALLOC;
-  }
-  return CUFZ_CLS_WILD;
-}
-
-struct LaneAcc {
-  uint32_t n_acc;
-  uint32_t n_branch;
-  uint32_t n_ops;
-  unsigned long long digest;
-  unsigned long long first_key;
-};
-
 // Runs the test threads [g0, g0 + count) of one input on this warp's lanes.
 __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* in,
                                          const uint8_t* sprog, uint8_t* rf_warp, uint32_t* hash,
@@ -180,10 +85,9 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
   uint8_t* rf = rf_warp + lane * kLaneBytes;
   const uint32_t lanemask_lt = (1u << lane) - 1u;
 
-  LaneAcc acc{0, 0, 0, 0ull, ~0ull};
-  uint32_t warp_viol = 0;  // warp-uniform
-  bool full = false;       // warp-uniform: record area known to be full
-  bool budget_hit = false;
+  LaneAcc acc;
+  acc_init(acc);
+  bool full = false;  // warp-uniform: record area known to be full
 
   const uint32_t g_end = g0 + count;
   for (uint32_t base = g0 + warp * 32u; base < g_end; base += nwarps * 32u) {
@@ -278,7 +182,6 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           if (vm) {
             const uint32_t k = __popc(vm);
             const uint32_t leader = __ffs(vm) - 1;
-            warp_viol += k;
             uint32_t rbase = 0xFFFFFFFFu;
             if (!full) {
               if (lane == leader) rbase = atomicAdd(&S->rec_reserved, k);
@@ -286,25 +189,14 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
               if (rbase + k >= cap) full = true;
             }
             if (viol) {
-              const uint32_t ord = ordinal < 0x3FFFFFu ? ordinal : 0x3FFFFFu;
-              const unsigned long long key =
-                  ((unsigned long long)bl << 32) | ((unsigned long long)tl << 22) | ord;
-              if (key < acc.first_key) acc.first_key = key;
+              acc.n_viol++;
+              if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
               const uint32_t rank = __popc(vm & lanemask_lt);
               if (rbase != 0xFFFFFFFFu && rbase + rank < cap) {
-                const uint32_t cls = classify(in, shared_mask, n_bufs, buf, off, w, (int64_t)T.redzone);
-                uint4 lo, hi;
-                lo.x = bl;
-                lo.y = tl;
-                lo.z = ordinal;
-                lo.w = (uint32_t)op.imm | (buf << 16) | ((opc == D_ST ? 1u : 0u) << 24);
-                hi.x = w | (((shared_mask >> buf) & 1u) << 8) | (cls << 16);
-                hi.y = 0;
-                hi.z = (uint32_t)(uint64_t)off;
-                hi.w = (uint32_t)((uint64_t)off >> 32);
-                uint4* dst = reinterpret_cast<uint4*>(recs + rbase + rank);
-                dst[0] = lo;
-                dst[1] = hi;
+                const uint32_t cls =
+                    classify(in, shared_mask, n_bufs, buf, off, w, (int64_t)T.redzone);
+                write_record(recs + rbase + rank, bl, tl, ordinal, (uint32_t)op.imm, buf,
+                             opc == D_ST ? 1u : 0u, w, (shared_mask >> buf) & 1u, cls, off);
               }
             }
           }
@@ -370,7 +262,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
             if (back > budget) {
               alive = false;
               act = false;
-              budget_hit = true;
+              acc.budget_hit = true;
               stk_aux &= ~1u;
             } else {
               rf_st(rf, op.d, rf_ld(rf, op.d) + 1);
@@ -411,105 +303,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
     }
   }
 
-  // warp reductions, then one atomic per counter per warp
-  unsigned long long dig = acc.digest;
-  unsigned long long fk = acc.first_key;
-  uint32_t na = acc.n_acc, nb = acc.n_branch, no = acc.n_ops;
-#pragma unroll
-  for (int s = 16; s > 0; s >>= 1) {
-    dig += __shfl_xor_sync(FULL, dig, s);
-    unsigned long long o = __shfl_xor_sync(FULL, fk, s);
-    fk = o < fk ? o : fk;
-    na += __shfl_xor_sync(FULL, na, s);
-    nb += __shfl_xor_sync(FULL, nb, s);
-    no += __shfl_xor_sync(FULL, no, s);
-  }
-  const bool bh = __any_sync(FULL, budget_hit);
-  if (lane == 0) {
-    if (na) atomicAdd(&S->n_accesses, (unsigned long long)na);
-    if (dig) atomicAdd(&S->digest, dig);
-    if (nb) atomicAdd(&S->n_branch, (unsigned long long)nb);
-    if (no) atomicAdd(&S->n_ops, (unsigned long long)no);
-    if (warp_viol) atomicAdd(&S->n_violations, (unsigned long long)warp_viol);
-    if (fk != ~0ull) atomicMin(&S->first_key, fk);
-    if (bh) atomicOr(&S->flags, (uint32_t)CUFZ_FL_BUDGET);
-  }
-}
-
-// Last CTA of an input: bucket the touched edges into the bitmap, OR them
-// into the union, compare with the epoch snapshot, publish the result.
-__device__ void finalize_input(const EngineTables& T, const DevInput* in, uint32_t* s_flag) {
-  const uint32_t slot = in->slot;
-  SlotState* S = &T.slots[slot];
-  const uint32_t nt = *reinterpret_cast<volatile uint32_t*>(&S->n_touched);
-  const bool keep = T.flags & CUFZ_CF_KEEP_BITMAPS;
-  uint8_t* bm = T.bitmaps ? T.bitmaps + (size_t)slot * kBitmapBytes : nullptr;
-  uint32_t* counts = T.counts + (size_t)slot * kEdgeCount;
-  const uint16_t* touched = T.touched + (size_t)slot * kEdgeCount;
-  if (keep) {
-    uint4 z = make_uint4(0, 0, 0, 0);
-    for (uint32_t i = threadIdx.x; i < kBitmapBytes / 16; i += blockDim.x)
-      reinterpret_cast<uint4*>(bm)[i] = z;
-  }
-  __syncthreads();
-  int newcov = 0;
-  for (uint32_t k = threadIdx.x; k < nt; k += blockDim.x) {
-    const uint32_t e = touched[k];
-    const uint32_t c = counts[e];
-    counts[e] = 0;
-    const uint32_t b = afl_bucket(c);
-    if (keep) bm[e] = (uint8_t)b;
-    const uint32_t sh = (e & 3u) * 8u;
-    const uint32_t snap = (T.union_snap[e >> 2] >> sh) & 0xFFu;
-    if (b & ~snap) newcov = 1;
-    atomicOr(&T.union_map[e >> 2], b << sh);
-  }
-  newcov = __syncthreads_or(newcov);
-  if (threadIdx.x == 0) {
-    volatile SlotState* vS = S;
-    const unsigned long long nviol = vS->n_violations;
-    const uint32_t reserved = vS->rec_reserved;
-    HostDone* hd = &T.done[slot];
-    cufz_result r;
-    r.ticket = in->ticket;
-    r.user_tag = in->user_tag;
-    uint32_t flags = vS->flags;
-    r.status = (flags & kFlagEngineError) ? CUFZ_E_DEVICE_FAULT
-                                          : (nviol ? CUFZ_ST_VIOLATION : CUFZ_ST_OK);
-    flags &= ~kFlagEngineError;
-    if (nviol > T.record_cap) flags |= CUFZ_FL_OVERFLOW;
-    if (newcov) flags |= CUFZ_FL_NEW_COV;
-    r.flags = flags;
-    r.n_accesses = vS->n_accesses;
-    r.n_violations = nviol;
-    r.first_key = vS->first_key;
-    r.digest = vS->digest;
-    r.n_branch = vS->n_branch;
-    r.n_threads = in->n_threads;
-    r.n_ops = vS->n_ops;
-    r.n_records = reserved < T.record_cap ? reserved : T.record_cap;
-    r.n_edges = nt;
-    r.reserved = 0;
-    // reset the slot for its next input
-    vS->n_accesses = 0;
-    vS->n_violations = 0;
-    vS->digest = 0;
-    vS->n_branch = 0;
-    vS->n_ops = 0;
-    vS->first_key = ~0ull;
-    vS->rec_reserved = 0;
-    vS->n_touched = 0;
-    vS->items_done = 0;
-    vS->flags = 0;
-    const uint64_t* src = reinterpret_cast<const uint64_t*>(&r);
-    volatile uint64_t* dst = reinterpret_cast<volatile uint64_t*>(&hd->res);
-#pragma unroll
-    for (int k = 0; k < (int)(sizeof(cufz_result) / 8); k++) dst[k] = src[k];
-    __threadfence_system();
-    hd->seq = in->seq;
-    __threadfence_system();
-  }
-  (void)s_flag;
+  acc_flush(T, slot, acc);
 }
 
 // Shared memory: hash table | program blob | DevInput | register file.
@@ -522,94 +316,16 @@ __global__ void __launch_bounds__(1024) interp_kernel(EngineTables T, BatchHdr* 
   uint8_t* sprog = smem + kHashSlots * 4;
   DevInput* sin = reinterpret_cast<DevInput*>(sprog + max_prog_bytes);
   uint8_t* rf = reinterpret_cast<uint8_t*>(sin) + kInputSmemBytes;
-  __shared__ uint32_t s_item, s_last, s_skip;
-
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t nwarps = blockDim.x >> 5;
-  const DevInput* inputs =
-      reinterpret_cast<const DevInput*>(reinterpret_cast<const uint8_t*>(batch) + batch->inputs_off);
-  const WorkItem* items =
-      reinterpret_cast<const WorkItem*>(reinterpret_cast<const uint8_t*>(batch) + batch->items_off);
-  const uint32_t n_items = kPersistent ? batch->n_items : 1u;
-
-  for (uint32_t i = threadIdx.x; i < kHashSlots; i += blockDim.x) hash[i] = 0;
-  uint32_t cur_input = 0xFFFFFFFFu, cur_prog = 0xFFFFFFFFu;
-  bool first = true;
-
-  for (;;) {
-    uint32_t in_idx, g0, cnt;
-    if (kPersistent) {
-      if (threadIdx.x == 0) s_item = atomicAdd(&batch->next_item, 1u);
-      __syncthreads();
-      const uint32_t it = s_item;
-      if (it >= n_items) break;
-      const WorkItem w = items[it];
-      in_idx = w.input;
-      g0 = w.g0;
-      cnt = w.count;
-    } else {
-      if (!first) break;
-      in_idx = plain_input;
-      const uint32_t Tb = inputs[in_idx].T;
-      g0 = blockIdx.x * Tb;
-      cnt = Tb;
-    }
-    first = false;
-    if (in_idx != cur_input) {
-      const uint32_t* src = reinterpret_cast<const uint32_t*>(&inputs[in_idx]);
-      uint32_t* dst = reinterpret_cast<uint32_t*>(sin);
-      for (uint32_t i = threadIdx.x; i < sizeof(DevInput) / 4; i += blockDim.x) dst[i] = src[i];
-      __syncthreads();
-      if (threadIdx.x == 0) {
-        uint32_t skip = 0;
-        if (sin->prog_bytes > max_prog_bytes) skip = 1;
-        s_skip = skip;
-      }
-      __syncthreads();
-      if (!s_skip && sin->prog_off != cur_prog) {
-        const uint4* ps = reinterpret_cast<const uint4*>(T.progs + sin->prog_off);
-        uint4* pd = reinterpret_cast<uint4*>(sprog);
-        for (uint32_t i = threadIdx.x; i < sin->prog_bytes / 16; i += blockDim.x) pd[i] = ps[i];
-        cur_prog = sin->prog_off;
-      }
-      __syncthreads();
-      if (!s_skip && reinterpret_cast<const DevProgHdr*>(sprog)->n_regs > max_regs && threadIdx.x == 0)
-        s_skip = 1;
-      __syncthreads();
-      cur_input = in_idx;
-    }
-    if (!s_skip) {
-      run_warp(T, sin, sprog, rf + (size_t)warp * max_regs * kRegStride, hash, g0, cnt, warp,
-               nwarps);
-    } else if (threadIdx.x == 0) {
-      atomicOr(&T.slots[sin->slot].flags, kFlagEngineError);
-      atomicOr(&batch->error, 1u);
-    }
-    __syncthreads();
-    // flush the CTA's edge table into the slot's counters
-    const uint32_t slot = sin->slot;
-    for (uint32_t i = threadIdx.x; i < kHashSlots; i += blockDim.x) {
-      const uint32_t v = hash[i];
-      if (v) {
-        const uint32_t e = (v >> kHashTagShift) - 1u;
-        uint32_t c = v & kHashCountMask;
-        edge_global_add(T, slot, e, c < 128u ? c : 128u);
-        hash[i] = 0;
-      }
-    }
-    __threadfence();
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      const uint32_t done = atomicAdd(&T.slots[slot].items_done, 1u);
-      s_last = (done + 1u == sin->n_items) ? 1u : 0u;
-    }
-    __syncthreads();
-    if (s_last) {
-      __threadfence();
-      finalize_input(T, sin, &s_last);
-    }
-    __syncthreads();
-  }
+  run_items<kPersistent, true>(
+      T, batch, plain_input, max_regs, max_prog_bytes, hash, sprog, sin,
+      [&](const DevInput* in, uint32_t g0, uint32_t cnt, bool skip) -> bool {
+        if (skip) return false;
+        run_warp(T, in, sprog, rf + (size_t)warp * max_regs * kRegStride, hash, g0, cnt, warp,
+                 nwarps);
+        return true;
+      });
 }
 
 template __global__ void interp_kernel<true>(EngineTables, BatchHdr*, uint32_t, uint32_t, uint32_t);

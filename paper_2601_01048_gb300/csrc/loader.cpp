@@ -14,6 +14,8 @@
 #include <cstdint>
 #include <cstdlib>
 #include <cstring>
+#include <cstdio>
+#include <string>
 #include <vector>
 
 #include "engine.h"
@@ -454,12 +456,248 @@ void fill_stats(const Ir& ir, int n_in, int regs_alloc, cufz_prog_stats* st) {
 
 }  // namespace
 
-// ---------------------------------------------------------------- public
 
-cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
+// ------------------------------------------------------------ code generator
+// Emits one __device__ function running a work item of program `index`: a
+// loop over the item's test threads (one per CUDA thread) whose body is the
+// pruned program as straight-line CUDA.  Program registers become int32
+// locals (all 0 at thread start, as in the program semantics), structured
+// IF/LOOP become C++ if/for, every access is an inline bounds check with
+// constant buffer, width and site, and every branch evaluation an inline AFL
+// edge update with constant LOC values.
+namespace {
+
+struct Gen {
+  const Ir& ir;
+  std::string& o;
+  int index;
+  bool has_loop = false;
+
+  void line(int ind, const std::string& t) {
+    o.append((size_t)ind * 2, ' ');
+    o += t;
+    o += '\n';
+  }
+  static std::string hex32(uint32_t v) {
+    char b[24];
+    snprintf(b, sizeof b, "0x%08Xu", v);
+    return b;
+  }
+  static std::string r(int v) { return "r" + std::to_string(v); }
+  static std::string imm(int32_t v) { return "((int32_t)" + hex32((uint32_t)v) + ")"; }
+
+  std::string alu_expr(int op, const std::string& x, const std::string& y) {
+    switch (op) {
+      case 0: return "(int32_t)((uint32_t)" + x + " + (uint32_t)" + y + ")";
+      case 1: return "(int32_t)((uint32_t)" + x + " - (uint32_t)" + y + ")";
+      case 2: return "(int32_t)((uint32_t)" + x + " * (uint32_t)" + y + ")";
+      case 3: return "(int32_t)((uint32_t)" + x + " << ((uint32_t)" + y + " & 31u))";
+      case 4: return "(int32_t)(" + x + " >> ((uint32_t)" + y + " & 31u))";
+      case 5: return "(int32_t)((uint32_t)" + x + " >> ((uint32_t)" + y + " & 31u))";
+      case 6: return "(int32_t)(" + x + " & " + y + ")";
+      case 7: return "(int32_t)(" + x + " | " + y + ")";
+      case 8: return "(int32_t)(" + x + " ^ " + y + ")";
+      case 9: return "(" + x + " < " + y + " ? " + x + " : " + y + ")";
+      case 10: return "(" + x + " > " + y + " ? " + x + " : " + y + ")";
+      case 11: return "(int32_t)(" + x + " < " + y + ")";
+      case 12: return "(int32_t)(" + x + " <= " + y + ")";
+      case 13: return "(int32_t)(" + x + " == " + y + ")";
+      case 14: return "(int32_t)(" + x + " != " + y + ")";
+      default: return "(int32_t)((uint32_t)" + x + " < (uint32_t)" + y + ")";
+    }
+  }
+
+  static const char* sreg_name(int id) {
+    static const char* n[16] = {"s_tx", "s_ty", "s_tz", "s_ntx", "s_nty", "s_ntz", "s_bx", "s_by",
+                                "s_bz", "s_ngx", "s_ngy", "s_ngz", "s_a0", "s_a1", "s_a2", "s_a3"};
+    return n[id];
+  }
+
+  bool counted(const IrOp& o2) const {
+    return o2.kept && o2.opc != B_SREG && is_value_op(o2.opc);
+  }
+
+  // n_ops of the straight-line run starting at pc (up to the next IF/LOOP or end)
+  int run_ops(int pc, int end) const {
+    int k = 0;
+    while (pc < end) {
+      const IrOp& o2 = ir.ops[pc];
+      if (o2.opc == B_IF || o2.opc == B_LOOP) break;
+      if (counted(o2)) k++;
+      pc++;
+    }
+    return k;
+  }
+
+  void cover(int ind, int site, const std::string& cond) {
+    uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
+    line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
+                  "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1; acc.n_branch++;"
+                  " jit_cover(T, hash, slot, e); }");
+  }
+
+  void access(int ind, const IrOp& o2) {
+    int lw = log2w(o2.width);
+    bool shared = (ir.shared_mask >> o2.buf) & 1u;
+    std::string L = "L" + std::to_string(o2.buf);
+    line(ind, "{");
+    line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
+    line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
+    line(ind + 1, "const bool viol = (ix < 0) | (off + " + std::to_string(o2.width) + " > " + L + ");");
+    line(ind + 1, "acc.n_acc++;");
+    line(ind + 1, "if (dig) acc.digest += jit_digest(th, ordinal, " +
+                      hex32((uint32_t)o2.site * 0xC2B2AE3Du) + ", off);");
+    uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
+                    ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
+    line(ind + 1, "if (viol) jit_violation(T, in, acc, bl, tl, ordinal, " + hex32(what) + ", off);");
+    if (o2.opc == B_LD && !o2.value_dead) {
+      if (shared) {
+        line(ind + 1, r(o2.dst) + " = 0;");
+      } else {
+        uint32_t seedx = ir.seed ^ ((uint32_t)o2.buf * 0x9E3779B9u);
+        line(ind + 1, r(o2.dst) + " = viol ? 0 : jit_content(" + hex32(seedx) + ", off, " +
+                          std::to_string(lw) + "u);");
+      }
+    }
+    line(ind + 1, "ordinal++;");
+    line(ind, "}");
+  }
+
+  void range(int ind, int pc, int end) {
+    int k = run_ops(pc, end);
+    if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
+    while (pc < end) {
+      const IrOp& o2 = ir.ops[pc];
+      if (!o2.kept) {
+        pc++;
+        continue;
+      }
+      uint8_t opc = o2.opc;
+      if (is_alu_reg(opc)) {
+        line(ind, r(o2.dst) + " = " + alu_expr(opc - 0x10, r(o2.a), r(o2.b)) + ";");
+      } else if (is_alu_imm(opc)) {
+        line(ind, r(o2.dst) + " = " + alu_expr(opc - 0x30, r(o2.a), imm(o2.imm)) + ";");
+      } else if (opc == B_SREG) {
+        line(ind, r(o2.dst) + " = " + sreg_name(o2.sreg) + ";");
+      } else if (opc == B_IMM) {
+        line(ind, r(o2.dst) + " = " + imm(o2.imm) + ";");
+      } else if (opc == B_MOV) {
+        line(ind, r(o2.dst) + " = " + r(o2.a) + ";");
+      } else if (opc == B_SEL) {
+        line(ind, r(o2.dst) + " = " + r(o2.a) + " != 0 ? " + r(o2.b) + " : " + r(o2.c) + ";");
+      } else if (opc == B_LD || opc == B_ST) {
+        access(ind, o2);
+      } else if (opc == B_IF) {
+        std::string c = "c" + std::to_string(o2.site);
+        line(ind, "{");
+        line(ind + 1, "const bool " + c + " = " + r(o2.a) + " != 0;");
+        cover(ind + 1, o2.site, c);
+        line(ind + 1, "if (" + c + ") {");
+        range(ind + 2, pc + 1, o2.else_pc >= 0 ? o2.else_pc : o2.end_pc);
+        if (o2.else_pc >= 0) {
+          line(ind + 1, "} else {");
+          range(ind + 2, o2.else_pc + 1, o2.end_pc);
+        }
+        line(ind + 1, "}");
+        line(ind, "}");
+        pc = o2.end_pc + 1;
+        int k2 = run_ops(pc, end);
+        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        continue;
+      } else if (opc == B_LOOP) {
+        has_loop = true;
+        std::string t = "trip" + std::to_string(o2.site), c = "cont" + std::to_string(o2.site);
+        std::string n = "n" + std::to_string(o2.site);
+        line(ind, "{");
+        line(ind + 1, "const int32_t " + n + " = " + r(o2.a) + ";");
+        line(ind + 1, "const int32_t " + t + " = " + n + " < 0 ? 0 : (" + n + " > " +
+                          std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + " : " + n + ");");
+        line(ind + 1, r(o2.dst) + " = 0;");
+        line(ind + 1, "#pragma unroll 1");
+        line(ind + 1, "for (;;) {");
+        line(ind + 2, "const bool " + c + " = " + r(o2.dst) + " < " + t + ";");
+        cover(ind + 2, o2.site, c);
+        line(ind + 2, "if (!" + c + ") break;");
+        range(ind + 2, pc + 1, o2.end_pc);
+        line(ind + 2, "if (++back > budget) { acc.budget_hit = true; goto cufz_done; }");
+        line(ind + 2, r(o2.dst) + "++;");
+        line(ind + 1, "}");
+        line(ind, "}");
+        pc = o2.end_pc + 1;
+        int k2 = run_ops(pc, end);
+        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        continue;
+      }
+      pc++;
+    }
+  }
+
+  void emit() {
+    std::vector<bool> used(ir.nv, false), sreg_used(16, false), buf_used(kMaxBufs, false);
+    int U[4], D[4], nu, nd;
+    for (const auto& op : ir.ops) {
+      uses_defs(op, false, U, &nu, D, &nd);
+      for (int k = 0; k < nu; k++) used[U[k]] = true;
+      for (int k = 0; k < nd; k++) used[D[k]] = true;
+      if (op.kept && op.opc == B_SREG) sreg_used[op.sreg] = true;
+      if (op.kept && (op.opc == B_LD || op.opc == B_ST)) buf_used[op.buf] = true;
+    }
+    std::string fn = "cufz_prog_" + std::to_string(index);
+    line(0, "__device__ __noinline__ void " + fn +
+                "(const EngineTables* __restrict__ T, const DevInput* __restrict__ in, uint32_t* hash,"
+                " uint32_t g0, uint32_t g_end) {");
+    line(1, "const uint32_t slot = in->slot;");
+    line(1, "LaneAcc acc;");
+    line(1, "acc_init(acc);");
+    line(1, "const uint32_t budget = T->iter_budget;");
+    line(1, "const bool dig = !(T->flags & CUFZ_CF_NO_DIGEST);");
+    line(1, "const uint64_t mT = in->mT; const uint32_t Tb = in->T;");
+    for (int b = 0; b < ir.n_bufs; b++)
+      if (buf_used[b]) line(1, "const int64_t L" + std::to_string(b) + " = in->len[" + std::to_string(b) + "];");
+    bool need_t = sreg_used[0] || sreg_used[1] || sreg_used[2];
+    bool need_b = sreg_used[6] || sreg_used[7] || sreg_used[8];
+    if (need_t) line(1, "const uint64_t mBx = in->mBx, mBxy = in->mBxy; const uint32_t Bx = in->Bx, By = in->block[1];");
+    if (need_b) line(1, "const uint64_t mGx = in->mGx, mGxy = in->mGxy; const uint32_t Gx = in->gx, Gy = in->grid[1];");
+    for (int k = 0; k < 3; k++) {
+      if (sreg_used[3 + k]) line(1, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)in->block[" + std::to_string(k) + "];");
+      if (sreg_used[9 + k]) line(1, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)in->grid[" + std::to_string(k) + "];");
+    }
+    for (int k = 0; k < 4; k++)
+      if (sreg_used[12 + k]) line(1, std::string("const int32_t ") + sreg_name(12 + k) + " = in->args[" + std::to_string(k) + "];");
+    line(1, "#pragma unroll 1");
+    line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
+    line(2, "const uint32_t bl = udiv(g, mT);");
+    line(2, "const uint32_t tl = g - bl * Tb;");
+    if (need_t) {
+      line(2, "const uint32_t q1 = udiv(tl, mBx), tz_ = udiv(tl, mBxy);");
+      line(2, "const int32_t s_tx = (int32_t)(tl - q1 * Bx), s_ty = (int32_t)(q1 - tz_ * By), s_tz = (int32_t)tz_;");
+    }
+    if (need_b) {
+      line(2, "const uint32_t p1 = udiv(bl, mGx), bz_ = udiv(bl, mGxy);");
+      line(2, "const int32_t s_bx = (int32_t)(bl - p1 * Gx), s_by = (int32_t)(p1 - bz_ * Gy), s_bz = (int32_t)bz_;");
+    }
+    line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
+    line(2, "uint32_t prev = 0, ordinal = 0, back = 0;");
+    line(2, "(void)prev; (void)ordinal; (void)back; (void)th;");
+    std::string decl;
+    for (int v = 0; v < 256; v++)
+      if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
+    if (!decl.empty()) line(2, decl + ";");
+    range(2, 0, (int)ir.ops.size());
+    if (has_loop) line(1, "cufz_done:;");
+    line(1, "}");
+    line(1, "__syncwarp();");
+    line(1, "acc_flush(*T, slot, acc);");
+    line(0, "}");
+  }
+};
+
+}  // namespace
+
+cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, uint32_t index,
+                       std::string* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
-  int n_in = (int)ir.ops.size();
   if (do_prune) {
     prune(&ir);
   } else {
@@ -467,6 +705,19 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
     for (size_t pc = 0; pc < ir.ops.size(); pc++)
       if (ir.ops[pc].opc == B_LD) ir.ops[pc].value_dead = !L.out[pc].get(ir.ops[pc].dst);
   }
+  out->clear();
+  Gen g{ir, *out, (int)index};
+  g.emit();
+  return CUFZ_OK;
+}
+
+// ---------------------------------------------------------------- public
+
+cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
+  Ir ir;
+  if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  int n_in = (int)ir.ops.size();
+  if (do_prune) prune(&ir);
   propagate_sregs(&ir);
   std::vector<int> map;
   Bits entry;

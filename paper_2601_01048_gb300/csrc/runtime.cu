@@ -10,6 +10,7 @@
 // run, and each input's work is split into block ranges that persistent
 // CTAs pull from a device queue.
 #include <cuda_runtime.h>
+#include <nvrtc.h>
 
 #include <algorithm>
 #include <atomic>
@@ -18,10 +19,12 @@
 #include <deque>
 #include <mutex>
 #include <thread>
+#include <future>
 #include <unordered_map>
 #include <vector>
 
 #include "engine.h"
+#include "jit_embed.h"  // generated at build time: header texts for the runtime compiler
 
 using namespace cufz;
 
@@ -60,6 +63,7 @@ struct Lane {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphNode_t copy_node = nullptr;
   uint32_t graph_regs = 0, graph_prog = 0, graph_ctas = 0, graph_threads = 0;
+  const void* graph_kernel = nullptr;
 };
 
 struct HostOnlyResult {
@@ -101,6 +105,13 @@ struct cufz_ctx {
   uint32_t* d_scratch_word = nullptr;
   cudaStream_t copy_stream = nullptr;
   cufz_stats stats{};
+  // compiled path
+  std::vector<std::string> prog_src;  // CUDA source of each program's item function
+  cudaLibrary_t jit_lib = nullptr;
+  cudaKernel_t jit_persist = nullptr, jit_plain = nullptr;
+  uint32_t jit_progs = 0;             // programs in the loaded module
+  uint32_t jit_ctas_per_sm = 0;
+  std::string jit_log;
 };
 
 namespace {
@@ -222,18 +233,156 @@ cufz_status ensure_smem(cufz_ctx* c) {
   return CUFZ_OK;
 }
 
+
+bool use_jit(const cufz_ctx* c) { return (c->cfg.flags & CUFZ_CF_JIT) != 0; }
+
+// The compiled path's module: every program's item function, the dispatcher
+// and the kernels, compiled as one translation unit so the program functions
+// are register-allocated together with the kernel that calls them.
+std::string jit_module_source(const std::vector<std::string>& prog_src, bool plain_kernel) {
+  std::string src = "#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
+  for (const auto& f : prog_src) src += f;
+  src += "static __device__ bool jit_run(uint32_t prog, const EngineTables* T, const DevInput* in, "
+         "uint32_t* hash, uint32_t g0, uint32_t g_end) {\n  switch (prog) {\n";
+  for (size_t k = 0; k < prog_src.size(); k++)
+    src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
+           "(T, in, hash, g0, g_end); return true;\n";
+  src += "    default: return false;\n  }\n}\n}  // namespace cufz\n";
+  if (plain_kernel) src += "#define CUFZ_JIT_PLAIN 1\n";
+  src += "#include \"jit_launch.cuh\"\n";
+  return src;
+}
+
+// Runtime-compiles the module to sm_103a code (no device needed).
+cufz_status jit_nvrtc(const std::string& src, std::vector<char>* cubin, std::string* log) {
+  nvrtcProgram prog = nullptr;
+  if (nvrtcCreateProgram(&prog, src.c_str(), "cufz_programs.cu", kJitHeaderCount, kJitHeaderText,
+                         kJitHeaderName) != NVRTC_SUCCESS) {
+    *log = "nvrtcCreateProgram failed\n";
+    return CUFZ_E_CUDA;
+  }
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--Ofast-compile=min",
+                        "--diag-suppress=177,550,128"};
+  nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  size_t log_n = 0;
+  nvrtcGetProgramLogSize(prog, &log_n);
+  log->assign(log_n, '\0');
+  if (log_n) nvrtcGetProgramLog(prog, &(*log)[0]);
+  while (!log->empty() && log->back() == '\0') log->pop_back();
+  if (rc != NVRTC_SUCCESS) {
+    *log += std::string("nvrtc: ") + nvrtcGetErrorString(rc) + "\n";
+    nvrtcDestroyProgram(&prog);
+    return CUFZ_E_INVALID_PROGRAM;
+  }
+  size_t n = 0;
+  nvrtcGetCUBINSize(prog, &n);
+  cubin->resize(n);
+  nvrtcGetCUBIN(prog, cubin->data());
+  nvrtcDestroyProgram(&prog);
+  return CUFZ_OK;
+}
+
+std::mutex g_jit_cache_mu;
+std::unordered_map<std::string, std::vector<char>> g_jit_cache;  // module source -> image
+
+// Compiled image of a module source, cached for the life of the process.
+cufz_status jit_build_image(const std::vector<std::string>& prog_src, bool plain_kernel,
+                            std::vector<char>* image, std::string* log) {
+  const std::string src = jit_module_source(prog_src, plain_kernel);
+  {
+    std::lock_guard<std::mutex> g(g_jit_cache_mu);
+    auto it = g_jit_cache.find(src);
+    if (it != g_jit_cache.end()) {
+      *image = it->second;
+      log->clear();
+      return CUFZ_OK;
+    }
+  }
+  cufz_status st = jit_nvrtc(src, image, log);
+  if (st == CUFZ_OK) {
+    std::lock_guard<std::mutex> g(g_jit_cache_mu);
+    g_jit_cache[src] = *image;
+  }
+  return st;
+}
+
+// Compiles every loaded program into one module and loads it; the
+// persistent and plain kernels of the compiled path come from it.
+cufz_status jit_compile(cufz_ctx* c) {
+  if (c->jit_progs == c->progs.size() && c->jit_lib) return CUFZ_OK;
+  std::vector<char> cubin;
+  const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
+  cufz_status cs = jit_build_image(c->prog_src, plain, &cubin, &c->jit_log);
+  if (cs != CUFZ_OK) return cs;
+  // wait for work that may still run on the old module
+  for (uint32_t k = 0; k < c->n_lanes; k++) {
+    Lane& L = c->lanes[k];
+    if (L.busy) cudaEventSynchronize(L.ev_end);
+    lane_retire(c, L);
+    lane_reset_graph(L);
+  }
+  if (c->jit_lib) cudaLibraryUnload(c->jit_lib);
+  c->jit_lib = nullptr;
+  cudaError_t e = cudaLibraryLoadData(&c->jit_lib, cubin.data(), nullptr, nullptr, 0, nullptr,
+                                      nullptr, 0);
+  if (e == cudaSuccess) e = cudaLibraryGetKernel(&c->jit_persist, c->jit_lib, "cufz_jit_persistent");
+  if (e == cudaSuccess && plain) e = cudaLibraryGetKernel(&c->jit_plain, c->jit_lib, "cufz_jit_plain");
+  int occ = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
+        &occ, reinterpret_cast<const void*>(c->jit_persist), (int)c->shape.cta_threads, 0);
+  if (e != cudaSuccess || occ < 1) {
+    cudaGetLastError();
+    return CUFZ_E_CUDA;
+  }
+  c->jit_ctas_per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
+  c->jit_progs = (uint32_t)c->progs.size();
+  return CUFZ_OK;
+}
+
+cudaError_t launch_jit_persistent(cufz_ctx* c, const BatchHdr* d_batch, uint32_t ctas, cudaStream_t st) {
+  EngineTables T = c->T;
+  BatchHdr* b = const_cast<BatchHdr*>(d_batch);
+  void* args[] = {&T, &b};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->jit_persist), dim3(ctas), dim3(c->shape.cta_threads),
+                          args, 0, st);
+}
+
+cudaError_t launch_jit_plain(cufz_ctx* c, const BatchHdr* d_batch, uint32_t input, uint32_t blocks,
+                             uint32_t threads, cudaStream_t st) {
+  EngineTables T = c->T;
+  BatchHdr* b = const_cast<BatchHdr*>(d_batch);
+  void* args[] = {&T, &b, &input};
+  return cudaLaunchKernel(reinterpret_cast<const void*>(c->jit_plain), dim3(blocks), dim3(threads),
+                          args, 0, st);
+}
+
+uint32_t persistent_ctas(const cufz_ctx* c) {
+  return use_jit(c) ? c->jit_ctas_per_sm * (uint32_t)c->n_sms : c->shape.ctas;
+}
+
+// one persistent launch of the active path
+cudaError_t launch_batch_kernel(cufz_ctx* c, const BatchHdr* d_batch, uint32_t ctas, cudaStream_t st) {
+  if (use_jit(c)) return launch_jit_persistent(c, d_batch, ctas, st);
+  LaunchShape s = c->shape;
+  s.ctas = ctas;
+  return launch_persistent(c->T, d_batch, s, st);
+}
+
 // Captures (or re-captures) the lane's graph: batch upload + persistent kernel.
 cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   const LaunchShape& s = c->shape;
+  const uint32_t ctas = persistent_ctas(c);
+  const void* kern = use_jit(c) ? reinterpret_cast<const void*>(c->jit_persist) : nullptr;
   if (L.gexec && L.graph_regs == s.max_regs && L.graph_prog == s.max_prog_bytes &&
-      L.graph_ctas == s.ctas && L.graph_threads == s.cta_threads)
+      L.graph_ctas == ctas && L.graph_threads == s.cta_threads && L.graph_kernel == kern)
     return CUFZ_OK;
   lane_reset_graph(L);
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return CUFZ_E_CUDA;
   cudaError_t e1 = cudaMemcpyAsync(L.d_batch, L.h_stage, sizeof(BatchHdr), cudaMemcpyHostToDevice, L.stream);
-  cudaError_t e2 = launch_persistent(c->T, reinterpret_cast<const BatchHdr*>(L.d_batch), s, L.stream);
+  cudaError_t e2 = launch_batch_kernel(c, reinterpret_cast<const BatchHdr*>(L.d_batch), ctas, L.stream);
   cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -256,8 +405,9 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   }
   L.graph_regs = s.max_regs;
   L.graph_prog = s.max_prog_bytes;
-  L.graph_ctas = s.ctas;
+  L.graph_ctas = ctas;
   L.graph_threads = s.cta_threads;
+  L.graph_kernel = kern;
   return CUFZ_OK;
 }
 
@@ -293,6 +443,8 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
     d->base[k] = next[sp];
     next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
   }
+  d->shared_mask = P.shared_mask;
+  d->n_bufs = P.n_bufs;
   d->prog_off = c->prog_off[in.program_id];
   d->prog_bytes = P.blob_bytes;
   d->user_tag = in.user_tag;
@@ -301,7 +453,7 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
-  uint64_t target = batch_threads / (8ull * std::max(c->shape.ctas, 1u));
+  uint64_t target = batch_threads / (8ull * std::max(persistent_ctas(c), 1u));
   uint64_t lo = 2ull * cta, hi = 256ull * cta;
   target = std::min(std::max(target, lo), hi);
   return (uint32_t)align_up(target, 32);
@@ -356,7 +508,7 @@ cufz_status cufz_create(const cufz_config* cfg_in, cufz_ctx** out) {
   if (!cfg.cta_threads) cfg.cta_threads = 256;
   if (cfg.cta_threads < 64 || cfg.cta_threads > 1024 || cfg.cta_threads % 32) return CUFZ_E_INVALID_ARG;
   if (cfg.item_threads % 32) return CUFZ_E_INVALID_ARG;
-  if (!cfg.max_threads || cfg.max_threads > 0xFFFFFFFFull) cfg.max_threads = 0xFFFFFFFFull;
+  if (!cfg.max_threads || cfg.max_threads > (1ull << 31)) cfg.max_threads = 1ull << 31;
   if (cfg.redzone > (1u << 20)) return CUFZ_E_INVALID_ARG;
   cfg.n_lanes = std::max(1u, std::min(cfg.n_lanes, kMaxLanes));
   int ndev = 0;
@@ -482,6 +634,7 @@ cufz_status cufz_destroy(cufz_ctx* c) {
       if (L.h_stage) cudaFreeHost(L.h_stage);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->jit_lib) cudaLibraryUnload(c->jit_lib);
     if (c->done_h) cudaFreeHost(c->done_h);
     for (auto& p : c->progs) free_program(&p);
   }
@@ -507,6 +660,13 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     free_program(&P);
     return CUFZ_E_CUDA;
   }
+  std::string fsrc;
+  st = jit_source(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), (uint32_t)c->progs.size(), &fsrc);
+  if (st != CUFZ_OK) {
+    free_program(&P);
+    return st;
+  }
+  c->prog_src.push_back(fsrc);
   c->prog_used = align_up(c->prog_used + P.blob_bytes, 16);
   if (stats) *stats = P.stats;
   *program_id = (uint32_t)c->progs.size();
@@ -538,6 +698,10 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     }
   }
   if (!L) return CUFZ_E_BUSY;
+  if (use_jit(c) && c->jit_progs != c->progs.size()) {
+    cufz_status cs = jit_compile(c);
+    if (cs != CUFZ_OK) return cs;
+  }
   const bool plain = c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH;
   // admission
   BatchHdr* hdr = reinterpret_cast<BatchHdr*>(L->h_stage);
@@ -672,20 +836,24 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
       if (!use_graph && e == cudaSuccess) {
         e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess && !plain) {
-          LaunchShape s = c->shape;
-          s.ctas = std::min<uint32_t>(s.ctas, std::max<uint32_t>(n_items, 1));
-          e = launch_persistent(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), s, L->stream);
+          uint32_t ctas = std::min<uint32_t>(persistent_ctas(c), std::max<uint32_t>(n_items, 1));
+          e = launch_batch_kernel(c, reinterpret_cast<const BatchHdr*>(L->d_batch), ctas, L->stream);
           if (e == cudaSuccess) c->stats.kernel_launches++;
         } else if (e == cudaSuccess) {
           for (uint32_t i = 0; i < n_dev && e == cudaSuccess; i++) {
             LaunchShape s = c->shape;
             s.cta_threads = (uint32_t)align_up(dins[i].T, 32);
-            if (smem_for(s, s.cta_threads) > c->smem_set) {
-              e = cudaErrorInvalidConfiguration;
-              break;
+            if (use_jit(c)) {
+              e = launch_jit_plain(c, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
+                                   dins[i].n_items, s.cta_threads, L->stream);
+            } else {
+              if (smem_for(s, s.cta_threads) > c->smem_set) {
+                e = cudaErrorInvalidConfiguration;
+                break;
+              }
+              e = launch_plain(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
+                               dins[i].n_items, s, L->stream);
             }
-            e = launch_plain(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
-                             dins[i].n_items, s, L->stream);
             if (e == cudaSuccess) c->stats.kernel_launches++;
           }
         }
@@ -844,6 +1012,50 @@ cufz_status cufz_release(cufz_ctx* c, uint64_t ticket) {
   c->free_slots.push_back(it->second);
   c->ticket_slot.erase(it);
   return CUFZ_OK;
+}
+
+cufz_status cufz_program_cuda(const void* bytes, size_t nbytes, uint32_t flags, char* out,
+                              size_t out_cap, size_t* out_bytes) {
+  if (!bytes || !out_bytes) return CUFZ_E_INVALID_ARG;
+  std::string f;
+  cufz_status st = jit_source(bytes, nbytes, !(flags & CUFZ_CF_NO_PRUNE), 0, &f);
+  if (st != CUFZ_OK) return st;
+  *out_bytes = f.size() + 1;
+  if (!out || out_cap < f.size() + 1) return CUFZ_E_NOMEM;
+  memcpy(out, f.c_str(), f.size() + 1);
+  return CUFZ_OK;
+}
+
+cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, uint32_t n,
+                               uint32_t flags, char* log, uint32_t log_cap, size_t* cubin_bytes) {
+  if ((!progs || !sizes) && n) return CUFZ_E_INVALID_ARG;
+  std::vector<std::string> srcs(n);
+  for (uint32_t k = 0; k < n; k++) {
+    cufz_status st = jit_source(progs[k], sizes[k], !(flags & CUFZ_CF_NO_PRUNE), k, &srcs[k]);
+    if (st != CUFZ_OK) return st;
+  }
+  std::vector<char> image;
+  std::string lg;
+  cufz_status st = jit_build_image(srcs, (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, &image, &lg);
+  if (log && log_cap) {
+    size_t m = std::min<size_t>(lg.size(), log_cap - 1);
+    memcpy(log, lg.data(), m);
+    log[m] = 0;
+  }
+  if (cubin_bytes) *cubin_bytes = image.size();
+  return st;
+}
+
+cufz_status cufz_compile_programs(cufz_ctx* c, char* log, uint32_t log_cap) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  cufz_status st = jit_compile(c);
+  if (log && log_cap) {
+    size_t n = std::min<size_t>(c->jit_log.size(), log_cap - 1);
+    memcpy(log, c->jit_log.data(), n);
+    log[n] = 0;
+  }
+  return st;
 }
 
 cufz_status cufz_get_stats(cufz_ctx* c, cufz_stats* out) {

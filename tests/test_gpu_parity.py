@@ -71,22 +71,28 @@ def run_both(B, orc, progs, inputs, cap=1 << 15, flags=None, budget=4096, redzon
     return dres, drecs, dbms, ores, orecs, obms, st
 
 
-def test_c1_full(B, orc):
+PATHS = [0, 64]  # bytecode interpreter, compiled programs (CUFZ_CF_JIT)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_c1_full(B, orc, path):
     """Config 1 at full size: 1,000 inputs of the guarded 1D kernel."""
     progs = [gen.c1_program()]
     inputs = gen.c1_inputs(1000)
     cap = 1 << 15
-    dres, drecs, dbms, ores, orecs, obms, st = run_both(B, orc, progs, inputs, cap=cap)
+    dres, drecs, dbms, ores, orecs, obms, st = run_both(B, orc, progs, inputs, cap=cap,
+                                                        flags=B.CF_KEEP_BITMAPS | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
     assert st.kernel_launches >= 1 and int(ores["n_violations"].sum()) > 1000
 
 
-def test_c1_plain_launch(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_c1_plain_launch(B, orc, path):
     progs = [gen.c1_program()]
     inputs = gen.c1_inputs(64)
     cap = 1 << 15
     dres, drecs, dbms, ores, orecs, obms, st = run_both(
-        B, orc, progs, inputs, cap=cap, flags=B.CF_KEEP_BITMAPS | B.CF_PLAIN_LAUNCH)
+        B, orc, progs, inputs, cap=cap, flags=B.CF_KEEP_BITMAPS | B.CF_PLAIN_LAUNCH | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
     assert st.kernel_launches == 64 and st.graph_launches == 0
 
@@ -105,24 +111,27 @@ def small_c2_inputs(progs, per_program, seed, max_grid=6):
     return ins
 
 
-def test_c2_small_grids(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_c2_small_grids(B, orc, path):
     """All 32 random programs, 6 inputs each, grids up to 6 x 6 blocks of 16 x 16."""
     progs = gen.c2_programs()
     inputs = small_c2_inputs(progs, 6, seed=1234)
     cap = 1 << 14
     dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs, cap=cap,
-                                                       orc_cap=1 << 17)
+                                                       orc_cap=1 << 17,
+                                                       flags=B.CF_KEEP_BITMAPS | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
 
 
-def test_c2_unpruned_digest_equal(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_c2_unpruned_digest_equal(B, orc, path):
     """Sec. 5.2 invariant on the device: pruned and unpruned programs give the
     same digest, counts, bitmaps and records."""
     progs = gen.c2_programs()
     inputs = small_c2_inputs(progs, 3, seed=777)
     cap = 1 << 14
     out = []
-    for flags in (B.CF_KEEP_BITMAPS, B.CF_KEEP_BITMAPS | B.CF_NO_PRUNE):
+    for flags in (B.CF_KEEP_BITMAPS | path, B.CF_KEEP_BITMAPS | B.CF_NO_PRUNE | path):
         with B.Engine(record_cap=cap, flags=flags, max_slots=512) as E:
             for p in progs:
                 E.load(p)
@@ -142,28 +151,32 @@ def test_c2_unpruned_digest_equal(B, orc):
     assert np.all(r0["n_ops"] <= r1["n_ops"]) and r0["n_ops"].sum() < r1["n_ops"].sum()
 
 
-def test_c3_ragged_blocks(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_c3_ragged_blocks(B, orc, path):
     """Config-3 programs (widths 1/4/8/16, offsets) with log-uniform grids and
     block sizes that are rarely multiples of 32, persistent and plain paths."""
     progs = gen.c3_programs()
     inputs = gen.c3_inputs(160, seed=31, max_blocks=64, min_threads=1, max_threads=1024)
     cap = 1 << 15
-    for flags in (B.CF_KEEP_BITMAPS, B.CF_KEEP_BITMAPS | B.CF_PLAIN_LAUNCH):
+    for flags in (B.CF_KEEP_BITMAPS | path, B.CF_KEEP_BITMAPS | B.CF_PLAIN_LAUNCH | path):
         dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs, cap=cap,
                                                            flags=flags, orc_cap=1 << 17)
         compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
 
 
-def test_c4_branch_heavy(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_c4_branch_heavy(B, orc, path):
     progs = gen.c4_programs()
     inputs = gen.c4_inputs(256, seed=4, max_blocks=12)
     dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs, cap=1 << 13,
-                                                       orc_cap=1 << 16)
+                                                       orc_cap=1 << 16,
+                                                       flags=B.CF_KEEP_BITMAPS | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, 1 << 13)
     assert int(dres["n_edges"].max()) > 50
 
 
-def test_listing_programs(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_listing_programs(B, orc, path):
     progs = [gen.vecadd_shared_program(256), gen.guarded_plus1_program(256)]
     inputs = gen.make_inputs(6)
     n = 256 * 40 - 1
@@ -173,14 +186,16 @@ def test_listing_programs(B, orc):
     gen.set_input(inputs[3], 1, (40, 1, 1), (256, 1, 1), (5000,), (4 * 5000,) * 3)
     gen.set_input(inputs[4], 1, (0, 1, 1), (256, 1, 1), (0,), (0,) * 3)
     gen.set_input(inputs[5], 1, (3, 1, 1), (1025, 1, 1), (5,), (0,) * 3)
-    dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs)
+    dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs,
+                                                       flags=B.CF_KEEP_BITMAPS | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, 1 << 15)
     assert int(dres[2]["n_violations"]) == 3
     assert int(dres[4]["status"]) == B.ST_INVALID_CONFIG
     assert int(dres[5]["status"]) == B.ST_INVALID_CONFIG
 
 
-def test_edge_cases(B, orc):
+@pytest.mark.parametrize("path", PATHS)
+def test_edge_cases(B, orc, path):
     """Zero-length buffers, every-access violations with a tiny record cap
     (OVERFLOW, exact counts), the back-edge budget, LIMIT, a bad program id,
     3D grids and blocks, one-thread inputs."""
@@ -211,7 +226,8 @@ def test_edge_cases(B, orc):
     gen.set_input(ins[8], 0, (2, 2, 2), (4, 4, 4), (9, 5), (3, 17))
     cap = 64
     for budget in (4096, 12):
-        with B.Engine(record_cap=cap, iter_budget=budget, max_threads=1 << 24, max_slots=64) as E:
+        with B.Engine(record_cap=cap, iter_budget=budget, max_threads=1 << 24, max_slots=64,
+                      flags=B.CF_KEEP_BITMAPS | path) as E:
             E.load(progs[0])
             E.load(progs[1])
             dres, drecs, dbms = E.run(ins)

@@ -147,3 +147,25 @@ def test_engine_needs_a_gpu():
         pytest.skip("a GPU is present")
     with pytest.raises(B.CufzError):
         B.Engine()
+
+
+@pytest.mark.parametrize("which", ["listings", "c3", "c2", "c4"])
+def test_generated_code_compiles_for_sm103a(which):
+    """The compiled path: every workload program's generated CUDA compiles
+    for sm_103a with the runtime compiler (no device needed)."""
+    progs = {"listings": [gen.c1_program(), gen.vecadd_shared_program(64),
+                          gen.guarded_plus1_program(128)],
+             "c3": gen.c3_programs(), "c2": gen.c2_programs()[:8],
+             "c4": gen.c4_programs()[:3]}[which]
+    st, log, nbytes = B.cufz_compile_check(progs)
+    assert st == 0, log[-4000:]
+    assert nbytes > 0
+
+
+def test_generated_code_shape():
+    src = B.cufz_program_cuda(gen.c1_program())
+    assert "cufz_prog_0" in src and "jit_violation" in src and "jit_cover" in src
+    assert src.count("acc.n_acc++") == 3               # three checked accesses
+    assert "r11" not in src                            # the pruned sum x + y is gone
+    full = B.cufz_program_cuda(gen.c1_program(), B.CF_NO_PRUNE)
+    assert "r11 =" in full
