@@ -55,6 +55,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--cta-threads", type=int, default=256)
+    ap.add_argument("--jit-min-ctas", type=int, default=0)
+    ap.add_argument("--jit-fast-compile", action="store_true")
     ap.add_argument("--item-threads", type=int, default=0)
     return ap.parse_args()
 
@@ -229,9 +231,10 @@ def run_engine(args, rank, world, local, pg):
     per_step = args.inputs_per_step or n_all
     flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
     if args.path == "jit":
-        flags |= B.CF_JIT
+        flags |= B.CF_JIT | (B.CF_JIT_FAST_COMPILE if args.jit_fast_compile else 0)
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
-                 cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2)
+                 cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2,
+                 jit_min_ctas=args.jit_min_ctas)
     for p in progs:
         E.load(p)
     n_batches = (n_all + per_step - 1) // per_step
@@ -324,6 +327,7 @@ def run_engine(args, rank, world, local, pg):
             "engine": ("programs compiled to sm_103a at load" if args.path == "jit" else
                        "bytecode interpreter"),
             "cta_threads": int(st.cta_threads),
+            "jit_min_ctas": args.jit_min_ctas or 4,
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),
             "record_cap": cap,

@@ -83,6 +83,7 @@ typedef int32_t cufz_status;
 #define CUFZ_CF_NO_DIGEST 32   /* skip the per-access digest */
 #define CUFZ_CF_JIT 64         /* run programs compiled to sm_103a code at load time
                                   instead of through the bytecode interpreter */
+#define CUFZ_CF_JIT_FAST_COMPILE 128 /* compile faster, run slower (compiled path) */
 
 /* Engine configuration.  cufz_config_default fills every field; a zero in
  * max_slots, item_threads or cta_threads means "choose automatically". */
@@ -101,6 +102,8 @@ typedef struct {
   uint32_t cta_threads;  /* threads per CTA of the persistent kernel (64..1024) */
   uint32_t n_lanes;      /* batches that may overlap on the device (1..8) */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM (0 = from occupancy) */
+  uint32_t jit_min_ctas; /* compiled path: CTAs per SM its registers must allow (0 = 4) */
+  uint32_t reserved;
 } cufz_config;
 
 /* One fuzz input, 128 bytes.  grid/block are the launch shape of the kernel

@@ -22,7 +22,7 @@ E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUN
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
 CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \
-    CF_JIT = 1, 2, 4, 8, 16, 32, 64
+    CF_JIT, CF_JIT_FAST_COMPILE = 1, 2, 4, 8, 16, 32, 64, 128
 
 RESULT_DTYPE = np.dtype([
     ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),
@@ -47,7 +47,8 @@ class cufz_config(ctypes.Structure):
                 ("record_cap", ctypes.c_uint32), ("redzone", ctypes.c_uint32),
                 ("iter_budget", ctypes.c_uint32), ("max_threads", ctypes.c_uint64),
                 ("item_threads", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
-                ("n_lanes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32)]
+                ("n_lanes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
+                ("jit_min_ctas", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class cufz_stats(ctypes.Structure):
@@ -294,7 +295,8 @@ class Engine:
     def __init__(self, device: int = 0, arena_bytes: int | None = None, max_slots: int = 0,
                  record_cap: int = 4096, flags: int = CF_KEEP_BITMAPS, redzone: int = 256,
                  iter_budget: int = 4096, max_threads: int = 1 << 31, cta_threads: int = 256,
-                 item_threads: int = 0, n_lanes: int = 4, ctas_per_sm: int = 0):
+                 item_threads: int = 0, n_lanes: int = 4, ctas_per_sm: int = 0,
+                 jit_min_ctas: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -311,6 +313,7 @@ class Engine:
         cfg.item_threads = item_threads
         cfg.n_lanes = n_lanes
         cfg.ctas_per_sm = ctas_per_sm
+        cfg.jit_min_ctas = jit_min_ctas
         cfg.max_slots = max_slots
         if arena_bytes is None:
             arena_bytes = cufz_arena_bytes(cfg, max_slots or 1024)

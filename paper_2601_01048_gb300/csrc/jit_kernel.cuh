@@ -51,7 +51,18 @@ static __device__ __forceinline__ void jit_cover(const EngineTables* T, uint32_t
                                           uint32_t e) {
   const uint32_t am = __activemask();
   const uint32_t peers = __match_any_sync(am, e);
-  if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) edge_add(hash, *T, slot, e, __popc(peers));
+  if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
+    // first probe inline: the edge is usually already in its home slot
+    const uint32_t c = __popc(peers);
+    const uint32_t tag = (e + 1u) << kHashTagShift;
+    uint32_t* p = &hash[(e * 2654435761u) >> (32 - 11)];
+    const uint32_t cur = *p;
+    if ((cur & ~kHashCountMask) == tag) {
+      if ((cur & kHashCountMask) < 128u) atomicAdd(p, c);
+    } else {
+      edge_add(hash, *T, slot, e, c);
+    }
+  }
 }
 
 // Seeded content of a global buffer (seedx = program seed ^ buf * 0x9E3779B9).

@@ -239,8 +239,10 @@ bool use_jit(const cufz_ctx* c) { return (c->cfg.flags & CUFZ_CF_JIT) != 0; }
 // The compiled path's module: every program's item function, the dispatcher
 // and the kernels, compiled as one translation unit so the program functions
 // are register-allocated together with the kernel that calls them.
-std::string jit_module_source(const std::vector<std::string>& prog_src, bool plain_kernel) {
-  std::string src = "#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
+std::string jit_module_source(const std::vector<std::string>& prog_src, bool plain_kernel,
+                              uint32_t min_ctas) {
+  std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas ? min_ctas : 4) +
+                    "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
   for (const auto& f : prog_src) src += f;
   src += "static __device__ bool jit_run(uint32_t prog, const EngineTables* T, const DevInput* in, "
          "uint32_t* hash, uint32_t g0, uint32_t g_end) {\n  switch (prog) {\n";
@@ -254,16 +256,16 @@ std::string jit_module_source(const std::vector<std::string>& prog_src, bool pla
 }
 
 // Runtime-compiles the module to sm_103a code (no device needed).
-cufz_status jit_nvrtc(const std::string& src, std::vector<char>* cubin, std::string* log) {
+cufz_status jit_nvrtc(const std::string& src, bool fast, std::vector<char>* cubin, std::string* log) {
   nvrtcProgram prog = nullptr;
   if (nvrtcCreateProgram(&prog, src.c_str(), "cufz_programs.cu", kJitHeaderCount, kJitHeaderText,
                          kJitHeaderName) != NVRTC_SUCCESS) {
     *log = "nvrtcCreateProgram failed\n";
     return CUFZ_E_CUDA;
   }
-  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--Ofast-compile=min",
-                        "--diag-suppress=177,550,128"};
-  nvrtcResult rc = nvrtcCompileProgram(prog, 4, opts);
+  const char* opts[] = {"--gpu-architecture=sm_103a", "--std=c++17", "--diag-suppress=177,550,128",
+                        "--Ofast-compile=min"};
+  nvrtcResult rc = nvrtcCompileProgram(prog, fast ? 4 : 3, opts);
   size_t log_n = 0;
   nvrtcGetProgramLogSize(prog, &log_n);
   log->assign(log_n, '\0');
@@ -287,8 +289,9 @@ std::unordered_map<std::string, std::vector<char>> g_jit_cache;  // module sourc
 
 // Compiled image of a module source, cached for the life of the process.
 cufz_status jit_build_image(const std::vector<std::string>& prog_src, bool plain_kernel,
-                            std::vector<char>* image, std::string* log) {
-  const std::string src = jit_module_source(prog_src, plain_kernel);
+                            uint32_t min_ctas, bool fast, std::vector<char>* image,
+                            std::string* log) {
+  const std::string src = jit_module_source(prog_src, plain_kernel, min_ctas) + (fast ? "//fast\n" : "");
   {
     std::lock_guard<std::mutex> g(g_jit_cache_mu);
     auto it = g_jit_cache.find(src);
@@ -298,7 +301,7 @@ cufz_status jit_build_image(const std::vector<std::string>& prog_src, bool plain
       return CUFZ_OK;
     }
   }
-  cufz_status st = jit_nvrtc(src, image, log);
+  cufz_status st = jit_nvrtc(src, fast, image, log);
   if (st == CUFZ_OK) {
     std::lock_guard<std::mutex> g(g_jit_cache_mu);
     g_jit_cache[src] = *image;
@@ -312,7 +315,9 @@ cufz_status jit_compile(cufz_ctx* c) {
   if (c->jit_progs == c->progs.size() && c->jit_lib) return CUFZ_OK;
   std::vector<char> cubin;
   const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
-  cufz_status cs = jit_build_image(c->prog_src, plain, &cubin, &c->jit_log);
+  cufz_status cs = jit_build_image(c->prog_src, plain, c->cfg.jit_min_ctas,
+                                   (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &cubin,
+                                   &c->jit_log);
   if (cs != CUFZ_OK) return cs;
   // wait for work that may still run on the old module
   for (uint32_t k = 0; k < c->n_lanes; k++) {
@@ -1036,7 +1041,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
   }
   std::vector<char> image;
   std::string lg;
-  cufz_status st = jit_build_image(srcs, (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, &image, &lg);
+  cufz_status st = jit_build_image(srcs, (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0,
+                                   (flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &image, &lg);
   if (log && log_cap) {
     size_t m = std::min<size_t>(lg.size(), log_cap - 1);
     memcpy(log, lg.data(), m);
