@@ -31,8 +31,8 @@ void free_program(LoadedProgram* p);
 
 // CUDA source of one program's work-item function `cufz_prog_<index>` for
 // the compiled path (see jit_kernel.cuh).
-cufz_status jit_source(const void* bytes, size_t nbytes, bool prune, uint32_t index,
-                       std::string* out);
+cufz_status jit_source(const void* bytes, size_t nbytes, bool prune, bool digest,
+                       uint32_t index, std::string* out);
 
 // ---------------------------------------------------------------- kernels
 struct LaunchShape {

@@ -40,9 +40,15 @@ static __device__ __noinline__ bool jit_record(const EngineTables* T, const DevI
 static __device__ __forceinline__ void jit_violation(const EngineTables* T, const DevInput* in,
                                               LaneAcc& acc, uint32_t bl, uint32_t tl,
                                               uint32_t ordinal, uint32_t what, int64_t off) {
-  acc.n_viol++;
   if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
   if (!acc.rec_full) acc.rec_full = jit_record(T, in, bl, tl, ordinal, what, off);
+}
+
+// Number of in-bounds indices of a buffer of len bytes for accesses of
+// width 2^lw, clamped to 2^31 (every int32 index below it is in bounds).
+static __device__ __forceinline__ uint32_t jit_index_limit(int64_t len, uint32_t lw) {
+  const uint64_t n = (uint64_t)len >> lw;
+  return n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
 }
 
 // Warp-aggregated edge hit: lanes of the current group with equal e are

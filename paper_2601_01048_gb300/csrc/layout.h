@@ -102,7 +102,7 @@ struct DevProgHdr {
 };
 static_assert(sizeof(DevProgHdr) == 80, "DevProgHdr size");
 
-// Everything a kernel needs about one admitted input, 320 bytes.
+// Everything a kernel needs about one admitted input, 576 bytes.
 struct DevInput {
   uint32_t slot;
   uint32_t prog;          // program index
@@ -127,8 +127,11 @@ struct DevInput {
   uint32_t shared_mask;   // of the input's program: bit k = buffer k is shared
   uint32_t n_bufs;
   uint32_t pad[5];
+  // in-bounds index count of buffer k for width 2^lw: min(len[k] >> lw, 2^31)
+  uint32_t lim[kMaxBufs * 5];
+  uint32_t pad2[19];
 };
-static_assert(sizeof(DevInput) == 320, "DevInput size");
+static_assert(sizeof(DevInput) == 576, "DevInput size");
 
 // A contiguous range of linear test threads g = block_lin * T + thread_lin.
 struct WorkItem {

@@ -471,6 +471,7 @@ struct Gen {
   const Ir& ir;
   std::string& o;
   int index;
+  bool digest_ = true;
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -536,19 +537,26 @@ struct Gen {
                   " jit_cover(T, hash, slot, e); }");
   }
 
+  static std::string lim_name(int buf, int lw) {
+    return "lim[" + std::to_string(buf * 5 + lw) + "]";
+  }
+
+  // An access of width w = 2^lw at index ix is in bounds iff
+  // 0 <= ix < floor(len / w); with the limit clamped to 2^31 a single
+  // unsigned compare decides it for every int32 index (negative indices
+  // wrap to >= 2^31).
   void access(int ind, const IrOp& o2) {
     int lw = log2w(o2.width);
     bool shared = (ir.shared_mask >> o2.buf) & 1u;
-    std::string L = "L" + std::to_string(o2.buf);
     line(ind, "{");
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
+    line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
     line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
-    line(ind + 1, "const bool viol = (ix < 0) | (off + " + std::to_string(o2.width) + " > " + L + ");");
-    line(ind + 1, "acc.n_acc++;");
     line(ind + 1, "if (dig) acc.digest += jit_digest(th, ordinal, " +
                       hex32((uint32_t)o2.site * 0xC2B2AE3Du) + ", off);");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
+    line(ind + 1, "acc.n_viol += viol ? 1u : 0u;");
     line(ind + 1, "if (viol) jit_violation(T, in, acc, bl, tl, ordinal, " + hex32(what) + ", off);");
     if (o2.opc == B_LD && !o2.value_dead) {
       if (shared) {
@@ -650,32 +658,37 @@ struct Gen {
     line(1, "LaneAcc acc;");
     line(1, "acc_init(acc);");
     line(1, "const uint32_t budget = T->iter_budget;");
-    line(1, "const bool dig = !(T->flags & CUFZ_CF_NO_DIGEST);");
-    line(1, "const uint64_t mT = in->mT; const uint32_t Tb = in->T;");
-    for (int b = 0; b < ir.n_bufs; b++)
-      if (buf_used[b]) line(1, "const int64_t L" + std::to_string(b) + " = in->len[" + std::to_string(b) + "];");
+    line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
+    // loop-invariant launch constants are re-read from the CTA's shared copy
+    // of the input where used, rather than held in registers for the item
+    line(1, "const volatile DevInput* vin = in;");
+    std::vector<bool> lim_used(kMaxBufs * 5, false);
+    for (const auto& op : ir.ops)
+      if (op.kept && (op.opc == B_LD || op.opc == B_ST)) lim_used[op.buf * 5 + log2w(op.width)] = true;
+    // index limits are re-read from the CTA's shared copy of the input at
+    // each use instead of occupying registers for the whole item
+    line(1, "const volatile uint32_t* lim = vin->lim;");
     bool need_t = sreg_used[0] || sreg_used[1] || sreg_used[2];
     bool need_b = sreg_used[6] || sreg_used[7] || sreg_used[8];
-    if (need_t) line(1, "const uint64_t mBx = in->mBx, mBxy = in->mBxy; const uint32_t Bx = in->Bx, By = in->block[1];");
-    if (need_b) line(1, "const uint64_t mGx = in->mGx, mGxy = in->mGxy; const uint32_t Gx = in->gx, Gy = in->grid[1];");
-    for (int k = 0; k < 3; k++) {
-      if (sreg_used[3 + k]) line(1, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)in->block[" + std::to_string(k) + "];");
-      if (sreg_used[9 + k]) line(1, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)in->grid[" + std::to_string(k) + "];");
-    }
-    for (int k = 0; k < 4; k++)
-      if (sreg_used[12 + k]) line(1, std::string("const int32_t ") + sreg_name(12 + k) + " = in->args[" + std::to_string(k) + "];");
+
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
-    line(2, "const uint32_t bl = udiv(g, mT);");
-    line(2, "const uint32_t tl = g - bl * Tb;");
+    line(2, "const uint32_t bl = udiv(g, vin->mT);");
+    line(2, "const uint32_t tl = g - bl * vin->T;");
     if (need_t) {
-      line(2, "const uint32_t q1 = udiv(tl, mBx), tz_ = udiv(tl, mBxy);");
-      line(2, "const int32_t s_tx = (int32_t)(tl - q1 * Bx), s_ty = (int32_t)(q1 - tz_ * By), s_tz = (int32_t)tz_;");
+      line(2, "const uint32_t q1 = udiv(tl, vin->mBx), tz_ = udiv(tl, vin->mBxy);");
+      line(2, "const int32_t s_tx = (int32_t)(tl - q1 * vin->Bx), s_ty = (int32_t)(q1 - tz_ * vin->block[1]), s_tz = (int32_t)tz_;");
     }
     if (need_b) {
-      line(2, "const uint32_t p1 = udiv(bl, mGx), bz_ = udiv(bl, mGxy);");
-      line(2, "const int32_t s_bx = (int32_t)(bl - p1 * Gx), s_by = (int32_t)(p1 - bz_ * Gy), s_bz = (int32_t)bz_;");
+      line(2, "const uint32_t p1 = udiv(bl, vin->mGx), bz_ = udiv(bl, vin->mGxy);");
+      line(2, "const int32_t s_bx = (int32_t)(bl - p1 * vin->gx), s_by = (int32_t)(p1 - bz_ * vin->grid[1]), s_bz = (int32_t)bz_;");
     }
+    for (int k = 0; k < 3; k++) {
+      if (sreg_used[3 + k]) line(2, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
+      if (sreg_used[9 + k]) line(2, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)vin->grid[" + std::to_string(k) + "];");
+    }
+    for (int k = 0; k < 4; k++)
+      if (sreg_used[12 + k]) line(2, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
     line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
     line(2, "uint32_t prev = 0, ordinal = 0, back = 0;");
     line(2, "(void)prev; (void)ordinal; (void)back; (void)th;");
@@ -684,7 +697,8 @@ struct Gen {
       if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
     if (!decl.empty()) line(2, decl + ";");
     range(2, 0, (int)ir.ops.size());
-    if (has_loop) line(1, "cufz_done:;");
+    if (has_loop) line(1, "cufz_done:");
+    line(2, "acc.n_acc += ordinal;");
     line(1, "}");
     line(1, "__syncwarp();");
     line(1, "acc_flush(*T, slot, acc);");
@@ -694,8 +708,8 @@ struct Gen {
 
 }  // namespace
 
-cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, uint32_t index,
-                       std::string* out) {
+cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool digest,
+                       uint32_t index, std::string* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
   if (do_prune) {
@@ -707,6 +721,7 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, uint32_t
   }
   out->clear();
   Gen g{ir, *out, (int)index};
+  g.digest_ = digest;
   g.emit();
   return CUFZ_OK;
 }

@@ -207,7 +207,7 @@ void harvest(cufz_ctx* c) {
 }
 
 uint32_t smem_for(const LaunchShape& s, uint32_t cta_threads) {
-  return kHashSlots * 4 + s.max_prog_bytes + 336 + (cta_threads / 32) * s.max_regs * kRegStride;
+  return kHashSlots * 4 + s.max_prog_bytes + 576 + (cta_threads / 32) * s.max_regs * kRegStride;
 }
 
 // Sets the kernels' dynamic shared memory limit to what the persistent shape
@@ -450,6 +450,11 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
   }
   d->shared_mask = P.shared_mask;
   d->n_bufs = P.n_bufs;
+  for (uint32_t k = 0; k < P.n_bufs; k++)
+    for (uint32_t lw = 0; lw < 5; lw++) {
+      uint64_t n = (uint64_t)in.buf_len[k] >> lw;
+      d->lim[k * 5 + lw] = n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
+    }
   d->prog_off = c->prog_off[in.program_id];
   d->prog_bytes = P.blob_bytes;
   d->user_tag = in.user_tag;
@@ -666,7 +671,8 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     return CUFZ_E_CUDA;
   }
   std::string fsrc;
-  st = jit_source(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), (uint32_t)c->progs.size(), &fsrc);
+  st = jit_source(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE),
+                  !(c->cfg.flags & CUFZ_CF_NO_DIGEST), (uint32_t)c->progs.size(), &fsrc);
   if (st != CUFZ_OK) {
     free_program(&P);
     return st;
@@ -1023,7 +1029,8 @@ cufz_status cufz_program_cuda(const void* bytes, size_t nbytes, uint32_t flags, 
                               size_t out_cap, size_t* out_bytes) {
   if (!bytes || !out_bytes) return CUFZ_E_INVALID_ARG;
   std::string f;
-  cufz_status st = jit_source(bytes, nbytes, !(flags & CUFZ_CF_NO_PRUNE), 0, &f);
+  cufz_status st = jit_source(bytes, nbytes, !(flags & CUFZ_CF_NO_PRUNE),
+                              !(flags & CUFZ_CF_NO_DIGEST), 0, &f);
   if (st != CUFZ_OK) return st;
   *out_bytes = f.size() + 1;
   if (!out || out_cap < f.size() + 1) return CUFZ_E_NOMEM;
@@ -1036,7 +1043,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
   if ((!progs || !sizes) && n) return CUFZ_E_INVALID_ARG;
   std::vector<std::string> srcs(n);
   for (uint32_t k = 0; k < n; k++) {
-    cufz_status st = jit_source(progs[k], sizes[k], !(flags & CUFZ_CF_NO_PRUNE), k, &srcs[k]);
+    cufz_status st = jit_source(progs[k], sizes[k], !(flags & CUFZ_CF_NO_PRUNE),
+                                !(flags & CUFZ_CF_NO_DIGEST), k, &srcs[k]);
     if (st != CUFZ_OK) return st;
   }
   std::vector<char> image;
