@@ -290,6 +290,35 @@ cufz_status cufz_compile_programs(cufz_ctx* ctx, char* log, uint32_t log_cap);
 cufz_status cufz_get_stats(cufz_ctx* ctx, cufz_stats* out);
 cufz_status cufz_reset_stats(cufz_ctx* ctx);
 
+/* Checked execution of one input without any device allocation, for callers
+ * that cannot allocate device memory: code running while a CUDA graph is
+ * captured, plugins whose host framework owns every allocation, services
+ * that must not grow their device footprint.  The paper has no counterpart
+ * (its runtime is a CPU process).
+ *
+ * Runs `input` of the program (bytes, nbytes) on the current device with
+ * the bytecode interpreter, exactly as a context would (pruned unless flags
+ * has CUFZ_CF_NO_PRUNE; CUFZ_CF_NO_DIGEST honoured; redzone R and back-edge
+ * budget as given), and writes: up to record_cap violation records to
+ * `records` (device memory, may be NULL with record_cap 0), the 64 KiB
+ * bucketed bitmap to `bitmap` (device memory, may be NULL), and the result
+ * summary to `result` (device or host memory).  NEW_COV is measured against
+ * an empty union.  Work is queued on `stream` (NULL: the legacy default
+ * stream) and the call returns after it has completed.
+ *
+ * Scratch memory is a fixed 2 MiB array inside this library, held by every
+ * GPU that loads it until the process exits; nothing is allocated.  The
+ * first call on a device looks up the array's device address (keep that
+ * first call outside any stream capture).  Programs whose loaded form
+ * exceeds 64 KiB are rejected with CUFZ_E_NOMEM.  Every call shares the
+ * array (what must start at zero is cleared per call): calls that overlap
+ * on the GPU -- from several host threads or streams -- race and must be
+ * serialised by the caller. */
+cufz_status cufz_run_noalloc(const void* program, size_t nbytes, const cufz_input* input,
+                             uint32_t flags, uint32_t redzone, uint32_t iter_budget,
+                             cufz_violation* records, uint32_t record_cap, uint8_t* bitmap,
+                             cufz_result* result, void* stream);
+
 /* Measures the INT32 issue rate of device `device` with a kernel of
  * independent integer add/logic chains on the caller's stream; writes lane
  * operations per second. */

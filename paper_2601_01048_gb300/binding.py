@@ -81,6 +81,7 @@ EXPORTS = [
     "cufz_poll_results", "cufz_get_records", "cufz_get_bitmap", "cufz_get_union",
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
+    "cufz_run_noalloc",
 ]
 
 
@@ -117,6 +118,7 @@ def lib():
                 "cufz_compile_programs": (i32, [vp, ctypes.c_char_p, u32]),
                 "cufz_program_cuda": (i32, [vp, sz, u32, ctypes.c_char_p, sz, P(sz)]),
                 "cufz_compile_check": (i32, [vp, vp, u32, u32, ctypes.c_char_p, u32, P(sz)]),
+                "cufz_run_noalloc": (i32, [vp, sz, vp, u32, u32, u32, vp, u32, vp, vp, vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -278,6 +280,18 @@ def cufz_compile_check(progs: list[bytes], flags: int = 0) -> tuple[int, str, in
                                   ctypes.cast(sizes, ctypes.c_void_p), len(progs), flags, log,
                                   len(log), ctypes.byref(nb))
     return st, log.value.decode(errors="replace"), nb.value
+
+
+def cufz_run_noalloc(prog: bytes, inp, records_ptr: int, record_cap: int, bitmap_ptr: int,
+                     result_ptr: int, flags: int = 0, redzone: int = 256,
+                     iter_budget: int = 4096, stream: int = 0) -> None:
+    """One input without device allocation (see include/cufz.h); the output
+    pointers are raw addresses (device memory; the result may be host)."""
+    rec = np.ascontiguousarray(np.asarray(inp, dtype=INPUT_DTYPE).reshape(1))
+    _check(lib().cufz_run_noalloc(_bytes_ptr(prog), len(prog), rec.ctypes.data, flags, redzone,
+                                  iter_budget, records_ptr or None, record_cap,
+                                  bitmap_ptr or None, result_ptr, stream or None),
+           "cufz_run_noalloc")
 
 
 def cufz_int32_peak(device: int = 0, stream: int = 0) -> float:

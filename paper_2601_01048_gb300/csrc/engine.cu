@@ -344,6 +344,10 @@ cudaError_t set_kernel_smem(uint32_t smem_bytes) {
                               (int)smem_bytes);
 }
 
+cudaError_t persistent_func_attributes(cudaFuncAttributes* out) {
+  return cudaFuncGetAttributes(out, interp_kernel<true>);
+}
+
 cudaError_t persistent_occupancy(uint32_t cta_threads, uint32_t smem_bytes, int* ctas_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, interp_kernel<true>,
                                                        (int)cta_threads, smem_bytes);

@@ -51,6 +51,7 @@ cudaError_t launch_clear(void* p, uint64_t bytes, uint64_t pattern, cudaStream_t
 cudaError_t launch_int32_peak(uint32_t* out, uint32_t blocks, uint32_t threads, uint32_t iters,
                               cudaStream_t st);
 cudaError_t persistent_occupancy(uint32_t cta_threads, uint32_t smem_bytes, int* ctas_per_sm);
+cudaError_t persistent_func_attributes(cudaFuncAttributes* out);
 cudaError_t set_kernel_smem(uint32_t smem_bytes);
 
 // unsigned division helpers shared by host (magic computation) and device
