@@ -783,7 +783,15 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     uint32_t item = choose_item_threads(c, batch_threads);
     c->stats.item_threads = item;
     bool overflow = false;
-    for (uint32_t i = 0; i < n_dev; i++) {
+    // work items grouped by program (stable): CTAs running at the same time
+    // then mostly run the same program, which keeps the compiled path's
+    // instruction working set small
+    std::vector<uint32_t> order(n_dev);
+    for (uint32_t i = 0; i < n_dev; i++) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](uint32_t x, uint32_t y) { return dins[x].prog < dins[y].prog; });
+    for (uint32_t oi = 0; oi < n_dev; oi++) {
+      const uint32_t i = order[oi];
       DevInput* d = &dins[i];
       if (plain) {
         d->n_items = (uint32_t)(d->n_threads / d->T);
