@@ -237,6 +237,13 @@ def run_engine(args, rank, world, local, pg):
                  jit_min_ctas=args.jit_min_ctas)
     for p in progs:
         E.load(p)
+    tuned = None
+    if args.path == "jit":
+        # the project's autotuner: per program, compiled vs interpreted on a
+        # sample of that program's inputs (two per program)
+        sample = np.concatenate([inputs[inputs["program_id"] == p][:2]
+                                 for p in np.unique(inputs["program_id"])])
+        tuned = B.cufz_autotune(E.ctx, sample)
     n_batches = (n_all + per_step - 1) // per_step
     batches = [inputs[(k * per_step) % n_all: (k * per_step) % n_all + per_step]
                for k in range(n_batches)]
@@ -324,10 +331,11 @@ def run_engine(args, rank, world, local, pg):
             "inputs_per_step": per_step,
             "path": ("plain one launch per input" if args.plain else
                      "persistent kernel in a CUDA graph"),
-            "engine": ("programs compiled to sm_103a at load" if args.path == "jit" else
-                       "bytecode interpreter"),
+            "engine": ("programs compiled to sm_103a at load or interpreted, chosen per program "
+                       "by the autotuner" if args.path == "jit" else "bytecode interpreter"),
             "cta_threads": int(st.cta_threads),
             "jit_min_ctas": args.jit_min_ctas or 4,
+            "programs_compiled": tuned,
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),
             "record_cap": cap,

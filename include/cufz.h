@@ -287,6 +287,22 @@ cufz_status cufz_sync(cufz_ctx* ctx, int32_t timeout_us);
  * compiler's log is copied to log (capacity log_cap, may be NULL). */
 cufz_status cufz_compile_programs(cufz_ctx* ctx, char* log, uint32_t log_cap);
 
+/* Chooses how a program runs when CUFZ_CF_JIT is set: compiled (1) or by the
+ * bytecode interpreter (0).  A batch runs its compiled programs' work items
+ * and its interpreted programs' work items as two persistent launches.
+ * The default at load is compiled unless the program has more than 32
+ * branch sites (divergent branch-heavy code outgrows the instruction cache
+ * when compiled). */
+cufz_status cufz_set_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t compiled);
+cufz_status cufz_get_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t* compiled);
+
+/* Autotuner: for every program in the sample, times the sample's inputs of
+ * that program run compiled and interpreted (twice each) and keeps the
+ * faster path.  Needs an idle context; the sample's results are discarded.
+ * *n_compiled receives the number of programs left on the compiled path. */
+cufz_status cufz_autotune(cufz_ctx* ctx, const cufz_input* sample, uint32_t n,
+                          uint32_t* n_compiled);
+
 cufz_status cufz_get_stats(cufz_ctx* ctx, cufz_stats* out);
 cufz_status cufz_reset_stats(cufz_ctx* ctx);
 

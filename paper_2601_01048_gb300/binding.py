@@ -81,7 +81,7 @@ EXPORTS = [
     "cufz_poll_results", "cufz_get_records", "cufz_get_bitmap", "cufz_get_union",
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
-    "cufz_run_noalloc",
+    "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
 ]
 
 
@@ -119,6 +119,9 @@ def lib():
                 "cufz_program_cuda": (i32, [vp, sz, u32, ctypes.c_char_p, sz, P(sz)]),
                 "cufz_compile_check": (i32, [vp, vp, u32, u32, ctypes.c_char_p, u32, P(sz)]),
                 "cufz_run_noalloc": (i32, [vp, sz, vp, u32, u32, u32, vp, u32, vp, vp, vp]),
+                "cufz_set_program_path": (i32, [vp, u32, u32]),
+                "cufz_get_program_path": (i32, [vp, u32, P(u32)]),
+                "cufz_autotune": (i32, [vp, vp, u32, P(u32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -292,6 +295,27 @@ def cufz_run_noalloc(prog: bytes, inp, records_ptr: int, record_cap: int, bitmap
                                   iter_budget, records_ptr or None, record_cap,
                                   bitmap_ptr or None, result_ptr, stream or None),
            "cufz_run_noalloc")
+
+
+def cufz_set_program_path(ctx, program_id: int, compiled: bool) -> None:
+    _check(lib().cufz_set_program_path(ctx, program_id, int(bool(compiled))),
+           "cufz_set_program_path")
+
+
+def cufz_get_program_path(ctx, program_id: int) -> bool:
+    v = ctypes.c_uint32(0)
+    _check(lib().cufz_get_program_path(ctx, program_id, ctypes.byref(v)), "cufz_get_program_path")
+    return bool(v.value)
+
+
+def cufz_autotune(ctx, sample: np.ndarray) -> int:
+    """Times each program of the sample compiled and interpreted, keeps the
+    faster; returns how many programs stay compiled."""
+    sample = np.ascontiguousarray(sample, dtype=INPUT_DTYPE)
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_autotune(ctx, sample.ctypes.data, len(sample), ctypes.byref(n)),
+           "cufz_autotune")
+    return n.value
 
 
 def cufz_int32_peak(device: int = 0, stream: int = 0) -> float:

@@ -34,6 +34,7 @@ constexpr uint32_t kMaxLanes = 8;
 constexpr uint64_t kProgAreaBytes = 8ull << 20;
 constexpr uint64_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
+constexpr uint32_t kCompileMaxBranchSites = 32;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -64,6 +65,7 @@ struct Lane {
   cudaGraphNode_t copy_node = nullptr;
   uint32_t graph_regs = 0, graph_prog = 0, graph_ctas = 0, graph_threads = 0;
   const void* graph_kernel = nullptr;
+  uint32_t graph_launches = 0;
 };
 
 struct HostOnlyResult {
@@ -110,6 +112,7 @@ struct cufz_ctx {
   cudaLibrary_t jit_lib = nullptr;
   cudaKernel_t jit_persist = nullptr, jit_plain = nullptr;
   uint32_t jit_progs = 0;             // programs in the loaded module
+  std::vector<uint8_t> prog_compiled; // per program: run compiled (1) or interpreted (0)
   uint32_t jit_ctas_per_sm = 0;
   std::string jit_log;
 };
@@ -127,8 +130,10 @@ bool invalid_launch(const cufz_input& in) {
 }
 
 
+// A lane's batch buffer: the compiled path's header, the interpreter's
+// header, the inputs, the compiled path's items, the interpreter's items.
 uint64_t lane_bytes(uint32_t max_inputs, uint32_t max_items) {
-  return align_up(sizeof(BatchHdr) + (uint64_t)max_inputs * sizeof(DevInput) +
+  return align_up(2 * sizeof(BatchHdr) + (uint64_t)max_inputs * sizeof(DevInput) +
                       (uint64_t)max_items * sizeof(WorkItem),
                   kAlign);
 }
@@ -362,23 +367,39 @@ cudaError_t launch_jit_plain(cufz_ctx* c, const BatchHdr* d_batch, uint32_t inpu
                           args, 0, st);
 }
 
-uint32_t persistent_ctas(const cufz_ctx* c) {
-  return use_jit(c) ? c->jit_ctas_per_sm * (uint32_t)c->n_sms : c->shape.ctas;
+uint32_t interp_ctas(const cufz_ctx* c) { return c->shape.ctas; }
+uint32_t jit_ctas(const cufz_ctx* c) { return c->jit_ctas_per_sm * (uint32_t)c->n_sms; }
+bool has_jit_kernel(const cufz_ctx* c) { return use_jit(c) && c->jit_persist; }
+
+const BatchHdr* jit_hdr(const Lane& L) { return reinterpret_cast<const BatchHdr*>(L.d_batch); }
+const BatchHdr* interp_hdr(const Lane& L) {
+  return reinterpret_cast<const BatchHdr*>(L.d_batch + sizeof(BatchHdr));
 }
 
-// one persistent launch of the active path
-cudaError_t launch_batch_kernel(cufz_ctx* c, const BatchHdr* d_batch, uint32_t ctas, cudaStream_t st) {
-  if (use_jit(c)) return launch_jit_persistent(c, d_batch, ctas, st);
-  LaunchShape s = c->shape;
-  s.ctas = ctas;
-  return launch_persistent(c->T, d_batch, s, st);
+// The persistent launches of one batch: the compiled programs' items, then
+// the interpreted programs' items (an empty list costs one short launch).
+cudaError_t launch_batch_kernels(cufz_ctx* c, const Lane& L, uint32_t n_jit, uint32_t n_int,
+                                 bool all, cudaStream_t st, uint32_t* launches) {
+  cudaError_t e = cudaSuccess;
+  if (has_jit_kernel(c) && (all || n_jit)) {
+    uint32_t ctas = all ? jit_ctas(c) : std::min<uint32_t>(jit_ctas(c), n_jit);
+    e = launch_jit_persistent(c, jit_hdr(L), ctas, st);
+    if (e == cudaSuccess) (*launches)++;
+  }
+  if (e == cudaSuccess && (all || n_int)) {
+    LaunchShape s = c->shape;
+    s.ctas = all ? interp_ctas(c) : std::min<uint32_t>(interp_ctas(c), n_int);
+    e = launch_persistent(c->T, interp_hdr(L), s, st);
+    if (e == cudaSuccess) (*launches)++;
+  }
+  return e;
 }
 
 // Captures (or re-captures) the lane's graph: batch upload + persistent kernel.
 cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   const LaunchShape& s = c->shape;
-  const uint32_t ctas = persistent_ctas(c);
-  const void* kern = use_jit(c) ? reinterpret_cast<const void*>(c->jit_persist) : nullptr;
+  const uint32_t ctas = interp_ctas(c) ^ (has_jit_kernel(c) ? jit_ctas(c) << 16 : 0);
+  const void* kern = has_jit_kernel(c) ? reinterpret_cast<const void*>(c->jit_persist) : nullptr;
   if (L.gexec && L.graph_regs == s.max_regs && L.graph_prog == s.max_prog_bytes &&
       L.graph_ctas == ctas && L.graph_threads == s.cta_threads && L.graph_kernel == kern)
     return CUFZ_OK;
@@ -386,8 +407,10 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   cudaGraph_t g = nullptr;
   if (cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
     return CUFZ_E_CUDA;
-  cudaError_t e1 = cudaMemcpyAsync(L.d_batch, L.h_stage, sizeof(BatchHdr), cudaMemcpyHostToDevice, L.stream);
-  cudaError_t e2 = launch_batch_kernel(c, reinterpret_cast<const BatchHdr*>(L.d_batch), ctas, L.stream);
+  uint32_t nl = 0;
+  cudaError_t e1 = cudaMemcpyAsync(L.d_batch, L.h_stage, 2 * sizeof(BatchHdr), cudaMemcpyHostToDevice,
+                                   L.stream);
+  cudaError_t e2 = launch_batch_kernels(c, L, 0, 0, true, L.stream, &nl);
   cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -413,6 +436,7 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   L.graph_ctas = ctas;
   L.graph_threads = s.cta_threads;
   L.graph_kernel = kern;
+  L.graph_launches = nl;
   return CUFZ_OK;
 }
 
@@ -463,7 +487,7 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
-  uint64_t target = batch_threads / (8ull * std::max(persistent_ctas(c), 1u));
+  uint64_t target = batch_threads / (8ull * std::max(std::max(interp_ctas(c), jit_ctas(c)), 1u));
   uint64_t lo = 2ull * cta, hi = 256ull * cta;
   target = std::min(std::max(target, lo), hi);
   return (uint32_t)align_up(target, 32);
@@ -678,6 +702,10 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     return st;
   }
   c->prog_src.push_back(fsrc);
+  // default path: compiled, unless the program is branch-heavy (its compiled
+  // form then outgrows the instruction cache when lanes diverge); the
+  // autotuner measures and can override
+  c->prog_compiled.push_back(P.stats.n_branch_sites <= kCompileMaxBranchSites ? 1 : 0);
   c->prog_used = align_up(c->prog_used + P.blob_bytes, 16);
   if (stats) *stats = P.stats;
   *program_id = (uint32_t)c->progs.size();
@@ -715,8 +743,9 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   }
   const bool plain = c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH;
   // admission
-  BatchHdr* hdr = reinterpret_cast<BatchHdr*>(L->h_stage);
-  DevInput* dins = reinterpret_cast<DevInput*>(L->h_stage + sizeof(BatchHdr));
+  BatchHdr* hdr_j = reinterpret_cast<BatchHdr*>(L->h_stage);
+  BatchHdr* hdr_i = reinterpret_cast<BatchHdr*>(L->h_stage + sizeof(BatchHdr));
+  DevInput* dins = reinterpret_cast<DevInput*>(L->h_stage + 2 * sizeof(BatchHdr));
   uint32_t n_dev = 0;
   uint64_t batch_threads = 0;
   std::vector<uint32_t> dev_slots;
@@ -776,43 +805,24 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   }
   *n_accepted = accepted;
   if (n_dev) {
-    // work items
-    WorkItem* items = reinterpret_cast<WorkItem*>(reinterpret_cast<uint8_t*>(dins) +
-                                                  (uint64_t)n_dev * sizeof(DevInput));
-    uint32_t n_items = 0;
+    // work items: one list per path, each grouped by program (stable), so
+    // CTAs running at the same time mostly run the same program
+    uint8_t* items_base = reinterpret_cast<uint8_t*>(dins) + (uint64_t)n_dev * sizeof(DevInput);
     uint32_t item = choose_item_threads(c, batch_threads);
     c->stats.item_threads = item;
-    bool overflow = false;
-    // work items grouped by program (stable): CTAs running at the same time
-    // then mostly run the same program, which keeps the compiled path's
-    // instruction working set small
     std::vector<uint32_t> order(n_dev);
     for (uint32_t i = 0; i < n_dev; i++) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](uint32_t x, uint32_t y) { return dins[x].prog < dins[y].prog; });
-    for (uint32_t oi = 0; oi < n_dev; oi++) {
-      const uint32_t i = order[oi];
+    auto compiled = [&](uint32_t prog) { return use_jit(c) && c->prog_compiled[prog]; };
+    uint64_t want[2] = {0, 0};
+    for (uint32_t i = 0; i < n_dev; i++) {
       DevInput* d = &dins[i];
-      if (plain) {
-        d->n_items = (uint32_t)(d->n_threads / d->T);
-        continue;
-      }
-      uint32_t cnt = (uint32_t)((d->n_threads + item - 1) / item);
-      if (n_items + cnt > c->lane_max_items) {
-        overflow = true;
-        cnt = 0;
-      }
-      d->n_items = cnt;
-      for (uint32_t k = 0; k < cnt; k++) {
-        WorkItem& w = items[n_items++];
-        w.input = i;
-        w.g0 = k * item;
-        uint64_t rem = d->n_threads - (uint64_t)k * item;
-        w.count = (uint32_t)std::min<uint64_t>(rem, item);
-        w.pad = 0;
-      }
+      d->n_items = plain ? (uint32_t)(d->n_threads / d->T)
+                         : (uint32_t)((d->n_threads + item - 1) / item);
+      if (!plain) want[compiled(d->prog) ? 0 : 1] += d->n_items;
     }
-    if (overflow) {
+    if (want[0] + want[1] > c->lane_max_items) {
       // roll back every device input of this call: more work items than a lane holds
       for (uint32_t s : dev_slots) {
         c->ticket_slot.erase(c->slots[s].ticket);
@@ -822,13 +832,34 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
       *n_accepted = 0;
       return CUFZ_E_NOMEM;
     }
-    memset(hdr, 0, sizeof(*hdr));
-    hdr->n_inputs = n_dev;
-    hdr->n_items = n_items;
-    hdr->next_item = 0;
-    hdr->inputs_off = sizeof(BatchHdr);
-    hdr->items_off = sizeof(BatchHdr) + (uint64_t)n_dev * sizeof(DevInput);
-    uint64_t bytes = hdr->items_off + (uint64_t)n_items * sizeof(WorkItem);
+    WorkItem* lists[2] = {reinterpret_cast<WorkItem*>(items_base),
+                          reinterpret_cast<WorkItem*>(items_base) + want[0]};
+    uint32_t counts[2] = {0, 0};
+    if (!plain) {
+      for (uint32_t oi = 0; oi < n_dev; oi++) {
+        const uint32_t i = order[oi];
+        const DevInput* d = &dins[i];
+        const int li = compiled(d->prog) ? 0 : 1;
+        for (uint32_t k = 0; k < d->n_items; k++) {
+          WorkItem& w = lists[li][counts[li]++];
+          w.input = i;
+          w.g0 = k * item;
+          uint64_t rem = d->n_threads - (uint64_t)k * item;
+          w.count = (uint32_t)std::min<uint64_t>(rem, item);
+          w.pad = 0;
+        }
+      }
+    }
+    const uint32_t n_items = counts[0] + counts[1];
+    memset(hdr_j, 0, 2 * sizeof(BatchHdr));
+    hdr_j->n_inputs = hdr_i->n_inputs = n_dev;
+    hdr_j->n_items = counts[0];
+    hdr_i->n_items = counts[1];
+    hdr_j->inputs_off = 2 * sizeof(BatchHdr);
+    hdr_i->inputs_off = sizeof(BatchHdr);
+    hdr_j->items_off = (uint64_t)(items_base - L->h_stage);
+    hdr_i->items_off = hdr_j->items_off - sizeof(BatchHdr) + (uint64_t)counts[0] * sizeof(WorkItem);
+    uint64_t bytes = (uint64_t)(items_base - L->h_stage) + (uint64_t)n_items * sizeof(WorkItem);
     cufz_status st = CUFZ_OK;
     L->batch_id = c->next_batch++;
     cudaError_t e = cudaEventRecord(L->ev_start, L->stream);
@@ -848,30 +879,28 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
           e = cudaGraphLaunch(L->gexec, L->stream);
           if (e == cudaSuccess) {
             c->stats.graph_launches++;
-            c->stats.kernel_launches++;
+            c->stats.kernel_launches += L->graph_launches;
           }
         }
       }
       if (!use_graph && e == cudaSuccess) {
         e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
         if (e == cudaSuccess && !plain) {
-          uint32_t ctas = std::min<uint32_t>(persistent_ctas(c), std::max<uint32_t>(n_items, 1));
-          e = launch_batch_kernel(c, reinterpret_cast<const BatchHdr*>(L->d_batch), ctas, L->stream);
-          if (e == cudaSuccess) c->stats.kernel_launches++;
+          uint32_t nl = 0;
+          e = launch_batch_kernels(c, *L, counts[0], counts[1], false, L->stream, &nl);
+          c->stats.kernel_launches += nl;
         } else if (e == cudaSuccess) {
           for (uint32_t i = 0; i < n_dev && e == cudaSuccess; i++) {
             LaunchShape s = c->shape;
             s.cta_threads = (uint32_t)align_up(dins[i].T, 32);
-            if (use_jit(c)) {
-              e = launch_jit_plain(c, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
-                                   dins[i].n_items, s.cta_threads, L->stream);
+            if (compiled(dins[i].prog)) {
+              e = launch_jit_plain(c, jit_hdr(*L), i, dins[i].n_items, s.cta_threads, L->stream);
             } else {
               if (smem_for(s, s.cta_threads) > c->smem_set) {
                 e = cudaErrorInvalidConfiguration;
                 break;
               }
-              e = launch_plain(c->T, reinterpret_cast<const BatchHdr*>(L->d_batch), i,
-                               dins[i].n_items, s, L->stream);
+              e = launch_plain(c->T, interp_hdr(*L), i, dins[i].n_items, s, L->stream);
             }
             if (e == cudaSuccess) c->stats.kernel_launches++;
           }
@@ -1078,6 +1107,124 @@ cufz_status cufz_compile_programs(cufz_ctx* c, char* log, uint32_t log_cap) {
     log[n] = 0;
   }
   return st;
+}
+
+cufz_status cufz_set_program_path(cufz_ctx* c, uint32_t program_id, uint32_t compiled) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (program_id >= c->progs.size()) return CUFZ_E_NOT_FOUND;
+  c->prog_compiled[program_id] = compiled ? 1 : 0;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_get_program_path(cufz_ctx* c, uint32_t program_id, uint32_t* compiled) {
+  if (!c || !compiled) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (program_id >= c->progs.size()) return CUFZ_E_NOT_FOUND;
+  *compiled = use_jit(c) && c->prog_compiled[program_id];
+  return CUFZ_OK;
+}
+
+// Runs inputs to completion for the autotuner; their results and slots are
+// taken back so that they never reach the caller.  Returns the device time.
+static cufz_status autotune_run(cufz_ctx* c, const cufz_input* in, uint32_t n, double* ms) {
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    harvest(c);
+    c->stats.kernel_ms = 0;
+  }
+  uint32_t pos = 0;
+  std::vector<uint64_t> tickets;
+  while (pos < n) {
+    uint32_t acc = 0;
+    uint64_t first = 0;
+    cufz_status st = cufz_submit_inputs(c, in + pos, n - pos, &acc, &first);
+    for (uint32_t k = 0; k < acc; k++) tickets.push_back(first + k);
+    pos += acc;
+    if (st != CUFZ_OK && st != CUFZ_E_BUSY) return st;
+    if (st == CUFZ_E_BUSY || acc == 0) {
+      cufz_status s2 = cufz_sync(c, -1);
+      if (s2 != CUFZ_OK) return s2;
+      std::lock_guard<std::mutex> g(c->mu);
+      harvest(c);
+      std::unordered_map<uint64_t, bool> mine;
+      for (uint64_t t : tickets) mine[t] = true;
+      std::deque<cufz_result> keep;
+      for (auto& r : c->ready) {
+        if (!mine.count(r.ticket)) {
+          keep.push_back(r);
+          continue;
+        }
+        c->host_done.erase(r.ticket);
+        auto it = c->ticket_slot.find(r.ticket);
+        if (it != c->ticket_slot.end()) {
+          c->slots[it->second].state = 0;
+          c->free_slots.push_back(it->second);
+          c->ticket_slot.erase(it);
+        }
+      }
+      c->ready.swap(keep);
+      tickets.clear();
+    }
+  }
+  cufz_status st = cufz_sync(c, -1);
+  if (st != CUFZ_OK) return st;
+  std::lock_guard<std::mutex> g(c->mu);
+  harvest(c);
+  std::unordered_map<uint64_t, bool> mine;
+  for (uint64_t t : tickets) mine[t] = true;
+  std::deque<cufz_result> keep;
+  for (auto& r : c->ready) {
+    if (!mine.count(r.ticket)) {
+      keep.push_back(r);
+      continue;
+    }
+    c->host_done.erase(r.ticket);
+    auto it = c->ticket_slot.find(r.ticket);
+    if (it != c->ticket_slot.end()) {
+      c->slots[it->second].state = 0;
+      c->free_slots.push_back(it->second);
+      c->ticket_slot.erase(it);
+    }
+  }
+  c->ready.swap(keep);
+  *ms = c->stats.kernel_ms;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uint32_t* n_compiled) {
+  if (!c || (!sample && n)) return CUFZ_E_INVALID_ARG;
+  if (n_compiled) *n_compiled = 0;
+  if (!use_jit(c)) return CUFZ_OK;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (!c->inflight.empty()) return CUFZ_E_BUSY;
+    cufz_status cs = jit_compile(c);
+    if (cs != CUFZ_OK) return cs;
+  }
+  cufz_stats saved;
+  cufz_get_stats(c, &saved);
+  std::unordered_map<uint32_t, std::vector<cufz_input>> by_prog;
+  for (uint32_t i = 0; i < n; i++) by_prog[sample[i].program_id].push_back(sample[i]);
+  for (auto& kv : by_prog) {
+    const uint32_t p = kv.first;
+    if (p >= c->progs.size()) continue;
+    double best[2] = {1e30, 1e30};
+    for (int rep = 0; rep < 2; rep++)
+      for (uint32_t path = 0; path < 2; path++) {
+        cufz_set_program_path(c, p, path);
+        double ms = 0;
+        cufz_status st = autotune_run(c, kv.second.data(), (uint32_t)kv.second.size(), &ms);
+        if (st != CUFZ_OK) return st;
+        best[path] = std::min(best[path], ms);
+      }
+    cufz_set_program_path(c, p, best[1] < best[0] ? 1 : 0);
+  }
+  std::lock_guard<std::mutex> g(c->mu);
+  c->stats = saved;
+  if (n_compiled)
+    for (uint8_t b : c->prog_compiled) *n_compiled += b;
+  return CUFZ_OK;
 }
 
 cufz_status cufz_get_stats(cufz_ctx* c, cufz_stats* out) {

@@ -269,3 +269,40 @@ def test_union_and_new_coverage(B, orc):
 def test_int32_peak_probe(B):
     v = B.cufz_int32_peak(0, 0)
     assert 1e12 < v < 1e14
+
+
+def test_mixed_paths_and_autotune(B, orc):
+    """Compiled and interpreted programs in one batch (config-5 style mix of
+    1D guarded, random 2D and branch-heavy programs): the default split, every
+    program forced to each path, and the autotuner's choice all agree with
+    the oracle."""
+    progs = gen.c3_programs()[:4] + gen.c2_programs()[:4] + gen.c4_programs()[:4]
+    ins = []
+    ins.append(gen.c3_inputs(24, seed=5, max_blocks=16, max_threads=300))
+    c2 = gen.c2_inputs(progs[4:8], per_program=4, seed=6, max_grid=3)
+    c2["program_id"] += 4
+    ins.append(c2)
+    c4 = gen.c4_inputs(16, n_programs=4, seed=7, max_blocks=6)
+    c4["program_id"] += 8
+    ins.append(c4)
+    inputs = np.concatenate(ins)
+    inputs = inputs[inputs["program_id"] < 12]
+    inputs["program_id"] = np.where(inputs["program_id"] < 4, inputs["program_id"],
+                                    inputs["program_id"])
+    cap = 1 << 14
+    ores, orecs, obms = orc.run_batch(progs, inputs, rec_cap=1 << 17, bitmaps=True)
+    with B.Engine(record_cap=cap, max_slots=256, flags=B.CF_KEEP_BITMAPS | B.CF_JIT) as E:
+        for p in progs:
+            E.load(p)
+        default = [B.cufz_get_program_path(E.ctx, k) for k in range(len(progs))]
+        assert any(default) and not all(default)          # branch-heavy ones interpreted
+        runs = [E.run(inputs)]
+        for forced in (True, False):
+            for k in range(len(progs)):
+                B.cufz_set_program_path(E.ctx, k, forced)
+            runs.append(E.run(inputs))
+        n_comp = B.cufz_autotune(E.ctx, inputs[::3])
+        assert 0 <= n_comp <= len(progs)
+        runs.append(E.run(inputs))
+    for dres, drecs, dbms in runs:
+        compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
