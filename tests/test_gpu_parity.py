@@ -277,18 +277,13 @@ def test_mixed_paths_and_autotune(B, orc):
     program forced to each path, and the autotuner's choice all agree with
     the oracle."""
     progs = gen.c3_programs()[:4] + gen.c2_programs()[:4] + gen.c4_programs()[:4]
-    ins = []
-    ins.append(gen.c3_inputs(24, seed=5, max_blocks=16, max_threads=300))
+    c3 = gen.c3_inputs(24, seed=5, max_blocks=16, max_threads=300)
+    c3["program_id"] %= 4
     c2 = gen.c2_inputs(progs[4:8], per_program=4, seed=6, max_grid=3)
     c2["program_id"] += 4
-    ins.append(c2)
     c4 = gen.c4_inputs(16, n_programs=4, seed=7, max_blocks=6)
     c4["program_id"] += 8
-    ins.append(c4)
-    inputs = np.concatenate(ins)
-    inputs = inputs[inputs["program_id"] < 12]
-    inputs["program_id"] = np.where(inputs["program_id"] < 4, inputs["program_id"],
-                                    inputs["program_id"])
+    inputs = np.concatenate([c3, c2, c4])
     cap = 1 << 14
     ores, orecs, obms = orc.run_batch(progs, inputs, rec_cap=1 << 17, bitmaps=True)
     with B.Engine(record_cap=cap, max_slots=256, flags=B.CF_KEEP_BITMAPS | B.CF_JIT) as E:
