@@ -1,0 +1,59 @@
+"""Serving: inputs admitted while others run give the same result as when
+each runs alone (exact: statuses, counts, digests, records, bitmaps,
+NEW_COV against the same empty epoch snapshot)."""
+import numpy as np
+import pytest
+
+from paper_2601_01048_gb300 import gen
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def B():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2601_01048_gb300 import binding
+    binding.lib()
+    return binding
+
+
+def keyed(recs):
+    cols = ("block_lin", "thread_lin", "ordinal", "site", "buf", "kind", "width", "space", "cls",
+            "byte_off")
+    return sorted(tuple(int(r[c]) for c in cols) for r in recs)
+
+
+FIELDS = ("status", "flags", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+          "n_threads", "n_records", "n_edges")
+
+
+@pytest.mark.parametrize("path", [0, 64])
+def test_alone_equals_in_mix(B, path):
+    from paper_2601_01048_gb300.serve import serve_open_loop
+
+    progs = gen.c5_programs()
+    corpus = gen.c5_corpus(progs, per_program=2, max_blocks=64)
+    stream = gen.c5_stream(progs, corpus, 600, seed=99)
+    arrivals = gen.poisson_arrivals(20000.0, 1.0, seed=3)[:600]
+    stream = stream[: len(arrivals)]
+    watch = list(range(0, len(stream), 37))
+    cap = 1 << 14
+    flags = B.CF_KEEP_BITMAPS | path
+    with B.Engine(record_cap=cap, max_slots=128, n_lanes=4, flags=flags) as E:
+        for p in progs:
+            E.load(p)
+        mix, lat, kept, wall = serve_open_loop(E, stream, arrivals, keep=set(watch))
+        st = E.stats()
+    assert np.all(np.isfinite(lat)) and st.batches > 1
+    with B.Engine(record_cap=cap, max_slots=8, n_lanes=1, flags=flags) as A:
+        for p in progs:
+            A.load(p)
+        for i in watch:
+            alone, recs, bms = A.run(stream[i:i + 1])
+            for f in FIELDS:
+                assert int(alone[0][f]) == int(mix[i][f]), (i, f)
+            assert np.array_equal(bms[0], kept[i][1]), i
+            if int(alone[0]["n_violations"]) <= cap:
+                assert keyed(recs[0]) == keyed(kept[i][0]), i
