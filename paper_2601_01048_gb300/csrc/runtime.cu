@@ -113,6 +113,7 @@ struct cufz_ctx {
   cudaKernel_t jit_persist = nullptr, jit_plain = nullptr;
   uint32_t jit_progs = 0;             // programs in the loaded module
   std::vector<uint8_t> prog_compiled; // per program: run compiled (1) or interpreted (0)
+  std::vector<uint8_t> prog_in_module; // per program: its code is in the loaded module
   uint32_t jit_ctas_per_sm = 0;
   std::string jit_log;
 };
@@ -244,16 +245,19 @@ bool use_jit(const cufz_ctx* c) { return (c->cfg.flags & CUFZ_CF_JIT) != 0; }
 // The compiled path's module: every program's item function, the dispatcher
 // and the kernels, compiled as one translation unit so the program functions
 // are register-allocated together with the kernel that calls them.
-std::string jit_module_source(const std::vector<std::string>& prog_src, bool plain_kernel,
+std::string jit_module_source(const std::vector<std::string>& prog_src,
+                              const std::vector<uint8_t>& include, bool plain_kernel,
                               uint32_t min_ctas) {
   std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas ? min_ctas : 4) +
                     "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
-  for (const auto& f : prog_src) src += f;
+  for (size_t k = 0; k < prog_src.size(); k++)
+    if (include[k]) src += prog_src[k];
   src += "static __device__ bool jit_run(uint32_t prog, const EngineTables* T, const DevInput* in, "
          "uint32_t* hash, uint32_t g0, uint32_t g_end) {\n  switch (prog) {\n";
   for (size_t k = 0; k < prog_src.size(); k++)
-    src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
-           "(T, in, hash, g0, g_end); return true;\n";
+    if (include[k])
+      src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
+             "(T, in, hash, g0, g_end); return true;\n";
   src += "    default: return false;\n  }\n}\n}  // namespace cufz\n";
   if (plain_kernel) src += "#define CUFZ_JIT_PLAIN 1\n";
   src += "#include \"jit_launch.cuh\"\n";
@@ -293,10 +297,12 @@ std::mutex g_jit_cache_mu;
 std::unordered_map<std::string, std::vector<char>> g_jit_cache;  // module source -> image
 
 // Compiled image of a module source, cached for the life of the process.
-cufz_status jit_build_image(const std::vector<std::string>& prog_src, bool plain_kernel,
+cufz_status jit_build_image(const std::vector<std::string>& prog_src,
+                            const std::vector<uint8_t>& include, bool plain_kernel,
                             uint32_t min_ctas, bool fast, std::vector<char>* image,
                             std::string* log) {
-  const std::string src = jit_module_source(prog_src, plain_kernel, min_ctas) + (fast ? "//fast\n" : "");
+  const std::string src =
+      jit_module_source(prog_src, include, plain_kernel, min_ctas) + (fast ? "//fast\n" : "");
   {
     std::lock_guard<std::mutex> g(g_jit_cache_mu);
     auto it = g_jit_cache.find(src);
@@ -316,11 +322,19 @@ cufz_status jit_build_image(const std::vector<std::string>& prog_src, bool plain
 
 // Compiles every loaded program into one module and loads it; the
 // persistent and plain kernels of the compiled path come from it.
+bool jit_current(const cufz_ctx* c) {
+  if (!c->jit_lib || c->prog_in_module.size() != c->progs.size()) return false;
+  for (size_t k = 0; k < c->progs.size(); k++)
+    if (c->prog_compiled[k] && !c->prog_in_module[k]) return false;
+  return true;
+}
+
 cufz_status jit_compile(cufz_ctx* c) {
-  if (c->jit_progs == c->progs.size() && c->jit_lib) return CUFZ_OK;
+  if (jit_current(c)) return CUFZ_OK;
   std::vector<char> cubin;
   const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
-  cufz_status cs = jit_build_image(c->prog_src, plain, c->cfg.jit_min_ctas,
+  std::vector<uint8_t> include = c->prog_compiled;
+  cufz_status cs = jit_build_image(c->prog_src, include, plain, c->cfg.jit_min_ctas,
                                    (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &cubin,
                                    &c->jit_log);
   if (cs != CUFZ_OK) return cs;
@@ -347,6 +361,7 @@ cufz_status jit_compile(cufz_ctx* c) {
   }
   c->jit_ctas_per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
   c->jit_progs = (uint32_t)c->progs.size();
+  c->prog_in_module = include;
   return CUFZ_OK;
 }
 
@@ -737,7 +752,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     }
   }
   if (!L) return CUFZ_E_BUSY;
-  if (use_jit(c) && c->jit_progs != c->progs.size()) {
+  if (use_jit(c) && !jit_current(c)) {
     cufz_status cs = jit_compile(c);
     if (cs != CUFZ_OK) return cs;
   }
@@ -1086,7 +1101,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
   }
   std::vector<char> image;
   std::string lg;
-  cufz_status st = jit_build_image(srcs, (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0,
+  cufz_status st = jit_build_image(srcs, std::vector<uint8_t>(n, 1),
+                                   (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0,
                                    (flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &image, &lg);
   if (log && log_cap) {
     size_t m = std::min<size_t>(lg.size(), log_cap - 1);
@@ -1196,10 +1212,14 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   if (!c || (!sample && n)) return CUFZ_E_INVALID_ARG;
   if (n_compiled) *n_compiled = 0;
   if (!use_jit(c)) return CUFZ_OK;
+  std::vector<uint8_t> before;
   {
     std::lock_guard<std::mutex> g(c->mu);
     if (!c->inflight.empty()) return CUFZ_E_BUSY;
+    before = c->prog_compiled;
+    for (auto& b : c->prog_compiled) b = 1;  // one module with every program
     cufz_status cs = jit_compile(c);
+    c->prog_compiled = before;
     if (cs != CUFZ_OK) return cs;
   }
   cufz_stats saved;
