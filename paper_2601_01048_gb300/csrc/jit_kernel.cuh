@@ -71,18 +71,6 @@ static __device__ __forceinline__ void jit_cover(const EngineTables* T, uint32_t
   }
 }
 
-// Flush of a thread's run of n hits of edge e: lanes of the current group
-// with equal e are merged, their counts summed, and the leader adds the sum,
-// capped at 128 (every count >= 128 falls in the same bucket), to the table.
-static __device__ __noinline__ void jit_cover_run(const EngineTables* T, uint32_t* hash,
-                                                  uint32_t slot, uint32_t e, uint32_t n) {
-  const uint32_t am = __activemask();
-  const uint32_t peers = __match_any_sync(am, e);
-  const uint32_t total = __reduce_add_sync(peers, n);
-  if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
-    edge_add(hash, *T, slot, e, total < 128u ? total : 128u);
-}
-
 // Seeded content of a global buffer (seedx = program seed ^ buf * 0x9E3779B9).
 static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t off, uint32_t lw) {
   const uint32_t word = mix32(seedx ^ (uint32_t)(off >> 2));

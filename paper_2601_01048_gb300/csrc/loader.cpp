@@ -530,14 +530,11 @@ struct Gen {
     return k;
   }
 
-  // A branch evaluation: the edge extends the thread's current run when it
-  // repeats (loop heads), else the run is flushed and a new one starts.
   void cover(int ind, int site, const std::string& cond) {
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
                   "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1; acc.n_branch++;"
-                  " if (e == run_e) { run_n++; } else { if (run_n) jit_cover_run(T, hash, slot,"
-                  " run_e, run_n); run_e = e; run_n = 1; } }");
+                  " jit_cover(T, hash, slot, e); }");
   }
 
   static std::string lim_name(int buf, int lw) {
@@ -693,15 +690,14 @@ struct Gen {
     for (int k = 0; k < 4; k++)
       if (sreg_used[12 + k]) line(2, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
     line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
-    line(2, "uint32_t prev = 0, ordinal = 0, back = 0, run_e = 0xFFFFFFFFu, run_n = 0;");
-    line(2, "(void)prev; (void)ordinal; (void)back; (void)th; (void)run_e;");
+    line(2, "uint32_t prev = 0, ordinal = 0, back = 0;");
+    line(2, "(void)prev; (void)ordinal; (void)back; (void)th;");
     std::string decl;
     for (int v = 0; v < 256; v++)
       if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
     if (!decl.empty()) line(2, decl + ";");
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
-    line(2, "if (run_n) jit_cover_run(T, hash, slot, run_e, run_n);");
     line(2, "acc.n_acc += ordinal;");
     line(1, "}");
     line(1, "__syncwarp();");

@@ -164,7 +164,7 @@ def test_generated_code_compiles_for_sm103a(which):
 
 def test_generated_code_shape():
     src = B.cufz_program_cuda(gen.c1_program())
-    assert "cufz_prog_0" in src and "jit_violation" in src and "jit_cover_run" in src
+    assert "cufz_prog_0" in src and "jit_violation" in src and "jit_cover" in src
     assert src.count("ordinal++") == 3                 # three checked accesses
     assert "r11" not in src                            # the pruned sum x + y is gone
     full = B.cufz_program_cuda(gen.c1_program(), B.CF_NO_PRUNE)
