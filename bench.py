@@ -374,6 +374,9 @@ def run_engine(args, rank, world, local, pg):
                            "kind": "submit-to-poll within a whole-batch step"},
         },
         "gpu_launches": launches,
+        "graph_launches": int(st.graph_launches),
+        "graph_failures": int(st.graph_failures),
+        "last_cuda_error": int(st.last_cuda_error),
         "clocks": clk,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -169,6 +169,8 @@ typedef struct {
   uint32_t n_sms;
   uint32_t max_slots;
   uint32_t smem_bytes;
+  uint32_t graph_failures;    /* batches that fell back to direct launches */
+  int32_t last_cuda_error;    /* last CUDA error code seen by the runtime (0 = none) */
 } cufz_stats;
 
 /* Statistics of a loaded (or pruned) program. */

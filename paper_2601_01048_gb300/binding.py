@@ -57,7 +57,8 @@ class cufz_stats(ctypes.Structure):
                 ("batches", ctypes.c_uint64), ("kernel_ms", ctypes.c_double),
                 ("cta_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("item_threads", ctypes.c_uint32), ("n_sms", ctypes.c_uint32),
-                ("max_slots", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32)]
+                ("max_slots", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
+                ("graph_failures", ctypes.c_uint32), ("last_cuda_error", ctypes.c_int32)]
 
 
 class cufz_prog_stats(ctypes.Structure):

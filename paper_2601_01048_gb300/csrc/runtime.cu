@@ -429,6 +429,7 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
+    c->stats.last_cuda_error = (int32_t)(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3);
     cudaGetLastError();
     return CUFZ_E_CUDA;
   }
@@ -443,6 +444,8 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   cudaError_t e4 = cudaGraphInstantiate(&L.gexec, g, 0);
   cudaGraphDestroy(g);
   if (e4 != cudaSuccess || !L.copy_node) {
+    c->stats.last_cuda_error = (int32_t)(e4 != cudaSuccess ? e4 : cudaErrorUnknown);
+    cudaGetLastError();
     lane_reset_graph(L);
     return CUFZ_E_CUDA;
   }
@@ -879,13 +882,18 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     L->batch_id = c->next_batch++;
     cudaError_t e = cudaEventRecord(L->ev_start, L->stream);
     bool use_graph = !plain && !(c->cfg.flags & CUFZ_CF_NO_GRAPH);
-    if (use_graph && lane_graph(c, *L) != CUFZ_OK) use_graph = false;
+    if (use_graph && lane_graph(c, *L) != CUFZ_OK) {
+      use_graph = false;
+      c->stats.graph_failures++;
+    }
     if (e == cudaSuccess) {
       if (use_graph) {
         e = cudaGraphExecMemcpyNodeSetParams1D(L->gexec, L->copy_node, L->d_batch, L->h_stage,
                                                bytes, cudaMemcpyHostToDevice);
         if (e != cudaSuccess) {
           // the graph cannot take this batch: drop it and launch directly
+          c->stats.last_cuda_error = (int32_t)e;
+          c->stats.graph_failures++;
           cudaGetLastError();
           lane_reset_graph(*L);
           use_graph = false;

@@ -84,6 +84,9 @@ def test_c1_full(B, orc, path):
                                                         flags=B.CF_KEEP_BITMAPS | path)
     compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
     assert st.kernel_launches >= 1 and int(ores["n_violations"].sum()) > 1000
+    # every batch went through the lane's CUDA graph
+    assert st.graph_failures == 0 and st.graph_launches == st.batches, (
+        st.graph_failures, st.graph_launches, st.batches, st.last_cuda_error)
 
 
 @pytest.mark.parametrize("path", PATHS)
