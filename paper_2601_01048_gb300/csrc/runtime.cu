@@ -62,7 +62,6 @@ struct Lane {
   bool timed = false;
   uint64_t batch_id = 0;
   cudaGraphExec_t gexec = nullptr;
-  cudaGraphNode_t copy_node = nullptr;
   uint32_t graph_regs = 0, graph_prog = 0, graph_ctas = 0, graph_threads = 0;
   const void* graph_kernel = nullptr;
   uint32_t graph_launches = 0;
@@ -165,7 +164,6 @@ cufz_status cuda_err(cudaError_t e) { return e == cudaSuccess ? CUFZ_OK : CUFZ_E
 void lane_reset_graph(Lane& L) {
   if (L.gexec) cudaGraphExecDestroy(L.gexec);
   L.gexec = nullptr;
-  L.copy_node = nullptr;
 }
 
 // Accounts the finished batch of a lane (timing) and marks it free.
@@ -410,7 +408,8 @@ cudaError_t launch_batch_kernels(cufz_ctx* c, const Lane& L, uint32_t n_jit, uin
   return e;
 }
 
-// Captures (or re-captures) the lane's graph: batch upload + persistent kernel.
+// Captures (or re-captures) the lane's graph: the persistent kernels of a
+// batch (compiled programs' items, interpreted programs' items).
 cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   const LaunchShape& s = c->shape;
   const uint32_t ctas = interp_ctas(c) ^ (has_jit_kernel(c) ? jit_ctas(c) << 16 : 0);
@@ -420,31 +419,29 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
     return CUFZ_OK;
   lane_reset_graph(L);
   cudaGraph_t g = nullptr;
-  if (cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+  cudaGetLastError();  // a stale error must not be taken for the capture's
+  cudaError_t e0 = cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal);
+  if (e0 != cudaSuccess) {
+    c->stats.last_cuda_error = 70000 + (int32_t)e0;
+    cudaGetLastError();
     return CUFZ_E_CUDA;
+  }
   uint32_t nl = 0;
-  cudaError_t e1 = cudaMemcpyAsync(L.d_batch, L.h_stage, 2 * sizeof(BatchHdr), cudaMemcpyHostToDevice,
-                                   L.stream);
+  cudaError_t e1 = cudaSuccess;
   cudaError_t e2 = launch_batch_kernels(c, L, 0, 0, true, L.stream, &nl);
   cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
-    c->stats.last_cuda_error = (int32_t)(e1 != cudaSuccess ? e1 : e2 != cudaSuccess ? e2 : e3);
+    c->stats.last_cuda_error = e1 != cudaSuccess ? 10000 + (int32_t)e1
+                             : e2 != cudaSuccess ? 20000 + (int32_t)e2
+                                                 : 30000 + (int32_t)e3;
     cudaGetLastError();
     return CUFZ_E_CUDA;
   }
-  size_t n = 0;
-  cudaGraphGetNodes(g, nullptr, &n);
-  std::vector<cudaGraphNode_t> nodes(n);
-  cudaGraphGetNodes(g, nodes.data(), &n);
-  for (auto nd : nodes) {
-    cudaGraphNodeType t;
-    if (cudaGraphNodeGetType(nd, &t) == cudaSuccess && t == cudaGraphNodeTypeMemcpy) L.copy_node = nd;
-  }
   cudaError_t e4 = cudaGraphInstantiate(&L.gexec, g, 0);
   cudaGraphDestroy(g);
-  if (e4 != cudaSuccess || !L.copy_node) {
-    c->stats.last_cuda_error = (int32_t)(e4 != cudaSuccess ? e4 : cudaErrorUnknown);
+  if (e4 != cudaSuccess) {
+    c->stats.last_cuda_error = e4 != cudaSuccess ? 40000 + (int32_t)e4 : 50000;
     cudaGetLastError();
     lane_reset_graph(L);
     return CUFZ_E_CUDA;
@@ -887,32 +884,29 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
       c->stats.graph_failures++;
     }
     if (e == cudaSuccess) {
-      if (use_graph) {
-        e = cudaGraphExecMemcpyNodeSetParams1D(L->gexec, L->copy_node, L->d_batch, L->h_stage,
-                                               bytes, cudaMemcpyHostToDevice);
-        if (e != cudaSuccess) {
-          // the graph cannot take this batch: drop it and launch directly
-          c->stats.last_cuda_error = (int32_t)e;
+      // the batch image goes up on the lane's stream, then its kernels run
+      e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
+      if (use_graph && e == cudaSuccess) {
+        e = cudaGraphLaunch(L->gexec, L->stream);
+        if (e == cudaSuccess) {
+          c->stats.graph_launches++;
+          c->stats.kernel_launches += L->graph_launches;
+        } else {
+          // the graph cannot run this batch: drop it and launch directly
+          c->stats.last_cuda_error = 60000 + (int32_t)e;
           c->stats.graph_failures++;
           cudaGetLastError();
           lane_reset_graph(*L);
           use_graph = false;
           e = cudaSuccess;
-        } else {
-          e = cudaGraphLaunch(L->gexec, L->stream);
-          if (e == cudaSuccess) {
-            c->stats.graph_launches++;
-            c->stats.kernel_launches += L->graph_launches;
-          }
         }
       }
       if (!use_graph && e == cudaSuccess) {
-        e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
-        if (e == cudaSuccess && !plain) {
+        if (!plain) {
           uint32_t nl = 0;
           e = launch_batch_kernels(c, *L, counts[0], counts[1], false, L->stream, &nl);
           c->stats.kernel_launches += nl;
-        } else if (e == cudaSuccess) {
+        } else {
           for (uint32_t i = 0; i < n_dev && e == cudaSuccess; i++) {
             LaunchShape s = c->shape;
             s.cta_threads = (uint32_t)align_up(dins[i].T, 32);
