@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--cta-threads", type=int, default=256)
     ap.add_argument("--jit-min-ctas", type=int, default=0)
     ap.add_argument("--jit-fast-compile", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the load-time path choice (for profiling a single launch)")
     ap.add_argument("--item-threads", type=int, default=0)
     return ap.parse_args()
 
@@ -244,7 +246,7 @@ def run_engine(args, rank, world, local, pg):
     for p in progs:
         E.load(p)
     tuned = None
-    if args.path == "jit":
+    if args.path == "jit" and not args.no_autotune:
         # the project's autotuner: per program, compiled vs interpreted on a
         # sample of that program's inputs (two per program)
         sample = np.concatenate([inputs[inputs["program_id"] == p][:2]
