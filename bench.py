@@ -248,8 +248,8 @@ def run_engine(args, rank, world, local, pg):
     tuned = None
     if args.path == "jit" and not args.no_autotune:
         # the project's autotuner: per program, compiled vs interpreted on a
-        # sample of that program's inputs (two per program)
-        sample = np.concatenate([inputs[inputs["program_id"] == p][:2]
+        # sample of that program's inputs (up to eight per program)
+        sample = np.concatenate([inputs[inputs["program_id"] == p][:8]
                                  for p in np.unique(inputs["program_id"])])
         tuned = B.cufz_autotune(E.ctx, sample)
     n_batches = (n_all + per_step - 1) // per_step

@@ -128,7 +128,8 @@ typedef struct {
   uint64_t n_accesses;   /* executed loads + stores (checked thread-accesses) */
   uint64_t n_violations; /* exact, even when records overflowed */
   uint64_t first_key;    /* min of block_lin<<32 | thread_lin<<22 | min(ordinal, 2^22-1) */
-  uint64_t digest;       /* sum of per-access hashes mod 2^64 (pruning check) */
+  uint64_t digest;       /* sum of per-access hashes of (thread, ordinal, site, index)
+                            mod 2^64 (pruning check) */
   uint64_t n_branch;     /* branch evaluations (coverage events) */
   uint64_t n_threads;    /* test threads run */
   uint64_t n_ops;        /* executed program ops, summed over test threads */
@@ -299,8 +300,9 @@ cufz_status cufz_set_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t c
 cufz_status cufz_get_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t* compiled);
 
 /* Autotuner: for every program in the sample, times the sample's inputs of
- * that program run compiled and interpreted (twice each) and keeps the
- * faster path.  Needs an idle context; the sample's results are discarded.
+ * that program run compiled and interpreted (best of three each) and moves
+ * the program off its load-time path only if the other is at least 25%
+ * faster.  Needs an idle context; the sample's results are discarded.
  * *n_compiled receives the number of programs left on the compiled path. */
 cufz_status cufz_autotune(cufz_ctx* ctx, const cufz_input* sample, uint32_t n,
                           uint32_t* n_compiled);

@@ -54,9 +54,12 @@
  * Per-input digest of all executed accesses (the pruning check, Sec. 5.2:
  * all memory accesses are preserved exactly):
  *   th = fmix32(block_lin * 0x9E3779B1 + thread_lin)
- *   h  = fmix32(th ^ (ordinal * 0x85EBCA77 + site * 0xC2B2AE3D)
- *               ^ lo32(off) ^ (hi32(off) * 0x27D4EB2F))
+ *   K  = (site * 0xC2B2AE3D) | 1                (odd: idx * K is a bijection)
+ *   m  = th ^ (ordinal * 0x85EBCA77) ^ (idx * K)     (32-bit arithmetic)
+ *   h  = ((m ^ (m >> 16)) * 0x7FEB352D) ^ (that >> 15)  (first half of the
+ *        lowbias32 integer hash, C. Wellons)
  *   D  = sum of h mod 2^64
+ * idx is the access's int32 index; the site fixes buffer, kind and width.
  * ordinal = the number of accesses the thread executed before this one.
  *
  * first_key = min over violations of
@@ -349,9 +352,10 @@ static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
   int viol = off < 0 || off + w > c->len[buf];
   orc_result* res = c->res;
   res->n_accesses++;
-  uint32_t mix = (c->ordinal * 0x85EBCA77u + (uint32_t)op->site * 0xC2B2AE3Du) ^ (uint32_t)off ^
-                 ((uint32_t)((uint64_t)off >> 32) * 0x27D4EB2Fu);
-  res->digest += fmix32(c->th ^ mix);
+  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 1u;
+  uint32_t m = c->th ^ (c->ordinal * 0x85EBCA77u) ^ ((uint32_t)idx * K);
+  uint32_t h = (m ^ (m >> 16)) * 0x7FEB352Du;
+  res->digest += h ^ (h >> 15);
   int32_t value = 0;
   if (viol) {
     uint64_t ord = c->ordinal < 0x3FFFFFu ? c->ordinal : 0x3FFFFFu;

@@ -25,6 +25,16 @@ static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   return h;
 }
 
+// Per-access term of the input's digest: k = (site * 0xC2B2AE3D) | 1 (odd,
+// so idx * k is a bijection), then one multiply-xorshift round (the first
+// half of C. Wellons' lowbias32 integer hash).
+static __device__ __forceinline__ uint32_t access_hash(uint32_t th, uint32_t ordinal, uint32_t k,
+                                                       int32_t idx) {
+  const uint32_t m = th ^ (ordinal * 0x85EBCA77u) ^ ((uint32_t)idx * k);
+  const uint32_t h = (m ^ (m >> 16)) * 0x7FEB352Du;
+  return h ^ (h >> 15);
+}
+
 // floor(n / d) for n < 2^32 with m = ceil(2^64 / d) (m == 0 means d == 1).
 static __device__ __forceinline__ uint32_t udiv(uint32_t n, uint64_t m) {
   if (m == 0) return n;

@@ -39,28 +39,6 @@ __device__ __forceinline__ void rf_st(uint8_t* rf, uint32_t off, int32_t v) {
   *reinterpret_cast<int32_t*>(rf + off) = v;
 }
 
-__device__ __forceinline__ int32_t alu(uint32_t op, int32_t x, int32_t y) {
-  uint32_t ux = (uint32_t)x, uy = (uint32_t)y;
-  switch (op) {
-    case A_ADD: return (int32_t)(ux + uy);
-    case A_SUB: return (int32_t)(ux - uy);
-    case A_MUL: return (int32_t)(ux * uy);
-    case A_SHL: return (int32_t)(ux << (uy & 31u));
-    case A_SHR: return x >> (int)(uy & 31u);
-    case A_SHRU: return (int32_t)(ux >> (uy & 31u));
-    case A_AND: return (int32_t)(ux & uy);
-    case A_OR: return (int32_t)(ux | uy);
-    case A_XOR: return (int32_t)(ux ^ uy);
-    case A_MIN: return min(x, y);
-    case A_MAX: return max(x, y);
-    case A_SETLT: return x < y;
-    case A_SETLE: return x <= y;
-    case A_SETEQ: return x == y;
-    case A_SETNE: return x != y;
-    default: return ux < uy;  // A_SETLTU
-  }
-}
-
 // Runs the test threads [g0, g0 + count) of one input on this warp's lanes.
 __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* in,
                                          const uint8_t* sprog, uint8_t* rf_warp, uint32_t* hash,
@@ -136,21 +114,55 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
     for (;;) {
       const DevOp op = ops[pc];
       const uint32_t opc = op.opc;
-      if (opc < D_LD) {
-        // value ops
-        int32_t x = rf_ld(rf, op.a);
-        int32_t r;
-        if (opc >= D_ALUI0) {
-          r = alu(opc - D_ALUI0, x, op.imm);
-        } else if (opc >= D_ALU0) {
-          r = alu(opc - D_ALU0, x, rf_ld(rf, op.b));
-        } else if (opc == D_MOV) {
-          r = x;
-        } else if (opc == D_IMM) {
+      // value ops: one dispatch, the op inline, a predicated store
+      int32_t r;
+      switch (opc) {
+#define CUFZ_ALU_CASES(ID, EXPR)                                        \
+  case D_ALU0 + ID: {                                                   \
+    const int32_t x = rf_ld(rf, op.a), y = rf_ld(rf, op.b);             \
+    const uint32_t ux = (uint32_t)x, uy = (uint32_t)y;                  \
+    (void)ux; (void)uy;                                                 \
+    r = (EXPR);                                                         \
+    goto value_done;                                                    \
+  }                                                                     \
+  case D_ALUI0 + ID: {                                                  \
+    const int32_t x = rf_ld(rf, op.a), y = op.imm;                      \
+    const uint32_t ux = (uint32_t)x, uy = (uint32_t)y;                  \
+    (void)ux; (void)uy;                                                 \
+    r = (EXPR);                                                         \
+    goto value_done;                                                    \
+  }
+        CUFZ_ALU_CASES(A_ADD, (int32_t)(ux + uy))
+        CUFZ_ALU_CASES(A_SUB, (int32_t)(ux - uy))
+        CUFZ_ALU_CASES(A_MUL, (int32_t)(ux * uy))
+        CUFZ_ALU_CASES(A_SHL, (int32_t)(ux << (uy & 31u)))
+        CUFZ_ALU_CASES(A_SHR, x >> (int)(uy & 31u))
+        CUFZ_ALU_CASES(A_SHRU, (int32_t)(ux >> (uy & 31u)))
+        CUFZ_ALU_CASES(A_AND, (int32_t)(ux & uy))
+        CUFZ_ALU_CASES(A_OR, (int32_t)(ux | uy))
+        CUFZ_ALU_CASES(A_XOR, (int32_t)(ux ^ uy))
+        CUFZ_ALU_CASES(A_MIN, min(x, y))
+        CUFZ_ALU_CASES(A_MAX, max(x, y))
+        CUFZ_ALU_CASES(A_SETLT, (int32_t)(x < y))
+        CUFZ_ALU_CASES(A_SETLE, (int32_t)(x <= y))
+        CUFZ_ALU_CASES(A_SETEQ, (int32_t)(x == y))
+        CUFZ_ALU_CASES(A_SETNE, (int32_t)(x != y))
+        CUFZ_ALU_CASES(A_SETLTU, (int32_t)(ux < uy))
+#undef CUFZ_ALU_CASES
+        case D_MOV:
+          r = rf_ld(rf, op.a);
+          goto value_done;
+        case D_IMM:
           r = op.imm;
-        } else {  // D_SEL
-          r = x != 0 ? rf_ld(rf, op.b) : rf_ld(rf, (uint32_t)op.imm);
-        }
+          goto value_done;
+        case D_SEL:
+          r = rf_ld(rf, op.a) != 0 ? rf_ld(rf, op.b) : rf_ld(rf, (uint32_t)op.imm);
+          goto value_done;
+        default:
+          break;
+      }
+      if (false) {
+      value_done:
         if (act) {
           rf_st(rf, op.d, r);
           acc.n_ops++;
@@ -172,11 +184,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           const bool viol = act && (idx < 0 || off + (int64_t)w > len);
           if (act) {
             acc.n_acc++;
-            if (do_digest) {
-              uint32_t mixv = (ordinal * 0x85EBCA77u + (uint32_t)op.imm * 0xC2B2AE3Du) ^
-                              (uint32_t)off ^ ((uint32_t)((uint64_t)off >> 32) * 0x27D4EB2Fu);
-              acc.digest += mix32(th ^ mixv);
-            }
+            if (do_digest) acc.digest += access_hash(th, ordinal, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
           }
           const uint32_t vm = __ballot_sync(FULL, viol);
           if (vm) {

@@ -77,11 +77,6 @@ static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t of
   return lw == 0 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word;
 }
 
-static __device__ __forceinline__ uint32_t jit_digest(uint32_t th, uint32_t ordinal, uint32_t site_c2,
-                                               int64_t off) {
-  const uint32_t m = (ordinal * 0x85EBCA77u + site_c2) ^ (uint32_t)off ^
-                     ((uint32_t)((uint64_t)off >> 32) * 0x27D4EB2Fu);
-  return mix32(th ^ m);
-}
+
 
 }  // namespace cufz

@@ -552,8 +552,8 @@ struct Gen {
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
     line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
-    line(ind + 1, "if (dig) acc.digest += jit_digest(th, ordinal, " +
-                      hex32((uint32_t)o2.site * 0xC2B2AE3Du) + ", off);");
+    line(ind + 1, "if (dig) acc.digest += access_hash(th, ordinal, " +
+                      hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) + ", ix);");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
     line(ind + 1, "acc.n_viol += viol ? 1u : 0u;");

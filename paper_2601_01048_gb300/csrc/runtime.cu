@@ -35,6 +35,7 @@ constexpr uint64_t kProgAreaBytes = 8ull << 20;
 constexpr uint64_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
 constexpr uint32_t kCompileMaxBranchSites = 32;
+constexpr double kAutotuneMargin = 1.25;  // the other path must be 25% faster
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -1231,8 +1232,9 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   for (auto& kv : by_prog) {
     const uint32_t p = kv.first;
     if (p >= c->progs.size()) continue;
+    const uint32_t dflt = before[p];
     double best[2] = {1e30, 1e30};
-    for (int rep = 0; rep < 2; rep++)
+    for (int rep = 0; rep < 3; rep++)
       for (uint32_t path = 0; path < 2; path++) {
         cufz_set_program_path(c, p, path);
         double ms = 0;
@@ -1240,7 +1242,9 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
         if (st != CUFZ_OK) return st;
         best[path] = std::min(best[path], ms);
       }
-    cufz_set_program_path(c, p, best[1] < best[0] ? 1 : 0);
+    // leave the load-time choice only for a clear win
+    const uint32_t other = 1u - dflt;
+    cufz_set_program_path(c, p, best[other] * kAutotuneMargin < best[dflt] ? other : dflt);
   }
   std::lock_guard<std::mutex> g(c->mu);
   c->stats = saved;

@@ -140,9 +140,10 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         def mem(is_st, d, a, buf, w, site):
             off = regs[a] * w
             bad = off < 0 or off + w > lens[buf]
-            mix = ((t["ordinal"] * 0x85EBCA77 + site * 0xC2B2AE3D) & M32) ^ (off & M32) ^ \
-                (((off & M64) >> 32) * 0x27D4EB2F & M32)
-            st["digest"] = (st["digest"] + murmur_fmix32(th ^ mix)) & M64
+            k = ((site * 0xC2B2AE3D) & M32) | 1
+            m = th ^ ((t["ordinal"] * 0x85EBCA77) & M32) ^ ((regs[a] * k) & M32)
+            h = ((m ^ (m >> 16)) * 0x7FEB352D) & M32
+            st["digest"] = (st["digest"] + (h ^ (h >> 15))) & M64
             st["n_accesses"] += 1
             val = 0
             if bad:
