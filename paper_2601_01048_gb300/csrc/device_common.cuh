@@ -25,14 +25,16 @@ static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   return h;
 }
 
-// Per-access term of the input's digest: k = (site * 0xC2B2AE3D) | 1 (odd,
-// so idx * k is a bijection), then one multiply-xorshift round (the first
-// half of C. Wellons' lowbias32 integer hash).
-static __device__ __forceinline__ uint32_t access_hash(uint32_t th, uint32_t ordinal, uint32_t k,
-                                                       int32_t idx) {
-  const uint32_t m = th ^ (ordinal * 0x85EBCA77u) ^ ((uint32_t)idx * k);
-  const uint32_t h = (m ^ (m >> 16)) * 0x7FEB352Du;
-  return h ^ (h >> 15);
+// Digest of the accesses: per access m = th ^ ordinal * kOrdMul ^ idx * k
+// with k = (site * 0xC2B2AE3D) | 1 (odd, so idx * k is a bijection), term
+// (m ^ m >> 16) * 0x7FEB352D (a bijection of m: the first step of C.
+// Wellons' lowbias32 hash); terms summed mod 2^32 per test thread, thread
+// sums mod 2^64 per input.  `tho` = th ^ ordinal * kOrdMul.
+constexpr uint32_t kOrdMul = 0x85EBCA77u;
+constexpr uint32_t kOrdInv = 0xB6C92F47u;  // kOrdMul * kOrdInv == 1 mod 2^32
+static __device__ __forceinline__ uint32_t access_term(uint32_t tho, uint32_t k, int32_t idx) {
+  const uint32_t m = tho ^ ((uint32_t)idx * k);
+  return (m ^ (m >> 16)) * 0x7FEB352Du;
 }
 
 // floor(n / d) for n < 2^32 with m = ceil(2^64 / d) (m == 0 means d == 1).
@@ -64,8 +66,21 @@ static __device__ __forceinline__ void edge_global_add(const EngineTables& T, ui
   }
 }
 
-// Per-CTA hash table entry: (e + 1) << 15 | count (count saturates near 128;
-// at most 127 + 32 * 32 < 2^15 with every warp adding at once).
+// The CTA's edge state in shared memory: a hash table of kHashSlots entries
+// (e + 1) << 15 | count, followed by a bitmap of the edges whose count in
+// the table reached 128 (their AFL bucket can no longer change, so later hits
+// are skipped).  Counts saturate near 128: at most 127 + 32 * 32 < 2^15 with
+// every warp adding at once.
+static __device__ __forceinline__ bool edge_saturated(const uint32_t* hash, uint32_t e) {
+  return (hash[kHashSlots + (e >> 5)] >> (e & 31u)) & 1u;
+}
+
+static __device__ __forceinline__ void edge_hit(uint32_t* hash, uint32_t h, uint32_t e, uint32_t c) {
+  const uint32_t cur = hash[h] & kHashCountMask;
+  const uint32_t old = cur < 128u ? (atomicAdd(&hash[h], c) & kHashCountMask) : cur;
+  if (old + c >= 128u) atomicOr(&hash[kHashSlots + (e >> 5)], 1u << (e & 31u));
+}
+
 static __device__ __noinline__ void edge_add(uint32_t* hash, const EngineTables& T, uint32_t slot,
                                       uint32_t e, uint32_t c) {
   uint32_t tag = (e + 1u) << kHashTagShift;
@@ -75,14 +90,14 @@ static __device__ __noinline__ void edge_add(uint32_t* hash, const EngineTables&
   for (int p = 0; p < kHashProbes; p++) {
     uint32_t cur = hash[h];
     if ((cur & ~kHashCountMask) == tag) {
-      if ((cur & kHashCountMask) < 128u) atomicAdd(&hash[h], c);
+      edge_hit(hash, h, e, c);
       return;
     }
     if (cur == 0) {
       uint32_t old = atomicCAS(&hash[h], 0u, tag | c);
       if (old == 0) return;
       if ((old & ~kHashCountMask) == tag) {
-        if ((old & kHashCountMask) < 128u) atomicAdd(&hash[h], c);
+        edge_hit(hash, h, e, c);
         return;
       }
     }
@@ -275,7 +290,7 @@ static __device__ __forceinline__ void run_items(const EngineTables& T, BatchHdr
       reinterpret_cast<const uint8_t*>(batch) + batch->items_off);
   const uint32_t n_items = kPersistent ? batch->n_items : 1u;
 
-  for (uint32_t i = threadIdx.x; i < kHashSlots; i += blockDim.x) hash[i] = 0;
+  for (uint32_t i = threadIdx.x; i < kHashSlots + kSatWords; i += blockDim.x) hash[i] = 0;
   uint32_t cur_input = 0xFFFFFFFFu, cur_prog = 0xFFFFFFFFu;
   bool first = true;
 
@@ -335,6 +350,7 @@ static __device__ __forceinline__ void run_items(const EngineTables& T, BatchHdr
         hash[i] = 0;
       }
     }
+    for (uint32_t i = threadIdx.x; i < kSatWords; i += blockDim.x) hash[kHashSlots + i] = 0;
     __threadfence();
     __syncthreads();
     if (threadIdx.x == 0) {

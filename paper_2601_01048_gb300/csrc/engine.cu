@@ -106,7 +106,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
 
     bool act = valid, alive = valid;
     uint32_t stk_act = 0, stk_aux = 0;
-    uint32_t prev = 0, ordinal = 0, back = 0;
+    uint32_t prev = 0, ordinal = 0, back = 0, dsum = 0;
     const uint32_t th = mix32(bl * 0x9E3779B1u + tl);
 
     uint32_t pc = 0;
@@ -184,7 +184,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           const bool viol = act && (idx < 0 || off + (int64_t)w > len);
           if (act) {
             acc.n_acc++;
-            if (do_digest) acc.digest += access_hash(th, ordinal, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
+            if (do_digest) dsum += access_term(th ^ (ordinal * kOrdMul), ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
           }
           const uint32_t vm = __ballot_sync(FULL, viol);
           if (vm) {
@@ -230,8 +230,11 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
               prev = cur >> 1;
               acc.n_branch++;
             }
-            const uint32_t peers = __match_any_sync(FULL, act ? e : 0xFFFFFFFFu);
-            if (act && lane == (uint32_t)(__ffs(peers) - 1)) edge_add(hash, T, slot, e, __popc(peers));
+            const bool hit = act && !edge_saturated(hash, e);
+            if (__any_sync(FULL, hit)) {
+              const uint32_t peers = __match_any_sync(FULL, hit ? e : 0xFFFFFFFFu);
+              if (hit && lane == (uint32_t)(__ffs(peers) - 1)) edge_add(hash, T, slot, e, __popc(peers));
+            }
           }
           stk_act = (stk_act << 1) | (act ? 1u : 0u);
           stk_aux = (stk_aux << 1) | ((act && !c) ? 1u : 0u);
@@ -294,8 +297,11 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
             prev = cur >> 1;
             acc.n_branch++;
           }
-          const uint32_t peers = __match_any_sync(FULL, inl ? e : 0xFFFFFFFFu);
-          if (inl && lane == (uint32_t)(__ffs(peers) - 1)) edge_add(hash, T, slot, e, __popc(peers));
+          const bool hit = inl && !edge_saturated(hash, e);
+          if (__any_sync(FULL, hit)) {
+            const uint32_t peers = __match_any_sync(FULL, hit ? e : 0xFFFFFFFFu);
+            if (hit && lane == (uint32_t)(__ffs(peers) - 1)) edge_add(hash, T, slot, e, __popc(peers));
+          }
         }
         if (inl && !cont) stk_aux &= ~1u;
         act = cont;
@@ -309,6 +315,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
         }
       }
     }
+    acc.digest += dsum;
   }
 
   acc_flush(T, slot, acc);
@@ -321,7 +328,7 @@ __global__ void __launch_bounds__(1024) interp_kernel(EngineTables T, BatchHdr* 
                                                       uint32_t max_prog_bytes) {
   extern __shared__ __align__(16) uint8_t smem[];
   uint32_t* hash = reinterpret_cast<uint32_t*>(smem);
-  uint8_t* sprog = smem + kHashSlots * 4;
+  uint8_t* sprog = smem + kEdgeSmemBytes;
   DevInput* sin = reinterpret_cast<DevInput*>(sprog + max_prog_bytes);
   uint8_t* rf = reinterpret_cast<uint8_t*>(sin) + kInputSmemBytes;
   const uint32_t warp = threadIdx.x >> 5;
@@ -340,7 +347,7 @@ template __global__ void interp_kernel<true>(EngineTables, BatchHdr*, uint32_t, 
 template __global__ void interp_kernel<false>(EngineTables, BatchHdr*, uint32_t, uint32_t, uint32_t);
 
 static uint32_t smem_bytes_for(const LaunchShape& s) {
-  return kHashSlots * 4 + s.max_prog_bytes + kInputSmemBytes +
+  return kEdgeSmemBytes + s.max_prog_bytes + kInputSmemBytes +
          (s.cta_threads / 32) * s.max_regs * kRegStride;
 }
 

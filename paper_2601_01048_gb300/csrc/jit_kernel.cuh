@@ -3,45 +3,55 @@
 // variables, buffer/width/site/LOC values become constants); these helpers
 // are what the emitted code calls for checks, records and coverage.  The
 // emitted code runs each test thread as one CUDA thread; lanes that take the
-// same path are aggregated with __activemask() groups.
+// same path are aggregated with __activemask() groups.  Per access the
+// emitted code keeps counts, the first violating access and the digest in
+// registers; jit_record runs only while the input's record area has room.
 #pragma once
 
 #include "device_common.cuh"
 
 namespace cufz {
 
+// The CTA's engine tables, copy of the current input and edge state.  They
+// sit at file scope so that the program functions (which take no pointers)
+// reach them as shared memory: 32-bit addresses and shared-memory atomics,
+// and no registers held for base pointers.
+static __shared__ EngineTables s_T;
+static __shared__ __align__(16) DevInput s_in;
+static __shared__ __align__(16) uint32_t s_hash[kHashSlots + kSatWords];
+
 // Record path of a violating access, entered by the violating lanes of a
 // warp that may still reserve record space: one atomicAdd per group, ranks
 // from popc.  `what` packs site | buf << 16 | kind << 20 | log2(width) << 24.
 // Returns true once the input's record area is full.
-static __device__ __noinline__ bool jit_record(const EngineTables* T, const DevInput* in, uint32_t bl,
-                                        uint32_t tl, uint32_t ordinal, uint32_t what,
-                                        int64_t off) {
+static __device__ __noinline__ bool jit_record(uint32_t bl, uint32_t tl, uint32_t ordinal,
+                                               uint32_t what, int64_t off) {
   const uint32_t am = __activemask();
   const uint32_t lane = threadIdx.x & 31u;
   const uint32_t leader = __ffs(am) - 1;
   const uint32_t k = __popc(am);
-  const uint32_t cap = T->record_cap;
+  const uint32_t cap = s_T.record_cap;
+  const uint32_t slot = s_in.slot;
   uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(&T->slots[in->slot].rec_reserved, k);
+  if (lane == leader) base = atomicAdd(&s_T.slots[slot].rec_reserved, k);
   base = __shfl_sync(am, base, leader);
   const uint32_t rank = __popc(am & ((1u << lane) - 1u));
   if (base + rank < cap) {
     const uint32_t site = what & 0xFFFFu, buf = (what >> 16) & 0xFu, kind = (what >> 20) & 1u;
     const uint32_t w = 1u << ((what >> 24) & 7u);
-    const uint32_t sm = in->shared_mask;
-    const uint32_t cls = classify(in, sm, in->n_bufs, buf, off, w, (int64_t)T->redzone);
-    write_record(T->records + (size_t)in->slot * cap + base + rank, bl, tl, ordinal, site, buf,
+    const uint32_t sm = s_in.shared_mask;
+    const uint32_t cls = classify(&s_in, sm, s_in.n_bufs, buf, off, w, (int64_t)s_T.redzone);
+    write_record(s_T.records + (size_t)slot * cap + base + rank, bl, tl, ordinal, site, buf,
                  kind, w, (sm >> buf) & 1u, cls, off);
   }
   return base + k >= cap;
 }
 
-static __device__ __forceinline__ void jit_violation(const EngineTables* T, const DevInput* in,
-                                              LaneAcc& acc, uint32_t bl, uint32_t tl,
-                                              uint32_t ordinal, uint32_t what, int64_t off) {
-  if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
-  if (!acc.rec_full) acc.rec_full = jit_record(T, in, bl, tl, ordinal, what, off);
+// Whether the input's record area had room when the item started; a lane
+// stops calling jit_record once a reservation comes back full.
+static __device__ __forceinline__ bool jit_records_open(uint32_t slot) {
+  const volatile uint32_t* r = &s_T.slots[slot].rec_reserved;
+  return *r < s_T.record_cap;
 }
 
 // Number of in-bounds indices of a buffer of len bytes for accesses of
@@ -51,23 +61,22 @@ static __device__ __forceinline__ uint32_t jit_index_limit(int64_t len, uint32_t
   return n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
 }
 
-// Warp-aggregated edge hit: lanes of the current group with equal e are
-// merged and their leader adds the group size into the CTA's edge table.
-static __device__ __forceinline__ void jit_cover(const EngineTables* T, uint32_t* hash, uint32_t slot,
-                                          uint32_t e) {
+// Edge hit: nothing to do once the edge is saturated in this CTA's table;
+// otherwise lanes of the current group with equal e are merged and their
+// leader adds the group size.
+static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
+  if (edge_saturated(s_hash, e)) return;
   const uint32_t am = __activemask();
   const uint32_t peers = __match_any_sync(am, e);
   if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
     // first probe inline: the edge is usually already in its home slot
     const uint32_t c = __popc(peers);
     const uint32_t tag = (e + 1u) << kHashTagShift;
-    uint32_t* p = &hash[(e * 2654435761u) >> (32 - 11)];
-    const uint32_t cur = *p;
-    if ((cur & ~kHashCountMask) == tag) {
-      if ((cur & kHashCountMask) < 128u) atomicAdd(p, c);
-    } else {
-      edge_add(hash, *T, slot, e, c);
-    }
+    const uint32_t h = (e * 2654435761u) >> (32 - 11);
+    if ((s_hash[h] & ~kHashCountMask) == tag)
+      edge_hit(s_hash, h, e, c);
+    else
+      edge_add(s_hash, s_T, slot, e, c);
   }
 }
 

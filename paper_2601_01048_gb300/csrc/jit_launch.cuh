@@ -7,17 +7,27 @@
 #ifndef CUFZ_JIT_MIN_CTAS
 #define CUFZ_JIT_MIN_CTAS 4
 #endif
+#ifndef CUFZ_JIT_CTA_THREADS
+#define CUFZ_JIT_CTA_THREADS 256
+#endif
+
+// Copies the launch's engine tables into the CTA's shared copy.
+static __device__ __forceinline__ void jit_stage_tables(const cufz::EngineTables& T) {
+  static_assert(sizeof(cufz::EngineTables) % 4 == 0, "word copy");
+  const uint32_t* src = reinterpret_cast<const uint32_t*>(&T);
+  uint32_t* dst = reinterpret_cast<uint32_t*>(&cufz::s_T);
+  for (uint32_t i = threadIdx.x; i < sizeof(cufz::EngineTables) / 4; i += blockDim.x) dst[i] = src[i];
+  __syncthreads();
+}
 
 // Persistent: CTAs pull work items from the batch until it is drained.
-extern "C" __global__ void __launch_bounds__(256, CUFZ_JIT_MIN_CTAS) cufz_jit_persistent(cufz::EngineTables T,
-                                                                      cufz::BatchHdr* batch) {
+extern "C" __global__ void __launch_bounds__(CUFZ_JIT_CTA_THREADS, CUFZ_JIT_MIN_CTAS)
+    cufz_jit_persistent(cufz::EngineTables T, cufz::BatchHdr* batch) {
   using namespace cufz;
-  __shared__ __align__(16) uint32_t hash[kHashSlots];
-  __shared__ __align__(16) uint8_t sin_raw[kInputSmemBytes];
-  DevInput* sin = reinterpret_cast<DevInput*>(sin_raw);
-  run_items<true, false>(T, batch, 0u, 0u, 0u, hash, nullptr, sin,
+  jit_stage_tables(T);
+  run_items<true, false>(s_T, batch, 0u, 0u, 0u, s_hash, nullptr, &s_in,
                          [&](const DevInput* in, uint32_t g0, uint32_t cnt, bool) -> bool {
-                           return jit_run(in->prog, &T, in, hash, g0, g0 + cnt);
+                           return jit_run(in->prog, g0, g0 + cnt);
                          });
 }
 
@@ -27,12 +37,10 @@ extern "C" __global__ void __launch_bounds__(1024) cufz_jit_plain(cufz::EngineTa
                                                                   cufz::BatchHdr* batch,
                                                                   uint32_t input) {
   using namespace cufz;
-  __shared__ __align__(16) uint32_t hash[kHashSlots];
-  __shared__ __align__(16) uint8_t sin_raw[kInputSmemBytes];
-  DevInput* sin = reinterpret_cast<DevInput*>(sin_raw);
-  run_items<false, false>(T, batch, input, 0u, 0u, hash, nullptr, sin,
+  jit_stage_tables(T);
+  run_items<false, false>(s_T, batch, input, 0u, 0u, s_hash, nullptr, &s_in,
                           [&](const DevInput* in, uint32_t g0, uint32_t cnt, bool) -> bool {
-                            return jit_run(in->prog, &T, in, hash, g0, g0 + cnt);
+                            return jit_run(in->prog, g0, g0 + cnt);
                           });
 }
 #endif

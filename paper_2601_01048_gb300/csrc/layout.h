@@ -31,6 +31,8 @@ constexpr int kBitmapBytes = 65536;
 constexpr int kEdgeCount = 65536;
 constexpr int kHashSlots = 2048;    // per-CTA edge hash table (power of two)
 constexpr int kHashProbes = 8;
+constexpr int kSatWords = kEdgeCount / 32;  // per-CTA bitmap of edges whose count reached 128
+constexpr int kEdgeSmemBytes = (kHashSlots + kSatWords) * 4;  // hash table, then the bitmap
 constexpr uint32_t kLaneBytes = 4;  // one i32 per lane per register
 constexpr uint32_t kRegStride = 32 * kLaneBytes;  // register r of a warp: r * 128 + lane * 4
 

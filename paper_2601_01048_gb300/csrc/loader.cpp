@@ -534,7 +534,7 @@ struct Gen {
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
                   "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1; acc.n_branch++;"
-                  " jit_cover(T, hash, slot, e); }");
+                  " jit_cover(slot, e); }");
   }
 
   static std::string lim_name(int buf, int lw) {
@@ -552,12 +552,14 @@ struct Gen {
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
     line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
-    line(ind + 1, "if (dig) acc.digest += access_hash(th, ordinal, " +
+    line(ind + 1, "if (dig) dsum += access_term(th ^ oc, " +
                       hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) + ", ix);");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
-    line(ind + 1, "acc.n_viol += viol ? 1u : 0u;");
-    line(ind + 1, "if (viol) jit_violation(T, in, acc, bl, tl, ordinal, " + hex32(what) + ", off);");
+    line(ind + 1, "fv = (viol && nv == 0u) ? oc : fv;");
+    line(ind + 1, "nv += viol ? 1u : 0u;");
+    line(ind + 1, "if (viol && rec_open) rec_open = !jit_record(bl, tl, oc * kOrdInv, " +
+                      hex32(what) + ", off);");
     if (o2.opc == B_LD && !o2.value_dead) {
       if (shared) {
         line(ind + 1, r(o2.dst) + " = 0;");
@@ -567,7 +569,7 @@ struct Gen {
                           std::to_string(lw) + "u);");
       }
     }
-    line(ind + 1, "ordinal++;");
+    line(ind + 1, "oc += kOrdMul;");
     line(ind, "}");
   }
 
@@ -651,17 +653,16 @@ struct Gen {
       if (op.kept && (op.opc == B_LD || op.opc == B_ST)) buf_used[op.buf] = true;
     }
     std::string fn = "cufz_prog_" + std::to_string(index);
-    line(0, "__device__ __noinline__ void " + fn +
-                "(const EngineTables* __restrict__ T, const DevInput* __restrict__ in, uint32_t* hash,"
-                " uint32_t g0, uint32_t g_end) {");
-    line(1, "const uint32_t slot = in->slot;");
+    line(0, "__device__ __noinline__ void " + fn + "(uint32_t g0, uint32_t g_end) {");
+    line(1, "const uint32_t slot = s_in.slot;");
     line(1, "LaneAcc acc;");
     line(1, "acc_init(acc);");
-    line(1, "const uint32_t budget = T->iter_budget;");
+    line(1, "const uint32_t budget = s_T.iter_budget;");
+    line(1, "bool rec_open = jit_records_open(slot);");
     line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
     // loop-invariant launch constants are re-read from the CTA's shared copy
     // of the input where used, rather than held in registers for the item
-    line(1, "const volatile DevInput* vin = in;");
+    line(1, "const volatile DevInput* vin = &s_in;");
     std::vector<bool> lim_used(kMaxBufs * 5, false);
     for (const auto& op : ir.ops)
       if (op.kept && (op.opc == B_LD || op.opc == B_ST)) lim_used[op.buf * 5 + log2w(op.width)] = true;
@@ -690,18 +691,26 @@ struct Gen {
     for (int k = 0; k < 4; k++)
       if (sreg_used[12 + k]) line(2, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
     line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
-    line(2, "uint32_t prev = 0, ordinal = 0, back = 0;");
-    line(2, "(void)prev; (void)ordinal; (void)back; (void)th;");
+    // oc = ordinal * kOrdMul (the ordinal is recovered as oc * kOrdInv);
+    // nv = the thread's violations, fv = oc of its first one, dsum = its
+    // digest sum
+    line(2, "uint32_t prev = 0, oc = 0, back = 0, nv = 0, fv = 0, dsum = 0;");
+    line(2, "(void)prev; (void)oc; (void)back; (void)th; (void)nv; (void)fv; (void)dsum;");
     std::string decl;
     for (int v = 0; v < 256; v++)
       if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
     if (!decl.empty()) line(2, decl + ";");
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
-    line(2, "acc.n_acc += ordinal;");
+    line(2, "acc.n_acc += oc * kOrdInv;");
+    line(2, "acc.digest += dsum;");
+    line(2, "if (nv) {");
+    line(3, "acc.n_viol += nv;");
+    line(3, "if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, fv * kOrdInv);");
+    line(2, "}");
     line(1, "}");
     line(1, "__syncwarp();");
-    line(1, "acc_flush(*T, slot, acc);");
+    line(1, "acc_flush(s_T, slot, acc);");
     line(0, "}");
   }
 };

@@ -200,7 +200,7 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
   shape.cta_threads = 256;
   shape.max_regs = P.hdr.n_regs;
   shape.max_prog_bytes = (P.blob_bytes + 15u) & ~15u;
-  const uint32_t smem = kHashSlots * 4 + shape.max_prog_bytes + 576 +
+  const uint32_t smem = kEdgeSmemBytes + shape.max_prog_bytes + 576 +
                         (shape.cta_threads / 32) * shape.max_regs * kRegStride;
   cudaError_t e = cudaSuccess;
   // raise (never lower) the kernel's dynamic shared memory limit

@@ -212,7 +212,7 @@ void harvest(cufz_ctx* c) {
 }
 
 uint32_t smem_for(const LaunchShape& s, uint32_t cta_threads) {
-  return kHashSlots * 4 + s.max_prog_bytes + 576 + (cta_threads / 32) * s.max_regs * kRegStride;
+  return kEdgeSmemBytes + s.max_prog_bytes + 576 + (cta_threads / 32) * s.max_regs * kRegStride;
 }
 
 // Sets the kernels' dynamic shared memory limit to what the persistent shape
@@ -246,17 +246,21 @@ bool use_jit(const cufz_ctx* c) { return (c->cfg.flags & CUFZ_CF_JIT) != 0; }
 // are register-allocated together with the kernel that calls them.
 std::string jit_module_source(const std::vector<std::string>& prog_src,
                               const std::vector<uint8_t>& include, bool plain_kernel,
-                              uint32_t min_ctas) {
-  std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas ? min_ctas : 4) +
+                              uint32_t min_ctas, uint32_t cta_threads) {
+  // the persistent kernel's launch bounds follow the context's CTA size;
+  // at most 2048 resident threads per SM
+  min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : 4u, 2048u / cta_threads));
+  std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas) +
+                    "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) +
                     "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
   for (size_t k = 0; k < prog_src.size(); k++)
     if (include[k]) src += prog_src[k];
-  src += "static __device__ bool jit_run(uint32_t prog, const EngineTables* T, const DevInput* in, "
-         "uint32_t* hash, uint32_t g0, uint32_t g_end) {\n  switch (prog) {\n";
+  src += "static __device__ bool jit_run(uint32_t prog, uint32_t g0, uint32_t g_end) {\n"
+         "  switch (prog) {\n";
   for (size_t k = 0; k < prog_src.size(); k++)
     if (include[k])
       src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
-             "(T, in, hash, g0, g_end); return true;\n";
+             "(g0, g_end); return true;\n";
   src += "    default: return false;\n  }\n}\n}  // namespace cufz\n";
   if (plain_kernel) src += "#define CUFZ_JIT_PLAIN 1\n";
   src += "#include \"jit_launch.cuh\"\n";
@@ -298,10 +302,10 @@ std::unordered_map<std::string, std::vector<char>> g_jit_cache;  // module sourc
 // Compiled image of a module source, cached for the life of the process.
 cufz_status jit_build_image(const std::vector<std::string>& prog_src,
                             const std::vector<uint8_t>& include, bool plain_kernel,
-                            uint32_t min_ctas, bool fast, std::vector<char>* image,
-                            std::string* log) {
-  const std::string src =
-      jit_module_source(prog_src, include, plain_kernel, min_ctas) + (fast ? "//fast\n" : "");
+                            uint32_t min_ctas, uint32_t cta_threads, bool fast,
+                            std::vector<char>* image, std::string* log) {
+  const std::string src = jit_module_source(prog_src, include, plain_kernel, min_ctas, cta_threads) +
+                          (fast ? "//fast\n" : "");
   {
     std::lock_guard<std::mutex> g(g_jit_cache_mu);
     auto it = g_jit_cache.find(src);
@@ -334,7 +338,7 @@ cufz_status jit_compile(cufz_ctx* c) {
   const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
   std::vector<uint8_t> include = c->prog_compiled;
   cufz_status cs = jit_build_image(c->prog_src, include, plain, c->cfg.jit_min_ctas,
-                                   (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &cubin,
+                                   c->shape.cta_threads, (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &cubin,
                                    &c->jit_log);
   if (cs != CUFZ_OK) return cs;
   // wait for work that may still run on the old module
@@ -1105,7 +1109,7 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
   std::vector<char> image;
   std::string lg;
   cufz_status st = jit_build_image(srcs, std::vector<uint8_t>(n, 1),
-                                   (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0,
+                                   (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0, 256,
                                    (flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &image, &lg);
   if (log && log_cap) {
     size_t m = std::min<size_t>(lg.size(), log_cap - 1);
