@@ -258,6 +258,7 @@ static __device__ __noinline__ void finalize_input(const EngineTables& T, const 
     vS->n_ops = 0;
     vS->first_key = ~0ull;
     vS->rec_reserved = 0;
+    vS->rec_listed = 0;
     vS->n_touched = 0;
     vS->items_done = 0;
     vS->flags = 0;

@@ -47,11 +47,33 @@ static __device__ __noinline__ bool jit_record(uint32_t bl, uint32_t tl, uint32_
   return base + k >= cap;
 }
 
-// Whether the input's record area had room when the item started; a lane
-// stops calling jit_record once a reservation comes back full.
+// Records of the compiled path come from a second run of a violating test
+// thread (the record function).  A thread is listed for it while the
+// violations of the threads listed before it are fewer than the record cap,
+// so the listed threads hold min(n_violations, cap) records or more and the
+// record area is filled exactly as a single pass would fill it.
+
+// Whether the input's record list had room when the item started.
 static __device__ __forceinline__ bool jit_records_open(uint32_t slot) {
-  const volatile uint32_t* r = &s_T.slots[slot].rec_reserved;
+  const volatile uint32_t* r = &s_T.slots[slot].rec_listed;
   return *r < s_T.record_cap;
+}
+
+// Adds a finished thread's nv violations to the listed total; returns the
+// total before it (the thread is listed iff that is below the cap).
+static __device__ __forceinline__ uint32_t jit_list_violations(uint32_t slot, uint32_t nv) {
+  return atomicAdd(&s_T.slots[slot].rec_listed, nv);
+}
+
+// Whether a violating thread that is not listed still has to be re-run for
+// its first-violation key: only the lane's first violating thread can hold
+// the lane's minimum key, and none can beat a smaller key already published
+// by a finished item of the input.
+static __device__ __forceinline__ bool jit_first_key_wanted(const LaneAcc& acc, uint32_t slot,
+                                                            uint32_t bl, uint32_t tl) {
+  if (acc.first_key != ~0ull) return false;
+  const volatile unsigned long long* fk = &s_T.slots[slot].first_key;
+  return *fk > first_key_of(bl, tl, 0u);
 }
 
 // Number of in-bounds indices of a buffer of len bytes for accesses of

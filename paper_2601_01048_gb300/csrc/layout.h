@@ -169,7 +169,8 @@ struct SlotState {
   uint32_t n_touched;
   uint32_t items_done;
   uint32_t flags;
-  uint32_t pad[4];
+  uint32_t rec_listed;  // compiled path: violations of threads listed for records
+  uint32_t pad[3];
 };
 static_assert(sizeof(SlotState) == 80, "SlotState size");
 

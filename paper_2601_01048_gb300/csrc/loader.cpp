@@ -458,13 +458,20 @@ void fill_stats(const Ir& ir, int n_in, int regs_alloc, cufz_prog_stats* st) {
 
 
 // ------------------------------------------------------------ code generator
-// Emits one __device__ function running a work item of program `index`: a
-// loop over the item's test threads (one per CUDA thread) whose body is the
-// pruned program as straight-line CUDA.  Program registers become int32
-// locals (all 0 at thread start, as in the program semantics), structured
-// IF/LOOP become C++ if/for, every access is an inline bounds check with
-// constant buffer, width and site, and every branch evaluation an inline AFL
-// edge update with constant LOC values.
+// Emits two __device__ functions for program `index`, both with the pruned
+// program as straight-line CUDA: program registers become int32 locals (all 0
+// at thread start, as in the program semantics), structured IF/LOOP become
+// C++ if/for, and every access is an inline bounds check with constant
+// buffer, width and site.
+//  - cufz_prog_K(g0, g_end) runs a work item (one test thread per CUDA
+//    thread): counts, digest and AFL edges (constant LOC values) inline, and
+//    no record code, so the per-access path is compare-and-count.  A thread
+//    that violated calls the record function at its end while the input's
+//    record area still has room, and the first violating thread of each lane
+//    calls it for the first-violation key.
+//  - cufz_prog_K_rec(g, write) re-runs test thread g with no coverage, digest
+//    or counts: it writes the thread's violation records (if `write`) and
+//    returns the ordinal of its first violation.
 namespace {
 
 struct Gen {
@@ -472,6 +479,7 @@ struct Gen {
   std::string& o;
   int index;
   bool digest_ = true;
+  bool rec_ = false;  // emitting the record function
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -531,6 +539,7 @@ struct Gen {
   }
 
   void cover(int ind, int site, const std::string& cond) {
+    if (rec_) return;
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
                   "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1; acc.n_branch++;"
@@ -551,15 +560,21 @@ struct Gen {
     line(ind, "{");
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
-    line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
-    line(ind + 1, "if (dig) dsum += access_term(th ^ oc, " +
-                      hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) + ", ix);");
+    const bool loads_value = o2.opc == B_LD && !o2.value_dead && !shared;
+    if (rec_ || loads_value)
+      line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
-    line(ind + 1, "fv = (viol && nv == 0u) ? oc : fv;");
-    line(ind + 1, "nv += viol ? 1u : 0u;");
-    line(ind + 1, "if (viol && rec_open) rec_open = !jit_record(bl, tl, oc * kOrdInv, " +
-                      hex32(what) + ", off);");
+    if (rec_) {
+      line(ind + 1, "if (viol) {");
+      line(ind + 2, "if (fo == ~0u) fo = ordinal;");
+      line(ind + 2, "if (write) write = !jit_record(bl, tl, ordinal, " + hex32(what) + ", off);");
+      line(ind + 1, "}");
+    } else {
+      line(ind + 1, "if (dig) dsum += access_term(th ^ oc, " +
+                        hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) + ", ix);");
+      line(ind + 1, "nv += viol ? 1u : 0u;");
+    }
     if (o2.opc == B_LD && !o2.value_dead) {
       if (shared) {
         line(ind + 1, r(o2.dst) + " = 0;");
@@ -569,12 +584,12 @@ struct Gen {
                           std::to_string(lw) + "u);");
       }
     }
-    line(ind + 1, "oc += kOrdMul;");
+    line(ind + 1, rec_ ? "ordinal++;" : "oc += kOrdMul;");
     line(ind, "}");
   }
 
   void range(int ind, int pc, int end) {
-    int k = run_ops(pc, end);
+    int k = rec_ ? 0 : run_ops(pc, end);
     if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
     while (pc < end) {
       const IrOp& o2 = ir.ops[pc];
@@ -611,7 +626,7 @@ struct Gen {
         line(ind + 1, "}");
         line(ind, "}");
         pc = o2.end_pc + 1;
-        int k2 = run_ops(pc, end);
+        int k2 = rec_ ? 0 : run_ops(pc, end);
         if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
         continue;
       } else if (opc == B_LOOP) {
@@ -629,12 +644,13 @@ struct Gen {
         cover(ind + 2, o2.site, c);
         line(ind + 2, "if (!" + c + ") break;");
         range(ind + 2, pc + 1, o2.end_pc);
-        line(ind + 2, "if (++back > budget) { acc.budget_hit = true; goto cufz_done; }");
+        line(ind + 2, rec_ ? "if (++back > budget) goto cufz_done;"
+                           : "if (++back > budget) { acc.budget_hit = true; goto cufz_done; }");
         line(ind + 2, r(o2.dst) + "++;");
         line(ind + 1, "}");
         line(ind, "}");
         pc = o2.end_pc + 1;
-        int k2 = run_ops(pc, end);
+        int k2 = rec_ ? 0 : run_ops(pc, end);
         if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
         continue;
       }
@@ -642,17 +658,63 @@ struct Gen {
     }
   }
 
+  // Decodes test thread g into bl, tl and the used special registers.
+  void thread_setup(int ind, const std::vector<bool>& sreg_used) {
+    line(ind, "const uint32_t bl = udiv(g, vin->mT);");
+    line(ind, "const uint32_t tl = g - bl * vin->T;");
+    if (sreg_used[0] || sreg_used[1] || sreg_used[2]) {
+      line(ind, "const uint32_t q1 = udiv(tl, vin->mBx), tz_ = udiv(tl, vin->mBxy);");
+      line(ind, "const int32_t s_tx = (int32_t)(tl - q1 * vin->Bx), s_ty = (int32_t)(q1 - tz_ * vin->block[1]), s_tz = (int32_t)tz_;");
+    }
+    if (sreg_used[6] || sreg_used[7] || sreg_used[8]) {
+      line(ind, "const uint32_t p1 = udiv(bl, vin->mGx), bz_ = udiv(bl, vin->mGxy);");
+      line(ind, "const int32_t s_bx = (int32_t)(bl - p1 * vin->gx), s_by = (int32_t)(p1 - bz_ * vin->grid[1]), s_bz = (int32_t)bz_;");
+    }
+    for (int k = 0; k < 3; k++) {
+      if (sreg_used[3 + k]) line(ind, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
+      if (sreg_used[9 + k]) line(ind, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)vin->grid[" + std::to_string(k) + "];");
+    }
+    for (int k = 0; k < 4; k++)
+      if (sreg_used[12 + k]) line(ind, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
+  }
+
+  void reg_decls(int ind, const std::vector<bool>& used) {
+    std::string decl;
+    for (int v = 0; v < 256; v++)
+      if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
+    if (!decl.empty()) line(ind, decl + ";");
+  }
+
   void emit() {
-    std::vector<bool> used(ir.nv, false), sreg_used(16, false), buf_used(kMaxBufs, false);
+    std::vector<bool> used(ir.nv, false), sreg_used(16, false);
     int U[4], D[4], nu, nd;
     for (const auto& op : ir.ops) {
       uses_defs(op, false, U, &nu, D, &nd);
       for (int k = 0; k < nu; k++) used[U[k]] = true;
       for (int k = 0; k < nd; k++) used[D[k]] = true;
       if (op.kept && op.opc == B_SREG) sreg_used[op.sreg] = true;
-      if (op.kept && (op.opc == B_LD || op.opc == B_ST)) buf_used[op.buf] = true;
     }
-    std::string fn = "cufz_prog_" + std::to_string(index);
+    const std::string fn = "cufz_prog_" + std::to_string(index);
+
+    // record function: one test thread, records and the first violation
+    rec_ = true;
+    has_loop = false;
+    line(0, "__device__ __noinline__ uint32_t " + fn + "_rec(uint32_t g, bool write) {");
+    line(1, "const uint32_t budget = s_T.iter_budget;");
+    line(1, "const volatile DevInput* vin = &s_in;");
+    line(1, "const volatile uint32_t* lim = vin->lim;");
+    thread_setup(1, sreg_used);
+    line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
+    line(1, "(void)back;");
+    reg_decls(1, used);
+    range(1, 0, (int)ir.ops.size());
+    if (has_loop) line(0, "cufz_done:");
+    line(1, "return fo;");
+    line(0, "}");
+
+    // count function: a work item
+    rec_ = false;
+    has_loop = false;
     line(0, "__device__ __noinline__ void " + fn + "(uint32_t g0, uint32_t g_end) {");
     line(1, "const uint32_t slot = s_in.slot;");
     line(1, "LaneAcc acc;");
@@ -660,53 +722,35 @@ struct Gen {
     line(1, "const uint32_t budget = s_T.iter_budget;");
     line(1, "bool rec_open = jit_records_open(slot);");
     line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
-    // loop-invariant launch constants are re-read from the CTA's shared copy
-    // of the input where used, rather than held in registers for the item
+    // launch constants and index limits are re-read from the CTA's shared
+    // copy of the input where used, rather than held in registers
     line(1, "const volatile DevInput* vin = &s_in;");
-    std::vector<bool> lim_used(kMaxBufs * 5, false);
-    for (const auto& op : ir.ops)
-      if (op.kept && (op.opc == B_LD || op.opc == B_ST)) lim_used[op.buf * 5 + log2w(op.width)] = true;
-    // index limits are re-read from the CTA's shared copy of the input at
-    // each use instead of occupying registers for the whole item
     line(1, "const volatile uint32_t* lim = vin->lim;");
-    bool need_t = sreg_used[0] || sreg_used[1] || sreg_used[2];
-    bool need_b = sreg_used[6] || sreg_used[7] || sreg_used[8];
-
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
-    line(2, "const uint32_t bl = udiv(g, vin->mT);");
-    line(2, "const uint32_t tl = g - bl * vin->T;");
-    if (need_t) {
-      line(2, "const uint32_t q1 = udiv(tl, vin->mBx), tz_ = udiv(tl, vin->mBxy);");
-      line(2, "const int32_t s_tx = (int32_t)(tl - q1 * vin->Bx), s_ty = (int32_t)(q1 - tz_ * vin->block[1]), s_tz = (int32_t)tz_;");
-    }
-    if (need_b) {
-      line(2, "const uint32_t p1 = udiv(bl, vin->mGx), bz_ = udiv(bl, vin->mGxy);");
-      line(2, "const int32_t s_bx = (int32_t)(bl - p1 * vin->gx), s_by = (int32_t)(p1 - bz_ * vin->grid[1]), s_bz = (int32_t)bz_;");
-    }
-    for (int k = 0; k < 3; k++) {
-      if (sreg_used[3 + k]) line(2, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
-      if (sreg_used[9 + k]) line(2, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)vin->grid[" + std::to_string(k) + "];");
-    }
-    for (int k = 0; k < 4; k++)
-      if (sreg_used[12 + k]) line(2, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
+    thread_setup(2, sreg_used);
     line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
-    // oc = ordinal * kOrdMul (the ordinal is recovered as oc * kOrdInv);
-    // nv = the thread's violations, fv = oc of its first one, dsum = its
-    // digest sum
-    line(2, "uint32_t prev = 0, oc = 0, back = 0, nv = 0, fv = 0, dsum = 0;");
-    line(2, "(void)prev; (void)oc; (void)back; (void)th; (void)nv; (void)fv; (void)dsum;");
-    std::string decl;
-    for (int v = 0; v < 256; v++)
-      if (used[v]) decl += (decl.empty() ? "int32_t " : ", ") + r(v) + " = 0";
-    if (!decl.empty()) line(2, decl + ";");
+    // oc = ordinal * kOrdMul (the ordinal is oc * kOrdInv); nv = the
+    // thread's violations; dsum = its digest sum
+    line(2, "uint32_t prev = 0, oc = 0, back = 0, nv = 0, dsum = 0;");
+    line(2, "(void)prev; (void)back; (void)th; (void)dsum;");
+    reg_decls(2, used);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
     line(2, "acc.n_acc += oc * kOrdInv;");
     line(2, "acc.digest += dsum;");
     line(2, "if (nv) {");
     line(3, "acc.n_viol += nv;");
-    line(3, "if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, fv * kOrdInv);");
+    line(3, "bool listed = false;");
+    line(3, "if (rec_open) {");
+    line(4, "const uint32_t old = jit_list_violations(slot, nv);");
+    line(4, "listed = old < s_T.record_cap;");
+    line(4, "rec_open = old + nv < s_T.record_cap;");
+    line(3, "}");
+    line(3, "if (listed || jit_first_key_wanted(acc, slot, bl, tl)) {");
+    line(4, "const uint32_t f = " + fn + "_rec(g, listed);");
+    line(4, "if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, f);");
+    line(3, "}");
     line(2, "}");
     line(1, "}");
     line(1, "__syncwarp();");
