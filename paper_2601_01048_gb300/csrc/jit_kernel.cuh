@@ -102,6 +102,42 @@ static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
   }
 }
 
+// n hits of edge e at once (n may differ between lanes, and be 0): lanes
+// with equal e are merged and their leader adds the sum, clamped to 128
+// (counts only matter up to 128), into the CTA's edge table.
+static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
+  if (n == 0 || edge_saturated(s_hash, e)) return;
+  const uint32_t am = __activemask();
+  const uint32_t peers = __match_any_sync(am, e);
+  uint32_t c = __reduce_add_sync(peers, n < 128u ? n : 128u);
+  if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
+    c = c < 128u ? c : 128u;
+    const uint32_t tag = (e + 1u) << kHashTagShift;
+    const uint32_t h = (e * 2654435761u) >> (32 - 11);
+    if ((s_hash[h] & ~kHashCountMask) == tag)
+      edge_hit(s_hash, h, e, c);
+    else
+      edge_add(s_hash, s_T, slot, e, c);
+  }
+}
+
+// Edges of the head evaluations of one execution of a loop whose body has no
+// branch sites: n_true taken evaluations, then one not taken if the loop ran
+// to its end (not when the iteration budget stopped the thread inside it).
+// Taken evaluations after the first all see prev = lt >> 1, so their edge is
+// the same constant; three table updates replace n_true + 1.
+static __device__ __forceinline__ void jit_loop_cover(uint32_t slot, uint32_t& prev, LaneAcc& acc,
+                                                      uint32_t n_true, bool exited, uint32_t lt,
+                                                      uint32_t lf) {
+  acc.n_branch += n_true + (exited ? 1u : 0u);
+  const uint32_t p_in = prev;
+  jit_cover_n(slot, (lt ^ p_in) & 0xFFFFu, n_true ? 1u : 0u);
+  jit_cover_n(slot, (lt ^ (lt >> 1)) & 0xFFFFu, n_true ? n_true - 1u : 0u);
+  const uint32_t p_exit = n_true ? (lt >> 1) : p_in;
+  jit_cover_n(slot, (lf ^ p_exit) & 0xFFFFu, exited ? 1u : 0u);
+  prev = exited ? (lf >> 1) : p_exit;
+}
+
 // Seeded content of a global buffer (seedx = program seed ^ buf * 0x9E3779B9).
 static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t off, uint32_t lw) {
   const uint32_t word = mix32(seedx ^ (uint32_t)(off >> 2));

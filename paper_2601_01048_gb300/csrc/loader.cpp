@@ -526,6 +526,13 @@ struct Gen {
     return o2.kept && o2.opc != B_SREG && is_value_op(o2.opc);
   }
 
+  // whether ops [pc, end) hold a kept IF or LOOP (a branch site)
+  bool has_branch_sites(int pc, int end) const {
+    for (; pc < end; pc++)
+      if (ir.ops[pc].kept && (ir.ops[pc].opc == B_IF || ir.ops[pc].opc == B_LOOP)) return true;
+    return false;
+  }
+
   // n_ops of the straight-line run starting at pc (up to the next IF/LOOP or end)
   int run_ops(int pc, int end) const {
     int k = 0;
@@ -627,6 +634,31 @@ struct Gen {
         line(ind, "}");
         pc = o2.end_pc + 1;
         int k2 = rec_ ? 0 : run_ops(pc, end);
+        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        continue;
+      } else if (opc == B_LOOP && !rec_ && !has_branch_sites(pc + 1, o2.end_pc)) {
+        // a loop without branch sites in its body: its head edges in
+        // closed form after the loop (or at a budget stop inside it)
+        has_loop = true;
+        const std::string t = "trip" + std::to_string(o2.site), n = "n" + std::to_string(o2.site);
+        const std::string lt = hex32(ir.loc1[o2.site]), lf = hex32(ir.loc0[o2.site]);
+        line(ind, "{");
+        line(ind + 1, "const int32_t " + n + " = " + r(o2.a) + ";");
+        line(ind + 1, "const int32_t " + t + " = " + n + " < 0 ? 0 : (" + n + " > " +
+                          std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + " : " + n + ");");
+        const std::string stop = "stop" + std::to_string(o2.site);
+        line(ind + 1, "bool " + stop + " = false;");
+        line(ind + 1, "#pragma unroll 1");
+        line(ind + 1, "for (" + r(o2.dst) + " = 0; " + r(o2.dst) + " < " + t + "; " + r(o2.dst) + "++) {");
+        range(ind + 2, pc + 1, o2.end_pc);
+        line(ind + 2, "if (++back > budget) { " + stop + " = true; break; }");
+        line(ind + 1, "}");
+        line(ind + 1, "jit_loop_cover(slot, prev, acc, " + stop + " ? (uint32_t)" + r(o2.dst) +
+                          " + 1u : (uint32_t)" + t + ", !" + stop + ", " + lt + ", " + lf + ");");
+        line(ind + 1, "if (" + stop + ") { acc.budget_hit = true; goto cufz_done; }");
+        line(ind, "}");
+        pc = o2.end_pc + 1;
+        int k2 = run_ops(pc, end);
         if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
         continue;
       } else if (opc == B_LOOP) {
