@@ -128,8 +128,9 @@ typedef struct {
   uint64_t n_accesses;   /* executed loads + stores (checked thread-accesses) */
   uint64_t n_violations; /* exact, even when records overflowed */
   uint64_t first_key;    /* min of block_lin<<32 | thread_lin<<22 | min(ordinal, 2^22-1) */
-  uint64_t digest;       /* sum of per-access hashes of (thread, ordinal, site, index)
-                            mod 2^64 (pruning check) */
+  uint64_t digest;       /* sum over test threads of a hash of the thread's
+                            (site, index) access sequence, mod 2^64
+                            (pruning check) */
   uint64_t n_branch;     /* branch evaluations (coverage events) */
   uint64_t n_threads;    /* test threads run */
   uint64_t n_ops;        /* executed program ops, summed over test threads */

@@ -54,13 +54,13 @@
  * Per-input digest of all executed accesses (the pruning check, Sec. 5.2:
  * all memory accesses are preserved exactly):
  *   th = fmix32(block_lin * 0x9E3779B1 + thread_lin)
- *   K  = (site * 0xC2B2AE3D) | 1                (odd: idx * K is a bijection)
- *   m  = th ^ (ordinal * 0x85EBCA77) ^ (idx * K)     (32-bit arithmetic)
- *   h  = (m ^ (m >> 16)) * 0x7FEB352D          (a bijection of m; the first
- *        step of the lowbias32 integer hash, C. Wellons)
- *   S  = sum of h over the thread's accesses, mod 2^32
- *   D  = sum of S over the input's test threads, mod 2^64
+ *   H  = th, then for each access of the thread, in program order:
+ *        H = (H ^ idx) * K + 0x9E3779B9  (32-bit), K = (site * 0xC2B2AE3D) | 1
+ *   D  = sum over the input's test threads of fmix32(H), mod 2^64
  * idx is the access's int32 index; the site fixes buffer, kind and width.
+ * K is odd, so each step is a bijection of H: a thread whose access sequence
+ * differs in one access (site or index), or has one more or fewer, ends with
+ * a different H.
  * ordinal = the number of accesses the thread executed before this one.
  *
  * first_key = min over violations of
@@ -320,7 +320,7 @@ typedef struct {
   int32_t sreg[16];
   int32_t r[256];
   uint32_t block_lin, thread_lin, ordinal, prev_loc, th;
-  uint32_t tsum; /* the thread's digest sum S */
+  uint32_t h; /* the thread's digest state H */
   uint64_t backedges;
   int stopped;
 } orc_ctx;
@@ -355,8 +355,7 @@ static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
   orc_result* res = c->res;
   res->n_accesses++;
   uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 1u;
-  uint32_t m = c->th ^ (c->ordinal * 0x85EBCA77u) ^ ((uint32_t)idx * K);
-  c->tsum += (m ^ (m >> 16)) * 0x7FEB352Du;
+  c->h = (c->h ^ (uint32_t)idx) * K + 0x9E3779B9u;
   int32_t value = 0;
   if (viol) {
     uint64_t ord = c->ordinal < 0x3FFFFFu ? c->ordinal : 0x3FFFFFu;
@@ -552,9 +551,9 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
       c->backedges = 0;
       c->stopped = 0;
       c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
-      c->tsum = 0;
+      c->h = c->th;
       exec_range(c, 0, P->n_ops);
-      res->digest += c->tsum;
+      res->digest += fmix32(c->h);
     }
   }
   res->n_records = (uint32_t)(res->n_violations < rec_cap ? res->n_violations : rec_cap);

@@ -25,16 +25,14 @@ static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   return h;
 }
 
-// Digest of the accesses: per access m = th ^ ordinal * kOrdMul ^ idx * k
-// with k = (site * 0xC2B2AE3D) | 1 (odd, so idx * k is a bijection), term
-// (m ^ m >> 16) * 0x7FEB352D (a bijection of m: the first step of C.
-// Wellons' lowbias32 hash); terms summed mod 2^32 per test thread, thread
-// sums mod 2^64 per input.  `tho` = th ^ ordinal * kOrdMul.
-constexpr uint32_t kOrdMul = 0x85EBCA77u;
-constexpr uint32_t kOrdInv = 0xB6C92F47u;  // kOrdMul * kOrdInv == 1 mod 2^32
-static __device__ __forceinline__ uint32_t access_term(uint32_t tho, uint32_t k, int32_t idx) {
-  const uint32_t m = tho ^ ((uint32_t)idx * k);
-  return (m ^ (m >> 16)) * 0x7FEB352Du;
+// Digest of the accesses: each test thread folds its accesses, in program
+// order, into h (starting at th = mix32(block_lin * 0x9E3779B1 + thread_lin))
+// with h = (h ^ idx) * k + 0x9E3779B9, k = (site * 0xC2B2AE3D) | 1; the input's
+// digest is the sum of mix32(h) over its threads, mod 2^64.  k is odd, so a
+// step is a bijection of h and one changed, added or dropped access changes
+// the thread's h.
+static __device__ __forceinline__ uint32_t access_step(uint32_t h, uint32_t k, int32_t idx) {
+  return (h ^ (uint32_t)idx) * k + 0x9E3779B9u;
 }
 
 // floor(n / d) for n < 2^32 with m = ceil(2^64 / d) (m == 0 means d == 1).

@@ -106,8 +106,8 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
 
     bool act = valid, alive = valid;
     uint32_t stk_act = 0, stk_aux = 0;
-    uint32_t prev = 0, ordinal = 0, back = 0, dsum = 0;
-    const uint32_t th = mix32(bl * 0x9E3779B1u + tl);
+    uint32_t prev = 0, ordinal = 0, back = 0;
+    uint32_t dh = mix32(bl * 0x9E3779B1u + tl);  // digest state of the thread
 
     uint32_t pc = 0;
 #pragma unroll 1
@@ -184,7 +184,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           const bool viol = act && (idx < 0 || off + (int64_t)w > len);
           if (act) {
             acc.n_acc++;
-            if (do_digest) dsum += access_term(th ^ (ordinal * kOrdMul), ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
+            if (do_digest) dh = access_step(dh, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
           }
           const uint32_t vm = __ballot_sync(FULL, viol);
           if (vm) {
@@ -315,7 +315,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
         }
       }
     }
-    acc.digest += dsum;
+    if (valid && do_digest) acc.digest += mix32(dh);
   }
 
   acc_flush(T, slot, acc);

@@ -533,7 +533,8 @@ struct Gen {
     return false;
   }
 
-  // n_ops of the straight-line run starting at pc (up to the next IF/LOOP or end)
+  // ops and accesses of the straight-line run starting at pc (up to the
+  // next IF/LOOP or end)
   int run_ops(int pc, int end) const {
     int k = 0;
     while (pc < end) {
@@ -543,6 +544,23 @@ struct Gen {
       pc++;
     }
     return k;
+  }
+  int run_acc(int pc, int end) const {
+    int k = 0;
+    while (pc < end) {
+      const IrOp& o2 = ir.ops[pc];
+      if (o2.opc == B_IF || o2.opc == B_LOOP) break;
+      if (o2.kept && (o2.opc == B_LD || o2.opc == B_ST)) k++;
+      pc++;
+    }
+    return k;
+  }
+  // the counter increments of the run starting at pc
+  void run_counts(int ind, int pc, int end) {
+    if (rec_) return;
+    const int k = run_ops(pc, end), m = run_acc(pc, end);
+    if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
+    if (m) line(ind, "acc.n_acc += " + std::to_string(m) + "u;");
   }
 
   void cover(int ind, int site, const std::string& cond) {
@@ -578,8 +596,8 @@ struct Gen {
       line(ind + 2, "if (write) write = !jit_record(bl, tl, ordinal, " + hex32(what) + ", off);");
       line(ind + 1, "}");
     } else {
-      line(ind + 1, "if (dig) dsum += access_term(th ^ oc, " +
-                        hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) + ", ix);");
+      line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) +
+                        ", ix);");
       line(ind + 1, "nv += viol ? 1u : 0u;");
     }
     if (o2.opc == B_LD && !o2.value_dead) {
@@ -591,13 +609,12 @@ struct Gen {
                           std::to_string(lw) + "u);");
       }
     }
-    line(ind + 1, rec_ ? "ordinal++;" : "oc += kOrdMul;");
+    if (rec_) line(ind + 1, "ordinal++;");
     line(ind, "}");
   }
 
   void range(int ind, int pc, int end) {
-    int k = rec_ ? 0 : run_ops(pc, end);
-    if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
+    run_counts(ind, pc, end);
     while (pc < end) {
       const IrOp& o2 = ir.ops[pc];
       if (!o2.kept) {
@@ -633,8 +650,7 @@ struct Gen {
         line(ind + 1, "}");
         line(ind, "}");
         pc = o2.end_pc + 1;
-        int k2 = rec_ ? 0 : run_ops(pc, end);
-        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        run_counts(ind, pc, end);
         continue;
       } else if (opc == B_LOOP && !rec_ && !has_branch_sites(pc + 1, o2.end_pc)) {
         // a loop without branch sites in its body: its head edges in
@@ -658,8 +674,7 @@ struct Gen {
         line(ind + 1, "if (" + stop + ") { acc.budget_hit = true; goto cufz_done; }");
         line(ind, "}");
         pc = o2.end_pc + 1;
-        int k2 = run_ops(pc, end);
-        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        run_counts(ind, pc, end);
         continue;
       } else if (opc == B_LOOP) {
         has_loop = true;
@@ -682,8 +697,7 @@ struct Gen {
         line(ind + 1, "}");
         line(ind, "}");
         pc = o2.end_pc + 1;
-        int k2 = rec_ ? 0 : run_ops(pc, end);
-        if (k2) line(ind, "acc.n_ops += " + std::to_string(k2) + "u;");
+        run_counts(ind, pc, end);
         continue;
       }
       pc++;
@@ -761,16 +775,14 @@ struct Gen {
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
     thread_setup(2, sreg_used);
-    line(2, "const uint32_t th = mix32(bl * 0x9E3779B1u + tl);");
-    // oc = ordinal * kOrdMul (the ordinal is oc * kOrdInv); nv = the
-    // thread's violations; dsum = its digest sum
-    line(2, "uint32_t prev = 0, oc = 0, back = 0, nv = 0, dsum = 0;");
-    line(2, "(void)prev; (void)back; (void)th; (void)dsum;");
+    // dh = the thread's digest state, nv = its violations
+    line(2, "uint32_t dh = dig ? mix32(bl * 0x9E3779B1u + tl) : 0u;");
+    line(2, "uint32_t prev = 0, back = 0, nv = 0;");
+    line(2, "(void)prev; (void)back; (void)dh;");
     reg_decls(2, used);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
-    line(2, "acc.n_acc += oc * kOrdInv;");
-    line(2, "acc.digest += dsum;");
+    line(2, "if (dig) acc.digest += mix32(dh);");
     line(2, "if (nv) {");
     line(3, "acc.n_viol += nv;");
     line(3, "bool listed = false;");

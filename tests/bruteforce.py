@@ -127,8 +127,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
 
     def run_thread(bl, tl, sregs):
         regs = [0] * max(P["n_regs"], 1)
-        t = dict(ordinal=0, prev=0, back=0, stop=False, dsum=0)
         th = murmur_fmix32((bl * 0x9E3779B1 + tl) & M32)
+        t = dict(ordinal=0, prev=0, back=0, stop=False, h=th)
 
         def edge(site, out):
             cur = P["loc"][site][out]
@@ -141,8 +141,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
             off = regs[a] * w
             bad = off < 0 or off + w > lens[buf]
             k = ((site * 0xC2B2AE3D) & M32) | 1
-            m = th ^ ((t["ordinal"] * 0x85EBCA77) & M32) ^ ((regs[a] * k) & M32)
-            t["dsum"] = (t["dsum"] + (m ^ (m >> 16)) * 0x7FEB352D) & M32
+            t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
             st["n_accesses"] += 1
             val = 0
             if bad:
@@ -201,7 +200,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                         regs[ctr] += 1
 
         run(P["body"])
-        st["digest"] = (st["digest"] + t["dsum"]) & M64
+        st["digest"] = (st["digest"] + murmur_fmix32(t["h"])) & M64
 
     args = [s32(v) for v in inp["args"]]
     for bz in range(g[2]):

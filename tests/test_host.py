@@ -165,7 +165,7 @@ def test_generated_code_compiles_for_sm103a(which):
 def test_generated_code_shape():
     src = B.cufz_program_cuda(gen.c1_program())
     assert "cufz_prog_0" in src and "jit_record" in src and "jit_cover" in src
-    assert src.count("oc += kOrdMul") == 3             # three checked accesses
+    assert src.count("dh = access_step(") == 3         # three checked accesses
     assert "r11" not in src                            # the pruned sum x + y is gone
     full = B.cufz_program_cuda(gen.c1_program(), B.CF_NO_PRUNE)
     assert "r11 =" in full
