@@ -342,7 +342,7 @@ def run_engine(args, rank, world, local, pg):
             "engine": ("programs compiled to sm_103a at load or interpreted, chosen per program "
                        "by the autotuner" if args.path == "jit" else "bytecode interpreter"),
             "cta_threads": int(st.cta_threads),
-            "jit_min_ctas": args.jit_min_ctas or 4,
+            "jit_min_ctas": args.jit_min_ctas or 3,
             "programs_compiled": tuned,
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),

@@ -102,7 +102,7 @@ typedef struct {
   uint32_t cta_threads;  /* threads per CTA of the persistent kernel (64..1024) */
   uint32_t n_lanes;      /* batches that may overlap on the device (1..8) */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM (0 = from occupancy) */
-  uint32_t jit_min_ctas; /* compiled path: CTAs per SM its registers must allow (0 = 4) */
+  uint32_t jit_min_ctas; /* compiled path: CTAs per SM its registers must allow (0 = 3) */
   uint32_t reserved;
 } cufz_config;
 

@@ -68,12 +68,16 @@ static __device__ __forceinline__ uint32_t jit_list_violations(uint32_t slot, ui
 // Whether a violating thread that is not listed still has to be re-run for
 // its first-violation key: only the lane's first violating thread can hold
 // the lane's minimum key, and none can beat a smaller key already published
-// by a finished item of the input.
-static __device__ __forceinline__ bool jit_first_key_wanted(const LaneAcc& acc, uint32_t slot,
+// by a finished item of the input (the lane then takes that key, which
+// leaves the input's minimum unchanged and ends the checks).
+static __device__ __forceinline__ bool jit_first_key_wanted(LaneAcc& acc, uint32_t slot,
                                                             uint32_t bl, uint32_t tl) {
   if (acc.first_key != ~0ull) return false;
   const volatile unsigned long long* fk = &s_T.slots[slot].first_key;
-  return *fk > first_key_of(bl, tl, 0u);
+  const unsigned long long published = *fk;
+  if (published > first_key_of(bl, tl, 0u)) return true;
+  acc.first_key = published;
+  return false;
 }
 
 // Number of in-bounds indices of a buffer of len bytes for accesses of

@@ -5,7 +5,7 @@
 #include "device_common.cuh"
 
 #ifndef CUFZ_JIT_MIN_CTAS
-#define CUFZ_JIT_MIN_CTAS 4
+#define CUFZ_JIT_MIN_CTAS 3
 #endif
 #ifndef CUFZ_JIT_CTA_THREADS
 #define CUFZ_JIT_CTA_THREADS 256

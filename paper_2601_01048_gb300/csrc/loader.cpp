@@ -768,10 +768,11 @@ struct Gen {
     line(1, "const uint32_t budget = s_T.iter_budget;");
     line(1, "bool rec_open = jit_records_open(slot);");
     line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
-    // launch constants and index limits are re-read from the CTA's shared
-    // copy of the input where used, rather than held in registers
+    // launch constants are re-read from the CTA's shared copy of the input
+    // where used rather than held in registers; the index limits are plain
+    // shared loads the compiler may keep or reload
     line(1, "const volatile DevInput* vin = &s_in;");
-    line(1, "const volatile uint32_t* lim = vin->lim;");
+    line(1, "const uint32_t* lim = s_in.lim;");
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
     thread_setup(2, sreg_used);

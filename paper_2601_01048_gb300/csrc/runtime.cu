@@ -36,6 +36,9 @@ constexpr uint64_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
 constexpr uint32_t kCompileMaxBranchSites = 32;
 constexpr double kAutotuneMargin = 1.25;  // the other path must be 25% faster
+// resident CTAs per SM the compiled kernel's registers must allow when the
+// config leaves it open: 3 x 256 threads gives it 85 registers a thread
+constexpr uint32_t kJitMinCtasDefault = 3;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -249,7 +252,7 @@ std::string jit_module_source(const std::vector<std::string>& prog_src,
                               uint32_t min_ctas, uint32_t cta_threads) {
   // the persistent kernel's launch bounds follow the context's CTA size;
   // at most 2048 resident threads per SM
-  min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : 4u, 2048u / cta_threads));
+  min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : kJitMinCtasDefault, 2048u / cta_threads));
   std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas) +
                     "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) +
                     "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
