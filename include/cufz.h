@@ -294,14 +294,14 @@ cufz_status cufz_compile_programs(cufz_ctx* ctx, char* log, uint32_t log_cap);
 /* Chooses how a program runs when CUFZ_CF_JIT is set: compiled (1) or by the
  * bytecode interpreter (0).  A batch runs its compiled programs' work items
  * and its interpreted programs' work items as two persistent launches.
- * The default at load is compiled unless the program has more than 32
- * branch sites (divergent branch-heavy code outgrows the instruction cache
- * when compiled). */
+ * The default at load is compiled. */
 cufz_status cufz_set_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t compiled);
 cufz_status cufz_get_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t* compiled);
 
 /* Autotuner: for every program in the sample, times the sample's inputs of
- * that program run compiled and interpreted (best of three each) and moves
+ * that program run compiled and interpreted (best of three each; the sample
+ * is repeated up to 2^24 test threads, at most 2048 inputs, so that the
+ * timing measures throughput rather than launch costs) and moves
  * the program off its load-time path only if the other is at least 25%
  * faster.  Needs an idle context; the sample's results are discarded.
  * *n_compiled receives the number of programs left on the compiled path. */

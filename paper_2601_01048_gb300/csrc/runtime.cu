@@ -34,8 +34,9 @@ constexpr uint32_t kMaxLanes = 8;
 constexpr uint64_t kProgAreaBytes = 8ull << 20;
 constexpr uint64_t kAlign = 256;
 constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
-constexpr uint32_t kCompileMaxBranchSites = 32;
 constexpr double kAutotuneMargin = 1.25;  // the other path must be 25% faster
+constexpr uint64_t kAutotuneMinThreads = 1ull << 24;  // test threads timed per program and path
+constexpr size_t kAutotuneMaxInputs = 2048;
 // resident CTAs per SM the compiled kernel's registers must allow when the
 // config leaves it open: 3 x 256 threads gives it 85 registers a thread
 constexpr uint32_t kJitMinCtasDefault = 3;
@@ -725,10 +726,10 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     return st;
   }
   c->prog_src.push_back(fsrc);
-  // default path: compiled, unless the program is branch-heavy (its compiled
-  // form then outgrows the instruction cache when lanes diverge); the
-  // autotuner measures and can override
-  c->prog_compiled.push_back(P.stats.n_branch_sites <= kCompileMaxBranchSites ? 1 : 0);
+  // default path: compiled (measured faster than the interpreter on every
+  // workload family here, branch-heavy ones included); the autotuner
+  // measures and can override
+  c->prog_compiled.push_back(1);
   c->prog_used = align_up(c->prog_used + P.blob_bytes, 16);
   if (stats) *stats = P.stats;
   *program_id = (uint32_t)c->progs.size();
@@ -1236,6 +1237,20 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   cufz_get_stats(c, &saved);
   std::unordered_map<uint32_t, std::vector<cufz_input>> by_prog;
   for (uint32_t i = 0; i < n; i++) by_prog[sample[i].program_id].push_back(sample[i]);
+  // a few small inputs measure launch and finalize costs, not the paths:
+  // repeat each program's sample until it fills the GPU many times over
+  for (auto& kv : by_prog) {
+    std::vector<cufz_input>& v = kv.second;
+    uint64_t threads = 0;
+    for (const cufz_input& in : v)
+      threads += (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * in.block[0] * in.block[1] * in.block[2];
+    const size_t n0 = v.size();
+    for (size_t k = 0; threads && threads < kAutotuneMinThreads && v.size() < kAutotuneMaxInputs; k++) {
+      const cufz_input& in = v[k % n0];
+      threads += (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * in.block[0] * in.block[1] * in.block[2];
+      v.push_back(in);
+    }
+  }
   for (auto& kv : by_prog) {
     const uint32_t p = kv.first;
     if (p >= c->progs.size()) continue;

@@ -276,9 +276,9 @@ def test_int32_peak_probe(B):
 
 def test_mixed_paths_and_autotune(B, orc):
     """Compiled and interpreted programs in one batch (config-5 style mix of
-    1D guarded, random 2D and branch-heavy programs): the default split, every
-    program forced to each path, and the autotuner's choice all agree with
-    the oracle."""
+    1D guarded, random 2D and branch-heavy programs): the default (all
+    compiled), an alternating split, every program interpreted, and the
+    autotuner's choice all agree with the oracle."""
     progs = gen.c3_programs()[:4] + gen.c2_programs()[:4] + gen.c4_programs()[:4]
     c3 = gen.c3_inputs(24, seed=5, max_blocks=16, max_threads=300)
     c3["program_id"] %= 4
@@ -293,11 +293,13 @@ def test_mixed_paths_and_autotune(B, orc):
         for p in progs:
             E.load(p)
         default = [B.cufz_get_program_path(E.ctx, k) for k in range(len(progs))]
-        assert any(default) and not all(default)          # branch-heavy ones interpreted
+        assert all(default)
         runs = [E.run(inputs)]
-        for forced in (True, False):
+        for split in ((lambda k: k % 2 == 0), (lambda k: False)):
             for k in range(len(progs)):
-                B.cufz_set_program_path(E.ctx, k, forced)
+                B.cufz_set_program_path(E.ctx, k, split(k))
+            assert [B.cufz_get_program_path(E.ctx, k) for k in range(len(progs))] == \
+                [split(k) for k in range(len(progs))]
             runs.append(E.run(inputs))
         n_comp = B.cufz_autotune(E.ctx, inputs[::3])
         assert 0 <= n_comp <= len(progs)
