@@ -67,8 +67,9 @@ static __device__ __forceinline__ void edge_global_add(const EngineTables& T, ui
 // The CTA's edge state in shared memory: a hash table of kHashSlots entries
 // (e + 1) << 15 | count, followed by a bitmap of the edges whose count in
 // the table reached 128 (their AFL bucket can no longer change, so later hits
-// are skipped).  Counts saturate near 128: at most 127 + 32 * 32 < 2^15 with
-// every warp adding at once.
+// are skipped).  Counts saturate near 128: a count is added to only while it
+// is below 128, by at most one add of <= 128 per warp or of 1 per thread at
+// a time, so it stays below 127 + 1024 * 128 / 32 + 1024 < 2^15.
 static __device__ __forceinline__ bool edge_saturated(const uint32_t* hash, uint32_t e) {
   return (hash[kHashSlots + (e >> 5)] >> (e & 31u)) & 1u;
 }

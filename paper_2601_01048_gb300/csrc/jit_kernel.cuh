@@ -87,30 +87,12 @@ static __device__ __forceinline__ uint32_t jit_index_limit(int64_t len, uint32_t
   return n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
 }
 
-// Edge hit: nothing to do once the edge is saturated in this CTA's table;
-// otherwise lanes of the current group with equal e are merged and their
-// leader adds the group size.
-static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
-  if (edge_saturated(s_hash, e)) return;
-  const uint32_t am = __activemask();
-  const uint32_t peers = __match_any_sync(am, e);
-  if ((threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1)) {
-    // first probe inline: the edge is usually already in its home slot
-    const uint32_t c = __popc(peers);
-    const uint32_t tag = (e + 1u) << kHashTagShift;
-    const uint32_t h = (e * 2654435761u) >> (32 - 11);
-    if ((s_hash[h] & ~kHashCountMask) == tag)
-      edge_hit(s_hash, h, e, c);
-    else
-      edge_add(s_hash, s_T, slot, e, c);
-  }
-}
-
-// n hits of edge e at once (n may differ between lanes, and be 0): lanes
-// with equal e are merged and their leader adds the sum, clamped to 128
-// (counts only matter up to 128), into the CTA's edge table.
-static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
-  if (n == 0 || edge_saturated(s_hash, e)) return;
+// Edge update for c hits of e by the calling group of lanes, taken only when
+// e is not yet saturated in this CTA's table: lanes with equal e are merged
+// (__match_any_sync) and their leader adds the group's hits, clamped to 128
+// (counts only matter up to 128).  Out of line: it is rare after the first
+// hits of each edge, and one copy keeps every site's inline code small.
+static __device__ __noinline__ void jit_cover_slow(uint32_t slot, uint32_t e, uint32_t n) {
   const uint32_t am = __activemask();
   const uint32_t peers = __match_any_sync(am, e);
   uint32_t c = __reduce_add_sync(peers, n < 128u ? n : 128u);
@@ -123,6 +105,30 @@ static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, ui
     else
       edge_add(s_hash, s_T, slot, e, c);
   }
+}
+
+// One hit of edge e.  Nothing to do once the edge is saturated in this CTA's
+// table, the common case.  Otherwise the lane adds its hit at the edge's home
+// slot itself (inserting the edge there if the slot is empty); only when
+// another edge holds the home slot does it take the out-of-line path.
+static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
+  if (edge_saturated(s_hash, e)) return;
+  const uint32_t tag = (e + 1u) << kHashTagShift;
+  const uint32_t h = (e * 2654435761u) >> (32 - 11);
+  uint32_t v = s_hash[h];
+  if (v == 0) {
+    v = atomicCAS(&s_hash[h], 0u, tag | 1u);
+    if (v == 0) return;
+  }
+  if ((v & ~kHashCountMask) == tag)
+    edge_hit(s_hash, h, e, 1u);
+  else
+    jit_cover_slow(slot, e, 1u);
+}
+
+// n hits of edge e at once (n may differ between lanes, and be 0).
+static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
+  if (n != 0 && !edge_saturated(s_hash, e)) jit_cover_slow(slot, e, n);
 }
 
 // Edges of the head evaluations of one execution of a loop whose body has no
