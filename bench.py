@@ -11,12 +11,14 @@ inputs, run as one persistent launch in a CUDA graph.
 Prints one JSON line (rank 0): checked thread-accesses per second, timed with
 CUDA events on the engine's stream (value) and end to end through the C ABI
 with host input records and host result records (e2e), with the roofline of
-the interpreter kernel against the INT32 issue rate and the CPU oracle's rate
-on a bounded sample.  `--impl reference` times the CPU oracle instead.
+the dominant kernel (the compiled-program kernel) against the INT32 issue
+rate and the CPU oracle's rate on a bounded sample.  `--impl reference` times
+the CPU oracle instead.
 """
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -36,6 +38,32 @@ UNIT = "checked accesses/s"
 # 32 lanes per clock, at the maximum SM clock (MEASURED_PEAKS sm_max_mhz).
 N_SM_GB300 = 152
 LANES_PER_SM = 128
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
+# the dominant kernel on a whole workload, from one ncu capture (the command
+# is in profiles/), keyed by the hash of the compiled-path sources it was
+# taken on: once those change the figure no longer applies and is reported
+# as null.
+TRAFFIC_SOURCES = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h",
+                   "loader.cpp", "runtime.cu")
+TRAFFIC_BYTES: dict[str, tuple[str, int]] = {}
+
+
+def kernel_sources_sha() -> str:
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_2601_01048_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(args, per_step: int, n_all: int):
+    """DRAM bytes per launch if captured for this workload and these sources."""
+    entry = TRAFFIC_BYTES.get(args.workload)
+    if entry is None or per_step != n_all or args.plain or args.path != "jit":
+        return None
+    return entry[1] if entry[0] == kernel_sources_sha() else None
+
+
 # algorithmic integer ops per checked access and per branch evaluation
 OPS_PER_ACCESS = 5
 OPS_PER_BRANCH = 4
@@ -360,7 +388,8 @@ def run_engine(args, rank, world, local, pg):
             "peak": peak_ops / 1e12,
             "unit": "Tops/s (int32 lane-ops)",
             "frac": achieved / peak_ops,
-            "traffic": None,
+            "traffic": measured_traffic(args, per_step, n_all),
+            "kernel_sources_sha": kernel_sources_sha(),
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
             "alg_ops_per_step": alg_ops // max(args.steps, 1),
             "measured_int32_peak": measured_peak / 1e12 if measured_peak else None,

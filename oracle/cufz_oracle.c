@@ -53,10 +53,10 @@
  *
  * Per-input digest of all executed accesses (the pruning check, Sec. 5.2:
  * all memory accesses are preserved exactly):
- *   th = fmix32(block_lin * 0x9E3779B1 + thread_lin)
- *   H  = th, then for each access of the thread, in program order:
+ *   H  = block_lin * 0x9E3779B1 + thread_lin (32-bit), then for each access
+ *        of the thread, in program order:
  *        H = (H ^ idx) * K + 0x9E3779B9  (32-bit), K = (site * 0xC2B2AE3D) | 1
- *   D  = sum over the input's test threads of fmix32(H), mod 2^64
+ *   D  = sum over the input's test threads of H, mod 2^64
  * idx is the access's int32 index; the site fixes buffer, kind and width.
  * K is odd, so each step is a bijection of H: a thread whose access sequence
  * differs in one access (site or index), or has one more or fewer, ends with
@@ -551,9 +551,9 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
       c->backedges = 0;
       c->stopped = 0;
       c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
-      c->h = c->th;
+      c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
       exec_range(c, 0, P->n_ops);
-      res->digest += fmix32(c->h);
+      res->digest += c->h;
     }
   }
   res->n_records = (uint32_t)(res->n_violations < rec_cap ? res->n_violations : rec_cap);

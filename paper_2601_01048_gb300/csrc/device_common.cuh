@@ -26,11 +26,11 @@ static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 }
 
 // Digest of the accesses: each test thread folds its accesses, in program
-// order, into h (starting at th = mix32(block_lin * 0x9E3779B1 + thread_lin))
-// with h = (h ^ idx) * k + 0x9E3779B9, k = (site * 0xC2B2AE3D) | 1; the input's
-// digest is the sum of mix32(h) over its threads, mod 2^64.  k is odd, so a
-// step is a bijection of h and one changed, added or dropped access changes
-// the thread's h.
+// order, into h (starting at block_lin * 0x9E3779B1 + thread_lin) with
+// h = (h ^ idx) * k + 0x9E3779B9, k = (site * 0xC2B2AE3D) | 1; the input's
+// digest is the sum of the threads' h, mod 2^64.  k is odd, so a step is a
+// bijection of h and one changed, added or dropped access changes the
+// thread's h.
 static __device__ __forceinline__ uint32_t access_step(uint32_t h, uint32_t k, int32_t idx) {
   return (h ^ (uint32_t)idx) * k + 0x9E3779B9u;
 }

@@ -107,7 +107,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
     bool act = valid, alive = valid;
     uint32_t stk_act = 0, stk_aux = 0;
     uint32_t prev = 0, ordinal = 0, back = 0;
-    uint32_t dh = mix32(bl * 0x9E3779B1u + tl);  // digest state of the thread
+    uint32_t dh = bl * 0x9E3779B1u + tl;  // digest state of the thread
 
     uint32_t pc = 0;
 #pragma unroll 1
@@ -315,7 +315,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
         }
       }
     }
-    if (valid && do_digest) acc.digest += mix32(dh);
+    if (valid && do_digest) acc.digest += dh;
   }
 
   acc_flush(T, slot, acc);

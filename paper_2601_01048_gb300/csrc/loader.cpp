@@ -704,17 +704,26 @@ struct Gen {
     }
   }
 
-  // Decodes test thread g into bl, tl and the used special registers.
+  // Decodes test thread g into bl, tl and the used special registers, with
+  // only the divisions those need: x = lin % n_x, y = (lin / n_x) % n_y,
+  // z = lin / (n_x * n_y) for the thread (tl) and the block (bl).
   void thread_setup(int ind, const std::vector<bool>& sreg_used) {
     line(ind, "const uint32_t bl = udiv(g, vin->mT);");
     line(ind, "const uint32_t tl = g - bl * vin->T;");
-    if (sreg_used[0] || sreg_used[1] || sreg_used[2]) {
-      line(ind, "const uint32_t q1 = udiv(tl, vin->mBx), tz_ = udiv(tl, vin->mBxy);");
-      line(ind, "const int32_t s_tx = (int32_t)(tl - q1 * vin->Bx), s_ty = (int32_t)(q1 - tz_ * vin->block[1]), s_tz = (int32_t)tz_;");
-    }
-    if (sreg_used[6] || sreg_used[7] || sreg_used[8]) {
-      line(ind, "const uint32_t p1 = udiv(bl, vin->mGx), bz_ = udiv(bl, vin->mGxy);");
-      line(ind, "const int32_t s_bx = (int32_t)(bl - p1 * vin->gx), s_by = (int32_t)(p1 - bz_ * vin->grid[1]), s_bz = (int32_t)bz_;");
+    const char* lin[2] = {"tl", "bl"};
+    const char* m1[2] = {"vin->mBx", "vin->mGx"};
+    const char* m2[2] = {"vin->mBxy", "vin->mGxy"};
+    const char* n1[2] = {"vin->Bx", "vin->gx"};
+    const char* ny[2] = {"vin->block[1]", "vin->grid[1]"};
+    const char* nm[2][3] = {{"s_tx", "s_ty", "s_tz"}, {"s_bx", "s_by", "s_bz"}};
+    for (int k = 0; k < 2; k++) {
+      const bool ux = sreg_used[k * 6 + 0], uy = sreg_used[k * 6 + 1], uz = sreg_used[k * 6 + 2];
+      const std::string q = std::string("q") + lin[k], z = std::string("z") + lin[k];
+      if (ux || uy) line(ind, "const uint32_t " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");");
+      if (uy || uz) line(ind, "const uint32_t " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");");
+      if (ux) line(ind, std::string("const int32_t ") + nm[k][0] + " = (int32_t)(" + lin[k] + " - " + q + " * " + n1[k] + ");");
+      if (uy) line(ind, std::string("const int32_t ") + nm[k][1] + " = (int32_t)(" + q + " - " + z + " * " + ny[k] + ");");
+      if (uz) line(ind, std::string("const int32_t ") + nm[k][2] + " = (int32_t)" + z + ";");
     }
     for (int k = 0; k < 3; k++) {
       if (sreg_used[3 + k]) line(ind, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
@@ -747,7 +756,7 @@ struct Gen {
     has_loop = false;
     line(0, "__device__ __noinline__ uint32_t " + fn + "_rec(uint32_t g, bool write) {");
     line(1, "const uint32_t budget = s_T.iter_budget;");
-    line(1, "const volatile DevInput* vin = &s_in;");
+    line(1, "const DevInput* vin = &s_in;");
     line(1, "const volatile uint32_t* lim = vin->lim;");
     thread_setup(1, sreg_used);
     line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
@@ -768,22 +777,21 @@ struct Gen {
     line(1, "const uint32_t budget = s_T.iter_budget;");
     line(1, "bool rec_open = jit_records_open(slot);");
     line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
-    // launch constants are re-read from the CTA's shared copy of the input
-    // where used rather than held in registers; the index limits are plain
-    // shared loads the compiler may keep or reload
-    line(1, "const volatile DevInput* vin = &s_in;");
+    // launch constants and index limits are plain loads from the CTA's
+    // shared copy of the input, which the compiler may keep or reload
+    line(1, "const DevInput* vin = &s_in;");
     line(1, "const uint32_t* lim = s_in.lim;");
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
     thread_setup(2, sreg_used);
     // dh = the thread's digest state, nv = its violations
-    line(2, "uint32_t dh = dig ? mix32(bl * 0x9E3779B1u + tl) : 0u;");
+    line(2, "uint32_t dh = bl * 0x9E3779B1u + tl;");
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
     reg_decls(2, used);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
-    line(2, "if (dig) acc.digest += mix32(dh);");
+    line(2, "if (dig) acc.digest += dh;");
     line(2, "if (nv) {");
     line(3, "acc.n_viol += nv;");
     line(3, "bool listed = false;");

@@ -127,8 +127,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
 
     def run_thread(bl, tl, sregs):
         regs = [0] * max(P["n_regs"], 1)
-        th = murmur_fmix32((bl * 0x9E3779B1 + tl) & M32)
-        t = dict(ordinal=0, prev=0, back=0, stop=False, h=th)
+        t = dict(ordinal=0, prev=0, back=0, stop=False, h=(bl * 0x9E3779B1 + tl) & M32)
 
         def edge(site, out):
             cur = P["loc"][site][out]
@@ -200,7 +199,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                         regs[ctr] += 1
 
         run(P["body"])
-        st["digest"] = (st["digest"] + murmur_fmix32(t["h"])) & M64
+        st["digest"] = (st["digest"] + t["h"]) & M64
 
     args = [s32(v) for v in inp["args"]]
     for bz in range(g[2]):
