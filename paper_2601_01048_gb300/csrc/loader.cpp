@@ -706,11 +706,20 @@ struct Gen {
 
   // Decodes test thread g into bl, tl and the used special registers, with
   // only the divisions those need: x = lin % n_x, y = (lin / n_x) % n_y,
-  // z = lin / (n_x * n_y) for the thread (tl) and the block (bl).
-  void thread_setup(int ind, const std::vector<bool>& sreg_used) {
-    line(ind, "const uint32_t bl = udiv(g, vin->mT);");
-    line(ind, "const uint32_t tl = g - bl * vin->T;");
+  // z = lin / (n_x * n_y) for the thread (tl) and the block (bl).  With
+  // `stepped` (the work-item loop), bl and tl are kept across the loop's
+  // steps when a block has at least as many threads as the CTA (they then
+  // wrap at most once per step), and the divisions for a 1D block (b1) or
+  // 1D grid (g1) are skipped: their quotients are 0.
+  void thread_setup(int ind, const std::vector<bool>& sreg_used, bool stepped) {
+    if (stepped) {
+      line(ind, "if (!inc) { bl = udiv(g, vin->mT); tl = g - bl * vin->T; }");
+    } else {
+      line(ind, "const uint32_t bl = udiv(g, vin->mT);");
+      line(ind, "const uint32_t tl = g - bl * vin->T;");
+    }
     const char* lin[2] = {"tl", "bl"};
+    const char* one[2] = {"b1", "g1"};
     const char* m1[2] = {"vin->mBx", "vin->mGx"};
     const char* m2[2] = {"vin->mBxy", "vin->mGxy"};
     const char* n1[2] = {"vin->Bx", "vin->gx"};
@@ -719,8 +728,19 @@ struct Gen {
     for (int k = 0; k < 2; k++) {
       const bool ux = sreg_used[k * 6 + 0], uy = sreg_used[k * 6 + 1], uz = sreg_used[k * 6 + 2];
       const std::string q = std::string("q") + lin[k], z = std::string("z") + lin[k];
-      if (ux || uy) line(ind, "const uint32_t " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");");
-      if (uy || uz) line(ind, "const uint32_t " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");");
+      if (stepped) {
+        if (ux || uy) line(ind, "uint32_t " + q + " = 0;");
+        if (uy || uz) line(ind, "uint32_t " + z + " = 0;");
+        if (ux || uy || uz) {
+          std::string t = std::string("if (!") + one[k] + ") {";
+          if (ux || uy) t += " " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");";
+          if (uy || uz) t += " " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");";
+          line(ind, t + " }");
+        }
+      } else {
+        if (ux || uy) line(ind, "const uint32_t " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");");
+        if (uy || uz) line(ind, "const uint32_t " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");");
+      }
       if (ux) line(ind, std::string("const int32_t ") + nm[k][0] + " = (int32_t)(" + lin[k] + " - " + q + " * " + n1[k] + ");");
       if (uy) line(ind, std::string("const int32_t ") + nm[k][1] + " = (int32_t)(" + q + " - " + z + " * " + ny[k] + ");");
       if (uz) line(ind, std::string("const int32_t ") + nm[k][2] + " = (int32_t)" + z + ";");
@@ -757,8 +777,8 @@ struct Gen {
     line(0, "__device__ __noinline__ uint32_t " + fn + "_rec(uint32_t g, bool write) {");
     line(1, "const uint32_t budget = s_T.iter_budget;");
     line(1, "const DevInput* vin = &s_in;");
-    line(1, "const volatile uint32_t* lim = vin->lim;");
-    thread_setup(1, sreg_used);
+    line(1, "const uint32_t* lim = vin->lim;");
+    thread_setup(1, sreg_used, false);
     line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
     line(1, "(void)back;");
     reg_decls(1, used);
@@ -781,9 +801,15 @@ struct Gen {
     // shared copy of the input, which the compiler may keep or reload
     line(1, "const DevInput* vin = &s_in;");
     line(1, "const uint32_t* lim = s_in.lim;");
+    line(1, "const bool inc = vin->T >= blockDim.x;");
+    line(1, "const bool b1 = vin->block[1] == 1u && vin->block[2] == 1u;");
+    line(1, "const bool g1 = vin->grid[1] == 1u && vin->grid[2] == 1u;");
+    line(1, "(void)b1; (void)g1;");
+    line(1, "uint32_t bl = 0, tl = 0;");
+    line(1, "if (inc) { bl = udiv(g0 + threadIdx.x, vin->mT); tl = g0 + threadIdx.x - bl * vin->T; }");
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
-    thread_setup(2, sreg_used);
+    thread_setup(2, sreg_used, true);
     // dh = the thread's digest state, nv = its violations
     line(2, "uint32_t dh = bl * 0x9E3779B1u + tl;");
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
@@ -805,6 +831,8 @@ struct Gen {
     line(4, "if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, f);");
     line(3, "}");
     line(2, "}");
+    line(2, "tl += blockDim.x;");
+    line(2, "if (tl >= vin->T) { tl -= vin->T; bl++; }");
     line(1, "}");
     line(1, "__syncwarp();");
     line(1, "acc_flush(s_T, slot, acc);");
