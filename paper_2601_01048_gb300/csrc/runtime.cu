@@ -66,10 +66,12 @@ struct Lane {
   bool busy = false;
   bool timed = false;
   uint64_t batch_id = 0;
-  cudaGraphExec_t gexec = nullptr;
-  uint32_t graph_regs = 0, graph_prog = 0, graph_ctas = 0, graph_threads = 0;
-  const void* graph_kernel = nullptr;
-  uint32_t graph_launches = 0;
+  // one graph per kernel set a batch needs: bit 0 compiled, bit 1 interpreted
+  struct Graph {
+    cudaGraphExec_t exec = nullptr;
+    uint32_t regs = 0, prog = 0, ctas = 0, threads = 0, launches = 0;
+    const void* kernel = nullptr;
+  } graphs[4];
 };
 
 struct HostOnlyResult {
@@ -167,8 +169,10 @@ uint64_t total_bytes(const cufz_config& c, uint32_t n_slots) {
 cufz_status cuda_err(cudaError_t e) { return e == cudaSuccess ? CUFZ_OK : CUFZ_E_CUDA; }
 
 void lane_reset_graph(Lane& L) {
-  if (L.gexec) cudaGraphExecDestroy(L.gexec);
-  L.gexec = nullptr;
+  for (auto& G : L.graphs) {
+    if (G.exec) cudaGraphExecDestroy(G.exec);
+    G.exec = nullptr;
+  }
 }
 
 // Accounts the finished batch of a lane (timing) and marks it free.
@@ -400,15 +404,19 @@ const BatchHdr* interp_hdr(const Lane& L) {
 
 // The persistent launches of one batch: the compiled programs' items, then
 // the interpreted programs' items (an empty list costs one short launch).
+// Launches the persistent kernels of a batch: the compiled programs' items
+// (if n_jit) and the interpreted programs' items (if n_int).  With `all`
+// (graph capture) each runs on its full grid, for any batch with items of
+// that kind.
 cudaError_t launch_batch_kernels(cufz_ctx* c, const Lane& L, uint32_t n_jit, uint32_t n_int,
                                  bool all, cudaStream_t st, uint32_t* launches) {
   cudaError_t e = cudaSuccess;
-  if (has_jit_kernel(c) && (all || n_jit)) {
+  if (has_jit_kernel(c) && n_jit) {
     uint32_t ctas = all ? jit_ctas(c) : std::min<uint32_t>(jit_ctas(c), n_jit);
     e = launch_jit_persistent(c, jit_hdr(L), ctas, st);
     if (e == cudaSuccess) (*launches)++;
   }
-  if (e == cudaSuccess && (all || n_int)) {
+  if (e == cudaSuccess && n_int) {
     LaunchShape s = c->shape;
     s.ctas = all ? interp_ctas(c) : std::min<uint32_t>(interp_ctas(c), n_int);
     e = launch_persistent(c->T, interp_hdr(L), s, st);
@@ -417,16 +425,19 @@ cudaError_t launch_batch_kernels(cufz_ctx* c, const Lane& L, uint32_t n_jit, uin
   return e;
 }
 
-// Captures (or re-captures) the lane's graph: the persistent kernels of a
-// batch (compiled programs' items, interpreted programs' items).
-cufz_status lane_graph(cufz_ctx* c, Lane& L) {
+// Captures (or re-captures) the lane's graph for the kernel set `mask` of a
+// batch (bit 0: compiled programs' items, bit 1: interpreted programs'
+// items), so that a batch launches only the kernels it has items for.
+cufz_status lane_graph(cufz_ctx* c, Lane& L, uint32_t mask) {
   const LaunchShape& s = c->shape;
   const uint32_t ctas = interp_ctas(c) ^ (has_jit_kernel(c) ? jit_ctas(c) << 16 : 0);
   const void* kern = has_jit_kernel(c) ? reinterpret_cast<const void*>(c->jit_persist) : nullptr;
-  if (L.gexec && L.graph_regs == s.max_regs && L.graph_prog == s.max_prog_bytes &&
-      L.graph_ctas == ctas && L.graph_threads == s.cta_threads && L.graph_kernel == kern)
+  Lane::Graph& G = L.graphs[mask & 3u];
+  if (G.exec && G.regs == s.max_regs && G.prog == s.max_prog_bytes && G.ctas == ctas &&
+      G.threads == s.cta_threads && G.kernel == kern)
     return CUFZ_OK;
-  lane_reset_graph(L);
+  if (G.exec) cudaGraphExecDestroy(G.exec);
+  G.exec = nullptr;
   cudaGraph_t g = nullptr;
   cudaGetLastError();  // a stale error must not be taken for the capture's
   cudaError_t e0 = cudaStreamBeginCapture(L.stream, cudaStreamCaptureModeThreadLocal);
@@ -437,7 +448,7 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
   }
   uint32_t nl = 0;
   cudaError_t e1 = cudaSuccess;
-  cudaError_t e2 = launch_batch_kernels(c, L, 0, 0, true, L.stream, &nl);
+  cudaError_t e2 = launch_batch_kernels(c, L, mask & 1u, mask & 2u, true, L.stream, &nl);
   cudaError_t e3 = cudaStreamEndCapture(L.stream, &g);
   if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess || !g) {
     if (g) cudaGraphDestroy(g);
@@ -447,20 +458,20 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L) {
     cudaGetLastError();
     return CUFZ_E_CUDA;
   }
-  cudaError_t e4 = cudaGraphInstantiate(&L.gexec, g, 0);
+  cudaError_t e4 = cudaGraphInstantiate(&G.exec, g, 0);
   cudaGraphDestroy(g);
   if (e4 != cudaSuccess) {
-    c->stats.last_cuda_error = e4 != cudaSuccess ? 40000 + (int32_t)e4 : 50000;
+    c->stats.last_cuda_error = 40000 + (int32_t)e4;
     cudaGetLastError();
-    lane_reset_graph(L);
+    G.exec = nullptr;
     return CUFZ_E_CUDA;
   }
-  L.graph_regs = s.max_regs;
-  L.graph_prog = s.max_prog_bytes;
-  L.graph_ctas = ctas;
-  L.graph_threads = s.cta_threads;
-  L.graph_kernel = kern;
-  L.graph_launches = nl;
+  G.regs = s.max_regs;
+  G.prog = s.max_prog_bytes;
+  G.ctas = ctas;
+  G.threads = s.cta_threads;
+  G.kernel = kern;
+  G.launches = nl;
   return CUFZ_OK;
 }
 
@@ -888,7 +899,9 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     L->batch_id = c->next_batch++;
     cudaError_t e = cudaEventRecord(L->ev_start, L->stream);
     bool use_graph = !plain && !(c->cfg.flags & CUFZ_CF_NO_GRAPH);
-    if (use_graph && lane_graph(c, *L) != CUFZ_OK) {
+    const uint32_t kmask = (counts[0] ? 1u : 0u) | (counts[1] ? 2u : 0u);
+    if (kmask == 0) use_graph = false;  // no device items (not reached: every device input has one)
+    if (use_graph && lane_graph(c, *L, kmask) != CUFZ_OK) {
       use_graph = false;
       c->stats.graph_failures++;
     }
@@ -896,10 +909,10 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
       // the batch image goes up on the lane's stream, then its kernels run
       e = cudaMemcpyAsync(L->d_batch, L->h_stage, bytes, cudaMemcpyHostToDevice, L->stream);
       if (use_graph && e == cudaSuccess) {
-        e = cudaGraphLaunch(L->gexec, L->stream);
+        e = cudaGraphLaunch(L->graphs[kmask].exec, L->stream);
         if (e == cudaSuccess) {
           c->stats.graph_launches++;
-          c->stats.kernel_launches += L->graph_launches;
+          c->stats.kernel_launches += L->graphs[kmask].launches;
         } else {
           // the graph cannot run this batch: drop it and launch directly
           c->stats.last_cuda_error = 60000 + (int32_t)e;
