@@ -87,11 +87,10 @@ static __device__ __forceinline__ uint32_t jit_index_limit(int64_t len, uint32_t
   return n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
 }
 
-// Edge update for c hits of e by the calling group of lanes, taken only when
-// e is not yet saturated in this CTA's table: lanes with equal e are merged
-// (__match_any_sync) and their leader adds the group's hits, clamped to 128
-// (counts only matter up to 128).  Out of line: it is rare after the first
-// hits of each edge, and one copy keeps every site's inline code small.
+// Edge update for n hits of e per lane (a loop's repeated head edge), taken
+// only when e is not yet saturated in this CTA's table: lanes with equal e
+// are merged (__match_any_sync) and their leader adds the group's hits,
+// clamped to 128 (counts only matter up to 128).  Out of line, one copy.
 static __device__ __noinline__ void jit_cover_slow(uint32_t slot, uint32_t e, uint32_t n) {
   const uint32_t am = __activemask();
   const uint32_t peers = __match_any_sync(am, e);
@@ -107,12 +106,13 @@ static __device__ __noinline__ void jit_cover_slow(uint32_t slot, uint32_t e, ui
   }
 }
 
-// One hit of edge e.  Nothing to do once the edge is saturated in this CTA's
-// table, the common case.  Otherwise the lane adds its hit at the edge's home
-// slot itself (inserting the edge there if the slot is empty); only when
-// another edge holds the home slot does it take the out-of-line path.
-static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
-  if (edge_saturated(s_hash, e)) return;
+// One hit of e by this lane, for an edge not yet saturated in this CTA's
+// table: the lane adds its hit at the edge's home slot (inserting the edge
+// there if the slot is empty), or probes on if another edge holds it.  No
+// warp-level merging: on divergent branch-heavy code the few lanes that
+// arrive together rarely share an edge, and merging them cost more than the
+// atomics it saves.  Out of line, one copy for all sites.
+static __device__ __noinline__ void jit_cover_lane(uint32_t slot, uint32_t e) {
   const uint32_t tag = (e + 1u) << kHashTagShift;
   const uint32_t h = (e * 2654435761u) >> (32 - 11);
   uint32_t v = s_hash[h];
@@ -123,7 +123,13 @@ static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
   if ((v & ~kHashCountMask) == tag)
     edge_hit(s_hash, h, e, 1u);
   else
-    jit_cover_slow(slot, e, 1u);
+    edge_add(s_hash, s_T, slot, e, 1u);
+}
+
+// One hit of edge e: nothing to do once the edge is saturated in this CTA's
+// table, the common case.
+static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
+  if (!edge_saturated(s_hash, e)) jit_cover_lane(slot, e);
 }
 
 // n hits of edge e at once (n may differ between lanes, and be 0).
