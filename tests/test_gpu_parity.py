@@ -198,6 +198,40 @@ def test_listing_programs(B, orc, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+def test_flat_loop_edges(B, orc, path):
+    """Loops without branch sites in their bodies, whose head edges the
+    compiled path adds in closed form: trip counts that differ between the
+    lanes of a warp (0, 1 and many), a loop right after another (its first
+    edge follows the previous exit), an IF after the loops, and iteration
+    budgets that stop some threads inside a loop and not others."""
+    A = bc.Asm(n_bufs=2)
+    tx, a0, a1 = A.sreg(bc.TID_X), A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    n1 = A.alu(bc.AND, A.alu(bc.ADD, tx, a0), bc.Imm(15))          # 0..15 per lane
+    i = A.loop(n1, 12)
+    A.ld(0, A.alu(bc.ADD, i, tx), 4)
+    A.endloop()
+    n2 = A.alu(bc.SUB, A.alu(bc.AND, tx, bc.Imm(3)), bc.Imm(1))     # -1..2 per lane
+    j = A.loop(n2, 64)
+    A.st(1, A.alu(bc.MUL, j, a1), tx, 4)
+    A.endloop()
+    A.if_(A.alu(bc.SETLT, tx, a1))
+    A.ld(1, tx, 4)
+    A.endif()
+    prog = A.build()
+    ins = gen.make_inputs(4)
+    gen.set_input(ins[0], 0, (3, 1, 1), (96, 1, 1), (0, 40), (400, 400))
+    gen.set_input(ins[1], 0, (2, 1, 1), (256, 1, 1), (7, 3), (64, 1 << 12))
+    gen.set_input(ins[2], 0, (5, 1, 1), (33, 1, 1), (3, 100), (48, 96))
+    gen.set_input(ins[3], 0, (1, 1, 1), (1024, 1, 1), (11, 9), (1 << 14, 4))
+    for budget in (4096, 7, 1):
+        dres, drecs, dbms, ores, orecs, obms, _ = run_both(
+            B, orc, [prog], ins, budget=budget, flags=B.CF_KEEP_BITMAPS | path)
+        compare(B, orc, ins, dres, drecs, dbms, ores, orecs, obms, 1 << 15)
+        if budget < 12:
+            assert all(int(r["flags"]) & B.FL_BUDGET for r in dres)
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_edge_cases(B, orc, path):
     """Zero-length buffers, every-access violations with a tiny record cap
     (OVERFLOW, exact counts), the back-edge budget, LIMIT, a bad program id,
