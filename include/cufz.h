@@ -55,6 +55,7 @@ typedef int32_t cufz_status;
 #define CUFZ_E_NOT_FOUND (-7)       /* unknown ticket or program id */
 #define CUFZ_E_NO_DEVICE (-8)       /* no usable CUDA device */
 #define CUFZ_E_DEVICE_FAULT (-9)    /* the device reported an internal error word */
+#define CUFZ_E_IO (-10)             /* the autotune cache file could not be written */
 
 /* per-input status (cufz_result.status) */
 #define CUFZ_ST_OK 0
@@ -104,6 +105,10 @@ typedef struct {
   uint32_t ctas_per_sm;  /* persistent CTAs per SM (0 = from occupancy) */
   uint32_t jit_min_ctas; /* compiled path: CTAs per SM its registers must allow (0 = 3) */
   uint32_t reserved;
+  const char* autotune_cache; /* NULL, or a file that keeps the autotuner's
+                                 per-program choices across contexts and
+                                 processes (read at create, applied at load,
+                                 rewritten by cufz_autotune) */
 } cufz_config;
 
 /* One fuzz input, 128 bytes.  grid/block are the launch shape of the kernel
@@ -237,10 +242,20 @@ cufz_status cufz_create(const cufz_config* cfg, cufz_ctx** out);
 cufz_status cufz_destroy(cufz_ctx* ctx);
 
 /* Validates, prunes (unless CUFZ_CF_NO_PRUNE), allocates registers and
- * uploads one program; *program_id receives its id (0, 1, ...).  Programs
- * stay resident until the context is destroyed.  Up to 256 programs. */
+ * uploads one program; *program_id receives its id: the lowest id freed by
+ * cufz_unload_program, else the next new one (0, 1, ...).  Programs stay
+ * resident until unloaded or the context is destroyed.  Up to 256 loaded at
+ * a time, 8 MiB of loaded program blobs (CUFZ_E_NOMEM beyond). */
 cufz_status cufz_load_program(cufz_ctx* ctx, const void* bytes, size_t nbytes,
                               uint32_t* program_id, cufz_prog_stats* stats);
+
+/* Unloads a program: its device blob's space and its id become free for
+ * later loads, and inputs that name it complete with CUFZ_ST_BAD_PROGRAM.
+ * CUFZ_E_BUSY while inputs of the program are in flight (poll, then retry);
+ * CUFZ_E_NOT_FOUND for an id that is not loaded.  Results already completed
+ * stay readable until released.  (Program loading and unloading are the
+ * harness's job in the paper, Sec. 4; the call has no counterpart there.) */
+cufz_status cufz_unload_program(cufz_ctx* ctx, uint32_t program_id);
 
 /* Admits a prefix of in[0..n) while slots are free; each admitted input gets
  * ticket first_ticket + i.  Inputs with an invalid launch configuration,

@@ -18,7 +18,7 @@ from .gen import INPUT_DTYPE
 # ---------------------------------------------------------------- constants
 OK = 0
 E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUND, \
-    E_NO_DEVICE, E_DEVICE_FAULT = range(-1, -10, -1)
+    E_NO_DEVICE, E_DEVICE_FAULT, E_IO = range(-1, -11, -1)
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
 CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \
@@ -48,7 +48,8 @@ class cufz_config(ctypes.Structure):
                 ("iter_budget", ctypes.c_uint32), ("max_threads", ctypes.c_uint64),
                 ("item_threads", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
                 ("n_lanes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("jit_min_ctas", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+                ("jit_min_ctas", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("autotune_cache", ctypes.c_char_p)]
 
 
 class cufz_stats(ctypes.Structure):
@@ -83,6 +84,7 @@ EXPORTS = [
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
+    "cufz_unload_program",
 ]
 
 
@@ -123,6 +125,7 @@ def lib():
                 "cufz_set_program_path": (i32, [vp, u32, u32]),
                 "cufz_get_program_path": (i32, [vp, u32, P(u32)]),
                 "cufz_autotune": (i32, [vp, vp, u32, P(u32)]),
+                "cufz_unload_program": (i32, [vp, u32]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -188,6 +191,10 @@ def cufz_load_program(ctx, prog: bytes) -> tuple[int, cufz_prog_stats]:
     _check(lib().cufz_load_program(ctx, _bytes_ptr(prog), len(prog), ctypes.byref(pid),
                                    ctypes.byref(st)), "cufz_load_program")
     return pid.value, st
+
+
+def cufz_unload_program(ctx, program_id: int) -> None:
+    _check(lib().cufz_unload_program(ctx, program_id), "cufz_unload_program")
 
 
 def cufz_submit_inputs(ctx, inputs: np.ndarray) -> tuple[int, int, int]:
@@ -335,7 +342,7 @@ class Engine:
                  record_cap: int = 4096, flags: int = CF_KEEP_BITMAPS, redzone: int = 256,
                  iter_budget: int = 4096, max_threads: int = 1 << 31, cta_threads: int = 256,
                  item_threads: int = 0, n_lanes: int = 4, ctas_per_sm: int = 0,
-                 jit_min_ctas: int = 0):
+                 jit_min_ctas: int = 0, autotune_cache: str | None = None):
         import torch
 
         if not torch.cuda.is_available():
@@ -353,6 +360,8 @@ class Engine:
         cfg.n_lanes = n_lanes
         cfg.ctas_per_sm = ctas_per_sm
         cfg.jit_min_ctas = jit_min_ctas
+        self._tune_path = autotune_cache.encode() if autotune_cache else None
+        cfg.autotune_cache = self._tune_path
         cfg.max_slots = max_slots
         if arena_bytes is None:
             arena_bytes = cufz_arena_bytes(cfg, max_slots or 1024)

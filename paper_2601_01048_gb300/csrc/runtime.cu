@@ -15,7 +15,9 @@
 #include <algorithm>
 #include <atomic>
 #include <chrono>
+#include <cstdio>
 #include <cstring>
+#include <string>
 #include <deque>
 #include <mutex>
 #include <thread>
@@ -55,6 +57,7 @@ struct SlotHost {
   int state = 0;  // 0 free, 1 in flight, 2 completed (held until release)
   uint32_t lane = 0;
   uint64_t batch = 0;
+  uint32_t prog = 0;  // program of the input in the slot
 };
 
 struct Lane {
@@ -91,6 +94,11 @@ struct cufz_ctx {
   uint64_t prog_used = 0;
   std::vector<LoadedProgram> progs;
   std::vector<uint32_t> prog_off;
+  std::vector<uint8_t> prog_live;                          // 0 once unloaded
+  std::vector<uint64_t> prog_key;                          // autotune-cache key of each program
+  std::string tune_path;                                   // autotune cache file, if any
+  std::unordered_map<uint64_t, uint8_t> tune_cache;        // key -> compiled (1) or interpreted (0)
+  std::vector<std::pair<uint32_t, uint32_t>> prog_free;    // unloaded program-area ranges
   uint32_t max_regs = 1, max_prog_bytes = 16;
   uint32_t max_slots = 0;
   std::vector<SlotHost> slots;
@@ -519,6 +527,46 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
   d->user_tag = in.user_tag;
 }
 
+// Autotune cache: one "key path" line per program, the key a 64-bit FNV-1a
+// hash of the program's bytes and of the kernel shape it was tuned for.
+uint64_t tune_key(const cufz_ctx* c, const void* bytes, size_t n) {
+  uint64_t h = 0xCBF29CE484222325ull;
+  auto mix = [&](uint8_t b) { h = (h ^ b) * 0x100000001B3ull; };
+  const uint8_t* p = static_cast<const uint8_t*>(bytes);
+  for (size_t i = 0; i < n; i++) mix(p[i]);
+  const uint32_t shape[3] = {c->cfg.cta_threads, c->cfg.jit_min_ctas, c->cfg.flags & (CUFZ_CF_NO_PRUNE | CUFZ_CF_NO_DIGEST)};
+  for (uint32_t v : shape)
+    for (int k = 0; k < 4; k++) mix((uint8_t)(v >> (8 * k)));
+  return h;
+}
+
+void tune_cache_read(cufz_ctx* c) {
+  if (c->tune_path.empty()) return;
+  FILE* f = fopen(c->tune_path.c_str(), "r");
+  if (!f) return;  // no cache yet
+  char line[128];
+  if (fgets(line, sizeof line, f) && strncmp(line, "cufz-autotune 1", 15) == 0) {
+    unsigned long long key = 0;
+    unsigned path = 0;
+    while (fscanf(f, "%16llx %u", &key, &path) == 2) c->tune_cache[(uint64_t)key] = path ? 1 : 0;
+  }
+  fclose(f);
+}
+
+// Rewrites the cache (through a temporary file and a rename, so a reader
+// never sees half a file).  False if the file could not be written.
+bool tune_cache_write(const cufz_ctx* c) {
+  if (c->tune_path.empty()) return true;
+  const std::string tmp = c->tune_path + ".tmp";
+  FILE* f = fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  bool ok = fprintf(f, "cufz-autotune 1\n") > 0;
+  for (const auto& kv : c->tune_cache)
+    ok = ok && fprintf(f, "%016llx %u\n", (unsigned long long)kv.first, (unsigned)kv.second) > 0;
+  ok = (fclose(f) == 0) && ok;
+  return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
+}
+
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
@@ -564,6 +612,7 @@ const char* cufz_status_str(cufz_status s) {
     case CUFZ_E_NOT_FOUND: return "not found";
     case CUFZ_E_NO_DEVICE: return "no CUDA device";
     case CUFZ_E_DEVICE_FAULT: return "device reported an engine error";
+    case CUFZ_E_IO: return "autotune cache file could not be written";
     default: return "unknown status";
   }
 }
@@ -600,6 +649,9 @@ cufz_status cufz_create(const cufz_config* cfg_in, cufz_ctx** out) {
   if (total_bytes(cfg, n_slots) > cfg.arena_bytes) return CUFZ_E_NOMEM;
   cufz_ctx* c = new cufz_ctx();
   c->cfg = cfg;
+  if (cfg.autotune_cache) c->tune_path = cfg.autotune_cache;
+  c->cfg.autotune_cache = nullptr;  // the caller's string need not outlive the call
+  tune_cache_read(c);
   c->device = cfg.device;
   cudaDeviceGetAttribute(&c->n_sms, cudaDevAttrMultiProcessorCount, cfg.device);
   c->arena = reinterpret_cast<uint8_t*>(cfg.arena);
@@ -715,15 +767,34 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
                               cufz_prog_stats* stats) {
   if (!c || !bytes || !program_id) return CUFZ_E_INVALID_ARG;
   std::lock_guard<std::mutex> g(c->mu);
-  if (c->progs.size() >= (size_t)kMaxPrograms) return CUFZ_E_NOMEM;
+  // the id: the lowest unloaded one, else a new one
+  uint32_t id = (uint32_t)c->progs.size();
+  for (uint32_t k = 0; k < c->progs.size(); k++)
+    if (!c->prog_live[k]) {
+      id = k;
+      break;
+    }
+  if (id >= (uint32_t)kMaxPrograms) return CUFZ_E_NOMEM;
   LoadedProgram P;
   cufz_status st = load_program(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), &P);
   if (st != CUFZ_OK) return st;
-  if (c->prog_used + P.blob_bytes > kProgAreaBytes) {
+  // program-area space: the first unloaded range that fits, else the end
+  const uint32_t need = (uint32_t)align_up(P.blob_bytes, 16);
+  uint32_t off = 0;
+  size_t fi = c->prog_free.size();
+  for (size_t k = 0; k < c->prog_free.size(); k++)
+    if (c->prog_free[k].second >= need) {
+      fi = k;
+      break;
+    }
+  if (fi < c->prog_free.size()) {
+    off = c->prog_free[fi].first;
+  } else if (c->prog_used + need > kProgAreaBytes) {
     free_program(&P);
     return CUFZ_E_NOMEM;
+  } else {
+    off = (uint32_t)c->prog_used;
   }
-  uint32_t off = (uint32_t)c->prog_used;
   cudaError_t e = cudaMemcpy(c->d_progs + off, P.blob, P.blob_bytes, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) {
     free_program(&P);
@@ -731,21 +802,42 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
   }
   std::string fsrc;
   st = jit_source(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE),
-                  !(c->cfg.flags & CUFZ_CF_NO_DIGEST), (uint32_t)c->progs.size(), &fsrc);
+                  !(c->cfg.flags & CUFZ_CF_NO_DIGEST), id, &fsrc);
   if (st != CUFZ_OK) {
     free_program(&P);
     return st;
   }
-  c->prog_src.push_back(fsrc);
+  if (fi < c->prog_free.size()) {
+    c->prog_free[fi].first += need;
+    c->prog_free[fi].second -= need;
+    if (!c->prog_free[fi].second) c->prog_free.erase(c->prog_free.begin() + (long)fi);
+  } else {
+    c->prog_used += need;
+  }
+  if (stats) *stats = P.stats;
+  *program_id = id;
+  const uint64_t key = tune_key(c, bytes, nbytes);
+  const auto cached = c->tune_cache.find(key);
+  const uint8_t path0 = cached == c->tune_cache.end() ? 1 : cached->second;
   // default path: compiled (measured faster than the interpreter on every
   // workload family here, branch-heavy ones included); the autotuner
   // measures and can override
-  c->prog_compiled.push_back(1);
-  c->prog_used = align_up(c->prog_used + P.blob_bytes, 16);
-  if (stats) *stats = P.stats;
-  *program_id = (uint32_t)c->progs.size();
-  c->progs.push_back(P);
-  c->prog_off.push_back(off);
+  if (id == c->progs.size()) {
+    c->prog_src.push_back(fsrc);
+    c->prog_compiled.push_back(path0);
+    c->progs.push_back(P);
+    c->prog_off.push_back(off);
+    c->prog_live.push_back(1);
+    c->prog_key.push_back(key);
+  } else {
+    c->prog_src[id] = fsrc;
+    c->prog_compiled[id] = path0;
+    c->progs[id] = P;
+    c->prog_off[id] = off;
+    c->prog_live[id] = 1;
+    c->prog_key[id] = key;
+    if (id < c->prog_in_module.size()) c->prog_in_module[id] = 0;  // the module has the old code
+  }
   c->shape.max_regs = std::max(c->shape.max_regs, P.hdr.n_regs);
   c->shape.max_prog_bytes = std::max(c->shape.max_prog_bytes, (uint32_t)align_up(P.blob_bytes, 16));
   return ensure_smem(c);
@@ -789,7 +881,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   for (uint32_t i = 0; i < n; i++) {
     const cufz_input& x = in[i];
     int32_t status = CUFZ_ST_OK;
-    if (x.program_id >= c->progs.size()) status = CUFZ_ST_BAD_PROGRAM;
+    if (x.program_id >= c->progs.size() || !c->prog_live[x.program_id]) status = CUFZ_ST_BAD_PROGRAM;
     else if (invalid_launch(x)) status = CUFZ_ST_INVALID_CONFIG;
     else {
       uint64_t nt = (uint64_t)x.grid[0] * x.grid[1] * x.grid[2] * x.block[0] * x.block[1] * x.block[2];
@@ -830,6 +922,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     sh.seq = d->seq;
     sh.state = 1;
     sh.lane = lane_idx;
+    sh.prog = x.program_id;
     c->ticket_slot[ticket] = s;
     dev_slots.push_back(s);
     batch_threads += d->n_threads;
@@ -1152,15 +1245,31 @@ cufz_status cufz_compile_programs(cufz_ctx* c, char* log, uint32_t log_cap) {
 cufz_status cufz_set_program_path(cufz_ctx* c, uint32_t program_id, uint32_t compiled) {
   if (!c) return CUFZ_E_INVALID_ARG;
   std::lock_guard<std::mutex> g(c->mu);
-  if (program_id >= c->progs.size()) return CUFZ_E_NOT_FOUND;
+  if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
   c->prog_compiled[program_id] = compiled ? 1 : 0;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_unload_program(cufz_ctx* c, uint32_t program_id) {
+  if (!c) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  harvest(c);
+  if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+  for (const SlotHost& sh : c->slots)
+    if (sh.state == 1 && sh.prog == program_id) return CUFZ_E_BUSY;
+  LoadedProgram& P = c->progs[program_id];
+  c->prog_free.emplace_back(c->prog_off[program_id], (uint32_t)align_up(P.blob_bytes, 16));
+  free_program(&P);
+  c->prog_live[program_id] = 0;
+  c->prog_compiled[program_id] = 0;
+  c->prog_src[program_id].clear();
   return CUFZ_OK;
 }
 
 cufz_status cufz_get_program_path(cufz_ctx* c, uint32_t program_id, uint32_t* compiled) {
   if (!c || !compiled) return CUFZ_E_INVALID_ARG;
   std::lock_guard<std::mutex> g(c->mu);
-  if (program_id >= c->progs.size()) return CUFZ_E_NOT_FOUND;
+  if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
   *compiled = use_jit(c) && c->prog_compiled[program_id];
   return CUFZ_OK;
 }
@@ -1266,7 +1375,7 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   }
   for (auto& kv : by_prog) {
     const uint32_t p = kv.first;
-    if (p >= c->progs.size()) continue;
+    if (p >= c->progs.size() || !c->prog_live[p]) continue;
     const uint32_t dflt = before[p];
     double best[2] = {1e30, 1e30};
     for (int rep = 0; rep < 3; rep++)
@@ -1279,10 +1388,13 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
       }
     // leave the load-time choice only for a clear win
     const uint32_t other = 1u - dflt;
-    cufz_set_program_path(c, p, best[other] * kAutotuneMargin < best[dflt] ? other : dflt);
+    const uint32_t chosen = best[other] * kAutotuneMargin < best[dflt] ? other : dflt;
+    cufz_set_program_path(c, p, chosen);
+    c->tune_cache[c->prog_key[p]] = (uint8_t)chosen;
   }
   std::lock_guard<std::mutex> g(c->mu);
   c->stats = saved;
+  if (!tune_cache_write(c)) return CUFZ_E_IO;
   if (n_compiled)
     for (uint8_t b : c->prog_compiled) *n_compiled += b;
   return CUFZ_OK;

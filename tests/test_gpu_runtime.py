@@ -1,6 +1,7 @@
 """Runtime behaviour on the GPU: admission by free slots (a prefix is
 accepted, BUSY otherwise), slots reused after release, error codes for
-unknown tickets and programs, host-completed statuses, bounded waits."""
+unknown tickets and programs, host-completed statuses, bounded waits,
+program unloading and id reuse."""
 import numpy as np
 import pytest
 
@@ -65,3 +66,73 @@ def test_errors_and_host_completed_inputs(B):
         assert ei.value.status == B.E_NOT_FOUND
         assert len(B.cufz_poll_results(E.ctx, 8, 1000)) == 0          # bounded, nothing pending
         B.cufz_sync(E.ctx, 1000)
+
+
+@pytest.mark.parametrize("path", [0, 64])
+def test_unload_and_reload(B, orc, path):
+    """Unloading is refused while the program's inputs are in flight; after
+    it the id's inputs complete as BAD_PROGRAM, a new load takes the id and
+    its space, and the new program's results match the oracle (the compiled
+    module is rebuilt for the reused id)."""
+    p_old, p_other = gen.c1_program(), gen.c3_programs()[3]
+    p_new = gen.c3_programs()[5]
+    c1 = gen.c1_inputs(12, seed=21)
+    c3 = gen.c3_inputs(12, seed=22, max_blocks=8, max_threads=256)
+    with B.Engine(max_slots=64, record_cap=1 << 14, flags=B.CF_KEEP_BITMAPS | path) as E:
+        assert E.load(p_old) == 0 and E.load(p_other) == 1
+        st, acc, first = B.cufz_submit_inputs(E.ctx, c1)
+        assert acc == len(c1)
+        with pytest.raises(B.CufzError) as ei:
+            B.cufz_unload_program(E.ctx, 0)                      # its inputs are in flight
+        assert ei.value.status == B.E_BUSY
+        B.cufz_sync(E.ctx, -1)
+        for r in B.cufz_poll_results(E.ctx, 64, 0):
+            B.cufz_release(E.ctx, int(r["ticket"]))
+        B.cufz_unload_program(E.ctx, 0)
+        with pytest.raises(B.CufzError) as ei:
+            B.cufz_unload_program(E.ctx, 0)                      # not loaded any more
+        assert ei.value.status == B.E_NOT_FOUND
+        res, _, _ = E.run(c1[:3], records=False, bitmaps=False)
+        assert all(int(r["status"]) == B.ST_BAD_PROGRAM for r in res)
+        assert E.load(p_new) == 0                                # the freed id
+        ins = c3.copy()
+        ins["program_id"] = np.arange(len(ins)) % 2               # new program 0 and program 1
+        dres, drecs, dbms = E.run(ins)
+    ores, orecs, obms = orc.run_batch([p_new, p_other], ins, rec_cap=1 << 20, bitmaps=True)
+    for k in range(len(ins)):
+        for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch", "n_edges"):
+            assert int(dres[k][f]) == int(ores[k][f]), (k, f)
+        assert np.array_equal(dbms[k], obms[k]), k
+
+
+def _tune_key(prog: bytes, cta_threads: int, jit_min_ctas: int, flags: int) -> int:
+    """The cache key (64-bit FNV-1a of the program bytes, then the kernel
+    shape as little-endian u32s), restated from the cache's definition."""
+    h = 0xCBF29CE484222325
+    for b in prog + b"".join(int(v).to_bytes(4, "little") for v in (cta_threads, jit_min_ctas, flags & (4 | 32))):
+        h = ((h ^ b) * 0x100000001B3) & ((1 << 64) - 1)
+    return h
+
+
+def test_autotune_cache(B, orc, tmp_path):
+    """A cache file's choices apply at load in a new context, results stay
+    exact on the cached paths, and cufz_autotune rewrites the file."""
+    progs = [gen.c3_programs()[k] for k in (0, 1, 2)]
+    cache = tmp_path / "tune.txt"
+    keys = [_tune_key(p, 256, 0, B.CF_JIT) for p in progs]
+    cache.write_text("cufz-autotune 1\n" + f"{keys[1]:016x} 0\n")
+    ins = gen.c3_inputs(24, seed=31, max_blocks=8, max_threads=256)
+    ins["program_id"] %= 3
+    with B.Engine(max_slots=64, flags=B.CF_KEEP_BITMAPS | B.CF_JIT, autotune_cache=str(cache)) as E:
+        for p in progs:
+            E.load(p)
+        assert [B.cufz_get_program_path(E.ctx, k) for k in range(3)] == [True, False, True]
+        dres, _, dbms = E.run(ins)
+        B.cufz_autotune(E.ctx, ins)
+    ores, _, obms = orc.run_batch(progs, ins, rec_cap=1 << 20, bitmaps=True)
+    for k in range(len(ins)):
+        assert int(dres[k]["digest"]) == int(ores[k]["digest"]) and np.array_equal(dbms[k], obms[k])
+    lines = cache.read_text().split("\n")
+    assert lines[0] == "cufz-autotune 1"
+    got = {int(a, 16): int(b) for a, b in (l.split() for l in lines[1:] if l)}
+    assert set(keys) <= set(got) and all(v in (0, 1) for v in got.values())
