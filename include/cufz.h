@@ -251,7 +251,8 @@ cufz_status cufz_load_program(cufz_ctx* ctx, const void* bytes, size_t nbytes,
 
 /* Unloads a program: its device blob's space and its id become free for
  * later loads, and inputs that name it complete with CUFZ_ST_BAD_PROGRAM.
- * CUFZ_E_BUSY while inputs of the program are in flight (poll, then retry);
+ * CUFZ_E_BUSY while inputs of the program are in flight, i.e. submitted and
+ * not yet collected by cufz_poll_results or cufz_sync (collect, then retry);
  * CUFZ_E_NOT_FOUND for an id that is not loaded.  Results already completed
  * stay readable until released.  (Program loading and unloading are the
  * harness's job in the paper, Sec. 4; the call has no counterpart there.) */

@@ -1253,8 +1253,8 @@ cufz_status cufz_set_program_path(cufz_ctx* c, uint32_t program_id, uint32_t com
 cufz_status cufz_unload_program(cufz_ctx* c, uint32_t program_id) {
   if (!c) return CUFZ_E_INVALID_ARG;
   std::lock_guard<std::mutex> g(c->mu);
-  harvest(c);
   if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+  // in flight = submitted and not yet collected by a poll or sync
   for (const SlotHost& sh : c->slots)
     if (sh.state == 1 && sh.prog == program_id) return CUFZ_E_BUSY;
   LoadedProgram& P = c->progs[program_id];
