@@ -258,6 +258,19 @@ cufz_status cufz_load_program(cufz_ctx* ctx, const void* bytes, size_t nbytes,
  * harness's job in the paper, Sec. 4; the call has no counterpart there.) */
 cufz_status cufz_unload_program(cufz_ctx* ctx, uint32_t program_id);
 
+/* The pruning check (Sec. 5.2: AXIPrune drops only instructions that feed no
+ * memory address or branch, so every access is kept exactly).  Runs the n
+ * inputs (their program_id is ignored) on loaded program `program_id` and
+ * on the same program loaded unpruned (interpreted, a temporary id unloaded
+ * afterwards), and counts in *n_mismatch the inputs whose outcomes differ
+ * in anything pruning must keep: status, budget and overflow flags, access,
+ * violation, branch and thread counts, first-violation key, access digest,
+ * record count, edge count, bitmap (if kept) and, when not overflowing, the
+ * record set.  Needs an idle context (CUFZ_E_BUSY otherwise); both runs
+ * update the coverage union like any other inputs. */
+cufz_status cufz_verify_prune(cufz_ctx* ctx, uint32_t program_id, const cufz_input* inputs,
+                              uint32_t n, uint32_t* n_mismatch);
+
 /* Admits a prefix of in[0..n) while slots are free; each admitted input gets
  * ticket first_ticket + i.  Inputs with an invalid launch configuration,
  * beyond the limits or naming no program are admitted and complete at once

@@ -84,7 +84,7 @@ EXPORTS = [
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
-    "cufz_unload_program",
+    "cufz_unload_program", "cufz_verify_prune",
 ]
 
 
@@ -126,6 +126,7 @@ def lib():
                 "cufz_get_program_path": (i32, [vp, u32, P(u32)]),
                 "cufz_autotune": (i32, [vp, vp, u32, P(u32)]),
                 "cufz_unload_program": (i32, [vp, u32]),
+                "cufz_verify_prune": (i32, [vp, u32, vp, u32, P(u32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -195,6 +196,16 @@ def cufz_load_program(ctx, prog: bytes) -> tuple[int, cufz_prog_stats]:
 
 def cufz_unload_program(ctx, program_id: int) -> None:
     _check(lib().cufz_unload_program(ctx, program_id), "cufz_unload_program")
+
+
+def cufz_verify_prune(ctx, program_id: int, inputs: np.ndarray) -> int:
+    """Number of inputs whose outcome differs between the pruned and the
+    unpruned program."""
+    inputs = np.ascontiguousarray(inputs, dtype=INPUT_DTYPE)
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_verify_prune(ctx, program_id, inputs.ctypes.data, len(inputs), ctypes.byref(n)),
+           "cufz_verify_prune")
+    return n.value
 
 
 def cufz_submit_inputs(ctx, inputs: np.ndarray) -> tuple[int, int, int]:

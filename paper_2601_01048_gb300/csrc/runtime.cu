@@ -21,6 +21,7 @@
 #include <deque>
 #include <mutex>
 #include <thread>
+#include <tuple>
 #include <future>
 #include <unordered_map>
 #include <vector>
@@ -96,6 +97,7 @@ struct cufz_ctx {
   std::vector<uint32_t> prog_off;
   std::vector<uint8_t> prog_live;                          // 0 once unloaded
   std::vector<uint64_t> prog_key;                          // autotune-cache key of each program
+  std::vector<std::vector<uint8_t>> prog_bytes;            // each program as loaded (unpruned)
   std::string tune_path;                                   // autotune cache file, if any
   std::unordered_map<uint64_t, uint8_t> tune_cache;        // key -> compiled (1) or interpreted (0)
   std::vector<std::pair<uint32_t, uint32_t>> prog_free;    // unloaded program-area ranges
@@ -763,9 +765,26 @@ cufz_status cufz_destroy(cufz_ctx* c) {
   return CUFZ_OK;
 }
 
+namespace {
+cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune, int path,
+                      uint32_t* program_id, cufz_prog_stats* stats);
+}
+
 cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uint32_t* program_id,
                               cufz_prog_stats* stats) {
   if (!c || !bytes || !program_id) return CUFZ_E_INVALID_ARG;
+  return load_into(c, bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), -1, program_id, stats);
+}
+
+}  // extern "C"
+
+namespace {
+
+// Loads a program (pruned or not) under the context lock.  path: -1 the
+// default (the autotune cache's choice, else compiled), 0 interpreted,
+// 1 compiled.
+cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune, int path,
+                      uint32_t* program_id, cufz_prog_stats* stats) {
   std::lock_guard<std::mutex> g(c->mu);
   // the id: the lowest unloaded one, else a new one
   uint32_t id = (uint32_t)c->progs.size();
@@ -776,7 +795,7 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     }
   if (id >= (uint32_t)kMaxPrograms) return CUFZ_E_NOMEM;
   LoadedProgram P;
-  cufz_status st = load_program(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE), &P);
+  cufz_status st = load_program(bytes, nbytes, prune, &P);
   if (st != CUFZ_OK) return st;
   // program-area space: the first unloaded range that fits, else the end
   const uint32_t need = (uint32_t)align_up(P.blob_bytes, 16);
@@ -801,8 +820,7 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     return CUFZ_E_CUDA;
   }
   std::string fsrc;
-  st = jit_source(bytes, nbytes, !(c->cfg.flags & CUFZ_CF_NO_PRUNE),
-                  !(c->cfg.flags & CUFZ_CF_NO_DIGEST), id, &fsrc);
+  st = jit_source(bytes, nbytes, prune, !(c->cfg.flags & CUFZ_CF_NO_DIGEST), id, &fsrc);
   if (st != CUFZ_OK) {
     free_program(&P);
     return st;
@@ -818,7 +836,8 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
   *program_id = id;
   const uint64_t key = tune_key(c, bytes, nbytes);
   const auto cached = c->tune_cache.find(key);
-  const uint8_t path0 = cached == c->tune_cache.end() ? 1 : cached->second;
+  const uint8_t path0 = path >= 0 ? (uint8_t)path : cached == c->tune_cache.end() ? 1 : cached->second;
+  std::vector<uint8_t> original(static_cast<const uint8_t*>(bytes), static_cast<const uint8_t*>(bytes) + nbytes);
   // default path: compiled (measured faster than the interpreter on every
   // workload family here, branch-heavy ones included); the autotuner
   // measures and can override
@@ -829,6 +848,7 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     c->prog_off.push_back(off);
     c->prog_live.push_back(1);
     c->prog_key.push_back(key);
+    c->prog_bytes.push_back(std::move(original));
   } else {
     c->prog_src[id] = fsrc;
     c->prog_compiled[id] = path0;
@@ -836,12 +856,17 @@ cufz_status cufz_load_program(cufz_ctx* c, const void* bytes, size_t nbytes, uin
     c->prog_off[id] = off;
     c->prog_live[id] = 1;
     c->prog_key[id] = key;
+    c->prog_bytes[id] = std::move(original);
     if (id < c->prog_in_module.size()) c->prog_in_module[id] = 0;  // the module has the old code
   }
   c->shape.max_regs = std::max(c->shape.max_regs, P.hdr.n_regs);
   c->shape.max_prog_bytes = std::max(c->shape.max_prog_bytes, (uint32_t)align_up(P.blob_bytes, 16));
   return ensure_smem(c);
 }
+
+}  // namespace
+
+extern "C" {
 
 cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, uint32_t* n_accepted,
                                uint64_t* first_ticket) {
@@ -1263,6 +1288,116 @@ cufz_status cufz_unload_program(cufz_ctx* c, uint32_t program_id) {
   c->prog_live[program_id] = 0;
   c->prog_compiled[program_id] = 0;
   c->prog_src[program_id].clear();
+  return CUFZ_OK;
+}
+
+namespace {
+
+// What a run of one input leaves: its result, bitmap (if kept) and records.
+struct Outcome {
+  cufz_result res{};
+  std::vector<uint8_t> bitmap;
+  std::vector<cufz_violation> recs;
+};
+
+// Runs inputs on an idle context and collects their outcomes, releasing
+// their slots.
+cufz_status run_collect(cufz_ctx* c, const std::vector<cufz_input>& in, std::vector<Outcome>* out) {
+  out->assign(in.size(), Outcome{});
+  const bool keep = (c->cfg.flags & CUFZ_CF_KEEP_BITMAPS) != 0;
+  const bool auto_rel = (c->cfg.flags & CUFZ_CF_AUTO_RELEASE) != 0;
+  std::unordered_map<uint64_t, size_t> index;
+  std::vector<cufz_result> got(256);
+  size_t pos = 0, done = 0;
+  while (done < in.size()) {
+    if (pos < in.size()) {
+      uint32_t acc = 0;
+      uint64_t first = 0;
+      cufz_status st = cufz_submit_inputs(c, in.data() + pos, (uint32_t)(in.size() - pos), &acc, &first);
+      if (st != CUFZ_OK && st != CUFZ_E_BUSY) return st;
+      for (uint32_t k = 0; k < acc; k++) index[first + k] = pos + k;
+      pos += acc;
+    }
+    cufz_status st = cufz_sync(c, -1);
+    if (st != CUFZ_OK) return st;
+    for (;;) {
+      uint32_t n = 0;
+      st = cufz_poll_results(c, got.data(), (uint32_t)got.size(), &n, 0);
+      if (st != CUFZ_OK) return st;
+      if (!n) break;
+      for (uint32_t k = 0; k < n; k++) {
+        const auto it = index.find(got[k].ticket);
+        if (it == index.end()) continue;
+        Outcome& o = (*out)[it->second];
+        o.res = got[k];
+        if (!auto_rel) {
+          if (keep) {
+            o.bitmap.resize(kBitmapBytes);
+            if (cufz_get_bitmap(c, o.res.ticket, o.bitmap.data()) != CUFZ_OK) o.bitmap.clear();
+          }
+          o.recs.resize(o.res.n_records);
+          uint32_t nr = 0;
+          if (o.res.n_records &&
+              cufz_get_records(c, o.res.ticket, o.recs.data(), o.res.n_records, &nr) != CUFZ_OK)
+            nr = 0;
+          o.recs.resize(nr);
+          cufz_release(c, o.res.ticket);
+        }
+        done++;
+      }
+    }
+  }
+  return CUFZ_OK;
+}
+
+bool same_outcome(const Outcome& a, const Outcome& b, uint32_t cap) {
+  const cufz_result &x = a.res, &y = b.res;
+  const uint32_t fl = CUFZ_FL_BUDGET | CUFZ_FL_OVERFLOW;
+  if (x.status != y.status || (x.flags & fl) != (y.flags & fl) || x.n_accesses != y.n_accesses ||
+      x.n_violations != y.n_violations || x.first_key != y.first_key || x.digest != y.digest ||
+      x.n_branch != y.n_branch || x.n_threads != y.n_threads || x.n_records != y.n_records ||
+      x.n_edges != y.n_edges || a.bitmap != b.bitmap)
+    return false;
+  if (x.n_violations > cap) return true;  // any cap records of the violations: not unique
+  auto key = [](const cufz_violation& v) {
+    return std::make_tuple(v.block_lin, v.thread_lin, v.ordinal, v.site, v.buf, v.kind, v.width,
+                           v.space, v.cls, v.byte_off);
+  };
+  std::vector<decltype(key(cufz_violation{}))> ka, kb;
+  for (const auto& v : a.recs) ka.push_back(key(v));
+  for (const auto& v : b.recs) kb.push_back(key(v));
+  std::sort(ka.begin(), ka.end());
+  std::sort(kb.begin(), kb.end());
+  return ka == kb;
+}
+
+}  // namespace
+
+cufz_status cufz_verify_prune(cufz_ctx* c, uint32_t program_id, const cufz_input* inputs, uint32_t n,
+                              uint32_t* n_mismatch) {
+  if (!c || (!inputs && n) || !n_mismatch) return CUFZ_E_INVALID_ARG;
+  *n_mismatch = 0;
+  std::vector<uint8_t> bytes;
+  {
+    std::lock_guard<std::mutex> g(c->mu);
+    if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+    if (!c->inflight.empty() || !c->ready.empty()) return CUFZ_E_BUSY;
+    bytes = c->prog_bytes[program_id];
+  }
+  uint32_t full = 0;
+  cufz_status st = load_into(c, bytes.data(), bytes.size(), false, 0, &full, nullptr);
+  if (st != CUFZ_OK) return st;
+  std::vector<cufz_input> a(inputs, inputs + n), b(inputs, inputs + n);
+  for (auto& x : a) x.program_id = program_id;
+  for (auto& x : b) x.program_id = full;
+  std::vector<Outcome> ra, rb;
+  st = run_collect(c, a, &ra);
+  if (st == CUFZ_OK) st = run_collect(c, b, &rb);
+  const cufz_status su = cufz_unload_program(c, full);
+  if (st != CUFZ_OK) return st;
+  if (su != CUFZ_OK) return su;
+  for (uint32_t i = 0; i < n; i++)
+    if (!same_outcome(ra[i], rb[i], c->cfg.record_cap)) (*n_mismatch)++;
   return CUFZ_OK;
 }
 

@@ -136,3 +136,24 @@ def test_autotune_cache(B, orc, tmp_path):
     assert lines[0] == "cufz-autotune 1"
     got = {int(a, 16): int(b) for a, b in (l.split() for l in lines[1:] if l)}
     assert set(keys) <= set(got) and all(v in (0, 1) for v in got.values())
+
+
+@pytest.mark.parametrize("path", [0, 64])
+def test_verify_prune(B, path):
+    """The library's own pruning check finds no difference between pruned and
+    unpruned runs of random and branch-heavy programs, records included, and
+    leaves the context as it found it (the temporary program is unloaded)."""
+    progs = gen.c2_programs()[:3] + gen.c4_programs()[:2]
+    c2 = gen.c2_inputs(progs[:3], per_program=3, seed=41, max_grid=3)
+    c4 = gen.c4_inputs(6, n_programs=2, seed=42, max_blocks=4)
+    with B.Engine(max_slots=64, record_cap=1 << 14, flags=B.CF_KEEP_BITMAPS | path) as E:
+        for p in progs:
+            E.load(p)
+        for k in range(3):
+            assert B.cufz_verify_prune(E.ctx, k, c2[c2["program_id"] == k]) == 0
+        for k in range(2):
+            assert B.cufz_verify_prune(E.ctx, 3 + k, c4[c4["program_id"] == k]) == 0
+        assert E.load(gen.c1_program()) == 5                     # the temporary id was freed
+        with pytest.raises(B.CufzError) as ei:
+            B.cufz_verify_prune(E.ctx, 9, c2[:1])
+        assert ei.value.status == B.E_NOT_FOUND
