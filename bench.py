@@ -44,7 +44,7 @@ LANES_PER_SM = 128
 # taken on: once those change the figure no longer applies and is reported
 # as null.
 TRAFFIC_SOURCES = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h",
-                   "loader.cpp", "runtime.cu")
+                   "loader.cpp")
 TRAFFIC_BYTES: dict[str, tuple[str, int]] = {
     "c2": ("a3c6a42b63e3d3f5", 60_760_576 + 1_452_110_336),
 }

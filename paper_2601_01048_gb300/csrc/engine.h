@@ -9,6 +9,7 @@
 #include <stdint.h>
 
 #include <string>
+#include <vector>
 
 #include "layout.h"
 
@@ -28,6 +29,16 @@ struct LoadedProgram {
 // without pruning).  Returns CUFZ_OK or CUFZ_E_INVALID_PROGRAM.
 cufz_status load_program(const void* bytes, size_t nbytes, bool prune, LoadedProgram* out);
 void free_program(LoadedProgram* p);
+
+// Resident CTAs per SM the compiled kernel's registers must allow when the
+// config leaves it open: 3 x 256 threads gives it 85 registers a thread.
+constexpr uint32_t kJitMinCtasDefault = 3;
+
+// The compiled path's module source: the included programs' functions (from
+// jit_source), the dispatcher and the kernels.
+std::string jit_module_source(const std::vector<std::string>& prog_src,
+                              const std::vector<uint8_t>& include, bool plain_kernel,
+                              uint32_t min_ctas, uint32_t cta_threads);
 
 // CUDA source of one program's work-item function `cufz_prog_<index>` for
 // the compiled path (see jit_kernel.cuh).

@@ -842,6 +842,32 @@ struct Gen {
 
 }  // namespace
 
+// The compiled path's module: every program's item function, the dispatcher
+// and the kernels, compiled as one translation unit so the program functions
+// are register-allocated together with the kernel that calls them.
+std::string jit_module_source(const std::vector<std::string>& prog_src,
+                              const std::vector<uint8_t>& include, bool plain_kernel,
+                              uint32_t min_ctas, uint32_t cta_threads) {
+  // the persistent kernel's launch bounds follow the context's CTA size;
+  // at most 2048 resident threads per SM
+  min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : kJitMinCtasDefault, 2048u / cta_threads));
+  std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas) +
+                    "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) +
+                    "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
+  for (size_t k = 0; k < prog_src.size(); k++)
+    if (include[k]) src += prog_src[k];
+  src += "static __device__ bool jit_run(uint32_t prog, uint32_t g0, uint32_t g_end) {\n"
+         "  switch (prog) {\n";
+  for (size_t k = 0; k < prog_src.size(); k++)
+    if (include[k])
+      src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
+             "(g0, g_end); return true;\n";
+  src += "    default: return false;\n  }\n}\n}  // namespace cufz\n";
+  if (plain_kernel) src += "#define CUFZ_JIT_PLAIN 1\n";
+  src += "#include \"jit_launch.cuh\"\n";
+  return src;
+}
+
 cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool digest,
                        uint32_t index, std::string* out) {
   Ir ir;

@@ -40,9 +40,6 @@ constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
 constexpr double kAutotuneMargin = 1.25;  // the other path must be 25% faster
 constexpr uint64_t kAutotuneMinThreads = 1ull << 24;  // test threads timed per program and path
 constexpr size_t kAutotuneMaxInputs = 2048;
-// resident CTAs per SM the compiled kernel's registers must allow when the
-// config leaves it open: 3 x 256 threads gives it 85 registers a thread
-constexpr uint32_t kJitMinCtasDefault = 3;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -258,32 +255,6 @@ cufz_status ensure_smem(cufz_ctx* c) {
 
 
 bool use_jit(const cufz_ctx* c) { return (c->cfg.flags & CUFZ_CF_JIT) != 0; }
-
-// The compiled path's module: every program's item function, the dispatcher
-// and the kernels, compiled as one translation unit so the program functions
-// are register-allocated together with the kernel that calls them.
-std::string jit_module_source(const std::vector<std::string>& prog_src,
-                              const std::vector<uint8_t>& include, bool plain_kernel,
-                              uint32_t min_ctas, uint32_t cta_threads) {
-  // the persistent kernel's launch bounds follow the context's CTA size;
-  // at most 2048 resident threads per SM
-  min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : kJitMinCtasDefault, 2048u / cta_threads));
-  std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas) +
-                    "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) +
-                    "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
-  for (size_t k = 0; k < prog_src.size(); k++)
-    if (include[k]) src += prog_src[k];
-  src += "static __device__ bool jit_run(uint32_t prog, uint32_t g0, uint32_t g_end) {\n"
-         "  switch (prog) {\n";
-  for (size_t k = 0; k < prog_src.size(); k++)
-    if (include[k])
-      src += "    case " + std::to_string(k) + ": cufz_prog_" + std::to_string(k) +
-             "(g0, g_end); return true;\n";
-  src += "    default: return false;\n  }\n}\n}  // namespace cufz\n";
-  if (plain_kernel) src += "#define CUFZ_JIT_PLAIN 1\n";
-  src += "#include \"jit_launch.cuh\"\n";
-  return src;
-}
 
 // Runtime-compiles the module to sm_103a code (no device needed).
 cufz_status jit_nvrtc(const std::string& src, bool fast, std::vector<char>* cubin, std::string* log) {
