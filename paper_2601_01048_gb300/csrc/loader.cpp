@@ -555,24 +555,40 @@ struct Gen {
     }
     return k;
   }
-  // the counter increments of the run starting at pc
+  // the counter increments of the run starting at pc, including the
+  // evaluation of the IF that ends it (always reached once the run starts:
+  // a run holds no loop, so no budget stop)
   void run_counts(int ind, int pc, int end) {
     if (rec_) return;
     const int k = run_ops(pc, end), m = run_acc(pc, end);
+    int q = pc;
+    while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
+    const bool ends_at_if = q < end && ir.ops[q].opc == B_IF && ir.ops[q].kept;
     if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
     if (m) line(ind, "acc.n_acc += " + std::to_string(m) + "u;");
+    if (ends_at_if) line(ind, "acc.n_branch += 1u;");
   }
 
-  void cover(int ind, int site, const std::string& cond) {
+  // One branch evaluation's edge.  count: add it to n_branch here (loop
+  // heads); an IF's evaluation is counted with the run that ends at it.
+  void cover(int ind, int site, const std::string& cond, bool count) {
     if (rec_) return;
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
-                  "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1; acc.n_branch++;"
-                  " jit_cover(slot, e); }");
+                  "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1;" +
+                  (count ? " acc.n_branch++;" : "") + " jit_cover(slot, e); }");
   }
 
-  static std::string lim_name(int buf, int lw) {
-    return "lim[" + std::to_string(buf * 5 + lw) + "]";
+  // index limits are read once per function call into constants (a
+  // program uses a few (buffer, width) pairs)
+  static std::string lim_name(int buf, int lw) { return "L" + std::to_string(buf * 5 + lw); }
+  void lim_decls(int ind) {
+    for (int k = 0; k < kMaxBufs * 5; k++) {
+      bool used = false;
+      for (const auto& op : ir.ops)
+        if (op.kept && (op.opc == B_LD || op.opc == B_ST) && op.buf * 5 + log2w(op.width) == k) used = true;
+      if (used) line(ind, "const uint32_t L" + std::to_string(k) + " = lim[" + std::to_string(k) + "];");
+    }
   }
 
   // An access of width w = 2^lw at index ix is in bounds iff
@@ -640,7 +656,7 @@ struct Gen {
         std::string c = "c" + std::to_string(o2.site);
         line(ind, "{");
         line(ind + 1, "const bool " + c + " = " + r(o2.a) + " != 0;");
-        cover(ind + 1, o2.site, c);
+        cover(ind + 1, o2.site, c, false);
         line(ind + 1, "if (" + c + ") {");
         range(ind + 2, pc + 1, o2.else_pc >= 0 ? o2.else_pc : o2.end_pc);
         if (o2.else_pc >= 0) {
@@ -688,7 +704,7 @@ struct Gen {
         line(ind + 1, "#pragma unroll 1");
         line(ind + 1, "for (;;) {");
         line(ind + 2, "const bool " + c + " = " + r(o2.dst) + " < " + t + ";");
-        cover(ind + 2, o2.site, c);
+        cover(ind + 2, o2.site, c, true);
         line(ind + 2, "if (!" + c + ") break;");
         range(ind + 2, pc + 1, o2.end_pc);
         line(ind + 2, rec_ ? "if (++back > budget) goto cufz_done;"
@@ -778,6 +794,7 @@ struct Gen {
     line(1, "const uint32_t budget = s_T.iter_budget;");
     line(1, "const DevInput* vin = &s_in;");
     line(1, "const uint32_t* lim = vin->lim;");
+    lim_decls(1);
     thread_setup(1, sreg_used, false);
     line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
     line(1, "(void)back;");
@@ -801,6 +818,7 @@ struct Gen {
     // shared copy of the input, which the compiler may keep or reload
     line(1, "const DevInput* vin = &s_in;");
     line(1, "const uint32_t* lim = s_in.lim;");
+    lim_decls(1);
     line(1, "const bool inc = vin->T >= blockDim.x;");
     line(1, "const bool b1 = vin->block[1] == 1u && vin->block[2] == 1u;");
     line(1, "const bool g1 = vin->grid[1] == 1u && vin->grid[2] == 1u;");
