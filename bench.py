@@ -46,7 +46,7 @@ LANES_PER_SM = 128
 TRAFFIC_SOURCES = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h",
                    "loader.cpp")
 TRAFFIC_BYTES: dict[str, tuple[str, int]] = {
-    "c2": ("e7f9b9616d2be89b", 57_360_896 + 1_471_149_312),
+    "c2": ("dd381d39bb60a8c3", 58_376_448 + 1_471_800_576),
 }
 
 
@@ -77,7 +77,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
+    ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "affine"])
+    ap.add_argument("--prex", action="store_true",
+                    help="partial representative execution: qualifying inputs run their corner threads")
     ap.add_argument("--rate", type=float, default=50000.0, help="c5: offered inputs/s")
     ap.add_argument("--duration", type=float, default=2.0, help="c5: seconds of arrivals")
     ap.add_argument("--inputs-per-step", type=int, default=0, help="0: the whole workload")
@@ -110,6 +112,9 @@ def workload(name: str, rank: int = 0):
     if name == "c3":
         return ("c3: 4096 inputs over 16 C1-family programs, 1-65536 blocks x 32-1024 threads",
                 gen.c3_programs(), gen.c3_inputs(4096), 4096)
+    if name == "affine":
+        return ("affine: 4096 inputs over 16 unguarded affine-access programs (PREX's class), "
+                "1-65536 blocks x 32-1024 threads", gen.affine_programs(), gen.affine_inputs(4096), 4096)
     if name == "c5":
         progs = gen.c5_programs()
         return ("c5: mutated inputs over 64 resident programs", progs,
@@ -268,6 +273,8 @@ def run_engine(args, rank, world, local, pg):
     n_all = len(inputs)
     per_step = args.inputs_per_step or n_all
     flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
+    if args.prex:
+        flags |= B.CF_PREX
     if args.path == "jit":
         flags |= B.CF_JIT | (B.CF_JIT_FAST_COMPILE if args.jit_fast_compile else 0)
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
@@ -313,7 +320,7 @@ def run_engine(args, rank, world, local, pg):
     clocks.start()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    tot = dict(acc=0, inputs=0, ops=0, br=0, viol=0, threads=0)
+    tot = dict(acc=0, inputs=0, ops=0, br=0, viol=0, threads=0, partial=0, bug_inputs=0)
     lats = []
     h2d = d2h = 0
     for k in range(args.steps):
@@ -325,6 +332,8 @@ def run_engine(args, rank, world, local, pg):
         tot["br"] += int(res["n_branch"].sum())
         tot["viol"] += int(res["n_violations"].sum())
         tot["threads"] += int(res["n_threads"].sum())
+        tot["partial"] += int(((res["flags"] & B.FL_PARTIAL) != 0).sum())
+        tot["bug_inputs"] += int((res["status"] == B.ST_VIOLATION).sum())
         h2d += len(res) * 128
         d2h += len(res) * 96
     torch.cuda.synchronize(dev)
@@ -382,6 +391,11 @@ def run_engine(args, rank, world, local, pg):
             "parallelism": f"replicas x{world}",
         },
         "inputs_per_s": inputs_all / kernel_s_max if kernel_s_max > 0 else 0.0,
+        "violating_inputs_per_step": tot["bug_inputs"] // max(args.steps, 1),
+        "prex": ({"partial_inputs_per_step": tot["partial"] // max(args.steps, 1),
+                  "note": "partial inputs ran their corner threads only; their verdict is the "
+                          "full grid's, their accesses are the corners'"}
+                 if args.prex else None),
         "test_threads_per_step": tot["threads"] // max(args.steps, 1),
         "violations_per_step": tot["viol"] // max(args.steps, 1),
         "roofline": {

@@ -68,6 +68,9 @@ typedef int32_t cufz_status;
 #define CUFZ_FL_BUDGET 1   /* some thread exceeded the back-edge budget (hang analog) */
 #define CUFZ_FL_OVERFLOW 2 /* more violations than record_cap; counts stay exact */
 #define CUFZ_FL_NEW_COV 4  /* bitmap has a bucket bit the epoch's union lacks */
+#define CUFZ_FL_PARTIAL 8  /* CUFZ_CF_PREX ran only the corner threads: the status
+                              (violation or not) is the full grid's; counts,
+                              records, digest and bitmap cover the corners */
 
 /* violation classes (cufz_violation.cls) */
 #define CUFZ_CLS_UNDERFLOW_RZ 1 /* byte_off in [-R, 0) */
@@ -85,6 +88,9 @@ typedef int32_t cufz_status;
 #define CUFZ_CF_JIT 64         /* run programs compiled to sm_103a code at load time
                                   instead of through the bytecode interpreter */
 #define CUFZ_CF_JIT_FAST_COMPILE 128 /* compile faster, run slower (compiled path) */
+#define CUFZ_CF_PREX 256       /* partial representative execution (Sec. 5.1): an input
+                                  whose program qualifies (cufz_prex_check) runs only
+                                  its corner threads, flagged CUFZ_FL_PARTIAL */
 
 /* Engine configuration.  cufz_config_default fills every field; a zero in
  * max_slots, item_threads or cta_threads means "choose automatically". */
@@ -227,6 +233,20 @@ cufz_status cufz_program_cuda(const void* bytes, size_t nbytes, uint32_t flags, 
  * with the compiler's log in log. */
 cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, uint32_t n,
                                uint32_t flags, char* log, uint32_t log_cap, size_t* cubin_bytes);
+
+/* PREX check (Sec. 5.1): *eligible = 1 when the corner threads of `in`
+ * (every thread and block coordinate first or last: at most 64) decide
+ * whether any thread of its grid violates.  That holds (the theorem of
+ * Sec. 5.1.1) when, executing the program once with thread-invariant
+ * values, every branch condition and loop trip count is the same for all
+ * threads, every access index is thread-invariant or an affine function of
+ * the thread and block indices with thread-invariant coefficients, and no
+ * such affine value can leave the int32 range in the launch box (the device
+ * computes in wrapping 32-bit arithmetic).  Programs with thread-dependent
+ * guards (the paper's Alg. 1 case, a heuristic) are not eligible.
+ * iter_budget: the context's back-edge budget (0 = 4096). */
+cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
+                            uint32_t iter_budget, uint32_t* eligible);
 
 /* Human-readable name of a status code. */
 const char* cufz_status_str(cufz_status s);

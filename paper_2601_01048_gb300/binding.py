@@ -20,9 +20,9 @@ OK = 0
 E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUND, \
     E_NO_DEVICE, E_DEVICE_FAULT, E_IO = range(-1, -11, -1)
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
-FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
+FL_BUDGET, FL_OVERFLOW, FL_NEW_COV, FL_PARTIAL = 1, 2, 4, 8
 CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \
-    CF_JIT, CF_JIT_FAST_COMPILE = 1, 2, 4, 8, 16, 32, 64, 128
+    CF_JIT, CF_JIT_FAST_COMPILE, CF_PREX = 1, 2, 4, 8, 16, 32, 64, 128, 256
 
 RESULT_DTYPE = np.dtype([
     ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),
@@ -84,7 +84,7 @@ EXPORTS = [
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
-    "cufz_unload_program", "cufz_verify_prune",
+    "cufz_unload_program", "cufz_verify_prune", "cufz_prex_check",
 ]
 
 
@@ -127,6 +127,7 @@ def lib():
                 "cufz_autotune": (i32, [vp, vp, u32, P(u32)]),
                 "cufz_unload_program": (i32, [vp, u32]),
                 "cufz_verify_prune": (i32, [vp, u32, vp, u32, P(u32)]),
+                "cufz_prex_check": (i32, [vp, sz, vp, u32, P(u32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -196,6 +197,15 @@ def cufz_load_program(ctx, prog: bytes) -> tuple[int, cufz_prog_stats]:
 
 def cufz_unload_program(ctx, program_id: int) -> None:
     _check(lib().cufz_unload_program(ctx, program_id), "cufz_unload_program")
+
+
+def cufz_prex_check(prog: bytes, inp: np.ndarray, iter_budget: int = 0) -> bool:
+    """Whether the corner threads of the input decide its verdict."""
+    inp = np.ascontiguousarray(np.asarray(inp, dtype=INPUT_DTYPE).reshape(1))
+    ok = ctypes.c_uint32(0)
+    _check(lib().cufz_prex_check(_bytes_ptr(prog), len(prog), inp.ctypes.data, iter_budget,
+                                 ctypes.byref(ok)), "cufz_prex_check")
+    return bool(ok.value)
 
 
 def cufz_verify_prune(ctx, program_id: int, inputs: np.ndarray) -> int:

@@ -8,6 +8,7 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -16,6 +17,14 @@
 namespace cufz {
 
 // ---------------------------------------------------------------- loader
+// A program's decoded form for the PREX check (Sec. 5.1).
+struct PrexInfo;
+
+// Whether the corner threads of input `in` decide its verdict: every branch
+// and loop trip uniform, every access index uniform or affine in the thread
+// and block indices, no affine value leaving int32 in the launch box.
+bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget);
+
 struct LoadedProgram {
   DevProgHdr hdr;
   uint8_t* blob = nullptr;   // host copy of the device blob
@@ -23,6 +32,7 @@ struct LoadedProgram {
   cufz_prog_stats stats{};
   uint32_t n_bufs = 0;
   uint32_t shared_mask = 0;
+  std::shared_ptr<const PrexInfo> prex;  // the program as given, for the PREX check
 };
 
 // Decodes and validates program bytes; fills `out` (device blob built with or

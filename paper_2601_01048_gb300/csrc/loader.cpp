@@ -904,11 +904,260 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
   return CUFZ_OK;
 }
 
+
+namespace {
+
+// ------------------------------------------------------------------ PREX
+// Partial representative execution (Sec. 5.1).  Theorem (Sec. 5.1.1): in a
+// kernel whose access indices are affine in the thread and block indices
+// with coefficients shared by all threads, and whose accesses sit under no
+// thread-dependent condition, a violating thread exists iff one of the
+// corner threads (every thread and block coordinate first or last) violates.
+// The check executes the program once on the host over abstract values:
+// uniform (one int32 for every thread), affine (exact integer coefficients
+// of tid.x/y/z, ctaid.x/y/z plus a constant) or other.  An input qualifies
+// when every branch decision and loop trip is uniform, every access index
+// is uniform or affine, and no affine value leaves the int32 range anywhere
+// in the launch box (the device computes in wrapping 32-bit arithmetic, so
+// an index that could wrap would not be affine).
+
+struct AVal {
+  uint8_t k = 0;  // 0 uniform, 1 affine, 2 other
+  int32_t u = 0;
+  int64_t c[6] = {0, 0, 0, 0, 0, 0};
+  int64_t b = 0;
+};
+
+constexpr int64_t kAffMax = (int64_t)1 << 40;  // coefficient bound of the exact arithmetic
+
+uint32_t host_fmix32(uint32_t h) {  // MurmurHash3 finalizer, as the device's mix32
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+int32_t uniform_alu(int op, int32_t x, int32_t y) {
+  const uint32_t ux = (uint32_t)x, uy = (uint32_t)y;
+  switch (op) {
+    case 0: return (int32_t)(ux + uy);
+    case 1: return (int32_t)(ux - uy);
+    case 2: return (int32_t)(ux * uy);
+    case 3: return (int32_t)(ux << (uy & 31u));
+    case 4: return x >> (int)(uy & 31u);
+    case 5: return (int32_t)(ux >> (uy & 31u));
+    case 6: return (int32_t)(ux & uy);
+    case 7: return (int32_t)(ux | uy);
+    case 8: return (int32_t)(ux ^ uy);
+    case 9: return x < y ? x : y;
+    case 10: return x > y ? x : y;
+    case 11: return x < y;
+    case 12: return x <= y;
+    case 13: return x == y;
+    case 14: return x != y;
+    default: return ux < uy;
+  }
+}
+
+struct PrexRun {
+  const Ir& ir;
+  const cufz_input& in;
+  uint32_t budget;
+  int64_t ext[6];  // largest value of each coordinate
+  std::vector<AVal> r;
+  uint64_t back = 0;
+  bool stopped = false;
+
+  static AVal uni(int32_t x) {
+    AVal v;
+    v.u = x;
+    return v;
+  }
+  static AVal other() {
+    AVal v;
+    v.k = 2;
+    return v;
+  }
+  static AVal as_affine(const AVal& x) {
+    if (x.k == 1) return x;
+    AVal v;
+    v.k = 1;
+    v.b = x.u;
+    return v;
+  }
+  // Range check of an affine value over the launch box; a value constant
+  // over the box becomes uniform.  False when it could leave int32.
+  bool norm(AVal& v) const {
+    if (v.k != 1) return true;
+    if (v.b > kAffMax || v.b < -kAffMax) return false;
+    int64_t lo = v.b, hi = v.b;
+    for (int k = 0; k < 6; k++) {
+      if (v.c[k] > kAffMax || v.c[k] < -kAffMax) return false;
+      const int64_t t = v.c[k] * ext[k];
+      (t > 0 ? hi : lo) += t;
+    }
+    if (lo < INT32_MIN || hi > INT32_MAX) return false;
+    if (lo == hi) {
+      v = uni((int32_t)lo);
+    }
+    return true;
+  }
+  static bool scale(AVal& v, int64_t s) {
+    for (int k = 0; k < 6; k++) {
+      const __int128 p = (__int128)v.c[k] * s;
+      if (p > kAffMax || p < -kAffMax) return false;
+      v.c[k] = (int64_t)p;
+    }
+    const __int128 p = (__int128)v.b * s;
+    if (p > kAffMax || p < -kAffMax) return false;
+    v.b = (int64_t)p;
+    return true;
+  }
+  AVal alu(int op, const AVal& x, const AVal& y) const {
+    if (x.k == 0 && y.k == 0) return uni(uniform_alu(op, x.u, y.u));
+    if (x.k == 2 || y.k == 2) return other();
+    AVal v;
+    switch (op) {
+      case 0:
+      case 1: {
+        const AVal a = as_affine(x), b = as_affine(y);
+        v.k = 1;
+        for (int k = 0; k < 6; k++) v.c[k] = op == 0 ? a.c[k] + b.c[k] : a.c[k] - b.c[k];
+        v.b = op == 0 ? a.b + b.b : a.b - b.b;
+        return v;
+      }
+      case 2:
+        if (x.k == 1 && y.k == 1) return other();
+        v = x.k == 1 ? x : y;
+        return scale(v, x.k == 1 ? y.u : x.u) ? v : other();
+      case 3:
+        if (y.k != 0) return other();
+        v = x;
+        return scale(v, (int64_t)1 << ((uint32_t)y.u & 31u)) ? v : other();
+      default:
+        return other();
+    }
+  }
+  AVal sreg(int id) const {
+    if (id <= 2 || (id >= 6 && id <= 8)) {
+      AVal v;
+      v.k = 1;
+      v.c[id <= 2 ? id : id - 3] = 1;
+      return v;
+    }
+    if (id <= 5) return uni((int32_t)in.block[id - 3]);
+    if (id <= 11) return uni((int32_t)in.grid[id - 9]);
+    return uni(in.args[id - 12]);
+  }
+  // The value a uniform index loads (0 when it violates or the buffer is shared).
+  AVal load(const IrOp& o, int32_t idx) const {
+    const int64_t w = o.width, off = (int64_t)idx * w;
+    const int64_t len = (int64_t)in.buf_len[o.buf];
+    if (off < 0 || off + w > len || ((ir.shared_mask >> o.buf) & 1u)) return uni(0);
+    const uint32_t word =
+        host_fmix32(ir.seed ^ ((uint32_t)o.buf * 0x9E3779B9u) ^ (uint32_t)((uint64_t)off >> 2));
+    return uni(w == 1 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word);
+  }
+  // Executes ops [pc, end); false as soon as the input does not qualify.
+  bool exec(int pc, int end) {
+    while (pc < end && !stopped) {
+      const IrOp& o = ir.ops[pc];
+      const uint8_t opc = o.opc;
+      if (is_alu_reg(opc) || is_alu_imm(opc)) {
+        const bool im = is_alu_imm(opc);
+        AVal v = alu(opc - (im ? 0x30 : 0x10), r[o.a], im ? uni(o.imm) : r[o.b]);
+        if (!norm(v)) return false;
+        r[o.dst] = v;
+        pc++;
+        continue;
+      }
+      switch (opc) {
+        case B_SREG: {
+          AVal v = sreg(o.sreg);
+          if (!norm(v)) return false;
+          r[o.dst] = v;
+          pc++;
+          break;
+        }
+        case B_IMM: r[o.dst] = uni(o.imm); pc++; break;
+        case B_MOV: r[o.dst] = r[o.a]; pc++; break;
+        case B_SEL: {
+          const AVal& cnd = r[o.a];
+          if (cnd.k == 0) r[o.dst] = cnd.u ? r[o.b] : r[o.c];
+          else if (r[o.b].k == 0 && r[o.c].k == 0 && r[o.b].u == r[o.c].u) r[o.dst] = r[o.b];
+          else r[o.dst] = other();
+          pc++;
+          break;
+        }
+        case B_LD:
+        case B_ST: {
+          const AVal idx = r[o.a];
+          if (idx.k == 2) return false;  // an index that is neither uniform nor affine
+          if (opc == B_LD) r[o.dst] = idx.k == 0 ? load(o, idx.u) : other();
+          pc++;
+          break;
+        }
+        case B_IF: {
+          if (r[o.a].k != 0) return false;  // a thread-dependent condition
+          const int then_end = o.else_pc >= 0 ? o.else_pc : o.end_pc;
+          if (r[o.a].u) {
+            if (!exec(pc + 1, then_end)) return false;
+          } else if (o.else_pc >= 0) {
+            if (!exec(o.else_pc + 1, o.end_pc)) return false;
+          }
+          pc = o.end_pc + 1;
+          break;
+        }
+        case B_LOOP: {
+          if (r[o.a].k != 0) return false;  // a thread-dependent trip count
+          const int32_t n = r[o.a].u;
+          const int32_t trip = n < 0 ? 0 : (n > o.imm ? o.imm : n);
+          int32_t k = 0;
+          for (; k < trip && !stopped; k++) {
+            r[o.dst] = uni(k);
+            if (!exec(pc + 1, o.end_pc)) return false;
+            if (stopped) break;
+            if (++back > budget) stopped = true;  // every thread stops here
+          }
+          if (!stopped) r[o.dst] = uni(trip);
+          pc = o.end_pc + 1;
+          break;
+        }
+        default: pc++; break;
+      }
+    }
+    return true;
+  }
+};
+
+bool prex_run(const Ir& ir, const cufz_input& in, uint32_t budget) {
+  PrexRun run{ir, in, budget, {}, std::vector<AVal>(std::max(ir.n_regs, 1))};
+  for (int d = 0; d < 3; d++) {
+    run.ext[d] = (int64_t)in.block[d] - 1;
+    run.ext[3 + d] = (int64_t)in.grid[d] - 1;
+  }
+  return run.exec(0, (int)ir.ops.size());
+}
+
+}  // namespace
+
 // ---------------------------------------------------------------- public
+
+struct PrexInfo {
+  Ir ir;  // the program as given (unpruned): PREX looks at every access
+};
+
+bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget) {
+  return prex_run(p.ir, in, iter_budget);
+}
 
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  auto prex = std::make_shared<PrexInfo>();
+  prex->ir = ir;
   int n_in = (int)ir.ops.size();
   if (do_prune) prune(&ir);
   propagate_sregs(&ir);
@@ -1039,6 +1288,7 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
   out->blob_bytes = bytes_total;
   out->n_bufs = (uint32_t)ir.n_bufs;
   out->shared_mask = ir.shared_mask;
+  out->prex = std::move(prex);
   fill_stats(ir, n_in, n_regs, &out->stats);
   return CUFZ_OK;
 }
@@ -1046,11 +1296,21 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
 void free_program(LoadedProgram* p) {
   free(p->blob);
   p->blob = nullptr;
+  p->prex.reset();
 }
 
 }  // namespace cufz
 
 using namespace cufz;
+
+extern "C" cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
+                                       uint32_t iter_budget, uint32_t* eligible) {
+  if (!bytes || !in || !eligible) return CUFZ_E_INVALID_ARG;
+  PrexInfo p;
+  if (!decode((const uint8_t*)bytes, nbytes, &p.ir)) return CUFZ_E_INVALID_PROGRAM;
+  *eligible = prex_input_ok(p, *in, iter_budget ? iter_budget : 4096u) ? 1u : 0u;
+  return CUFZ_OK;
+}
 
 extern "C" cufz_status cufz_validate_program(const void* bytes, size_t nbytes) {
   Ir ir;

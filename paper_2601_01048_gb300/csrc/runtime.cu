@@ -56,6 +56,7 @@ struct SlotHost {
   uint32_t lane = 0;
   uint64_t batch = 0;
   uint32_t prog = 0;  // program of the input in the slot
+  bool partial = false;  // PREX: only the corner threads run
 };
 
 struct Lane {
@@ -211,6 +212,7 @@ void harvest(cufz_ctx* c) {
       std::atomic_thread_fence(std::memory_order_acquire);
       cufz_result r;
       memcpy(&r, const_cast<const cufz_result*>(&c->done_h[s].res), sizeof(r));
+      if (sh.partial) r.flags |= CUFZ_FL_PARTIAL;
       c->ready.push_back(r);
       c->stats.inputs_completed++;
       if (c->cfg.flags & CUFZ_CF_AUTO_RELEASE) {
@@ -538,6 +540,33 @@ bool tune_cache_write(const cufz_ctx* c) {
     ok = ok && fprintf(f, "%016llx %u\n", (unsigned long long)kv.first, (unsigned)kv.second) > 0;
   ok = (fclose(f) == 0) && ok;
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
+}
+
+// PREX (Sec. 5.1.1): the linear ids g = block_lin * T + thread_lin of the
+// threads whose every thread and block coordinate is first or last, sorted.
+std::vector<uint32_t> corner_threads(const cufz_input& in) {
+  std::vector<uint32_t> t[3], b[3];
+  for (int d = 0; d < 3; d++) {
+    t[d] = {0u};
+    if (in.block[d] > 1) t[d].push_back(in.block[d] - 1);
+    b[d] = {0u};
+    if (in.grid[d] > 1) b[d].push_back(in.grid[d] - 1);
+  }
+  const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
+  std::vector<uint32_t> out;
+  for (uint32_t bz : b[2])
+    for (uint32_t by : b[1])
+      for (uint32_t bx : b[0])
+        for (uint32_t tz : t[2])
+          for (uint32_t ty : t[1])
+            for (uint32_t tx : t[0]) {
+              const uint64_t bl = bx + (uint64_t)in.grid[0] * (by + (uint64_t)in.grid[1] * bz);
+              const uint64_t tl = tx + (uint64_t)in.block[0] * (ty + (uint64_t)in.block[1] * tz);
+              out.push_back((uint32_t)(bl * T + tl));
+            }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
 }
 
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
@@ -871,6 +900,8 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   DevInput* dins = reinterpret_cast<DevInput*>(L->h_stage + 2 * sizeof(BatchHdr));
   uint32_t n_dev = 0;
   uint64_t batch_threads = 0;
+  const bool prex_on = (c->cfg.flags & CUFZ_CF_PREX) != 0 && !plain;
+  std::vector<std::vector<uint32_t>> corners;  // per device input under PREX
   std::vector<uint32_t> dev_slots;
   uint32_t accepted = 0;
   bool busy = false;
@@ -919,6 +950,15 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     sh.state = 1;
     sh.lane = lane_idx;
     sh.prog = x.program_id;
+    sh.partial = false;
+    if (prex_on && c->progs[x.program_id].prex &&
+        prex_input_ok(*c->progs[x.program_id].prex, x, c->T.iter_budget)) {
+      // the corner threads decide the verdict: run only them
+      corners.resize(n_dev + 1);
+      corners[n_dev] = corner_threads(x);
+      d->n_threads = corners[n_dev].size();
+      sh.partial = true;
+    }
     c->ticket_slot[ticket] = s;
     dev_slots.push_back(s);
     batch_threads += d->n_threads;
@@ -940,10 +980,12 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
                      [&](uint32_t x, uint32_t y) { return dins[x].prog < dins[y].prog; });
     auto compiled = [&](uint32_t prog) { return use_jit(c) && c->prog_compiled[prog]; };
     uint64_t want[2] = {0, 0};
+    corners.resize(n_dev);
     for (uint32_t i = 0; i < n_dev; i++) {
       DevInput* d = &dins[i];
       d->n_items = plain ? (uint32_t)(d->n_threads / d->T)
-                         : (uint32_t)((d->n_threads + item - 1) / item);
+                 : !corners[i].empty() ? (uint32_t)corners[i].size()  // one item per corner thread
+                                       : (uint32_t)((d->n_threads + item - 1) / item);
       if (!plain) want[compiled(d->prog) ? 0 : 1] += d->n_items;
     }
     if (want[0] + want[1] > c->lane_max_items) {
@@ -967,9 +1009,14 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
         for (uint32_t k = 0; k < d->n_items; k++) {
           WorkItem& w = lists[li][counts[li]++];
           w.input = i;
-          w.g0 = k * item;
-          uint64_t rem = d->n_threads - (uint64_t)k * item;
-          w.count = (uint32_t)std::min<uint64_t>(rem, item);
+          if (!corners[i].empty()) {
+            w.g0 = corners[i][k];
+            w.count = 1;
+          } else {
+            w.g0 = k * item;
+            uint64_t rem = d->n_threads - (uint64_t)k * item;
+            w.count = (uint32_t)std::min<uint64_t>(rem, item);
+          }
           w.pad = 0;
         }
       }

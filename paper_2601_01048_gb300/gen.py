@@ -235,6 +235,67 @@ def c3_inputs(n: int = 4096, seed: int | None = None, max_blocks: int = 65536,
 
 
 # --------------------------------------------------------------------------
+# PREX workload: unguarded affine-access programs (Sec. 5.1's class, like the
+# paper's vecadd/matmul/aes), launch shapes as configuration 3
+# --------------------------------------------------------------------------
+
+AFF_WIDTHS = (4, 8, 4, 1, 16, 4, 4, 8, 4, 1, 4, 16, 4, 8, 4, 4)
+
+
+def affine_family_program(off: int, w: int, k_inner: int, seed: int) -> bytes:
+    """i = ctaid.x * ntid.x + tid.x + arg0; loads A[i], B[i + off] (width w),
+    a uniform loop over k < min(arg1, 8) reading C[i * k_inner + k], a store
+    D[i]; no thread-dependent branch (the affine-access class)."""
+    A = Asm(n_bufs=4, seed=seed)
+    tx, bx, nx = A.sreg(bc.TID_X), A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)
+    a0, a1 = A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    i = A.alu(bc.ADD, A.alu(bc.ADD, A.alu(bc.MUL, bx, nx), tx), a0)
+    A.ld(0, i, 4)
+    A.ld(1, A.alu(bc.ADD, i, Imm(off)), w)
+    k = A.loop(a1, 8)
+    A.ld(2, A.alu(bc.ADD, A.alu(bc.MUL, i, Imm(k_inner)), k), 4)
+    A.endloop()
+    A.st(3, i, tx, 4)
+    return A.build()
+
+
+def affine_programs() -> list[bytes]:
+    rng = SplitMix64(sub_seed("affprog"))
+    return [affine_family_program(rng.randint(-2, 2), AFF_WIDTHS[p], rng.randint(1, 4),
+                                  seed=rng.next32()) for p in range(16)]
+
+
+def affine_inputs(n: int = 4096, seed: int | None = None, max_blocks: int = 65536,
+                  min_threads: int = 32, max_threads: int = 1024) -> np.ndarray:
+    """Configuration-3 shapes; each buffer sized for the grid, one in ten an
+    element short (the off-by-one bug PREX must still find)."""
+    rng = SplitMix64(sub_seed("aff") if seed is None else seed)
+    progs_k = []
+    rk = SplitMix64(sub_seed("affprog"))
+    for p in range(16):
+        rk.randint(-2, 2)
+        progs_k.append(rk.randint(1, 4))
+        rk.next32()
+    out = make_inputs(n)
+    for k in range(n):
+        p = rng.below(16)
+        nb = rng.loguniform_int(1, max_blocks)
+        nt = rng.loguniform_int(min_threads, max_threads)
+        total = nb * nt
+        a0 = rng.randint(-1, 1)
+        a1 = rng.randint(0, 8)
+        ws = (4, AFF_WIDTHS[p], 4, 4)
+        lens = []
+        for b in range(4):
+            e = total + 2 if b != 2 else total * progs_k[p] + 8
+            if rng.uniform() < 0.10:
+                e -= 3
+            lens.append(ws[b] * e)
+        set_input(out[k], p, (nb, 1, 1), (nt, 1, 1), (a0, a1), lens, tag=k)
+    return out
+
+
+# --------------------------------------------------------------------------
 # config 2: random 2D programs with shared buffers and loops
 # --------------------------------------------------------------------------
 
