@@ -2,8 +2,10 @@
  * cufz.h - C ABI of the GB300 checked-execution engine.
  *
  * The engine runs a kernel under test, given as an integer access-index
- * program, over its full grid once per fuzz input; it checks every load and
- * store against its buffer's bounds and records AFL-style edge coverage.
+ * program, over its full grid once per fuzz input (or, with CUFZ_CF_PREX,
+ * over the corner threads that decide the verdict, Sec. 5.1); it checks
+ * every load and store against its buffer's bounds and records AFL-style
+ * edge coverage.
  * This is the work the paper moves to the CPU through IR translation and
  * AddressSanitizer (Sec. 4, Fig. 2: translate, instrument with ASan and AFL,
  * run every GPU thread of every block) and then reduces with AXIPrune

@@ -19,11 +19,12 @@
 // ballot: one atomicAdd reserves their record slots, ranks come from popc.
 //
 // Coverage (Sec. 2.1, AFL payload after branches): e = (loc ^ prev) & 0xFFFF,
-// prev = loc >> 1.  Lanes with equal e are merged with __match_any_sync and
-// the group leader adds the group size into a per-CTA shared-memory hash
-// table; the table is flushed into the slot's global counters after each
-// item, and the last CTA of an input buckets the counts into the 64 KiB
-// bitmap and ORs them into the device union.
+// prev = loc >> 1.  Lanes whose edge already reached 128 in the CTA's table
+// skip it (its bucket is final); the others are merged by equal e with
+// __match_any_sync and the group leader adds the group size into the per-CTA
+// shared-memory hash table; the table is flushed into the slot's global
+// counters after each item, and the last CTA of an input buckets the counts
+// into the 64 KiB bitmap and ORs them into the device union.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

@@ -1,11 +1,11 @@
-// Device helpers for programs compiled at load time.  The loader emits one
-// function per program (straight-line CUDA: program registers become local
-// variables, buffer/width/site/LOC values become constants); these helpers
-// are what the emitted code calls for checks, records and coverage.  The
-// emitted code runs each test thread as one CUDA thread; lanes that take the
-// same path are aggregated with __activemask() groups.  Per access the
-// emitted code keeps counts, the first violating access and the digest in
-// registers; jit_record runs only while the input's record area has room.
+// Device helpers for programs compiled at load time.  The loader emits two
+// functions per program (straight-line CUDA: program registers become local
+// variables, buffer/width/site/LOC values become constants), each running
+// one test thread per CUDA thread: a work-item function that counts
+// accesses, violations and branch evaluations, folds the digest and updates
+// edges, with no record code; and a record function that re-runs one
+// violating thread to write its records (jit_record, active-mask groups) and
+// find its first violation.  These helpers are what the emitted code calls.
 #pragma once
 
 #include "device_common.cuh"
