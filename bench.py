@@ -46,13 +46,14 @@ LANES_PER_SM = 128
 TRAFFIC_SOURCES = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h",
                    "loader.cpp")
 TRAFFIC_BYTES: dict[str, tuple[str, int]] = {
-    "c2": ("0002e7d174e59cf5", 58_376_448 + 1_471_800_576),
+    "c2": ("e9e30ca7f27a2f57", 58_376_448 + 1_471_800_576),
 }
 
 
 def _code_only(text: str) -> str:
-    """The source without comments and blank lines (string and character
-    literals kept as they are), so that comment edits keep the hash."""
+    """The source without comments, blank lines and runs of whitespace
+    (string and character literals kept), so that comment and layout edits
+    keep the hash."""
     out, i, n = [], 0, len(text)
     while i < n:
         c = text[i]
@@ -71,7 +72,7 @@ def _code_only(text: str) -> str:
         else:
             out.append(c)
             i += 1
-    return "\n".join(l.rstrip() for l in "".join(out).split("\n") if l.strip())
+    return "\n".join(" ".join(l.split()) for l in "".join(out).split("\n") if l.strip())
 
 
 def kernel_sources_sha() -> str:

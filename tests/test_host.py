@@ -29,8 +29,32 @@ def test_library_exports_every_declared_function():
 
 
 def test_status_strings():
-    for st in range(0, -10, -1):
-        assert B.cufz_status_str(st)
+    for st in range(0, -11, -1):
+        assert B.cufz_status_str(st) and B.cufz_status_str(st) != b"unknown status"
+
+
+def test_header_constants_match_binding():
+    """Every CUFZ_E_/ST_/FL_/CF_ constant of the header has the same value in
+    the binding (they are written twice: C for the ABI, Python for ctypes)."""
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "cufz.h")).read()
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define CUFZ_((?:E|ST|FL|CF)_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", hdr)}
+    assert len(defs) >= 25
+    for name, value in defs.items():
+        assert getattr(B, name) == value, name
+
+
+def test_traffic_key_ignores_comments_only():
+    """The bench's DRAM-traffic figure is keyed by the kernel code without
+    comments: comments and blank lines do not change the key, code does."""
+    import bench
+    code = 'int f(int x) {  // twice\n  /* c */ return 2 * x;\n}\nconst char* s = "// kept";\n'
+    same = 'int f(int x) {\n\n  return 2 * x;  // doubled\n}\nconst char* s = "// kept";\n'
+    assert bench._code_only(code) == bench._code_only(same)
+    assert bench._code_only(code) != bench._code_only(code.replace("2 * x", "3 * x"))
+    assert '"// kept"' in bench._code_only(code)
 
 
 def all_programs():
