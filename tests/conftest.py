@@ -30,3 +30,16 @@ def orc():
     from oracle import oracle
     oracle.lib()
     return oracle
+
+
+RECORD_KEYS = ("block_lin", "thread_lin", "ordinal", "site", "buf", "kind", "width", "space", "cls",
+               "byte_off")
+
+
+def record_keys(recs):
+    """A record array (engine or oracle) as the sorted list of its records'
+    identifying fields, for comparing record sets."""
+    if recs is None or len(recs) == 0:
+        return []
+    return sorted(zip(*(recs[c].tolist() for c in RECORD_KEYS)))
+

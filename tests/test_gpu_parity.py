@@ -6,6 +6,7 @@ import pytest
 
 from paper_2601_01048_gb300 import bytecode as bc
 from paper_2601_01048_gb300 import gen
+from conftest import record_keys
 
 pytestmark = pytest.mark.gpu
 
@@ -23,10 +24,6 @@ def B():
     return binding
 
 
-def keyed(recs):
-    cols = ("block_lin", "thread_lin", "ordinal", "site", "buf", "kind", "width", "space", "cls",
-            "byte_off")
-    return sorted(tuple(int(r[c]) for c in cols) for r in recs)
 
 
 def compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap, check_newcov=False):
@@ -45,13 +42,13 @@ def compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap, check_new
                 assert np.array_equal(dbms[i], obms[i]), "bitmap"
             if drecs is not None:
                 n_o = int(o["n_violations"])
-                dk = keyed(drecs[i])
+                dk = record_keys(drecs[i])
                 if n_o <= cap:
-                    assert dk == keyed(orecs[i][:n_o]), "records"
+                    assert dk == record_keys(orecs[i][:n_o]), "records"
                 else:
                     assert len(dk) == cap and int(d["n_records"]) == cap
                     if orecs is not None and len(orecs[i]) >= n_o:
-                        assert set(dk) <= set(keyed(orecs[i][:n_o])), "record subset"
+                        assert set(dk) <= set(record_keys(orecs[i][:n_o])), "record subset"
         except AssertionError as e:
             bad.append((i, str(e), d, o))
     assert not bad, f"{len(bad)} mismatches, first: {bad[0]}"
@@ -150,7 +147,7 @@ def test_c2_unpruned_digest_equal(B, orc, path):
     assert np.array_equal(b0, b1)
     for k, (a, b) in enumerate(zip(c0, c1)):
         if int(r0[k]["n_violations"]) <= cap:   # overflowed record sets are any cap-subset
-            assert keyed(a) == keyed(b)
+            assert record_keys(a) == record_keys(b)
     assert np.all(r0["n_ops"] <= r1["n_ops"]) and r0["n_ops"].sum() < r1["n_ops"].sum()
 
 

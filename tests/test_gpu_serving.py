@@ -5,6 +5,7 @@ import numpy as np
 import pytest
 
 from paper_2601_01048_gb300 import gen
+from conftest import record_keys
 
 pytestmark = pytest.mark.gpu
 
@@ -19,10 +20,6 @@ def B():
     return binding
 
 
-def keyed(recs):
-    cols = ("block_lin", "thread_lin", "ordinal", "site", "buf", "kind", "width", "space", "cls",
-            "byte_off")
-    return sorted(tuple(int(r[c]) for c in cols) for r in recs)
 
 
 FIELDS = ("status", "flags", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
@@ -56,4 +53,4 @@ def test_alone_equals_in_mix(B, path):
                 assert int(alone[0][f]) == int(mix[i][f]), (i, f)
             assert np.array_equal(bms[0], kept[i][1]), i
             if int(alone[0]["n_violations"]) <= cap:
-                assert keyed(recs[0]) == keyed(kept[i][0]), i
+                assert record_keys(recs[0]) == record_keys(kept[i][0]), i

@@ -8,6 +8,7 @@ library, shared by every call, so two calls in a row must not see each
 other's leftovers.  This file is collected last on purpose."""
 import numpy as np
 import pytest
+from conftest import record_keys
 
 pytestmark = pytest.mark.gpu
 
@@ -15,10 +16,6 @@ FIELDS = ("status", "n_accesses", "n_violations", "first_key", "digest", "n_bran
           "n_threads", "n_records", "n_edges")
 
 
-def keyed(recs):
-    cols = ("block_lin", "thread_lin", "ordinal", "site", "buf", "kind", "width", "space", "cls",
-            "byte_off")
-    return sorted(tuple(int(r[c]) for c in cols) for r in recs)
 
 
 def test_noalloc_matches_context_on_two_calls_in_a_row():
@@ -60,6 +57,6 @@ def test_noalloc_matches_context_on_two_calls_in_a_row():
         n = int(res["n_records"])
         recs = np.frombuffer(records.cpu().numpy().tobytes(), dtype=B.VIOLATION_DTYPE)[:n]
         assert int(ref[k]["n_violations"]) <= cap          # record sets are unique then
-        assert keyed(recs) == keyed(ref_recs[k])
+        assert record_keys(recs) == record_keys(ref_recs[k])
         assert np.array_equal(bitmap.cpu().numpy(), ref_bms[k])
     assert int(ref[0]["n_violations"]) > 0 and int(ref[1]["n_edges"]) > 0
