@@ -397,6 +397,44 @@ def test_prex_corner_theorem(orc):
     assert checked > 20
 
 
+def test_prex_guarded_1d_interval_theorem(orc):
+    """The extension of Sec. 5.1.1's theorem to guarded 1D kernels (the case
+    the paper leaves to its heuristic Alg. 1): when every value is affine in
+    lin = ctaid.x * ntid.x + tid.x and the guard is `lin + c < a1`, the threads
+    reaching the accesses are an interval of lin, so the threads at 0, N - 1
+    and the guard's threshold t = a1 - c (and t +- 1) decide, site by site,
+    whether any thread violates.  Checked on configuration 3's guarded
+    program family over random small launches with off-by-one lengths."""
+    rng = gen.SplitMix64(99)
+    progs = gen.c3_programs()
+    offsets = []
+    rp = gen.SplitMix64(gen.sub_seed("c3prog"))
+    for p in range(16):
+        offsets.append(rp.randint(-3, 3) if p else 0)
+        rp.next32()
+    sites_checked = 0
+    for trial in range(120):
+        p = trial % 16
+        w = gen.C3_WIDTHS[p]
+        nb, nt = rng.randint(1, 9), rng.randint(1, 40)
+        n = nb * nt
+        a0, a1 = rng.randint(-4, 4), rng.randint(-2, n + 3)
+        lens = [w * max(rng.randint(a1 - 3, a1 + 2), 0) for _ in range(4)]
+        res, recs, _ = orc.run(orc.Program(progs[p]), mk((nb, 1, 1), (nt, 1, 1), (a0, a1), lens),
+                               rec_cap=1 << 16)
+        assert int(res["n_records"]) == int(res["n_violations"])
+        t = a1 - (a0 + offsets[p])
+        cand = {0, n - 1} | {v for v in (t - 1, t, t + 1) if 0 <= v < n}
+
+        def lin(r):
+            return int(r["block_lin"]) * nt + int(r["thread_lin"])
+
+        sites = {int(r["site"]) for r in recs}
+        assert sites == {int(r["site"]) for r in recs if lin(r) in cand}
+        sites_checked += len(sites)
+    assert sites_checked > 40
+
+
 # ---------------------------------------------------------------- brute force
 
 def _compare_bruteforce(orc, prog, inp_kwargs, budget=4096):
