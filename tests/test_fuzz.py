@@ -1,0 +1,112 @@
+"""The fuzzing campaign's host logic (queue, corpus, bug buckets,
+checkpoints) against a fake executor with a deterministic coverage and bug
+model; the engine behind the real executor is tested on the GPU elsewhere."""
+import numpy as np
+
+from paper_2601_01048_gb300 import binding as B
+from paper_2601_01048_gb300 import gen
+from paper_2601_01048_gb300.fuzz import Campaign
+
+VIOL = np.dtype([("site", "<u2"), ("cls", "u1")])
+
+
+class FakeExecutor:
+    """Edges of an input: (program, arg0 // 64, len0 // 256); it violates
+    when len0 < 100, at site arg1 & 3 with class 1 + (len0 & 1).  NEW_COV and
+    the union follow the engine's rules (snapshot at each epoch)."""
+
+    def __init__(self):
+        self.union_set, self.snapshot = set(), set()
+        self.log = []
+
+    @staticmethod
+    def edges(x):
+        p = int(x["program_id"])
+        return {(p, 0, int(x["args"][0]) // 64), (p, 1, int(x["buf_len"][0]) // 256)}
+
+    def run(self, inputs):
+        res = np.zeros(len(inputs), B.RESULT_DTYPE)
+        first = []
+        for k, x in enumerate(inputs):
+            e = self.edges(x)
+            if e - self.snapshot:
+                res[k]["flags"] |= B.FL_NEW_COV
+            self.union_set |= e
+            bad = int(x["buf_len"][0]) < 100
+            res[k]["status"] = B.ST_VIOLATION if bad else B.ST_OK
+            if bad:
+                r = np.zeros(1, VIOL)[0]
+                r["site"], r["cls"] = int(x["args"][1]) & 3, 1 + (int(x["buf_len"][0]) & 1)
+                first.append(r)
+            else:
+                first.append(None)
+        self.log.append(len(inputs))
+        return res, first
+
+    def new_epoch(self):
+        self.snapshot = set(self.union_set)
+
+    def union(self):
+        return self.union_set
+
+
+def seeds(n=6):
+    s = gen.make_inputs(n)
+    for k in range(n):
+        gen.set_input(s[k], k % 2, (4, 1, 1), (64, 1, 1), (k * 10, k), (1000 + k, 500, 500))
+    return s
+
+
+def test_corpus_grows_with_new_coverage_only_and_buckets_dedupe():
+    ex = FakeExecutor()
+    c = Campaign(ex, [3, 3], seeds(), seed=7, batch=32)
+    assert ex.log == [6]                                       # the dry run
+    total_new, buckets = 0, 0
+    for _ in range(12):
+        before = len(c.corpus)
+        snapshot = set(ex.snapshot)                            # the union when the round starts
+        st = c.run_round()
+        assert st.executed == 32 and st.corpus_size == before + st.new_coverage
+        # every entry the round added has an edge the union lacked at its start
+        for x in c.corpus[before:]:
+            assert ex.edges(x) - snapshot
+        total_new += st.new_coverage
+        buckets += st.new_buckets
+    assert total_new > 0 and len(c.corpus) == 6 + total_new
+    assert buckets == len(c.buckets) > 0
+    assert sum(b["hits"] for b in c.buckets.values()) >= buckets
+    # the union is the OR of the corpus's coverage
+    cov = set()
+    for x in c.corpus:
+        cov |= ex.edges(x)
+    assert cov == ex.union_set
+
+
+def test_new_entries_are_picked_first():
+    ex = FakeExecutor()
+    c = Campaign(ex, [3, 3], seeds(), seed=3, batch=8)
+    c.run_round()
+    c.run_round()
+    fav = np.flatnonzero(c.favoured)
+    if len(fav):
+        parents = c._parents()
+        assert set(parents[: len(fav)].tolist()) == set(fav.tolist())
+
+
+def test_checkpoint_resume_continues_exactly(tmp_path):
+    a_ex = FakeExecutor()
+    a = Campaign(a_ex, [3, 3], seeds(), seed=11, batch=16)
+    for _ in range(4):
+        a.run_round()
+    path = str(tmp_path / "ckpt")
+    a.checkpoint(path)
+    union_at_ckpt = set(a_ex.union_set)
+    after_a = [a.run_round() for _ in range(5)]
+
+    b_ex = FakeExecutor()
+    b = Campaign.resume(path, b_ex)
+    assert b_ex.union_set == union_at_ckpt                    # rebuilt by running the corpus
+    after_b = [b.run_round() for _ in range(5)]
+    assert after_a == after_b
+    assert np.array_equal(a.corpus, b.corpus) and a.rounds == b.rounds == 9
+    assert {k: v["hits"] for k, v in a.buckets.items()} == {k: v["hits"] for k, v in b.buckets.items()}
