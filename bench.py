@@ -40,13 +40,13 @@ N_SM_GB300 = 152
 LANES_PER_SM = 128
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one launch of
 # the dominant kernel on a whole workload, from one ncu capture (the command
-# is in profiles/), keyed by the hash of the compiled-path sources it was
-# taken on (their code without comments): once that code changes the figure
-# no longer applies and is reported as null.
-TRAFFIC_SOURCES = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h",
-                   "loader.cpp")
+# is in profiles/), keyed by a hash of that kernel: the device headers of the
+# compiled path (code without comments) and the CUDA the loader emits for the
+# workload's programs, with the module's launch shape.  Once the kernel
+# changes the figure no longer applies and is reported as null.
+TRAFFIC_HEADERS = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h")
 TRAFFIC_BYTES: dict[str, tuple[str, int]] = {
-    "c2": ("e9e30ca7f27a2f57", 58_376_448 + 1_471_800_576),
+    "c2": ("87b412013a63f0b3", 58_376_448 + 1_471_800_576),
 }
 
 
@@ -75,20 +75,28 @@ def _code_only(text: str) -> str:
     return "\n".join(" ".join(l.split()) for l in "".join(out).split("\n") if l.strip())
 
 
-def kernel_sources_sha() -> str:
+def kernel_key(programs, cta_threads: int = 256, min_ctas: int = 3) -> str:
+    """Hash of the compiled module a workload runs: device headers, the
+    emitted code of each program, the module's launch shape."""
+    from paper_2601_01048_gb300 import binding as B
+
     h = hashlib.sha256()
-    for name in TRAFFIC_SOURCES:
+    for name in TRAFFIC_HEADERS:
         with open(os.path.join(ROOT, "paper_2601_01048_gb300", "csrc", name), encoding="utf-8") as f:
             h.update(_code_only(f.read()).encode())
+    for p in programs:
+        h.update(_code_only(B.cufz_program_cuda(p)).encode())
+    h.update(f"cta_threads={cta_threads} min_ctas={min_ctas}".encode())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(args, per_step: int, n_all: int):
-    """DRAM bytes per launch if captured for this workload and these sources."""
+def measured_traffic(args, programs, per_step: int, n_all: int):
+    """DRAM bytes per launch if captured for this workload and this kernel."""
     entry = TRAFFIC_BYTES.get(args.workload)
-    if entry is None or per_step != n_all or args.plain or args.path != "jit":
+    if (entry is None or per_step != n_all or args.plain or args.path != "jit"
+            or args.cta_threads not in (0, 256) or args.jit_min_ctas not in (0, 3)):
         return None
-    return entry[1] if entry[0] == kernel_sources_sha() else None
+    return entry[1] if entry[0] == kernel_key(programs) else None
 
 
 # algorithmic integer ops per checked access and per branch evaluation
@@ -429,8 +437,8 @@ def run_engine(args, rank, world, local, pg):
             "peak": peak_ops / 1e12,
             "unit": "Tops/s (int32 lane-ops)",
             "frac": achieved / peak_ops,
-            "traffic": measured_traffic(args, per_step, n_all),
-            "kernel_sources_sha": kernel_sources_sha(),
+            "traffic": measured_traffic(args, progs, per_step, n_all),
+            "kernel_key": kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3),
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
             "alg_ops_per_step": alg_ops // max(args.steps, 1),
             "measured_int32_peak": measured_peak / 1e12 if measured_peak else None,
