@@ -250,6 +250,30 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
 cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
                             uint32_t iter_budget, uint32_t* eligible);
 
+/* PREX plan (Sec. 5.1): the test threads whose execution decides whether any
+ * thread of `in`'s grid violates, as sorted linear ids g = block_lin * T +
+ * thread_lin (T = threads per block), written to threads[0 .. *n_threads).
+ * Two rules give a plan:
+ *   - corners: cufz_prex_check's rule; the plan is the corner threads;
+ *   - guarded 1D lines (the guarded kernels of Sec. 5.1's Alg. 1, decided
+ *     exactly rather than heuristically): a launch with grid and block 1D
+ *     (y = z = 1), whose values are thread-invariant or affine in the linear
+ *     thread id t = ctaid.x * ntid.x + tid.x (no int32 wrap in the box), and
+ *     whose branch conditions compare such values (<, <=, ==, !=) or test an
+ *     affine value against zero.  Each comparison's truth changes at most
+ *     once along t; the plan is t = 0, t = n-1 and the threads around each
+ *     comparison's change point.  Between consecutive planned threads every
+ *     condition is constant, so each access index is affine there, and an
+ *     interval's violation shows at one of its ends.  Branches are explored
+ *     both ways, loops need a thread-invariant trip, and iter_budget bounds
+ *     the abstract back-edges (0 = 4096).
+ * *n_threads = 0 when neither rule applies (run the full grid).  CUFZ_E_NOMEM
+ * when the plan has more than cap threads (*n_threads gives the size).
+ * Host-only; no device needed. */
+cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* in,
+                           uint32_t iter_budget, uint32_t* threads, uint32_t cap,
+                           uint32_t* n_threads);
+
 /* Human-readable name of a status code. */
 const char* cufz_status_str(cufz_status s);
 

@@ -85,6 +85,7 @@ EXPORTS = [
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
     "cufz_unload_program", "cufz_verify_prune", "cufz_prex_check",
+    "cufz_prex_plan",
 ]
 
 
@@ -128,6 +129,7 @@ def lib():
                 "cufz_unload_program": (i32, [vp, u32]),
                 "cufz_verify_prune": (i32, [vp, u32, vp, u32, P(u32)]),
                 "cufz_prex_check": (i32, [vp, sz, vp, u32, P(u32)]),
+                "cufz_prex_plan": (i32, [vp, sz, vp, u32, P(u32), u32, P(u32)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -206,6 +208,24 @@ def cufz_prex_check(prog: bytes, inp: np.ndarray, iter_budget: int = 0) -> bool:
     _check(lib().cufz_prex_check(_bytes_ptr(prog), len(prog), inp.ctypes.data, iter_budget,
                                  ctypes.byref(ok)), "cufz_prex_check")
     return bool(ok.value)
+
+
+def cufz_prex_plan(prog: bytes, inp: np.ndarray, iter_budget: int = 0) -> np.ndarray | None:
+    """The linear ids of the threads that decide the input's verdict, or None
+    when no PREX rule applies."""
+    inp = np.ascontiguousarray(np.asarray(inp, dtype=INPUT_DTYPE).reshape(1))
+    n = ctypes.c_uint32(0)
+    cap = 256
+    while True:
+        out = np.zeros(cap, dtype=np.uint32)
+        st = lib().cufz_prex_plan(_bytes_ptr(prog), len(prog), inp.ctypes.data, iter_budget,
+                                  out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32)), cap,
+                                  ctypes.byref(n))
+        if st == E_NOMEM:
+            cap = int(n.value)
+            continue
+        _check(st, "cufz_prex_plan")
+        return out[: n.value].copy() if n.value else None
 
 
 def cufz_verify_prune(ctx, program_id: int, inputs: np.ndarray) -> int:

@@ -25,6 +25,17 @@ struct PrexInfo;
 // and block indices, no affine value leaving int32 in the launch box.
 bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget);
 
+// The corner threads of `in` (every coordinate first or last) as linear ids
+// g = block_lin * T + thread_lin, sorted.
+std::vector<uint32_t> prex_corners(const cufz_input& in);
+
+// The threads whose verdict is the whole grid's: the corners when
+// prex_input_ok holds, else, for a 1D launch whose values are affine in the
+// linear thread id and whose guards compare such values, the first and last
+// thread and each guard's threshold neighbourhood.  False when neither holds.
+bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
+               std::vector<uint32_t>* threads);
+
 struct LoadedProgram {
   DevProgHdr hdr;
   uint8_t* blob = nullptr;   // host copy of the device blob

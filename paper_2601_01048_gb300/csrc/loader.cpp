@@ -1132,6 +1132,269 @@ struct PrexRun {
   }
 };
 
+
+// Guarded 1D kernels (the case Sec. 5.1.2 leaves to the heuristic Alg. 1),
+// exactly.  With one-dimensional blocks and grid, a value affine in (tx, bx)
+// with c_b = c_t * nx is affine in the linear thread id lin = bx * nx + tx
+// (lin in [0, N), N = nx * gx).  When every guard compares such values, the
+// threads that reach an access form intervals of lin bounded by 0, N - 1 and
+// the guards' thresholds, and an access index affine in lin violates
+// somewhere in an interval iff it does at one of its ends.  So the threads at
+// 0, N - 1 and each threshold (with its neighbours) decide the verdict.  Both
+// sides of a guard are executed (registers that differ between them become
+// "other" at the join); loops need a thread-invariant trip count, and no
+// path may reach the iteration budget.
+
+struct LVal {
+  uint8_t k = 0;  // 0 uniform, 1 affine in (tx, bx), 2 predicate "d op 0" on lin, 3 other
+  int32_t u = 0;
+  int64_t ct = 0, cb = 0, b = 0;  // affine: ct * tx + cb * bx + b (exact)
+  int op = 0;                      // predicate: 11 <, 12 <=, 13 ==, 14 !=, on d = ct * lin + b
+  bool operator==(const LVal& o) const {
+    return k == o.k && u == o.u && ct == o.ct && cb == o.cb && b == o.b && op == o.op;
+  }
+};
+
+struct PrexLine {
+  const Ir& ir;
+  const cufz_input& in;
+  uint32_t budget;
+  int64_t nx, gx, n;  // block size, grid size, threads
+  std::vector<int64_t> thresholds;
+
+  static LVal uni(int32_t x) {
+    LVal v;
+    v.u = x;
+    return v;
+  }
+  static LVal other() {
+    LVal v;
+    v.k = 3;
+    return v;
+  }
+  static LVal affine(int64_t ct, int64_t cb, int64_t b) {
+    LVal v;
+    v.k = 1;
+    v.ct = ct;
+    v.cb = cb;
+    v.b = b;
+    return v;
+  }
+  // Range check over the launch; affine values constant over it become uniform.
+  bool norm(LVal& v) const {
+    if (v.k != 1) return true;
+    for (int64_t c : {v.ct, v.cb, v.b})
+      if (c > kAffMax || c < -kAffMax) return false;
+    int64_t lo = v.b, hi = v.b;
+    const int64_t t1 = v.ct * (nx - 1), t2 = v.cb * (gx - 1);
+    (t1 > 0 ? hi : lo) += t1;
+    (t2 > 0 ? hi : lo) += t2;
+    if (lo < INT32_MIN || hi > INT32_MAX) return false;
+    if (lo == hi) v = uni((int32_t)lo);
+    return true;
+  }
+  // Coefficient of lin when v is affine in lin; false otherwise.
+  bool lin_coef(const LVal& v, int64_t* a) const {
+    if (gx == 1) {
+      *a = v.ct;
+      return true;
+    }
+    if (nx == 1) {
+      *a = v.cb;
+      return true;
+    }
+    if (v.cb != v.ct * nx) return false;
+    *a = v.ct;
+    return true;
+  }
+  static bool scale(LVal& v, int64_t s) {
+    for (int64_t* c : {&v.ct, &v.cb, &v.b}) {
+      const __int128 p = (__int128)*c * s;
+      if (p > kAffMax || p < -kAffMax) return false;
+      *c = (int64_t)p;
+    }
+    return true;
+  }
+  LVal as_affine(const LVal& x) const { return x.k == 1 ? x : affine(0, 0, x.u); }
+  LVal alu(int op, const LVal& x, const LVal& y) {
+    if (x.k == 0 && y.k == 0) return uni(uniform_alu(op, x.u, y.u));
+    if (x.k >= 2 || y.k >= 2) return other();
+    switch (op) {
+      case 0:
+      case 1: {
+        const LVal a = as_affine(x), c = as_affine(y);
+        return op == 0 ? affine(a.ct + c.ct, a.cb + c.cb, a.b + c.b)
+                       : affine(a.ct - c.ct, a.cb - c.cb, a.b - c.b);
+      }
+      case 2: {
+        if (x.k == 1 && y.k == 1) return other();
+        LVal v = x.k == 1 ? x : y;
+        return scale(v, x.k == 1 ? y.u : x.u) ? v : other();
+      }
+      case 3: {
+        if (y.k != 0) return other();
+        LVal v = x;
+        return scale(v, (int64_t)1 << ((uint32_t)y.u & 31u)) ? v : other();
+      }
+      case 11:
+      case 12:
+      case 13:
+      case 14: {  // a signed comparison of affine values: a predicate on lin
+        const LVal a = as_affine(x), c = as_affine(y);
+        LVal d = affine(a.ct - c.ct, a.cb - c.cb, a.b - c.b);
+        int64_t al = 0;
+        if (!norm(d)) return other();
+        if (d.k == 0)  // the coefficients cancel: the same comparison in every thread
+          return uni(op == 11 ? d.u < 0 : op == 12 ? d.u <= 0 : op == 13 ? d.u == 0 : d.u != 0);
+        if (!lin_coef(d, &al)) return other();
+        LVal p;
+        p.k = 2;
+        p.op = op;
+        p.ct = al;
+        p.b = d.b;
+        return p;
+      }
+      default:
+        return other();
+    }
+  }
+  LVal sreg(int id) const {
+    if (id == 0) return affine(1, 0, 0);
+    if (id == 6) return affine(0, 1, 0);
+    if (id == 1 || id == 2 || id == 7 || id == 8) return uni(0);
+    if (id <= 5) return uni((int32_t)in.block[id - 3]);
+    if (id <= 11) return uni((int32_t)in.grid[id - 9]);
+    return uni(in.args[id - 12]);
+  }
+  LVal load(const IrOp& o, int32_t idx) const {
+    const int64_t w = o.width, off = (int64_t)idx * w;
+    const int64_t len = (int64_t)in.buf_len[o.buf];
+    if (off < 0 || off + w > len || ((ir.shared_mask >> o.buf) & 1u)) return uni(0);
+    const uint32_t word =
+        host_fmix32(ir.seed ^ ((uint32_t)o.buf * 0x9E3779B9u) ^ (uint32_t)((uint64_t)off >> 2));
+    return uni(w == 1 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word);
+  }
+  // The lins around where d = a * lin + b (a != 0) changes sign or is 0:
+  // with f = floor(-b / a), the truth of d < 0 and of d <= 0 flips between
+  // f - 1 and f or between f and f + 1 (whatever the sign of a), and d = 0
+  // can hold at f alone.
+  void add_threshold(int64_t a, int64_t b) {
+    if (a == 0) return;  // not reached: a predicate's d varies over the launch
+    int64_t f = -b / a;
+    if ((-b % a) != 0 && ((-b < 0) != (a < 0))) f--;
+    for (int64_t t = f - 1; t <= f + 1; t++)
+      if (t >= 0 && t < n) thresholds.push_back(t);
+  }
+  struct State {
+    std::vector<LVal> r;
+    uint64_t back = 0;
+  };
+  // Executes [pc, end) on st; false if the input does not qualify.
+  bool exec(int pc, int end, State& st) {
+    while (pc < end) {
+      const IrOp& o = ir.ops[pc];
+      const uint8_t opc = o.opc;
+      if (is_alu_reg(opc) || is_alu_imm(opc)) {
+        const bool im = is_alu_imm(opc);
+        LVal v = alu(opc - (im ? 0x30 : 0x10), st.r[o.a], im ? uni(o.imm) : st.r[o.b]);
+        if (!norm(v)) return false;
+        st.r[o.dst] = v;
+        pc++;
+        continue;
+      }
+      switch (opc) {
+        case B_SREG: {
+          LVal v = sreg(o.sreg);
+          if (!norm(v)) return false;
+          st.r[o.dst] = v;
+          pc++;
+          break;
+        }
+        case B_IMM: st.r[o.dst] = uni(o.imm); pc++; break;
+        case B_MOV: st.r[o.dst] = st.r[o.a]; pc++; break;
+        case B_SEL: {
+          const LVal& c = st.r[o.a];
+          if (c.k == 0) st.r[o.dst] = c.u ? st.r[o.b] : st.r[o.c];
+          else st.r[o.dst] = st.r[o.b] == st.r[o.c] ? st.r[o.b] : other();
+          pc++;
+          break;
+        }
+        case B_LD:
+        case B_ST: {
+          const LVal idx = st.r[o.a];
+          int64_t al = 0;
+          if (idx.k >= 2 || (idx.k == 1 && !lin_coef(idx, &al))) return false;
+          if (opc == B_LD) st.r[o.dst] = idx.k == 0 ? load(o, idx.u) : other();
+          pc++;
+          break;
+        }
+        case B_IF: {
+          LVal c = st.r[o.a];
+          int64_t al = 0;
+          if (c.k == 1) {  // "value != 0" with value affine in lin
+            if (!lin_coef(c, &al)) return false;
+            LVal p;
+            p.k = 2;
+            p.op = 14;
+            p.ct = al;
+            p.b = c.b;
+            c = p;
+          }
+          const int then_end = o.else_pc >= 0 ? o.else_pc : o.end_pc;
+          if (c.k == 0) {
+            if (c.u) {
+              if (!exec(pc + 1, then_end, st)) return false;
+            } else if (o.else_pc >= 0) {
+              if (!exec(o.else_pc + 1, o.end_pc, st)) return false;
+            }
+          } else if (c.k == 2) {
+            add_threshold(c.ct, c.b);
+            State a = st, e = st;
+            if (!exec(pc + 1, then_end, a)) return false;
+            if (o.else_pc >= 0 && !exec(o.else_pc + 1, o.end_pc, e)) return false;
+            for (size_t k = 0; k < st.r.size(); k++) st.r[k] = a.r[k] == e.r[k] ? a.r[k] : other();
+            st.back = std::max(a.back, e.back);
+          } else {
+            return false;
+          }
+          pc = o.end_pc + 1;
+          break;
+        }
+        case B_LOOP: {
+          if (st.r[o.a].k != 0) return false;
+          const int32_t nt = st.r[o.a].u;
+          const int32_t trip = nt < 0 ? 0 : (nt > o.imm ? o.imm : nt);
+          for (int32_t k = 0; k < trip; k++) {
+            st.r[o.dst] = uni(k);
+            if (!exec(pc + 1, o.end_pc, st)) return false;
+            if (++st.back > budget) return false;  // a budget stop: not covered here
+          }
+          st.r[o.dst] = uni(trip);
+          pc = o.end_pc + 1;
+          break;
+        }
+        default: pc++; break;
+      }
+    }
+    return true;
+  }
+};
+
+// The threads (linear ids g) that decide a 1D input's verdict, or false.
+bool prex_line_plan(const Ir& ir, const cufz_input& in, uint32_t budget, std::vector<uint32_t>* g) {
+  if (in.block[1] != 1 || in.block[2] != 1 || in.grid[1] != 1 || in.grid[2] != 1) return false;
+  PrexLine pl{ir, in, budget, in.block[0], in.grid[0], (int64_t)in.block[0] * in.grid[0], {}};
+  PrexLine::State st;
+  st.r.assign(std::max(ir.n_regs, 1), PrexLine::uni(0));
+  if (!pl.exec(0, (int)ir.ops.size(), st)) return false;
+  pl.thresholds.push_back(0);
+  pl.thresholds.push_back(pl.n - 1);
+  std::sort(pl.thresholds.begin(), pl.thresholds.end());
+  pl.thresholds.erase(std::unique(pl.thresholds.begin(), pl.thresholds.end()), pl.thresholds.end());
+  g->assign(pl.thresholds.begin(), pl.thresholds.end());
+  return true;
+}
+
 bool prex_run(const Ir& ir, const cufz_input& in, uint32_t budget) {
   PrexRun run{ir, in, budget, {}, std::vector<AVal>(std::max(ir.n_regs, 1))};
   for (int d = 0; d < 3; d++) {
@@ -1151,6 +1414,40 @@ struct PrexInfo {
 
 bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget) {
   return prex_run(p.ir, in, iter_budget);
+}
+
+std::vector<uint32_t> prex_corners(const cufz_input& in) {
+  std::vector<uint32_t> t[3], b[3];
+  for (int d = 0; d < 3; d++) {
+    t[d] = {0u};
+    if (in.block[d] > 1) t[d].push_back(in.block[d] - 1);
+    b[d] = {0u};
+    if (in.grid[d] > 1) b[d].push_back(in.grid[d] - 1);
+  }
+  const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
+  std::vector<uint32_t> out;
+  for (uint32_t bz : b[2])
+    for (uint32_t by : b[1])
+      for (uint32_t bx : b[0])
+        for (uint32_t tz : t[2])
+          for (uint32_t ty : t[1])
+            for (uint32_t tx : t[0]) {
+              const uint64_t bl = bx + (uint64_t)in.grid[0] * (by + (uint64_t)in.grid[1] * bz);
+              const uint64_t tl = tx + (uint64_t)in.block[0] * (ty + (uint64_t)in.block[1] * tz);
+              out.push_back((uint32_t)(bl * T + tl));
+            }
+  std::sort(out.begin(), out.end());
+  out.erase(std::unique(out.begin(), out.end()), out.end());
+  return out;
+}
+
+bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
+               std::vector<uint32_t>* threads) {
+  if (prex_run(p.ir, in, iter_budget)) {
+    *threads = prex_corners(in);
+    return true;
+  }
+  return prex_line_plan(p.ir, in, iter_budget, threads);
 }
 
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
@@ -1309,6 +1606,21 @@ extern "C" cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const c
   PrexInfo p;
   if (!decode((const uint8_t*)bytes, nbytes, &p.ir)) return CUFZ_E_INVALID_PROGRAM;
   *eligible = prex_input_ok(p, *in, iter_budget ? iter_budget : 4096u) ? 1u : 0u;
+  return CUFZ_OK;
+}
+
+extern "C" cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* in,
+                                      uint32_t iter_budget, uint32_t* threads, uint32_t cap,
+                                      uint32_t* n_threads) {
+  if (!bytes || !in || !n_threads || (!threads && cap)) return CUFZ_E_INVALID_ARG;
+  PrexInfo p;
+  if (!decode((const uint8_t*)bytes, nbytes, &p.ir)) return CUFZ_E_INVALID_PROGRAM;
+  std::vector<uint32_t> g;
+  *n_threads = 0;
+  if (!prex_plan(p, *in, iter_budget ? iter_budget : 4096u, &g)) return CUFZ_OK;
+  *n_threads = (uint32_t)g.size();
+  if (g.size() > cap) return CUFZ_E_NOMEM;
+  std::copy(g.begin(), g.end(), threads);
   return CUFZ_OK;
 }
 

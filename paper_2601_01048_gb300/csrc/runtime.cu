@@ -542,33 +542,6 @@ bool tune_cache_write(const cufz_ctx* c) {
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
 }
 
-// PREX (Sec. 5.1.1): the linear ids g = block_lin * T + thread_lin of the
-// threads whose every thread and block coordinate is first or last, sorted.
-std::vector<uint32_t> corner_threads(const cufz_input& in) {
-  std::vector<uint32_t> t[3], b[3];
-  for (int d = 0; d < 3; d++) {
-    t[d] = {0u};
-    if (in.block[d] > 1) t[d].push_back(in.block[d] - 1);
-    b[d] = {0u};
-    if (in.grid[d] > 1) b[d].push_back(in.grid[d] - 1);
-  }
-  const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
-  std::vector<uint32_t> out;
-  for (uint32_t bz : b[2])
-    for (uint32_t by : b[1])
-      for (uint32_t bx : b[0])
-        for (uint32_t tz : t[2])
-          for (uint32_t ty : t[1])
-            for (uint32_t tx : t[0]) {
-              const uint64_t bl = bx + (uint64_t)in.grid[0] * (by + (uint64_t)in.grid[1] * bz);
-              const uint64_t tl = tx + (uint64_t)in.block[0] * (ty + (uint64_t)in.block[1] * tz);
-              out.push_back((uint32_t)(bl * T + tl));
-            }
-  std::sort(out.begin(), out.end());
-  out.erase(std::unique(out.begin(), out.end()), out.end());
-  return out;
-}
-
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
@@ -955,7 +928,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
         prex_input_ok(*c->progs[x.program_id].prex, x, c->T.iter_budget)) {
       // the corner threads decide the verdict: run only them
       corners.resize(n_dev + 1);
-      corners[n_dev] = corner_threads(x);
+      corners[n_dev] = prex_corners(x);
       d->n_threads = corners[n_dev].size();
       sh.partial = true;
     }

@@ -122,3 +122,181 @@ def test_prex_wrap_case_really_breaks_the_theorem(orc):
     ok, full = corner_verdict_matches(orc, prog, inp)
     assert full and not ok
     assert not B.cufz_prex_check(prog, inp)
+
+
+# ---------------------------------------------------------------------------
+# the plan: corners, or for guarded 1D launches the guards' change points
+# ---------------------------------------------------------------------------
+
+def plan_decides_every_site(orc, prog, inp, plan):
+    """The oracle's full grid against the planned threads alone: for every
+    access site, some thread violates there iff a planned thread does."""
+    res, recs, _ = orc.run(orc.Program(prog), inp, rec_cap=1 << 17, bitmap=False)
+    assert int(res["n_records"]) == int(res["n_violations"])        # every record kept
+    T = int(np.prod([int(v) for v in inp["block"]]))
+    g = recs["block_lin"].astype(np.int64) * T + recs["thread_lin"]
+    full = set(recs["site"].tolist())
+    planned = set(recs["site"][np.isin(g, plan)].tolist())
+    return full == planned, bool(full)
+
+
+def guarded_1d_program(rng):
+    """Accesses at indices affine in lin = ctaid.x * ntid.x + tid.x, under
+    nested guards comparing affine values with arguments (<, <=, ==, !=, a
+    value tested against zero), with else arms, and inside a uniform loop
+    whose guard threshold moves with the counter."""
+    A = Asm(n_bufs=3, seed=rng.next32())
+    lin = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    a0, a1, a2 = A.sreg(bc.ARG0), A.sreg(bc.ARG1), A.sreg(bc.ARG2)
+
+    def aff():
+        c = rng.choice((1, 1, 2, -1, 3))
+        v = lin if c == 1 else A.alu(bc.MUL, lin, Imm(c))
+        return A.alu(bc.ADD, A.alu(bc.ADD, v, a0), Imm(rng.randint(-3, 3)))
+
+    def guard():
+        kind = rng.below(5)
+        if kind == 0:
+            return A.alu(bc.SETLT, aff(), a1)
+        if kind == 1:
+            return A.alu(bc.SETLE, a1, aff())
+        if kind == 2:
+            return A.alu(bc.SETEQ, lin, a2)
+        if kind == 3:
+            return A.alu(bc.SETNE, aff(), a2)
+        return A.alu(bc.SUB, lin, a2)                            # "lin - a2 != 0"
+
+    def body(depth):
+        for _ in range(rng.randint(1, 3)):
+            r = rng.below(4)
+            if r == 0 or depth >= 2:
+                A.ld(rng.below(3), aff(), rng.choice(bc.WIDTHS))
+            elif r == 1:
+                A.st(rng.below(3), aff(), A.imm(1), rng.choice(bc.WIDTHS))
+            elif r == 2:
+                A.if_(guard())
+                body(depth + 1)
+                if rng.below(2):
+                    A.else_()
+                    body(depth + 1)
+                A.endif()
+            else:
+                k = A.loop(A.sreg(bc.ARG3), 4)
+                A.if_(A.alu(bc.SETLT, A.alu(bc.ADD, lin, A.alu(bc.SHL, k, Imm(3))), a1))
+                A.ld(rng.below(3), A.alu(bc.ADD, aff(), k), 4)
+                A.endif()
+                A.endloop()
+
+    body(0)
+    return A.build()
+
+
+def test_plan_decides_random_guarded_1d(orc):
+    rng = gen.SplitMix64(1048)
+    planned = violating = 0
+    for trial in range(60):
+        prog = guarded_1d_program(rng)
+        for _ in range(4):
+            nx, gx = rng.randint(1, 40), rng.randint(1, 6)
+            n = nx * gx
+            args = (rng.randint(-4, 4), rng.randint(-5, n + 5), rng.randint(-2, n + 2),
+                    rng.randint(0, 4))
+            inp = mk((gx, 1, 1), (nx, 1, 1), args,
+                     [rng.randint(0, 4 * (3 * n + 12)) for _ in range(3)])
+            plan = B.cufz_prex_plan(prog, inp)
+            assert plan is not None
+            assert np.all(np.diff(plan.astype(np.int64)) > 0) and plan[0] == 0 and plan[-1] == n - 1
+            ok, full = plan_decides_every_site(orc, prog, inp, plan)
+            assert ok, (trial, args)
+            planned += 1
+            violating += full
+    assert planned == 240 and 40 < violating < 220
+
+
+def test_plan_decides_guarded_configs(orc):
+    """The guarded 1D workloads (one program over grids of 64 x 128, sixteen
+    programs of the family with offsets and widths over log-uniform
+    launches): a plan for every input, a handful of threads each, and every
+    site's verdict decided by it."""
+    c1 = gen.c1_inputs(24, seed=77)
+    c3 = gen.c3_inputs(48, seed=78, max_blocks=64, max_threads=256)
+    progs = gen.c3_programs()
+    for inp, prog in [(x, gen.c1_program()) for x in c1] + [(x, progs[int(x["program_id"])]) for x in c3]:
+        assert not B.cufz_prex_check(prog, inp) or int(inp["args"][1]) <= 0
+        plan = B.cufz_prex_plan(prog, inp)
+        assert plan is not None and len(plan) <= 5
+        ok, _ = plan_decides_every_site(orc, prog, inp, plan)
+        assert ok
+
+
+def test_plan_needs_the_threshold_threads(orc):
+    """Why the guard's change point is planned: with i < 100 guarding A[i]
+    and A 99 elements long, thread 99 alone violates; threads 0 and N - 1
+    (the corners) see nothing."""
+    prog = gen.c1_program()
+    inp = mk((64, 1, 1), (128, 1, 1), (0, 100), (4 * 99, 4 * 8192, 4 * 8192, 4 * 8192))
+    plan = B.cufz_prex_plan(prog, inp)
+    assert 99 in plan.tolist()
+    res, recs, _ = orc.run(orc.Program(prog), inp, rec_cap=64, bitmap=False)
+    assert int(res["n_violations"]) == 1 and int(recs[0]["block_lin"]) * 128 + int(recs[0]["thread_lin"]) == 99
+    ok, full = plan_decides_every_site(orc, prog, inp, np.array([0, 64 * 128 - 1]))
+    assert full and not ok
+
+
+def test_plan_is_the_corners_when_the_check_holds():
+    rng = gen.SplitMix64(9)
+    from test_oracle_pins import affine_program
+    for dims in (1, 2, 3):
+        prog = affine_program(rng, dims, 4)
+        grid = [3, 2, 2][:dims] + [1] * (3 - dims)
+        block = [5, 4, 3][:dims] + [1] * (3 - dims)
+        inp = mk(grid, block, (1, 2, 0, 0), (400, 400, 400))
+        assert B.cufz_prex_check(prog, inp)
+        T = int(np.prod(block))
+        want = sorted({B_ * T + t
+                       for B_ in range(int(np.prod(grid))) if corner(B_, grid)
+                       for t in range(T) if corner(t, block)})
+        assert B.cufz_prex_plan(prog, inp).tolist() == want
+
+
+def test_plan_refuses():
+    tx = lambda A: A.sreg(bc.TID_X)
+    lin = lambda A: A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), tx(A))
+    guarded = _prog(lambda A: (A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0))),
+                               A.ld(0, lin(A), 4), A.endif()))
+    on_tx = _prog(lambda A: (A.if_(A.alu(bc.SETLT, tx(A), A.sreg(bc.ARG0))),
+                             A.ld(0, lin(A), 4), A.endif()))
+    both = _prog(lambda A: (A.if_(A.alu(bc.AND, A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0)),
+                                        A.alu(bc.SETLT, A.sreg(bc.ARG1), lin(A)))),
+                            A.ld(0, lin(A), 4), A.endif()))
+    loaded = _prog(lambda A: (A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0))),
+                              A.ld(1, A.ld(0, lin(A), 4), 4), A.endif()))
+
+    def diverged(A):
+        r = A.imm(0)
+        A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0)))
+        A.mov(lin(A), dst=r)
+        A.endif()
+        A.ld(0, r, 4)
+
+    diverged = _prog(diverged)
+
+    def looped(A):
+        k = A.loop(A.sreg(bc.ARG1), 200)
+        A.if_(A.alu(bc.SETLT, A.alu(bc.ADD, lin(A), k), A.sreg(bc.ARG0)))
+        A.ld(0, lin(A), 4)
+        A.endif()
+        A.endloop()
+
+    budget = _prog(looped)
+    one_d = mk((4, 1, 1), (32, 1, 1), (50, 100), (400, 400))
+    two_d = mk((4, 1, 1), (8, 4, 1), (50, 100), (400, 400))
+    assert B.cufz_prex_plan(guarded, one_d) is not None
+    assert B.cufz_prex_plan(guarded, two_d) is None                   # a 2D block
+    assert B.cufz_prex_plan(on_tx, one_d) is None                     # tid.x alone over 4 blocks
+    assert B.cufz_prex_plan(on_tx, mk((1, 1, 1), (32, 1, 1), (5, 0), (400, 400))) is not None
+    assert B.cufz_prex_plan(both, one_d) is None                      # two guards combined
+    assert B.cufz_prex_plan(loaded, one_d) is None                    # a loaded index
+    assert B.cufz_prex_plan(diverged, one_d) is None                  # the arms leave different values
+    assert B.cufz_prex_plan(budget, one_d, iter_budget=4096) is not None
+    assert B.cufz_prex_plan(budget, one_d, iter_budget=50) is None     # a budget stop
