@@ -3,7 +3,7 @@
  *
  * The engine runs a kernel under test, given as an integer access-index
  * program, over its full grid once per fuzz input (or, with CUFZ_CF_PREX,
- * over the corner threads that decide the verdict, Sec. 5.1); it checks
+ * over the few threads that decide the verdict, Sec. 5.1); it checks
  * every load and store against its buffer's bounds and records AFL-style
  * edge coverage.
  * This is the work the paper moves to the CPU through IR translation and
@@ -70,9 +70,9 @@ typedef int32_t cufz_status;
 #define CUFZ_FL_BUDGET 1   /* some thread exceeded the back-edge budget (hang analog) */
 #define CUFZ_FL_OVERFLOW 2 /* more violations than record_cap; counts stay exact */
 #define CUFZ_FL_NEW_COV 4  /* bitmap has a bucket bit the epoch's union lacks */
-#define CUFZ_FL_PARTIAL 8  /* CUFZ_CF_PREX ran only the corner threads: the status
+#define CUFZ_FL_PARTIAL 8  /* CUFZ_CF_PREX ran only the planned threads: the status
                               (violation or not) is the full grid's; counts,
-                              records, digest and bitmap cover the corners */
+                              records, digest and bitmap cover those threads */
 
 /* violation classes (cufz_violation.cls) */
 #define CUFZ_CLS_UNDERFLOW_RZ 1 /* byte_off in [-R, 0) */
@@ -91,8 +91,11 @@ typedef int32_t cufz_status;
                                   instead of through the bytecode interpreter */
 #define CUFZ_CF_JIT_FAST_COMPILE 128 /* compile faster, run slower (compiled path) */
 #define CUFZ_CF_PREX 256       /* partial representative execution (Sec. 5.1): an input
-                                  whose program qualifies (cufz_prex_check) runs only
-                                  its corner threads, flagged CUFZ_FL_PARTIAL */
+                                  with a plan (cufz_prex_plan) of at most
+                                  CUFZ_PREX_MAX_PLAN threads runs only those threads,
+                                  flagged CUFZ_FL_PARTIAL */
+
+#define CUFZ_PREX_MAX_PLAN 4096 /* larger plans run the full grid */
 
 /* Engine configuration.  cufz_config_default fills every field; a zero in
  * max_slots, item_threads or cta_threads means "choose automatically". */

@@ -23,6 +23,7 @@ ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV, FL_PARTIAL = 1, 2, 4, 8
 CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \
     CF_JIT, CF_JIT_FAST_COMPILE, CF_PREX = 1, 2, 4, 8, 16, 32, 64, 128, 256
+PREX_MAX_PLAN = 4096
 
 RESULT_DTYPE = np.dtype([
     ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),

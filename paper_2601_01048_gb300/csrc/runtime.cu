@@ -56,7 +56,7 @@ struct SlotHost {
   uint32_t lane = 0;
   uint64_t batch = 0;
   uint32_t prog = 0;  // program of the input in the slot
-  bool partial = false;  // PREX: only the corner threads run
+  bool partial = false;  // PREX: only the planned threads run
 };
 
 struct Lane {
@@ -874,7 +874,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   uint32_t n_dev = 0;
   uint64_t batch_threads = 0;
   const bool prex_on = (c->cfg.flags & CUFZ_CF_PREX) != 0 && !plain;
-  std::vector<std::vector<uint32_t>> corners;  // per device input under PREX
+  std::vector<std::vector<uint32_t>> planned;  // per device input under PREX: its threads
   std::vector<uint32_t> dev_slots;
   uint32_t accepted = 0;
   bool busy = false;
@@ -924,12 +924,14 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     sh.lane = lane_idx;
     sh.prog = x.program_id;
     sh.partial = false;
+    std::vector<uint32_t> plan;
     if (prex_on && c->progs[x.program_id].prex &&
-        prex_input_ok(*c->progs[x.program_id].prex, x, c->T.iter_budget)) {
-      // the corner threads decide the verdict: run only them
-      corners.resize(n_dev + 1);
-      corners[n_dev] = prex_corners(x);
-      d->n_threads = corners[n_dev].size();
+        prex_plan(*c->progs[x.program_id].prex, x, c->T.iter_budget, &plan) &&
+        plan.size() <= CUFZ_PREX_MAX_PLAN) {
+      // these threads decide the verdict: run only them
+      planned.resize(n_dev + 1);
+      planned[n_dev] = std::move(plan);
+      d->n_threads = planned[n_dev].size();
       sh.partial = true;
     }
     c->ticket_slot[ticket] = s;
@@ -953,11 +955,11 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
                      [&](uint32_t x, uint32_t y) { return dins[x].prog < dins[y].prog; });
     auto compiled = [&](uint32_t prog) { return use_jit(c) && c->prog_compiled[prog]; };
     uint64_t want[2] = {0, 0};
-    corners.resize(n_dev);
+    planned.resize(n_dev);
     for (uint32_t i = 0; i < n_dev; i++) {
       DevInput* d = &dins[i];
       d->n_items = plain ? (uint32_t)(d->n_threads / d->T)
-                 : !corners[i].empty() ? (uint32_t)corners[i].size()  // one item per corner thread
+                 : !planned[i].empty() ? (uint32_t)planned[i].size()  // one item per planned thread
                                        : (uint32_t)((d->n_threads + item - 1) / item);
       if (!plain) want[compiled(d->prog) ? 0 : 1] += d->n_items;
     }
@@ -982,8 +984,8 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
         for (uint32_t k = 0; k < d->n_items; k++) {
           WorkItem& w = lists[li][counts[li]++];
           w.input = i;
-          if (!corners[i].empty()) {
-            w.g0 = corners[i][k];
+          if (!planned[i].empty()) {
+            w.g0 = planned[i][k];
             w.count = 1;
           } else {
             w.g0 = k * item;

@@ -34,13 +34,13 @@ def test_status_strings():
 
 
 def test_header_constants_match_binding():
-    """Every CUFZ_E_/ST_/FL_/CF_ constant of the header has the same value in
+    """Every CUFZ_E_/ST_/FL_/CF_/PREX_ constant of the header has the same value in
     the binding (they are written twice: C for the ABI, Python for ctypes)."""
     import os
     import re
     hdr = open(os.path.join(os.path.dirname(__file__), "..", "include", "cufz.h")).read()
     defs = {m.group(1): int(m.group(2)) for m in
-            re.finditer(r"#define CUFZ_((?:E|ST|FL|CF)_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", hdr)}
+            re.finditer(r"#define CUFZ_((?:E|ST|FL|CF|PREX)_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", hdr)}
     assert len(defs) >= 25
     for name, value in defs.items():
         assert getattr(B, name) == value, name
