@@ -36,6 +36,20 @@ std::vector<uint32_t> prex_corners(const cufz_input& in);
 bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
                std::vector<uint32_t>* threads);
 
+// ---------------------------------------------------------------- inputs
+// Launch shapes CUDA would refuse (a zero dimension, more than 1024 threads
+// per block, block.z > 64, grid.x > 2^31 - 1, grid.y or grid.z > 65535):
+// such inputs complete as CUFZ_ST_INVALID_CONFIG without running.
+bool launch_rejected(const cufz_input& in);
+
+// The part of a DevInput that follows from the input and its program: launch
+// shape, division magics, arguments, buffer lengths, redzone-separated
+// virtual bases (per space: base_0 = R, base_k+1 = align256(base_k + len_k
+// + R)) and per-width index limits.  Zeroes the rest (slot, program
+// placement, items, ticket, sequence), which the caller sets.
+void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
+                    DevInput* d);
+
 struct LoadedProgram {
   DevProgHdr hdr;
   uint8_t* blob = nullptr;   // host copy of the device blob

@@ -1441,6 +1441,52 @@ std::vector<uint32_t> prex_corners(const cufz_input& in) {
   return out;
 }
 
+bool launch_rejected(const cufz_input& in) {
+  const uint32_t* g = in.grid;
+  const uint32_t* b = in.block;
+  if (!g[0] || !g[1] || !g[2] || !b[0] || !b[1] || !b[2]) return true;
+  if (b[0] > 1024 || b[1] > 1024 || b[2] > 64) return true;
+  if ((uint64_t)b[0] * b[1] * b[2] > 1024) return true;
+  return g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535;
+}
+
+void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
+                    DevInput* d) {
+  memset(d, 0, sizeof(*d));
+  for (int k = 0; k < 3; k++) {
+    d->grid[k] = in.grid[k];
+    d->block[k] = in.block[k];
+  }
+  for (int k = 0; k < 4; k++) d->args[k] = in.args[k];
+  const uint32_t Bx = in.block[0], By = in.block[1], Bz = in.block[2];
+  d->T = Bx * By * Bz;
+  d->n_threads = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * d->T;
+  d->mT = div_magic(d->T);
+  d->Bx = Bx;
+  d->mBx = div_magic(Bx);
+  d->Bxy = Bx * By;
+  d->mBxy = div_magic(d->Bxy);
+  d->gx = in.grid[0];
+  d->mGx = div_magic(in.grid[0]);
+  d->gxy = (uint32_t)((uint64_t)in.grid[0] * in.grid[1]);
+  d->mGxy = div_magic(d->gxy);
+  const int64_t R = (int64_t)redzone;
+  int64_t next[2] = {R, R};
+  for (uint32_t k = 0; k < n_bufs; k++) {
+    const int sp = (shared_mask >> k) & 1;
+    d->len[k] = (int64_t)in.buf_len[k];
+    d->base[k] = next[sp];
+    next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
+    for (uint32_t lw = 0; lw < 5; lw++) {
+      const uint64_t n = in.buf_len[k] >> lw;
+      d->lim[k * 5 + lw] = n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
+    }
+  }
+  d->shared_mask = shared_mask;
+  d->n_bufs = n_bufs;
+  d->user_tag = in.user_tag;
+}
+
 bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
                std::vector<uint32_t>* threads) {
   if (prex_run(p.ir, in, iter_budget)) {

@@ -57,15 +57,6 @@ cudaError_t scratch_on(int dev, uint8_t** out) {
   return cudaSuccess;
 }
 
-bool launch_rejected(const cufz_input& in) {
-  const uint32_t* g = in.grid;
-  const uint32_t* b = in.block;
-  if (!g[0] || !g[1] || !g[2] || !b[0] || !b[1] || !b[2]) return true;
-  if (b[0] > 1024 || b[1] > 1024 || b[2] > 64) return true;
-  if ((uint64_t)b[0] * b[1] * b[2] > 1024) return true;
-  return g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535;
-}
-
 }  // namespace
 
 extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
@@ -133,42 +124,9 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
   hdr->n_items = n_items;
   hdr->inputs_off = sizeof(BatchHdr);
   hdr->items_off = sizeof(BatchHdr) + sizeof(DevInput);
-  d->slot = 0;
-  d->prog = 0;
-  for (int k = 0; k < 3; k++) {
-    d->grid[k] = input->grid[k];
-    d->block[k] = input->block[k];
-  }
-  for (int k = 0; k < 4; k++) d->args[k] = input->args[k];
-  d->T = (uint32_t)T;
+  fill_dev_input(*input, P.n_bufs, P.shared_mask, redzone, d);
   d->n_items = n_items;
-  d->n_threads = n_threads;
-  d->mT = div_magic((uint32_t)T);
-  d->Bx = input->block[0];
-  d->mBx = div_magic(input->block[0]);
-  d->Bxy = input->block[0] * input->block[1];
-  d->mBxy = div_magic(d->Bxy);
-  d->gx = input->grid[0];
-  d->mGx = div_magic(input->grid[0]);
-  d->gxy = (uint32_t)((uint64_t)input->grid[0] * input->grid[1]);
-  d->mGxy = div_magic(d->gxy);
-  int64_t R = redzone, next[2] = {R, R};
-  for (uint32_t k = 0; k < P.n_bufs; k++) {
-    int sp = (P.shared_mask >> k) & 1;
-    d->len[k] = (int64_t)input->buf_len[k];
-    d->base[k] = next[sp];
-    next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
-    for (uint32_t lw = 0; lw < 5; lw++) {
-      uint64_t n = input->buf_len[k] >> lw;
-      d->lim[k * 5 + lw] = n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
-    }
-  }
-  d->shared_mask = P.shared_mask;
-  d->n_bufs = P.n_bufs;
-  d->prog_off = 0;
   d->prog_bytes = P.blob_bytes;
-  d->ticket = 0;
-  d->user_tag = input->user_tag;
   d->seq = 1;
   for (uint32_t k = 0; k < n_items; k++) {
     items[k].input = 0;

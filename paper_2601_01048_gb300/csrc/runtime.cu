@@ -134,17 +134,6 @@ struct cufz_ctx {
 
 namespace {
 
-bool invalid_launch(const cufz_input& in) {
-  const uint32_t* g = in.grid;
-  const uint32_t* b = in.block;
-  if (!g[0] || !g[1] || !g[2] || !b[0] || !b[1] || !b[2]) return true;
-  if (b[0] > 1024 || b[1] > 1024 || b[2] > 64) return true;
-  if ((uint64_t)b[0] * b[1] * b[2] > 1024) return true;
-  if (g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535) return true;
-  return false;
-}
-
-
 // A lane's batch buffer: the compiled path's header, the interpreter's
 // header, the inputs, the compiled path's items, the interpreter's items.
 uint64_t lane_bytes(uint32_t max_inputs, uint32_t max_items) {
@@ -459,47 +448,12 @@ cufz_status lane_graph(cufz_ctx* c, Lane& L, uint32_t mask) {
 }
 
 void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput* d) {
-  memset(d, 0, sizeof(*d));
   const LoadedProgram& P = c->progs[in.program_id];
+  fill_dev_input(in, P.n_bufs, P.shared_mask, c->cfg.redzone, d);
   d->slot = slot;
   d->prog = in.program_id;
-  for (int k = 0; k < 3; k++) {
-    d->grid[k] = in.grid[k];
-    d->block[k] = in.block[k];
-  }
-  for (int k = 0; k < 4; k++) d->args[k] = in.args[k];
-  uint32_t Bx = in.block[0], By = in.block[1], Bz = in.block[2];
-  uint32_t T = Bx * By * Bz;
-  uint64_t nb = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2];
-  d->T = T;
-  d->n_threads = nb * T;
-  d->mT = div_magic(T);
-  d->Bx = Bx;
-  d->mBx = div_magic(Bx);
-  d->Bxy = Bx * By;
-  d->mBxy = div_magic(Bx * By);
-  d->gx = in.grid[0];
-  d->mGx = div_magic(in.grid[0]);
-  d->gxy = (uint32_t)((uint64_t)in.grid[0] * in.grid[1]);
-  d->mGxy = div_magic(d->gxy);
-  int64_t R = (int64_t)c->cfg.redzone;
-  int64_t next[2] = {R, R};
-  for (uint32_t k = 0; k < P.n_bufs; k++) {
-    int sp = (P.shared_mask >> k) & 1;
-    d->len[k] = (int64_t)in.buf_len[k];
-    d->base[k] = next[sp];
-    next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
-  }
-  d->shared_mask = P.shared_mask;
-  d->n_bufs = P.n_bufs;
-  for (uint32_t k = 0; k < P.n_bufs; k++)
-    for (uint32_t lw = 0; lw < 5; lw++) {
-      uint64_t n = (uint64_t)in.buf_len[k] >> lw;
-      d->lim[k * 5 + lw] = n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
-    }
   d->prog_off = c->prog_off[in.program_id];
   d->prog_bytes = P.blob_bytes;
-  d->user_tag = in.user_tag;
 }
 
 // Autotune cache: one "key path" line per program, the key a 64-bit FNV-1a
@@ -882,7 +836,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     const cufz_input& x = in[i];
     int32_t status = CUFZ_ST_OK;
     if (x.program_id >= c->progs.size() || !c->prog_live[x.program_id]) status = CUFZ_ST_BAD_PROGRAM;
-    else if (invalid_launch(x)) status = CUFZ_ST_INVALID_CONFIG;
+    else if (launch_rejected(x)) status = CUFZ_ST_INVALID_CONFIG;
     else {
       uint64_t nt = (uint64_t)x.grid[0] * x.grid[1] * x.grid[2] * x.block[0] * x.block[1] * x.block[2];
       if (nt > c->cfg.max_threads) status = CUFZ_ST_LIMIT;
