@@ -1,10 +1,10 @@
 """The loader's host code (decoder, validator, pruning, code generator,
-PREX check and plan) built with AddressSanitizer and
-UndefinedBehaviorSanitizer and run over every workload program and random
-PREX-shaped programs, each as given and with random byte mutations (most
-rejected by the validator, some valid but unusual), with inputs at the
-launch and argument extremes.  Any out-of-bounds access, leak, overflow of
-a signed integer or other undefined behaviour fails the test."""
+PREX check and plan) and the CPU oracle, each built with AddressSanitizer
+and UndefinedBehaviorSanitizer and run over every workload program and
+random PREX-shaped programs, each as given and with random byte mutations
+(most rejected by the validators, some valid but unusual), with inputs at
+the launch and argument extremes.  Any out-of-bounds access, leak, overflow
+of a signed integer or other undefined behaviour fails the test."""
 import os
 import shutil
 import struct
@@ -19,7 +19,17 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 EXTREMES = [0, 1, -1, 2**31 - 1, -2**31, 2**30, -2**30, 7, 1024, 65535]
 
 
-def build_driver(tmp_path):
+SAN = ["-O1", "-g", "-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
+
+
+def compile_or_skip(cmd):
+    r = subprocess.run(cmd, capture_output=True, text=True)
+    if r.returncode != 0 and "asan" in (r.stderr + r.stdout).lower():
+        pytest.skip("sanitizer runtime not available")
+    assert r.returncode == 0, r.stderr[-4000:]
+
+
+def build_loader_driver(tmp_path):
     gxx = shutil.which("g++")
     if not gxx:
         pytest.skip("no g++")
@@ -28,14 +38,19 @@ def build_driver(tmp_path):
     except RuntimeError:
         pytest.skip("no CUDA toolkit headers")
     exe = str(tmp_path / "loader_sanitized")
-    cmd = [gxx, "-std=c++17", "-O1", "-g", "-fsanitize=address,undefined",
-           "-fno-sanitize-recover=all", "-I", cuda_inc, "-I", CSRC,
-           "-x", "c++", os.path.join(CSRC, "loader.cpp"),
-           os.path.join(HERE, "sanitize", "loader_driver.cpp"), "-o", exe]
-    r = subprocess.run(cmd, capture_output=True, text=True)
-    if r.returncode != 0 and "asan" in (r.stderr + r.stdout).lower():
-        pytest.skip("sanitizer runtime not available")
-    assert r.returncode == 0, r.stderr[-4000:]
+    compile_or_skip([gxx, "-std=c++17", *SAN, "-I", cuda_inc, "-I", CSRC,
+                     "-x", "c++", os.path.join(CSRC, "loader.cpp"),
+                     os.path.join(HERE, "sanitize", "loader_driver.cpp"), "-o", exe])
+    return exe
+
+
+def build_oracle_driver(tmp_path):
+    gcc = shutil.which("gcc")
+    if not gcc:
+        pytest.skip("no gcc")
+    exe = str(tmp_path / "oracle_sanitized")
+    compile_or_skip([gcc, "-std=c11", *SAN, os.path.join(HERE, "sanitize", "oracle_driver.c"),
+                     "-o", exe])
     return exe
 
 
@@ -83,14 +98,34 @@ def corpus(path, seed=0x5A17, mutations=10):
     return n
 
 
-def test_loader_under_sanitizers(tmp_path):
-    exe = build_driver(tmp_path)
-    path = str(tmp_path / "corpus.bin")
-    n = corpus(path)
+def run_clean(exe, path):
     env = dict(os.environ, ASAN_OPTIONS="detect_leaks=1:abort_on_error=0",
                UBSAN_OPTIONS="print_stacktrace=1")
     r = subprocess.run([exe, path], capture_output=True, text=True, env=env, timeout=600)
     assert r.returncode == 0, (r.stdout + r.stderr)[-4000:]
     assert "runtime error" not in r.stderr and "Sanitizer" not in r.stderr, r.stderr[-4000:]
-    counts = dict(zip(r.stdout.split()[0::2], map(int, r.stdout.split()[1::2])))
-    assert counts["programs"] == n and counts["valid"] > 150 and counts["planned"] > 100
+    return dict(zip(r.stdout.split()[0::2], map(int, r.stdout.split()[1::2])))
+
+
+@pytest.fixture(scope="module")
+def shared_corpus(tmp_path_factory):
+    path = str(tmp_path_factory.mktemp("corpus") / "corpus.bin")
+    return path, corpus(path)
+
+
+@pytest.fixture(scope="module")
+def loader_counts(tmp_path_factory, shared_corpus):
+    return run_clean(build_loader_driver(tmp_path_factory.mktemp("loader")), shared_corpus[0])
+
+
+def test_loader_under_sanitizers(loader_counts, shared_corpus):
+    assert loader_counts["programs"] == shared_corpus[1]
+    assert loader_counts["valid"] > 150 and loader_counts["planned"] > 100
+
+
+def test_oracle_under_sanitizers(tmp_path, shared_corpus, loader_counts):
+    path, n = shared_corpus
+    counts = run_clean(build_oracle_driver(tmp_path), path)
+    assert counts["programs"] == n and counts["ran"] > 4 * 150
+    # the two independent decoders accept the same programs
+    assert counts["valid"] == loader_counts["valid"]
