@@ -248,7 +248,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
  * the thread and block indices with thread-invariant coefficients, and no
  * such affine value can leave the int32 range in the launch box (the device
  * computes in wrapping 32-bit arithmetic).  Programs with thread-dependent
- * guards (the paper's Alg. 1 case, a heuristic) are not eligible.
+ * guards (the paper's Alg. 1 case, a heuristic) are not eligible, nor are
+ * launches the engine does not run (invalid shapes, more than 2^31 threads).
  * iter_budget: the context's back-edge budget (0 = 4096). */
 cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
                             uint32_t iter_budget, uint32_t* eligible);
@@ -258,19 +259,24 @@ cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* 
  * thread_lin (T = threads per block), written to threads[0 .. *n_threads).
  * Two rules give a plan:
  *   - corners: cufz_prex_check's rule; the plan is the corner threads;
- *   - guarded 1D lines (the guarded kernels of Sec. 5.1's Alg. 1, decided
- *     exactly rather than heuristically): a launch with grid and block 1D
- *     (y = z = 1), whose values are thread-invariant or affine in the linear
- *     thread id t = ctaid.x * ntid.x + tid.x (no int32 wrap in the box), and
- *     whose branch conditions compare such values (<, <=, ==, !=) or test an
- *     affine value against zero.  Each comparison's truth changes at most
- *     once along t; the plan is t = 0, t = n-1 and the threads around each
- *     comparison's change point.  Between consecutive planned threads every
- *     condition is constant, so each access index is affine there, and an
- *     interval's violation shows at one of its ends.  Branches are explored
- *     both ways, loops need a thread-invariant trip, and iter_budget bounds
- *     the abstract back-edges (0 = 4096).
- * *n_threads = 0 when neither rule applies (run the full grid).  CUFZ_E_NOMEM
+ *   - guarded grids (the guarded kernels of Sec. 5.1's Alg. 1, decided
+ *     exactly rather than heuristically): each launch dimension is one axis,
+ *     its global coordinate ctaid * ntid + tid, or two, tid and ctaid.  The
+ *     program's values must be thread-invariant or affine in the thread and
+ *     block indices (no int32 wrap in the launch box).  Its branch
+ *     conditions must be guards or combinations of guards.  A guard compares
+ *     values affine in one dimension's coordinates (<, <=, ==, !=, or an
+ *     affine value against zero), so its truth changes only at a few cuts
+ *     of that dimension's axes.  The cuts split the launch box into cells in
+ *     which every condition is constant and every access index is affine.
+ *     An affine index violates somewhere in a cell iff it does at one of the
+ *     cell's corners.  The plan is the threads whose every axis coordinate
+ *     is an end of its axis or lies next to a cut.  Both sides of each guard
+ *     are explored, loop trips must be thread-invariant, and iter_budget
+ *     bounds the abstract back-edges (0 = 4096).
+ * *n_threads = 0 when neither rule applies (run the full grid), and for
+ * launches the engine does not run (invalid shapes, more than 2^31 threads).
+ * CUFZ_E_NOMEM
  * when the plan has more than cap threads (*n_threads gives the size).
  * Host-only; no device needed. */
 cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* in,

@@ -30,9 +30,10 @@ bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget
 std::vector<uint32_t> prex_corners(const cufz_input& in);
 
 // The threads whose verdict is the whole grid's: the corners when
-// prex_input_ok holds, else, for a 1D launch whose values are affine in the
-// linear thread id and whose guards compare such values, the first and last
-// thread and each guard's threshold neighbourhood.  False when neither holds.
+// prex_input_ok holds, else, for a launch whose values are affine in the
+// thread and block indices and whose branch conditions are guards on one
+// dimension's coordinates each, the corners of the cells the guards cut the
+// launch box into.  False when neither holds.
 bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
                std::vector<uint32_t>* threads);
 

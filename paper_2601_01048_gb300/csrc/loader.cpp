@@ -1133,140 +1133,245 @@ struct PrexRun {
 };
 
 
-// Guarded 1D kernels (the case Sec. 5.1.2 leaves to the heuristic Alg. 1),
-// exactly.  With one-dimensional blocks and grid, a value affine in (tx, bx)
-// with c_b = c_t * nx is affine in the linear thread id lin = bx * nx + tx
-// (lin in [0, N), N = nx * gx).  When every guard compares such values, the
-// threads that reach an access form intervals of lin bounded by 0, N - 1 and
-// the guards' thresholds, and an access index affine in lin violates
-// somewhere in an interval iff it does at one of its ends.  So the threads at
-// 0, N - 1 and each threshold (with its neighbours) decide the verdict.  Both
-// sides of a guard are executed (registers that differ between them become
-// "other" at the join); loops need a thread-invariant trip count, and no
-// path may reach the iteration budget.
+// Guarded kernels (the case Sec. 5.1.2 leaves to the heuristic Alg. 1),
+// exactly.  Each launch dimension d is one axis, the global coordinate
+// G_d = b_d * n_d + t_d in [0, n_d * g_d), when every access index and
+// every compared value depends on (t_d, b_d) only through G_d; otherwise it
+// is two axes, t_d in [0, n_d) and b_d in [0, g_d).  A guard compares
+// values affine in one dimension's coordinates, so its truth changes only
+// at a few *cuts* of that dimension's axes: a cut at v separates v - 1 from
+// v.  The cuts of all guards split the launch box into cells (boxes) in
+// which every guard, and so every branch condition and loop trip, is
+// constant; in a cell each access index is affine (or constant), and an
+// affine function is out of bounds somewhere in a box iff it is at one of
+// the box's corners.  So the threads whose every axis coordinate is an axis
+// end or next to a cut (v - 1 or v) decide the verdict: the plan.  Both
+// sides of a guard are executed; values computed from guards and
+// thread-invariant values only (a guard, a combination of guards, a value
+// loaded at such an index, a register the two sides leave different) are
+// constant in each cell.  A guard on a combination of two dimensions
+// (x + y < n) is refused, as is any value that could wrap int32, a loop
+// trip that varies between threads, and a path that reaches the iteration
+// budget.
 
-struct LVal {
-  uint8_t k = 0;  // 0 uniform, 1 affine in (tx, bx), 2 predicate "d op 0" on lin, 3 other
+struct GVal {
+  uint8_t k = 0;  // 0 uniform, 1 affine, 2 constant in each cell, 3 other
   int32_t u = 0;
-  int64_t ct = 0, cb = 0, b = 0;  // affine: ct * tx + cb * bx + b (exact)
-  int op = 0;                      // predicate: 11 <, 12 <=, 13 ==, 14 !=, on d = ct * lin + b
-  bool operator==(const LVal& o) const {
-    return k == o.k && u == o.u && ct == o.ct && cb == o.cb && b == o.b && op == o.op;
+  int64_t ct[3] = {0, 0, 0}, cb[3] = {0, 0, 0}, b = 0;  // affine: sum ct*t + cb*b_ + b
+  bool operator==(const GVal& o) const {
+    if (k != o.k || u != o.u || b != o.b) return false;
+    for (int d = 0; d < 3; d++)
+      if (ct[d] != o.ct[d] || cb[d] != o.cb[d]) return false;
+    return true;
   }
 };
 
-struct PrexLine {
+struct PrexGrid {
   const Ir& ir;
   const cufz_input& in;
   uint32_t budget;
-  int64_t nx, gx, n;  // block size, grid size, threads
-  std::vector<int64_t> thresholds;
+  bool merged[3];          // dimension d is one axis G_d
+  bool need_split[3] = {false, false, false};
+  int64_t n[3], g[3];      // block and grid extents
+  std::vector<int64_t> cut_t[3], cut_b[3], cut_g[3];
 
-  static LVal uni(int32_t x) {
-    LVal v;
+  static GVal uni(int32_t x) {
+    GVal v;
     v.u = x;
     return v;
   }
-  static LVal other() {
-    LVal v;
-    v.k = 3;
+  static GVal kind(uint8_t k) {
+    GVal v;
+    v.k = k;
     return v;
   }
-  static LVal affine(int64_t ct, int64_t cb, int64_t b) {
-    LVal v;
-    v.k = 1;
-    v.ct = ct;
-    v.cb = cb;
-    v.b = b;
-    return v;
+  static int64_t floor_div(int64_t p, int64_t q) {
+    int64_t f = p / q;
+    if ((p % q != 0) && ((p < 0) != (q < 0))) f--;
+    return f;
   }
-  // Range check over the launch; affine values constant over it become uniform.
-  bool norm(LVal& v) const {
+  static int64_t ceil_div(int64_t p, int64_t q) { return -floor_div(-p, q); }
+
+  // Drops coefficients of coordinates fixed at 0, checks the int32 range over
+  // the launch box; affine values constant over it become uniform.
+  bool norm(GVal& v) const {
     if (v.k != 1) return true;
-    for (int64_t c : {v.ct, v.cb, v.b})
-      if (c > kAffMax || c < -kAffMax) return false;
     int64_t lo = v.b, hi = v.b;
-    const int64_t t1 = v.ct * (nx - 1), t2 = v.cb * (gx - 1);
-    (t1 > 0 ? hi : lo) += t1;
-    (t2 > 0 ? hi : lo) += t2;
-    if (lo < INT32_MIN || hi > INT32_MAX) return false;
+    for (int d = 0; d < 3; d++) {
+      if (n[d] == 1) v.ct[d] = 0;
+      if (g[d] == 1) v.cb[d] = 0;
+      for (int64_t c : {v.ct[d], v.cb[d]})
+        if (c > kAffMax || c < -kAffMax) return false;
+      const int64_t t1 = v.ct[d] * (n[d] - 1), t2 = v.cb[d] * (g[d] - 1);
+      (t1 > 0 ? hi : lo) += t1;
+      (t2 > 0 ? hi : lo) += t2;
+    }
+    if (v.b > kAffMax || v.b < -kAffMax || lo < INT32_MIN || hi > INT32_MAX) return false;
     if (lo == hi) v = uni((int32_t)lo);
     return true;
   }
-  // Coefficient of lin when v is affine in lin; false otherwise.
-  bool lin_coef(const LVal& v, int64_t* a) const {
-    if (gx == 1) {
-      *a = v.ct;
+  // Whether v depends on dimension d's coordinates only through G_d (and
+  // then its coefficient of G_d).
+  bool global_form(const GVal& v, int d, int64_t* c) const {
+    if (g[d] == 1) {
+      *c = v.ct[d];
       return true;
     }
-    if (nx == 1) {
-      *a = v.cb;
+    if (n[d] == 1) {
+      *c = v.cb[d];
       return true;
     }
-    if (v.cb != v.ct * nx) return false;
-    *a = v.ct;
+    *c = v.ct[d];
+    return v.cb[d] == v.ct[d] * n[d];
+  }
+  // An access index in a merged dimension must be in global form; otherwise
+  // the dimension is split and the analysis runs again.
+  bool merge_ok(const GVal& v) {
+    if (v.k != 1) return true;
+    bool ok = true;
+    for (int d = 0; d < 3; d++) {
+      int64_t c = 0;
+      if (merged[d] && !global_form(v, d, &c)) {
+        need_split[d] = true;
+        ok = false;
+      }
+    }
+    return ok;
+  }
+  // Cuts where "c * x + b op 0" changes along x in [0, m) (c != 0).
+  static void add_cuts(std::vector<int64_t>& cuts, int64_t m, int op, int64_t c, int64_t b) {
+    auto add = [&](int64_t v) {
+      if (v >= 1 && v < m) cuts.push_back(v);
+    };
+    switch (op) {
+      case 11: add(c > 0 ? ceil_div(-b, c) : floor_div(-b, c) + 1); break;  // c x + b < 0
+      case 12: add(c > 0 ? floor_div(-b, c) + 1 : ceil_div(-b, c)); break;  // c x + b <= 0
+      default:                                                              // == 0, != 0
+        if ((-b) % c == 0) {
+          add(-b / c);
+          add(-b / c + 1);
+        }
+        break;
+    }
+  }
+  // The guard "v op 0" for v affine: records its cuts; false when its truth
+  // does not follow the axes (two dimensions, or one split dimension
+  // through both coordinates other than as G_d).
+  bool guard(const GVal& v, int op) {
+    int dim = -1;
+    for (int d = 0; d < 3; d++)
+      if (v.ct[d] || v.cb[d]) {
+        if (dim >= 0) return false;
+        dim = d;
+      }
+    if (dim < 0) return true;  // constant (norm makes this uniform first)
+    const int d = dim;
+    int64_t c = 0;
+    if (merged[d]) {
+      if (!global_form(v, d, &c)) {
+        need_split[d] = true;
+        return false;
+      }
+      add_cuts(cut_g[d], n[d] * g[d], op, c, v.b);
+      return true;
+    }
+    if (!v.cb[d]) {
+      add_cuts(cut_t[d], n[d], op, v.ct[d], v.b);
+      return true;
+    }
+    if (!v.ct[d]) {
+      add_cuts(cut_b[d], g[d], op, v.cb[d], v.b);
+      return true;
+    }
+    if (!global_form(v, d, &c)) return false;
+    // a staircase in (t_d, b_d): a cut at G = q * n + r splits block q
+    // between threads r - 1 and r, and blocks q - 1 | q | q + 1 apart
+    std::vector<int64_t> gc;
+    add_cuts(gc, n[d] * g[d], op, c, v.b);
+    for (int64_t x : gc) {
+      const int64_t q = x / n[d], r = x % n[d];
+      if (q >= 1) cut_b[d].push_back(q);
+      if (r != 0) {
+        cut_t[d].push_back(r);
+        if (q + 1 < g[d]) cut_b[d].push_back(q + 1);
+      }
+    }
     return true;
   }
-  static bool scale(LVal& v, int64_t s) {
-    for (int64_t* c : {&v.ct, &v.cb, &v.b}) {
+  GVal as_affine(const GVal& x) const {
+    if (x.k == 1) return x;
+    GVal v;
+    v.k = 1;
+    v.b = x.u;
+    return v;
+  }
+  static bool scale(GVal& v, int64_t s) {
+    for (int64_t* c : {&v.ct[0], &v.ct[1], &v.ct[2], &v.cb[0], &v.cb[1], &v.cb[2], &v.b}) {
       const __int128 p = (__int128)*c * s;
       if (p > kAffMax || p < -kAffMax) return false;
       *c = (int64_t)p;
     }
     return true;
   }
-  LVal as_affine(const LVal& x) const { return x.k == 1 ? x : affine(0, 0, x.u); }
-  LVal alu(int op, const LVal& x, const LVal& y) {
+  GVal alu(int op, const GVal& x, const GVal& y) {
     if (x.k == 0 && y.k == 0) return uni(uniform_alu(op, x.u, y.u));
-    if (x.k >= 2 || y.k >= 2) return other();
+    if (x.k == 3 || y.k == 3) return kind(3);
+    if (x.k != 1 && y.k != 1) return kind(2);  // cell constants and uniforms
+    if (x.k == 2 || y.k == 2) return kind(3);  // affine with a cell constant
     switch (op) {
       case 0:
       case 1: {
-        const LVal a = as_affine(x), c = as_affine(y);
-        return op == 0 ? affine(a.ct + c.ct, a.cb + c.cb, a.b + c.b)
-                       : affine(a.ct - c.ct, a.cb - c.cb, a.b - c.b);
+        const GVal a = as_affine(x), c = as_affine(y);
+        GVal v = a;
+        const int64_t s = op == 0 ? 1 : -1;
+        for (int d = 0; d < 3; d++) {
+          v.ct[d] += s * c.ct[d];
+          v.cb[d] += s * c.cb[d];
+        }
+        v.b += s * c.b;
+        return v;
       }
       case 2: {
-        if (x.k == 1 && y.k == 1) return other();
-        LVal v = x.k == 1 ? x : y;
-        return scale(v, x.k == 1 ? y.u : x.u) ? v : other();
+        if (x.k == 1 && y.k == 1) return kind(3);
+        GVal v = x.k == 1 ? x : y;
+        return scale(v, x.k == 1 ? y.u : x.u) ? v : kind(3);
       }
       case 3: {
-        if (y.k != 0) return other();
-        LVal v = x;
-        return scale(v, (int64_t)1 << ((uint32_t)y.u & 31u)) ? v : other();
+        if (y.k != 0) return kind(3);
+        GVal v = x;
+        return scale(v, (int64_t)1 << ((uint32_t)y.u & 31u)) ? v : kind(3);
       }
       case 11:
       case 12:
       case 13:
-      case 14: {  // a signed comparison of affine values: a predicate on lin
-        const LVal a = as_affine(x), c = as_affine(y);
-        LVal d = affine(a.ct - c.ct, a.cb - c.cb, a.b - c.b);
-        int64_t al = 0;
-        if (!norm(d)) return other();
-        if (d.k == 0)  // the coefficients cancel: the same comparison in every thread
-          return uni(op == 11 ? d.u < 0 : op == 12 ? d.u <= 0 : op == 13 ? d.u == 0 : d.u != 0);
-        if (!lin_coef(d, &al)) return other();
-        LVal p;
-        p.k = 2;
-        p.op = op;
-        p.ct = al;
-        p.b = d.b;
-        return p;
+      case 14: {  // a signed comparison of affine values: a guard
+        GVal dv = alu(1, as_affine(x), as_affine(y));
+        if (!norm(dv)) return kind(3);
+        if (dv.k == 0)
+          return uni(op == 11 ? dv.u < 0 : op == 12 ? dv.u <= 0 : op == 13 ? dv.u == 0 : dv.u != 0);
+        return guard(dv, op) ? kind(2) : kind(3);
       }
       default:
-        return other();
+        return kind(3);
     }
   }
-  LVal sreg(int id) const {
-    if (id == 0) return affine(1, 0, 0);
-    if (id == 6) return affine(0, 1, 0);
-    if (id == 1 || id == 2 || id == 7 || id == 8) return uni(0);
+  GVal sreg(int id) const {
+    GVal v;
+    if (id <= 2) {
+      v.k = 1;
+      v.ct[id] = 1;
+      return v;
+    }
     if (id <= 5) return uni((int32_t)in.block[id - 3]);
+    if (id <= 8) {
+      v.k = 1;
+      v.cb[id - 6] = 1;
+      return v;
+    }
     if (id <= 11) return uni((int32_t)in.grid[id - 9]);
     return uni(in.args[id - 12]);
   }
-  LVal load(const IrOp& o, int32_t idx) const {
+  GVal load(const IrOp& o, int32_t idx) const {
     const int64_t w = o.width, off = (int64_t)idx * w;
     const int64_t len = (int64_t)in.buf_len[o.buf];
     if (off < 0 || off + w > len || ((ir.shared_mask >> o.buf) & 1u)) return uni(0);
@@ -1274,19 +1379,8 @@ struct PrexLine {
         host_fmix32(ir.seed ^ ((uint32_t)o.buf * 0x9E3779B9u) ^ (uint32_t)((uint64_t)off >> 2));
     return uni(w == 1 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word);
   }
-  // The lins around where d = a * lin + b (a != 0) changes sign or is 0:
-  // with f = floor(-b / a), the truth of d < 0 and of d <= 0 flips between
-  // f - 1 and f or between f and f + 1 (whatever the sign of a), and d = 0
-  // can hold at f alone.
-  void add_threshold(int64_t a, int64_t b) {
-    if (a == 0) return;  // not reached: a predicate's d varies over the launch
-    int64_t f = -b / a;
-    if ((-b % a) != 0 && ((-b < 0) != (a < 0))) f--;
-    for (int64_t t = f - 1; t <= f + 1; t++)
-      if (t >= 0 && t < n) thresholds.push_back(t);
-  }
   struct State {
-    std::vector<LVal> r;
+    std::vector<GVal> r;
     uint64_t back = 0;
   };
   // Executes [pc, end) on st; false if the input does not qualify.
@@ -1296,7 +1390,7 @@ struct PrexLine {
       const uint8_t opc = o.opc;
       if (is_alu_reg(opc) || is_alu_imm(opc)) {
         const bool im = is_alu_imm(opc);
-        LVal v = alu(opc - (im ? 0x30 : 0x10), st.r[o.a], im ? uni(o.imm) : st.r[o.b]);
+        GVal v = alu(opc - (im ? 0x30 : 0x10), st.r[o.a], im ? uni(o.imm) : st.r[o.b]);
         if (!norm(v)) return false;
         st.r[o.dst] = v;
         pc++;
@@ -1304,7 +1398,7 @@ struct PrexLine {
       }
       switch (opc) {
         case B_SREG: {
-          LVal v = sreg(o.sreg);
+          GVal v = sreg(o.sreg);
           if (!norm(v)) return false;
           st.r[o.dst] = v;
           pc++;
@@ -1313,32 +1407,28 @@ struct PrexLine {
         case B_IMM: st.r[o.dst] = uni(o.imm); pc++; break;
         case B_MOV: st.r[o.dst] = st.r[o.a]; pc++; break;
         case B_SEL: {
-          const LVal& c = st.r[o.a];
-          if (c.k == 0) st.r[o.dst] = c.u ? st.r[o.b] : st.r[o.c];
-          else st.r[o.dst] = st.r[o.b] == st.r[o.c] ? st.r[o.b] : other();
+          const GVal& c = st.r[o.a];
+          const GVal &x = st.r[o.b], &y = st.r[o.c];
+          if (c.k == 0) st.r[o.dst] = c.u ? x : y;
+          else if (x == y) st.r[o.dst] = x;
+          else if (c.k == 2 && x.k != 1 && x.k != 3 && y.k != 1 && y.k != 3) st.r[o.dst] = kind(2);
+          else st.r[o.dst] = kind(3);
           pc++;
           break;
         }
         case B_LD:
         case B_ST: {
-          const LVal idx = st.r[o.a];
-          int64_t al = 0;
-          if (idx.k >= 2 || (idx.k == 1 && !lin_coef(idx, &al))) return false;
-          if (opc == B_LD) st.r[o.dst] = idx.k == 0 ? load(o, idx.u) : other();
+          const GVal idx = st.r[o.a];
+          if (idx.k == 3 || !merge_ok(idx)) return false;
+          if (opc == B_LD) st.r[o.dst] = idx.k == 0 ? load(o, idx.u) : kind(idx.k == 2 ? 2 : 3);
           pc++;
           break;
         }
         case B_IF: {
-          LVal c = st.r[o.a];
-          int64_t al = 0;
-          if (c.k == 1) {  // "value != 0" with value affine in lin
-            if (!lin_coef(c, &al)) return false;
-            LVal p;
-            p.k = 2;
-            p.op = 14;
-            p.ct = al;
-            p.b = c.b;
-            c = p;
+          GVal c = st.r[o.a];
+          if (c.k == 1) {  // "value != 0" with value affine: a guard
+            if (!guard(c, 14)) return false;
+            c = kind(2);
           }
           const int then_end = o.else_pc >= 0 ? o.else_pc : o.end_pc;
           if (c.k == 0) {
@@ -1348,11 +1438,13 @@ struct PrexLine {
               if (!exec(o.else_pc + 1, o.end_pc, st)) return false;
             }
           } else if (c.k == 2) {
-            add_threshold(c.ct, c.b);
             State a = st, e = st;
             if (!exec(pc + 1, then_end, a)) return false;
             if (o.else_pc >= 0 && !exec(o.else_pc + 1, o.end_pc, e)) return false;
-            for (size_t k = 0; k < st.r.size(); k++) st.r[k] = a.r[k] == e.r[k] ? a.r[k] : other();
+            for (size_t k = 0; k < st.r.size(); k++) {
+              const GVal &x = a.r[k], &y = e.r[k];
+              st.r[k] = x == y ? x : (x.k == 1 || x.k == 3 || y.k == 1 || y.k == 3) ? kind(3) : kind(2);
+            }
             st.back = std::max(a.back, e.back);
           } else {
             return false;
@@ -1380,19 +1472,73 @@ struct PrexLine {
   }
 };
 
-// The threads (linear ids g) that decide a 1D input's verdict, or false.
-bool prex_line_plan(const Ir& ir, const cufz_input& in, uint32_t budget, std::vector<uint32_t>* g) {
-  if (in.block[1] != 1 || in.block[2] != 1 || in.grid[1] != 1 || in.grid[2] != 1) return false;
-  PrexLine pl{ir, in, budget, in.block[0], in.grid[0], (int64_t)in.block[0] * in.grid[0], {}};
-  PrexLine::State st;
-  st.r.assign(std::max(ir.n_regs, 1), PrexLine::uni(0));
-  if (!pl.exec(0, (int)ir.ops.size(), st)) return false;
-  pl.thresholds.push_back(0);
-  pl.thresholds.push_back(pl.n - 1);
-  std::sort(pl.thresholds.begin(), pl.thresholds.end());
-  pl.thresholds.erase(std::unique(pl.thresholds.begin(), pl.thresholds.end()), pl.thresholds.end());
-  g->assign(pl.thresholds.begin(), pl.thresholds.end());
-  return true;
+// Coordinates on one axis that the plan takes: the ends and both sides of
+// every cut.
+std::vector<int64_t> axis_points(std::vector<int64_t> cuts, int64_t m) {
+  std::vector<int64_t> p = {0, m - 1};
+  for (int64_t v : cuts) {
+    p.push_back(v - 1);
+    p.push_back(v);
+  }
+  std::sort(p.begin(), p.end());
+  p.erase(std::unique(p.begin(), p.end()), p.end());
+  return p;
+}
+
+constexpr uint64_t kPrexPlanLimit = 1u << 16;  // larger plans: not eligible
+
+// The threads (linear ids g) that decide a guarded input's verdict, or false.
+bool prex_grid_plan(const Ir& ir, const cufz_input& in, uint32_t budget, std::vector<uint32_t>* out) {
+  bool merged[3];
+  for (int d = 0; d < 3; d++) merged[d] = true;
+  for (int pass = 0; pass < 4; pass++) {
+    PrexGrid pg{ir, in, budget, {merged[0], merged[1], merged[2]}};
+    for (int d = 0; d < 3; d++) {
+      pg.n[d] = in.block[d];
+      pg.g[d] = in.grid[d];
+    }
+    PrexGrid::State st;
+    st.r.assign(std::max(ir.n_regs, 1), PrexGrid::uni(0));
+    if (!pg.exec(0, (int)ir.ops.size(), st)) {
+      bool again = false;
+      for (int d = 0; d < 3; d++)
+        if (pg.need_split[d] && merged[d]) {
+          merged[d] = false;
+          again = true;
+        }
+      if (again) continue;
+      return false;
+    }
+    // per dimension: the (t, b) pairs of the plan
+    std::vector<std::pair<int64_t, int64_t>> tb[3];
+    uint64_t total = 1;
+    for (int d = 0; d < 3; d++) {
+      if (merged[d]) {
+        for (int64_t x : axis_points(pg.cut_g[d], pg.n[d] * pg.g[d]))
+          tb[d].push_back({x % pg.n[d], x / pg.n[d]});
+      } else {
+        const std::vector<int64_t> pt = axis_points(pg.cut_t[d], pg.n[d]);
+        const std::vector<int64_t> pb = axis_points(pg.cut_b[d], pg.g[d]);
+        for (int64_t b : pb)
+          for (int64_t t : pt) tb[d].push_back({t, b});
+      }
+      total *= tb[d].size();
+      if (total > kPrexPlanLimit) return false;
+    }
+    const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
+    out->clear();
+    for (const auto& z : tb[2])
+      for (const auto& y : tb[1])
+        for (const auto& x : tb[0]) {
+          const uint64_t bl = x.second + (uint64_t)in.grid[0] * (y.second + (uint64_t)in.grid[1] * z.second);
+          const uint64_t tl = x.first + (uint64_t)in.block[0] * (y.first + (uint64_t)in.block[1] * z.first);
+          out->push_back((uint32_t)(bl * T + tl));
+        }
+    std::sort(out->begin(), out->end());
+    out->erase(std::unique(out->begin(), out->end()), out->end());
+    return true;
+  }
+  return false;
 }
 
 bool prex_run(const Ir& ir, const cufz_input& in, uint32_t budget) {
@@ -1412,8 +1558,17 @@ struct PrexInfo {
   Ir ir;  // the program as given (unpruned): PREX looks at every access
 };
 
+// Launches the engine runs at all: valid shapes of at most 2^31 threads
+// (their linear thread ids fit 32 bits).
+bool prex_launch_ok(const cufz_input& in) {
+  if (launch_rejected(in)) return false;
+  const uint64_t nt = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * in.block[0] * in.block[1] *
+                      in.block[2];
+  return nt <= (1ull << 31);
+}
+
 bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget) {
-  return prex_run(p.ir, in, iter_budget);
+  return prex_launch_ok(in) && prex_run(p.ir, in, iter_budget);
 }
 
 std::vector<uint32_t> prex_corners(const cufz_input& in) {
@@ -1489,11 +1644,12 @@ void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask,
 
 bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
                std::vector<uint32_t>* threads) {
+  if (!prex_launch_ok(in)) return false;
   if (prex_run(p.ir, in, iter_budget)) {
     *threads = prex_corners(in);
     return true;
   }
-  return prex_line_plan(p.ir, in, iter_budget, threads);
+  return prex_grid_plan(p.ir, in, iter_budget, threads);
 }
 
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {

@@ -1,11 +1,16 @@
-"""PREX (Sec. 5.1): the engine's eligibility check, pinned to the oracle.
+"""PREX (Sec. 5.1): the engine's eligibility check and plan, pinned to the
+oracle.
 
-For every input the check accepts, the oracle's full-grid verdict (some
-thread violates or none does) must equal the verdict of the corner threads
-alone (every block and thread coordinate first or last), which is what the
-GPU runs under CUFZ_CF_PREX.  Inputs it must refuse: thread-dependent
-branches or loop trips, indices that are not affine in the thread and block
-indices, affine values that could wrap int32 in the launch box."""
+For every input the corner check accepts, the oracle's full-grid verdict
+(some thread violates or none does) must equal the verdict of the corner
+threads alone (every block and thread coordinate first or last).  For every
+input the plan covers (the corners, or for guarded launches the corners of
+the cells the guards cut the launch box into), each access site's verdict
+must equal the planned threads' verdict there.  The GPU runs exactly the
+plan under CUFZ_CF_PREX.  Inputs that must be refused: thread-dependent
+loop trips, indices that are not affine in the thread and block indices,
+guards across dimensions, affine values that could wrap int32 in the launch
+box, budget stops."""
 import numpy as np
 import pytest
 
@@ -125,7 +130,7 @@ def test_prex_wrap_case_really_breaks_the_theorem(orc):
 
 
 # ---------------------------------------------------------------------------
-# the plan: corners, or for guarded 1D launches the guards' change points
+# the plan: the corners, or for guarded launches the cells' corners
 # ---------------------------------------------------------------------------
 
 def plan_decides_every_site(orc, prog, inp, plan):
@@ -259,44 +264,200 @@ def test_plan_is_the_corners_when_the_check_holds():
         assert B.cufz_prex_plan(prog, inp).tolist() == want
 
 
-def test_plan_refuses():
-    tx = lambda A: A.sreg(bc.TID_X)
+def guarded_nd_program(rng, dims):
+    """Guards on one dimension's coordinate each (global G = ctaid * ntid +
+    tid, tid alone or ctaid alone, scaled), compared with arguments by <,
+    <=, ==, != or tested against zero, combined by AND / OR or nested, with
+    else arms; accesses at indices affine in all coordinates, at guard
+    values, and at selections between uniform values by a guard; a guard on
+    a value loaded at such an index; a guard inside a uniform loop."""
+    A = Asm(n_bufs=3, seed=rng.next32())
+    t = [A.sreg(bc.TID_X + d) for d in range(dims)]
+    b = [A.sreg(bc.CTAID_X + d) for d in range(dims)]
+    G = [A.alu(bc.ADD, A.alu(bc.MUL, b[d], A.sreg(bc.NTID_X + d)), t[d]) for d in range(dims)]
+    a0, a1, a2 = A.sreg(bc.ARG0), A.sreg(bc.ARG1), A.sreg(bc.ARG2)
+
+    def coord():
+        d, r = rng.below(dims), rng.below(4)
+        return G[d] if r < 2 else t[d] if r == 2 else b[d]
+
+    def aff():
+        v = A.alu(bc.ADD, a0, Imm(rng.randint(-3, 3)))
+        for _ in range(rng.randint(1, dims + 1)):
+            c = rng.choice((1, 1, 2, -1, 3, 8))
+            x = coord()
+            v = A.alu(bc.ADD, v, x if c == 1 else A.alu(bc.MUL, x, Imm(c)))
+        return v
+
+    def guard(truth_value=True):
+        x = coord()
+        if rng.below(3) == 0:
+            x = A.alu(bc.MUL, x, Imm(rng.choice((2, -1, 3))))
+        kind = rng.below(5 if truth_value else 4)
+        if kind == 0:
+            return A.alu(bc.SETLT, x, a1)
+        if kind == 1:
+            return A.alu(bc.SETLE, a2, x)
+        if kind == 2:
+            return A.alu(bc.SETEQ, x, a2)
+        if kind == 3:
+            return A.alu(bc.SETNE, A.alu(bc.ADD, x, Imm(1)), a1)
+        return A.alu(bc.SUB, x, a2)
+
+    def cond():
+        r = rng.below(4)
+        if r == 0:   # comparisons only: AND of 0/1 values is the logical and
+            return A.alu(bc.AND, guard(False), guard(False))
+        if r == 1:
+            return A.alu(bc.OR, guard(False), guard(False))
+        return guard()
+
+    def body(depth):
+        for _ in range(rng.randint(1, 3)):
+            r = rng.below(7)
+            if r <= 1 or depth >= 2:
+                A.ld(rng.below(3), aff(), rng.choice(bc.WIDTHS))
+            elif r == 2:
+                A.st(rng.below(3), aff(), A.imm(1), rng.choice((1, 4)))
+            elif r == 3:
+                A.if_(cond())
+                body(depth + 1)
+                if rng.below(2):
+                    A.else_()
+                    body(depth + 1)
+                A.endif()
+            elif r == 4:
+                sel = A.sel(guard(False), A.imm(rng.randint(-2, 40)), a0)
+                v = A.ld(rng.below(3), sel, 4)
+                A.if_(A.alu(bc.SETLT, A.alu(bc.AND, v, Imm(7)), Imm(3)))
+                A.ld(rng.below(3), aff(), 4)
+                A.endif()
+            elif r == 5:
+                A.ld(rng.below(3), guard(False), 8)
+            else:
+                k = A.loop(A.sreg(bc.ARG3), 3)
+                A.if_(A.alu(bc.SETLT, A.alu(bc.ADD, coord(), k), a1))
+                A.ld(rng.below(3), A.alu(bc.ADD, aff(), k), 4)
+                A.endif()
+                A.endloop()
+
+    body(0)
+    return A.build()
+
+
+def test_plan_decides_random_guarded_nd(orc):
+    rng = gen.SplitMix64(0x2D3D)
+    planned = violating = 0
+    sizes = []
+    for trial in range(72):
+        dims = 1 + trial % 3
+        prog = guarded_nd_program(rng, dims)
+        for _ in range(3):
+            block = [rng.randint(1, 8) for _ in range(dims)] + [1] * (3 - dims)
+            grid = [rng.randint(1, 4) for _ in range(dims)] + [1] * (3 - dims)
+            span = max(n * g for n, g in zip(block, grid))
+            args = (rng.randint(-4, 4), rng.randint(-3, span + 3), rng.randint(-2, span + 2),
+                    rng.randint(0, 3))
+            lens = [rng.randint(0, 4 * (12 * span + 16)) for _ in range(3)]
+            inp = mk(grid, block, args, lens)
+            plan = B.cufz_prex_plan(prog, inp)
+            assert plan is not None, (trial, args)
+            ok, full = plan_decides_every_site(orc, prog, inp, plan)
+            assert ok, (trial, args)
+            planned += 1
+            violating += full
+            sizes.append(len(plan) / float(np.prod(block) * np.prod(grid)))
+    assert planned == 216 and 30 < violating < 200
+    assert np.median(sizes) < 0.6                   # the plan is a fraction of the grid
+
+
+def test_plan_for_a_2d_bounds_guard_is_small(orc):
+    """row = ctaid.y * ntid.y + tid.y, col likewise; if (row < n && col < m)
+    C[row * m + col]: both dimensions stay merged, each contributes its ends
+    and the two threads around its bound, 16 threads of 65,536."""
+    A = Asm(n_bufs=1)
+    row = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_Y), A.sreg(bc.NTID_Y)), A.sreg(bc.TID_Y))
+    col = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    m = A.sreg(bc.ARG1)
+    A.if_(A.alu(bc.AND, A.alu(bc.SETLT, row, A.sreg(bc.ARG0)), A.alu(bc.SETLT, col, m)))
+    A.st(0, A.alu(bc.ADD, A.alu(bc.MUL, row, m), col), A.imm(1), 4)
+    A.endif()
+    prog = A.build()
+    for lens in (4 * 200 * 150, 4 * 200 * 150 - 4):          # exact, one element short
+        inp = mk((16, 16, 1), (16, 16, 1), (200, 150), (lens,))
+        plan = B.cufz_prex_plan(prog, inp)
+        assert len(plan) == 16
+        ok, full = plan_decides_every_site(orc, prog, inp, plan)
+        assert ok and full == (lens < 4 * 200 * 150)
+
+
+def test_plan_accepts_and_refuses(orc):
+    tx, ty = (lambda A: A.sreg(bc.TID_X)), (lambda A: A.sreg(bc.TID_Y))
     lin = lambda A: A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), tx(A))
-    guarded = _prog(lambda A: (A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0))),
-                               A.ld(0, lin(A), 4), A.endif()))
-    on_tx = _prog(lambda A: (A.if_(A.alu(bc.SETLT, tx(A), A.sreg(bc.ARG0))),
-                             A.ld(0, lin(A), 4), A.endif()))
-    both = _prog(lambda A: (A.if_(A.alu(bc.AND, A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0)),
-                                        A.alu(bc.SETLT, A.sreg(bc.ARG1), lin(A)))),
-                            A.ld(0, lin(A), 4), A.endif()))
-    loaded = _prog(lambda A: (A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0))),
-                              A.ld(1, A.ld(0, lin(A), 4), 4), A.endif()))
+    lt = lambda A, x, y: A.alu(bc.SETLT, x, y)
+
+    def guarded_by(cond):
+        return _prog(lambda A: (A.if_(cond(A)), A.ld(0, lin(A), 4), A.endif()))
 
     def diverged(A):
         r = A.imm(0)
-        A.if_(A.alu(bc.SETLT, lin(A), A.sreg(bc.ARG0)))
+        A.if_(lt(A, lin(A), A.sreg(bc.ARG0)))
         A.mov(lin(A), dst=r)
         A.endif()
         A.ld(0, r, 4)
 
-    diverged = _prog(diverged)
-
     def looped(A):
         k = A.loop(A.sreg(bc.ARG1), 200)
-        A.if_(A.alu(bc.SETLT, A.alu(bc.ADD, lin(A), k), A.sreg(bc.ARG0)))
+        A.if_(lt(A, A.alu(bc.ADD, lin(A), k), A.sreg(bc.ARG0)))
         A.ld(0, lin(A), 4)
         A.endif()
         A.endloop()
 
-    budget = _prog(looped)
     one_d = mk((4, 1, 1), (32, 1, 1), (50, 100), (400, 400))
-    two_d = mk((4, 1, 1), (8, 4, 1), (50, 100), (400, 400))
-    assert B.cufz_prex_plan(guarded, one_d) is not None
-    assert B.cufz_prex_plan(guarded, two_d) is None                   # a 2D block
-    assert B.cufz_prex_plan(on_tx, one_d) is None                     # tid.x alone over 4 blocks
-    assert B.cufz_prex_plan(on_tx, mk((1, 1, 1), (32, 1, 1), (5, 0), (400, 400))) is not None
-    assert B.cufz_prex_plan(both, one_d) is None                      # two guards combined
-    assert B.cufz_prex_plan(loaded, one_d) is None                    # a loaded index
-    assert B.cufz_prex_plan(diverged, one_d) is None                  # the arms leave different values
+    two_d = mk((4, 1, 1), (8, 4, 1), (5, 100), (400, 400))
+    accepted = {
+        "guard on the global index": (guarded_by(lambda A: lt(A, lin(A), A.sreg(bc.ARG0))), one_d),
+        "guard on tid.x over four blocks": (guarded_by(lambda A: lt(A, tx(A), A.sreg(bc.ARG0))), one_d),
+        "guard in a 2D block": (guarded_by(lambda A: lt(A, ty(A), Imm(2))), two_d),
+        "two guards and-ed": (guarded_by(lambda A: A.alu(bc.AND, lt(A, lin(A), A.sreg(bc.ARG0)),
+                                                         lt(A, A.sreg(bc.ARG1), lin(A)))), one_d),
+    }
+    for name, (prog, inp) in accepted.items():
+        plan = B.cufz_prex_plan(prog, inp)
+        assert plan is not None, name
+        assert plan_decides_every_site(orc, prog, inp, plan)[0], name
+    refused = {
+        "a guard across two dimensions": (guarded_by(lambda A: lt(A, A.alu(bc.ADD, tx(A), ty(A)),
+                                                                  Imm(5))), two_d),
+        "tid.x and ctaid.x in another mix than the global index":
+            (guarded_by(lambda A: lt(A, A.alu(bc.ADD, A.alu(bc.SHL, tx(A), Imm(1)),
+                                              A.sreg(bc.CTAID_X)), A.sreg(bc.ARG0))), one_d),
+        "a guard and-ed bitwise with a non-guard":
+            (guarded_by(lambda A: A.alu(bc.AND, lt(A, lin(A), A.sreg(bc.ARG0)),
+                                        A.alu(bc.SUB, lin(A), A.sreg(bc.ARG1)))), one_d),
+        "a loaded index": (_prog(lambda A: (A.if_(lt(A, lin(A), A.sreg(bc.ARG0))),
+                                            A.ld(1, A.ld(0, lin(A), 4), 4), A.endif())), one_d),
+        "an index plus a guard": (_prog(lambda A: A.ld(0, A.alu(bc.ADD, lin(A),
+                                                                lt(A, lin(A), A.sreg(bc.ARG0))),
+                                                      4)), one_d),
+        "arms leaving different indices": (_prog(diverged), one_d),
+        "a thread-dependent trip": (_prog(lambda A: (A.loop(tx(A), 8), A.ld(0, A.imm(0), 4),
+                                                     A.endloop())), one_d),
+    }
+    for name, (prog, inp) in refused.items():
+        assert B.cufz_prex_plan(prog, inp) is None, name
+    budget = _prog(looped)
     assert B.cufz_prex_plan(budget, one_d, iter_budget=4096) is not None
     assert B.cufz_prex_plan(budget, one_d, iter_budget=50) is None     # a budget stop
+
+
+def test_no_plan_for_launches_the_engine_does_not_run():
+    """Invalid shapes complete as INVALID_CONFIG and launches above 2^31
+    threads as LIMIT without running, so neither has a plan."""
+    prog = gen.c1_program()
+    for grid, block in (((0, 1, 1), (32, 1, 1)), ((4, 1, 1), (0, 1, 1)), ((1, 1, 1), (2048, 1, 1)),
+                        ((1, 70000, 1), (1, 1, 1)), ((2**31 - 1, 1, 1), (1024, 1, 1))):
+        inp = mk(grid, block, (0, 100), (400, 400, 400, 400))
+        assert B.cufz_prex_plan(prog, inp) is None, (grid, block)
+        assert not B.cufz_prex_check(prog, inp), (grid, block)
+    assert B.cufz_prex_plan(prog, mk((2**21, 1, 1), (1024, 1, 1), (0, 100), (400,) * 4)) is not None
