@@ -1,0 +1,61 @@
+// Internal program representation shared by the loader (decode, prune,
+// register allocation, code generation) and the PREX analysis: the decoded
+// program format (opcodes, structured control flow, sites).  Host-only.
+#pragma once
+
+#include <stdint.h>
+
+#include <vector>
+
+#include "engine.h"
+
+namespace cufz {
+
+enum : uint8_t {
+  B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04,
+  B_LD = 0x40, B_ST = 0x41, B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53,
+  B_ENDLOOP = 0x54
+};
+constexpr uint32_t kMagic = 0x315A4643u;
+
+inline bool is_alu_reg(uint8_t o) { return o >= 0x10 && o <= 0x1F; }
+inline bool is_alu_imm(uint8_t o) { return o >= 0x30 && o <= 0x3F; }
+
+// Virtual registers: 0..255 program registers, 256..271 special registers
+// (materialised at thread start), 272.. hidden loop-trip registers.
+constexpr int kSregBase = 256;
+constexpr int kTripBase = 272;
+
+struct IrOp {
+  uint8_t opc = 0;     // program-format opcode
+  int dst = -1, a = -1, b = -1, c = -1;
+  int32_t imm = 0;
+  int else_pc = -1, end_pc = -1, head_pc = -1;  // structure (head_pc: the IF/LOOP of an ELSE/ENDIF/ENDLOOP)
+  int site = -1;       // branch site (IF/LOOP) or access site (LD/ST)
+  int depth = 0;       // nesting depth of the op itself
+  int trip = -1;       // hidden trip vreg (LOOP, ENDLOOP)
+  bool kept = true;
+  bool value_dead = false;
+  int sreg = -1;       // SREG id (format level)
+  int buf = -1;
+  int width = 0;
+};
+
+struct Ir {
+  int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0;
+  uint32_t shared_mask = 0, seed = 0;
+  std::vector<uint16_t> loc0, loc1;
+  std::vector<IrOp> ops;
+  int nv = 0;  // vreg count (kTripBase + loops)
+};
+
+// Decodes and validates program bytes; false on any violation of the format.
+bool decode(const uint8_t* p, size_t n, Ir* ir);
+
+// A program's decoded form as given (unpruned) for PREX, which looks at
+// every access.
+struct PrexInfo {
+  Ir ir;
+};
+
+}  // namespace cufz

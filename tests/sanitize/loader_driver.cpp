@@ -1,5 +1,6 @@
-// Host-only driver for the loader built with AddressSanitizer and
-// UndefinedBehaviorSanitizer (tests/test_loader_sanitized.py).  Reads a
+// Host-only driver for the loader and the PREX analysis built with
+// AddressSanitizer and UndefinedBehaviorSanitizer
+// (tests/test_loader_sanitized.py).  Reads a
 // corpus of (program, inputs) records and runs every host-side analysis on
 // each: validation, pruning, code generation for both pruning modes,
 // loading, the PREX check and the PREX plan.  Any sanitizer report aborts
