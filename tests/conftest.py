@@ -15,6 +15,12 @@ def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
 
 
+def pytest_collection_modifyitems(config, items):
+    """The full-size workload tests run last: they take the longest, and the
+    quick parity tests should report first."""
+    items.sort(key=lambda item: "test_gpu_fullsize" in item.nodeid)
+
+
 def golden(name):
     rows = []
     with open(os.path.join(HERE, "golden", name)) as f:
