@@ -188,3 +188,34 @@ def test_prex_items_match_oracle(tmp_path, host_objs, orc):
         keep = np.isin(full["block_lin"].astype(np.int64) * T + full["thread_lin"], plans[k])
         assert record_set(recs) == record_set(full[keep]), k
         assert int(res["n_violations"]) == int(keep.sum()) and int(res["n_threads"]) == len(plans[k])
+
+
+def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
+    """Random and branch-heavy programs with random bit flips in their ops,
+    kept when both validators accept them (unusual opcode, operand and
+    nesting mixes the generators do not produce), under the default budget
+    and one that stops threads early."""
+    rng = gen.SplitMix64(0x3A7E)
+    progs, k = [], 0
+    while len(progs) < 24:
+        p = bytearray(gen.c2_program(500 + k) if k % 3 < 2 else gen.c4_program(500 + k))
+        k += 1
+        for _ in range(1 + rng.below(3)):
+            j = 32 + rng.below(len(p) - 32)
+            p[j] ^= 1 << rng.below(8)
+        if B.cufz_validate_program(bytes(p)) == 0 and orc.validate(bytes(p)) == 0:
+            progs.append(bytes(p))
+    ins = gen.c2_inputs(progs, per_program=2, seed=307, max_grid=2)
+    exe = build(tmp_path, host_objs, progs)
+    for budget in (4096, 5):
+        got = run(tmp_path, exe, progs, ins, budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
+                                          rec_cap=1 << 14, bitmaps=True)
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records"):
+                assert int(res[f]) == int(o[f]), (budget, i, f)
+            assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
+            assert np.array_equal(bm, obms[i]), (budget, i)
