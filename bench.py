@@ -427,8 +427,9 @@ def run_engine(args, rank, world, local, pg):
         "violating_inputs_per_step": tot["bug_inputs"] // max(args.steps, 1),
         "prex": ({"partial_inputs_per_step": tot["partial"] // max(args.steps, 1),
                   "note": "partial inputs ran only their PREX plan's threads (the corners, or for "
-                          "guarded 1D launches the guards' change points); their verdict is "
-                          "the full grid's, their accesses are the planned threads'"}
+                          "guarded launches the corners of the cells the guards cut the grid "
+                          "into); their verdict is the full grid's, their accesses are the "
+                          "planned threads'"}
                  if args.prex else None),
         "test_threads_per_step": tot["threads"] // max(args.steps, 1),
         "violations_per_step": tot["viol"] // max(args.steps, 1),
