@@ -221,7 +221,9 @@ cufz_status cufz_validate_program(const void* bytes, size_t nbytes);
  * drops every op whose result reaches no access index, branch condition or
  * loop trip count (stored values are dropped; loads stay as checked
  * accesses), then renumbers registers.  Writes the pruned program in the
- * same format to out (capacity out_cap bytes; *out_bytes gets its size).
+ * same format to out (capacity out_cap bytes; *out_bytes gets its size;
+ * CUFZ_E_NOMEM if out_cap is smaller, so out = NULL, out_cap = 0 asks for
+ * the size).  stats (may be NULL) receives the op and register counts.
  * Every access and branch decision of every thread is unchanged. */
 cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void* out, size_t out_cap,
                                size_t* out_bytes, cufz_prog_stats* stats);

@@ -1077,7 +1077,7 @@ extern "C" cufz_status cufz_validate_program(const void* bytes, size_t nbytes) {
 extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void* out,
                                           size_t out_cap, size_t* out_bytes,
                                           cufz_prog_stats* stats) {
-  if (!out || !out_bytes) return CUFZ_E_INVALID_ARG;
+  if ((!out && out_cap) || !out_bytes) return CUFZ_E_INVALID_ARG;
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
   int n_in = (int)ir.ops.size();

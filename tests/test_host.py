@@ -193,3 +193,40 @@ def test_generated_code_shape():
     assert "r11" not in src                            # the pruned sum x + y is gone
     full = B.cufz_program_cuda(gen.c1_program(), B.CF_NO_PRUNE)
     assert "r11 =" in full
+
+
+def test_abi_rejects_missing_arguments():
+    """Every entry point answers a missing context or output pointer with
+    CUFZ_E_INVALID_ARG (checked before any device call), and the host-only
+    calls report the size they need when the caller's buffer is too small."""
+    import ctypes
+    L = B.lib()
+    u32, u64, sz = ctypes.c_uint32(), ctypes.c_uint64(), ctypes.c_size_t()
+    ref = ctypes.byref
+    null_ctx = {
+        "cufz_destroy": (), "cufz_unload_program": (0,), "cufz_new_epoch": (), "cufz_release": (1,),
+        "cufz_sync": (0,), "cufz_reset_stats": (), "cufz_set_program_path": (0, 1),
+        "cufz_compile_programs": (None, 0), "cufz_get_union": (None,),
+        "cufz_get_bitmap": (1, None), "cufz_get_program_path": (0, ref(u32)),
+        "cufz_load_program": (None, 0, ref(u32), None),
+        "cufz_submit_inputs": (None, 0, ref(u32), ref(u64)),
+        "cufz_poll_results": (None, 0, ref(u32), 0), "cufz_get_records": (1, None, 0, ref(u32)),
+        "cufz_autotune": (None, 0, ref(u32)), "cufz_verify_prune": (0, None, 0, ref(u32)),
+        "cufz_get_stats": (None,),
+    }
+    for name, args in null_ctx.items():
+        assert getattr(L, name)(None, *args) == B.E_INVALID_ARG, name
+    prog = gen.c1_program()
+    inp = gen.c1_inputs(1)
+    assert L.cufz_create(None, None) == B.E_INVALID_ARG
+    assert L.cufz_validate_program(None, 0) == B.E_INVALID_PROGRAM
+    assert L.cufz_prex_check(None, 0, None, 0, ref(u32)) == B.E_INVALID_ARG
+    assert L.cufz_prex_plan(prog, len(prog), inp.ctypes.data, 0, None, 4, ref(u32)) == B.E_INVALID_ARG
+    assert L.cufz_prex_plan(prog, len(prog), inp.ctypes.data, 0, None, 0, ref(u32)) == B.E_NOMEM
+    assert u32.value == 4                                     # the plan's size
+    assert L.cufz_run_noalloc(None, 0, None, 0, 0, 0, None, 0, None, None, None) == B.E_INVALID_ARG
+    assert L.cufz_int32_peak(0, None, None) == B.E_INVALID_ARG
+    assert L.cufz_program_cuda(prog, len(prog), 0, None, 0, ref(sz)) == B.E_NOMEM and sz.value > 100
+    stats = B.cufz_prog_stats()
+    assert L.cufz_prune_program(prog, len(prog), None, 0, ref(sz), ref(stats)) == B.E_NOMEM
+    assert sz.value == len(B.cufz_prune_program(prog)[0])
