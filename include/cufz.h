@@ -27,9 +27,31 @@
  *   - A context may be used from several host threads; calls on one
  *     context are serialised by an internal lock.
  *
- * Program format: see the header comment of bytecode.py in the Python
- * package (32-byte header, LOC table, 8-byte ops).  Input, result and
- * violation records are the fixed-layout structs below.
+ * Program format (little endian; the Python package's bytecode.py encodes
+ * it):
+ *   header, 32 bytes: u32 magic 0x315A4643 ("CFZ1"), u16 version 1, u16
+ *     n_ops (1..2048), u8 n_regs, u8 n_bufs (<= 9), u8 n_sites (IF and LOOP
+ *     ops), u8 0, u16 shared_mask (bit k: buffer k is per-block shared
+ *     memory), u16 0, u32 seed (content of the global buffers), u32 0 x 3;
+ *   LOC table: n_sites x {u16 LOC not taken / exit, u16 LOC taken};
+ *   ops, 8 bytes each: u8 opcode, u8 dst, u8 a, u8 b, i32 imm (unused
+ *     fields 0).  The size is exactly 32 + 4 n_sites + 8 n_ops.
+ * Opcodes: 0x01 SREG dst = special register imm (0-2 tid.xyz, 3-5
+ * ntid.xyz, 6-8 ctaid.xyz, 9-11 nctaid.xyz, 12-15 scalar args 0-3); 0x02 IMM
+ * dst = imm; 0x03 MOV dst = a; 0x04 SEL dst = a != 0 ? b : register imm;
+ * 0x10-0x1F ALU dst = a op b and 0x30-0x3F the same with b = imm, op in
+ * order add, sub, mul, shl, shr (arithmetic), shru, and, or, xor, min, max
+ * (signed), setlt, setle, seteq, setne (signed, 0 or 1), setltu (unsigned),
+ * all on int32 with wrap-around and shift counts taken mod 32; 0x40 LD dst =
+ * buffer b at index a, width imm (1, 4, 8 or 16 bytes); 0x41 ST register
+ * dst to buffer b at index a, width imm (checked, never performed); 0x50 IF
+ * a, 0x51 ELSE, 0x52 ENDIF; 0x53 LOOP with counter dst and trip count
+ * clamp(a, 0, imm), 0x54 ENDLOOP.
+ * Control flow is structured, at most 16 deep; a loop counter is read-only
+ * in its body.  The k-th LD/ST in program order is access site k, the k-th
+ * IF/LOOP branch site k.
+ *
+ * Input, result and violation records are the fixed-layout structs below.
  */
 #ifndef CUFZ_H
 #define CUFZ_H
