@@ -307,6 +307,21 @@ cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* i
                            uint32_t iter_budget, uint32_t* threads, uint32_t cap,
                            uint32_t* n_threads);
 
+/* The fuzzing campaign's mutator (host-only, no device needed): mutates n
+ * input records in place.  Each input gets one to three mutations of a
+ * scalar argument or of the length of one of its program's buffers
+ * (buffers 0 .. n_bufs[program_id] - 1).  A mutation flips one bit (of the
+ * low 24 for a length), adds or subtracts 1..35 (a length stops at 0), or
+ * substitutes a boundary value: 0, +-1, 2^k, 2^k +- 1 or -2^k for an
+ * argument, and one of 29 lengths from 0 to 65536.  These are AFL's
+ * deterministic-stage kinds drawn at random (Sec. 2.1).  Launch shapes are
+ * left alone.  The draws come from a SplitMix64 stream whose 64-bit state
+ * *rng_state is read and advanced, so a campaign resumes exactly from a
+ * saved state.  CUFZ_E_INVALID_ARG for a program_id >= n_programs or an
+ * n_bufs entry above 9 (and then nothing is changed). */
+cufz_status cufz_mutate_inputs(cufz_input* inputs, uint32_t n, const uint8_t* n_bufs,
+                               uint32_t n_programs, uint64_t* rng_state);
+
 /* Human-readable name of a status code. */
 const char* cufz_status_str(cufz_status s);
 

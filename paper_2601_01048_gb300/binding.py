@@ -86,7 +86,7 @@ EXPORTS = [
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
     "cufz_unload_program", "cufz_verify_prune", "cufz_prex_check",
-    "cufz_prex_plan",
+    "cufz_prex_plan", "cufz_mutate_inputs",
 ]
 
 
@@ -131,6 +131,7 @@ def lib():
                 "cufz_verify_prune": (i32, [vp, u32, vp, u32, P(u32)]),
                 "cufz_prex_check": (i32, [vp, sz, vp, u32, P(u32)]),
                 "cufz_prex_plan": (i32, [vp, sz, vp, u32, P(u32), u32, P(u32)]),
+                "cufz_mutate_inputs": (i32, [vp, u32, vp, u32, P(u64)]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -227,6 +228,18 @@ def cufz_prex_plan(prog: bytes, inp: np.ndarray, iter_budget: int = 0) -> np.nda
             continue
         _check(st, "cufz_prex_plan")
         return out[: n.value].copy() if n.value else None
+
+
+def cufz_mutate_inputs(inputs: np.ndarray, n_bufs, rng_state: int) -> int:
+    """Mutates the input records in place (they must be a contiguous
+    INPUT_DTYPE array); returns the advanced generator state."""
+    if inputs.dtype != INPUT_DTYPE or not inputs.flags["C_CONTIGUOUS"]:
+        raise CufzError(E_INVALID_ARG, "cufz_mutate_inputs")
+    nb = np.ascontiguousarray(n_bufs, dtype=np.uint8)
+    st = ctypes.c_uint64(rng_state)
+    _check(lib().cufz_mutate_inputs(inputs.ctypes.data, len(inputs), nb.ctypes.data, len(nb),
+                                    ctypes.byref(st)), "cufz_mutate_inputs")
+    return st.value
 
 
 def cufz_verify_prune(ctx, program_id: int, inputs: np.ndarray) -> int:

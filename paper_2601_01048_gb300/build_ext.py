@@ -14,7 +14,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcufz.so")
-SOURCES = ["engine.cu", "runtime.cu", "loader.cpp", "prex.cpp", "noalloc.cu"]
+SOURCES = ["engine.cu", "runtime.cu", "loader.cpp", "prex.cpp", "mutate.cpp", "noalloc.cu"]
 # device headers handed to the runtime compiler for the compiled path, under
 # the names the sources include them by
 JIT_HEADERS = [("jit_kernel.cuh", "jit_kernel.cuh"), ("jit_launch.cuh", "jit_launch.cuh"),

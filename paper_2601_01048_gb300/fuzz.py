@@ -10,7 +10,8 @@ bitmaps) runs on the device through the engine:
   - each round takes `batch` parents from the corpus, favoured entries first
     (those that brought new coverage and were picked least often), mutates
     copies of them (bit flips, +-1..35, boundary values on the scalar
-    arguments and buffer lengths, gen.Mutator) and runs them as one batch;
+    arguments and buffer lengths: cufz_mutate_inputs, the library's native
+    form of gen.Mutator) and runs them as one batch;
   - an input whose result carries CUFZ_FL_NEW_COV (a bucket bit the union
     lacked when the round started) joins the corpus as a favoured entry;
   - a violating input is filed under (program, first record's site, class),
@@ -31,6 +32,7 @@ import dataclasses
 
 import numpy as np
 
+from . import binding as B
 from .gen import INPUT_DTYPE, Mutator, SplitMix64
 
 
@@ -102,8 +104,8 @@ class Campaign:
     def run_round(self) -> RoundStats:
         parents = self._parents()
         kids = self.corpus[parents].copy()
-        for k in range(len(kids)):
-            self.mutator.mutate(kids[k], self.n_bufs[int(kids[k]["program_id"])])
+        # the library's mutator: the same draws as gen.Mutator, natively
+        self.mutator.rng.state = B.cufz_mutate_inputs(kids, self.n_bufs, self.mutator.rng.state)
         np.add.at(self.picks, parents, 1)
         self.favoured[parents] = False
         res, first = self.ex.run(kids)

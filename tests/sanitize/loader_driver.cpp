@@ -3,7 +3,7 @@
 // (tests/test_loader_sanitized.py).  Reads a
 // corpus of (program, inputs) records and runs every host-side analysis on
 // each: validation, pruning, code generation for both pruning modes,
-// loading, the PREX check and the PREX plan.  Any sanitizer report aborts
+// loading, the PREX check and the PREX plan, and the input mutator.  Any sanitizer report aborts
 // the process with a non-zero status.
 //
 // Corpus record: u32 program bytes, u32 input count, the program, then the
@@ -54,6 +54,11 @@ int main(int argc, char** argv) {
     LoadedProgram lp;
     if (load_program(prog.data(), plen, true, &lp) == CUFZ_OK) free_program(&lp);
     std::vector<uint32_t> threads(4096);
+    std::vector<cufz_input> mutated(ins);
+    for (cufz_input& in : mutated) in.program_id = 0;
+    const uint8_t n_bufs = prog[9];
+    uint64_t state = (uint64_t)programs;
+    cufz_mutate_inputs(mutated.data(), (uint32_t)mutated.size(), &n_bufs, 1, &state);
     for (const cufz_input& in : ins) {
       uint32_t eligible = 0, nt = 0;
       cufz_prex_check(prog.data(), plen, &in, 0, &eligible);

@@ -110,3 +110,33 @@ def test_checkpoint_resume_continues_exactly(tmp_path):
     assert after_a == after_b
     assert np.array_equal(a.corpus, b.corpus) and a.rounds == b.rounds == 9
     assert {k: v["hits"] for k, v in a.buckets.items()} == {k: v["hits"] for k, v in b.buckets.items()}
+
+
+def test_native_mutator_draws_like_the_generator_mutator():
+    """cufz_mutate_inputs (the campaign's mutator) makes the same draws as
+    gen.Mutator: the same records and the same generator state after them,
+    over programs with 0 to 9 buffers and arguments and lengths at random;
+    a program id without an entry is refused and changes nothing."""
+    rng = gen.SplitMix64(7)
+    n_bufs = [rng.below(10) for _ in range(20)]
+    x = gen.make_inputs(3000)
+    for k in range(len(x)):
+        gen.set_input(x[k], rng.below(20), (rng.randint(1, 9), 1, 1), (32, 1, 1),
+                      [rng.randint(-2**31, 2**31 - 1) for _ in range(4)],
+                      [rng.randint(0, 1 << 40) for _ in range(9)])
+    a, b = x.copy(), x.copy()
+    m = gen.Mutator(0xF022)
+    for k in range(len(a)):
+        m.mutate(a[k], n_bufs[int(a[k]["program_id"])])
+    state = B.cufz_mutate_inputs(b, n_bufs, 0xF022)
+    assert state == m.rng.state
+    assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+    assert (a != x).all()                                 # every record changed
+    c = x[:4].copy()
+    c[2]["program_id"] = 20
+    try:
+        B.cufz_mutate_inputs(c, n_bufs, 1)
+        raise AssertionError("accepted a program id without a buffer count")
+    except B.CufzError as e:
+        assert e.status == B.E_INVALID_ARG
+    assert np.array_equal(c[[0, 1, 3]], x[[0, 1, 3]])

@@ -1,5 +1,5 @@
-"""The loader's host code (decoder, validator, pruning, code generator) and
-the PREX check and plan, and the CPU oracle, each built with AddressSanitizer
+"""The loader's host code (decoder, validator, pruning, code generator), the
+PREX check and plan, the input mutator, and the CPU oracle, each built with AddressSanitizer
 and UndefinedBehaviorSanitizer and run over every workload program and
 random PREX-shaped programs, each as given and with random byte mutations
 (most rejected by the validators, some valid but unusual), with inputs at
@@ -40,6 +40,7 @@ def build_loader_driver(tmp_path):
     exe = str(tmp_path / "loader_sanitized")
     compile_or_skip([gxx, "-std=c++17", *SAN, "-I", cuda_inc, "-I", CSRC,
                      "-x", "c++", os.path.join(CSRC, "loader.cpp"), os.path.join(CSRC, "prex.cpp"),
+                     os.path.join(CSRC, "mutate.cpp"),
                      os.path.join(HERE, "sanitize", "loader_driver.cpp"), "-o", exe])
     return exe
 
