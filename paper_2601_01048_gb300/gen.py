@@ -296,6 +296,54 @@ def affine_inputs(n: int = 4096, seed: int | None = None, max_blocks: int = 6553
 
 
 # --------------------------------------------------------------------------
+# guarded 2D workload: bounds-guarded matrix kernels (the guarded class of
+# Sec. 5.1's Alg. 1 in two dimensions, like the paper's matmul)
+# --------------------------------------------------------------------------
+
+G2_WIDTHS = (4, 4, 8, 1, 16, 4, 8, 4, 4, 1, 4, 16, 8, 4, 4, 4)
+
+
+def guard2d_family_program(off: int, w: int, seed: int) -> bytes:
+    """row = ctaid.y * ntid.y + tid.y, col = ctaid.x * ntid.x + tid.x;
+    if (row < arg0 && col < arg1) { A[row * arg1 + col]; B[row * arg1 + col
+    + off]; C[row * arg1 + col] = ... } with accesses of width w."""
+    A = Asm(n_bufs=3, seed=seed)
+    row = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_Y), A.sreg(bc.NTID_Y)), A.sreg(bc.TID_Y))
+    col = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    n, m = A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    A.if_(A.alu(bc.AND, A.alu(bc.SETLT, row, n), A.alu(bc.SETLT, col, m)))
+    i = A.alu(bc.ADD, A.alu(bc.MUL, row, m), col)
+    x = A.ld(0, i, w)
+    y = A.ld(1, A.alu(bc.ADD, i, Imm(off)), w)
+    A.st(2, i, A.alu(bc.ADD, x, y), w)
+    A.endif()
+    return A.build()
+
+
+def guard2d_programs() -> list[bytes]:
+    rng = SplitMix64(sub_seed("g2prog"))
+    return [guard2d_family_program(rng.randint(-2, 2) if p else 0, G2_WIDTHS[p], seed=rng.next32())
+            for p in range(16)]
+
+
+def guard2d_inputs(n: int = 4096, seed: int | None = None, max_grid: int = 256) -> np.ndarray:
+    """Blocks 8x8, 16x16, 32x8 or 32x32; gx, gy log-uniform in [1, max_grid];
+    rows and columns uniform up to the grid's extent (the guards cut inside
+    the grid); each buffer holds rows x columns elements, one in ten an
+    element short."""
+    rng = SplitMix64(sub_seed("g2") if seed is None else seed)
+    out = make_inputs(n)
+    for k in range(n):
+        p = rng.below(16)
+        bx, by = rng.choice(((8, 8), (16, 16), (32, 8), (32, 32)))
+        gx, gy = rng.loguniform_int(1, max_grid), rng.loguniform_int(1, max_grid)
+        rows, cols = rng.randint(1, gy * by), rng.randint(1, gx * bx)
+        lens = [G2_WIDTHS[p] * (rows * cols - (1 if rng.uniform() < 0.10 else 0)) for _ in range(3)]
+        set_input(out[k], p, (gx, gy, 1), (bx, by, 1), (rows, cols), lens, tag=k)
+    return out
+
+
+# --------------------------------------------------------------------------
 # config 2: random 2D programs with shared buffers and loops
 # --------------------------------------------------------------------------
 

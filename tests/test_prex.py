@@ -461,3 +461,19 @@ def test_no_plan_for_launches_the_engine_does_not_run():
         assert B.cufz_prex_plan(prog, inp) is None, (grid, block)
         assert not B.cufz_prex_check(prog, inp), (grid, block)
     assert B.cufz_prex_plan(prog, mk((2**21, 1, 1), (1024, 1, 1), (0, 100), (400,) * 4)) is not None
+
+
+def test_plan_decides_guard2d_workload(orc):
+    """The bounds-guarded 2D workload (if (row < n && col < m) over the
+    matrix): at most 16 planned threads per input, every site decided."""
+    progs = gen.guard2d_programs()
+    ins = gen.guard2d_inputs(32, seed=9, max_grid=6)
+    violating = 0
+    for x in ins:
+        prog = progs[int(x["program_id"])]
+        plan = B.cufz_prex_plan(prog, x)
+        assert plan is not None and len(plan) <= 16
+        ok, full = plan_decides_every_site(orc, prog, x, plan)
+        assert ok
+        violating += full
+    assert 0 < violating < len(ins)
