@@ -88,7 +88,8 @@ def test_prex_verdicts(B, orc, path):
         for p in progs:
             E.load(p)
         dres, drecs, dbms = E.run(ins)
-    ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 20, bitmaps=True)
+    ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 15, bitmaps=True)
+    assert np.array_equal(ores["n_records"], ores["n_violations"])   # every record kept
     n_viol = [0, 0]
     for k in range(len(ins)):
         d, o = dres[k], ores[k]
