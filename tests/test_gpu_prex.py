@@ -81,7 +81,7 @@ def test_prex_verdicts(B, orc, path):
     n_aff, n_c1, n_c2 = len(aff), len(c1), len(c2)
     assert all(corner[:n_aff]) and not any(corner[n_aff:])
     guarded = list(range(n_aff, n_aff + n_c1)) + list(range(n_aff + n_c1 + n_c2, len(ins)))
-    assert all(plans[k] is not None for k in guarded)          # guarded 1D: line plans
+    assert all(plans[k] is not None for k in guarded)          # guarded launches: cell plans
     # random programs: masked, clamped and loaded indices
     assert all(plans[k] is None for k in range(n_aff + n_c1, n_aff + n_c1 + n_c2))
     with B.Engine(max_slots=128, record_cap=1 << 15, flags=B.CF_KEEP_BITMAPS | B.CF_PREX | path) as E:
