@@ -16,19 +16,26 @@ bitmaps) runs on the device through the engine:
     lacked when the round started) joins the corpus as a favoured entry;
   - a violating input is filed under (program, first record's site, class),
     so repeated reports of one bug collapse into one bucket;
+  - an input that hit the back-edge budget (CUFZ_FL_BUDGET, the analog of
+    the paper's hang timeout, Sec. 7.1) is a hang; as in AFL, a hang is
+    unique, and kept, when it also reached new coverage;
   - the round ends with cufz_new_epoch, so the next round's NEW_COV is
     measured against everything seen so far.
 
 A campaign starts by running its seed corpus once (AFL's dry run), so the
 union is at every moment the OR of the corpus's bitmaps: every input that
 added a bucket bit is in the corpus.  `checkpoint` writes the corpus, the bug
-buckets and the random state to one .npz file; `Campaign.resume` reads it and
-runs the corpus once, which rebuilds the device union, after which the
-campaign continues exactly as it would have without the interruption.
+buckets, the unique hangs and the random state to one .npz file;
+`Campaign.resume` reads it and runs the corpus once, which rebuilds the
+device union, after which the campaign continues exactly as it would have
+without the interruption.  `stats()` reports the columns of the paper's
+Table 2: executions and executions per second, unique crashes (bug
+buckets), unique hangs, queue cycles and the corpus size.
 """
 from __future__ import annotations
 
 import dataclasses
+import time
 
 import numpy as np
 
@@ -43,6 +50,9 @@ class RoundStats:
     violating: int
     new_buckets: int
     corpus_size: int
+    hangs: int = 0
+    new_hangs: int = 0
+    seconds: float = dataclasses.field(default=0.0, compare=False)
 
 
 class EngineExecutor:
@@ -71,6 +81,7 @@ class Campaign:
     lengths of buffers the program has)."""
 
     NEW_COV = 4   # CUFZ_FL_NEW_COV
+    BUDGET = 1    # CUFZ_FL_BUDGET
     VIOLATION = 1  # CUFZ_ST_VIOLATION
 
     def __init__(self, executor, n_bufs: list[int], seeds: np.ndarray, seed: int = 0xF022,
@@ -86,8 +97,11 @@ class Campaign:
         self.favoured = np.ones(len(self.corpus), dtype=bool)
         self.picks = np.zeros(len(self.corpus), dtype=np.int64)
         self.buckets: dict[tuple[int, int, int], dict] = {}
+        self.hangs: list[dict] = []   # unique hangs: {"input", "round"}
+        self.n_hangs = 0              # executions that hit the budget
         self.rounds = 0
         self.executed = 0
+        self.seconds = 0.0
         # the dry run: the seeds' coverage becomes the union's starting point
         self.ex.run(self.corpus)
         self.ex.new_epoch()
@@ -102,6 +116,7 @@ class Campaign:
         return np.tile(order, reps)[: self.batch]
 
     def run_round(self) -> RoundStats:
+        t0 = time.perf_counter()
         parents = self._parents()
         kids = self.corpus[parents].copy()
         # the library's mutator: the same draws as gen.Mutator, natively
@@ -124,14 +139,32 @@ class Campaign:
                 new_buckets += 1
             else:
                 b["hits"] += 1
+        hang = (res["flags"] & self.BUDGET) != 0
+        new_hang = hang & new_cov
+        for k in np.flatnonzero(new_hang):
+            self.hangs.append({"input": kids[k].copy(), "round": self.rounds})
+        self.n_hangs += int(hang.sum())
         if new_cov.any():
             self.corpus = np.concatenate([self.corpus, kids[new_cov]])
             self.favoured = np.concatenate([self.favoured, np.ones(int(new_cov.sum()), bool)])
             self.picks = np.concatenate([self.picks, np.zeros(int(new_cov.sum()), np.int64)])
         self.ex.new_epoch()
         self.rounds += 1
+        dt = time.perf_counter() - t0
+        self.seconds += dt
         return RoundStats(len(kids), int(new_cov.sum()), int(violating.sum()), new_buckets,
-                          len(self.corpus))
+                          len(self.corpus), int(hang.sum()), int(new_hang.sum()), dt)
+
+    def stats(self) -> dict:
+        """The campaign so far in the terms of the paper's Table 2."""
+        return {"execs_done": self.executed,
+                "execs_per_sec": self.executed / self.seconds if self.seconds > 0 else 0.0,
+                "unique_crashes": len(self.buckets),
+                "unique_hangs": len(self.hangs),
+                "hang_execs": self.n_hangs,
+                "cycles_done": int(self.picks.min()) if len(self.picks) else 0,
+                "corpus_count": len(self.corpus),
+                "rounds": self.rounds}
 
     # ------------------------------------------------------ checkpoints
     def checkpoint(self, path: str) -> None:
@@ -144,8 +177,10 @@ class Campaign:
                                       dtype=np.int64),
                  bucket_rounds=np.array([self.buckets[tuple(k)]["round"] for k in keys.tolist()],
                                         dtype=np.int64),
+                 hang_inputs=np.array([h["input"] for h in self.hangs], dtype=INPUT_DTYPE),
+                 hang_rounds=np.array([h["round"] for h in self.hangs], dtype=np.int64),
                  state=np.array([self.rng.state, self.mutator.rng.state, self.rounds,
-                                 self.executed, self.batch], dtype=np.uint64),
+                                 self.executed, self.batch, self.n_hangs], dtype=np.uint64),
                  n_bufs=np.array(self.n_bufs, dtype=np.int64))
 
     @classmethod
@@ -158,7 +193,9 @@ class Campaign:
         c.favoured = z["favoured"].astype(bool)
         c.picks = z["picks"].astype(np.int64)
         c.rng.state, c.mutator.rng.state = state[0], state[1]
-        c.rounds, c.executed = state[2], state[3]
+        c.rounds, c.executed, c.n_hangs = state[2], state[3], state[5]
+        c.hangs = [{"input": inp.copy(), "round": rnd}
+                   for inp, rnd in zip(z["hang_inputs"], z["hang_rounds"].tolist())]
         for k, inp, hits, rnd in zip(z["bucket_keys"].tolist(), z["bucket_inputs"],
                                      z["bucket_hits"].tolist(), z["bucket_rounds"].tolist()):
             c.buckets[tuple(k)] = {"input": inp.copy(), "hits": hits, "round": rnd}

@@ -12,8 +12,9 @@ VIOL = np.dtype([("site", "<u2"), ("cls", "u1")])
 
 class FakeExecutor:
     """Edges of an input: (program, arg0 // 64, len0 // 256); it violates
-    when len0 < 100, at site arg1 & 3 with class 1 + (len0 & 1).  NEW_COV and
-    the union follow the engine's rules (snapshot at each epoch)."""
+    when len0 < 100, at site arg1 & 3 with class 1 + (len0 & 1), and hits the
+    back-edge budget when arg1 is a multiple of 5.  NEW_COV and the union
+    follow the engine's rules (snapshot at each epoch)."""
 
     def __init__(self):
         self.union_set, self.snapshot = set(), set()
@@ -32,6 +33,8 @@ class FakeExecutor:
             if e - self.snapshot:
                 res[k]["flags"] |= B.FL_NEW_COV
             self.union_set |= e
+            if int(x["args"][1]) % 5 == 0:
+                res[k]["flags"] |= B.FL_BUDGET
             bad = int(x["buf_len"][0]) < 100
             res[k]["status"] = B.ST_VIOLATION if bad else B.ST_OK
             if bad:
@@ -109,6 +112,9 @@ def test_checkpoint_resume_continues_exactly(tmp_path):
     after_b = [b.run_round() for _ in range(5)]
     assert after_a == after_b
     assert np.array_equal(a.corpus, b.corpus) and a.rounds == b.rounds == 9
+    assert [(h["round"], h["input"].tobytes()) for h in a.hangs] == \
+        [(h["round"], h["input"].tobytes()) for h in b.hangs]
+    assert a.n_hangs == b.n_hangs
     assert {k: v["hits"] for k, v in a.buckets.items()} == {k: v["hits"] for k, v in b.buckets.items()}
 
 
@@ -140,3 +146,23 @@ def test_native_mutator_draws_like_the_generator_mutator():
     except B.CufzError as e:
         assert e.status == B.E_INVALID_ARG
     assert np.array_equal(c[[0, 1, 3]], x[[0, 1, 3]])
+
+
+def test_hangs_and_campaign_stats():
+    """Budget stops are hangs; a hang that also reached new coverage is a
+    unique hang and is kept (AFL's rule); stats() reports the paper's Table 2
+    columns."""
+    ex = FakeExecutor()
+    c = Campaign(ex, [3, 3], seeds(), seed=5, batch=64)
+    rounds = [c.run_round() for _ in range(10)]
+    assert sum(r.hangs for r in rounds) == c.n_hangs > 0
+    assert sum(r.new_hangs for r in rounds) == len(c.hangs) > 0
+    assert all(r.new_hangs <= min(r.hangs, r.new_coverage) for r in rounds)
+    for h in c.hangs:
+        assert int(h["input"]["args"][1]) % 5 == 0
+        assert any(h["input"].tobytes() == x.tobytes() for x in c.corpus)
+    s = c.stats()
+    assert s["execs_done"] == 640 and s["execs_per_sec"] > 0
+    assert s["unique_crashes"] == len(c.buckets) and s["unique_hangs"] == len(c.hangs)
+    assert s["corpus_count"] == len(c.corpus) and s["rounds"] == 10
+    assert s["cycles_done"] == int(c.picks.min())
