@@ -181,6 +181,7 @@ class Campaign:
                  hang_rounds=np.array([h["round"] for h in self.hangs], dtype=np.int64),
                  state=np.array([self.rng.state, self.mutator.rng.state, self.rounds,
                                  self.executed, self.batch, self.n_hangs], dtype=np.uint64),
+                 seconds=np.array([self.seconds], dtype=np.float64),
                  n_bufs=np.array(self.n_bufs, dtype=np.int64))
 
     @classmethod
@@ -194,6 +195,7 @@ class Campaign:
         c.picks = z["picks"].astype(np.int64)
         c.rng.state, c.mutator.rng.state = state[0], state[1]
         c.rounds, c.executed, c.n_hangs = state[2], state[3], state[5]
+        c.seconds = float(z["seconds"][0])
         c.hangs = [{"input": inp.copy(), "round": rnd}
                    for inp, rnd in zip(z["hang_inputs"], z["hang_rounds"].tolist())]
         for k, inp, hits, rnd in zip(z["bucket_keys"].tolist(), z["bucket_inputs"],

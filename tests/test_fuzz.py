@@ -114,7 +114,7 @@ def test_checkpoint_resume_continues_exactly(tmp_path):
     assert np.array_equal(a.corpus, b.corpus) and a.rounds == b.rounds == 9
     assert [(h["round"], h["input"].tobytes()) for h in a.hangs] == \
         [(h["round"], h["input"].tobytes()) for h in b.hangs]
-    assert a.n_hangs == b.n_hangs
+    assert a.n_hangs == b.n_hangs and b.seconds >= sum(r.seconds for r in after_b)
     assert {k: v["hits"] for k, v in a.buckets.items()} == {k: v["hits"] for k, v in b.buckets.items()}
 
 
