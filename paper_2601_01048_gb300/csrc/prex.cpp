@@ -248,28 +248,53 @@ struct PrexRun {
 // at a few *cuts* of that dimension's axes: a cut at v separates v - 1 from
 // v.  The cuts of all guards split the launch box into cells (boxes) in
 // which every guard, and so every branch condition and loop trip, is
-// constant; in a cell each access index is affine (or constant), and an
-// affine function is out of bounds somewhere in a box iff it is at one of
-// the box's corners.  So the threads whose every axis coordinate is an axis
-// end or next to a cut (v - 1 or v) decide the verdict: the plan.  Both
-// sides of a guard are executed; values computed from guards and
-// thread-invariant values only (a guard, a combination of guards, a value
-// loaded at such an index, a register the two sides leave different) are
-// constant in each cell.  A guard on a combination of two dimensions
-// (x + y < n) is refused, as is any value that could wrap int32, a loop
-// trip that varies between threads, and a path that reaches the iteration
-// budget.
+// constant.  In a cell each access index is one affine function of the
+// coordinates (or a constant), and an affine function is out of bounds
+// somewhere in a box iff it is at one of the box's corners.  So the threads
+// whose every axis coordinate is an axis end or next to a cut (v - 1 or v)
+// decide the verdict: the plan.
+//
+// Values are tracked per cell.  A value built from guards and
+// thread-invariant values only (a guard, a combination of guards, a load at
+// such an index) is constant in each cell.  A value that is one of a few
+// affine functions in each cell, the same one throughout the cell, is
+// piecewise affine: min and max of affine values (their comparison is a
+// guard), a register that the two sides of a guard leave different, a
+// selection by a guard.  Both sides of a guard are executed.  A guard on a
+// combination of two dimensions (x + y < n) is refused, as is any affine
+// piece that could wrap int32, a loop trip that varies between threads, and
+// a path that reaches the iteration budget.
 
-struct GVal {
-  uint8_t k = 0;  // 0 uniform, 1 affine, 2 constant in each cell, 3 other
-  int32_t u = 0;
-  int64_t ct[3] = {0, 0, 0}, cb[3] = {0, 0, 0}, b = 0;  // affine: sum ct*t + cb*b_ + b
-  bool operator==(const GVal& o) const {
-    if (k != o.k || u != o.u || b != o.b) return false;
+struct Aff {
+  int64_t ct[3] = {0, 0, 0}, cb[3] = {0, 0, 0}, b = 0;  // sum ct * t_d + cb * b_d + b
+  bool constant() const {
     for (int d = 0; d < 3; d++)
-      if (ct[d] != o.ct[d] || cb[d] != o.cb[d]) return false;
+      if (ct[d] || cb[d]) return false;
     return true;
   }
+  bool operator==(const Aff& o) const {
+    for (int d = 0; d < 3; d++)
+      if (ct[d] != o.ct[d] || cb[d] != o.cb[d]) return false;
+    return b == o.b;
+  }
+  bool operator<(const Aff& o) const {
+    for (int d = 0; d < 3; d++) {
+      if (ct[d] != o.ct[d]) return ct[d] < o.ct[d];
+      if (cb[d] != o.cb[d]) return cb[d] < o.cb[d];
+    }
+    return b < o.b;
+  }
+};
+
+constexpr size_t kMaxForms = 8;  // pieces of a piecewise-affine value
+
+struct GVal {
+  // 0 uniform, 1 affine, 2 constant in each cell, 3 other, 4 piecewise
+  // affine (one of the forms f in each cell)
+  uint8_t k = 0;
+  int32_t u = 0;
+  std::vector<Aff> f;  // k == 1: one form; k == 4: two or more, sorted
+  bool operator==(const GVal& o) const { return k == o.k && u == o.u && f == o.f; }
 };
 
 struct PrexGrid {
@@ -291,6 +316,13 @@ struct PrexGrid {
     v.k = k;
     return v;
   }
+  static bool affine_kind(const GVal& v) { return v.k == 0 || v.k == 1 || v.k == 4; }
+  static std::vector<Aff> forms(const GVal& v) {
+    if (v.k != 0) return v.f;
+    Aff a;
+    a.b = v.u;
+    return {a};
+  }
   static int64_t floor_div(int64_t p, int64_t q) {
     int64_t f = p / q;
     if ((p % q != 0) && ((p < 0) != (q < 0))) f--;
@@ -298,50 +330,73 @@ struct PrexGrid {
   }
   static int64_t ceil_div(int64_t p, int64_t q) { return -floor_div(-p, q); }
 
-  // Drops coefficients of coordinates fixed at 0, checks the int32 range over
-  // the launch box; affine values constant over it become uniform.
-  bool norm(GVal& v) const {
-    if (v.k != 1) return true;
-    int64_t lo = v.b, hi = v.b;
+  // Drops coefficients of coordinates fixed at 0 and checks the int32 range
+  // of the form over the launch box.
+  bool norm_form(Aff& a) const {
+    int64_t lo = a.b, hi = a.b;
     for (int d = 0; d < 3; d++) {
-      if (n[d] == 1) v.ct[d] = 0;
-      if (g[d] == 1) v.cb[d] = 0;
-      for (int64_t c : {v.ct[d], v.cb[d]})
+      if (n[d] == 1) a.ct[d] = 0;
+      if (g[d] == 1) a.cb[d] = 0;
+      for (int64_t c : {a.ct[d], a.cb[d]})
         if (c > kAffMax || c < -kAffMax) return false;
-      const int64_t t1 = v.ct[d] * (n[d] - 1), t2 = v.cb[d] * (g[d] - 1);
+      const int64_t t1 = a.ct[d] * (n[d] - 1), t2 = a.cb[d] * (g[d] - 1);
       (t1 > 0 ? hi : lo) += t1;
       (t2 > 0 ? hi : lo) += t2;
     }
-    if (v.b > kAffMax || v.b < -kAffMax || lo < INT32_MIN || hi > INT32_MAX) return false;
-    if (lo == hi) v = uni((int32_t)lo);
+    return a.b <= kAffMax && a.b >= -kAffMax && lo >= INT32_MIN && hi <= INT32_MAX;
+  }
+  // A value from its possible forms: uniform, affine, piecewise affine, or
+  // (all forms constant, several of them) constant in each cell.  False if a
+  // form could wrap int32; too many forms make it "other".
+  bool from_forms(std::vector<Aff> fs, GVal* out) const {
+    for (Aff& a : fs)
+      if (!norm_form(a)) return false;
+    std::sort(fs.begin(), fs.end());
+    fs.erase(std::unique(fs.begin(), fs.end()), fs.end());
+    if (fs.empty() || fs.size() > kMaxForms) {
+      *out = kind(3);
+      return true;
+    }
+    bool all_const = true;
+    for (const Aff& a : fs) all_const = all_const && a.constant();
+    if (fs.size() == 1 && all_const) {
+      *out = uni((int32_t)fs[0].b);
+    } else if (all_const) {
+      *out = kind(2);
+    } else {
+      out->k = fs.size() == 1 ? 1 : 4;
+      out->u = 0;
+      out->f = std::move(fs);
+    }
     return true;
   }
-  // Whether v depends on dimension d's coordinates only through G_d (and
-  // then its coefficient of G_d).
-  bool global_form(const GVal& v, int d, int64_t* c) const {
+  bool norm(GVal& v) const { return (v.k != 1 && v.k != 4) || from_forms(v.f, &v); }
+  // Whether form a depends on dimension d's coordinates only through G_d
+  // (and then its coefficient of G_d).
+  bool global_form(const Aff& a, int d, int64_t* c) const {
     if (g[d] == 1) {
-      *c = v.ct[d];
+      *c = a.ct[d];
       return true;
     }
     if (n[d] == 1) {
-      *c = v.cb[d];
+      *c = a.cb[d];
       return true;
     }
-    *c = v.ct[d];
-    return v.cb[d] == v.ct[d] * n[d];
+    *c = a.ct[d];
+    return a.cb[d] == a.ct[d] * n[d];
   }
   // An access index in a merged dimension must be in global form; otherwise
   // the dimension is split and the analysis runs again.
   bool merge_ok(const GVal& v) {
-    if (v.k != 1) return true;
     bool ok = true;
-    for (int d = 0; d < 3; d++) {
-      int64_t c = 0;
-      if (merged[d] && !global_form(v, d, &c)) {
-        need_split[d] = true;
-        ok = false;
+    for (const Aff& a : v.f)
+      for (int d = 0; d < 3; d++) {
+        int64_t c = 0;
+        if (merged[d] && !global_form(a, d, &c)) {
+          need_split[d] = true;
+          ok = false;
+        }
       }
-    }
     return ok;
   }
   // Cuts where "c * x + b op 0" changes along x in [0, m) (c != 0).
@@ -360,40 +415,40 @@ struct PrexGrid {
         break;
     }
   }
-  // The guard "v op 0" for v affine: records its cuts; false when its truth
-  // does not follow the axes (two dimensions, or one split dimension
-  // through both coordinates other than as G_d).
-  bool guard(const GVal& v, int op) {
+  // The guard "a op 0": records its cuts; false when its truth does not
+  // follow the axes (two dimensions, or one split dimension through both
+  // coordinates other than as G_d).  A constant a needs no cut.
+  bool guard(const Aff& a, int op) {
     int dim = -1;
     for (int d = 0; d < 3; d++)
-      if (v.ct[d] || v.cb[d]) {
+      if (a.ct[d] || a.cb[d]) {
         if (dim >= 0) return false;
         dim = d;
       }
-    if (dim < 0) return true;  // constant (norm makes this uniform first)
+    if (dim < 0) return true;
     const int d = dim;
     int64_t c = 0;
     if (merged[d]) {
-      if (!global_form(v, d, &c)) {
+      if (!global_form(a, d, &c)) {
         need_split[d] = true;
         return false;
       }
-      add_cuts(cut_g[d], n[d] * g[d], op, c, v.b);
+      add_cuts(cut_g[d], n[d] * g[d], op, c, a.b);
       return true;
     }
-    if (!v.cb[d]) {
-      add_cuts(cut_t[d], n[d], op, v.ct[d], v.b);
+    if (!a.cb[d]) {
+      add_cuts(cut_t[d], n[d], op, a.ct[d], a.b);
       return true;
     }
-    if (!v.ct[d]) {
-      add_cuts(cut_b[d], g[d], op, v.cb[d], v.b);
+    if (!a.ct[d]) {
+      add_cuts(cut_b[d], g[d], op, a.cb[d], a.b);
       return true;
     }
-    if (!global_form(v, d, &c)) return false;
+    if (!global_form(a, d, &c)) return false;
     // a staircase in (t_d, b_d): a cut at G = q * n + r splits block q
     // between threads r - 1 and r, and blocks q - 1 | q | q + 1 apart
     std::vector<int64_t> gc;
-    add_cuts(gc, n[d] * g[d], op, c, v.b);
+    add_cuts(gc, n[d] * g[d], op, c, a.b);
     for (int64_t x : gc) {
       const int64_t q = x / n[d], r = x % n[d];
       if (q >= 1) cut_b[d].push_back(q);
@@ -404,78 +459,126 @@ struct PrexGrid {
     }
     return true;
   }
-  GVal as_affine(const GVal& x) const {
-    if (x.k == 1) return x;
-    GVal v;
-    v.k = 1;
-    v.b = x.u;
-    return v;
+  // The difference x - y of two forms with the coefficients of fixed
+  // coordinates dropped.
+  Aff diff(const Aff& x, const Aff& y) const {
+    Aff a;
+    for (int d = 0; d < 3; d++) {
+      a.ct[d] = n[d] == 1 ? 0 : x.ct[d] - y.ct[d];
+      a.cb[d] = g[d] == 1 ? 0 : x.cb[d] - y.cb[d];
+    }
+    a.b = x.b - y.b;
+    return a;
   }
-  static bool scale(GVal& v, int64_t s) {
-    for (int64_t* c : {&v.ct[0], &v.ct[1], &v.ct[2], &v.cb[0], &v.cb[1], &v.cb[2], &v.b}) {
+  // Guards "p op q" for every pair of forms; false if one is not a guard.
+  bool guard_pairs(const std::vector<Aff>& xs, const std::vector<Aff>& ys, int op) {
+    for (const Aff& p : xs)
+      for (const Aff& q : ys)
+        if (!guard(diff(p, q), op)) return false;
+    return true;
+  }
+  static bool scale(Aff& a, int64_t s) {
+    for (int64_t* c : {&a.ct[0], &a.ct[1], &a.ct[2], &a.cb[0], &a.cb[1], &a.cb[2], &a.b}) {
       const __int128 p = (__int128)*c * s;
       if (p > kAffMax || p < -kAffMax) return false;
       *c = (int64_t)p;
     }
     return true;
   }
+  // The value that is x in some cells and y in the others (a join after a
+  // guard, a selection by a guard).
+  GVal combine(const GVal& x, const GVal& y) const {
+    if (x == y) return x;
+    if ((x.k == 0 || x.k == 2) && (y.k == 0 || y.k == 2)) return kind(2);
+    if (!affine_kind(x) || !affine_kind(y)) return kind(3);
+    std::vector<Aff> fs = forms(x), fy = forms(y);
+    fs.insert(fs.end(), fy.begin(), fy.end());
+    GVal v;
+    return from_forms(fs, &v) ? v : kind(3);
+  }
+  // Makes a truth value per cell of v (tested against zero); false if that
+  // needs a guard that is not one.
+  bool truth(GVal& v) {
+    if (v.k == 1 || v.k == 4) {
+      for (const Aff& a : v.f)
+        if (!guard(a, 14)) return false;
+      v = kind(2);
+    }
+    return true;
+  }
   GVal alu(int op, const GVal& x, const GVal& y) {
     if (x.k == 0 && y.k == 0) return uni(uniform_alu(op, x.u, y.u));
     if (x.k == 3 || y.k == 3) return kind(3);
-    if (x.k != 1 && y.k != 1) return kind(2);  // cell constants and uniforms
+    if ((x.k == 0 || x.k == 2) && (y.k == 0 || y.k == 2)) return kind(2);  // cell constants
     if (x.k == 2 || y.k == 2) return kind(3);  // affine with a cell constant
+    const std::vector<Aff> fx = forms(x), fy = forms(y);
+    std::vector<Aff> out;
     switch (op) {
       case 0:
-      case 1: {
-        const GVal a = as_affine(x), c = as_affine(y);
-        GVal v = a;
-        const int64_t s = op == 0 ? 1 : -1;
-        for (int d = 0; d < 3; d++) {
-          v.ct[d] += s * c.ct[d];
-          v.cb[d] += s * c.cb[d];
-        }
-        v.b += s * c.b;
-        return v;
-      }
-      case 2: {
-        if (x.k == 1 && y.k == 1) return kind(3);
-        GVal v = x.k == 1 ? x : y;
-        return scale(v, x.k == 1 ? y.u : x.u) ? v : kind(3);
-      }
+      case 1:
+        for (const Aff& p : fx)
+          for (const Aff& q : fy) {
+            Aff a = p;
+            const int64_t s = op == 0 ? 1 : -1;
+            for (int d = 0; d < 3; d++) {
+              a.ct[d] += s * q.ct[d];
+              a.cb[d] += s * q.cb[d];
+            }
+            a.b += s * q.b;
+            out.push_back(a);
+          }
+        break;
+      case 2:
       case 3: {
-        if (y.k != 0) return kind(3);
-        GVal v = x;
-        return scale(v, (int64_t)1 << ((uint32_t)y.u & 31u)) ? v : kind(3);
+        if (y.k != 0 && (op == 3 || x.k != 0)) return kind(3);
+        const bool x_scaled = y.k == 0;
+        const int64_t s = op == 3 ? (int64_t)1 << ((uint32_t)y.u & 31u) : x_scaled ? y.u : x.u;
+        for (Aff a : x_scaled ? fx : fy) {
+          if (!scale(a, s)) return kind(3);
+          out.push_back(a);
+        }
+        break;
       }
+      case 9:
+      case 10:  // min / max: x where x < y holds (a guard per pair), else y
+        if (!guard_pairs(fx, fy, 11)) return kind(3);
+        out = fx;
+        out.insert(out.end(), fy.begin(), fy.end());
+        break;
       case 11:
       case 12:
       case 13:
-      case 14: {  // a signed comparison of affine values: a guard
-        GVal dv = alu(1, as_affine(x), as_affine(y));
-        if (!norm(dv)) return kind(3);
-        if (dv.k == 0)
-          return uni(op == 11 ? dv.u < 0 : op == 12 ? dv.u <= 0 : op == 13 ? dv.u == 0 : dv.u != 0);
-        return guard(dv, op) ? kind(2) : kind(3);
+      case 14: {  // a signed comparison of affine values: a guard per pair
+        if (fx.size() == 1 && fy.size() == 1) {
+          const Aff dv = diff(fx[0], fy[0]);
+          if (dv.constant())
+            return uni(op == 11 ? dv.b < 0 : op == 12 ? dv.b <= 0 : op == 13 ? dv.b == 0 : dv.b != 0);
+        }
+        return guard_pairs(fx, fy, op) ? kind(2) : kind(3);
       }
       default:
         return kind(3);
     }
+    GVal v;
+    return from_forms(out, &v) ? v : kind(3);
   }
   GVal sreg(int id) const {
     GVal v;
+    Aff a;
     if (id <= 2) {
-      v.k = 1;
-      v.ct[id] = 1;
-      return v;
+      a.ct[id] = 1;
+    } else if (id >= 6 && id <= 8) {
+      a.cb[id - 6] = 1;
+    } else if (id <= 5) {
+      return uni((int32_t)in.block[id - 3]);
+    } else if (id <= 11) {
+      return uni((int32_t)in.grid[id - 9]);
+    } else {
+      return uni(in.args[id - 12]);
     }
-    if (id <= 5) return uni((int32_t)in.block[id - 3]);
-    if (id <= 8) {
-      v.k = 1;
-      v.cb[id - 6] = 1;
-      return v;
-    }
-    if (id <= 11) return uni((int32_t)in.grid[id - 9]);
-    return uni(in.args[id - 12]);
+    v.k = 1;
+    v.f = {a};
+    return v;
   }
   GVal load(const IrOp& o, int32_t idx) const {
     const int64_t w = o.width, off = (int64_t)idx * w;
@@ -513,12 +616,16 @@ struct PrexGrid {
         case B_IMM: st.r[o.dst] = uni(o.imm); pc++; break;
         case B_MOV: st.r[o.dst] = st.r[o.a]; pc++; break;
         case B_SEL: {
-          const GVal& c = st.r[o.a];
+          GVal c = st.r[o.a];
           const GVal &x = st.r[o.b], &y = st.r[o.c];
-          if (c.k == 0) st.r[o.dst] = c.u ? x : y;
-          else if (x == y) st.r[o.dst] = x;
-          else if (c.k == 2 && x.k != 1 && x.k != 3 && y.k != 1 && y.k != 3) st.r[o.dst] = kind(2);
-          else st.r[o.dst] = kind(3);
+          if (c.k == 0) {
+            st.r[o.dst] = c.u ? x : y;
+          } else if (x == y) {
+            st.r[o.dst] = x;
+          } else {
+            if (!truth(c)) return false;
+            st.r[o.dst] = c.k == 2 ? combine(x, y) : kind(3);
+          }
           pc++;
           break;
         }
@@ -532,10 +639,7 @@ struct PrexGrid {
         }
         case B_IF: {
           GVal c = st.r[o.a];
-          if (c.k == 1) {  // "value != 0" with value affine: a guard
-            if (!guard(c, 14)) return false;
-            c = kind(2);
-          }
+          if (!truth(c)) return false;
           const int then_end = o.else_pc >= 0 ? o.else_pc : o.end_pc;
           if (c.k == 0) {
             if (c.u) {
@@ -547,10 +651,7 @@ struct PrexGrid {
             State a = st, e = st;
             if (!exec(pc + 1, then_end, a)) return false;
             if (o.else_pc >= 0 && !exec(o.else_pc + 1, o.end_pc, e)) return false;
-            for (size_t k = 0; k < st.r.size(); k++) {
-              const GVal &x = a.r[k], &y = e.r[k];
-              st.r[k] = x == y ? x : (x.k == 1 || x.k == 3 || y.k == 1 || y.k == 3) ? kind(3) : kind(2);
-            }
+            for (size_t k = 0; k < st.r.size(); k++) st.r[k] = combine(a.r[k], e.r[k]);
             st.back = std::max(a.back, e.back);
           } else {
             return false;

@@ -264,13 +264,16 @@ def test_plan_is_the_corners_when_the_check_holds():
         assert B.cufz_prex_plan(prog, inp).tolist() == want
 
 
-def guarded_nd_program(rng, dims):
+def guarded_nd_program(rng, dims, piecewise=False):
     """Guards on one dimension's coordinate each (global G = ctaid * ntid +
     tid, tid alone or ctaid alone, scaled), compared with arguments by <,
     <=, ==, != or tested against zero, combined by AND / OR or nested, with
     else arms; accesses at indices affine in all coordinates, at guard
     values, and at selections between uniform values by a guard; a guard on
-    a value loaded at such an index; a guard inside a uniform loop."""
+    a value loaded at such an index; a guard inside a uniform loop.  With
+    `piecewise`, also indices that are affine only per cell: a clamped
+    coordinate plus an affine term, a register the arms of a guard set to
+    different affine values, a selection between affine values by a guard."""
     A = Asm(n_bufs=3, seed=rng.next32())
     t = [A.sreg(bc.TID_X + d) for d in range(dims)]
     b = [A.sreg(bc.CTAID_X + d) for d in range(dims)]
@@ -314,7 +317,7 @@ def guarded_nd_program(rng, dims):
 
     def body(depth):
         for _ in range(rng.randint(1, 3)):
-            r = rng.below(7)
+            r = rng.below(10 if piecewise else 7)
             if r <= 1 or depth >= 2:
                 A.ld(rng.below(3), aff(), rng.choice(bc.WIDTHS))
             elif r == 2:
@@ -334,6 +337,21 @@ def guarded_nd_program(rng, dims):
                 A.endif()
             elif r == 5:
                 A.ld(rng.below(3), guard(False), 8)
+            elif r == 7:
+                x = A.alu(bc.ADD, coord(), Imm(rng.randint(-3, 3)))
+                cl = A.alu(bc.MAX, A.alu(bc.MIN, x, a1), a0)
+                A.ld(rng.below(3), A.alu(bc.ADD, cl, aff()), rng.choice(bc.WIDTHS))
+            elif r == 8:
+                v = A.alu(bc.ADD, a0, Imm(0))
+                A.if_(cond())
+                A.mov(aff(), dst=v)
+                if rng.below(2):
+                    A.else_()
+                    A.mov(aff(), dst=v)
+                A.endif()
+                A.ld(rng.below(3), v, 4)
+            elif r == 9:
+                A.ld(rng.below(3), A.sel(guard(False), aff(), aff()), 4)
             else:
                 k = A.loop(A.sreg(bc.ARG3), 3)
                 A.if_(A.alu(bc.SETLT, A.alu(bc.ADD, coord(), k), a1))
@@ -415,7 +433,16 @@ def test_plan_accepts_and_refuses(orc):
 
     one_d = mk((4, 1, 1), (32, 1, 1), (50, 100), (400, 400))
     two_d = mk((4, 1, 1), (8, 4, 1), (5, 100), (400, 400))
+    clamp = lambda A, x: A.alu(bc.MAX, A.alu(bc.MIN, x, A.alu(bc.SUB, A.sreg(bc.ARG1), Imm(1))),
+                               Imm(0))
     accepted = {
+        "arms leaving different indices": (_prog(diverged), one_d),
+        "a clamped index": (_prog(lambda A: A.ld(0, clamp(A, A.alu(bc.SUB, lin(A), Imm(2))), 4)),
+                            mk((4, 1, 1), (32, 1, 1), (50, 90), (400, 400))),
+        "a selection between indices by a guard":
+            (_prog(lambda A: A.ld(0, A.sel(lt(A, tx(A), A.sreg(bc.ARG0)), lin(A),
+                                           A.alu(bc.MUL, lin(A), Imm(2))), 4)),
+             mk((4, 1, 1), (32, 1, 1), (7, 0), (400, 400))),
         "guard on the global index": (guarded_by(lambda A: lt(A, lin(A), A.sreg(bc.ARG0))), one_d),
         "guard on tid.x over four blocks": (guarded_by(lambda A: lt(A, tx(A), A.sreg(bc.ARG0))), one_d),
         "guard in a 2D block": (guarded_by(lambda A: lt(A, ty(A), Imm(2))), two_d),
@@ -429,6 +456,9 @@ def test_plan_accepts_and_refuses(orc):
     refused = {
         "a guard across two dimensions": (guarded_by(lambda A: lt(A, A.alu(bc.ADD, tx(A), ty(A)),
                                                                   Imm(5))), two_d),
+        "a clamp across two dimensions": (_prog(lambda A: A.ld(0, A.alu(bc.MIN, tx(A), ty(A)), 4)),
+                                          two_d),
+        "a masked index": (_prog(lambda A: A.ld(0, A.alu(bc.AND, lin(A), Imm(7)), 4)), one_d),
         "tid.x and ctaid.x in another mix than the global index":
             (guarded_by(lambda A: lt(A, A.alu(bc.ADD, A.alu(bc.SHL, tx(A), Imm(1)),
                                               A.sreg(bc.CTAID_X)), A.sreg(bc.ARG0))), one_d),
@@ -440,7 +470,6 @@ def test_plan_accepts_and_refuses(orc):
         "an index plus a guard": (_prog(lambda A: A.ld(0, A.alu(bc.ADD, lin(A),
                                                                 lt(A, lin(A), A.sreg(bc.ARG0))),
                                                       4)), one_d),
-        "arms leaving different indices": (_prog(diverged), one_d),
         "a thread-dependent trip": (_prog(lambda A: (A.loop(tx(A), 8), A.ld(0, A.imm(0), 4),
                                                      A.endloop())), one_d),
     }
@@ -477,3 +506,28 @@ def test_plan_decides_guard2d_workload(orc):
         assert ok
         violating += full
     assert 0 < violating < len(ins)
+
+
+def test_plan_decides_random_piecewise_indices(orc):
+    """Indices that are affine only per cell (clamps, diverging arms,
+    selections by guards) within the random guarded programs."""
+    rng = gen.SplitMix64(0x9A7C)
+    planned = violating = 0
+    for trial in range(72):
+        dims = 1 + trial % 3
+        prog = guarded_nd_program(rng, dims, piecewise=True)
+        for _ in range(3):
+            block = [rng.randint(1, 8) for _ in range(dims)] + [1] * (3 - dims)
+            grid = [rng.randint(1, 4) for _ in range(dims)] + [1] * (3 - dims)
+            span = max(n * g for n, g in zip(block, grid))
+            args = (rng.randint(-4, 4), rng.randint(-3, span + 3), rng.randint(-2, span + 2),
+                    rng.randint(0, 3))
+            inp = mk(grid, block, args, [rng.randint(0, 4 * (12 * span + 16)) for _ in range(3)])
+            plan = B.cufz_prex_plan(prog, inp)
+            if plan is None:
+                continue
+            ok, full = plan_decides_every_site(orc, prog, inp, plan)
+            assert ok, (trial, args)
+            planned += 1
+            violating += full
+    assert planned > 150 and 30 < violating < planned
