@@ -34,6 +34,7 @@ buckets), unique hangs, queue cycles and the corpus size.
 """
 from __future__ import annotations
 
+import contextlib
 import dataclasses
 import time
 
@@ -202,3 +203,57 @@ class Campaign:
                                      z["bucket_hits"].tolist(), z["bucket_rounds"].tolist()):
             c.buckets[tuple(k)] = {"input": inp.copy(), "hits": hits, "round": rnd}
         return c
+
+
+# ------------------------------------------------------------ command line
+@contextlib.contextmanager
+def _engine_executor(programs: list[bytes], batch: int):
+    """An engine context holding `programs`, for a campaign of `batch`
+    inputs per round (compiled path; per-input bitmaps are not kept, the
+    device union is)."""
+    with B.Engine(max_slots=batch, record_cap=64, flags=B.CF_JIT) as engine:
+        for p in programs:
+            engine.load(p)
+        yield EngineExecutor(engine)
+
+
+def main(argv=None, executor_factory=None) -> int:
+    """python -m paper_2601_01048_gb300.fuzz: a campaign over program files
+    (--program, repeatable; default the serving workload's 64 programs) from
+    a seed corpus of their shapes, printing stats() as one JSON line every
+    --report rounds and writing --checkpoint then; --resume continues a
+    saved campaign."""
+    import argparse
+    import json
+
+    from . import bytecode as bc
+    from .gen import c5_corpus, c5_programs
+
+    ap = argparse.ArgumentParser(prog="python -m paper_2601_01048_gb300.fuzz")
+    ap.add_argument("--program", action="append", default=[], help="program file (repeatable)")
+    ap.add_argument("--rounds", type=int, default=100)
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--seed", type=lambda s: int(s, 0), default=0xF022)
+    ap.add_argument("--report", type=int, default=10, help="rounds between stats lines")
+    ap.add_argument("--checkpoint", default=None)
+    ap.add_argument("--resume", default=None)
+    args = ap.parse_args(argv)
+    progs = [open(p, "rb").read() for p in args.program] or c5_programs()
+    make = executor_factory or _engine_executor
+    with make(progs, args.batch) as ex:
+        if args.resume:
+            c = Campaign.resume(args.resume, ex)
+        else:
+            c = Campaign(ex, [bc.decode_header(p)["n_bufs"] for p in progs], c5_corpus(progs),
+                         seed=args.seed, batch=args.batch)
+        for r in range(args.rounds):
+            c.run_round()
+            if (r + 1) % max(args.report, 1) == 0 or r + 1 == args.rounds:
+                print(json.dumps(c.stats()), flush=True)
+                if args.checkpoint:
+                    c.checkpoint(args.checkpoint)
+    return 0
+
+
+if __name__ == "__main__":
+    raise SystemExit(main())

@@ -166,3 +166,25 @@ def test_hangs_and_campaign_stats():
     assert s["unique_crashes"] == len(c.buckets) and s["unique_hangs"] == len(c.hangs)
     assert s["corpus_count"] == len(c.corpus) and s["rounds"] == 10
     assert s["cycles_done"] == int(c.picks.min())
+
+
+def test_command_line_reports_checkpoints_and_resumes(tmp_path, capsys):
+    import contextlib
+    import json
+
+    from paper_2601_01048_gb300 import fuzz
+
+    @contextlib.contextmanager
+    def fake(programs, batch):
+        assert len(programs) == 64 and batch == 32
+        yield FakeExecutor()
+
+    path = str(tmp_path / "campaign")
+    fuzz.main(["--rounds", "4", "--batch", "32", "--report", "2", "--checkpoint", path],
+              executor_factory=fake)
+    lines = [json.loads(x) for x in capsys.readouterr().out.splitlines()]
+    assert [x["rounds"] for x in lines] == [2, 4] and lines[-1]["execs_done"] == 128
+    fuzz.main(["--resume", path + ".npz", "--rounds", "3", "--batch", "32", "--report", "5"],
+              executor_factory=fake)
+    last = json.loads(capsys.readouterr().out.splitlines()[-1])
+    assert last["rounds"] == 7 and last["execs_done"] == 224
