@@ -531,3 +531,24 @@ def test_plan_decides_random_piecewise_indices(orc):
             planned += 1
             violating += full
     assert planned > 150 and 30 < violating < planned
+
+
+def test_head_tail_heuristic_misses_what_the_plan_finds(orc):
+    """Why the plan replaces the paper's Alg. 1.  j = (a0 <= i < a1) ? i +
+    4096 : i; load A[j].  The load runs in every thread, so the first and
+    last blocks cover every access instruction, and neither violates: Alg. 1
+    stops there and reports no bug.  The middle threads read past A.  The
+    plan cuts the launch at a0 and a1 and finds them."""
+    A = Asm(n_bufs=1)
+    i = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    mid = A.alu(bc.AND, A.alu(bc.SETLE, A.sreg(bc.ARG0), i), A.alu(bc.SETLT, i, A.sreg(bc.ARG1)))
+    A.ld(0, A.sel(mid, A.alu(bc.ADD, i, Imm(4096)), i), 4)
+    prog = A.build()
+    inp = mk((16, 1, 1), (64, 1, 1), (300, 700), (4 * 1024,))
+    res, recs, _ = orc.run(orc.Program(prog), inp, rec_cap=1 << 12, bitmap=False)
+    blocks = set(recs["block_lin"].tolist())
+    assert int(res["n_violations"]) == 400 and 0 not in blocks and 15 not in blocks
+    plan = B.cufz_prex_plan(prog, inp)
+    assert plan is not None and len(plan) <= 8
+    ok, full = plan_decides_every_site(orc, prog, inp, plan)
+    assert ok and full
