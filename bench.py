@@ -112,7 +112,7 @@ def parse_args():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2", choices=["c1", "c2", "c3", "c4", "c5", "affine", "guard2d"])
     ap.add_argument("--prex", action="store_true",
-                    help="partial representative execution: qualifying inputs run their corner threads")
+                    help="partial representative execution: inputs with a PREX plan run only its threads")
     ap.add_argument("--rate", type=float, default=50000.0, help="c5: offered inputs/s")
     ap.add_argument("--duration", type=float, default=2.0, help="c5: seconds of arrivals")
     ap.add_argument("--inputs-per-step", type=int, default=0, help="0: the whole workload")
