@@ -149,11 +149,26 @@ def test_generated_code_matches_oracle(tmp_path, host_objs, orc, flags):
     assert 0 < n_viol < len(ins)
 
 
-def test_budget_stop_matches_oracle(tmp_path, host_objs, orc):
-    """A back-edge budget small enough to stop threads inside loops."""
+def test_budget_stop_and_3d_shapes_match_oracle(tmp_path, host_objs, orc):
+    """A back-edge budget small enough to stop threads inside loops, and
+    random 3D launch shapes (every coordinate decomposition of the emitted
+    code)."""
     progs = gen.c2_programs()[:6]
     ins = gen.c2_inputs(progs, per_program=2, seed=306, max_grid=2)
     exe = build(tmp_path, host_objs, progs)
+    rng = gen.SplitMix64(308)
+    shaped = np.concatenate([ins, ins])
+    for x in shaped:
+        x["grid"] = [rng.randint(1, 3), rng.randint(1, 3), rng.randint(1, 3)]
+        x["block"] = [rng.randint(1, 9), rng.randint(1, 6), rng.randint(1, 4)]
+    got = run(tmp_path, exe, progs, shaped)
+    ores, orecs, obms = orc.run_batch(progs, shaped, rec_cap=1 << 14, bitmaps=True)
+    for k, (res, recs, bm) in enumerate(got):
+        for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                  "n_edges", "n_threads"):
+            assert int(res[f]) == int(ores[k][f]), (k, f)
+        assert record_set(recs) == record_set(orecs[k][: int(ores[k]["n_records"])]), k
+        assert np.array_equal(bm, obms[k]), k
     got = run(tmp_path, exe, progs, ins, budget=3)
     ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=3), rec_cap=1 << 14,
                                       bitmaps=True)
