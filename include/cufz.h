@@ -39,6 +39,9 @@
  * Opcodes: 0x01 SREG dst = special register imm (0-2 tid.xyz, 3-5
  * ntid.xyz, 6-8 ctaid.xyz, 9-11 nctaid.xyz, 12-15 scalar args 0-3); 0x02 IMM
  * dst = imm; 0x03 MOV dst = a; 0x04 SEL dst = a != 0 ? b : register imm;
+ * 0x05 DIV and 0x06 REM dst = a / b and a % b, signed and truncating: a zero
+ * divisor is a fault (a violation of kind 2, result 0), INT_MIN / -1 is
+ * INT_MIN and INT_MIN % -1 is 0;
  * 0x10-0x1F ALU dst = a op b and 0x30-0x3F the same with b = imm, op in
  * order add, sub, mul, shl, shr (arithmetic), shru, and, or, xor, min, max
  * (signed), setlt, setle, seteq, setne (signed, 0 or 1), setltu (unsigned),
@@ -49,7 +52,7 @@
  * clamp(a, 0, imm), 0x54 ENDLOOP.
  * Control flow is structured, at most 16 deep; a loop counter is read-only
  * in its body.  The k-th LD/ST in program order is access site k, the k-th
- * IF/LOOP branch site k.
+ * IF/LOOP branch site k, the k-th DIV/REM division site k.
  *
  * Input, result and violation records are the fixed-layout structs below.
  */
@@ -101,6 +104,7 @@ typedef int32_t cufz_status;
 #define CUFZ_CLS_OVERFLOW_RZ 2  /* access overlaps [len, len + R) */
 #define CUFZ_CLS_OTHER_ALLOC 3  /* lands in another buffer of the same space */
 #define CUFZ_CLS_WILD 4         /* anything else */
+#define CUFZ_CLS_DIV_ZERO 5     /* a division (record kind 2) by zero */
 
 /* configuration flags (cufz_config.flags) */
 #define CUFZ_CF_KEEP_BITMAPS 1 /* keep each input's 64 KiB bitmap until released */
@@ -182,16 +186,17 @@ typedef struct {
 typedef struct {
   uint32_t block_lin;
   uint32_t thread_lin;
-  uint32_t ordinal; /* accesses this thread executed before this one */
-  uint16_t site;    /* access site: index of the LD/ST among the program's LD/STs */
-  uint8_t buf;
-  uint8_t kind;     /* 0 load, 1 store */
-  uint8_t width;    /* bytes */
-  uint8_t space;    /* 0 global, 1 shared */
+  uint32_t ordinal; /* checked events (accesses, divisions) of this thread before this one */
+  uint16_t site;    /* kind 0/1: index of the LD/ST among the program's LD/STs;
+                       kind 2: index of the DIV/REM among its DIV/REMs */
+  uint8_t buf;      /* kind 2: 0 */
+  uint8_t kind;     /* 0 load, 1 store, 2 division by zero */
+  uint8_t width;    /* bytes (kind 2: 0) */
+  uint8_t space;    /* 0 global, 1 shared (kind 2: 0) */
   uint8_t cls;      /* CUFZ_CLS_* */
   uint8_t pad0;
   uint32_t pad1;
-  int64_t byte_off; /* index * width */
+  int64_t byte_off; /* index * width (kind 2: 0) */
 } cufz_violation;
 
 #if !defined(__CUDACC_RTC__)

@@ -61,7 +61,16 @@
  * K is odd, so each step is a bijection of H: a thread whose access sequence
  * differs in one access (site or index), or has one more or fewer, ends with
  * a different H.
- * ordinal = the number of accesses the thread executed before this one.
+ * ordinal = the number of checked events (accesses and divisions) the
+ * thread executed before this one.
+ *
+ * Division (the division-by-zero fault of the paper's kernel errors,
+ * Sec. 2.3): DIV and REM are signed, truncating toward zero.  A zero divisor
+ * is a fault: the result is 0 and the thread records a violation of kind 2
+ * (division) at the division's site (the k-th DIV/REM in program order),
+ * with class DIV_ZERO, buffer, width, space and byte offset 0.  INT_MIN / -1
+ * is INT_MIN and INT_MIN % -1 is 0, without a fault.  A division is not an
+ * access: it is not counted in n_accesses and does not enter the digest.
  *
  * first_key = min over violations of
  *   block_lin << 32 | thread_lin << 22 | min(ordinal, 2^22 - 1).
@@ -82,12 +91,13 @@
 enum { ORC_ST_OK = 0, ORC_ST_VIOLATION = 1, ORC_ST_INVALID_CONFIG = 2, ORC_ST_LIMIT = 3 };
 enum { ORC_FL_BUDGET = 1, ORC_FL_OVERFLOW = 2, ORC_FL_NEW_COV = 4 };
 enum { ORC_CLS_NONE = 0, ORC_CLS_UNDERFLOW_RZ = 1, ORC_CLS_OVERFLOW_RZ = 2,
-       ORC_CLS_OTHER_ALLOC = 3, ORC_CLS_WILD = 4 };
+       ORC_CLS_OTHER_ALLOC = 3, ORC_CLS_WILD = 4, ORC_CLS_DIV_ZERO = 5 };
 enum { ORC_E_FORMAT = -1, ORC_E_OPERAND = -2, ORC_E_STRUCTURE = -3, ORC_E_LOOPCTR = -4,
        ORC_E_SITES = -5, ORC_E_NOMEM = -6 };
 
 enum {
   OP_NOP = 0x00, OP_SREG = 0x01, OP_IMM = 0x02, OP_MOV = 0x03, OP_SEL = 0x04,
+  OP_DIV = 0x05, OP_REM = 0x06,
   OP_ADD = 0x10, OP_SUB, OP_MUL, OP_SHL, OP_SHR, OP_SHRU, OP_AND, OP_OR, OP_XOR,
   OP_MIN, OP_MAX, OP_SETLT, OP_SETLE, OP_SETEQ, OP_SETNE, OP_SETLTU,
   OP_LD = 0x40, OP_ST = 0x41,
@@ -127,11 +137,12 @@ typedef struct {
   uint8_t opc, dst, a, b;
   int32_t imm;
   int32_t else_pc, end_pc; /* IF: ELSE (or -1) and ENDIF; LOOP: ENDLOOP */
-  int32_t site;            /* branch site (IF/LOOP) or access site (LD/ST) */
+  int32_t site;            /* branch site (IF/LOOP), access site (LD/ST) or
+                              division site (DIV/REM) */
 } orc_op;
 
 typedef struct {
-  int n_ops, n_regs, n_bufs, n_sites, n_access;
+  int n_ops, n_regs, n_bufs, n_sites, n_access, n_div;
   uint32_t shared_mask, seed;
   uint16_t loc[256][2];
   orc_op ops[ORC_MAX_OPS];
@@ -173,7 +184,8 @@ static uint32_t rd32(const uint8_t* p) {
 
 static int writes_reg(const orc_op* o) {
   switch (o->opc) {
-    case OP_SREG: case OP_IMM: case OP_MOV: case OP_SEL: case OP_LD: case OP_LOOP: return 1;
+    case OP_SREG: case OP_IMM: case OP_MOV: case OP_SEL: case OP_LD: case OP_LOOP:
+    case OP_DIV: case OP_REM: return 1;
     default: return (o->opc >= 0x10 && o->opc <= 0x1F) || (o->opc >= 0x30 && o->opc <= 0x3F);
   }
 }
@@ -201,7 +213,7 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
   }
   const uint8_t* q = p + 32 + 4 * P->n_sites;
   int stack[ORC_MAX_DEPTH];
-  int depth = 0, bsite = 0, asite = 0;
+  int depth = 0, bsite = 0, asite = 0, dsite = 0;
   int R = P->n_regs;
   for (int pc = 0; pc < P->n_ops; pc++) {
     orc_op* o = &P->ops[pc];
@@ -226,6 +238,11 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
         case OP_IMM: ok = o->dst < R && !o->a && !o->b; break;
         case OP_MOV: ok = o->dst < R && o->a < R && !o->b && !o->imm; break;
         case OP_SEL: ok = o->dst < R && o->a < R && o->b < R && o->imm >= 0 && o->imm < R; break;
+        case OP_DIV:
+        case OP_REM:
+          ok = o->dst < R && o->a < R && o->b < R && !o->imm;
+          if (ok) o->site = dsite++;
+          break;
         case OP_LD:
         case OP_ST:
           ok = o->dst < R && o->a < R && o->b < P->n_bufs && valid_width(o->imm);
@@ -278,6 +295,7 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
   if (depth != 0) return ORC_E_STRUCTURE;
   if (bsite != P->n_sites) return ORC_E_SITES;
   P->n_access = asite;
+  P->n_div = dsite;
   /* a loop counter is read-only inside its own body */
   for (int pc = 0; pc < P->n_ops; pc++) {
     const orc_op* o = &P->ops[pc];
@@ -346,6 +364,23 @@ static uint8_t classify(const orc_ctx* c, int buf, int64_t off, int w) {
   return ORC_CLS_WILD;
 }
 
+/* A violation of the current thread at its current ordinal: counts it,
+ * lowers the first key, keeps the record while there is room. */
+static void violation(orc_ctx* c, const orc_record* proto) {
+  orc_result* res = c->res;
+  uint64_t ord = c->ordinal < 0x3FFFFFu ? c->ordinal : 0x3FFFFFu;
+  uint64_t key = ((uint64_t)c->block_lin << 32) | ((uint64_t)c->thread_lin << 22) | ord;
+  if (key < res->first_key) res->first_key = key;
+  if (res->n_violations < c->rec_cap) {
+    orc_record* rec = &c->recs[res->n_violations];
+    *rec = *proto;
+    rec->block_lin = c->block_lin;
+    rec->thread_lin = c->thread_lin;
+    rec->ordinal = c->ordinal;
+  }
+  res->n_violations++;
+}
+
 static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
   int32_t idx = c->r[op->a];
   int w = op->imm;
@@ -358,27 +393,40 @@ static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
   c->h = (c->h ^ (uint32_t)idx) * K + 0x9E3779B9u;
   int32_t value = 0;
   if (viol) {
-    uint64_t ord = c->ordinal < 0x3FFFFFu ? c->ordinal : 0x3FFFFFu;
-    uint64_t key = ((uint64_t)c->block_lin << 32) | ((uint64_t)c->thread_lin << 22) | ord;
-    if (key < res->first_key) res->first_key = key;
-    if (res->n_violations < c->rec_cap) {
-      orc_record* rec = &c->recs[res->n_violations];
-      memset(rec, 0, sizeof(*rec));
-      rec->block_lin = c->block_lin;
-      rec->thread_lin = c->thread_lin;
-      rec->ordinal = c->ordinal;
-      rec->site = (uint16_t)op->site;
-      rec->buf = (uint8_t)buf;
-      rec->kind = (uint8_t)is_store;
-      rec->width = (uint8_t)w;
-      rec->space = (uint8_t)((c->P->shared_mask >> buf) & 1u);
-      rec->cls = classify(c, buf, off, w);
-      rec->byte_off = off;
-    }
-    res->n_violations++;
+    orc_record proto;
+    memset(&proto, 0, sizeof(proto));
+    proto.site = (uint16_t)op->site;
+    proto.buf = (uint8_t)buf;
+    proto.kind = (uint8_t)is_store;
+    proto.width = (uint8_t)w;
+    proto.space = (uint8_t)((c->P->shared_mask >> buf) & 1u);
+    proto.cls = classify(c, buf, off, w);
+    proto.byte_off = off;
+    violation(c, &proto);
   } else if (!is_store && !((c->P->shared_mask >> buf) & 1u)) {
     uint32_t word = fmix32(c->P->seed ^ ((uint32_t)buf * 0x9E3779B9u) ^ (uint32_t)(off >> 2));
     value = (w == 1) ? (int32_t)((word >> (8 * (off & 3))) & 0xFFu) : (int32_t)word;
+  }
+  c->ordinal++;
+  return value;
+}
+
+/* DIV / REM: signed, truncating; a zero divisor faults and gives 0. */
+static int32_t do_divide(orc_ctx* c, const orc_op* op) {
+  int32_t x = c->r[op->a], y = c->r[op->b];
+  int32_t value;
+  if (y == 0) {
+    orc_record proto;
+    memset(&proto, 0, sizeof(proto));
+    proto.site = (uint16_t)op->site;
+    proto.kind = 2;
+    proto.cls = ORC_CLS_DIV_ZERO;
+    violation(c, &proto);
+    value = 0;
+  } else if (x == INT32_MIN && y == -1) {
+    value = op->opc == OP_DIV ? INT32_MIN : 0;
+  } else {
+    value = op->opc == OP_DIV ? x / y : x % y;
   }
   c->ordinal++;
   return value;
@@ -435,6 +483,8 @@ static void exec_range(orc_ctx* c, int pc, int end) {
       case OP_MOV: r[o->dst] = r[o->a]; pc++; break;
       case OP_SEL: r[o->dst] = r[o->a] != 0 ? r[o->b] : r[o->imm]; pc++; break;
       case OP_LD: r[o->dst] = do_access(c, o, 0); pc++; break;
+      case OP_DIV:
+      case OP_REM: r[o->dst] = do_divide(c, o); pc++; break;
       case OP_ST: (void)do_access(c, o, 1); pc++; break;
       case OP_IF: {
         int taken = r[o->a] != 0;

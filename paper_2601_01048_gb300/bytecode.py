@@ -39,6 +39,10 @@ Opcodes and the fields they use (unused fields must be 0):
     IMM   dst, imm             dst = imm
     MOV   dst, a               dst = a
     SEL   dst, a, b, imm=y     dst = a != 0 ? b : y   (y is a register, 0..255)
+    DIV   dst, a, b            dst = a / b, signed, truncating (0x05)
+    REM   dst, a, b            dst = a % b, signed, truncating (0x06); for both a
+                               zero divisor is a fault (result 0), and
+                               INT_MIN / -1 = INT_MIN, INT_MIN % -1 = 0
     ALU   dst, a, b            opcode 0x10-0x1F, register b
     ALUI  dst, a, imm          opcode 0x30-0x3F, immediate b
     LD    dst, a=idx, b=buf, imm=width in {1,4,8,16}
@@ -49,7 +53,7 @@ Opcodes and the fields they use (unused fields must be 0):
     ENDLOOP
 
 The k-th LD/ST in program order is access site k; the k-th IF/LOOP is branch
-site k.
+site k; the k-th DIV/REM is division site k.
 """
 from __future__ import annotations
 
@@ -70,6 +74,8 @@ SREG = 0x01
 IMM = 0x02
 MOV = 0x03
 SEL = 0x04
+DIV = 0x05
+REM = 0x06
 ADD, SUB, MUL, SHL, SHR, SHRU, AND, OR, XOR, MIN, MAX, SETLT, SETLE, SETEQ, SETNE, SETLTU = range(0x10, 0x20)
 IMM_FORM = 0x20
 LD = 0x40
@@ -162,6 +168,16 @@ class Asm:
             self.raw(op | IMM_FORM, d, a, 0, b.value)
         else:
             self.raw(op, d, a, b, 0)
+        return d
+
+    def div(self, a: int, b: int, dst: int | None = None) -> int:
+        d = self._dst(dst)
+        self.raw(DIV, d, a, b)
+        return d
+
+    def rem(self, a: int, b: int, dst: int | None = None) -> int:
+        d = self._dst(dst)
+        self.raw(REM, d, a, b)
         return d
 
     def sel(self, c: int, x: int, y: int, dst: int | None = None) -> int:
@@ -282,6 +298,8 @@ def disasm(prog: bytes) -> str:
             lines.append(f"{pc:4d}  r{dst} = r{a}")
         elif opc == SEL:
             lines.append(f"{pc:4d}  r{dst} = r{a} ? r{b} : r{imm}")
+        elif opc in (DIV, REM):
+            lines.append(f"{pc:4d}  r{dst} = {'div' if opc == DIV else 'rem'} r{a}, r{b}")
         elif opc == LD:
             lines.append(f"{pc:4d}  r{dst} = ld.w{imm} buf{b}[r{a}]")
         elif opc == ST:

@@ -6,6 +6,7 @@
 #pragma once
 
 #include "device_common.cuh"
+#include "divide.h"
 
 namespace cufz {
 
@@ -43,6 +44,20 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
   LaneAcc acc;
   acc_init(acc);
   bool full = false;  // warp-uniform: record area known to be full
+  // Reserves record slots for the violating lanes vm of the warp (every
+  // lane calls it): one atomicAdd by the first of them; the group's base,
+  // or ~0 once the record area is known to be full.
+  auto reserve = [&](uint32_t vm) -> uint32_t {
+    const uint32_t k = __popc(vm);
+    const uint32_t leader = __ffs(vm) - 1;
+    uint32_t rbase = 0xFFFFFFFFu;
+    if (!full) {
+      if (lane == leader) rbase = atomicAdd(&S->rec_reserved, k);
+      rbase = __shfl_sync(FULL, rbase, leader);
+      if (rbase + k >= cap) full = true;
+    }
+    return rbase;
+  };
 
   const uint32_t g_end = g0 + count;
   for (uint32_t base = g0 + warp * 32u; base < g_end; base += nwarps * 32u) {
@@ -165,14 +180,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           }
           const uint32_t vm = __ballot_sync(FULL, viol);
           if (vm) {
-            const uint32_t k = __popc(vm);
-            const uint32_t leader = __ffs(vm) - 1;
-            uint32_t rbase = 0xFFFFFFFFu;
-            if (!full) {
-              if (lane == leader) rbase = atomicAdd(&S->rec_reserved, k);
-              rbase = __shfl_sync(FULL, rbase, leader);
-              if (rbase + k >= cap) full = true;
-            }
+            const uint32_t rbase = reserve(vm);
             if (viol) {
               acc.n_viol++;
               if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
@@ -191,6 +199,33 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
               uint32_t word = mix32(seed ^ (buf * 0x9E3779B9u) ^ (uint32_t)(off >> 2));
               v = lw == 0 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word;
             }
+            rf_st(rf, op.d, v);
+          }
+          if (act) ordinal++;
+          pc++;
+          break;
+        }
+        case D_DIVREM: {  // a checked division: a zero divisor is a violation of kind 2
+          const int32_t y = rf_ld(rf, op.b);
+          const bool fault = act && y == 0;
+          if (act) acc.n_ops++;
+          const uint32_t vm = __ballot_sync(FULL, fault);
+          if (vm) {
+            const uint32_t rbase = reserve(vm);
+            if (fault) {
+              acc.n_viol++;
+              if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
+              const uint32_t rank = __popc(vm & lanemask_lt);
+              if (rbase != 0xFFFFFFFFu && rbase + rank < cap)
+                write_record(recs + rbase + rank, bl, tl, ordinal, (uint32_t)op.imm, 0u, 2u, 0u,
+                             0u, CUFZ_CLS_DIV_ZERO, 0);
+            }
+          }
+          if (act && (op.x & 2u)) {
+            const int32_t x = rf_ld(rf, op.a);
+            const int32_t mn = (int32_t)0x80000000u;
+            int32_t v = 0;
+            if (y != 0) v = (x == mn && y == -1) ? ((op.x & 1u) ? 0 : mn) : ((op.x & 1u) ? x % y : x / y);
             rf_st(rf, op.d, v);
           }
           if (act) ordinal++;

@@ -12,7 +12,7 @@
 namespace cufz {
 
 enum : uint8_t {
-  B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04,
+  B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04, B_DIV = 0x05, B_REM = 0x06,
   B_LD = 0x40, B_ST = 0x41, B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53,
   B_ENDLOOP = 0x54
 };
@@ -42,7 +42,7 @@ struct IrOp {
 };
 
 struct Ir {
-  int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0;
+  int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0, n_div = 0;
   uint32_t shared_mask = 0, seed = 0;
   std::vector<uint16_t> loc0, loc1;
   std::vector<IrOp> ops;

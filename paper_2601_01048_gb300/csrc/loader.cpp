@@ -18,6 +18,7 @@
 #include <string>
 #include <vector>
 
+#include "divide.h"
 #include "ir.h"
 
 namespace cufz {
@@ -54,7 +55,7 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
   const uint8_t* q = p + 32 + 4 * ir->n_sites;
   ir->ops.resize(n_ops);
   std::vector<int> open;
-  int bsites = 0, asites = 0, loops = 0;
+  int bsites = 0, asites = 0, dsites = 0, loops = 0;
   const int R = ir->n_regs;
   auto reg = [R](int r) { return r < R; };
   for (int pc = 0; pc < n_ops; pc++) {
@@ -94,6 +95,11 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
         case B_SEL:
           ok = reg(d) && reg(a) && reg(b) && imm >= 0 && imm < R;
           o.dst = d; o.a = a; o.b = b; o.c = imm;
+          break;
+        case B_DIV:
+        case B_REM:
+          ok = reg(d) && reg(a) && reg(b) && !imm;
+          o.dst = d; o.a = a; o.b = b; o.site = dsites++;
           break;
         case B_LD:
         case B_ST:
@@ -161,11 +167,13 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
     for (int j = pc + 1; j < h.end_pc; j++) {
       const IrOp& o = ir->ops[j];
       bool writes = (o.opc == B_SREG || o.opc == B_IMM || o.opc == B_MOV || o.opc == B_SEL ||
-                     o.opc == B_LD || o.opc == B_LOOP || is_alu_reg(o.opc) || is_alu_imm(o.opc));
+                     o.opc == B_LD || o.opc == B_LOOP || o.opc == B_DIV || o.opc == B_REM ||
+                     is_alu_reg(o.opc) || is_alu_imm(o.opc));
       if (writes && o.dst == h.dst) return false;
     }
   }
   ir->n_access = asites;
+  ir->n_div = dsites;
   ir->n_loops = loops;
   ir->nv = kTripBase + loops;
   return true;
@@ -214,6 +222,12 @@ void uses_defs(const IrOp& o, bool device_ir, int* U, int* nu, int* D, int* nd) 
       if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
       break;
     case B_ST: U[(*nu)++] = o.a; break;
+    case B_DIV:
+    case B_REM:  // a check: the divisor always, the dividend while the result is live
+      U[(*nu)++] = o.b;
+      if (!o.value_dead) U[(*nu)++] = o.a;
+      if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
+      break;
     case B_IF: U[(*nu)++] = o.a; break;
     case B_LOOP:
       U[(*nu)++] = o.a;
@@ -286,6 +300,8 @@ bool is_value_op(uint8_t opc) {
 }
 
 // MathElimination: drop value ops whose result is dead, to a fixed point.
+// A division stays as a check (its divisor decides the fault); once its
+// result is dead its dividend is no longer a use.
 void prune(Ir* ir) {
   for (;;) {
     Liveness L = liveness(*ir, false);
@@ -294,6 +310,10 @@ void prune(Ir* ir) {
       IrOp& o = ir->ops[pc];
       if (o.kept && is_value_op(o.opc) && !L.out[pc].get(o.dst)) {
         o.kept = false;
+        changed = true;
+      }
+      if ((o.opc == B_DIV || o.opc == B_REM) && !o.value_dead && !L.out[pc].get(o.dst)) {
+        o.value_dead = true;
         changed = true;
       }
     }
@@ -488,7 +508,8 @@ struct Gen {
   }
 
   bool counted(const IrOp& o2) const {
-    return o2.kept && o2.opc != B_SREG && is_value_op(o2.opc);
+    return o2.kept && ((o2.opc != B_SREG && is_value_op(o2.opc)) || o2.opc == B_DIV ||
+                       o2.opc == B_REM);
   }
 
   // whether ops [pc, end) hold a kept IF or LOOP (a branch site)
@@ -594,6 +615,31 @@ struct Gen {
     line(ind, "}");
   }
 
+  // A checked division: a zero divisor is a violation (its record written
+  // by the program's fault helper in the record function) and gives 0;
+  // INT_MIN / -1 wraps.
+  void divide(int ind, const IrOp& o2) {
+    line(ind, "{");
+    line(ind + 1, "const int32_t dv = " + r(o2.b) + ";");
+    if (rec_) {
+      line(ind + 1, "if (dv == 0) {");
+      line(ind + 2, "if (fo == ~0u) fo = ordinal;");
+      line(ind + 2, "if (write) write = !cufz_prog_" + std::to_string(index) +
+                        "_div_fault(bl, tl, ordinal, " + std::to_string(o2.site) + "u);");
+      line(ind + 1, "}");
+      line(ind + 1, "ordinal++;");
+    } else {
+      line(ind + 1, "nv += dv == 0 ? 1u : 0u;");
+    }
+    if (!o2.value_dead) {
+      const bool rem = o2.opc == B_REM;
+      const std::string x = r(o2.a), mn = "(int32_t)0x80000000u";
+      line(ind + 1, r(o2.dst) + " = dv == 0 ? 0 : (" + x + " == " + mn + " && dv == -1) ? " +
+                        (rem ? "0" : mn) + " : " + x + (rem ? " % dv;" : " / dv;"));
+    }
+    line(ind, "}");
+  }
+
   void range(int ind, int pc, int end) {
     run_counts(ind, pc, end);
     while (pc < end) {
@@ -617,6 +663,8 @@ struct Gen {
         line(ind, r(o2.dst) + " = " + r(o2.a) + " != 0 ? " + r(o2.b) + " : " + r(o2.c) + ";");
       } else if (opc == B_LD || opc == B_ST) {
         access(ind, o2);
+      } else if (opc == B_DIV || opc == B_REM) {
+        divide(ind, o2);
       } else if (opc == B_IF) {
         std::string c = "c" + std::to_string(o2.site);
         line(ind, "{");
@@ -751,6 +799,30 @@ struct Gen {
       if (op.kept && op.opc == B_SREG) sreg_used[op.sreg] = true;
     }
     const std::string fn = "cufz_prog_" + std::to_string(index);
+
+    // division faults: records of kind 2 (division), class DIV_ZERO, written
+    // like access records (one atomicAdd per active-mask group)
+    bool divides = false;
+    for (const auto& op : ir.ops) divides |= op.kept && (op.opc == B_DIV || op.opc == B_REM);
+    if (divides) {
+      line(0, "__device__ __noinline__ bool " + fn +
+                  "_div_fault(uint32_t bl, uint32_t tl, uint32_t ordinal, uint32_t site) {");
+      line(1, "const uint32_t am = __activemask();");
+      line(1, "const uint32_t lane = threadIdx.x & 31u;");
+      line(1, "const uint32_t leader = __ffs(am) - 1;");
+      line(1, "const uint32_t k = __popc(am);");
+      line(1, "const uint32_t cap = s_T.record_cap;");
+      line(1, "const uint32_t slot = s_in.slot;");
+      line(1, "uint32_t base = 0;");
+      line(1, "if (lane == leader) base = atomicAdd(&s_T.slots[slot].rec_reserved, k);");
+      line(1, "base = __shfl_sync(am, base, leader);");
+      line(1, "const uint32_t rank = __popc(am & ((1u << lane) - 1u));");
+      line(1, "if (base + rank < cap)");
+      line(2, "write_record(s_T.records + (size_t)slot * cap + base + rank, bl, tl, ordinal, site, "
+              "0u, 2u, 0u, 0u, CUFZ_CLS_DIV_ZERO, 0);");
+      line(1, "return base + k >= cap;");
+      line(0, "}");
+    }
 
     // record function: one test thread, records and the first violation
     rec_ = true;
@@ -975,6 +1047,17 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
           d.opc = D_SEL; d.d = off(o.dst); d.a = off(o.a); d.b = off(o.b);
           d.imm = (int32_t)off(o.c);
           break;
+        case B_DIV:
+        case B_REM:
+          d.opc = D_DIVREM;
+          d.b = off(o.b);
+          d.x = (uint8_t)((opc == B_REM ? 1u : 0u) | (o.value_dead ? 0u : 2u));
+          if (!o.value_dead) {
+            d.d = off(o.dst);
+            d.a = off(o.a);
+          }
+          d.imm = o.site;
+          break;
         case B_LD:
         case B_ST:
           d.opc = opc == B_ST ? D_ST : (o.value_dead ? D_LDX : D_LD);
@@ -1127,6 +1210,8 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
         case B_IMM: d = R(o.dst); imm = o.imm; break;
         case B_MOV: d = R(o.dst); a = R(o.a); break;
         case B_SEL: d = R(o.dst); a = R(o.a); b = R(o.b); imm = R(o.c); break;
+        case B_DIV:
+        case B_REM: d = R(o.dst); a = o.value_dead ? 0 : R(o.a); b = R(o.b); break;
         case B_LD: d = R(o.dst); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
         case B_ST: d = R(o.a); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
         case B_IF: a = R(o.a); break;

@@ -231,6 +231,8 @@ struct PrexRun {
           pc = o.end_pc + 1;
           break;
         }
+        case B_DIV:
+        case B_REM: return false;  // a division: not in either analysis
         default: pc++; break;
       }
     }
@@ -672,6 +674,8 @@ struct PrexGrid {
           pc = o.end_pc + 1;
           break;
         }
+        case B_DIV:
+        case B_REM: return false;  // a division: not in either analysis
         default: pc++; break;
       }
     }

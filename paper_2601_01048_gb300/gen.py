@@ -344,6 +344,88 @@ def guard2d_inputs(n: int = 4096, seed: int | None = None, max_grid: int = 256) 
 
 
 # --------------------------------------------------------------------------
+# division workload: signed DIV/REM whose divisors are zero for some threads
+# or inputs (the divide-by-zero kernel error of Sec. 2.3)
+# --------------------------------------------------------------------------
+
+def div_program(index: int) -> bytes:
+    """Random programs with signed divisions.  Divisors come from a
+    coordinate minus an argument, a masked argument, a loaded byte, or a
+    value plus a small constant: each is zero for some threads or inputs.
+    Quotients and remainders feed access indices, branch conditions and a
+    uniform loop."""
+    rng = SplitMix64(sub_seed("divprog", index))
+    A = Asm(n_bufs=3, seed=rng.next32())
+    tx, ty, bx = A.sreg(bc.TID_X), A.sreg(bc.TID_Y), A.sreg(bc.CTAID_X)
+    args = [A.sreg(bc.ARG0 + k) for k in range(4)]
+    lin = A.alu(bc.ADD, A.alu(bc.MUL, bx, A.sreg(bc.NTID_X)), tx)
+    coords = [tx, ty, lin]
+    vals = coords + args
+
+    def divisor():
+        r = rng.below(4)
+        if r == 0:
+            return A.alu(bc.SUB, rng.choice(coords), rng.choice(args))
+        if r == 1:
+            return A.alu(bc.AND, rng.choice(args), Imm(rng.choice((1, 3, 7))))
+        if r == 2:
+            return A.ld(0, A.alu(bc.AND, lin, Imm(63)), 1)
+        return A.alu(bc.ADD, rng.choice(vals), Imm(rng.randint(-2, 2)))
+
+    def division():
+        x = rng.choice(vals)
+        q = A.div(x, divisor()) if rng.below(2) else A.rem(x, divisor())
+        vals.append(q)
+        return q
+
+    def index():
+        v = rng.choice(vals[-4:])
+        return A.alu(bc.AND, v, Imm(rng.choice((63, 255, -1))))
+
+    def body(depth):
+        for _ in range(rng.randint(2, 5)):
+            r = rng.below(6)
+            if r <= 1 or depth >= 2:
+                division()
+            elif r == 2:
+                A.ld(rng.choice((1, 2)), index(), rng.choice((1, 4)))
+            elif r == 3:
+                A.if_(A.alu(bc.SETLT, rng.choice(vals), rng.choice(vals)))
+                body(depth + 1)
+                A.endif()
+            elif r == 4:
+                k = A.loop(A.alu(bc.AND, args[3], Imm(3)), 4)
+                q = A.div(A.alu(bc.ADD, k, rng.choice(vals)), divisor())
+                A.ld(1, A.alu(bc.AND, q, Imm(127)), 1)
+                A.endloop()
+            else:
+                A.st(2, index(), rng.choice(vals), 4)
+        A.ld(1, index(), 4)
+
+    body(0)
+    return A.build()
+
+
+def div_programs(n: int = 16) -> list[bytes]:
+    return [div_program(i) for i in range(n)]
+
+
+def div_inputs(n: int, n_programs: int = 16, seed: int | None = None,
+               max_blocks: int = 8) -> np.ndarray:
+    """Blocks of 16 x 4 threads, 1D grids up to max_blocks; arguments from
+    {0, +-1, 2, 3, 5, 16, -7, INT_MIN}; buffer 0 (the divisor bytes) 0-512
+    bytes, buffers 1 and 2 up to 4 KiB."""
+    rng = SplitMix64(sub_seed("div") if seed is None else seed)
+    out = make_inputs(n)
+    for k in range(n):
+        args = [rng.choice((0, 1, -1, 2, 3, 5, 16, -7, -(1 << 31))) for _ in range(4)]
+        lens = [rng.randint(0, 512), rng.randint(0, 4096), rng.randint(0, 4096)]
+        set_input(out[k], k % n_programs, (rng.randint(1, max_blocks), 1, 1), (16, 4, 1), args,
+                  lens, tag=k)
+    return out
+
+
+# --------------------------------------------------------------------------
 # config 2: random 2D programs with shared buffers and loops
 # --------------------------------------------------------------------------
 

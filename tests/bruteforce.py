@@ -42,7 +42,7 @@ def parse(prog: bytes):
     assert magic == 0x315A4643 and ver == 1
     loc = [struct.unpack_from("<HH", prog, 32 + 4 * s) for s in range(n_sites)]
     raw = [struct.unpack_from("<BBBBi", prog, 32 + 4 * n_sites + 8 * i) for i in range(n_ops)]
-    counters = {"b": 0, "a": 0}
+    counters = {"b": 0, "a": 0, "d": 0}
     pos = [0]
 
     def block(terminators):
@@ -71,6 +71,9 @@ def parse(prog: bytes):
             elif opc in (0x40, 0x41):
                 out.append(("mem", opc == 0x41, d, a, b, imm, counters["a"]))
                 counters["a"] += 1
+            elif opc in (0x05, 0x06):
+                out.append(("div", opc == 0x06, d, a, b, counters["d"]))
+                counters["d"] += 1
             else:
                 out.append(("op", opc, d, a, b, imm))
         return out, None
@@ -153,6 +156,18 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
             if not is_st:
                 regs[d] = val
 
+        def divide(is_rem, d, a, b, site):
+            x, y = regs[a], regs[b]
+            if y == 0:
+                st["records"].append((bl, tl, t["ordinal"], site, 0, 2, 0, 0, 5, 0))
+                val = 0
+            else:
+                q = abs(x) // abs(y)
+                q = q if (x < 0) == (y < 0) else -q
+                val = s32(x - y * q) if is_rem else s32(q)
+            t["ordinal"] += 1
+            regs[d] = val
+
         def run(stmts):
             for s in stmts:
                 if t["stop"]:
@@ -175,6 +190,9 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 elif kind == "mem":
                     _, is_st, d, a, buf, w, site = s
                     mem(is_st, d, a, buf, w, site)
+                elif kind == "div":
+                    _, is_rem, d, a, bb, site = s
+                    divide(is_rem, d, a, bb, site)
                 elif kind == "if":
                     _, a, site, then, els = s
                     taken = regs[a] != 0

@@ -16,9 +16,10 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    """The full-size workload tests run last: they take the longest, and the
-    quick parity tests should report first."""
-    items.sort(key=lambda item: "test_gpu_fullsize" in item.nodeid)
+    """The division-fault tests, then the full-size workload tests, run
+    last: the first are the newest device code, the second take the longest,
+    and the established parity tests should report first."""
+    items.sort(key=lambda item: ("test_gpu_divfault" in item.nodeid) + 2 * ("test_gpu_fullsize" in item.nodeid))
 
 
 def golden(name):

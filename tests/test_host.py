@@ -230,3 +230,53 @@ def test_abi_rejects_missing_arguments():
     stats = B.cufz_prog_stats()
     assert L.cufz_prune_program(prog, len(prog), None, 0, ref(sz), ref(stats)) == B.E_NOMEM
     assert sz.value == len(B.cufz_prune_program(prog)[0])
+
+
+@pytest.mark.parametrize("which", range(16))
+def test_prune_keeps_every_division(orc, which):
+    """Divisions are checks: pruning keeps every DIV/REM (and the values that
+    decide their faults), so the oracle gives the same fault and access
+    records, ordinals, digest, counts and bitmap on the pruned program."""
+    prog = gen.div_program(which)
+    pruned, st = B.cufz_prune_program(prog)
+    assert orc.validate(pruned) == 0 and B.cufz_validate_program(pruned) == 0
+    kinds = (bc.LD, bc.ST, bc.IF, bc.ELSE, bc.ENDIF, bc.LOOP, bc.ENDLOOP, bc.DIV, bc.REM)
+    assert [o[0] for o in bc.ops_of(prog) if o[0] in kinds] == \
+        [o[0] for o in bc.ops_of(pruned) if o[0] in kinds]
+    ins = gen.div_inputs(4, n_programs=1, seed=400 + which)
+    for o in (orc.opts(), orc.opts(iter_budget=2)):
+        r0, c0, b0 = orc.run_batch([prog], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+        r1, c1, b1 = orc.run_batch([pruned], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+        assert r0.tobytes() == r1.tobytes() and c0.tobytes() == c1.tobytes()
+        assert np.array_equal(b0, b1)
+
+
+def test_prune_drops_the_dividend_of_a_dead_quotient(orc):
+    """q = (t * t * a0) / (t - a1) with q unused: the division stays (its
+    divisor decides the fault); the dividend's two multiplications and the
+    read of a0 that only they use go."""
+    A = Asm(n_bufs=1)
+    t, a0, a1 = A.sreg(bc.TID_X), A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    A.div(A.alu(bc.MUL, A.alu(bc.MUL, t, t), a0), A.alu(bc.SUB, t, a1))
+    A.ld(0, t, 4)
+    prog = A.build()
+    pruned, st = B.cufz_prune_program(prog)
+    assert st.n_ops_kept == st.n_ops_in - 3
+    assert [o[0] for o in bc.ops_of(pruned)].count(bc.DIV) == 1
+    inp = gen.make_inputs(1)
+    gen.set_input(inp[0], 0, (2, 1, 1), (8, 1, 1), (3, 5), (16,))
+    r0, c0, _ = orc.run(orc.Program(prog), inp[0], rec_cap=64)
+    r1, c1, _ = orc.run(orc.Program(pruned), inp[0], rec_cap=64)
+    assert r0.tobytes() == r1.tobytes() and c0.tobytes() == c1.tobytes()
+    assert int(r0["n_violations"]) == 2 + 2 * 4                 # t == 5 faults; loads of t >= 4
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_validator_agrees_with_oracle_on_division_programs(orc, seed):
+    rng = gen.SplitMix64(seed + 500)
+    prog = bytearray(gen.div_program(seed % 16))
+    for _ in range(rng.randint(1, 3)):
+        pos = rng.randint(32, len(prog) - 1)
+        prog[pos] = rng.choice((0x05, 0x06, rng.below(256)))
+    p = bytes(prog)
+    assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)

@@ -144,3 +144,18 @@ def test_interpreter_prex_items(tmp_path, interp_exe, orc):
         keep = np.isin(full["block_lin"].astype(np.int64) * T + full["thread_lin"], plans[k])
         assert record_set(recs) == record_set(full[keep]), k
         assert int(res["n_violations"]) == int(keep.sum())
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_interpreter_division_programs(tmp_path, interp_exe, orc, flags):
+    """Programs with signed divisions: fault records (kind 2) from lanes of
+    one warp reserved together, ordinals that count divisions, values,
+    pruned (dead quotients kept as checks) and unpruned, with a small record
+    cap as well."""
+    progs = gen.div_programs()
+    ins = gen.div_inputs(48, seed=313)
+    for cap in (1 << 14, 8):
+        got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
+        ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
+        compare(got, ores, orecs, obms, cap)
+        assert sum(int((r["kind"] == 2).sum()) for _, r, _ in got) > 0

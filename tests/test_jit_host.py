@@ -234,3 +234,30 @@ def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
             assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
             assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
             assert np.array_equal(bm, obms[i]), (budget, i)
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_division_programs_match_oracle(tmp_path, host_objs, orc, flags):
+    """Programs with signed divisions (zero divisors from coordinates, masked
+    arguments and loaded bytes; quotients and remainders as indices, in
+    branches and a loop): fault records (kind 2), ordinals that count
+    divisions, values and every other result equal the oracle's, pruned and
+    unpruned, and under a budget that stops threads early."""
+    progs = gen.div_programs()
+    ins = gen.div_inputs(48, seed=312)
+    exe = build(tmp_path, host_objs, progs, flags)
+    for budget in (4096, 2):
+        got = run(tmp_path, exe, progs, ins, budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
+                                          rec_cap=1 << 14, bitmaps=True)
+        faults = 0
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records"):
+                assert int(res[f]) == int(o[f]), (budget, i, f)
+            assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
+            assert np.array_equal(bm, obms[i]), (budget, i)
+            faults += int((recs["kind"] == 2).sum())
+        assert faults > 0

@@ -509,3 +509,89 @@ def test_batch_equals_single_runs(orc):
         assert res[k].tobytes() == r1.tobytes()
         assert recs[k][: int(r1["n_records"])].tobytes() == rc1.tobytes()
         assert np.array_equal(bms[k], bm1)
+
+
+def _trunc_div(x, y):
+    """C's truncating division, from Python's floor division."""
+    q = abs(x) // abs(y)
+    return q if (x >= 0) == (y >= 0) else -q
+
+
+def test_division_values_faults_and_ordinals(orc):
+    """q = a0 / (tid - a1); r = a0 % (tid - a1); two 1-byte loads at q and r
+    from a zero-length buffer, so every load violates and its record's
+    byte offset shows the index.  Values: C truncation (checked against
+    Python's floor division), INT_MIN / -1 = INT_MIN with remainder 0.  A
+    zero divisor: two fault records (kind 2, class DIV_ZERO, division sites 0
+    and 1) and 0 as both results.  Ordinals count divisions and accesses
+    alike (faults at 0 and 1, loads at 2 and 3); n_accesses counts loads
+    only."""
+    A = Asm(n_bufs=1)
+    d = A.alu(bc.SUB, A.sreg(bc.TID_X), A.sreg(bc.ARG1))
+    a0 = A.sreg(bc.ARG0)
+    q, r = A.div(a0, d), A.rem(a0, d)
+    A.ld(0, q, 1)
+    A.ld(0, r, 1)
+    prog = A.build()
+    for a0v, a1v in ((-7, 5), (7, 3), (-(1 << 31), 1), (1 << 31 - 1, 15)):
+        res, recs, _ = orc.run(orc.Program(prog), mk((2, 1, 1), (16, 1, 1), (a0v, a1v), (0,)),
+                               rec_cap=1 << 10)
+        assert int(res["n_accesses"]) == 64
+        faults = [x for x in recs if int(x["kind"]) == 2]
+        loads = [x for x in recs if int(x["kind"]) == 0]
+        assert len(loads) == 64 and int(res["n_violations"]) == 64 + len(faults)
+        zero_threads = [t for t in range(16) if t - a1v == 0]
+        assert len(faults) == 2 * 2 * len(zero_threads)
+        for f in faults:
+            assert int(f["thread_lin"]) in zero_threads and int(f["cls"]) == 5
+            assert int(f["ordinal"]) == int(f["site"]) and int(f["buf"]) == 0
+            assert int(f["width"]) == 0 and int(f["byte_off"]) == 0
+        for x in loads:
+            t, dv = int(x["thread_lin"]), int(x["thread_lin"]) - a1v
+            if dv == 0:
+                want = 0
+            elif a0v == -(1 << 31) and dv == -1:
+                want = -(1 << 31) if int(x["ordinal"]) == 2 else 0
+            else:
+                qv = _trunc_div(a0v, dv)
+                want = qv if int(x["ordinal"]) == 2 else a0v - dv * qv
+            assert int(x["byte_off"]) == want, (a0v, a1v, t, int(x["ordinal"]))
+            assert int(x["ordinal"]) in (2, 3)
+        assert int(res["first_key"]) == 2 or (0 in zero_threads and int(res["first_key"]) == 0)
+
+
+def test_division_leaves_the_digest_and_counts_as_a_check(orc):
+    """A division whose result is unused changes neither the digest nor the
+    access count; it moves the accesses' ordinals (and so the first key) by
+    one, and faults in every thread whose divisor is 0."""
+    def prog(with_div):
+        A = Asm(n_bufs=1)
+        tx = A.sreg(bc.TID_X)
+        if with_div:
+            A.div(A.sreg(bc.ARG0), tx)
+        A.ld(0, A.alu(bc.SUB, tx, Imm(3)), 4)
+        return A.build()
+    inp = mk((3, 1, 1), (8, 1, 1), (11,), (4 * 8,))
+    r0, c0, _ = orc.run(orc.Program(prog(False)), inp, rec_cap=64)
+    r1, c1, _ = orc.run(orc.Program(prog(True)), inp, rec_cap=64)
+    assert int(r0["digest"]) == int(r1["digest"]) and int(r0["n_accesses"]) == int(r1["n_accesses"])
+    assert int(r1["n_violations"]) == int(r0["n_violations"]) + 3          # tid 0 in each block
+    assert int(r0["first_key"]) == 0 and int(r1["first_key"]) == 0          # the fault, ordinal 0
+    assert sorted(int(x["ordinal"]) for x in c1 if int(x["kind"]) == 0) == \
+        sorted(int(x["ordinal"]) + 1 for x in c0)
+
+
+@pytest.mark.parametrize("index", range(8))
+def test_bruteforce_division_programs(orc, index):
+    """Random programs with divisions (zero divisors from coordinates,
+    masked arguments and loaded bytes; quotients as indices, in branches and
+    in a loop): the oracle equals the independent evaluator exactly."""
+    prog = gen.div_program(index)
+    for x in gen.div_inputs(3, n_programs=1, seed=3000 + index, max_blocks=3):
+        _compare_bruteforce(orc, prog, dict(grid=tuple(int(v) for v in x["grid"]),
+                                            block=tuple(int(v) for v in x["block"]),
+                                            args=[int(v) for v in x["args"]],
+                                            lens=[int(v) for v in x["buf_len"][:3]]))
+    res, recs, _ = orc.run(orc.Program(prog), gen.div_inputs(1, n_programs=1, seed=9)[0],
+                           rec_cap=1 << 12)
+    assert int(res["n_accesses"]) > 0
