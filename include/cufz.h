@@ -291,9 +291,11 @@ cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* 
  *   - guarded grids (the guarded kernels of Sec. 5.1's Alg. 1, decided
  *     exactly rather than heuristically): each launch dimension is one axis,
  *     its global coordinate ctaid * ntid + tid, or two, tid and ctaid.  The
- *     program's values must be thread-invariant or affine in the thread and
- *     block indices (no int32 wrap in the launch box).  Its branch
- *     conditions must be guards or combinations of guards.  A guard compares
+ *     program's values must be thread-invariant, affine in the thread and
+ *     block indices, or piecewise affine: one of a few affine functions in
+ *     each cell (min/max of affine values, a register the two sides of a
+ *     guard set differently), all without int32 wrap in the launch box.  Its
+ *     branch conditions must be guards or combinations of guards.  A guard compares
  *     values affine in one dimension's coordinates (<, <=, ==, !=, or an
  *     affine value against zero), so its truth changes only at a few cuts
  *     of that dimension's axes.  The cuts split the launch box into cells in
@@ -304,9 +306,9 @@ cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* 
  *     are explored, loop trips must be thread-invariant, and iter_budget
  *     bounds the abstract back-edges (0 = 4096).
  * *n_threads = 0 when neither rule applies (run the full grid), and for
- * launches the engine does not run (invalid shapes, more than 2^31 threads).
- * CUFZ_E_NOMEM
- * when the plan has more than cap threads (*n_threads gives the size).
+ * launches the engine does not run (invalid shapes, more than 2^31 threads)
+ * and for programs with divisions.  CUFZ_E_NOMEM when the plan has more than
+ * cap threads (*n_threads gives the size).
  * Host-only; no device needed. */
 cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* in,
                            uint32_t iter_budget, uint32_t* threads, uint32_t cap,
