@@ -278,7 +278,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
  * such affine value can leave the int32 range in the launch box (the device
  * computes in wrapping 32-bit arithmetic).  Programs with thread-dependent
  * guards (the paper's Alg. 1 case, a heuristic) are not eligible, nor are
- * launches the engine does not run (invalid shapes, more than 2^31 threads).
+ * programs with divisions and launches the engine does not run (invalid
+ * shapes, more than 2^31 threads).
  * iter_budget: the context's back-edge budget (0 = 4096). */
 cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
                             uint32_t iter_budget, uint32_t* eligible);
