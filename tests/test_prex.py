@@ -552,3 +552,14 @@ def test_head_tail_heuristic_misses_what_the_plan_finds(orc):
     assert plan is not None and len(plan) <= 8
     ok, full = plan_decides_every_site(orc, prog, inp, plan)
     assert ok and full
+
+
+def test_no_plan_for_programs_that_divide():
+    """A division is a check of its own that neither analysis models: an
+    otherwise affine program with a division gets no plan."""
+    A = Asm(n_bufs=1)
+    i = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    A.div(A.sreg(bc.ARG0), A.alu(bc.SUB, i, A.sreg(bc.ARG1)))
+    A.ld(0, i, 4)
+    inp = mk((4, 1, 1), (32, 1, 1), (1, 7), (400,))
+    assert not B.cufz_prex_check(A.build(), inp) and B.cufz_prex_plan(A.build(), inp) is None
