@@ -42,6 +42,17 @@
  * 0x05 DIV and 0x06 REM dst = a / b and a % b, signed and truncating: a zero
  * divisor is a fault (a violation of kind 2, result 0), INT_MIN / -1 is
  * INT_MIN and INT_MIN % -1 is 0;
+ * 0x07 HALLOC dst = a heap block of a bytes (the device heap of Sec. 2.3,
+ * per test thread): the k-th HALLOC's block, handle k + 1, live with a
+ * bytes, or 0 (NULL, nothing changes) when a <= 0; 0x08 HFREE frees the
+ * block of handle a: 0 is a no-op, a handle of no block this thread
+ * allocated is an invalid free and a freed block a double free (both
+ * violations of kind 3, space 2, the block stays as it was); 0x42 HLD dst
+ * = heap block of handle b at index a, width imm (reads 0), and 0x43 HST
+ * (register dst, never performed): accesses to space 2, a handle of no
+ * allocated block a wild access, a freed block a use after free, otherwise
+ * checked against the block's size like a buffer of the redzone classes
+ * (no neighbours);
  * 0x10-0x1F ALU dst = a op b and 0x30-0x3F the same with b = imm, op in
  * order add, sub, mul, shl, shr (arithmetic), shru, and, or, xor, min, max
  * (signed), setlt, setle, seteq, setne (signed, 0 or 1), setltu (unsigned),
@@ -51,8 +62,11 @@
  * a, 0x51 ELSE, 0x52 ENDIF; 0x53 LOOP with counter dst and trip count
  * clamp(a, 0, imm), 0x54 ENDLOOP.
  * Control flow is structured, at most 16 deep; a loop counter is read-only
- * in its body.  The k-th LD/ST in program order is access site k, the k-th
- * IF/LOOP branch site k, the k-th DIV/REM division site k.
+ * in its body.  The k-th LD/ST/HLD/HST in program order is access site k,
+ * the k-th IF/LOOP branch site k, the k-th DIV/REM division site k, the
+ * k-th HFREE free site k.  The program's registers and one register per
+ * HALLOC must fit the interpreter's 128 per thread: a program above that
+ * loads as CUFZ_E_INVALID_PROGRAM.
  *
  * Input, result and violation records are the fixed-layout structs below.
  */
@@ -105,6 +119,9 @@ typedef int32_t cufz_status;
 #define CUFZ_CLS_OTHER_ALLOC 3  /* lands in another buffer of the same space */
 #define CUFZ_CLS_WILD 4         /* anything else */
 #define CUFZ_CLS_DIV_ZERO 5     /* a division (record kind 2) by zero */
+#define CUFZ_CLS_USE_AFTER_FREE 6 /* a heap access to a freed block */
+#define CUFZ_CLS_DOUBLE_FREE 7    /* HFREE (record kind 3) of a freed block */
+#define CUFZ_CLS_INVALID_FREE 8   /* HFREE of a handle of no allocated block */
 
 /* configuration flags (cufz_config.flags) */
 #define CUFZ_CF_KEEP_BITMAPS 1 /* keep each input's 64 KiB bitmap until released */
@@ -186,17 +203,20 @@ typedef struct {
 typedef struct {
   uint32_t block_lin;
   uint32_t thread_lin;
-  uint32_t ordinal; /* checked events (accesses, divisions) of this thread before this one */
-  uint16_t site;    /* kind 0/1: index of the LD/ST among the program's LD/STs;
-                       kind 2: index of the DIV/REM among its DIV/REMs */
-  uint8_t buf;      /* kind 2: 0 */
-  uint8_t kind;     /* 0 load, 1 store, 2 division by zero */
-  uint8_t width;    /* bytes (kind 2: 0) */
-  uint8_t space;    /* 0 global, 1 shared (kind 2: 0) */
+  uint32_t ordinal; /* checked events (accesses, divisions, frees) of this
+                       thread before this one */
+  uint16_t site;    /* kind 0/1: access site (LD/ST/HLD/HST in order);
+                       kind 2: index of the DIV/REM among its DIV/REMs;
+                       kind 3: index of the HFREE among its HFREEs */
+  uint8_t buf;      /* the buffer; space 2: the block's allocation site (0
+                       for a handle of no block); kinds 2 and 3: 0 */
+  uint8_t kind;     /* 0 load, 1 store, 2 division by zero, 3 bad free */
+  uint8_t width;    /* bytes (kinds 2 and 3: 0) */
+  uint8_t space;    /* 0 global, 1 shared, 2 device heap (kind 2: 0) */
   uint8_t cls;      /* CUFZ_CLS_* */
   uint8_t pad0;
   uint32_t pad1;
-  int64_t byte_off; /* index * width (kind 2: 0) */
+  int64_t byte_off; /* index * width (kinds 2 and 3: 0) */
 } cufz_violation;
 
 #if !defined(__CUDACC_RTC__)

@@ -72,6 +72,20 @@
  * is INT_MIN and INT_MIN % -1 is 0, without a fault.  A division is not an
  * access: it is not counted in n_accesses and does not enter the digest.
  *
+ * Device heap (the temporal errors of Sec. 2.3: use after free, double
+ * free, invalid free), per test thread.  HALLOC at allocation site s (the
+ * s-th HALLOC) with size n >= 1 makes block s live with n bytes and returns
+ * handle s + 1; with n <= 0 it returns 0 (NULL) and changes nothing.
+ * HFREE h: h = 0 does nothing; a handle of no block this thread allocated
+ * is an invalid free, a freed block a double free (both records of kind 3,
+ * space 2, at the free's site); otherwise the block is freed.  HLD / HST at
+ * index i of width w through handle h are accesses (counted, in the digest,
+ * access sites shared with LD / ST) to heap space 2: a handle of no
+ * allocated block is a wild access, a freed block a use after free, and
+ * otherwise byte offset i * w is checked against the block's size as for
+ * a buffer (redzone classes, no neighbours).  Heap loads read 0.  Every
+ * HFREE, like every access and division, is a checked event for ordinals.
+ *
  * first_key = min over violations of
  *   block_lin << 32 | thread_lin << 22 | min(ordinal, 2^22 - 1).
  *
@@ -91,16 +105,17 @@
 enum { ORC_ST_OK = 0, ORC_ST_VIOLATION = 1, ORC_ST_INVALID_CONFIG = 2, ORC_ST_LIMIT = 3 };
 enum { ORC_FL_BUDGET = 1, ORC_FL_OVERFLOW = 2, ORC_FL_NEW_COV = 4 };
 enum { ORC_CLS_NONE = 0, ORC_CLS_UNDERFLOW_RZ = 1, ORC_CLS_OVERFLOW_RZ = 2,
-       ORC_CLS_OTHER_ALLOC = 3, ORC_CLS_WILD = 4, ORC_CLS_DIV_ZERO = 5 };
+       ORC_CLS_OTHER_ALLOC = 3, ORC_CLS_WILD = 4, ORC_CLS_DIV_ZERO = 5,
+       ORC_CLS_USE_AFTER_FREE = 6, ORC_CLS_DOUBLE_FREE = 7, ORC_CLS_INVALID_FREE = 8 };
 enum { ORC_E_FORMAT = -1, ORC_E_OPERAND = -2, ORC_E_STRUCTURE = -3, ORC_E_LOOPCTR = -4,
        ORC_E_SITES = -5, ORC_E_NOMEM = -6 };
 
 enum {
   OP_NOP = 0x00, OP_SREG = 0x01, OP_IMM = 0x02, OP_MOV = 0x03, OP_SEL = 0x04,
-  OP_DIV = 0x05, OP_REM = 0x06,
+  OP_DIV = 0x05, OP_REM = 0x06, OP_HALLOC = 0x07, OP_HFREE = 0x08,
   OP_ADD = 0x10, OP_SUB, OP_MUL, OP_SHL, OP_SHR, OP_SHRU, OP_AND, OP_OR, OP_XOR,
   OP_MIN, OP_MAX, OP_SETLT, OP_SETLE, OP_SETEQ, OP_SETNE, OP_SETLTU,
-  OP_LD = 0x40, OP_ST = 0x41,
+  OP_LD = 0x40, OP_ST = 0x41, OP_HLD = 0x42, OP_HST = 0x43,
   OP_IF = 0x50, OP_ELSE = 0x51, OP_ENDIF = 0x52, OP_LOOP = 0x53, OP_ENDLOOP = 0x54
 };
 
@@ -142,7 +157,7 @@ typedef struct {
 } orc_op;
 
 typedef struct {
-  int n_ops, n_regs, n_bufs, n_sites, n_access, n_div;
+  int n_ops, n_regs, n_bufs, n_sites, n_access, n_div, n_alloc, n_free;
   uint32_t shared_mask, seed;
   uint16_t loc[256][2];
   orc_op ops[ORC_MAX_OPS];
@@ -185,7 +200,7 @@ static uint32_t rd32(const uint8_t* p) {
 static int writes_reg(const orc_op* o) {
   switch (o->opc) {
     case OP_SREG: case OP_IMM: case OP_MOV: case OP_SEL: case OP_LD: case OP_LOOP:
-    case OP_DIV: case OP_REM: return 1;
+    case OP_DIV: case OP_REM: case OP_HALLOC: case OP_HLD: return 1;
     default: return (o->opc >= 0x10 && o->opc <= 0x1F) || (o->opc >= 0x30 && o->opc <= 0x3F);
   }
 }
@@ -213,7 +228,7 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
   }
   const uint8_t* q = p + 32 + 4 * P->n_sites;
   int stack[ORC_MAX_DEPTH];
-  int depth = 0, bsite = 0, asite = 0, dsite = 0;
+  int depth = 0, bsite = 0, asite = 0, dsite = 0, hsite = 0, fsite = 0;
   int R = P->n_regs;
   for (int pc = 0; pc < P->n_ops; pc++) {
     orc_op* o = &P->ops[pc];
@@ -242,6 +257,19 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
         case OP_REM:
           ok = o->dst < R && o->a < R && o->b < R && !o->imm;
           if (ok) o->site = dsite++;
+          break;
+        case OP_HALLOC:
+          ok = o->dst < R && o->a < R && !o->b && !o->imm;
+          if (ok) o->site = hsite++;
+          break;
+        case OP_HFREE:
+          ok = !o->dst && o->a < R && !o->b && !o->imm;
+          if (ok) o->site = fsite++;
+          break;
+        case OP_HLD:
+        case OP_HST:
+          ok = o->dst < R && o->a < R && o->b < R && valid_width(o->imm);
+          if (ok) o->site = asite++;
           break;
         case OP_LD:
         case OP_ST:
@@ -296,6 +324,8 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
   if (bsite != P->n_sites) return ORC_E_SITES;
   P->n_access = asite;
   P->n_div = dsite;
+  P->n_alloc = hsite;
+  P->n_free = fsite;
   /* a loop counter is read-only inside its own body */
   for (int pc = 0; pc < P->n_ops; pc++) {
     const orc_op* o = &P->ops[pc];
@@ -341,6 +371,8 @@ typedef struct {
   uint32_t h; /* the thread's digest state H */
   uint64_t backedges;
   int stopped;
+  int32_t hsize[ORC_MAX_OPS];  /* per allocation site: the block's size */
+  uint8_t hstate[ORC_MAX_OPS]; /* 0 never allocated, 1 live, 2 freed */
 } orc_ctx;
 
 static void cover(orc_ctx* c, int site, int outcome) {
@@ -432,6 +464,76 @@ static int32_t do_divide(orc_ctx* c, const orc_op* op) {
   return value;
 }
 
+/* HALLOC: a live block of n >= 1 bytes at this site, handle site + 1. */
+static int32_t do_alloc(orc_ctx* c, const orc_op* op) {
+  int32_t n = c->r[op->a];
+  if (n < 1) return 0;
+  c->hstate[op->site] = 1;
+  c->hsize[op->site] = n;
+  return op->site + 1;
+}
+
+/* HFREE: NULL is a no-op; a handle of no allocated block is an invalid
+ * free, a freed block a double free. */
+static void do_free(orc_ctx* c, const orc_op* op) {
+  int32_t h = c->r[op->a];
+  if (h != 0) {
+    int cls = 0;
+    if (h < 1 || h > c->P->n_alloc || c->hstate[h - 1] == 0)
+      cls = ORC_CLS_INVALID_FREE;
+    else if (c->hstate[h - 1] == 2)
+      cls = ORC_CLS_DOUBLE_FREE;
+    else
+      c->hstate[h - 1] = 2;
+    if (cls) {
+      orc_record proto;
+      memset(&proto, 0, sizeof(proto));
+      proto.site = (uint16_t)op->site;
+      proto.kind = 3;
+      proto.space = 2;
+      proto.cls = (uint8_t)cls;
+      violation(c, &proto);
+    }
+  }
+  c->ordinal++;
+}
+
+/* HLD / HST: an access through a heap handle; heap loads read 0. */
+static void do_heap_access(orc_ctx* c, const orc_op* op, int is_store) {
+  int32_t idx = c->r[op->a];
+  int32_t h = c->r[op->b];
+  int w = op->imm;
+  int64_t off = (int64_t)idx * (int64_t)w;
+  c->res->n_accesses++;
+  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 1u;
+  c->h = (c->h ^ (uint32_t)idx) * K + 0x9E3779B9u;
+  int cls = 0, buf = 0;
+  if (h < 1 || h > c->P->n_alloc || c->hstate[h - 1] == 0) {
+    cls = ORC_CLS_WILD;
+  } else {
+    buf = h - 1;
+    int64_t len = c->hsize[h - 1], R = (int64_t)c->o->redzone;
+    if (c->hstate[h - 1] == 2)
+      cls = ORC_CLS_USE_AFTER_FREE;
+    else if (off < 0 || off + w > len)
+      cls = (off < 0 && off >= -R) ? ORC_CLS_UNDERFLOW_RZ
+            : (off >= 0 && off < len + R) ? ORC_CLS_OVERFLOW_RZ : ORC_CLS_WILD;
+  }
+  if (cls) {
+    orc_record proto;
+    memset(&proto, 0, sizeof(proto));
+    proto.site = (uint16_t)op->site;
+    proto.buf = (uint8_t)buf;
+    proto.kind = (uint8_t)is_store;
+    proto.width = (uint8_t)w;
+    proto.space = 2;
+    proto.cls = (uint8_t)cls;
+    proto.byte_off = off;
+    violation(c, &proto);
+  }
+  c->ordinal++;
+}
+
 static int32_t alu(int op, int32_t x, int32_t y) {
   uint32_t ux = (uint32_t)x, uy = (uint32_t)y;
   switch (op) {
@@ -485,6 +587,10 @@ static void exec_range(orc_ctx* c, int pc, int end) {
       case OP_LD: r[o->dst] = do_access(c, o, 0); pc++; break;
       case OP_DIV:
       case OP_REM: r[o->dst] = do_divide(c, o); pc++; break;
+      case OP_HALLOC: r[o->dst] = do_alloc(c, o); pc++; break;
+      case OP_HFREE: do_free(c, o); pc++; break;
+      case OP_HLD: do_heap_access(c, o, 0); r[o->dst] = 0; pc++; break;
+      case OP_HST: do_heap_access(c, o, 1); pc++; break;
       case OP_ST: (void)do_access(c, o, 1); pc++; break;
       case OP_IF: {
         int taken = r[o->a] != 0;
@@ -600,6 +706,7 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
       c->prev_loc = 0;
       c->backedges = 0;
       c->stopped = 0;
+      memset(c->hstate, 0, (size_t)P->n_alloc);
       c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
       c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
       exec_range(c, 0, P->n_ops);

@@ -39,7 +39,8 @@ assert RECORD_DTYPE.itemsize == 32
 
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT = 0, 1, 2, 3
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV = 1, 2, 4
-CLS_NONE, CLS_UNDERFLOW_RZ, CLS_OVERFLOW_RZ, CLS_OTHER_ALLOC, CLS_WILD = range(5)
+(CLS_NONE, CLS_UNDERFLOW_RZ, CLS_OVERFLOW_RZ, CLS_OTHER_ALLOC, CLS_WILD, CLS_DIV_ZERO,
+ CLS_USE_AFTER_FREE, CLS_DOUBLE_FREE, CLS_INVALID_FREE) = range(9)
 
 
 class Opts(ctypes.Structure):

@@ -20,7 +20,7 @@ SOURCES = ["engine.cu", "runtime.cu", "loader.cpp", "prex.cpp", "mutate.cpp", "n
 JIT_HEADERS = [("jit_kernel.cuh", "jit_kernel.cuh"), ("jit_launch.cuh", "jit_launch.cuh"),
                ("device_common.cuh", "device_common.cuh"), ("layout.h", "layout.h"),
                ("../../include/cufz.h", os.path.join("..", "..", "include", "cufz.h"))]
-HEADERS = ["engine.h", "ir.h", "interp_kernel.cuh", "divide.h"] + [h[1] for h in JIT_HEADERS]
+HEADERS = ["engine.h", "ir.h", "interp_kernel.cuh", "checked_ops.h"] + [h[1] for h in JIT_HEADERS]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

@@ -43,6 +43,11 @@ Opcodes and the fields they use (unused fields must be 0):
     REM   dst, a, b            dst = a % b, signed, truncating (0x06); for both a
                                zero divisor is a fault (result 0), and
                                INT_MIN / -1 = INT_MIN, INT_MIN % -1 = 0
+    HALLOC dst, a              heap block of a bytes (0x07): dst = its handle
+                               (allocation site + 1), or 0 when a <= 0
+    HFREE a                    free the block of handle a (0x08); 0 is a no-op
+    HLD   dst, a=idx, b=handle, imm=width   heap load (0x42), reads 0
+    HST   dst=value, a=idx, b=handle, imm=width   heap store (0x43)
     ALU   dst, a, b            opcode 0x10-0x1F, register b
     ALUI  dst, a, imm          opcode 0x30-0x3F, immediate b
     LD    dst, a=idx, b=buf, imm=width in {1,4,8,16}
@@ -53,7 +58,9 @@ Opcodes and the fields they use (unused fields must be 0):
     ENDLOOP
 
 The k-th LD/ST in program order is access site k; the k-th IF/LOOP is branch
-site k; the k-th DIV/REM is division site k.
+site k; the k-th DIV/REM is division site k.  HLD/HST share the access
+sites with LD/ST; the k-th HALLOC is allocation site k, the k-th HFREE free
+site k.
 """
 from __future__ import annotations
 
@@ -76,10 +83,14 @@ MOV = 0x03
 SEL = 0x04
 DIV = 0x05
 REM = 0x06
+HALLOC = 0x07
+HFREE = 0x08
 ADD, SUB, MUL, SHL, SHR, SHRU, AND, OR, XOR, MIN, MAX, SETLT, SETLE, SETEQ, SETNE, SETLTU = range(0x10, 0x20)
 IMM_FORM = 0x20
 LD = 0x40
 ST = 0x41
+HLD = 0x42
+HST = 0x43
 IF = 0x50
 ELSE = 0x51
 ENDIF = 0x52
@@ -179,6 +190,24 @@ class Asm:
         d = self._dst(dst)
         self.raw(REM, d, a, b)
         return d
+
+    def halloc(self, size: int, dst: int | None = None) -> int:
+        d = self._dst(dst)
+        self.raw(HALLOC, d, size)
+        return d
+
+    def hfree(self, handle: int) -> None:
+        self.raw(HFREE, 0, handle)
+
+    def hld(self, handle: int, idx: int, width: int = 4, dst: int | None = None) -> int:
+        d = self._dst(dst)
+        self.raw(HLD, d, idx, handle, width)
+        self.n_access += 1
+        return d
+
+    def hst(self, handle: int, idx: int, val: int, width: int = 4) -> None:
+        self.raw(HST, val, idx, handle, width)
+        self.n_access += 1
 
     def sel(self, c: int, x: int, y: int, dst: int | None = None) -> int:
         d = self._dst(dst)
@@ -300,6 +329,14 @@ def disasm(prog: bytes) -> str:
             lines.append(f"{pc:4d}  r{dst} = r{a} ? r{b} : r{imm}")
         elif opc in (DIV, REM):
             lines.append(f"{pc:4d}  r{dst} = {'div' if opc == DIV else 'rem'} r{a}, r{b}")
+        elif opc == HALLOC:
+            lines.append(f"{pc:4d}  r{dst} = halloc r{a}")
+        elif opc == HFREE:
+            lines.append(f"{pc:4d}  hfree r{a}")
+        elif opc == HLD:
+            lines.append(f"{pc:4d}  r{dst} = hld.w{imm} heap[r{b}][r{a}]")
+        elif opc == HST:
+            lines.append(f"{pc:4d}  hst.w{imm} heap[r{b}][r{a}] = r{dst}")
         elif opc == LD:
             lines.append(f"{pc:4d}  r{dst} = ld.w{imm} buf{b}[r{a}]")
         elif opc == ST:

@@ -6,7 +6,7 @@
 #pragma once
 
 #include "device_common.cuh"
-#include "divide.h"
+#include "checked_ops.h"
 
 namespace cufz {
 
@@ -228,6 +228,91 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
             if (y != 0) v = (x == mn && y == -1) ? ((op.x & 1u) ? 0 : mn) : ((op.x & 1u) ? x % y : x / y);
             rf_st(rf, op.d, v);
           }
+          if (act) ordinal++;
+          pc++;
+          break;
+        }
+        case D_HALLOC: {  // block of n >= 1 bytes at site s: state n, handle s + 1
+          if (act) {
+            const int32_t n = rf_ld(rf, op.a);
+            int32_t h = 0;
+            if (n >= 1) {
+              rf_st(rf, ((uint32_t)op.j0 + (uint32_t)op.imm) * kRegStride, n);
+              h = op.imm + 1;
+            }
+            rf_st(rf, op.d, h);
+            acc.n_ops++;
+          }
+          pc++;
+          break;
+        }
+        case D_HFREE: {  // NULL: no-op; no allocated block or a freed one: kind 3
+          uint32_t cls = 0;
+          if (act) {
+            const int32_t h = rf_ld(rf, op.a);
+            if (h != 0) {
+              const uint32_t s = (uint32_t)h - 1u;
+              const uint32_t so = ((uint32_t)op.j0 + s) * kRegStride;
+              const int32_t st = s < op.j1 ? rf_ld(rf, so) : 0;
+              if (st == 0)
+                cls = CUFZ_CLS_INVALID_FREE;
+              else if (st < 0)
+                cls = CUFZ_CLS_DOUBLE_FREE;
+              else
+                rf_st(rf, so, -1);
+            }
+            acc.n_ops++;
+          }
+          const uint32_t vm = __ballot_sync(FULL, cls != 0);
+          if (vm) {
+            const uint32_t rbase = reserve(vm);
+            if (cls) {
+              acc.n_viol++;
+              if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
+              const uint32_t rank = __popc(vm & lanemask_lt);
+              if (rbase != 0xFFFFFFFFu && rbase + rank < cap)
+                write_record(recs + rbase + rank, bl, tl, ordinal, (uint32_t)op.imm, 0u, 3u, 0u,
+                             2u, cls, 0);
+            }
+          }
+          if (act) ordinal++;
+          pc++;
+          break;
+        }
+        case D_HACC: {  // an access through a heap handle (space 2)
+          const int32_t idx = rf_ld(rf, op.a);
+          const int32_t h = rf_ld(rf, op.b);
+          const uint32_t w = 1u << (op.x & 7u);
+          const int64_t off = (int64_t)idx * (int64_t)w;
+          const uint32_t s = (uint32_t)h - 1u;
+          const int32_t st = s < op.j1 ? rf_ld(rf, ((uint32_t)op.j0 + s) * kRegStride) : 0;
+          uint32_t cls = 0;
+          if (act) {
+            acc.n_acc++;
+            if (do_digest) dh = access_step(dh, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
+            const int64_t len = st, R = (int64_t)T.redzone;
+            if (st == 0)
+              cls = CUFZ_CLS_WILD;
+            else if (st < 0)
+              cls = CUFZ_CLS_USE_AFTER_FREE;
+            else if (off < 0 || off + (int64_t)w > len)
+              cls = (off < 0 && off >= -R)       ? CUFZ_CLS_UNDERFLOW_RZ
+                    : (off >= 0 && off < len + R) ? CUFZ_CLS_OVERFLOW_RZ
+                                                  : CUFZ_CLS_WILD;
+          }
+          const uint32_t vm = __ballot_sync(FULL, cls != 0);
+          if (vm) {
+            const uint32_t rbase = reserve(vm);
+            if (cls) {
+              acc.n_viol++;
+              if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, ordinal);
+              const uint32_t rank = __popc(vm & lanemask_lt);
+              if (rbase != 0xFFFFFFFFu && rbase + rank < cap)
+                write_record(recs + rbase + rank, bl, tl, ordinal, (uint32_t)op.imm,
+                             st == 0 ? 0u : s, (op.x & 8u) ? 1u : 0u, w, 2u, cls, off);
+            }
+          }
+          if (act && (op.x & 16u)) rf_st(rf, op.d, 0);
           if (act) ordinal++;
           pc++;
           break;

@@ -13,13 +13,14 @@ namespace cufz {
 
 enum : uint8_t {
   B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04, B_DIV = 0x05, B_REM = 0x06,
-  B_LD = 0x40, B_ST = 0x41, B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53,
-  B_ENDLOOP = 0x54
+  B_HALLOC = 0x07, B_HFREE = 0x08, B_LD = 0x40, B_ST = 0x41, B_HLD = 0x42, B_HST = 0x43,
+  B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53, B_ENDLOOP = 0x54
 };
 constexpr uint32_t kMagic = 0x315A4643u;
 
 inline bool is_alu_reg(uint8_t o) { return o >= 0x10 && o <= 0x1F; }
 inline bool is_alu_imm(uint8_t o) { return o >= 0x30 && o <= 0x3F; }
+inline bool is_heap_op(uint8_t o) { return o == B_HALLOC || o == B_HFREE || o == B_HLD || o == B_HST; }
 
 // Virtual registers: 0..255 program registers, 256..271 special registers
 // (materialised at thread start), 272.. hidden loop-trip registers.
@@ -31,7 +32,8 @@ struct IrOp {
   int dst = -1, a = -1, b = -1, c = -1;
   int32_t imm = 0;
   int else_pc = -1, end_pc = -1, head_pc = -1;  // structure (head_pc: the IF/LOOP of an ELSE/ENDIF/ENDLOOP)
-  int site = -1;       // branch site (IF/LOOP) or access site (LD/ST)
+  int site = -1;       // branch site (IF/LOOP), access site (LD/ST/HLD/HST),
+                       // division, allocation or free site
   int depth = 0;       // nesting depth of the op itself
   int trip = -1;       // hidden trip vreg (LOOP, ENDLOOP)
   bool kept = true;
@@ -43,6 +45,7 @@ struct IrOp {
 
 struct Ir {
   int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0, n_div = 0;
+  int n_alloc = 0, n_free = 0;  // HALLOC and HFREE sites
   uint32_t shared_mask = 0, seed = 0;
   std::vector<uint16_t> loc0, loc1;
   std::vector<IrOp> ops;

@@ -18,7 +18,7 @@
 #include <string>
 #include <vector>
 
-#include "divide.h"
+#include "checked_ops.h"
 #include "ir.h"
 
 namespace cufz {
@@ -55,7 +55,7 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
   const uint8_t* q = p + 32 + 4 * ir->n_sites;
   ir->ops.resize(n_ops);
   std::vector<int> open;
-  int bsites = 0, asites = 0, dsites = 0, loops = 0;
+  int bsites = 0, asites = 0, dsites = 0, hsites = 0, fsites = 0, loops = 0;
   const int R = ir->n_regs;
   auto reg = [R](int r) { return r < R; };
   for (int pc = 0; pc < n_ops; pc++) {
@@ -100,6 +100,20 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
         case B_REM:
           ok = reg(d) && reg(a) && reg(b) && !imm;
           o.dst = d; o.a = a; o.b = b; o.site = dsites++;
+          break;
+        case B_HALLOC:
+          ok = reg(d) && reg(a) && !b && !imm;
+          o.dst = d; o.a = a; o.site = hsites++;
+          break;
+        case B_HFREE:
+          ok = !d && reg(a) && !b && !imm;
+          o.a = a; o.site = fsites++;
+          break;
+        case B_HLD:
+        case B_HST:  // b: the handle; HST's value register (d) is never a root
+          ok = reg(d) && reg(a) && reg(b) && width_ok(imm);
+          if (opc == B_HLD) o.dst = d;
+          o.a = a; o.b = b; o.width = imm; o.site = asites++;
           break;
         case B_LD:
         case B_ST:
@@ -168,12 +182,15 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
       const IrOp& o = ir->ops[j];
       bool writes = (o.opc == B_SREG || o.opc == B_IMM || o.opc == B_MOV || o.opc == B_SEL ||
                      o.opc == B_LD || o.opc == B_LOOP || o.opc == B_DIV || o.opc == B_REM ||
-                     is_alu_reg(o.opc) || is_alu_imm(o.opc));
+                     o.opc == B_HALLOC || o.opc == B_HLD || is_alu_reg(o.opc) ||
+                     is_alu_imm(o.opc));
       if (writes && o.dst == h.dst) return false;
     }
   }
   ir->n_access = asites;
   ir->n_div = dsites;
+  ir->n_alloc = hsites;
+  ir->n_free = fsites;
   ir->n_loops = loops;
   ir->nv = kTripBase + loops;
   return true;
@@ -222,6 +239,13 @@ void uses_defs(const IrOp& o, bool device_ir, int* U, int* nu, int* D, int* nd) 
       if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
       break;
     case B_ST: U[(*nu)++] = o.a; break;
+    case B_HALLOC: U[(*nu)++] = o.a; D[(*nd)++] = o.dst; break;
+    case B_HFREE: U[(*nu)++] = o.a; break;
+    case B_HLD:  // the handle and the index decide the check; the value reads 0
+      U[(*nu)++] = o.a; U[(*nu)++] = o.b;
+      if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
+      break;
+    case B_HST: U[(*nu)++] = o.a; U[(*nu)++] = o.b; break;
     case B_DIV:
     case B_REM:  // a check: the divisor always, the dividend while the result is live
       U[(*nu)++] = o.b;
@@ -320,7 +344,7 @@ void prune(Ir* ir) {
     if (!changed) {
       for (size_t pc = 0; pc < ir->ops.size(); pc++) {
         IrOp& o = ir->ops[pc];
-        if (o.opc == B_LD) o.value_dead = !L.out[pc].get(o.dst);
+        if (o.opc == B_LD || o.opc == B_HLD) o.value_dead = !L.out[pc].get(o.dst);
       }
       return;
     }
@@ -509,7 +533,7 @@ struct Gen {
 
   bool counted(const IrOp& o2) const {
     return o2.kept && ((o2.opc != B_SREG && is_value_op(o2.opc)) || o2.opc == B_DIV ||
-                       o2.opc == B_REM);
+                       o2.opc == B_REM || o2.opc == B_HALLOC || o2.opc == B_HFREE);
   }
 
   // whether ops [pc, end) hold a kept IF or LOOP (a branch site)
@@ -536,7 +560,7 @@ struct Gen {
     while (pc < end) {
       const IrOp& o2 = ir.ops[pc];
       if (o2.opc == B_IF || o2.opc == B_LOOP) break;
-      if (o2.kept && (o2.opc == B_LD || o2.opc == B_ST)) k++;
+      if (o2.kept && (o2.opc == B_LD || o2.opc == B_ST || o2.opc == B_HLD || o2.opc == B_HST)) k++;
       pc++;
     }
     return k;
@@ -640,6 +664,74 @@ struct Gen {
     line(ind, "}");
   }
 
+  // The device heap: hp[s] is allocation site s's block (0 never
+  // allocated, its size while live, -1 once freed), reset per test thread.
+  // A fault's record is written by the program's heap-fault helper in the
+  // record function.
+  void heap_fault(int ind, const std::string& site, const std::string& buf,
+                  const std::string& kind, const std::string& w, const std::string& cls,
+                  const std::string& off) {
+    line(ind, "if (fo == ~0u) fo = ordinal;");
+    line(ind, "if (write) write = !cufz_prog_" + std::to_string(index) + "_heap_fault(bl, tl, ordinal, " +
+                  site + ", " + buf + ", " + kind + ", " + w + ", " + cls + ", " + off + ");");
+  }
+  void heap(int ind, const IrOp& o2) {
+    // with no HALLOC every handle is one of no block
+    const std::string st_expr =
+        ir.n_alloc ? "hs < " + std::to_string(ir.n_alloc) + "u ? hp[hs] : 0" : std::string("0");
+    line(ind, "{");
+    if (o2.opc == B_HALLOC) {
+      line(ind + 1, "const int32_t hn = " + r(o2.a) + ";");
+      line(ind + 1, "if (hn >= 1) hp[" + std::to_string(o2.site) + "] = hn;");
+      line(ind + 1, r(o2.dst) + " = hn >= 1 ? " + std::to_string(o2.site + 1) + " : 0;");
+    } else if (o2.opc == B_HFREE) {
+      line(ind + 1, "const int32_t hh = " + r(o2.a) + ";");
+      line(ind + 1, "const uint32_t hs = (uint32_t)hh - 1u;");
+      line(ind + 1, "const int32_t st = " + st_expr + ";");
+      line(ind + 1, "if (hh != 0 && st > 0) hp[hs] = -1;");
+      if (rec_) {
+        line(ind + 1, "if (hh != 0 && st <= 0) {");
+        heap_fault(ind + 2, std::to_string(o2.site) + "u", "0u", "3u", "0u",
+                   "st == 0 ? " + std::to_string(CUFZ_CLS_INVALID_FREE) + "u : " +
+                       std::to_string(CUFZ_CLS_DOUBLE_FREE) + "u",
+                   "0");
+        line(ind + 1, "}");
+        line(ind + 1, "ordinal++;");
+      } else {
+        line(ind + 1, "nv += (hh != 0 && st <= 0) ? 1u : 0u;");
+      }
+    } else {
+      const int w = o2.width;
+      line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
+      line(ind + 1, "const uint32_t hs = (uint32_t)" + r(o2.b) + " - 1u;");
+      line(ind + 1, "const int32_t st = " + st_expr + ";");
+      line(ind + 1, "(void)hs;");
+      line(ind + 1, "const int64_t off = (int64_t)ix * " + std::to_string(w) + ";");
+      line(ind + 1, "const bool viol = st <= 0 || off < 0 || off + " + std::to_string(w) +
+                        " > (int64_t)st;");
+      if (rec_) {
+        line(ind + 1, "if (viol) {");
+        line(ind + 2, "const int64_t R = (int64_t)s_T.redzone;");
+        line(ind + 2, "const uint32_t cls = st == 0 ? " + std::to_string(CUFZ_CLS_WILD) +
+                          "u : st < 0 ? " + std::to_string(CUFZ_CLS_USE_AFTER_FREE) +
+                          "u : (off < 0 && off >= -R) ? " + std::to_string(CUFZ_CLS_UNDERFLOW_RZ) +
+                          "u : (off >= 0 && off < (int64_t)st + R) ? " +
+                          std::to_string(CUFZ_CLS_OVERFLOW_RZ) + "u : " +
+                          std::to_string(CUFZ_CLS_WILD) + "u;");
+        heap_fault(ind + 2, std::to_string(o2.site) + "u", "st == 0 ? 0u : hs",
+                   o2.opc == B_HST ? "1u" : "0u", std::to_string(w) + "u", "cls", "off");
+        line(ind + 1, "}");
+        line(ind + 1, "ordinal++;");
+      } else {
+        line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) +
+                          ", ix);");
+        line(ind + 1, "nv += viol ? 1u : 0u;");
+      }
+      if (o2.opc == B_HLD && !o2.value_dead) line(ind + 1, r(o2.dst) + " = 0;");
+    }
+    line(ind, "}");
+  }
+
   void range(int ind, int pc, int end) {
     run_counts(ind, pc, end);
     while (pc < end) {
@@ -665,6 +757,8 @@ struct Gen {
         access(ind, o2);
       } else if (opc == B_DIV || opc == B_REM) {
         divide(ind, o2);
+      } else if (is_heap_op(opc)) {
+        heap(ind, o2);
       } else if (opc == B_IF) {
         std::string c = "c" + std::to_string(o2.site);
         line(ind, "{");
@@ -824,6 +918,33 @@ struct Gen {
       line(0, "}");
     }
 
+    // heap faults: records of space 2 (kind 3 for a bad free), written
+    // like access records
+    bool heap_ops = false;
+    for (const auto& op : ir.ops) heap_ops |= op.kept && is_heap_op(op.opc);
+    const std::string heap_decl =
+        "int32_t hp[" + std::to_string(std::max(ir.n_alloc, 1)) + "] = {};";
+    if (heap_ops) {
+      line(0, "__device__ __noinline__ bool " + fn +
+                  "_heap_fault(uint32_t bl, uint32_t tl, uint32_t ordinal, uint32_t site, "
+                  "uint32_t buf, uint32_t kind, uint32_t w, uint32_t cls, int64_t off) {");
+      line(1, "const uint32_t am = __activemask();");
+      line(1, "const uint32_t lane = threadIdx.x & 31u;");
+      line(1, "const uint32_t leader = __ffs(am) - 1;");
+      line(1, "const uint32_t k = __popc(am);");
+      line(1, "const uint32_t cap = s_T.record_cap;");
+      line(1, "const uint32_t slot = s_in.slot;");
+      line(1, "uint32_t base = 0;");
+      line(1, "if (lane == leader) base = atomicAdd(&s_T.slots[slot].rec_reserved, k);");
+      line(1, "base = __shfl_sync(am, base, leader);");
+      line(1, "const uint32_t rank = __popc(am & ((1u << lane) - 1u));");
+      line(1, "if (base + rank < cap)");
+      line(2, "write_record(s_T.records + (size_t)slot * cap + base + rank, bl, tl, ordinal, site, "
+              "buf, kind, w, 2u, cls, off);");
+      line(1, "return base + k >= cap;");
+      line(0, "}");
+    }
+
     // record function: one test thread, records and the first violation
     rec_ = true;
     has_loop = false;
@@ -836,6 +957,7 @@ struct Gen {
     line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
     line(1, "(void)back;");
     reg_decls(1, used);
+    if (heap_ops) line(1, heap_decl);
     range(1, 0, (int)ir.ops.size());
     if (has_loop) line(0, "cufz_done:");
     line(1, "return fo;");
@@ -870,6 +992,7 @@ struct Gen {
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
     reg_decls(2, used);
+    if (heap_ops) line(2, heap_decl);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
     line(2, "if (dig) acc.digest += dh;");
@@ -932,7 +1055,8 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
   } else {
     Liveness L = liveness(ir, false);
     for (size_t pc = 0; pc < ir.ops.size(); pc++)
-      if (ir.ops[pc].opc == B_LD) ir.ops[pc].value_dead = !L.out[pc].get(ir.ops[pc].dst);
+      if (ir.ops[pc].opc == B_LD || ir.ops[pc].opc == B_HLD)
+        ir.ops[pc].value_dead = !L.out[pc].get(ir.ops[pc].dst);
   }
   out->clear();
   Gen g{ir, *out, (int)index};
@@ -1002,7 +1126,9 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
   std::vector<int> map;
   Bits entry;
   int n_regs = allocate(ir, true, &map, &entry);
-  if (n_regs > kMaxPhysRegs) return CUFZ_E_INVALID_PROGRAM;
+  // the heap state: one register per allocation site after the program's
+  const int heap_base = n_regs, n_heap = ir.n_alloc;
+  if (n_regs + n_heap > kMaxPhysRegs) return CUFZ_E_INVALID_PROGRAM;
 
   // device ops
   int N = (int)ir.ops.size();
@@ -1058,6 +1184,22 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
           }
           d.imm = o.site;
           break;
+        case B_HALLOC:
+        case B_HFREE:
+        case B_HLD:
+        case B_HST:
+          d.opc = opc == B_HALLOC ? D_HALLOC : opc == B_HFREE ? D_HFREE : D_HACC;
+          if (opc == B_HALLOC || (opc == B_HLD && !o.value_dead)) d.d = off(o.dst);
+          d.a = off(o.a);
+          if (d.opc == D_HACC) {
+            d.b = off(o.b);
+            d.x = (uint8_t)(log2w(o.width) | (opc == B_HST ? 8u : 0u) |
+                            (opc == B_HLD && !o.value_dead ? 16u : 0u));
+          }
+          d.imm = o.site;
+          d.j0 = (uint16_t)heap_base;
+          d.j1 = (uint16_t)n_heap;
+          break;
         case B_LD:
         case B_ST:
           d.opc = opc == B_ST ? D_ST : (o.value_dead ? D_LDX : D_LD);
@@ -1101,11 +1243,12 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
     if (entry.get(v) && map[v] >= 0) zero.push_back((uint16_t)(map[v] * kRegStride));
   for (int v = kTripBase; v < ir.nv; v++)
     if (entry.get(v) && map[v] >= 0) zero.push_back((uint16_t)(map[v] * kRegStride));
+  for (int s = 0; s < n_heap; s++) zero.push_back((uint16_t)((heap_base + s) * kRegStride));
   std::sort(zero.begin(), zero.end());
   zero.erase(std::unique(zero.begin(), zero.end()), zero.end());
 
   hdr.n_ops = (uint32_t)dops.size();
-  hdr.n_regs = (uint32_t)std::max(n_regs, 1);
+  hdr.n_regs = (uint32_t)std::max(n_regs + n_heap, 1);
   hdr.n_bufs = (uint32_t)ir.n_bufs;
   hdr.shared_mask = ir.shared_mask;
   hdr.seed = ir.seed;
@@ -1214,6 +1357,10 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
         case B_REM: d = R(o.dst); a = o.value_dead ? 0 : R(o.a); b = R(o.b); break;
         case B_LD: d = R(o.dst); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
         case B_ST: d = R(o.a); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
+        case B_HALLOC: d = R(o.dst); a = R(o.a); break;
+        case B_HFREE: a = R(o.a); break;
+        case B_HLD: d = R(o.dst); a = R(o.a); b = R(o.b); imm = o.width; break;
+        case B_HST: d = R(o.a); a = R(o.a); b = R(o.b); imm = o.width; break;
         case B_IF: a = R(o.a); break;
         case B_LOOP: d = R(o.dst); a = R(o.a); imm = o.imm; break;
         default: break;

@@ -232,7 +232,11 @@ struct PrexRun {
           break;
         }
         case B_DIV:
-        case B_REM: return false;  // a division: not in either analysis
+        case B_REM:
+        case B_HALLOC:
+        case B_HFREE:
+        case B_HLD:
+        case B_HST: return false;  // a division or a heap op: not in either analysis
         default: pc++; break;
       }
     }
@@ -675,7 +679,11 @@ struct PrexGrid {
           break;
         }
         case B_DIV:
-        case B_REM: return false;  // a division: not in either analysis
+        case B_REM:
+        case B_HALLOC:
+        case B_HFREE:
+        case B_HLD:
+        case B_HST: return false;  // a division or a heap op: not in either analysis
         default: pc++; break;
       }
     }

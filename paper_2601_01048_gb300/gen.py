@@ -426,6 +426,95 @@ def div_inputs(n: int, n_programs: int = 16, seed: int | None = None,
 
 
 # --------------------------------------------------------------------------
+# heap workload: per-thread device-heap blocks, accessed, freed and misused
+# (the temporal errors of Sec. 2.3: use after free, double free, invalid free)
+# --------------------------------------------------------------------------
+
+def heap_program(index: int) -> bytes:
+    """Random programs over the device heap.  Sizes come from arguments,
+    coordinates and constants (some <= 0: a NULL handle); handles are the
+    allocations' results or fabricated (small constants, coordinates);
+    blocks are loaded and stored at indices that may leave them, freed once,
+    twice or never, used after free, under guards and in a uniform loop."""
+    rng = SplitMix64(sub_seed("heapprog", index))
+    A = Asm(n_bufs=1, seed=rng.next32())
+    tx, bx = A.sreg(bc.TID_X), A.sreg(bc.CTAID_X)
+    args = [A.sreg(bc.ARG0 + k) for k in range(4)]
+    lin = A.alu(bc.ADD, A.alu(bc.MUL, bx, A.sreg(bc.NTID_X)), tx)
+    handles = []
+
+    def size():
+        r = rng.below(4)
+        if r == 0:
+            return rng.choice(args)
+        if r == 1:
+            return A.alu(bc.ADD, tx, Imm(rng.randint(-2, 8)))
+        if r == 2:
+            return A.imm(rng.choice((1, 4, 16, 64, 0, -3)))
+        return A.alu(bc.SUB, A.alu(bc.AND, rng.choice(args), Imm(63)), A.alu(bc.AND, lin, Imm(7)))
+
+    def handle():
+        if handles and rng.below(5):
+            return rng.choice(handles)
+        return A.imm(rng.randint(-1, 4)) if rng.below(2) else A.alu(bc.AND, lin, Imm(3))
+
+    def index():
+        r = rng.below(4)
+        if r == 0:
+            return tx
+        if r == 1:
+            return A.alu(bc.SUB, lin, rng.choice(args))
+        if r == 2:
+            return A.alu(bc.AND, rng.choice(args), Imm(31))
+        return A.alu(bc.SUB, A.alu(bc.MUL, tx, Imm(4)), Imm(2))
+
+    def body(depth):
+        for _ in range(rng.randint(3, 7)):
+            r = rng.below(8)
+            if r <= 1 or not handles:
+                handles.append(A.halloc(size()))
+            elif r == 2:
+                A.hld(handle(), index(), rng.choice((1, 4, 8)))
+            elif r == 3:
+                A.hst(handle(), index(), tx, rng.choice((1, 4)))
+            elif r == 4:
+                A.hfree(handle())
+            elif r == 5 and depth < 2:
+                A.if_(A.alu(bc.SETLT, tx, args[3]))
+                body(depth + 1)
+                A.endif()
+            elif r == 6 and depth < 2:
+                k = A.loop(A.alu(bc.AND, args[2], Imm(3)), 4)
+                h = A.halloc(A.alu(bc.ADD, k, Imm(rng.randint(0, 4))))
+                A.hst(h, A.alu(bc.SUB, k, Imm(1)), k, 1)
+                if rng.below(2):
+                    A.hfree(h)
+                A.endloop()
+            else:
+                A.ld(0, index(), 4)
+
+    body(0)
+    return A.build()
+
+
+def heap_programs(n: int = 16) -> list[bytes]:
+    return [heap_program(i) for i in range(n)]
+
+
+def heap_inputs(n: int, n_programs: int = 16, seed: int | None = None,
+                max_blocks: int = 4) -> np.ndarray:
+    """Blocks of 16 x 2 threads, 1D grids up to max_blocks; arguments from
+    {0, +-1, 2, 3, 5, 8, 16, 40, -7}; buffer 0 up to 256 bytes."""
+    rng = SplitMix64(sub_seed("heap") if seed is None else seed)
+    out = make_inputs(n)
+    for k in range(n):
+        args = [rng.choice((0, 1, -1, 2, 3, 5, 8, 16, 40, -7)) for _ in range(4)]
+        set_input(out[k], k % n_programs, (rng.randint(1, max_blocks), 1, 1), (16, 2, 1), args,
+                  [rng.randint(0, 256)], tag=k)
+    return out
+
+
+# --------------------------------------------------------------------------
 # config 2: random 2D programs with shared buffers and loops
 # --------------------------------------------------------------------------
 

@@ -42,7 +42,7 @@ def parse(prog: bytes):
     assert magic == 0x315A4643 and ver == 1
     loc = [struct.unpack_from("<HH", prog, 32 + 4 * s) for s in range(n_sites)]
     raw = [struct.unpack_from("<BBBBi", prog, 32 + 4 * n_sites + 8 * i) for i in range(n_ops)]
-    counters = {"b": 0, "a": 0, "d": 0}
+    counters = {"b": 0, "a": 0, "d": 0, "h": 0, "f": 0}
     pos = [0]
 
     def block(terminators):
@@ -74,12 +74,22 @@ def parse(prog: bytes):
             elif opc in (0x05, 0x06):
                 out.append(("div", opc == 0x06, d, a, b, counters["d"]))
                 counters["d"] += 1
+            elif opc == 0x07:
+                out.append(("halloc", d, a, counters["h"]))
+                counters["h"] += 1
+            elif opc == 0x08:
+                out.append(("hfree", a, counters["f"]))
+                counters["f"] += 1
+            elif opc in (0x42, 0x43):
+                out.append(("hmem", opc == 0x43, d, a, b, imm, counters["a"]))
+                counters["a"] += 1
             else:
                 out.append(("op", opc, d, a, b, imm))
         return out, None
 
     body, _ = block(())
-    return dict(n_regs=n_regs, n_bufs=n_bufs, shmask=shmask, seed=seed, loc=loc, body=body)
+    return dict(n_regs=n_regs, n_bufs=n_bufs, shmask=shmask, seed=seed, loc=loc, body=body,
+                n_alloc=counters["h"])
 
 
 def alu(opc, x, y):
@@ -168,6 +178,43 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
             t["ordinal"] += 1
             regs[d] = val
 
+        heap = {}  # allocation site -> [size, live]
+
+        def block_of(h):
+            return heap.get(h - 1) if 1 <= h <= P["n_alloc"] else None
+
+        def hfree(a, site):
+            h = regs[a]
+            if h != 0:
+                blk = block_of(h)
+                if blk is None:
+                    st["records"].append((bl, tl, t["ordinal"], site, 0, 3, 0, 2, 8, 0))
+                elif not blk[1]:
+                    st["records"].append((bl, tl, t["ordinal"], site, 0, 3, 0, 2, 7, 0))
+                else:
+                    blk[1] = False
+            t["ordinal"] += 1
+
+        def hmem(is_st, d, a, hreg, w, site):
+            off = regs[a] * w
+            k = ((site * 0xC2B2AE3D) & M32) | 1
+            t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
+            st["n_accesses"] += 1
+            h, blk, cls = regs[hreg], None, 0
+            blk = block_of(h)
+            if blk is None:
+                cls = 4
+            elif not blk[1]:
+                cls = 6
+            elif off < 0 or off + w > blk[0]:
+                cls = 1 if -redzone <= off < 0 else 2 if 0 <= off < blk[0] + redzone else 4
+            if cls:
+                st["records"].append((bl, tl, t["ordinal"], site, h - 1 if blk is not None else 0,
+                                      int(is_st), w, 2, cls, off))
+            t["ordinal"] += 1
+            if not is_st:
+                regs[d] = 0
+
         def run(stmts):
             for s in stmts:
                 if t["stop"]:
@@ -193,6 +240,18 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 elif kind == "div":
                     _, is_rem, d, a, bb, site = s
                     divide(is_rem, d, a, bb, site)
+                elif kind == "halloc":
+                    _, d, a, site = s
+                    if regs[a] >= 1:
+                        heap[site] = [regs[a], True]
+                        regs[d] = site + 1
+                    else:
+                        regs[d] = 0
+                elif kind == "hfree":
+                    hfree(s[1], s[2])
+                elif kind == "hmem":
+                    _, is_st, d, a, hreg, w, site = s
+                    hmem(is_st, d, a, hreg, w, site)
                 elif kind == "if":
                     _, a, site, then, els = s
                     taken = regs[a] != 0

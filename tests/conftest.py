@@ -16,10 +16,11 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    """The division-fault tests, then the full-size workload tests, run
-    last: the first are the newest device code, the second take the longest,
-    and the established parity tests should report first."""
-    items.sort(key=lambda item: ("test_gpu_divfault" in item.nodeid) + 2 * ("test_gpu_fullsize" in item.nodeid))
+    """The division-fault and heap-fault tests, then the full-size workload
+    tests, run last: the first two are the newest device code, the last take
+    the longest, and the established parity tests should report first."""
+    items.sort(key=lambda item: ("test_gpu_divfault" in item.nodeid)
+               + 2 * ("test_gpu_heap" in item.nodeid) + 3 * ("test_gpu_fullsize" in item.nodeid))
 
 
 def golden(name):

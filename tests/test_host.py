@@ -173,14 +173,15 @@ def test_engine_needs_a_gpu():
         B.Engine()
 
 
-@pytest.mark.parametrize("which", ["listings", "c3", "c2", "c4"])
+@pytest.mark.parametrize("which", ["listings", "c3", "c2", "c4", "div", "heap"])
 def test_generated_code_compiles_for_sm103a(which):
     """The compiled path: every workload program's generated CUDA compiles
     for sm_103a with the runtime compiler (no device needed)."""
     progs = {"listings": [gen.c1_program(), gen.vecadd_shared_program(64),
                           gen.guarded_plus1_program(128)],
              "c3": gen.c3_programs(), "c2": gen.c2_programs()[:8],
-             "c4": gen.c4_programs()[:3]}[which]
+             "c4": gen.c4_programs()[:3], "div": gen.div_programs()[:8],
+             "heap": gen.heap_programs()}[which]
     st, log, nbytes = B.cufz_compile_check(progs)
     assert st == 0, log[-4000:]
     assert nbytes > 0
@@ -251,6 +252,52 @@ def test_prune_keeps_every_division(orc, which):
         assert np.array_equal(b0, b1)
 
 
+@pytest.mark.parametrize("which", range(16))
+def test_prune_keeps_every_heap_op(orc, which):
+    """Heap operations are checks with state: pruning keeps every HALLOC,
+    HFREE, HLD and HST and the values of their sizes, handles and indices,
+    so the oracle gives the same records (use after free, double and invalid
+    free, heap bounds), ordinals, digest, counts and bitmap on the pruned
+    program."""
+    prog = gen.heap_program(which)
+    pruned, st = B.cufz_prune_program(prog)
+    assert orc.validate(pruned) == 0 and B.cufz_validate_program(pruned) == 0
+    kinds = (bc.LD, bc.ST, bc.IF, bc.ELSE, bc.ENDIF, bc.LOOP, bc.ENDLOOP, bc.HALLOC, bc.HFREE,
+             bc.HLD, bc.HST)
+    assert [o[0] for o in bc.ops_of(prog) if o[0] in kinds] == \
+        [o[0] for o in bc.ops_of(pruned) if o[0] in kinds]
+    ins = gen.heap_inputs(4, n_programs=1, seed=420 + which)
+    for o in (orc.opts(), orc.opts(iter_budget=2)):
+        r0, c0, b0 = orc.run_batch([prog], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+        r1, c1, b1 = orc.run_batch([pruned], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+        assert r0.tobytes() == r1.tobytes() and c0.tobytes() == c1.tobytes()
+        assert np.array_equal(b0, b1)
+
+
+def test_prune_drops_the_value_of_a_heap_load_and_a_stored_value(orc):
+    """A heap load whose value nothing reads and a heap store's value are
+    not roots: the arithmetic that only they use goes, the accesses (index
+    and handle) stay."""
+    A = Asm(n_bufs=1)
+    t, a0 = A.sreg(bc.TID_X), A.sreg(bc.ARG0)
+    h = A.halloc(A.imm(16))
+    v = A.hld(h, t, 4)
+    A.hst(h, A.alu(bc.SUB, t, Imm(1)), A.alu(bc.MUL, A.alu(bc.ADD, v, a0), a0), 4)
+    A.hfree(h)
+    A.hfree(h)
+    prog = A.build()
+    pruned, st = B.cufz_prune_program(prog)
+    assert st.n_ops_kept == st.n_ops_in - 3                    # add, mul and the read of a0
+    inp = gen.make_inputs(1)
+    gen.set_input(inp[0], 0, (2, 1, 1), (8, 1, 1), (3, 5), (16,))
+    r0, c0, _ = orc.run(orc.Program(prog), inp[0], rec_cap=64)
+    r1, c1, _ = orc.run(orc.Program(pruned), inp[0], rec_cap=64)
+    assert r0.tobytes() == r1.tobytes() and c0.tobytes() == c1.tobytes()
+    # per block: loads at t >= 4, stores at t - 1 outside [0, 4), and every
+    # thread's second free
+    assert int(r0["n_violations"]) == 2 * (4 + 4 + 8)
+
+
 def test_prune_drops_the_dividend_of_a_dead_quotient(orc):
     """q = (t * t * a0) / (t - a1) with q unused: the division stays (its
     divisor decides the fault); the dividend's two multiplications and the
@@ -278,5 +325,16 @@ def test_validator_agrees_with_oracle_on_division_programs(orc, seed):
     for _ in range(rng.randint(1, 3)):
         pos = rng.randint(32, len(prog) - 1)
         prog[pos] = rng.choice((0x05, 0x06, rng.below(256)))
+    p = bytes(prog)
+    assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_validator_agrees_with_oracle_on_heap_programs(orc, seed):
+    rng = gen.SplitMix64(seed + 700)
+    prog = bytearray(gen.heap_program(seed % 16))
+    for _ in range(rng.randint(1, 3)):
+        pos = rng.randint(32, len(prog) - 1)
+        prog[pos] = rng.choice((0x07, 0x08, 0x42, 0x43, rng.below(256)))
     p = bytes(prog)
     assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)

@@ -159,3 +159,20 @@ def test_interpreter_division_programs(tmp_path, interp_exe, orc, flags):
         ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
         compare(got, ores, orecs, obms, cap)
         assert sum(int((r["kind"] == 2).sum()) for _, r, _ in got) > 0
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_interpreter_heap_programs(tmp_path, interp_exe, orc, flags):
+    """Programs on the device heap: the per-site state registers after the
+    program's own, cleared per test thread; fault records of space 2 (kind 3
+    for a bad free) from lanes of one warp reserved together; ordinals that
+    count frees and heap accesses; pruned and unpruned, with a small record
+    cap as well."""
+    progs = gen.heap_programs()
+    ins = gen.heap_inputs(48, seed=315)
+    for cap in (1 << 14, 8):
+        got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
+        ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
+        compare(got, ores, orecs, obms, cap)
+        if cap > 8:
+            assert sum(int((r["kind"] == 3).sum()) for _, r, _ in got) > 0

@@ -261,3 +261,33 @@ def test_division_programs_match_oracle(tmp_path, host_objs, orc, flags):
             assert np.array_equal(bm, obms[i]), (budget, i)
             faults += int((recs["kind"] == 2).sum())
         assert faults > 0
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_heap_programs_match_oracle(tmp_path, host_objs, orc, flags):
+    """Programs on the device heap (blocks sized by arguments, coordinates
+    and loaded bytes; frees under branches and in loops; accesses through
+    live, freed, NULL and forged handles): every class of heap fault (use
+    after free, double and invalid free, redzone and wild heap accesses) in
+    its record, ordinals that count frees and heap accesses, digests, and
+    every other result equal the oracle's, pruned and unpruned, and under a
+    budget that stops threads early."""
+    progs = gen.heap_programs()
+    ins = gen.heap_inputs(48, seed=314)
+    exe = build(tmp_path, host_objs, progs, flags)
+    for budget in (4096, 2):
+        got = run(tmp_path, exe, progs, ins, budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
+                                          rec_cap=1 << 14, bitmaps=True)
+        seen = set()
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records"):
+                assert int(res[f]) == int(o[f]), (budget, i, f)
+            assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
+            assert np.array_equal(bm, obms[i]), (budget, i)
+            seen |= {(int(r["kind"]), int(r["cls"])) for r in recs if int(r["space"]) == 2}
+        if budget == 4096:
+            assert {(0, 6), (1, 6), (3, 7), (3, 8), (0, 4), (1, 2)} <= seen, seen

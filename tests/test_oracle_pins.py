@@ -595,3 +595,45 @@ def test_bruteforce_division_programs(orc, index):
     res, recs, _ = orc.run(orc.Program(prog), gen.div_inputs(1, n_programs=1, seed=9)[0],
                            rec_cap=1 << 12)
     assert int(res["n_accesses"]) > 0
+
+
+def test_heap_faults_by_class(orc):
+    """One block of a0 = 16 bytes per thread: a 4-byte store at tid * 4
+    overflows for tid >= 4; after the free, a load is a use after free and a
+    second free a double free; freeing handle 3 (no such block) is an
+    invalid free and freeing 0 nothing; a zero-size allocation gives the
+    NULL handle, through which a load is wild.  Ordinals count every heap
+    access and free (NULL included) but no allocation."""
+    A = Asm(n_bufs=0)
+    tx, a0, a1 = A.sreg(bc.TID_X), A.sreg(bc.ARG0), A.sreg(bc.ARG1)
+    h = A.halloc(a0)
+    A.hst(h, tx, tx, 4)                    # ordinal 0
+    A.hfree(h)                             # 1
+    A.hld(h, A.imm(0), 4)                  # 2: use after free
+    A.hfree(h)                             # 3: double free
+    A.hfree(A.imm(3))                      # 4: invalid free
+    A.hfree(A.imm(0))                      # 5: free(NULL)
+    A.hld(A.halloc(a1), A.imm(0), 1)       # 6: NULL handle, wild
+    res, recs, _ = orc.run(orc.Program(A.build()), mk((1, 1, 1), (8, 1, 1), (16, 0), ()),
+                           rec_cap=256)
+    got = sorted((int(r["thread_lin"]), int(r["ordinal"]), int(r["kind"]), int(r["cls"]),
+                  int(r["space"]), int(r["byte_off"])) for r in recs)
+    want = sorted([(t, 0, 1, 2, 2, 4 * t) for t in range(4, 8)] +
+                  [(t, 2, 0, 6, 2, 0) for t in range(8)] + [(t, 3, 3, 7, 2, 0) for t in range(8)] +
+                  [(t, 4, 3, 8, 2, 0) for t in range(8)] + [(t, 6, 0, 4, 2, 0) for t in range(8)])
+    assert got == want
+    assert int(res["n_accesses"]) == 3 * 8 and int(res["n_violations"]) == len(want)
+    assert int(res["first_key"]) == 2                      # thread 0's use after free
+
+
+@pytest.mark.parametrize("index", range(8))
+def test_bruteforce_heap_programs(orc, index):
+    """Random heap programs (allocation sizes from arguments and
+    coordinates, fabricated handles, frees under guards and in a loop): the
+    oracle equals the independent evaluator exactly."""
+    prog = gen.heap_program(index)
+    for x in gen.heap_inputs(3, n_programs=1, seed=4000 + index, max_blocks=2):
+        _compare_bruteforce(orc, prog, dict(grid=tuple(int(v) for v in x["grid"]),
+                                            block=tuple(int(v) for v in x["block"]),
+                                            args=[int(v) for v in x["args"]],
+                                            lens=[int(v) for v in x["buf_len"][:1]]))

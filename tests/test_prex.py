@@ -563,3 +563,23 @@ def test_no_plan_for_programs_that_divide():
     A.ld(0, i, 4)
     inp = mk((4, 1, 1), (32, 1, 1), (1, 7), (400,))
     assert not B.cufz_prex_check(A.build(), inp) and B.cufz_prex_plan(A.build(), inp) is None
+
+
+@pytest.mark.parametrize("op", ["halloc", "hfree", "hld", "hst"])
+def test_no_plan_for_programs_on_the_heap(op):
+    """Heap operations keep per-thread state (blocks live or freed) that
+    neither analysis models: an otherwise affine program with any heap
+    operation gets no plan."""
+    A = Asm(n_bufs=1)
+    i = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), A.sreg(bc.NTID_X)), A.sreg(bc.TID_X))
+    if op == "halloc":
+        A.halloc(A.sreg(bc.ARG0))
+    elif op == "hfree":
+        A.hfree(A.sreg(bc.ARG0))
+    elif op == "hld":
+        A.hld(A.sreg(bc.ARG0), i, 4)
+    else:
+        A.hst(A.sreg(bc.ARG0), i, i, 4)
+    A.ld(0, i, 4)
+    inp = mk((4, 1, 1), (32, 1, 1), (1, 7), (400,))
+    assert not B.cufz_prex_check(A.build(), inp) and B.cufz_prex_plan(A.build(), inp) is None
