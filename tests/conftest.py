@@ -16,11 +16,12 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    """The division-fault and heap-fault tests, then the full-size workload
-    tests, run last: the first two are the newest device code, the last take
-    the longest, and the established parity tests should report first."""
-    items.sort(key=lambda item: ("test_gpu_divfault" in item.nodeid)
-               + 2 * ("test_gpu_heap" in item.nodeid) + 3 * ("test_gpu_fullsize" in item.nodeid))
+    """The PREX, division-fault and heap-fault tests, then the full-size
+    workload tests, run last: the first three cover the newest device and
+    runtime code, the last take the longest, and the established parity
+    tests should report first."""
+    late = ("test_gpu_prex", "test_gpu_divfault", "test_gpu_heap", "test_gpu_fullsize")
+    items.sort(key=lambda item: next((k + 1 for k, f in enumerate(late) if f in item.nodeid), 0))
 
 
 def golden(name):
