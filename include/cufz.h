@@ -31,8 +31,9 @@
  * it):
  *   header, 32 bytes: u32 magic 0x315A4643 ("CFZ1"), u16 version 1, u16
  *     n_ops (1..2048), u8 n_regs, u8 n_bufs (<= 9), u8 n_sites (IF and LOOP
- *     ops), u8 0, u16 shared_mask (bit k: buffer k is per-block shared
- *     memory), u16 0, u32 seed (content of the global buffers), u32 0 x 3;
+ *     ops), u8 flags (bit 0: stores to shared buffers are performed, see
+ *     BAR), u16 shared_mask (bit k: buffer k is per-block shared memory),
+ *     u16 0, u32 seed (content of the global buffers), u32 0 x 3;
  *   LOC table: n_sites x {u16 LOC not taken / exit, u16 LOC taken};
  *   ops, 8 bytes each: u8 opcode, u8 dst, u8 a, u8 b, i32 imm (unused
  *     fields 0).  The size is exactly 32 + 4 n_sites + 8 n_ops.
@@ -60,7 +61,20 @@
  * buffer b at index a, width imm (1, 4, 8 or 16 bytes); 0x41 ST register
  * dst to buffer b at index a, width imm (checked, never performed); 0x50 IF
  * a, 0x51 ELSE, 0x52 ENDIF; 0x53 LOOP with counter dst and trip count
- * clamp(a, 0, imm), 0x54 ENDLOOP.
+ * clamp(a, 0, imm), 0x54 ENDLOOP; 0x55 BAR, a block-wide barrier outside
+ * every IF and LOOP.  With flags bit 0 each block's shared buffers start
+ * as zero bytes, an in-bounds ST to one writes the value's little-endian
+ * bytes (width 1: the low byte; widths 8 and 16: the four bytes, then
+ * zeros) and an in-bounds LD reads them back (width 1: the byte; wider: the
+ * int32 of the first four bytes); the BARs split the program into phases
+ * that every thread of a block finishes, in thread order, before the next
+ * phase.  The engine runs such a program only when BarrierElimination
+ * (Sec. 5.2, Alg. 2) applies: no value loaded from a shared buffer reaches
+ * an index, a branch, a loop trip, a divisor or a heap operand.  The
+ * stores then change no check, and it runs the program without them and
+ * without its barriers; any other such program loads as
+ * CUFZ_E_UNSUPPORTED.  Without the flag, stores are never performed,
+ * shared loads read 0 and BAR does nothing.
  * Control flow is structured, at most 16 deep; a loop counter is read-only
  * in its body.  The k-th LD/ST/HLD/HST in program order is access site k,
  * the k-th IF/LOOP branch site k, the k-th DIV/REM division site k, the
@@ -97,6 +111,10 @@ typedef int32_t cufz_status;
 #define CUFZ_E_NO_DEVICE (-8)       /* no usable CUDA device */
 #define CUFZ_E_DEVICE_FAULT (-9)    /* the device reported an internal error word */
 #define CUFZ_E_IO (-10)             /* the autotune cache file could not be written */
+#define CUFZ_E_UNSUPPORTED (-11)    /* a valid program the engine does not run: a value
+                                       loaded from a shared buffer whose stores are
+                                       performed reaches an index, a branch, a loop
+                                       trip, a divisor or a heap operand */
 
 /* per-input status (cufz_result.status) */
 #define CUFZ_ST_OK 0
@@ -264,10 +282,13 @@ uint64_t cufz_arena_bytes(const cufz_config* cfg, uint32_t n_slots);
  * read-only in their body).  Returns CUFZ_OK or CUFZ_E_INVALID_PROGRAM. */
 cufz_status cufz_validate_program(const void* bytes, size_t nbytes);
 
-/* AXIPrune's MathElimination (Sec. 5.2, Alg. 2) on the program format:
- * drops every op whose result reaches no access index, branch condition or
- * loop trip count (stored values are dropped; loads stay as checked
- * accesses), then renumbers registers.  Writes the pruned program in the
+/* AXIPrune (Sec. 5.2, Alg. 2) on the program format: BarrierElimination
+ * drops every BAR (CUFZ_E_UNSUPPORTED for a program with performed shared
+ * stores whose barriers cannot go: a loaded shared value reaches a check;
+ * the flag itself stays), and MathElimination drops every op whose result
+ * reaches no access index, branch condition or loop trip count (stored
+ * values are dropped; loads stay as checked accesses), then renumbers
+ * registers.  Writes the pruned program in the
  * same format to out (capacity out_cap bytes; *out_bytes gets its size;
  * CUFZ_E_NOMEM if out_cap is smaller, so out = NULL, out_cap = 0 asks for
  * the size).  stats (may be NULL) receives the op and register counts.
@@ -298,8 +319,9 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
  * such affine value can leave the int32 range in the launch box (the device
  * computes in wrapping 32-bit arithmetic).  Programs with thread-dependent
  * guards (the paper's Alg. 1 case, a heuristic) are not eligible, nor are
- * programs with divisions and launches the engine does not run (invalid
- * shapes, more than 2^31 threads).
+ * programs with divisions or heap ops, programs the engine does not load
+ * (CUFZ_E_UNSUPPORTED), and launches it does not run (invalid shapes, more
+ * than 2^31 threads).
  * iter_budget: the context's back-edge budget (0 = 4096). */
 cufz_status cufz_prex_check(const void* bytes, size_t nbytes, const cufz_input* in,
                             uint32_t iter_budget, uint32_t* eligible);
@@ -367,7 +389,10 @@ cufz_status cufz_destroy(cufz_ctx* ctx);
  * uploads one program; *program_id receives its id: the lowest id freed by
  * cufz_unload_program, else the next new one (0, 1, ...).  Programs stay
  * resident until unloaded or the context is destroyed.  Up to 256 loaded at
- * a time, 8 MiB of loaded program blobs (CUFZ_E_NOMEM beyond). */
+ * a time, 8 MiB of loaded program blobs (CUFZ_E_NOMEM beyond).
+ * CUFZ_E_INVALID_PROGRAM for bytes the format rejects, CUFZ_E_UNSUPPORTED
+ * for a program with performed shared stores whose barriers BarrierElimination
+ * cannot remove. */
 cufz_status cufz_load_program(cufz_ctx* ctx, const void* bytes, size_t nbytes,
                               uint32_t* program_id, cufz_prog_stats* stats);
 

@@ -86,6 +86,21 @@
  * a buffer (redzone classes, no neighbours).  Heap loads read 0.  Every
  * HFREE, like every access and division, is a checked event for ordinals.
  *
+ * Performed shared stores and barriers (the input of BarrierElimination,
+ * Sec. 5.2, Alg. 2).  Header byte 11 bit 0 marks a program whose stores to
+ * shared buffers are performed: each block's shared buffers start as zero
+ * bytes; an in-bounds ST writes the value's little-endian bytes (width 1:
+ * its low byte; widths 8 and 16: its four bytes, then zero bytes) and an
+ * in-bounds LD reads them back (width 1: the byte, zero-extended; wider:
+ * the int32 of the first four bytes); out-of-bounds accesses are checked as
+ * always and store nothing.  BAR (0x55, top level only) splits the program
+ * into phases; a block runs each phase for all of its threads, one thread
+ * after another in thread_lin order, before the next phase: the serial
+ * program that translation by loop fission gives (Sec. 5.2).  A thread
+ * stopped by the budget runs no later phase.  Without the flag BAR does
+ * nothing: stores are never performed and shared loads read 0.  Global
+ * buffers are never written.
+ *
  * first_key = min over violations of
  *   block_lin << 32 | thread_lin << 22 | min(ordinal, 2^22 - 1).
  *
@@ -116,8 +131,10 @@ enum {
   OP_ADD = 0x10, OP_SUB, OP_MUL, OP_SHL, OP_SHR, OP_SHRU, OP_AND, OP_OR, OP_XOR,
   OP_MIN, OP_MAX, OP_SETLT, OP_SETLE, OP_SETEQ, OP_SETNE, OP_SETLTU,
   OP_LD = 0x40, OP_ST = 0x41, OP_HLD = 0x42, OP_HST = 0x43,
-  OP_IF = 0x50, OP_ELSE = 0x51, OP_ENDIF = 0x52, OP_LOOP = 0x53, OP_ENDLOOP = 0x54
+  OP_IF = 0x50, OP_ELSE = 0x51, OP_ENDIF = 0x52, OP_LOOP = 0x53, OP_ENDLOOP = 0x54,
+  OP_BAR = 0x55
 };
+enum { ORC_PF_SHARED_STORES = 1 }; /* header byte 11 */
 
 typedef struct {
   uint32_t program_id, grid[3], block[3];
@@ -158,7 +175,7 @@ typedef struct {
 
 typedef struct {
   int n_ops, n_regs, n_bufs, n_sites, n_access, n_div, n_alloc, n_free;
-  uint32_t shared_mask, seed;
+  uint32_t shared_mask, seed, flags;
   uint16_t loc[256][2];
   orc_op ops[ORC_MAX_OPS];
 } orc_prog;
@@ -217,7 +234,9 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
   P->n_sites = p[10];
   P->shared_mask = rd16(p + 12);
   P->seed = rd32(p + 16);
-  if (p[11] != 0 || rd16(p + 14) != 0 || rd32(p + 20) || rd32(p + 24) || rd32(p + 28))
+  P->flags = p[11];
+  if ((P->flags & ~(uint32_t)ORC_PF_SHARED_STORES) || rd16(p + 14) != 0 || rd32(p + 20) ||
+      rd32(p + 24) || rd32(p + 28))
     return ORC_E_FORMAT;
   if (P->n_ops < 1 || P->n_ops > ORC_MAX_OPS || P->n_bufs > ORC_MAX_BUFS) return ORC_E_FORMAT;
   if (P->shared_mask >> P->n_bufs) return ORC_E_FORMAT;
@@ -315,6 +334,10 @@ static int decode(const uint8_t* p, size_t n, orc_prog* P) {
             P->ops[stack[--depth]].end_pc = pc;
           }
           break;
+        case OP_BAR: /* a block-wide barrier: outside every IF and LOOP */
+          ok = !o->dst && !o->a && !o->b && !o->imm;
+          if (ok && depth != 0) return ORC_E_STRUCTURE;
+          break;
         default: return ORC_E_FORMAT;
       }
     }
@@ -357,6 +380,60 @@ int orc_n_access_sites(const void* h) { return ((const orc_prog*)h)->n_access; }
 
 /* ------------------------------------------------------------ interpreter */
 
+/* The shared-buffer bytes one block has written (programs with performed
+ * shared stores), keyed by (buffer, byte offset); a byte never written
+ * reads 0.  Open addressing; the table doubles at half load. */
+typedef struct {
+  uint64_t* keys; /* 0 = empty, else ((buffer << 56) | offset) + 1 */
+  uint8_t* vals;
+  uint64_t cap, used;
+} orc_smem;
+
+static uint64_t smem_slot(const orc_smem* m, uint64_t key) {
+  uint64_t i = (key * 0x9E3779B97F4A7C15ull) & (m->cap - 1);
+  while (m->keys[i] && m->keys[i] != key) i = (i + 1) & (m->cap - 1);
+  return i;
+}
+
+static int smem_put(orc_smem* m, int buf, int64_t off, uint8_t v) {
+  if (2 * (m->used + 1) > m->cap) {
+    orc_smem g;
+    g.cap = m->cap ? 2 * m->cap : 1024;
+    g.used = 0;
+    g.keys = (uint64_t*)calloc(g.cap, sizeof(uint64_t));
+    g.vals = (uint8_t*)calloc(g.cap, 1);
+    if (!g.keys || !g.vals) {
+      free(g.keys);
+      free(g.vals);
+      return 0;
+    }
+    for (uint64_t i = 0; i < m->cap; i++)
+      if (m->keys[i]) {
+        uint64_t j = smem_slot(&g, m->keys[i]);
+        g.keys[j] = m->keys[i];
+        g.vals[j] = m->vals[i];
+        g.used++;
+      }
+    free(m->keys);
+    free(m->vals);
+    *m = g;
+  }
+  uint64_t key = (((uint64_t)buf << 56) | (uint64_t)off) + 1;
+  uint64_t i = smem_slot(m, key);
+  if (!m->keys[i]) {
+    m->keys[i] = key;
+    m->used++;
+  }
+  m->vals[i] = v;
+  return 1;
+}
+
+static uint8_t smem_get(const orc_smem* m, int buf, int64_t off) {
+  if (!m->cap) return 0;
+  uint64_t i = smem_slot(m, (((uint64_t)buf << 56) | (uint64_t)off) + 1);
+  return m->keys[i] ? m->vals[i] : 0;
+}
+
 typedef struct {
   const orc_prog* P;
   const orc_opts* o;
@@ -373,6 +450,9 @@ typedef struct {
   int stopped;
   int32_t hsize[ORC_MAX_OPS];  /* per allocation site: the block's size */
   uint8_t hstate[ORC_MAX_OPS]; /* 0 never allocated, 1 live, 2 freed */
+  orc_smem* sm;                /* the block's shared bytes, or NULL when
+                                  shared stores are not performed */
+  int nomem;
 } orc_ctx;
 
 static void cover(orc_ctx* c, int site, int outcome) {
@@ -435,9 +515,19 @@ static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
     proto.cls = classify(c, buf, off, w);
     proto.byte_off = off;
     violation(c, &proto);
-  } else if (!is_store && !((c->P->shared_mask >> buf) & 1u)) {
-    uint32_t word = fmix32(c->P->seed ^ ((uint32_t)buf * 0x9E3779B9u) ^ (uint32_t)(off >> 2));
-    value = (w == 1) ? (int32_t)((word >> (8 * (off & 3))) & 0xFFu) : (int32_t)word;
+  } else if (!((c->P->shared_mask >> buf) & 1u)) {
+    if (!is_store) {
+      uint32_t word = fmix32(c->P->seed ^ ((uint32_t)buf * 0x9E3779B9u) ^ (uint32_t)(off >> 2));
+      value = (w == 1) ? (int32_t)((word >> (8 * (off & 3))) & 0xFFu) : (int32_t)word;
+    }
+  } else if (c->sm && is_store) { /* a performed shared store */
+    uint32_t v = (uint32_t)c->r[op->dst];
+    for (int k = 0; k < w; k++)
+      if (!smem_put(c->sm, buf, off + k, k < 4 ? (uint8_t)(v >> (8 * k)) : 0)) c->nomem = 1;
+  } else if (c->sm) { /* a shared load of what the block stored */
+    uint32_t v = 0;
+    for (int k = 0; k < (w == 1 ? 1 : 4); k++) v |= (uint32_t)smem_get(c->sm, buf, off + k) << (8 * k);
+    value = (int32_t)v;
   }
   c->ordinal++;
   return value;
@@ -624,7 +714,8 @@ static void exec_range(orc_ctx* c, int pc, int end) {
         pc = o->end_pc + 1;
         break;
       }
-      default: pc++; break; /* ELSE/ENDIF/ENDLOOP are never reached inside a range */
+      default: pc++; break; /* BAR: phases are split by the caller; ELSE/ENDIF/ENDLOOP
+                               are never reached inside a range */
     }
   }
 }
@@ -639,8 +730,102 @@ static int invalid_config(const orc_input* in) {
   return 0;
 }
 
-/* Runs one input; records (up to rec_cap, in (block, thread, ordinal) order)
- * and the bucketed bitmap (may be NULL) are written to the caller's buffers.
+/* One thread's state between the phases of a block. */
+typedef struct {
+  int32_t r[256];
+  uint32_t ordinal, prev_loc, h;
+  uint64_t backedges;
+  int stopped;
+} orc_saved;
+
+static void thread_start(orc_ctx* c, uint64_t bl, uint64_t tl, uint32_t bx, uint32_t by) {
+  const orc_prog* P = c->P;
+  c->sreg[0] = (int32_t)(tl % bx);
+  c->sreg[1] = (int32_t)((tl / bx) % by);
+  c->sreg[2] = (int32_t)(tl / ((uint64_t)bx * by));
+  memset(c->r, 0, sizeof(int32_t) * (P->n_regs ? P->n_regs : 1));
+  c->block_lin = (uint32_t)bl;
+  c->thread_lin = (uint32_t)tl;
+  c->ordinal = 0;
+  c->prev_loc = 0;
+  c->backedges = 0;
+  c->stopped = 0;
+  memset(c->hstate, 0, (size_t)P->n_alloc);
+  c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
+  c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
+}
+
+static void thread_save(const orc_ctx* c, orc_saved* s, int32_t* hsize, uint8_t* hstate) {
+  memcpy(s->r, c->r, sizeof(s->r));
+  s->ordinal = c->ordinal;
+  s->prev_loc = c->prev_loc;
+  s->h = c->h;
+  s->backedges = c->backedges;
+  s->stopped = c->stopped;
+  memcpy(hsize, c->hsize, sizeof(int32_t) * (size_t)c->P->n_alloc);
+  memcpy(hstate, c->hstate, (size_t)c->P->n_alloc);
+}
+
+static void thread_load(orc_ctx* c, const orc_saved* s, const int32_t* hsize,
+                        const uint8_t* hstate, uint64_t tl, uint32_t bx, uint32_t by) {
+  c->sreg[0] = (int32_t)(tl % bx);
+  c->sreg[1] = (int32_t)((tl / bx) % by);
+  c->sreg[2] = (int32_t)(tl / ((uint64_t)bx * by));
+  memcpy(c->r, s->r, sizeof(s->r));
+  c->thread_lin = (uint32_t)tl;
+  c->ordinal = s->ordinal;
+  c->prev_loc = s->prev_loc;
+  c->h = s->h;
+  c->backedges = s->backedges;
+  c->stopped = s->stopped;
+  memcpy(c->hsize, hsize, sizeof(int32_t) * (size_t)c->P->n_alloc);
+  memcpy(c->hstate, hstate, (size_t)c->P->n_alloc);
+}
+
+/* A block of a program with performed shared stores: phase by phase (the
+ * top-level BARs split the ops), every thread in thread_lin order runs the
+ * phase's ops, its state kept in between.  Returns 0 or ORC_E_NOMEM. */
+static int run_block_phased(orc_ctx* c, uint64_t bl, uint64_t T, uint32_t bx, uint32_t by) {
+  const orc_prog* P = c->P;
+  size_t na = (size_t)(P->n_alloc ? P->n_alloc : 1);
+  orc_saved* st = (orc_saved*)malloc(sizeof(orc_saved) * T);
+  int32_t* hsize = (int32_t*)malloc(sizeof(int32_t) * na * T);
+  uint8_t* hstate = (uint8_t*)malloc(na * T);
+  if (!st || !hsize || !hstate) {
+    free(st);
+    free(hsize);
+    free(hstate);
+    return ORC_E_NOMEM;
+  }
+  if (c->sm->cap) memset(c->sm->keys, 0, sizeof(uint64_t) * c->sm->cap); /* shared bytes: 0 */
+  c->sm->used = 0;
+  for (uint64_t tl = 0; tl < T; tl++) {
+    thread_start(c, bl, tl, bx, by);
+    thread_save(c, &st[tl], hsize + na * tl, hstate + na * tl);
+  }
+  int begin = 0;
+  for (;;) {
+    int end = begin;
+    while (end < P->n_ops && P->ops[end].opc != OP_BAR) end++;
+    for (uint64_t tl = 0; tl < T; tl++) {
+      thread_load(c, &st[tl], hsize + na * tl, hstate + na * tl, tl, bx, by);
+      exec_range(c, begin, end);
+      thread_save(c, &st[tl], hsize + na * tl, hstate + na * tl);
+    }
+    if (end >= P->n_ops) break;
+    begin = end + 1;
+  }
+  for (uint64_t tl = 0; tl < T; tl++) c->res->digest += st[tl].h;
+  free(st);
+  free(hsize);
+  free(hstate);
+  return c->nomem ? ORC_E_NOMEM : 0;
+}
+
+/* Runs one input; records (up to rec_cap; in (block, thread, ordinal) order,
+ * or for programs with performed shared stores (block, phase, thread,
+ * ordinal) order) and the bucketed bitmap (may be NULL) are written to the
+ * caller's buffers.
  * snapshot (may be NULL = empty) is the union bitmap NEW_COV compares with. */
 int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_result* res,
             orc_record* recs, uint64_t rec_cap, uint8_t* bitmap, const uint8_t* snapshot) {
@@ -663,11 +848,14 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
   }
   orc_ctx* c = (orc_ctx*)calloc(1, sizeof(orc_ctx));
   uint64_t* counts = (uint64_t*)calloc(65536, sizeof(uint64_t));
+  orc_smem sm;
+  memset(&sm, 0, sizeof(sm));
   if (!c || !counts) {
     free(c);
     free(counts);
     return ORC_E_NOMEM;
   }
+  if (P->flags & ORC_PF_SHARED_STORES) c->sm = &sm;
   c->P = P;
   c->o = opts;
   c->res = res;
@@ -695,24 +883,25 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
     c->sreg[6] = (int32_t)(bl % gx);
     c->sreg[7] = (int32_t)((bl / gx) % gy);
     c->sreg[8] = (int32_t)(bl / ((uint64_t)gx * gy));
+    if (c->sm) {
+      int rc = run_block_phased(c, bl, nthreads_blk, bx, by);
+      if (rc) {
+        free(sm.keys);
+        free(sm.vals);
+        free(counts);
+        free(c);
+        return rc;
+      }
+      continue;
+    }
     for (uint64_t tl = 0; tl < nthreads_blk; tl++) {
-      c->sreg[0] = (int32_t)(tl % bx);
-      c->sreg[1] = (int32_t)((tl / bx) % by);
-      c->sreg[2] = (int32_t)(tl / ((uint64_t)bx * by));
-      memset(c->r, 0, sizeof(int32_t) * (P->n_regs ? P->n_regs : 1));
-      c->block_lin = (uint32_t)bl;
-      c->thread_lin = (uint32_t)tl;
-      c->ordinal = 0;
-      c->prev_loc = 0;
-      c->backedges = 0;
-      c->stopped = 0;
-      memset(c->hstate, 0, (size_t)P->n_alloc);
-      c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
-      c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
+      thread_start(c, bl, tl, bx, by);
       exec_range(c, 0, P->n_ops);
       res->digest += c->h;
     }
   }
+  free(sm.keys);
+  free(sm.vals);
   res->n_records = (uint32_t)(res->n_violations < rec_cap ? res->n_violations : rec_cap);
   if (res->n_violations > rec_cap) res->flags |= ORC_FL_OVERFLOW;
   res->status = res->n_violations ? ORC_ST_VIOLATION : ORC_ST_OK;

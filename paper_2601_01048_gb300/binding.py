@@ -18,7 +18,7 @@ from .gen import INPUT_DTYPE
 # ---------------------------------------------------------------- constants
 OK = 0
 E_INVALID_ARG, E_INVALID_PROGRAM, E_NOMEM, E_BUSY, E_TIMEOUT, E_CUDA, E_NOT_FOUND, \
-    E_NO_DEVICE, E_DEVICE_FAULT, E_IO = range(-1, -11, -1)
+    E_NO_DEVICE, E_DEVICE_FAULT, E_IO, E_UNSUPPORTED = range(-1, -12, -1)
 ST_OK, ST_VIOLATION, ST_INVALID_CONFIG, ST_LIMIT, ST_BAD_PROGRAM = range(5)
 FL_BUDGET, FL_OVERFLOW, FL_NEW_COV, FL_PARTIAL = 1, 2, 4, 8
 CF_KEEP_BITMAPS, CF_PLAIN_LAUNCH, CF_NO_PRUNE, CF_AUTO_RELEASE, CF_NO_GRAPH, CF_NO_DIGEST, \

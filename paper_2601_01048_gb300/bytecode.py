@@ -56,6 +56,16 @@ Opcodes and the fields they use (unused fields must be 0):
     ELSE, ENDIF
     LOOP  dst=ctr, a=n, imm=max_trip (0..65535)
     ENDLOOP
+    BAR                        block-wide barrier (0x55), top level only
+
+Header byte 11 holds flags; bit 0 (PF_SHARED_STORES) makes stores to shared
+buffers performed: each block's shared buffers start as zero bytes, an
+in-bounds ST writes the value's little-endian bytes (width 1: the low byte;
+widths 8 and 16: the four bytes, then zeros) and an in-bounds LD reads them
+(width 1: the byte, zero-extended; wider: the int32 of the first four
+bytes).  The BARs split the program into phases that a block runs for all
+of its threads, in thread order, one phase after another.  Without the flag
+stores are never performed, shared loads read 0 and BAR does nothing.
 
 The k-th LD/ST in program order is access site k; the k-th IF/LOOP is branch
 site k; the k-th DIV/REM is division site k.  HLD/HST share the access
@@ -96,6 +106,10 @@ ELSE = 0x51
 ENDIF = 0x52
 LOOP = 0x53
 ENDLOOP = 0x54
+BAR = 0x55
+
+# header byte 11: program flags
+PF_SHARED_STORES = 1   # stores to shared buffers are performed; BARs order them
 
 ALU_NAMES = {
     ADD: "add", SUB: "sub", MUL: "mul", SHL: "shl", SHR: "shr", SHRU: "shru",
@@ -130,11 +144,13 @@ class Asm:
     :meth:`raw`.
     """
 
-    def __init__(self, n_bufs: int, shared_mask: int = 0, seed: int = 0):
+    def __init__(self, n_bufs: int, shared_mask: int = 0, seed: int = 0,
+                 shared_stores: bool = False):
         if not 0 <= n_bufs <= MAX_BUFS:
             raise ValueError("n_bufs out of range")
         self.n_bufs = n_bufs
         self.shared_mask = shared_mask
+        self.flags = PF_SHARED_STORES if shared_stores else 0
         self.seed = seed & 0xFFFFFFFF
         self.ops: list[tuple[int, int, int, int, int]] = []
         self.n_regs = 0
@@ -256,6 +272,11 @@ class Asm:
         self._stack.pop()
         self.raw(ENDLOOP)
 
+    def bar(self) -> None:
+        if self._stack:
+            raise ValueError("BAR inside IF/LOOP")
+        self.raw(BAR)
+
     @property
     def depth(self) -> int:
         return len(self._stack)
@@ -270,7 +291,7 @@ class Asm:
         if len(loc) != n_sites:
             raise ValueError("LOC table size does not match the branch sites")
         return encode(self.ops, max(self.n_regs, 1), self.n_bufs, self.shared_mask,
-                      self.seed, loc)
+                      self.seed, loc, self.flags)
 
 
 def default_loc(seed: int, n_sites: int) -> list[tuple[int, int]]:
@@ -282,10 +303,10 @@ def default_loc(seed: int, n_sites: int) -> list[tuple[int, int]]:
 
 
 def encode(ops, n_regs: int, n_bufs: int, shared_mask: int, seed: int,
-           loc: list[tuple[int, int]]) -> bytes:
+           loc: list[tuple[int, int]], flags: int = 0) -> bytes:
     out = bytearray()
     out += struct.pack("<IHHBBBBHHIIII", MAGIC, VERSION, len(ops), n_regs, n_bufs,
-                       len(loc), 0, shared_mask, 0, seed & 0xFFFFFFFF, 0, 0, 0)
+                       len(loc), flags, shared_mask, 0, seed & 0xFFFFFFFF, 0, 0, 0)
     assert len(out) == HEADER_BYTES
     for l0, l1 in loc:
         out += struct.pack("<HH", l0 & 0xFFFF, l1 & 0xFFFF)
@@ -295,10 +316,10 @@ def encode(ops, n_regs: int, n_bufs: int, shared_mask: int, seed: int,
 
 
 def decode_header(prog: bytes) -> dict:
-    (magic, version, n_ops, n_regs, n_bufs, n_sites, _r0, shared_mask, _r1, seed,
+    (magic, version, n_ops, n_regs, n_bufs, n_sites, flags, shared_mask, _r1, seed,
      _r2, _r3, _r4) = struct.unpack_from("<IHHBBBBHHIIII", prog, 0)
     return dict(magic=magic, version=version, n_ops=n_ops, n_regs=n_regs, n_bufs=n_bufs,
-                n_sites=n_sites, shared_mask=shared_mask, seed=seed)
+                n_sites=n_sites, shared_mask=shared_mask, seed=seed, flags=flags)
 
 
 def ops_of(prog: bytes) -> list[tuple[int, int, int, int, int]]:
@@ -345,6 +366,10 @@ def disasm(prog: bytes) -> str:
             lines.append(f"{pc:4d}  if r{a}")
         elif opc == LOOP:
             lines.append(f"{pc:4d}  loop r{dst} < clamp(r{a}, 0, {imm})")
+        elif opc == BAR:
+            lines.append(f"{pc:4d}  bar")
+        elif opc in (ELSE, ENDIF, ENDLOOP):
+            lines.append(f"{pc:4d}  {({ELSE: 'else', ENDIF: 'endif', ENDLOOP: 'endloop'})[opc]}")
         else:
             lines.append(f"{pc:4d}  op{opc:#x} {dst} {a} {b} {imm}")
     return "\n".join(lines)

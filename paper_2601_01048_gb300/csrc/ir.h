@@ -14,9 +14,11 @@ namespace cufz {
 enum : uint8_t {
   B_NOP = 0x00, B_SREG = 0x01, B_IMM = 0x02, B_MOV = 0x03, B_SEL = 0x04, B_DIV = 0x05, B_REM = 0x06,
   B_HALLOC = 0x07, B_HFREE = 0x08, B_LD = 0x40, B_ST = 0x41, B_HLD = 0x42, B_HST = 0x43,
-  B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53, B_ENDLOOP = 0x54
+  B_IF = 0x50, B_ELSE = 0x51, B_ENDIF = 0x52, B_LOOP = 0x53, B_ENDLOOP = 0x54, B_BAR = 0x55
 };
 constexpr uint32_t kMagic = 0x315A4643u;
+// header byte 11: stores to shared buffers are performed (BARs order them)
+constexpr uint32_t kPfSharedStores = 1;
 
 inline bool is_alu_reg(uint8_t o) { return o >= 0x10 && o <= 0x1F; }
 inline bool is_alu_imm(uint8_t o) { return o >= 0x30 && o <= 0x3F; }
@@ -46,7 +48,7 @@ struct IrOp {
 struct Ir {
   int n_regs = 0, n_bufs = 0, n_sites = 0, n_access = 0, n_loops = 0, n_div = 0;
   int n_alloc = 0, n_free = 0;  // HALLOC and HFREE sites
-  uint32_t shared_mask = 0, seed = 0;
+  uint32_t shared_mask = 0, seed = 0, flags = 0;
   std::vector<uint16_t> loc0, loc1;
   std::vector<IrOp> ops;
   int nv = 0;  // vreg count (kTripBase + loops)
@@ -54,6 +56,14 @@ struct Ir {
 
 // Decodes and validates program bytes; false on any violation of the format.
 bool decode(const uint8_t* p, size_t n, Ir* ir);
+
+// BarrierElimination (Sec. 5.2, Alg. 2): whether no value loaded from a
+// shared buffer reaches an access index, a branch, a loop trip, a divisor or
+// a heap operand.  Then a program's performed shared stores and its
+// barriers change no check, edge or count, and it runs as if its stores
+// were not performed and its barriers were gone.  True for programs whose
+// shared stores are not performed.
+bool barriers_eliminable(const Ir& ir);
 
 // A program's decoded form as given (unpruned) for PREX, which looks at
 // every access.

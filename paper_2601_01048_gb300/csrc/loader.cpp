@@ -42,7 +42,10 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
   ir->n_sites = p[10];
   ir->shared_mask = get16(p + 12);
   ir->seed = get32(p + 16);
-  if (p[11] || get16(p + 14) || get32(p + 20) || get32(p + 24) || get32(p + 28)) return false;
+  ir->flags = p[11];
+  if ((ir->flags & ~kPfSharedStores) || get16(p + 14) || get32(p + 20) || get32(p + 24) ||
+      get32(p + 28))
+    return false;
   if (n_ops < 1 || n_ops > kMaxOps || ir->n_bufs > kMaxBufs) return false;
   if (ir->shared_mask >> ir->n_bufs) return false;
   if (n != 32u + 4u * (size_t)ir->n_sites + 8u * (size_t)n_ops) return false;
@@ -78,6 +81,10 @@ bool decode(const uint8_t* p, size_t n, Ir* ir) {
       switch (opc) {
         case B_NOP:
           ok = !d && !a && !b && !imm;
+          o.kept = false;
+          break;
+        case B_BAR:  // top level only; never executed (see barriers_eliminable)
+          ok = !d && !a && !b && !imm && open.empty();
           o.kept = false;
           break;
         case B_SREG:
@@ -464,6 +471,18 @@ void fill_stats(const Ir& ir, int n_in, int regs_alloc, cufz_prog_stats* st) {
 }
 
 }  // namespace
+
+// A shared load whose value is dead after MathElimination reaches no root
+// on any path (the liveness over the structured control flow may only
+// over-approximate), and stored values are not roots.
+bool barriers_eliminable(const Ir& ir) {
+  if (!(ir.flags & kPfSharedStores)) return true;
+  Ir pruned = ir;
+  prune(&pruned);
+  for (const IrOp& o : pruned.ops)
+    if (o.opc == B_LD && ((ir.shared_mask >> o.buf) & 1u) && !o.value_dead) return false;
+  return true;
+}
 
 
 // ------------------------------------------------------------ code generator
@@ -1050,6 +1069,7 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
                        uint32_t index, std::string* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
   if (do_prune) {
     prune(&ir);
   } else {
@@ -1118,6 +1138,7 @@ void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask,
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
   auto prex = std::make_shared<PrexInfo>();
   prex->ir = ir;
   int n_in = (int)ir.ops.size();
@@ -1306,6 +1327,7 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
   if ((!out && out_cap) || !out_bytes) return CUFZ_E_INVALID_ARG;
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
+  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
   int n_in = (int)ir.ops.size();
   prune(&ir);
   std::vector<int> map;
@@ -1327,7 +1349,7 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
   v.push_back((uint8_t)std::max(n_regs, 1));
   v.push_back((uint8_t)ir.n_bufs);
   v.push_back((uint8_t)ir.n_sites);
-  v.push_back(0);
+  v.push_back((uint8_t)ir.flags);  // the flag stays; the barriers are gone
   put16(v, (uint16_t)ir.shared_mask);
   put16(v, 0);
   put32(v, ir.seed);

@@ -708,6 +708,9 @@ constexpr uint64_t kPrexPlanLimit = 1u << 16;  // larger plans: not eligible
 
 // The threads (linear ids g) that decide a guarded input's verdict, or false.
 bool prex_grid_plan(const Ir& ir, const cufz_input& in, uint32_t budget, std::vector<uint32_t>* out) {
+  // shared loads are modelled as reading 0: true only while no loaded
+  // shared value reaches a check
+  if (!barriers_eliminable(ir)) return false;
   bool merged[3];
   for (int d = 0; d < 3; d++) merged[d] = true;
   for (int pass = 0; pass < 4; pass++) {
@@ -761,6 +764,7 @@ bool prex_grid_plan(const Ir& ir, const cufz_input& in, uint32_t budget, std::ve
 }
 
 bool prex_run(const Ir& ir, const cufz_input& in, uint32_t budget) {
+  if (!barriers_eliminable(ir)) return false;  // as in prex_grid_plan
   PrexRun run{ir, in, budget, {}, std::vector<AVal>(std::max(ir.n_regs, 1))};
   for (int d = 0; d < 3; d++) {
     run.ext[d] = (int64_t)in.block[d] - 1;

@@ -542,6 +542,7 @@ const char* cufz_status_str(cufz_status s) {
     case CUFZ_E_NO_DEVICE: return "no CUDA device";
     case CUFZ_E_DEVICE_FAULT: return "device reported an engine error";
     case CUFZ_E_IO: return "autotune cache file could not be written";
+    case CUFZ_E_UNSUPPORTED: return "a shared-memory value that stores set reaches a check";
     default: return "unknown status";
   }
 }

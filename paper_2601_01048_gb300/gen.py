@@ -515,6 +515,126 @@ def heap_inputs(n: int, n_programs: int = 16, seed: int | None = None,
 
 
 # --------------------------------------------------------------------------
+# barrier workload: performed shared stores ordered by barriers (the input
+# of AXIPrune's BarrierElimination, Sec. 5.2)
+# --------------------------------------------------------------------------
+
+BAR_BLOCKS = ((8, 2, 1), (16, 1, 1), (4, 4, 1), (32, 1, 1))
+
+
+def barrier_program(index: int, live: bool = False) -> bytes:
+    """Random programs whose stores to shared buffers are performed, in 2-4
+    phases split by barriers.  Buffers: 0 global (read), 1 global (written),
+    2 shared int32 (a tile, one word per thread), 3 shared bytes.  Threads
+    store loaded values, coordinates and arguments into the tiles at their
+    own or a neighbour's slot, read other threads' slots after a barrier,
+    and store what they read.  With `live`, some values read from a tile
+    also become indices or branch conditions, so the barriers matter; without
+    it, no value read from a tile reaches a check (BarrierElimination
+    applies)."""
+    rng = SplitMix64(sub_seed("barprog", 2 * index + (1 if live else 0)))
+    A = Asm(n_bufs=4, shared_mask=0b1100, seed=rng.next32(), shared_stores=True)
+    tx, ty, ntx = A.sreg(bc.TID_X), A.sreg(bc.TID_Y), A.sreg(bc.NTID_X)
+    args = [A.sreg(bc.ARG0 + k) for k in range(4)]
+    t = A.alu(bc.ADD, A.alu(bc.MUL, ty, ntx), tx)
+    T = A.alu(bc.MUL, ntx, A.sreg(bc.NTID_Y))
+    gid = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), T), t)
+    read = []            # values read from the tiles so far
+
+    def slot():
+        r = rng.below(6)
+        if r == 0:
+            return t
+        if r == 1:
+            return A.alu(bc.ADD, t, Imm(1))
+        if r == 2:
+            return A.alu(bc.XOR, t, Imm(1))
+        if r == 3:
+            return A.alu(bc.SUB, A.alu(bc.SUB, T, Imm(1)), t)
+        if r == 4:
+            return A.alu(bc.ADD, t, rng.choice(args))
+        return A.alu(bc.AND, A.alu(bc.MUL, t, Imm(rng.choice((2, 3, 5)))), Imm(31))
+
+    def value():
+        r = rng.below(5)
+        if r == 0:
+            return A.ld(0, gid, rng.choice((1, 4)))
+        if r == 1:
+            return A.alu(bc.MUL, t, Imm(rng.randint(1, 4)))
+        if r == 2 and read:
+            return A.alu(bc.ADD, rng.choice(read), Imm(rng.randint(-2, 2)))
+        return A.alu(bc.ADD, rng.choice(args), t)
+
+    def use(v):
+        """A value read from a tile: stored on, or (live) a check."""
+        if live and rng.below(2):
+            if rng.below(2):
+                A.ld(rng.choice((0, 1)), A.alu(bc.SUB, v, rng.choice(args)), 4)
+            else:
+                A.if_(A.alu(bc.SETLT, v, rng.choice(args)))
+                A.ld(0, t, 4)
+                A.endif()
+        elif rng.below(2):
+            A.st(1, gid, A.alu(bc.XOR, v, t), 4)
+        else:
+            read.append(v)
+
+    def statement(depth):
+        r = rng.below(7)
+        if r <= 1:
+            A.st(2, slot(), value(), 4)
+        elif r == 2:
+            A.st(3, slot(), value(), 1)
+        elif r == 3:
+            use(A.ld(2, slot(), 4))
+        elif r == 4:
+            use(A.ld(3, slot(), 1))
+        elif r == 5 and depth == 0:
+            A.if_(A.alu(bc.SETLT, t, rng.choice(args)))
+            statement(1)
+            A.endif()
+        elif depth == 0:
+            k = A.loop(A.alu(bc.AND, rng.choice(args), Imm(3)), 3)
+            A.st(2, A.alu(bc.ADD, t, k), A.alu(bc.MUL, k, t), 4)
+            A.endloop()
+        else:
+            A.st(1, gid, t, 4)
+
+    for phase in range(rng.randint(2, 4)):
+        if phase:
+            A.bar()
+        for _ in range(rng.randint(2, 5)):
+            statement(0)
+    if live:             # at least one read value is a check
+        A.bar()
+        A.ld(1, A.alu(bc.SUB, A.ld(2, A.alu(bc.XOR, t, Imm(1)), 4), args[0]), 4)
+    return A.build()
+
+
+def barrier_programs(n: int = 16, live: bool = False) -> list[bytes]:
+    return [barrier_program(i, live) for i in range(n)]
+
+
+def barrier_inputs(n: int, n_programs: int = 16, seed: int | None = None,
+                   max_blocks: int = 3) -> np.ndarray:
+    """Blocks from BAR_BLOCKS, 1D grids up to max_blocks; arguments from
+    {0, +-1, 2, 3, 5, 8, 16}; global buffers up to 256 bytes; the int32
+    tile one word per thread (+-1 word), the byte tile one byte per thread
+    (+-1)."""
+    rng = SplitMix64(sub_seed("barrier") if seed is None else seed)
+    out = make_inputs(n)
+    for k in range(n):
+        blk = rng.choice(BAR_BLOCKS)
+        T = blk[0] * blk[1] * blk[2]
+        args = [rng.choice((0, 1, -1, 2, 3, 5, 8, 16)) for _ in range(4)]
+        lens = [rng.randint(0, 256), rng.randint(0, 256), 4 * (T + rng.randint(-1, 1)),
+                T + rng.randint(-1, 1)]
+        set_input(out[k], k % n_programs, (rng.randint(1, max_blocks), 1, 1), blk, args, lens,
+                  tag=k)
+    return out
+
+
+# --------------------------------------------------------------------------
 # config 2: random 2D programs with shared buffers and loops
 # --------------------------------------------------------------------------
 

@@ -5,7 +5,9 @@ It is written independently of oracle/cufz_oracle.c: its own decoder (a
 recursive parse into nested blocks), Python integers with explicit masking,
 its own hash, classification and bucketing.  Both follow the same definition:
 serial execution of every thread (Sec. 4.1, Listings 1-2), exact bounds
-checks, AFL-style edges (Sec. 2.1).
+checks, AFL-style edges (Sec. 2.1).  A program with performed shared stores
+runs each block as Python generators, one per thread, advanced in thread
+order from one barrier to the next.
 """
 from __future__ import annotations
 
@@ -37,7 +39,7 @@ def afl_class(n):
 
 
 def parse(prog: bytes):
-    magic, ver, n_ops, n_regs, n_bufs, n_sites, _, shmask, _, seed = struct.unpack_from(
+    magic, ver, n_ops, n_regs, n_bufs, n_sites, flags, shmask, _, seed = struct.unpack_from(
         "<IHHBBBBHHI", prog, 0)
     assert magic == 0x315A4643 and ver == 1
     loc = [struct.unpack_from("<HH", prog, 32 + 4 * s) for s in range(n_sites)]
@@ -83,13 +85,15 @@ def parse(prog: bytes):
             elif opc in (0x42, 0x43):
                 out.append(("hmem", opc == 0x43, d, a, b, imm, counters["a"]))
                 counters["a"] += 1
+            elif opc == 0x55:
+                out.append(("bar",))
             else:
                 out.append(("op", opc, d, a, b, imm))
         return out, None
 
     body, _ = block(())
     return dict(n_regs=n_regs, n_bufs=n_bufs, shmask=shmask, seed=seed, loc=loc, body=body,
-                n_alloc=counters["h"])
+                n_alloc=counters["h"], stores=bool(flags & 1))
 
 
 def alu(opc, x, y):
@@ -125,6 +129,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         base[k] = nxt[sp]
         nxt[sp] = -(-(nxt[sp] + lens[k] + redzone) // 256) * 256
     st = dict(records=[], counts={}, digest=0, n_accesses=0, n_branch=0, budget_hit=False)
+    smem = {}  # (buffer, byte offset) -> byte: the current block's stored shared bytes
 
     def classify(buf, off, w):
         if -redzone <= off < 0:
@@ -162,6 +167,13 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
             elif not is_st and not (shm >> buf) & 1:
                 word = murmur_fmix32(P["seed"] ^ ((buf * 0x9E3779B9) & M32) ^ ((off >> 2) & M32))
                 val = s32((word >> (8 * (off & 3))) & 0xFF) if w == 1 else s32(word)
+            elif P["stores"] and (shm >> buf) & 1 and is_st:
+                data = (regs[d] & M32).to_bytes(4, "little") + bytes(max(w - 4, 0))
+                for k in range(w):
+                    smem[(buf, off + k)] = data[k]
+            elif P["stores"] and (shm >> buf) & 1:
+                data = bytes(smem.get((buf, off + k), 0) for k in range(1 if w == 1 else 4))
+                val = s32(int.from_bytes(data, "little"))
             t["ordinal"] += 1
             if not is_st:
                 regs[d] = val
@@ -275,7 +287,11 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                             return
                         regs[ctr] += 1
 
-        run(P["body"])
+        for s in P["body"]:       # a barrier ends a phase: the next thread runs
+            if s[0] == "bar":
+                yield
+            else:
+                run([s])
         st["digest"] = (st["digest"] + t["h"]) & M64
 
     args = [s32(v) for v in inp["args"]]
@@ -283,12 +299,22 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         for by in range(g[1]):
             for bx in range(g[0]):
                 bl = bx + by * g[0] + bz * g[0] * g[1]
+                smem.clear()
+                threads = []
                 for tz in range(b[2]):
                     for ty in range(b[1]):
                         for tx in range(b[0]):
                             tl = tx + ty * b[0] + tz * b[0] * b[1]
                             sregs = [tx, ty, tz, b[0], b[1], b[2], bx, by, bz, g[0], g[1], g[2]] + args
-                            run_thread(bl, tl, [s32(v) for v in sregs])
+                            threads.append(run_thread(bl, tl, [s32(v) for v in sregs]))
+                if P["stores"]:       # phase by phase, every thread in order
+                    for _ in range(1 + sum(1 for s in P["body"] if s[0] == "bar")):
+                        for th in threads:
+                            next(th, None)
+                else:                 # each thread to its end (BAR does nothing)
+                    for th in threads:
+                        for _ in th:
+                            pass
     recs = st["records"]
     fk = min(((r[0] << 32) | (r[1] << 22) | min(r[2], (1 << 22) - 1) for r in recs), default=M64)
     return dict(status=1 if recs else 0, flags=1 if st["budget_hit"] else 0, records=recs,

@@ -16,11 +16,12 @@ def pytest_configure(config):
 
 
 def pytest_collection_modifyitems(config, items):
-    """The PREX, division-fault and heap-fault tests, then the full-size
-    workload tests, run last: the first three cover the newest device and
-    runtime code, the last take the longest, and the established parity
-    tests should report first."""
-    late = ("test_gpu_prex", "test_gpu_divfault", "test_gpu_heap", "test_gpu_fullsize")
+    """The PREX, division-fault, heap-fault and barrier tests, then the
+    full-size workload tests, run last: the first four cover the newest
+    device and runtime code, the last take the longest, and the established
+    parity tests should report first."""
+    late = ("test_gpu_prex", "test_gpu_divfault", "test_gpu_heap", "test_gpu_barrier",
+            "test_gpu_fullsize")
     items.sort(key=lambda item: next((k + 1 for k, f in enumerate(late) if f in item.nodeid), 0))
 
 

@@ -338,3 +338,84 @@ def test_validator_agrees_with_oracle_on_heap_programs(orc, seed):
         prog[pos] = rng.choice((0x07, 0x08, 0x42, 0x43, rng.below(256)))
     p = bytes(prog)
     assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)
+
+
+def _without_barriers(prog: bytes) -> bytes:
+    """The same program with its BARs as NOPs and its stores not performed."""
+    ops = [(0, 0, 0, 0, 0) if o[0] == bc.BAR else o for o in bc.ops_of(prog)]
+    h = bc.decode_header(prog)
+    return bc.encode(ops, h["n_regs"], h["n_bufs"], h["shared_mask"], h["seed"], bc.loc_of(prog))
+
+
+def _same_results(orc, a, b, ins, o):
+    ra, ca, ma = orc.run_batch([a], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+    rb, cb, mb = orc.run_batch([b], ins, o, rec_cap=1 << 14, bitmaps=True, threads=2)
+    from conftest import record_keys
+    return (ra.tobytes() == rb.tobytes() and np.array_equal(ma, mb) and
+            all(record_keys(ca[k][: int(ra[k]["n_records"])]) ==
+                record_keys(cb[k][: int(rb[k]["n_records"])]) for k in range(len(ins))))
+
+
+@pytest.mark.parametrize("which", range(16))
+def test_barrier_elimination_keeps_every_check(orc, which):
+    """BarrierElimination (Sec. 5.2, Alg. 2): when no value read from a
+    shared buffer reaches a check, the barriers and the stores' effect can
+    go.  The oracle, which performs the stores phase by phase, gives the same
+    results (records, counts, digest, bitmap) for the program, for it
+    without barriers and without performed stores (what the engine runs),
+    and for the library's pruned program (flag kept, barriers gone)."""
+    prog = gen.barrier_program(which)
+    pruned, st = B.cufz_prune_program(prog)
+    assert bc.BAR not in [o[0] for o in bc.ops_of(pruned)]
+    assert bc.decode_header(pruned)["flags"] == bc.PF_SHARED_STORES
+    plain = _without_barriers(prog)
+    assert orc.validate(plain) == 0 and orc.validate(pruned) == 0
+    ins = gen.barrier_inputs(6, n_programs=1, seed=600 + which)
+    for o in (orc.opts(), orc.opts(iter_budget=2)):
+        assert _same_results(orc, prog, plain, ins, o)
+        assert _same_results(orc, prog, pruned, ins, o)
+
+
+def test_barriers_stay_where_shared_values_reach_checks(orc):
+    """Where a value read from a shared buffer reaches an index or a branch,
+    BarrierElimination does not apply: the library refuses to prune, compile
+    or plan such a program (CUFZ_E_UNSUPPORTED, no PREX plan), and the
+    oracle shows why: without its barriers and stores its checks change."""
+    differs = 0
+    for which in range(16):
+        prog = gen.barrier_program(which, live=True)
+        assert B.cufz_validate_program(prog) == 0 and orc.validate(prog) == 0
+        with pytest.raises(B.CufzError) as e:
+            B.cufz_prune_program(prog)
+        assert e.value.status == B.E_UNSUPPORTED
+        ins = gen.barrier_inputs(4, n_programs=1, seed=700 + which)
+        assert all(B.cufz_prex_plan(prog, x) is None and not B.cufz_prex_check(prog, x)
+                   for x in ins)
+        differs += not _same_results(orc, prog, _without_barriers(prog), ins, orc.opts())
+    st, log, _ = B.cufz_compile_check([gen.barrier_program(0, live=True)])
+    assert st == B.E_UNSUPPORTED
+    assert differs >= 8
+
+
+@pytest.mark.parametrize("seed", range(24))
+def test_validator_agrees_with_oracle_on_barrier_programs(orc, seed):
+    """Barriers inside IF/LOOP, unknown flag bits and stray BARs are format
+    errors for both validators alike."""
+    rng = gen.SplitMix64(seed + 800)
+    prog = bytearray(gen.barrier_program(seed % 16, live=bool(seed & 1)))
+    for _ in range(rng.randint(1, 3)):
+        if rng.below(3) == 0:
+            prog[11] = rng.choice((0, 1, 2, 3, 0x81))
+        else:
+            pos = rng.randint(32, len(prog) - 1)
+            prog[pos] = rng.choice((0x55, 0x50, 0x53, rng.below(256)))
+    p = bytes(prog)
+    assert (B.cufz_validate_program(p) == 0) == (orc.validate(p) == 0)
+
+
+def test_disassembler_names_every_op():
+    progs = (gen.c2_programs()[:4] + gen.c4_programs()[:2] + gen.div_programs()[:2]
+             + gen.heap_programs()[:2] + gen.barrier_programs(2) + [gen.c1_program()])
+    for p in progs:
+        text = bc.disasm(p)
+        assert "op0x" not in text and len(text.splitlines()) == bc.decode_header(p)["n_ops"]

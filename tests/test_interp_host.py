@@ -176,3 +176,17 @@ def test_interpreter_heap_programs(tmp_path, interp_exe, orc, flags):
         compare(got, ores, orecs, obms, cap)
         if cap > 8:
             assert sum(int((r["kind"] == 3).sum()) for _, r, _ in got) > 0
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_interpreter_barrier_programs(tmp_path, interp_exe, orc, flags):
+    """Programs with performed shared stores whose barriers BarrierElimination
+    removes: the interpreter, with no store performed and no barrier, equals
+    the oracle's phase-by-phase execution, pruned and unpruned, with a small
+    record cap as well."""
+    progs = gen.barrier_programs()
+    ins = gen.barrier_inputs(48, seed=317)
+    for cap in (1 << 14, 8):
+        got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
+        ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
+        compare(got, ores, orecs, obms, cap)

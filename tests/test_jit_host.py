@@ -291,3 +291,28 @@ def test_heap_programs_match_oracle(tmp_path, host_objs, orc, flags):
             seen |= {(int(r["kind"]), int(r["cls"])) for r in recs if int(r["space"]) == 2}
         if budget == 4096:
             assert {(0, 6), (1, 6), (3, 7), (3, 8), (0, 4), (1, 2)} <= seen, seen
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_barrier_programs_match_oracle(tmp_path, host_objs, orc, flags):
+    """Programs with performed shared stores and barriers that
+    BarrierElimination removes (no value read from a tile reaches a check):
+    the generated code, which performs no store and has no barrier, equals
+    the oracle, which performs the stores phase by phase, in every result,
+    pruned and unpruned, and under a budget that stops threads early."""
+    progs = gen.barrier_programs()
+    ins = gen.barrier_inputs(48, seed=316)
+    exe = build(tmp_path, host_objs, progs, flags)
+    for budget in (4096, 2):
+        got = run(tmp_path, exe, progs, ins, budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
+                                          rec_cap=1 << 14, bitmaps=True)
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records"):
+                assert int(res[f]) == int(o[f]), (budget, i, f)
+            assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
+            assert np.array_equal(bm, obms[i]), (budget, i)
+        assert sum(int(o["n_violations"]) for o in ores) > 0

@@ -61,7 +61,8 @@ def corpus(path, seed=0x5A17, mutations=10):
     rng = gen.SplitMix64(seed)
     progs = ([gen.c1_program()] + gen.c2_programs() + gen.c3_programs() + gen.c4_programs()
              + gen.affine_programs() + gen.c5_programs()[:8] + gen.div_programs()
-             + gen.heap_programs())
+             + gen.heap_programs() + gen.barrier_programs(8)
+             + gen.barrier_programs(8, live=True))
     for _ in range(20):
         progs += [guarded_1d_program(rng), affine_with_extras(rng, 1 + rng.below(3)),
                   affine_program(rng, 1 + rng.below(3), 4)]

@@ -637,3 +637,90 @@ def test_bruteforce_heap_programs(orc, index):
                                             block=tuple(int(v) for v in x["block"]),
                                             args=[int(v) for v in x["args"]],
                                             lens=[int(v) for v in x["buf_len"][:1]]))
+
+
+# ------------------------------------------------ performed shared stores and barriers
+
+def _exchange_program(flag, barrier):
+    """Each thread t of 8 stores 3 t to its tile word S[t]; then, after the
+    barrier, reads its neighbour's word S[(t + 1) & 7] and loads G at that
+    value - 12 (G: 8 words)."""
+    A = Asm(n_bufs=2, shared_mask=0b10, shared_stores=flag)
+    t = A.sreg(bc.TID_X)
+    A.st(1, t, A.alu(bc.MUL, t, Imm(3)), 4)
+    if barrier:
+        A.bar()
+    v = A.ld(1, A.alu(bc.AND, A.alu(bc.ADD, t, Imm(1)), Imm(7)), 4)
+    A.ld(0, A.alu(bc.SUB, v, Imm(12)), 4)
+    return A.build()
+
+
+def test_shared_stores_cross_a_barrier(orc):
+    """Sec. 5.2's barriers order shared stores: after the barrier thread t
+    reads 3 u, u = (t + 1) & 7, written by thread u, and its index 3 u - 12
+    leaves G (8 words) for u in {0, 1, 2, 3, 7}, i.e. t in {7, 0, 1, 2, 6}."""
+    res, recs, _ = orc.run(orc.Program(_exchange_program(True, True)),
+                           mk((2, 1, 1), (8, 1, 1), (), (32, 32)), rec_cap=64)
+    got = sorted((int(r["block_lin"]), int(r["thread_lin"]), int(r["ordinal"]), int(r["buf"]),
+                  int(r["byte_off"])) for r in recs)
+    want = sorted((b, t, 2, 0, 4 * (3 * ((t + 1) & 7) - 12))
+                  for b in range(2) for t in (7, 0, 1, 2, 6))
+    assert got == want and int(res["n_accesses"]) == 2 * 8 * 3
+
+
+def test_shared_stores_without_the_barrier_run_in_thread_order(orc):
+    """Without the barrier a block runs as one phase, thread after thread:
+    thread t < 7 reads S[t + 1] before its owner wrote it (0, index -12);
+    thread 7 reads S[0] = 0, written by thread 0.  Without the flag nothing
+    is stored and every read gives 0."""
+    inp = mk((1, 1, 1), (8, 1, 1), (), (32, 32))
+    for flag, barrier in ((True, False), (False, True), (False, False)):
+        res, recs, _ = orc.run(orc.Program(_exchange_program(flag, barrier)), inp, rec_cap=64)
+        assert sorted((int(r["thread_lin"]), int(r["byte_off"])) for r in recs) == \
+            [(t, -48) for t in range(8)], (flag, barrier)
+
+
+def test_shared_store_widths(orc):
+    """Thread 0 stores 0x1234 at width 1 (byte 0x34) to byte 0, -1 at width
+    8 (ff ff ff ff 00 00 00 00) to bytes 8-15, and 7 at width 4 to bytes
+    16-19; after the barrier each thread reads them back and uses them as
+    indices into G (length 0: every access violates, byte_off = 4 index).
+    An out-of-bounds store (bytes 64-67) stores nothing."""
+    A = Asm(n_bufs=2, shared_mask=0b10, shared_stores=True)
+    t = A.sreg(bc.TID_X)
+    A.if_(A.alu(bc.SETEQ, t, Imm(0)))
+    A.st(1, A.imm(0), A.imm(0x1234), 1)
+    A.st(1, A.imm(1), A.imm(-1), 8)
+    A.st(1, A.imm(4), A.imm(7), 4)
+    A.st(1, A.imm(16), A.imm(9), 4)
+    A.endif()
+    A.bar()
+    for idx, w in ((0, 1), (1, 1), (2, 4), (3, 4), (4, 4), (8, 1), (16, 4)):
+        A.ld(0, A.ld(1, A.imm(idx), w), 4)
+    res, recs, _ = orc.run(orc.Program(A.build()), mk((1, 1, 1), (2, 1, 1), (), (0, 64)),
+                           rec_cap=64)
+    loads = sorted((int(r["thread_lin"]), int(r["ordinal"]), int(r["byte_off"]))
+                   for r in recs if int(r["buf"]) == 0)
+    values = [0x34, 0, -1, 0, 7, 0xFF, 0]     # byte 1 was never written; byte 8 is ff
+    base = (4, 0)                             # thread 0 ran the four stores first
+    want = sorted((th, base[th] + 2 * k + 1, 4 * v) for th in range(2)
+                  for k, v in enumerate(values))
+    assert loads == want
+    tile = sorted((int(r["thread_lin"]), int(r["ordinal"]), int(r["kind"]), int(r["byte_off"]))
+                  for r in recs if int(r["buf"]) == 1)
+    # the store at bytes 64-67 and both threads' read of them leave the tile
+    assert tile == [(0, 3, 1, 64), (0, 16, 0, 64), (1, 12, 0, 64)]
+
+
+@pytest.mark.parametrize("index", range(8))
+def test_bruteforce_barrier_programs(orc, index):
+    """Random programs with performed shared stores in phases (values read
+    from the tiles stored on, and, for odd indices, used as indices and
+    branch conditions): the oracle equals the independent evaluator, which
+    runs each block's threads as generators from barrier to barrier."""
+    prog = gen.barrier_program(index // 2, live=bool(index & 1))
+    for x in gen.barrier_inputs(3, n_programs=1, seed=5000 + index, max_blocks=2):
+        _compare_bruteforce(orc, prog, dict(grid=tuple(int(v) for v in x["grid"]),
+                                            block=tuple(int(v) for v in x["block"]),
+                                            args=[int(v) for v in x["args"]],
+                                            lens=[int(v) for v in x["buf_len"][:4]]))
