@@ -583,3 +583,47 @@ def test_no_plan_for_programs_on_the_heap(op):
     A.ld(0, i, 4)
     inp = mk((4, 1, 1), (32, 1, 1), (1, 7), (400,))
     assert not B.cufz_prex_check(A.build(), inp) and B.cufz_prex_plan(A.build(), inp) is None
+
+
+def _tile_program():
+    """A tiled copy with a barrier (the shape of Sec. 5.2's example): each
+    thread stores A[i] into its tile slot, and after the barrier copies the
+    mirrored slot to C[i]; under the guard i < a1 it also reads A[i + 1]."""
+    A = Asm(n_bufs=3, shared_mask=0b100, shared_stores=True)
+    t, T = A.sreg(bc.TID_X), A.sreg(bc.NTID_X)
+    i = A.alu(bc.ADD, A.alu(bc.MUL, A.sreg(bc.CTAID_X), T), t)
+    A.st(2, t, A.ld(0, i, 4), 4)
+    A.bar()
+    A.st(1, i, A.ld(2, A.alu(bc.SUB, A.alu(bc.SUB, T, Imm(1)), t), 4), 4)
+    A.if_(A.alu(bc.SETLT, i, A.sreg(bc.ARG1)))
+    A.ld(0, A.alu(bc.ADD, i, Imm(1)), 4)
+    A.endif()
+    return A.build()
+
+
+def test_plans_for_eliminated_barriers_decide_the_phased_grid(orc):
+    """Programs whose barriers BarrierElimination removes keep PREX: where a
+    plan exists, its threads decide every access site's verdict under the
+    oracle's phase-by-phase execution with performed stores."""
+    prog = _tile_program()
+    rng = gen.SplitMix64(901)
+    planned = violating = 0
+    for _ in range(48):
+        T, nb = rng.choice((32, 64, 128)), rng.randint(1, 6)
+        n = T * nb
+        inp = mk((nb, 1, 1), (T, 1, 1), (0, n - rng.randint(0, 2)),
+                 (4 * (n - rng.randint(0, 1)), 4 * (n - rng.randint(0, 1)),
+                  4 * (T - rng.randint(0, 1))))
+        plan = B.cufz_prex_plan(prog, inp)
+        assert plan is not None and len(plan) < n
+        planned += 1
+        ok, full = plan_decides_every_site(orc, prog, inp, plan)
+        assert ok, inp
+        violating += full
+    for which in range(16):          # the random ones, where a plan exists
+        p = gen.barrier_program(which)
+        for inp in gen.barrier_inputs(8, n_programs=1, seed=900 + which, max_blocks=4):
+            plan = B.cufz_prex_plan(p, inp)
+            if plan is not None:
+                assert plan_decides_every_site(orc, p, inp, plan)[0], (which, inp)
+    assert planned == 48 and 8 <= violating < 48
