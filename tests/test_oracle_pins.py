@@ -626,6 +626,30 @@ def test_heap_faults_by_class(orc):
     assert int(res["first_key"]) == 2                      # thread 0's use after free
 
 
+def test_heap_reallocation_and_failed_frees(orc):
+    """A site's later HALLOC replaces its block (sizes 1 then 2 in a loop,
+    after a NULL allocation that changes nothing); a failed free leaves the
+    heap as it was (the freed block stays freed: the next load is a use
+    after free); a second site's block has its own handle and size."""
+    A = Asm(n_bufs=0)
+    k = A.loop(A.imm(3), 3)
+    A.hst(A.halloc(k), A.imm(1), k, 1)     # ordinals 0-2: NULL (wild), 1 byte (over), 2 bytes
+    A.endloop()
+    one = A.imm(1)
+    A.hld(one, A.imm(1), 1)                # 3: block 0 has 2 bytes
+    A.hfree(one)                           # 4
+    A.hfree(A.imm(5))                      # 5: invalid free, nothing changes
+    A.hld(one, A.imm(0), 1)                # 6: use after free
+    h2 = A.halloc(A.imm(8))                # site 1: handle 2
+    A.hld(h2, A.imm(7), 1)                 # 7: in bounds
+    A.hst(h2, A.imm(2), h2, 4)             # 8: bytes 8-11 of 8
+    res, recs, _ = orc.run(orc.Program(A.build()), mk((1, 1, 1), (1, 1, 1), (), ()), rec_cap=64)
+    assert rec_tuples(recs) == [(0, 0, 0, 0, 0, 1, 1, 2, 4, 1), (0, 0, 1, 0, 0, 1, 1, 2, 2, 1),
+                                (0, 0, 5, 1, 0, 3, 0, 2, 8, 0), (0, 0, 6, 2, 0, 0, 1, 2, 6, 0),
+                                (0, 0, 8, 4, 1, 1, 4, 2, 2, 8)]
+    assert int(res["n_accesses"]) == 7
+
+
 @pytest.mark.parametrize("index", range(8))
 def test_bruteforce_heap_programs(orc, index):
     """Random heap programs (allocation sizes from arguments and
