@@ -748,3 +748,21 @@ def test_bruteforce_barrier_programs(orc, index):
                                             block=tuple(int(v) for v in x["block"]),
                                             args=[int(v) for v in x["args"]],
                                             lens=[int(v) for v in x["buf_len"][:4]]))
+
+
+def test_a_thread_stopped_by_the_budget_runs_no_later_phase(orc):
+    """Thread 0 alone loops past the back-edge budget in the first phase
+    and stops; after the barrier only threads 1-3 reach the out-of-bounds
+    load, and the input carries the budget flag."""
+    A = Asm(n_bufs=2, shared_mask=0b10, shared_stores=True)
+    t = A.sreg(bc.TID_X)
+    A.if_(A.alu(bc.SETEQ, t, Imm(0)))
+    A.loop(A.imm(10), 10)
+    A.endloop()
+    A.endif()
+    A.bar()
+    A.ld(0, A.imm(-1), 4)
+    res, recs, _ = orc.run(orc.Program(A.build()), mk((1, 1, 1), (4, 1, 1), (), (16, 16)),
+                           orc.opts(iter_budget=3), rec_cap=64)
+    assert [(int(r["thread_lin"]), int(r["byte_off"])) for r in recs] == [(1, -4), (2, -4), (3, -4)]
+    assert int(res["flags"]) & orc.FL_BUDGET and int(res["n_accesses"]) == 3
