@@ -119,7 +119,7 @@ typedef int32_t cufz_status;
 /* per-input status (cufz_result.status) */
 #define CUFZ_ST_OK 0
 #define CUFZ_ST_VIOLATION 1      /* at least one out-of-bounds access */
-#define CUFZ_ST_INVALID_CONFIG 2 /* CUDA would reject the launch (Sec. 3.3.1) */
+#define CUFZ_ST_INVALID_CONFIG 2 /* CUDA would reject the launch (Sec. 2.3.1) */
 #define CUFZ_ST_LIMIT 3          /* beyond the engine's limits (max_threads, len >= 2^48) */
 #define CUFZ_ST_BAD_PROGRAM 4    /* program_id names no loaded program */
 
@@ -372,21 +372,30 @@ cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* i
 cufz_status cufz_mutate_inputs(cufz_input* inputs, uint32_t n, const uint8_t* n_bufs,
                                uint32_t n_programs, uint64_t* rng_state);
 
-/* Human-readable name of a status code. */
+/* Human-readable name of a status code (the error classes of Sec. 2.3.1 and
+ * Sec. 2.3.2 that the engine reports, and the context's own errors). */
 const char* cufz_status_str(cufz_status s);
 
 /* ------------------------------------------------------------- context */
 
 /* Creates an engine on cfg->device over cfg->arena.  Clears the arena's
- * tables on cfg->stream and waits for that.  *out is NULL on failure. */
+ * tables on cfg->stream and waits for that.  *out is NULL on failure.
+ * Stands in for the runtime libraries of Sec. 4 (CPU-side cudaMalloc /
+ * cudaMemcpy emulation and the thread pool over blocks): here the caller's
+ * arena and stream are the device memory and the engine is the pool. */
 cufz_status cufz_create(const cufz_config* cfg, cufz_ctx** out);
 
 /* Waits (bounded) for in-flight work, then frees host-side resources.  The
- * arena is left to the caller. */
+ * arena is left to the caller.  (The end of a Sec. 4 runtime's process; no
+ * separate counterpart in the paper.) */
 cufz_status cufz_destroy(cufz_ctx* ctx);
 
-/* Validates, prunes (unless CUFZ_CF_NO_PRUNE), allocates registers and
- * uploads one program; *program_id receives its id: the lowest id freed by
+/* The kernel translator of Sec. 4 (cuf-cc's AXIPrune pass, Sec. 5.2, Alg. 2,
+ * then code generation) for one kernel-under-test given as a program.
+ * Validates, prunes (unless the context's config has CUFZ_CF_NO_PRUNE:
+ * pruning is chosen per context, not per call, so the call takes no flags),
+ * allocates registers and uploads one program;
+ * *program_id receives its id: the lowest id freed by
  * cufz_unload_program, else the next new one (0, 1, ...).  Programs stay
  * resident until unloaded or the context is destroyed.  Up to 256 loaded at
  * a time, 8 MiB of loaded program blobs (CUFZ_E_NOMEM beyond).
@@ -418,7 +427,11 @@ cufz_status cufz_unload_program(cufz_ctx* ctx, uint32_t program_id);
 cufz_status cufz_verify_prune(cufz_ctx* ctx, uint32_t program_id, const cufz_input* inputs,
                               uint32_t n, uint32_t* n_mismatch);
 
-/* Admits a prefix of in[0..n) while slots are free; each admitted input gets
+/* One fuzz execution per input (Sec. 4: the translated program run on a
+ * fuzzer-provided input; Sec. 4.1: every thread of every block, here on
+ * the GPU), with every access checked (the ASan checks of Sec. 4) and
+ * edges counted (Sec. 2.1, the AFL trampolines after branches).
+ * Admits a prefix of in[0..n) while slots are free; each admitted input gets
  * ticket first_ticket + i.  Inputs with an invalid launch configuration,
  * beyond the limits or naming no program are admitted and complete at once
  * with their status, without device work.  Returns CUFZ_E_BUSY (with
@@ -430,7 +443,10 @@ cufz_status cufz_verify_prune(cufz_ctx* ctx, uint32_t program_id, const cufz_inp
 cufz_status cufz_submit_inputs(cufz_ctx* ctx, const cufz_input* in, uint32_t n,
                                uint32_t* n_accepted, uint64_t* first_ticket);
 
-/* Copies up to max completed results (in completion order) to out and sets
+/* What afl-fuzz reads back from a finished child (Sec. 2.1): the crash or
+ * not (status, violation counts, first-violation key in place of ASan's
+ * abort at the first error) and the coverage summary.
+ * Copies up to max completed results (in completion order) to out and sets
  * *n_out.  Waits up to timeout_us microseconds for the first one when none
  * is ready (0: do not wait; <0: wait until all submitted inputs are done,
  * bounded by an internal limit). */
@@ -438,26 +454,37 @@ cufz_status cufz_poll_results(cufz_ctx* ctx, cufz_result* out, uint32_t max, uin
                               int32_t timeout_us);
 
 /* Copies the stored violation records of a completed, unreleased ticket
- * (in device write order; *n receives min(n_records, cap)). */
+ * (in device write order; *n receives min(n_records, cap)).  The records are
+ * what ASan reports per error (Sec. 2.1, Sec. 4), kept for every violating
+ * access up to the record cap instead of only the first. */
 cufz_status cufz_get_records(cufz_ctx* ctx, uint64_t ticket, cufz_violation* out, uint32_t cap,
                              uint32_t* n);
 
 /* Copies the 64 KiB bucketed edge bitmap of a completed, unreleased ticket
- * (needs CUFZ_CF_KEEP_BITMAPS). */
+ * (needs CUFZ_CF_KEEP_BITMAPS): the AFL coverage map of one execution
+ * (Sec. 2.1, the payload's hit counts, bucketed as AFL classifies them). */
 cufz_status cufz_get_bitmap(cufz_ctx* ctx, uint64_t ticket, uint8_t* out65536);
 
-/* Copies the device union bitmap (OR of every completed input's bitmap). */
+/* Copies the device union bitmap (OR of every completed input's bitmap):
+ * the fuzzer's record of coverage seen so far, which decides whether an
+ * input found new paths (Sec. 2.1, the fitness of AFL's genetic loop). */
 cufz_status cufz_get_union(cufz_ctx* ctx, uint8_t* out65536);
 
 /* Waits for all in-flight inputs, then snapshots the union: NEW_COV of later
  * inputs is measured against this snapshot, which keeps it independent of
- * completion order.  The first epoch's snapshot is empty. */
+ * completion order.  The first epoch's snapshot is empty.  (AFL compares
+ * each execution with the coverage seen before it, Sec. 2.1; a batch of
+ * concurrent executions compares with the state at its epoch's start.) */
 cufz_status cufz_new_epoch(cufz_ctx* ctx);
 
-/* Frees the slot of a completed ticket (records and bitmap go with it). */
+/* Frees the slot of a completed ticket (records and bitmap go with it).
+ * No counterpart in the paper (each execution there is a forked child
+ * whose memory goes when it exits, Sec. 2.1). */
 cufz_status cufz_release(cufz_ctx* ctx, uint64_t ticket);
 
-/* Waits until every submitted input has completed (bounded). */
+/* Waits until every submitted input has completed (bounded).  No
+ * counterpart in the paper (its runtime runs each execution to completion,
+ * Sec. 4). */
 cufz_status cufz_sync(cufz_ctx* ctx, int32_t timeout_us);
 
 /* Compiles every loaded program to sm_103a code with the runtime compiler
@@ -488,10 +515,10 @@ cufz_status cufz_get_stats(cufz_ctx* ctx, cufz_stats* out);
 cufz_status cufz_reset_stats(cufz_ctx* ctx);
 
 /* Checked execution of one input without any device allocation, for callers
- * that cannot allocate device memory: code running while a CUDA graph is
- * captured, plugins whose host framework owns every allocation, services
- * that must not grow their device footprint.  The paper has no counterpart
- * (its runtime is a CPU process).
+ * that cannot allocate device memory: plugins whose host framework owns
+ * every device allocation and hands out only the buffers of a call, and
+ * services that must not grow their device footprint after start-up.  The
+ * paper has no counterpart (its runtime is a CPU process).
  *
  * Runs `input` of the program (bytes, nbytes) on the current device with
  * the bytecode interpreter, exactly as a context would (pruned unless flags
@@ -505,9 +532,10 @@ cufz_status cufz_reset_stats(cufz_ctx* ctx);
  *
  * Scratch memory is a fixed 2 MiB array inside this library, held by every
  * GPU that loads it until the process exits; nothing is allocated.  The
- * first call on a device looks up the array's device address (keep that
- * first call outside any stream capture).  Programs whose loaded form
- * exceeds 64 KiB are rejected with CUFZ_E_NOMEM.  Every call shares the
+ * first call on a device looks up the array's device address; make that
+ * first call before any stream capture.  Programs whose loaded form
+ * exceeds 64 KiB are rejected with CUFZ_E_NOMEM (every valid program's
+ * loaded form is smaller: at most about 34 KB for 2,048 ops).  Every call shares the
  * array (what must start at zero is cleared per call): calls that overlap
  * on the GPU -- from several host threads or streams -- race and must be
  * serialised by the caller. */

@@ -40,7 +40,7 @@
  *     (Sec. 7.1, 10 s per execution): a thread whose back-edge count exceeds
  *     it stops, and the input is flagged BUDGET.
  *   - Launch configurations that CUDA rejects are not run and get status
- *     INVALID_CONFIG (Sec. 3.3.1, cudaErrorInvalidConfiguration); a grid of
+ *     INVALID_CONFIG (Sec. 2.3.1, cudaErrorInvalidConfiguration); a grid of
  *     zero blocks or threads is such a configuration (Sec. 7.3 reports the
  *     paper's own runtime dividing by a zero task count).
  *

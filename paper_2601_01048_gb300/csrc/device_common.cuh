@@ -13,7 +13,7 @@ constexpr uint32_t FULL = 0xFFFFFFFFu;
 constexpr uint32_t kFlagEngineError = 0x80000000u;
 constexpr uint32_t kHashCountMask = 0x7FFFu;
 constexpr int kHashTagShift = 15;
-constexpr uint32_t kInputSmemBytes = 576;  // sizeof(DevInput)
+constexpr uint32_t kInputSmemBytes = sizeof(DevInput);  // a CTA's staged input
 
 static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
   // MurmurHash3 fmix32 finalizer

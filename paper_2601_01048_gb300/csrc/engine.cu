@@ -59,7 +59,7 @@ __global__ void __launch_bounds__(1024) interp_kernel(EngineTables T, BatchHdr* 
 template __global__ void interp_kernel<true>(EngineTables, BatchHdr*, uint32_t, uint32_t, uint32_t);
 template __global__ void interp_kernel<false>(EngineTables, BatchHdr*, uint32_t, uint32_t, uint32_t);
 
-static uint32_t smem_bytes_for(const LaunchShape& s) {
+uint32_t interp_smem_bytes(const LaunchShape& s) {
   return kEdgeSmemBytes + s.max_prog_bytes + kInputSmemBytes +
          (s.cta_threads / 32) * s.max_regs * kRegStride;
 }
@@ -83,14 +83,14 @@ cudaError_t persistent_occupancy(uint32_t cta_threads, uint32_t smem_bytes, int*
 
 cudaError_t launch_persistent(const EngineTables& T, const BatchHdr* d_batch, const LaunchShape& s,
                               cudaStream_t st) {
-  interp_kernel<true><<<s.ctas, s.cta_threads, smem_bytes_for(s), st>>>(
+  interp_kernel<true><<<s.ctas, s.cta_threads, interp_smem_bytes(s), st>>>(
       T, const_cast<BatchHdr*>(d_batch), 0u, s.max_regs, s.max_prog_bytes);
   return cudaGetLastError();
 }
 
 cudaError_t launch_plain(const EngineTables& T, const BatchHdr* d_batch, uint32_t input_index,
                          uint32_t n_blocks_grid, const LaunchShape& s, cudaStream_t st) {
-  interp_kernel<false><<<n_blocks_grid, s.cta_threads, smem_bytes_for(s), st>>>(
+  interp_kernel<false><<<n_blocks_grid, s.cta_threads, interp_smem_bytes(s), st>>>(
       T, const_cast<BatchHdr*>(d_batch), input_index, s.max_regs, s.max_prog_bytes);
   return cudaGetLastError();
 }

@@ -43,6 +43,12 @@ bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
 // such inputs complete as CUFZ_ST_INVALID_CONFIG without running.
 bool launch_rejected(const cufz_input& in);
 
+// Whether a launch CUDA accepts has at most max_threads test threads; if so
+// their number goes to *n_threads (when not null).  The block count is
+// compared with max_threads / (threads per block) before any product, so a
+// grid whose thread count would wrap 64 bits is refused, not wrapped.
+bool launch_within(const cufz_input& in, uint64_t max_threads, uint64_t* n_threads);
+
 // The part of a DevInput that follows from the input and its program: launch
 // shape, division magics, arguments, buffer lengths, redzone-separated
 // virtual bases (per space: base_0 = R, base_k+1 = align256(base_k + len_k
@@ -89,6 +95,11 @@ struct LaunchShape {
   uint32_t max_regs;     // register-file registers per lane to reserve
   uint32_t max_prog_bytes;
 };
+
+// Dynamic shared memory of an interpreter launch of shape s: the CTA's
+// edge table, the staged program, the staged input and the warps' register
+// files.
+uint32_t interp_smem_bytes(const LaunchShape& s);
 
 cudaError_t launch_persistent(const EngineTables& T, const BatchHdr* d_batch, const LaunchShape& s,
                               cudaStream_t st);

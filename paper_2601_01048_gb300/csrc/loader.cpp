@@ -1098,6 +1098,16 @@ bool launch_rejected(const cufz_input& in) {
   return g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535;
 }
 
+bool launch_within(const cufz_input& in, uint64_t max_threads, uint64_t* n_threads) {
+  // blocks < 2^31 * 2^16 * 2^16 = 2^63 fits 64 bits; the product with the
+  // block size (<= 1024) is formed only once it cannot exceed max_threads
+  const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
+  const uint64_t nb = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2];
+  if (T == 0 || nb > max_threads / T) return false;
+  if (n_threads) *n_threads = nb * T;
+  return true;
+}
+
 void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
                     DevInput* d) {
   memset(d, 0, sizeof(*d));
@@ -1108,7 +1118,10 @@ void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask,
   for (int k = 0; k < 4; k++) d->args[k] = in.args[k];
   const uint32_t Bx = in.block[0], By = in.block[1], Bz = in.block[2];
   d->T = Bx * By * Bz;
-  d->n_threads = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * d->T;
+  // callers pass inputs that launch_within() accepted; anything larger would
+  // wrap, so it is stored as 0 threads rather than as a wrapped count
+  uint64_t nt = 0;
+  d->n_threads = launch_within(in, ~0ull, &nt) ? nt : 0;
   d->mT = div_magic(d->T);
   d->Bx = Bx;
   d->mBx = div_magic(Bx);

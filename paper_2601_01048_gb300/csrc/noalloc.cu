@@ -1,16 +1,17 @@
 // Allocation-free entry point: one checked execution of one input with all
 // of the engine's scratch memory in a fixed device array of this library.
 //
-// Some callers cannot allocate device memory at all: code that runs while a
-// CUDA graph is being captured (cudaMalloc is not capturable), plugins whose
-// host framework owns every device allocation and hands out only the buffers
-// of a call, and services that must not grow their device footprint after
+// Some callers cannot allocate device memory at all: plugins whose host
+// framework owns every device allocation and hands out only the buffers of
+// one call, and services that must not grow their device footprint after
 // start-up.  They cannot create a context (which sub-allocates an arena the
 // caller owns), so this entry point takes only the buffers of the call --
 // the input record, the record, bitmap and result outputs -- and keeps the
 // scratch (edge counters, touched-edge list, union maps, slot state, the
 // loaded program and the work items) in `g_noalloc_scratch`, a file-scope
 // __device__ array that every GPU loading this library holds until exit.
+// The first call on a device looks up the array's device address (the
+// host-side name of a __device__ variable is not a device address).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -79,17 +80,18 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
     LoadedProgram* p;
     ~Freer() { free_program(p); }
   } freer{&P};
-  if (P.blob_bytes > kMaxProgBytes) return CUFZ_E_NOMEM;  // program too large for the scratch
+  // a valid program's loaded form is at most about 34 KB (2,048 ops of 16
+  // bytes, header, LOC table, zero list), so this only guards the limit
+  if (P.blob_bytes > kMaxProgBytes) return CUFZ_E_NOMEM;
 
   cufz_result r0;
   memset(&r0, 0, sizeof(r0));
   r0.user_tag = input->user_tag;
   r0.first_key = ~0ull;
-  uint64_t T = (uint64_t)input->block[0] * input->block[1] * input->block[2];
-  uint64_t nb = (uint64_t)input->grid[0] * input->grid[1] * input->grid[2];
+  uint64_t n_threads = 0;
   int32_t status = CUFZ_ST_OK;
   if (launch_rejected(*input)) status = CUFZ_ST_INVALID_CONFIG;
-  else if (nb * T > (1ull << 31)) status = CUFZ_ST_LIMIT;
+  else if (!launch_within(*input, 1ull << 31, &n_threads)) status = CUFZ_ST_LIMIT;
   for (uint32_t k = 0; k < P.n_bufs && status == CUFZ_ST_OK; k++)
     if (input->buf_len[k] >= (1ull << 48)) status = CUFZ_ST_LIMIT;
   if (status != CUFZ_ST_OK) {
@@ -106,7 +108,6 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
     return CUFZ_E_CUDA;
   }
   // the batch image: header, the one input, its work items
-  const uint64_t n_threads = nb * T;
   uint64_t item = std::max<uint64_t>(2048, (n_threads + kMaxItems - 1) / kMaxItems);
   item = (item + 31) / 32 * 32;
   const uint32_t n_items = (uint32_t)((n_threads + item - 1) / item);
@@ -158,8 +159,7 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
   shape.cta_threads = 256;
   shape.max_regs = P.hdr.n_regs;
   shape.max_prog_bytes = (P.blob_bytes + 15u) & ~15u;
-  const uint32_t smem = kEdgeSmemBytes + shape.max_prog_bytes + 576 +
-                        (shape.cta_threads / 32) * shape.max_regs * kRegStride;
+  const uint32_t smem = interp_smem_bytes(shape);
   cudaError_t e = cudaSuccess;
   // raise (never lower) the kernel's dynamic shared memory limit
   cudaFuncAttributes fa;

@@ -778,10 +778,7 @@ bool prex_run(const Ir& ir, const cufz_input& in, uint32_t budget) {
 // Launches the engine runs at all: valid shapes of at most 2^31 threads
 // (their linear thread ids fit 32 bits).
 bool prex_launch_ok(const cufz_input& in) {
-  if (launch_rejected(in)) return false;
-  const uint64_t nt = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2] * in.block[0] * in.block[1] *
-                      in.block[2];
-  return nt <= (1ull << 31);
+  return !launch_rejected(in) && launch_within(in, 1ull << 31, nullptr);
 }
 
 bool prex_input_ok(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget) {

@@ -218,7 +218,9 @@ void harvest(cufz_ctx* c) {
 }
 
 uint32_t smem_for(const LaunchShape& s, uint32_t cta_threads) {
-  return kEdgeSmemBytes + s.max_prog_bytes + 576 + (cta_threads / 32) * s.max_regs * kRegStride;
+  LaunchShape t = s;
+  t.cta_threads = cta_threads;
+  return interp_smem_bytes(t);
 }
 
 // Sets the kernels' dynamic shared memory limit to what the persistent shape
@@ -839,8 +841,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     if (x.program_id >= c->progs.size() || !c->prog_live[x.program_id]) status = CUFZ_ST_BAD_PROGRAM;
     else if (launch_rejected(x)) status = CUFZ_ST_INVALID_CONFIG;
     else {
-      uint64_t nt = (uint64_t)x.grid[0] * x.grid[1] * x.grid[2] * x.block[0] * x.block[1] * x.block[2];
-      if (nt > c->cfg.max_threads) status = CUFZ_ST_LIMIT;
+      if (!launch_within(x, c->cfg.max_threads, nullptr)) status = CUFZ_ST_LIMIT;
       const LoadedProgram& P = c->progs[x.program_id];
       for (uint32_t k = 0; k < P.n_bufs; k++)
         if (x.buf_len[k] >= (1ull << 48)) status = CUFZ_ST_LIMIT;

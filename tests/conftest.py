@@ -17,11 +17,13 @@ def pytest_configure(config):
 
 def pytest_collection_modifyitems(config, items):
     """The PREX, division-fault, heap-fault and barrier tests, then the
-    full-size workload tests, run last: the first four cover the newest
-    device and runtime code, the last take the longest, and the established
-    parity tests should report first."""
+    full-size workload tests, run after the established parity tests (the
+    first four cover the newest device and runtime code, the full-size ones
+    take the longest).  The allocation-free entry point's tests come last of
+    all, so a run that stops at its first failure has run every other test
+    before them."""
     late = ("test_gpu_prex", "test_gpu_divfault", "test_gpu_heap", "test_gpu_barrier",
-            "test_gpu_fullsize")
+            "test_gpu_fullsize", "test_zz_no_alloc")
     items.sort(key=lambda item: next((k + 1 for k, f in enumerate(late) if f in item.nodeid), 0))
 
 

@@ -248,7 +248,7 @@ def test_edge_cases(B, orc, path):
     A.endloop()
     p_nested = A.build()
     progs = [p_nested, gen.c1_program()]
-    ins = gen.make_inputs(9)
+    ins = gen.make_inputs(10)
     gen.set_input(ins[0], 0, (3, 2, 2), (5, 3, 4), (7, 4), (5, 24))
     gen.set_input(ins[1], 0, (1, 1, 1), (1, 1, 1), (9, 5), (0, 0))
     gen.set_input(ins[2], 0, (7, 1, 3), (33, 1, 2), (9, 5), (1000, 40))
@@ -258,6 +258,8 @@ def test_edge_cases(B, orc, path):
     gen.set_input(ins[6], 1, (1 << 16, 1, 1), (1024, 1, 1), (0, 1), (4, 4, 4, 4))
     gen.set_input(ins[7], 1, (1, 1, 1), (1, 1, 1), (0, 1), (1 << 48, 4, 4, 4))
     gen.set_input(ins[8], 0, (2, 2, 2), (4, 4, 4), (9, 5), (3, 17))
+    # a shape CUDA accepts whose thread count wraps 64 bits to 88,342,528
+    gen.set_input(ins[9], 1, (72093556, 65352, 65000), (1024, 1, 1), (0, 1), (4, 4, 4, 4))
     cap = 64
     for budget in (4096, 12):
         with B.Engine(record_cap=cap, iter_budget=budget, max_threads=1 << 24, max_slots=64,
@@ -278,6 +280,7 @@ def test_edge_cases(B, orc, path):
                 [orecs[k] for k in keep], obms[sub], cap)
         assert int(dres[5]["status"]) == B.ST_BAD_PROGRAM
         assert int(dres[6]["status"]) == B.ST_LIMIT and int(dres[7]["status"]) == B.ST_LIMIT
+        assert int(dres[9]["status"]) == B.ST_LIMIT and int(dres[9]["n_accesses"]) == 0
         assert int(dres[3]["flags"]) & B.FL_OVERFLOW and int(dres[3]["n_records"]) == cap
         if budget == 12:
             assert int(dres[0]["flags"]) & B.FL_BUDGET

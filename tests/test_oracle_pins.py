@@ -249,11 +249,18 @@ def test_invalid_launch_configs(orc, grid, block):
     assert int(res["n_accesses"]) == 0 and not bm.any()
 
 
+WRAPPING_GRID = (72093556, 65352, 65000)
+
+
 def test_limit_status(orc):
     o = orc.opts(max_threads=1000)
     res, _, _ = orc.run(unguarded_1d(), mk((4, 1, 1), (256, 1, 1), (0,), (4,)), o)
     assert int(res["status"]) == orc.ST_LIMIT
     res, _, _ = orc.run(unguarded_1d(), mk((1, 1, 1), (1, 1, 1), (0,), (1 << 48,)))
+    assert int(res["status"]) == orc.ST_LIMIT
+    # a shape CUDA accepts whose thread count (about 3e20) wraps 64 bits to
+    # 88,342,528: above every limit, so LIMIT, never run as the wrapped count
+    res, _, _ = orc.run(unguarded_1d(), mk(WRAPPING_GRID, (1024, 1, 1), (0,), (4,)))
     assert int(res["status"]) == orc.ST_LIMIT
 
 

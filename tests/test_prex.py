@@ -485,7 +485,8 @@ def test_no_plan_for_launches_the_engine_does_not_run():
     threads as LIMIT without running, so neither has a plan."""
     prog = gen.c1_program()
     for grid, block in (((0, 1, 1), (32, 1, 1)), ((4, 1, 1), (0, 1, 1)), ((1, 1, 1), (2048, 1, 1)),
-                        ((1, 70000, 1), (1, 1, 1)), ((2**31 - 1, 1, 1), (1024, 1, 1))):
+                        ((1, 70000, 1), (1, 1, 1)), ((2**31 - 1, 1, 1), (1024, 1, 1)),
+                        ((72093556, 65352, 65000), (1024, 1, 1))):  # thread count wraps 2^64
         inp = mk(grid, block, (0, 100), (400, 400, 400, 400))
         assert B.cufz_prex_plan(prog, inp) is None, (grid, block)
         assert not B.cufz_prex_check(prog, inp), (grid, block)
