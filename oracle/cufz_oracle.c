@@ -155,7 +155,8 @@ typedef struct {
   uint32_t flags;
   uint64_t n_accesses, n_violations, first_key, digest, n_branch, n_threads;
   uint32_t n_records, n_edges;
-} orc_result; /* 64 bytes */
+  uint64_t n_ops; /* executed value ops, see exec_range */
+} orc_result; /* 72 bytes */
 
 typedef struct {
   uint32_t block_lin, thread_lin, ordinal;
@@ -444,7 +445,7 @@ typedef struct {
   int64_t len[ORC_MAX_BUFS], base[ORC_MAX_BUFS];
   int32_t sreg[16];
   int32_t r[256];
-  uint32_t block_lin, thread_lin, ordinal, prev_loc, th;
+  uint32_t block_lin, thread_lin, ordinal, prev_loc;
   uint32_t h; /* the thread's digest state H */
   uint64_t backedges;
   int stopped;
@@ -652,6 +653,12 @@ static int32_t alu(int op, int32_t x, int32_t y) {
   return 0;
 }
 
+/* Runs ops [pc, end) of the current thread.  n_ops counts the executed ops
+ * that compute a value or make a check other than an access: IMM, MOV, SEL,
+ * the ALU ops, DIV / REM, HALLOC and HFREE.  SREG (reading a launch
+ * coordinate or an argument) and NOP are not counted, nor are accesses,
+ * branches and loop heads, which have counts of their own.  On a pruned
+ * program this is the work left after MathElimination (Sec. 5.2). */
 static void exec_range(orc_ctx* c, int pc, int end) {
   const orc_prog* P = c->P;
   int32_t* r = c->r;
@@ -660,25 +667,31 @@ static void exec_range(orc_ctx* c, int pc, int end) {
     int opc = o->opc;
     if (opc >= 0x10 && opc <= 0x1F) {
       r[o->dst] = alu(opc, r[o->a], r[o->b]);
+      c->res->n_ops++;
       pc++;
       continue;
     }
     if (opc >= 0x30 && opc <= 0x3F) {
       r[o->dst] = alu(opc - 0x20, r[o->a], o->imm);
+      c->res->n_ops++;
       pc++;
       continue;
     }
     switch (opc) {
       case OP_NOP: pc++; break;
       case OP_SREG: r[o->dst] = c->sreg[o->imm]; pc++; break;
-      case OP_IMM: r[o->dst] = o->imm; pc++; break;
-      case OP_MOV: r[o->dst] = r[o->a]; pc++; break;
-      case OP_SEL: r[o->dst] = r[o->a] != 0 ? r[o->b] : r[o->imm]; pc++; break;
+      case OP_IMM: r[o->dst] = o->imm; c->res->n_ops++; pc++; break;
+      case OP_MOV: r[o->dst] = r[o->a]; c->res->n_ops++; pc++; break;
+      case OP_SEL:
+        r[o->dst] = r[o->a] != 0 ? r[o->b] : r[o->imm];
+        c->res->n_ops++;
+        pc++;
+        break;
       case OP_LD: r[o->dst] = do_access(c, o, 0); pc++; break;
       case OP_DIV:
-      case OP_REM: r[o->dst] = do_divide(c, o); pc++; break;
-      case OP_HALLOC: r[o->dst] = do_alloc(c, o); pc++; break;
-      case OP_HFREE: do_free(c, o); pc++; break;
+      case OP_REM: r[o->dst] = do_divide(c, o); c->res->n_ops++; pc++; break;
+      case OP_HALLOC: r[o->dst] = do_alloc(c, o); c->res->n_ops++; pc++; break;
+      case OP_HFREE: do_free(c, o); c->res->n_ops++; pc++; break;
       case OP_HLD: do_heap_access(c, o, 0); r[o->dst] = 0; pc++; break;
       case OP_HST: do_heap_access(c, o, 1); pc++; break;
       case OP_ST: (void)do_access(c, o, 1); pc++; break;
@@ -751,7 +764,6 @@ static void thread_start(orc_ctx* c, uint64_t bl, uint64_t tl, uint32_t bx, uint
   c->backedges = 0;
   c->stopped = 0;
   memset(c->hstate, 0, (size_t)P->n_alloc);
-  c->th = fmix32((uint32_t)bl * 0x9E3779B1u + (uint32_t)tl);
   c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
 }
 

@@ -26,9 +26,9 @@ LIB = os.path.join(BUILD_DIR, "libcufz_oracle.so")
 RESULT_DTYPE = np.dtype([
     ("status", "<i4"), ("flags", "<u4"), ("n_accesses", "<u8"), ("n_violations", "<u8"),
     ("first_key", "<u8"), ("digest", "<u8"), ("n_branch", "<u8"), ("n_threads", "<u8"),
-    ("n_records", "<u4"), ("n_edges", "<u4"),
+    ("n_records", "<u4"), ("n_edges", "<u4"), ("n_ops", "<u8"),
 ])
-assert RESULT_DTYPE.itemsize == 64
+assert RESULT_DTYPE.itemsize == 72
 
 RECORD_DTYPE = np.dtype([
     ("block_lin", "<u4"), ("thread_lin", "<u4"), ("ordinal", "<u4"), ("site", "<u2"),

@@ -141,8 +141,9 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
         CUFZ_ALU_CASES(A_SETNE, (int32_t)(x != y))
         CUFZ_ALU_CASES(A_SETLTU, (int32_t)(ux < uy))
 #undef CUFZ_ALU_CASES
-        case D_MOV:
+        case D_MOV:  // x = 1: a special-register read, not an executed op
           r = rf_ld(rf, op.a);
+          if (op.x) goto value_store;
           goto value_done;
         case D_IMM:
           r = op.imm;
@@ -155,10 +156,9 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
       }
       if (false) {
       value_done:
-        if (act) {
-          rf_st(rf, op.d, r);
-          acc.n_ops++;
-        }
+        if (act) acc.n_ops++;
+      value_store:
+        if (act) rf_st(rf, op.d, r);
         pc++;
         continue;
       }

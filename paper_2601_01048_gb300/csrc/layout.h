@@ -63,7 +63,9 @@ enum AluOp : uint8_t {
 
 // One device op, 16 bytes.  Register operands are byte offsets into the
 // warp's register file (register r -> r * 128).
-//   ALU/ALUI/MOV/IMM/SEL: d = dst, a, b (SEL: a cond, b x, imm = y offset)
+//   ALU/ALUI/MOV/IMM/SEL: d = dst, a, b (SEL: a cond, b x, imm = y offset);
+//                         MOV: x = 1 for a special-register read (not
+//                         counted in n_ops)
 //   LD/LDX/ST:            d = dst (LD), a = index, b = buffer, x = log2 width,
 //                         imm = access site
 //   IF:                   a = cond, x = branch site, j0 = pc when no lane enters

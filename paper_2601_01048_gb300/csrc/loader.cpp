@@ -508,6 +508,7 @@ struct Gen {
   int index;
   bool digest_ = true;
   bool rec_ = false;  // emitting the record function
+  bool no_counts_ = false;  // a loop body whose counts are added after the loop
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -588,7 +589,7 @@ struct Gen {
   // evaluation of the IF that ends it (always reached once the run starts:
   // a run holds no loop, so no budget stop)
   void run_counts(int ind, int pc, int end) {
-    if (rec_) return;
+    if (rec_ || no_counts_) return;
     const int k = run_ops(pc, end), m = run_acc(pc, end);
     int q = pc;
     while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
@@ -795,24 +796,35 @@ struct Gen {
         run_counts(ind, pc, end);
         continue;
       } else if (opc == B_LOOP && !rec_ && !has_branch_sites(pc + 1, o2.end_pc)) {
-        // a loop without branch sites in its body: its head edges in
-        // closed form after the loop (or at a budget stop inside it)
+        // A loop without branch sites in its body.  Its body is one
+        // straight-line run, so everything but the body's own values is
+        // known before it starts: the budget stop (each iteration ends with
+        // a back-edge; the thread stops at back-edge budget + 1, so a loop
+        // of trip iterations entered with `back` taken stops iff trip >
+        // budget - back, after budget - back + 1 bodies), the counts (the
+        // run's counts times the iterations) and the head edges (in closed
+        // form after the loop).  The body runs without per-iteration checks.
         has_loop = true;
-        const std::string t = "trip" + std::to_string(o2.site), n = "n" + std::to_string(o2.site);
+        const std::string sfx = std::to_string(o2.site);
+        const std::string t = "trip" + sfx, n = "n" + sfx, stop = "stop" + sfx, it = "it" + sfx;
         const std::string lt = hex32(ir.loc1[o2.site]), lf = hex32(ir.loc0[o2.site]);
         line(ind, "{");
         line(ind + 1, "const int32_t " + n + " = " + r(o2.a) + ";");
-        line(ind + 1, "const int32_t " + t + " = " + n + " < 0 ? 0 : (" + n + " > " +
-                          std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + " : " + n + ");");
-        const std::string stop = "stop" + std::to_string(o2.site);
-        line(ind + 1, "bool " + stop + " = false;");
+        line(ind + 1, "const uint32_t " + t + " = " + n + " < 0 ? 0u : (" + n + " > " +
+                          std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + "u : (uint32_t)" + n + ");");
+        line(ind + 1, "const bool " + stop + " = " + t + " > budget - back;");
+        line(ind + 1, "const uint32_t " + it + " = " + stop + " ? budget - back + 1u : " + t + ";");
         line(ind + 1, "#pragma unroll 1");
-        line(ind + 1, "for (" + r(o2.dst) + " = 0; " + r(o2.dst) + " < " + t + "; " + r(o2.dst) + "++) {");
+        line(ind + 1, "for (" + r(o2.dst) + " = 0; (uint32_t)" + r(o2.dst) + " < " + it + "; " + r(o2.dst) + "++) {");
+        no_counts_ = true;
         range(ind + 2, pc + 1, o2.end_pc);
-        line(ind + 2, "if (++back > budget) { " + stop + " = true; break; }");
+        no_counts_ = false;
         line(ind + 1, "}");
-        line(ind + 1, "jit_loop_cover(slot, prev, acc, " + stop + " ? (uint32_t)" + r(o2.dst) +
-                          " + 1u : (uint32_t)" + t + ", !" + stop + ", " + lt + ", " + lf + ");");
+        const int k = run_ops(pc + 1, o2.end_pc), m = run_acc(pc + 1, o2.end_pc);
+        if (k) line(ind + 1, "acc.n_ops += " + std::to_string(k) + "u * " + it + ";");
+        if (m) line(ind + 1, "acc.n_acc += " + std::to_string(m) + "u * " + it + ";");
+        line(ind + 1, "back += " + it + ";");
+        line(ind + 1, "jit_loop_cover(slot, prev, acc, " + it + ", !" + stop + ", " + lt + ", " + lf + ");");
         line(ind + 1, "if (" + stop + ") { acc.budget_hit = true; goto cufz_done; }");
         line(ind, "}");
         pc = o2.end_pc + 1;
@@ -1200,7 +1212,9 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
       d.d = off(o.dst); d.a = off(o.a); d.imm = o.imm;
     } else {
       switch (opc) {
-        case B_SREG: d.opc = D_MOV; d.d = off(o.dst); d.a = off(kSregBase + o.sreg); break;
+        case B_SREG:  // x = 1: not counted as an executed op
+          d.opc = D_MOV; d.d = off(o.dst); d.a = off(kSregBase + o.sreg); d.x = 1;
+          break;
         case B_IMM: d.opc = D_IMM; d.d = off(o.dst); d.imm = o.imm; break;
         case B_MOV: d.opc = D_MOV; d.d = off(o.dst); d.a = off(o.a); break;
         case B_SEL:

@@ -113,13 +113,15 @@ def alu(opc, x, y):
 def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
     """inp: dict(grid=(x,y,z), block=(x,y,z), args=[4], lens=[...]).
     Returns dict(status, flags, records=[tuple], counts={e: n}, digest,
-    n_accesses, n_violations, first_key, n_branch)."""
+    n_accesses, n_violations, first_key, n_branch, n_ops, traces), where
+    traces maps (block_lin, thread_lin) to the thread's accesses in order,
+    as (site, index) pairs."""
     P = parse(prog)
     g, b = inp["grid"], inp["block"]
     if 0 in g or 0 in b or b[0] > 1024 or b[1] > 1024 or b[2] > 64 or b[0] * b[1] * b[2] > 1024 \
             or g[0] > 2**31 - 1 or g[1] > 65535 or g[2] > 65535:
         return dict(status=2, flags=0, records=[], counts={}, digest=0, n_accesses=0,
-                    n_violations=0, first_key=M64, n_branch=0)
+                    n_violations=0, first_key=M64, n_branch=0, n_ops=0, traces={})
     lens = list(inp["lens"]) + [0] * 9
     shm = P["shmask"]
     base = {}
@@ -128,7 +130,10 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         sp = (shm >> k) & 1
         base[k] = nxt[sp]
         nxt[sp] = -(-(nxt[sp] + lens[k] + redzone) // 256) * 256
-    st = dict(records=[], counts={}, digest=0, n_accesses=0, n_branch=0, budget_hit=False)
+    # n_ops: executed ops that compute a value or make a non-access check
+    # (IMM, MOV, SEL, ALU, DIV/REM, HALLOC, HFREE); SREG reads do not count
+    st = dict(records=[], counts={}, digest=0, n_accesses=0, n_branch=0, n_ops=0,
+              budget_hit=False, traces={})
     smem = {}  # (buffer, byte offset) -> byte: the current block's stored shared bytes
 
     def classify(buf, off, w):
@@ -146,6 +151,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
     def run_thread(bl, tl, sregs):
         regs = [0] * max(P["n_regs"], 1)
         t = dict(ordinal=0, prev=0, back=0, stop=False, h=(bl * 0x9E3779B1 + tl) & M32)
+        trace = st["traces"].setdefault((bl, tl), [])
 
         def edge(site, out):
             cur = P["loc"][site][out]
@@ -157,6 +163,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         def mem(is_st, d, a, buf, w, site):
             off = regs[a] * w
             bad = off < 0 or off + w > lens[buf]
+            trace.append((site, regs[a]))
             k = ((site * 0xC2B2AE3D) & M32) | 1
             t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
             st["n_accesses"] += 1
@@ -209,6 +216,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
 
         def hmem(is_st, d, a, hreg, w, site):
             off = regs[a] * w
+            trace.append((site, regs[a]))
             k = ((site * 0xC2B2AE3D) & M32) | 1
             t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
             st["n_accesses"] += 1
@@ -234,6 +242,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 kind = s[0]
                 if kind == "op":
                     _, opc, d, a, bb, imm = s
+                    if opc in (0x02, 0x03, 0x04) or 0x10 <= opc <= 0x1F or 0x30 <= opc <= 0x3F:
+                        st["n_ops"] += 1
                     if opc == 0x01:
                         regs[d] = sregs[imm]
                     elif opc == 0x02:
@@ -252,8 +262,10 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 elif kind == "div":
                     _, is_rem, d, a, bb, site = s
                     divide(is_rem, d, a, bb, site)
+                    st["n_ops"] += 1
                 elif kind == "halloc":
                     _, d, a, site = s
+                    st["n_ops"] += 1
                     if regs[a] >= 1:
                         heap[site] = [regs[a], True]
                         regs[d] = site + 1
@@ -261,6 +273,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                         regs[d] = 0
                 elif kind == "hfree":
                     hfree(s[1], s[2])
+                    st["n_ops"] += 1
                 elif kind == "hmem":
                     _, is_st, d, a, hreg, w, site = s
                     hmem(is_st, d, a, hreg, w, site)
@@ -319,7 +332,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
     fk = min(((r[0] << 32) | (r[1] << 22) | min(r[2], (1 << 22) - 1) for r in recs), default=M64)
     return dict(status=1 if recs else 0, flags=1 if st["budget_hit"] else 0, records=recs,
                 counts=st["counts"], digest=st["digest"], n_accesses=st["n_accesses"],
-                n_violations=len(recs), first_key=fk, n_branch=st["n_branch"])
+                n_violations=len(recs), first_key=fk, n_branch=st["n_branch"],
+                n_ops=st["n_ops"], traces=st["traces"])
 
 
 def bitmap_of(counts: dict) -> dict:

@@ -55,3 +55,12 @@ def record_keys(recs):
         return []
     return sorted(zip(*(recs[c].tolist() for c in RECORD_KEYS)))
 
+
+
+def checks_of(res):
+    """Oracle results as bytes with the executed-op count cleared: every
+    field pruning must leave unchanged (pruning removes ops, never checks,
+    branches or their outcomes)."""
+    r = res.copy()
+    r["n_ops"] = 0
+    return r.tobytes()

@@ -10,8 +10,10 @@ lane, with the per-program paths the autotuner picks, as bench.py runs it.
     records (any record_cap of them when an input overflows) and bitmap.
   - Every input, at any size: the compiled and autotuned run equals a run of
     the bytecode interpreter alone (two independent engines) in status,
-    flags, every count, digest, first key, record count and bitmap; and
-    status, record count and OVERFLOW agree with the counts."""
+    flags, every count (the executed-op count n_ops, the roofline's largest
+    term, included), digest, first key, record count and bitmap; and
+    status, record count and OVERFLOW agree with the counts.  The sampled
+    inputs' n_ops also equals the oracle's count on the pruned program."""
 import hashlib
 import sys
 import os
@@ -26,7 +28,7 @@ pytestmark = pytest.mark.gpu
 SMALL = 1 << 15
 N_SAMPLED = 48
 FIELDS = ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch", "n_threads",
-          "n_edges", "n_records")
+          "n_edges", "n_records", "n_ops")
 
 
 @pytest.fixture(scope="module")
@@ -109,12 +111,14 @@ def test_full_size_workload(B, orc, name):
     # sampled outputs: the oracle, input by input
     sub = inputs[small]
     ores, orecs, obms = orc.run_batch(progs, sub, rec_cap=1 << 18, bitmaps=True)
+    pres, _, _ = orc.run_batch([B.cufz_prune_program(p)[0] for p in progs], sub)
     for j, i in enumerate(small.tolist()):
         d, o = dres[i], ores[j]
         for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                   "n_threads", "n_edges"):
             assert int(d[f]) == int(o[f]), (i, f)
         assert int(d["flags"]) & B.FL_BUDGET == int(o["flags"]) & B.FL_BUDGET, i
+        assert int(d["n_ops"]) == int(pres[j]["n_ops"]), i
         recs, bm = dkept[i]
         assert np.array_equal(bm, obms[j]), i
         n_o = int(o["n_violations"])

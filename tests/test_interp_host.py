@@ -23,7 +23,7 @@ import pytest
 
 from paper_2601_01048_gb300 import binding as B
 from paper_2601_01048_gb300 import build_ext, gen
-from test_jit_host import CSRC, RESULT, SAN, SHIM, _gxx, record_set, workload
+from test_jit_host import CSRC, RESULT, SAN, SHIM, _gxx, engine_ops, record_set, workload
 
 
 @pytest.fixture(scope="module")
@@ -79,12 +79,14 @@ def run(tmp_path, exe, progs, inputs, plans=None, cap=1 << 14, budget=4096, item
     return outs
 
 
-def compare(got, ores, orecs, obms, cap):
+def compare(got, ores, orecs, obms, cap, ops=None):
     for k, (res, recs, bm) in enumerate(got):
         o = ores[k]
         for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                   "n_edges", "n_threads"):
             assert int(res[f]) == int(o[f]), (k, f)
+        if ops is not None:
+            assert int(res["n_ops"]) == ops[k], k
         assert int(res["flags"]) & B.FL_BUDGET == int(o["flags"]) & B.FL_BUDGET, k
         assert bool(int(res["flags"]) & B.FL_OVERFLOW) == (int(o["n_violations"]) > cap), k
         n_o = int(o["n_violations"])
@@ -103,7 +105,7 @@ def test_interpreter_matches_oracle(tmp_path, interp_exe, orc, flags):
     progs, ins = workload()
     got = run(tmp_path, interp_exe, progs, ins, flags=flags)
     ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 17, bitmaps=True)
-    compare(got, ores, orecs, obms, 1 << 14)
+    compare(got, ores, orecs, obms, 1 << 14, engine_ops(orc, progs, ins, flags))
     assert 0 < sum(int(o["status"]) == 1 for o in ores) < len(ins)
 
 
@@ -125,7 +127,7 @@ def test_interpreter_budget_shapes_and_record_cap(tmp_path, interp_exe, orc):
         got = run(tmp_path, interp_exe, progs, ins, budget=budget, cap=cap)
         ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
                                           rec_cap=1 << 16, bitmaps=True)
-        compare(got, ores, orecs, obms, cap)
+        compare(got, ores, orecs, obms, cap, engine_ops(orc, progs, ins, 0, budget))
 
 
 def test_interpreter_prex_items(tmp_path, interp_exe, orc):
@@ -157,7 +159,7 @@ def test_interpreter_division_programs(tmp_path, interp_exe, orc, flags):
     for cap in (1 << 14, 8):
         got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
         ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
-        compare(got, ores, orecs, obms, cap)
+        compare(got, ores, orecs, obms, cap, engine_ops(orc, progs, ins, flags))
         assert sum(int((r["kind"] == 2).sum()) for _, r, _ in got) > 0
 
 
@@ -173,7 +175,7 @@ def test_interpreter_heap_programs(tmp_path, interp_exe, orc, flags):
     for cap in (1 << 14, 8):
         got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
         ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
-        compare(got, ores, orecs, obms, cap)
+        compare(got, ores, orecs, obms, cap, engine_ops(orc, progs, ins, flags))
         if cap > 8:
             assert sum(int((r["kind"] == 3).sum()) for _, r, _ in got) > 0
 
@@ -189,4 +191,4 @@ def test_interpreter_barrier_programs(tmp_path, interp_exe, orc, flags):
     for cap in (1 << 14, 8):
         got = run(tmp_path, interp_exe, progs, ins, cap=cap, flags=flags)
         ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
-        compare(got, ores, orecs, obms, cap)
+        compare(got, ores, orecs, obms, cap, engine_ops(orc, progs, ins, flags))

@@ -112,6 +112,15 @@ def run(tmp_path, exe, progs, inputs, plans=None, cap=1 << 14, budget=4096, item
     return outs
 
 
+def engine_ops(orc, progs, ins, flags=0, budget=4096):
+    """The executed-op count (n_ops) each input must report: the oracle's
+    count on the program the engine runs, i.e. the bytes cufz_prune_program
+    returns (the unpruned program under CF_NO_PRUNE)."""
+    run_progs = progs if flags & B.CF_NO_PRUNE else [B.cufz_prune_program(p)[0] for p in progs]
+    res, _, _ = orc.run_batch(run_progs, ins, orc.opts(iter_budget=budget))
+    return [int(v) for v in res["n_ops"]]
+
+
 def record_set(recs, fields=KEYS):
     return set(zip(*(recs[f].tolist() for f in fields)))
 
@@ -137,12 +146,15 @@ def test_generated_code_matches_oracle(tmp_path, host_objs, orc, flags):
     exe = build(tmp_path, host_objs, progs, flags)
     got = run(tmp_path, exe, progs, ins)
     ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
+    ops = engine_ops(orc, progs, ins, flags)
+    assert sum(ops) > 0
     n_viol = 0
     for k, (res, recs, bm) in enumerate(got):
         o = ores[k]
         for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                   "n_edges", "n_records", "n_threads"):
             assert int(res[f]) == int(o[f]), (k, f)
+        assert int(res["n_ops"]) == ops[k], k
         assert record_set(recs) == record_set(orecs[k][: int(o["n_records"])]), k
         assert np.array_equal(bm, obms[k]), k
         n_viol += int(o["status"]) == 1
@@ -172,9 +184,11 @@ def test_budget_stop_and_3d_shapes_match_oracle(tmp_path, host_objs, orc):
     got = run(tmp_path, exe, progs, ins, budget=3)
     ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=3), rec_cap=1 << 14,
                                       bitmaps=True)
+    ops = engine_ops(orc, progs, ins, budget=3)
     stopped = 0
     for k, (res, recs, bm) in enumerate(got):
         o = ores[k]
+        assert int(res["n_ops"]) == ops[k], k
         assert int(res["flags"]) & 1 == int(o["flags"]) & 1, k
         for f in ("n_accesses", "n_violations", "first_key", "digest", "n_branch", "n_edges"):
             assert int(res[f]) == int(o[f]), (k, f)
@@ -226,8 +240,10 @@ def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
         got = run(tmp_path, exe, progs, ins, budget=budget)
         ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
                                           rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, 0, budget)
         for i, (res, recs, bm) in enumerate(got):
             o = ores[i]
+            assert int(res["n_ops"]) == ops[i], (budget, i)
             for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                       "n_edges", "n_records"):
                 assert int(res[f]) == int(o[f]), (budget, i, f)
@@ -250,9 +266,11 @@ def test_division_programs_match_oracle(tmp_path, host_objs, orc, flags):
         got = run(tmp_path, exe, progs, ins, budget=budget)
         ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
                                           rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, flags, budget)
         faults = 0
         for i, (res, recs, bm) in enumerate(got):
             o = ores[i]
+            assert int(res["n_ops"]) == ops[i], (budget, i)
             for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                       "n_edges", "n_records"):
                 assert int(res[f]) == int(o[f]), (budget, i, f)
@@ -279,9 +297,11 @@ def test_heap_programs_match_oracle(tmp_path, host_objs, orc, flags):
         got = run(tmp_path, exe, progs, ins, budget=budget)
         ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
                                           rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, flags, budget)
         seen = set()
         for i, (res, recs, bm) in enumerate(got):
             o = ores[i]
+            assert int(res["n_ops"]) == ops[i], (budget, i)
             for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                       "n_edges", "n_records"):
                 assert int(res[f]) == int(o[f]), (budget, i, f)
@@ -307,8 +327,10 @@ def test_barrier_programs_match_oracle(tmp_path, host_objs, orc, flags):
         got = run(tmp_path, exe, progs, ins, budget=budget)
         ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
                                           rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, flags, budget)
         for i, (res, recs, bm) in enumerate(got):
             o = ores[i]
+            assert int(res["n_ops"]) == ops[i], (budget, i)
             for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
                       "n_edges", "n_records"):
                 assert int(res[f]) == int(o[f]), (budget, i, f)

@@ -455,6 +455,7 @@ def _compare_bruteforce(orc, prog, inp_kwargs, budget=4096):
     assert int(res["n_accesses"]) == ref["n_accesses"]
     assert int(res["n_branch"]) == ref["n_branch"]
     assert int(res["first_key"]) == ref["first_key"]
+    assert int(res["n_ops"]) == ref["n_ops"]
     assert int(res["flags"]) & 1 == ref["flags"]
     assert {int(e): int(bm[e]) for e in np.nonzero(bm)[0]} == bf.bitmap_of(ref["counts"])
 
@@ -773,3 +774,123 @@ def test_a_thread_stopped_by_the_budget_runs_no_later_phase(orc):
                            orc.opts(iter_budget=3), rec_cap=64)
     assert [(int(r["thread_lin"]), int(r["byte_off"])) for r in recs] == [(1, -4), (2, -4), (3, -4)]
     assert int(res["flags"]) & orc.FL_BUDGET and int(res["n_accesses"]) == 3
+
+
+# ---------------------------------------------------------------- digest and op count
+
+def test_digest_hand_derived_golden(orc):
+    """The digest, op count, edges and first key of a tiny program equal the
+    values worked out by hand in tests/golden/digest_tiny.txt."""
+    want = {k: int(v) for k, v in golden("digest_tiny.txt")}
+    A = Asm(n_bufs=2, seed=0x7E57)
+    tx = A.sreg(bc.TID_X)
+    i0 = A.alu(bc.ADD, A.alu(bc.MUL, tx, Imm(3)), Imm(5))
+    A.ld(0, i0, 4)
+    n = A.sreg(bc.ARG0)
+    c = A.loop(n, 4)
+    A.ld(1, c, 1)
+    A.endloop()
+    prog = A.build(loc=[(0x1234, 0xABCD)])
+    inp = mk((1, 1, 1), (2, 1, 1), (2,), (64, 1))
+    res, recs, bm = orc.run(prog, inp)
+    for k in ("digest", "n_ops", "n_accesses", "n_branch", "n_violations", "first_key"):
+        assert int(res[k]) == want[k], k
+    edges = {int(k[5:], 16): v for k, v in want.items() if k.startswith("edge_")}
+    assert {int(e): int(bm[e]) for e in np.nonzero(bm)[0]} == edges
+    assert rec_tuples(recs[:2]) == [(0, 0, 2, 1, 1, 0, 1, 0, 2, 1), (0, 1, 2, 1, 1, 0, 1, 0, 2, 1)]
+
+
+def test_digest_changes_with_each_access(orc):
+    """One changed index, two accesses in swapped order, one access dropped:
+    each changes D (a constant or order-free digest would fail here)."""
+    def prog(index_plus=0, order=("x", "i0"), drop=False):
+        A = Asm(n_bufs=2, seed=0x7E57)
+        tx = A.sreg(bc.TID_X)
+        i0 = A.alu(bc.ADD, A.alu(bc.MUL, tx, Imm(3)), Imm(5))
+        x = A.alu(bc.ADD, tx, Imm(1))
+        regs = dict(x=x, i0=i0)
+        for name in order:
+            if not (drop and name == "x"):
+                A.ld(0, regs[name], 4)
+        n = A.sreg(bc.ARG0)
+        c = A.loop(n, 4)
+        A.ld(1, A.alu(bc.ADD, c, Imm(index_plus)) if index_plus else c, 1)
+        A.endloop()
+        return A.build(loc=[(0x1234, 0xABCD)])
+
+    inp = mk((2, 1, 1), (3, 1, 1), (2,), (64, 4))
+    base = orc.run(prog(), inp)[0]
+    variants = {"index": prog(index_plus=1), "swap": prog(order=("i0", "x")),
+                "drop": prog(drop=True)}
+    for name, p in variants.items():
+        r = orc.run(p, inp)[0]
+        assert int(r["digest"]) != int(base["digest"]), name
+        # each variant is also what the independent evaluator computes
+        ref = bf.evaluate(p, dict(grid=(2, 1, 1), block=(3, 1, 1), args=[2, 0, 0, 0],
+                                  lens=[64, 4]))
+        assert int(r["digest"]) == ref["digest"], name
+    assert int(orc.run(variants["drop"], inp)[0]["n_accesses"]) == int(base["n_accesses"]) - 6
+
+
+def _ops_of(prog):
+    return [prog[32 + 4 * bc.decode_header(prog)["n_sites"] + 8 * k:][:8]
+            for k in range(bc.decode_header(prog)["n_ops"])]
+
+
+def _rebuild(prog, ops):
+    h = bytearray(prog[:32 + 4 * bc.decode_header(prog)["n_sites"]])
+    h[6:8] = len(ops).to_bytes(2, "little")
+    return bytes(h) + b"".join(ops)
+
+
+@pytest.mark.parametrize("index", range(6))
+def test_digest_sensitivity_on_random_programs(orc, index):
+    """Random programs with one store dropped, or two adjacent stores
+    swapped: whenever some thread's sequence of (site, index) changes (by
+    the independent evaluator's trace), the oracle's digest changes, and it
+    stays the same when no sequence changes."""
+    prog = gen.c2_program(40 + index)
+    ops = _ops_of(prog)
+    st = [k for k, o in enumerate(ops) if o[0] == bc.ST]
+    h = bc.decode_header(prog)
+    rng = gen.SplitMix64(4000 + index)
+    lens = [rng.choice((16, 64, 256, 1024)) for _ in range(h["n_bufs"])]
+    args = [rng.choice((0, 1, 3, 16, -7)) for _ in range(4)]
+    kw = dict(grid=(2, 1, 1), block=(3, 2, 1), args=args, lens=lens)
+    inp = mk(**kw)
+    base_d = int(orc.run(prog, inp)[0]["digest"])
+    base_t = bf.evaluate(prog, dict(kw, args=args + [0] * 4))["traces"]
+    variants = [ops[:k] + ops[k + 1:] for k in st[:4]]
+    variants += [ops[:k] + [ops[k + 1], ops[k]] + ops[k + 2:] for k in st if k + 1 in st][:4]
+    changed = 0
+    for v in variants:
+        p = _rebuild(prog, v)
+        assert orc.validate(p) == 0
+        d = int(orc.run(p, inp)[0]["digest"])
+        t = bf.evaluate(p, dict(kw, args=args + [0] * 4))["traces"]
+        assert (d != base_d) == (t != base_t)
+        changed += t != base_t
+    assert changed >= 1
+
+
+def test_n_ops_closed_form(orc):
+    """Executed ops: a loop of trip t with k ops in its body runs k * t of
+    them, the ops of an IF arm run only in the threads taking it, SREG reads
+    and accesses are not ops, and a division is one."""
+    A = Asm(n_bufs=1)
+    tx = A.sreg(bc.TID_X)
+    n = A.sreg(bc.ARG0)
+    c = A.loop(n, 64)
+    v = A.alu(bc.ADD, c, tx)            # 3 ops per iteration
+    v = A.alu(bc.XOR, v, Imm(5))
+    A.ld(0, A.alu(bc.AND, v, Imm(3)), 4)
+    A.endloop()
+    A.if_(A.alu(bc.SETLT, tx, Imm(2)))  # 1 op per thread (the condition)
+    A.imm(7)                            # 1 op in threads 0 and 1
+    A.div(tx, tx)                       # 1 op in threads 0 and 1
+    A.endif()
+    prog = A.build()
+    for t in (0, 1, 5, 64, 100):
+        res = orc.run(prog, mk((1, 1, 1), (8, 1, 1), (t,), (16,)))[0]
+        trip = min(t, 64)
+        assert int(res["n_ops"]) == 8 * 3 * trip + 8 + 2 * 2, t
