@@ -129,6 +129,9 @@ def parse_args():
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the load-time path choice (for profiling a single launch)")
     ap.add_argument("--item-threads", type=int, default=0)
+    ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: occupancy)")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="default run: leave out the other configurations' sub-records")
     return ap.parse_args()
 
 
@@ -314,33 +317,69 @@ def oracle_rate(progs, inputs, seconds: float, seed: int = 11):
 
 # ------------------------------------------------------------------ engine arm
 
-def run_engine(args, rank, world, local, pg):
+# Per workload, the autotuner's choices of this process (an autotune cache
+# file): the first context of a workload tunes, later ones load the choices.
+TUNE_FILES: dict[str, str] = {}
+TUNED: set[str] = set()
+
+
+def tune_file(key: str):
+    """(cache path, whether it already holds this workload's choices)."""
+    import tempfile
+
+    if key not in TUNE_FILES:
+        fd, path = tempfile.mkstemp(prefix=f"cufz_tune_{key}_", suffix=".txt")
+        os.close(fd)
+        os.unlink(path)
+        TUNE_FILES[key] = path
+        return path, False
+    return TUNE_FILES[key], True
+
+
+def autotune_or_load(B, E, key, sample, n_programs):
+    """Runs the autotuner for the workload's first context; later contexts
+    got the same choices from the cache at load.  Returns the number of
+    programs on the compiled path."""
+    if key not in TUNED:
+        TUNED.add(key)
+        return B.cufz_autotune(E.ctx, sample)
+    return sum(int(B.cufz_get_program_path(E.ctx, p)) for p in range(n_programs))
+
+
+def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world, local, pg,
+                   prex=False, cta_threads=None):
+    """One workload through the engine: warm-up steps, then `steps` timed
+    steps (each a whole batch: submit host input records, poll host result
+    records).  Returns the JSON line's fields (without the CPU baseline)."""
     import torch
 
     from paper_2601_01048_gb300 import binding as B
 
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
-    wl_name, progs, inputs, cap = workload(args.workload, rank)
+    wl_name, progs, inputs, cap = workload(wl_key, rank)
     n_all = len(inputs)
-    per_step = args.inputs_per_step or n_all
-    flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
-    if args.prex:
+    per_step = per_step_arg or n_all
+    cta = args.cta_threads if cta_threads is None else cta_threads
+    flags = B.CF_AUTO_RELEASE | B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if plain else 0)
+    if prex:
         flags |= B.CF_PREX
     if args.path == "jit":
         flags |= B.CF_JIT | (B.CF_JIT_FAST_COMPILE if args.jit_fast_compile else 0)
+    tune_path = tune_file(wl_key)[0] if args.path == "jit" and not args.no_autotune else None
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
-                 cta_threads=args.cta_threads, item_threads=args.item_threads, n_lanes=2,
-                 jit_min_ctas=args.jit_min_ctas)
+                 cta_threads=cta, item_threads=args.item_threads, n_lanes=2,
+                 jit_min_ctas=args.jit_min_ctas, ctas_per_sm=args.ctas_per_sm,
+                 autotune_cache=tune_path)
     for p in progs:
         E.load(p)
     tuned = None
-    if args.path == "jit" and not args.no_autotune:
+    if tune_path:
         # the project's autotuner: per program, compiled vs interpreted on a
         # sample of that program's inputs (up to eight per program)
         sample = np.concatenate([inputs[inputs["program_id"] == p][:8]
                                  for p in np.unique(inputs["program_id"])])
-        tuned = B.cufz_autotune(E.ctx, sample)
+        tuned = autotune_or_load(B, E, wl_key, sample, len(progs))
     n_batches = (n_all + per_step - 1) // per_step
     batches = [inputs[(k * per_step) % n_all: (k * per_step) % n_all + per_step]
                for k in range(n_batches)]
@@ -363,7 +402,7 @@ def run_engine(args, rank, world, local, pg):
                 got += len(out)
         return acc, lat
 
-    for k in range(args.warmup):
+    for k in range(warmup):
         step(k)
     torch.cuda.synchronize(dev)
     barrier(pg)
@@ -372,16 +411,18 @@ def run_engine(args, rank, world, local, pg):
     clocks.start()
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
-    tot = dict(acc=0, inputs=0, ops=0, br=0, viol=0, threads=0, partial=0, bug_inputs=0)
+    tot = dict(acc=0, inputs=0, ops=0, br=0, folded=0, viol=0, threads=0, partial=0,
+               bug_inputs=0)
     lats = []
     h2d = d2h = 0
-    for k in range(args.steps):
-        res, lat = step(args.warmup + k)
+    for k in range(steps):
+        res, lat = step(warmup + k)
         lats += lat
         tot["acc"] += int(res["n_accesses"].sum())
         tot["inputs"] += len(res)
         tot["ops"] += int(res["n_ops"].sum())
         tot["br"] += int(res["n_branch"].sum())
+        tot["folded"] += int(res["n_branch_folded"].sum())
         tot["viol"] += int(res["n_violations"].sum())
         tot["threads"] += int(res["n_threads"].sum())
         tot["partial"] += int(((res["flags"] & B.FL_PARTIAL) != 0).sum())
@@ -401,25 +442,25 @@ def run_engine(args, rank, world, local, pg):
     inputs_all = allreduce_sum(pg, tot["inputs"], dev)
     launches = int(st.kernel_launches)
     E.close()
-    try:
-        measured_peak = B.cufz_int32_peak(local, torch.cuda.current_stream(dev).cuda_stream)
-    except Exception:
-        measured_peak = None
 
     peaks = load_peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     n_sm = int(st.n_sms) or N_SM_GB300
     peak_ops = n_sm * LANES_PER_SM * sm_max * 1e6
     alg_ops = tot["ops"] + OPS_PER_ACCESS * tot["acc"] + OPS_PER_BRANCH * tot["br"]
+    # the same work with each closed-form loop-head evaluation credited as a
+    # share of the one edge update it took instead of an update of its own
+    alg_ops_folded = alg_ops - OPS_PER_BRANCH * tot["folded"]
     achieved = alg_ops / kernel_s if kernel_s > 0 else 0.0
-    line = {
+    s = max(steps, 1)
+    return {
         "metric": METRIC,
         "value": acc_all / kernel_s_max if kernel_s_max > 0 else 0.0,
         "unit": UNIT,
         "n_gpus": world,
-        "steps": args.steps,
-        "warmup": args.warmup,
-        "ms_per_step": kernel_s_max * 1e3 / args.steps,
+        "steps": steps,
+        "warmup": warmup,
+        "ms_per_step": kernel_s_max * 1e3 / s,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
@@ -428,7 +469,7 @@ def run_engine(args, rank, world, local, pg):
         "config": {
             "workload": wl_name,
             "inputs_per_step": per_step,
-            "path": ("plain one launch per input" if args.plain else
+            "path": ("plain one launch per input" if plain else
                      "persistent kernel in a CUDA graph"),
             "engine": ("programs compiled to sm_103a at load or interpreted, chosen per program "
                        "by the autotuner" if args.path == "jit" else "bytecode interpreter"),
@@ -438,38 +479,40 @@ def run_engine(args, rank, world, local, pg):
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),
             "record_cap": cap,
-            "l2": "no flush: every step writes one 64 KiB bitmap per input (>= 512 MiB for the "
-                  "default workload) plus edge counters and records, far above the 129 MB L2",
+            "l2": "no flush: every step writes one 64 KiB bitmap per input (>= 64 MiB per "
+                  "step, 512 MiB for the default workload) plus edge counters and records, "
+                  "and reads no input twice within a step",
             "parallelism": f"replicas x{world}",
         },
         "inputs_per_s": inputs_all / kernel_s_max if kernel_s_max > 0 else 0.0,
-        "violating_inputs_per_step": tot["bug_inputs"] // max(args.steps, 1),
-        "prex": ({"partial_inputs_per_step": tot["partial"] // max(args.steps, 1),
+        "violating_inputs_per_step": tot["bug_inputs"] // s,
+        "prex": ({"partial_inputs_per_step": tot["partial"] // s,
                   "note": "partial inputs ran only their PREX plan's threads (the corners, or for "
                           "guarded launches the corners of the cells the guards cut the grid "
                           "into); their verdict is the full grid's, their accesses are the "
                           "planned threads'"}
-                 if args.prex else None),
-        "test_threads_per_step": tot["threads"] // max(args.steps, 1),
-        "violations_per_step": tot["viol"] // max(args.steps, 1),
+                 if prex else None),
+        "test_threads_per_step": tot["threads"] // s,
+        "violations_per_step": tot["viol"] // s,
         "roofline": {
             "bound": "alu",
             "achieved": achieved / 1e12,
             "peak": peak_ops / 1e12,
             "unit": "Tops/s (int32 lane-ops)",
             "frac": achieved / peak_ops,
-            "traffic": measured_traffic(args, progs, per_step, n_all),
+            "traffic": None if plain else measured_traffic(args, progs, per_step, n_all),
             "kernel_key": kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3),
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
-            "alg_ops_per_step": alg_ops // max(args.steps, 1),
-            "measured_int32_peak": measured_peak / 1e12 if measured_peak else None,
-            "frac_of_measured": achieved / measured_peak if measured_peak else None,
+            "alg_ops_per_step": alg_ops // s,
+            "loop_heads_folded_per_step": tot["folded"] // s,
+            "frac_folded_heads_uncredited": (alg_ops_folded / kernel_s / peak_ops
+                                             if kernel_s > 0 else 0.0),
         },
         "e2e": {
             "value": acc_all / wall_s_max if wall_s_max > 0 else 0.0,
             "unit": UNIT,
-            "h2d_bytes_per_step": h2d // max(args.steps, 1),
-            "d2h_bytes_per_step": d2h // max(args.steps, 1),
+            "h2d_bytes_per_step": h2d // s,
+            "d2h_bytes_per_step": d2h // s,
             "latency_ms": {"p50": 1e3 * float(np.percentile(lats, 50)) if lats else None,
                            "p99": 1e3 * float(np.percentile(lats, 99)) if lats else None,
                            "kind": "submit-to-poll within a whole-batch step"},
@@ -480,7 +523,52 @@ def run_engine(args, rank, world, local, pg):
         "last_cuda_error": int(st.last_cuda_error),
         "clocks": clk,
     }
+
+
+def sub_of(line):
+    """The compact form of a measured line kept inside the default line."""
+    r = line["roofline"]
+    return {
+        "workload": line["config"]["workload"], "path": line["config"]["path"],
+        "value": line["value"], "unit": line["unit"], "inputs_per_s": line["inputs_per_s"],
+        "ms_per_step": line["ms_per_step"], "steps": line["steps"], "warmup": line["warmup"],
+        "inputs_per_step": line["config"]["inputs_per_step"],
+        "programs_compiled": line["config"]["programs_compiled"],
+        "roofline": {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
+                     "unit": r["unit"], "frac": r["frac"],
+                     "frac_folded_heads_uncredited": r["frac_folded_heads_uncredited"]},
+        "e2e": {"value": line["e2e"]["value"], "unit": line["e2e"]["unit"],
+                "h2d_bytes_per_step": line["e2e"]["h2d_bytes_per_step"],
+                "d2h_bytes_per_step": line["e2e"]["d2h_bytes_per_step"]},
+        "gpu_launches": line["gpu_launches"], "clocks": line["clocks"],
+    }
+
+
+# the other configurations, measured on the default run beside the headline:
+# (workload, plain, timed steps, warm-up steps)
+SUB_BATCH = (("c1", False, 10, 3), ("c1", True, 5, 3), ("c3", False, 5, 3), ("c3", True, 2, 3),
+             ("c4", False, 5, 3), ("c4", True, 2, 3))
+# serving: (offered inputs/s, seconds of arrivals) for each path
+SUB_RATES = (20000.0, 100000.0, 200000.0)
+SUB_SERVE_S = {False: 1.0, True: 0.5}
+
+
+def run_engine(args, rank, world, local, pg):
+    line = measure_engine(args, args.workload, args.plain, args.steps, args.warmup,
+                          args.inputs_per_step, rank, world, local, pg, prex=args.prex)
+    try:
+        import torch
+
+        from paper_2601_01048_gb300 import binding as B
+
+        p = B.cufz_int32_peak(local, torch.cuda.current_stream(torch.device("cuda", local)).cuda_stream)
+    except Exception:
+        p = None
+    achieved = line["roofline"]["achieved"] * 1e12
+    line["roofline"]["measured_int32_peak"] = p / 1e12 if p else None
+    line["roofline"]["frac_of_measured"] = achieved / p if p else None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        _, progs, inputs, _ = workload(args.workload)
         rate, irate, cores, n_in, n_acc, dt = oracle_rate(progs, inputs, args.cpu_seconds)
         line["cpu_baseline"] = {
             "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -488,6 +576,21 @@ def run_engine(args, rank, world, local, pg):
                       f"{n_acc} checked accesses in {dt:.1f} s",
             "inputs_per_s": irate,
         }
+    default_run = (args.workload == "c2" and not args.plain and not args.prex
+                   and not args.inputs_per_step and world == 1 and not args.no_sub)
+    if default_run:
+        subs = {}
+        for wl, plain, steps, warm in SUB_BATCH:
+            rec = measure_engine(args, wl, plain, steps, warm, 0, rank, world, local, pg)
+            subs[wl + ("_plain" if plain else "")] = sub_of(rec)
+        for plain in (False, True):
+            out = []
+            for rate in SUB_RATES:
+                rec = measure_serving(args, rate, SUB_SERVE_S[plain], plain, rank, world, local,
+                                      pg)
+                out.append(serving_sub(rec))
+            subs["c5" + ("_plain" if plain else "")] = out
+        line["sub"] = subs
     if rank == 0:
         print(json.dumps(line), flush=True)
 
@@ -530,10 +633,10 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ serving
 
-def run_serving(args, rank, world, local, pg):
+def measure_serving(args, rate, duration, plain, rank, world, local, pg):
     """Config 5: an open-loop Poisson stream of mutated inputs over 64
-    resident programs; reports delivered checked accesses/s and per-input
-    latency from scheduled arrival to result."""
+    resident programs; delivered checked accesses/s and per-input latency
+    from scheduled arrival to result."""
     import torch
 
     from paper_2601_01048_gb300 import binding as B
@@ -543,21 +646,21 @@ def run_serving(args, rank, world, local, pg):
     torch.cuda.set_device(local)
     progs = gen.c5_programs()
     corpus = gen.c5_corpus(progs)
-    n = max(int(args.rate * args.duration), 1)
-    arrivals = gen.poisson_arrivals(args.rate, args.duration, seed=17 + rank)
+    arrivals = gen.poisson_arrivals(rate, duration, seed=17 + rank)
     stream = gen.c5_stream(progs, corpus, len(arrivals), seed=29 + rank)
-    warm_n = min(max(int(args.rate * 0.25), 64), len(stream))
-    warm_arr = gen.poisson_arrivals(args.rate, 10.0, seed=5)[:warm_n]
-    flags = B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if args.plain else 0)
+    warm_n = min(max(int(rate * 0.25), 64), len(stream))
+    warm_arr = gen.poisson_arrivals(rate, 10.0, seed=5)[:warm_n]
+    flags = B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if plain else 0)
     if args.path == "jit":
         flags |= B.CF_JIT
+    tune_path = tune_file("c5")[0] if args.path == "jit" else None
     E = B.Engine(device=local, max_slots=4096, record_cap=1024, flags=flags, n_lanes=4,
-                 cta_threads=args.cta_threads)
+                 cta_threads=args.cta_threads, autotune_cache=tune_path)
     for p in progs:
         E.load(p)
     tuned = None
-    if args.path == "jit":
-        tuned = B.cufz_autotune(E.ctx, corpus)
+    if tune_path:
+        tuned = autotune_or_load(B, E, "c5", corpus, len(progs))
     serve_open_loop(E, stream[:warm_n], warm_arr)
     torch.cuda.synchronize()
     barrier(pg)
@@ -571,15 +674,15 @@ def run_serving(args, rank, world, local, pg):
     acc = float(res["n_accesses"].sum())
     wall_max = allreduce_max(pg, wall, torch.device("cuda", local))
     acc_all = allreduce_sum(pg, acc, torch.device("cuda", local))
-    line = {
+    return {
         "metric": METRIC, "value": acc_all / wall_max, "unit": UNIT, "n_gpus": world,
         "steps": 1, "warmup": 1, "ms_per_step": wall_max * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int32",
         "data": "synthetic (seeded programs, mutated fuzz inputs, Poisson arrivals)",
         "config": {"workload": "c5: open-loop serving over 64 resident programs (16 guarded 1D, "
                                "32 random 2D, 16 branch-heavy), mutated inputs",
-                   "offered_rate": args.rate, "duration_s": args.duration, "inputs": len(stream),
-                   "path": "plain one launch per input" if args.plain else
+                   "offered_rate": rate, "duration_s": duration, "inputs": len(stream),
+                   "path": "plain one launch per input" if plain else
                            "persistent kernels in CUDA graphs, 4 overlapping lanes",
                    "programs_compiled": tuned, "parallelism": f"replicas x{world}"},
         "inputs_per_s": len(stream) / wall,
@@ -592,6 +695,20 @@ def run_serving(args, rank, world, local, pg):
         "e2e": {"value": acc_all / wall_max, "unit": UNIT,
                 "h2d_bytes_per_step": len(stream) * 128, "d2h_bytes_per_step": len(stream) * 96},
     }
+
+
+def serving_sub(line):
+    """The compact form of a serving line kept inside the default line."""
+    c = line["config"]
+    return {"path": c["path"], "offered_rate": c["offered_rate"], "duration_s": c["duration_s"],
+            "inputs": c["inputs"], "inputs_per_s": line["inputs_per_s"], "value": line["value"],
+            "unit": line["unit"], "latency_ms": line["latency_ms"],
+            "device_busy_ms": line["device_busy_ms"], "batches": line["batches"],
+            "gpu_launches": line["gpu_launches"], "clocks": line["clocks"]}
+
+
+def run_serving(args, rank, world, local, pg):
+    line = measure_serving(args, args.rate, args.duration, args.plain, rank, world, local, pg)
     if rank == 0:
         print(json.dumps(line), flush=True)
 

@@ -213,7 +213,10 @@ typedef struct {
   uint64_t n_ops;        /* executed program ops, summed over test threads */
   uint32_t n_records;    /* records stored (<= record_cap) */
   uint32_t n_edges;      /* nonzero bitmap entries */
-  uint64_t reserved;
+  uint64_t n_branch_folded; /* of n_branch: loop-head evaluations whose edge
+                               update the compiled path made in closed form,
+                               as part of one add for a loop's repeated head
+                               edge (0 on the interpreter) */
 } cufz_result;
 
 /* One violation record, 32 bytes; ids are linear:

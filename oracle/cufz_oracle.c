@@ -53,14 +53,17 @@
  *
  * Per-input digest of all executed accesses (the pruning check, Sec. 5.2:
  * all memory accesses are preserved exactly):
- *   H  = block_lin * 0x9E3779B1 + thread_lin (32-bit), then for each access
- *        of the thread, in program order:
- *        H = (H ^ idx) * K + 0x9E3779B9  (32-bit), K = (site * 0xC2B2AE3D) | 1
- *   D  = sum over the input's test threads of H, mod 2^64
+ *   H  = block_lin * 0x9E3779B1 + thread_lin + 0x7F4A7C15 (32-bit), then for
+ *        each access of the thread, in program order:
+ *        H = H * K + idx  (32-bit), K = (site * 0xC2B2AE3D) | 3
+ *   D  = sum over the input's test threads of H ^ (H >> 16), mod 2^64
  * idx is the access's int32 index; the site fixes buffer, kind and width.
  * K is odd, so each step is a bijection of H: a thread whose access sequence
- * differs in one access (site or index), or has one more or fewer, ends with
- * a different H.
+ * differs in one index ends with a different H.  K - 1 is twice an odd
+ * number, so one access more or fewer changes H unless H * (K - 1) + idx
+ * happens to be 0 mod 2^32.  H ^ (H >> 16), a bijection that is not linear,
+ * binds each thread's H to the thread before the sum: two threads that trade
+ * their access sequences change D.
  * ordinal = the number of checked events (accesses and divisions) the
  * thread executed before this one.
  *
@@ -502,8 +505,8 @@ static int32_t do_access(orc_ctx* c, const orc_op* op, int is_store) {
   int viol = off < 0 || off + w > c->len[buf];
   orc_result* res = c->res;
   res->n_accesses++;
-  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 1u;
-  c->h = (c->h ^ (uint32_t)idx) * K + 0x9E3779B9u;
+  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 3u;
+  c->h = c->h * K + (uint32_t)idx;
   int32_t value = 0;
   if (viol) {
     orc_record proto;
@@ -596,8 +599,8 @@ static void do_heap_access(orc_ctx* c, const orc_op* op, int is_store) {
   int w = op->imm;
   int64_t off = (int64_t)idx * (int64_t)w;
   c->res->n_accesses++;
-  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 1u;
-  c->h = (c->h ^ (uint32_t)idx) * K + 0x9E3779B9u;
+  uint32_t K = ((uint32_t)op->site * 0xC2B2AE3Du) | 3u;
+  c->h = c->h * K + (uint32_t)idx;
   int cls = 0, buf = 0;
   if (h < 1 || h > c->P->n_alloc || c->hstate[h - 1] == 0) {
     cls = ORC_CLS_WILD;
@@ -764,7 +767,7 @@ static void thread_start(orc_ctx* c, uint64_t bl, uint64_t tl, uint32_t bx, uint
   c->backedges = 0;
   c->stopped = 0;
   memset(c->hstate, 0, (size_t)P->n_alloc);
-  c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl;
+  c->h = (uint32_t)bl * 0x9E3779B1u + (uint32_t)tl + 0x7F4A7C15u;
 }
 
 static void thread_save(const orc_ctx* c, orc_saved* s, int32_t* hsize, uint8_t* hstate) {
@@ -827,7 +830,7 @@ static int run_block_phased(orc_ctx* c, uint64_t bl, uint64_t T, uint32_t bx, ui
     if (end >= P->n_ops) break;
     begin = end + 1;
   }
-  for (uint64_t tl = 0; tl < T; tl++) c->res->digest += st[tl].h;
+  for (uint64_t tl = 0; tl < T; tl++) c->res->digest += st[tl].h ^ (st[tl].h >> 16);
   free(st);
   free(hsize);
   free(hstate);
@@ -909,7 +912,7 @@ int orc_run(const void* handle, const orc_input* in, const orc_opts* opts, orc_r
     for (uint64_t tl = 0; tl < nthreads_blk; tl++) {
       thread_start(c, bl, tl, bx, by);
       exec_range(c, 0, P->n_ops);
-      res->digest += c->h;
+      res->digest += c->h ^ (c->h >> 16);
     }
   }
   free(sm.keys);

@@ -29,7 +29,7 @@ RESULT_DTYPE = np.dtype([
     ("ticket", "<u8"), ("user_tag", "<u8"), ("status", "<i4"), ("flags", "<u4"),
     ("n_accesses", "<u8"), ("n_violations", "<u8"), ("first_key", "<u8"), ("digest", "<u8"),
     ("n_branch", "<u8"), ("n_threads", "<u8"), ("n_ops", "<u8"), ("n_records", "<u4"),
-    ("n_edges", "<u4"), ("reserved", "<u8"),
+    ("n_edges", "<u4"), ("n_branch_folded", "<u8"),
 ])
 assert RESULT_DTYPE.itemsize == 96
 

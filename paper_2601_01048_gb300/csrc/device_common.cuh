@@ -26,14 +26,24 @@ static __device__ __forceinline__ uint32_t mix32(uint32_t h) {
 }
 
 // Digest of the accesses: each test thread folds its accesses, in program
-// order, into h (starting at block_lin * 0x9E3779B1 + thread_lin) with
-// h = (h ^ idx) * k + 0x9E3779B9, k = (site * 0xC2B2AE3D) | 1; the input's
-// digest is the sum of the threads' h, mod 2^64.  k is odd, so a step is a
-// bijection of h and one changed, added or dropped access changes the
-// thread's h.
-static __device__ __forceinline__ uint32_t access_step(uint32_t h, uint32_t k, int32_t idx) {
-  return (h ^ (uint32_t)idx) * k + 0x9E3779B9u;
+// order, into h (starting at digest_start(block_lin, thread_lin)) with
+// h = h * k + idx, k = access_k(site) = (site * 0xC2B2AE3D) | 3, one
+// multiply-add per access; the input's digest is the sum over threads of
+// digest_end(h) = h ^ (h >> 16), mod 2^64.  k is odd, so a step is a
+// bijection of h (a changed index changes h); k - 1 is twice an odd number,
+// so an added or dropped access changes h unless h * (k - 1) + idx is 0 mod
+// 2^32; digest_end, a bijection that is not linear, binds each thread's h
+// to its thread before the sum.
+static __device__ __forceinline__ uint32_t digest_start(uint32_t bl, uint32_t tl) {
+  return bl * 0x9E3779B1u + tl + 0x7F4A7C15u;
 }
+static __host__ __device__ __forceinline__ constexpr uint32_t access_k(uint32_t site) {
+  return (site * 0xC2B2AE3Du) | 3u;
+}
+static __device__ __forceinline__ uint32_t access_step(uint32_t h, uint32_t k, int32_t idx) {
+  return h * k + (uint32_t)idx;
+}
+static __device__ __forceinline__ uint32_t digest_end(uint32_t h) { return h ^ (h >> 16); }
 
 // floor(n / d) for n < 2^32 with m = ceil(2^64 / d) (m == 0 means d == 1).
 static __device__ __forceinline__ uint32_t udiv(uint32_t n, uint64_t m) {
@@ -151,6 +161,7 @@ struct LaneAcc {
   uint32_t n_branch;
   uint32_t n_ops;
   uint32_t n_viol;
+  uint32_t n_folded;
   unsigned long long digest;
   unsigned long long first_key;
   bool budget_hit;
@@ -158,7 +169,7 @@ struct LaneAcc {
 };
 
 static __device__ __forceinline__ void acc_init(LaneAcc& a) {
-  a.n_acc = a.n_branch = a.n_ops = a.n_viol = 0;
+  a.n_acc = a.n_branch = a.n_ops = a.n_viol = a.n_folded = 0;
   a.digest = 0ull;
   a.first_key = ~0ull;
   a.budget_hit = false;
@@ -170,7 +181,7 @@ static __device__ __forceinline__ void acc_init(LaneAcc& a) {
 static __device__ __forceinline__ void acc_flush(const EngineTables& T, uint32_t slot, const LaneAcc& a) {
   unsigned long long dig = a.digest;
   unsigned long long fk = a.first_key;
-  uint32_t na = a.n_acc, nb = a.n_branch, no = a.n_ops, nv = a.n_viol;
+  uint32_t na = a.n_acc, nb = a.n_branch, no = a.n_ops, nv = a.n_viol, nf = a.n_folded;
 #pragma unroll
   for (int s = 16; s > 0; s >>= 1) {
     dig += __shfl_xor_sync(FULL, dig, s);
@@ -180,6 +191,7 @@ static __device__ __forceinline__ void acc_flush(const EngineTables& T, uint32_t
     nb += __shfl_xor_sync(FULL, nb, s);
     no += __shfl_xor_sync(FULL, no, s);
     nv += __shfl_xor_sync(FULL, nv, s);
+    nf += __shfl_xor_sync(FULL, nf, s);
   }
   const bool bh = __any_sync(FULL, a.budget_hit);
   if ((threadIdx.x & 31u) == 0) {
@@ -189,6 +201,7 @@ static __device__ __forceinline__ void acc_flush(const EngineTables& T, uint32_t
     if (nb) atomicAdd(&S->n_branch, (unsigned long long)nb);
     if (no) atomicAdd(&S->n_ops, (unsigned long long)no);
     if (nv) atomicAdd(&S->n_violations, (unsigned long long)nv);
+    if (nf) atomicAdd(&S->n_branch_folded, (unsigned long long)nf);
     if (fk != ~0ull) atomicMin(&S->first_key, fk);
     if (bh) atomicOr(&S->flags, (uint32_t)CUFZ_FL_BUDGET);
   }
@@ -248,13 +261,14 @@ static __device__ __noinline__ void finalize_input(const EngineTables& T, const 
     r.n_ops = vS->n_ops;
     r.n_records = reserved < T.record_cap ? reserved : T.record_cap;
     r.n_edges = nt;
-    r.reserved = 0;
+    r.n_branch_folded = vS->n_branch_folded;
     // reset the slot for its next input
     vS->n_accesses = 0;
     vS->n_violations = 0;
     vS->digest = 0;
     vS->n_branch = 0;
     vS->n_ops = 0;
+    vS->n_branch_folded = 0;
     vS->first_key = ~0ull;
     vS->rec_reserved = 0;
     vS->rec_listed = 0;

@@ -99,7 +99,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
     bool act = valid, alive = valid;
     uint32_t stk_act = 0, stk_aux = 0;
     uint32_t prev = 0, ordinal = 0, back = 0;
-    uint32_t dh = bl * 0x9E3779B1u + tl;  // digest state of the thread
+    uint32_t dh = digest_start(bl, tl);  // digest state of the thread
 
     uint32_t pc = 0;
 #pragma unroll 1
@@ -176,7 +176,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           const bool viol = act && (idx < 0 || off + (int64_t)w > len);
           if (act) {
             acc.n_acc++;
-            if (do_digest) dh = access_step(dh, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
+            if (do_digest) dh = access_step(dh, access_k((uint32_t)op.imm), idx);
           }
           const uint32_t vm = __ballot_sync(FULL, viol);
           if (vm) {
@@ -289,7 +289,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           uint32_t cls = 0;
           if (act) {
             acc.n_acc++;
-            if (do_digest) dh = access_step(dh, ((uint32_t)op.imm * 0xC2B2AE3Du) | 1u, idx);
+            if (do_digest) dh = access_step(dh, access_k((uint32_t)op.imm), idx);
             const int64_t len = st, R = (int64_t)T.redzone;
             if (st == 0)
               cls = CUFZ_CLS_WILD;
@@ -412,7 +412,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
         }
       }
     }
-    if (valid && do_digest) acc.digest += dh;
+    if (valid && do_digest) acc.digest += digest_end(dh);
   }
 
   acc_flush(T, slot, acc);

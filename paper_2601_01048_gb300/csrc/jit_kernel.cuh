@@ -132,6 +132,10 @@ static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
   if (!edge_saturated(s_hash, e)) jit_cover_lane(slot, e);
 }
 
+// jit_cover as one shared out-of-line copy, for programs compiled to compact
+// code (many branch sites): a call at each site instead of the inline test.
+static __device__ __noinline__ void jit_cover_out(uint32_t slot, uint32_t e) { jit_cover(slot, e); }
+
 // n hits of edge e at once (n may differ between lanes, and be 0).
 static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
   if (n != 0 && !edge_saturated(s_hash, e)) jit_cover_slow(slot, e, n);
@@ -146,6 +150,7 @@ static __device__ __forceinline__ void jit_loop_cover(uint32_t slot, uint32_t& p
                                                       uint32_t n_true, bool exited, uint32_t lt,
                                                       uint32_t lf) {
   acc.n_branch += n_true + (exited ? 1u : 0u);
+  acc.n_folded += n_true > 1u ? n_true - 1u : 0u;
   const uint32_t p_in = prev;
   jit_cover_n(slot, (lt ^ p_in) & 0xFFFFu, n_true ? 1u : 0u);
   jit_cover_n(slot, (lt ^ (lt >> 1)) & 0xFFFFu, n_true ? n_true - 1u : 0u);
@@ -158,6 +163,11 @@ static __device__ __forceinline__ void jit_loop_cover(uint32_t slot, uint32_t& p
 static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t off, uint32_t lw) {
   const uint32_t word = mix32(seedx ^ (uint32_t)(off >> 2));
   return lw == 0 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word;
+}
+
+// jit_content as one shared out-of-line copy (compact code).
+static __device__ __noinline__ int32_t jit_content_out(uint32_t seedx, int64_t off, uint32_t lw) {
+  return jit_content(seedx, off, lw);
 }
 
 

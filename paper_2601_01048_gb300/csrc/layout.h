@@ -172,7 +172,8 @@ struct SlotState {
   uint32_t items_done;
   uint32_t flags;
   uint32_t rec_listed;  // compiled path: violations of threads listed for records
-  uint32_t pad[3];
+  uint32_t pad;
+  unsigned long long n_branch_folded;
 };
 static_assert(sizeof(SlotState) == 80, "SlotState size");
 

@@ -502,6 +502,9 @@ bool barriers_eliminable(const Ir& ir) {
 //    returns the ordinal of its first violation.
 namespace {
 
+// Programs with at least this many kept branch sites get compact code.
+constexpr int kCompactSites = 24;
+
 struct Gen {
   const Ir& ir;
   std::string& o;
@@ -509,6 +512,12 @@ struct Gen {
   bool digest_ = true;
   bool rec_ = false;  // emitting the record function
   bool no_counts_ = false;  // a loop body whose counts are added after the loop
+  // Compact code for programs with many branch sites: the edge update and
+  // the seeded-content hash of a live load become calls of one shared copy
+  // instead of inline code at every site, so the program's code stays small
+  // enough for the instruction caches (a branch-heavy program's warps
+  // diverge and walk most of its code).
+  bool compact_ = false;
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -606,7 +615,8 @@ struct Gen {
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
                   "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1;" +
-                  (count ? " acc.n_branch++;" : "") + " jit_cover(slot, e); }");
+                  (count ? " acc.n_branch++;" : "") +
+                  (compact_ ? " jit_cover_out(slot, e); }" : " jit_cover(slot, e); }"));
   }
 
   // index limits are read once per function call into constants (a
@@ -642,7 +652,7 @@ struct Gen {
       line(ind + 2, "if (write) write = !jit_record(bl, tl, ordinal, " + hex32(what) + ", off);");
       line(ind + 1, "}");
     } else {
-      line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) +
+      line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 3u) +
                         ", ix);");
       line(ind + 1, "nv += viol ? 1u : 0u;");
     }
@@ -651,8 +661,8 @@ struct Gen {
         line(ind + 1, r(o2.dst) + " = 0;");
       } else {
         uint32_t seedx = ir.seed ^ ((uint32_t)o2.buf * 0x9E3779B9u);
-        line(ind + 1, r(o2.dst) + " = viol ? 0 : jit_content(" + hex32(seedx) + ", off, " +
-                          std::to_string(lw) + "u);");
+        line(ind + 1, r(o2.dst) + " = viol ? 0 : " + (compact_ ? "jit_content_out(" : "jit_content(") +
+                          hex32(seedx) + ", off, " + std::to_string(lw) + "u);");
       }
     }
     if (rec_) line(ind + 1, "ordinal++;");
@@ -743,7 +753,7 @@ struct Gen {
         line(ind + 1, "}");
         line(ind + 1, "ordinal++;");
       } else {
-        line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 1u) +
+        line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 3u) +
                           ", ix);");
         line(ind + 1, "nv += viol ? 1u : 0u;");
       }
@@ -814,7 +824,7 @@ struct Gen {
                           std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + "u : (uint32_t)" + n + ");");
         line(ind + 1, "const bool " + stop + " = " + t + " > budget - back;");
         line(ind + 1, "const uint32_t " + it + " = " + stop + " ? budget - back + 1u : " + t + ";");
-        line(ind + 1, "#pragma unroll 1");
+        line(ind + 1, "#pragma unroll 2");
         line(ind + 1, "for (" + r(o2.dst) + " = 0; (uint32_t)" + r(o2.dst) + " < " + it + "; " + r(o2.dst) + "++) {");
         no_counts_ = true;
         range(ind + 2, pc + 1, o2.end_pc);
@@ -860,20 +870,13 @@ struct Gen {
 
   // Decodes test thread g into bl, tl and the used special registers, with
   // only the divisions those need: x = lin % n_x, y = (lin / n_x) % n_y,
-  // z = lin / (n_x * n_y) for the thread (tl) and the block (bl).  With
-  // `stepped` (the work-item loop), bl and tl are kept across the loop's
-  // steps when a block has at least as many threads as the CTA (they then
-  // wrap at most once per step), and the divisions for a 1D block (b1) or
-  // 1D grid (g1) are skipped: their quotients are 0.
-  void thread_setup(int ind, const std::vector<bool>& sreg_used, bool stepped) {
-    if (stepped) {
-      line(ind, "if (!inc) { bl = udiv(g, vin->mT); tl = g - bl * vin->T; }");
-    } else {
-      line(ind, "const uint32_t bl = udiv(g, vin->mT);");
-      line(ind, "const uint32_t tl = g - bl * vin->T;");
-    }
+  // z = lin / (n_x * n_y) for the thread (tl) and the block (bl).  (The
+  // record function's single thread; the count function's work-item loop
+  // steps its coordinates instead, see stepped_pre.)
+  void thread_setup(int ind, const std::vector<bool>& sreg_used) {
+    line(ind, "const uint32_t bl = udiv(g, vin->mT);");
+    line(ind, "const uint32_t tl = g - bl * vin->T;");
     const char* lin[2] = {"tl", "bl"};
-    const char* one[2] = {"b1", "g1"};
     const char* m1[2] = {"vin->mBx", "vin->mGx"};
     const char* m2[2] = {"vin->mBxy", "vin->mGxy"};
     const char* n1[2] = {"vin->Bx", "vin->gx"};
@@ -882,19 +885,8 @@ struct Gen {
     for (int k = 0; k < 2; k++) {
       const bool ux = sreg_used[k * 6 + 0], uy = sreg_used[k * 6 + 1], uz = sreg_used[k * 6 + 2];
       const std::string q = std::string("q") + lin[k], z = std::string("z") + lin[k];
-      if (stepped) {
-        if (ux || uy) line(ind, "uint32_t " + q + " = 0;");
-        if (uy || uz) line(ind, "uint32_t " + z + " = 0;");
-        if (ux || uy || uz) {
-          std::string t = std::string("if (!") + one[k] + ") {";
-          if (ux || uy) t += " " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");";
-          if (uy || uz) t += " " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");";
-          line(ind, t + " }");
-        }
-      } else {
-        if (ux || uy) line(ind, "const uint32_t " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");");
-        if (uy || uz) line(ind, "const uint32_t " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");");
-      }
+      if (ux || uy) line(ind, "const uint32_t " + q + " = udiv(" + lin[k] + ", " + m1[k] + ");");
+      if (uy || uz) line(ind, "const uint32_t " + z + " = udiv(" + lin[k] + ", " + m2[k] + ");");
       if (ux) line(ind, std::string("const int32_t ") + nm[k][0] + " = (int32_t)(" + lin[k] + " - " + q + " * " + n1[k] + ");");
       if (uy) line(ind, std::string("const int32_t ") + nm[k][1] + " = (int32_t)(" + q + " - " + z + " * " + ny[k] + ");");
       if (uz) line(ind, std::string("const int32_t ") + nm[k][2] + " = (int32_t)" + z + ";");
@@ -905,6 +897,82 @@ struct Gen {
     }
     for (int k = 0; k < 4; k++)
       if (sreg_used[12 + k]) line(ind, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
+  }
+
+  // The work-item loop's coordinates (count function).  A lane runs test
+  // threads g, g + blockDim.x, ...  With inc (a block has at least as many
+  // threads as the CTA) bl and tl are carried across steps and bl grows by at
+  // most one per step, so the block coordinates are stepped too (x, then the
+  // carry into y, then z) instead of divided out; with fix_t (a block has
+  // exactly the CTA's threads) tl never changes and the thread coordinates
+  // are computed once.  Quotients by a unit extent (b1/g1: 1D; bz1/gz1: no
+  // z extent) are 0 and skipped.
+  void stepped_pre(int ind, const std::vector<bool>& u) {
+    const bool tx = u[0], ty = u[1], tz = u[2], bx = u[6], by = u[7], bz = u[8];
+    line(ind, "const bool fix_t = inc && vin->T == blockDim.x;");
+    line(ind, "const bool bz1 = vin->block[2] == 1u, gz1 = vin->grid[2] == 1u;");
+    line(ind, "(void)fix_t; (void)bz1; (void)gz1;");
+    if (tx || ty) line(ind, "uint32_t qtl = 0;");
+    if (ty || tz) line(ind, "uint32_t ztl = 0;");
+    if (tx || ty || tz) {
+      std::string t = "if (fix_t && !b1) {";
+      if (tx || ty) t += " qtl = udiv(tl, vin->mBx);";
+      if (ty || tz) t += " ztl = bz1 ? 0u : udiv(tl, vin->mBxy);";
+      line(ind, t + " }");
+    }
+    if (bx || by || bz) line(ind, "uint32_t cbx = 0;");
+    if (by || bz) line(ind, "uint32_t cby = 0;");
+    if (bz) line(ind, "uint32_t cbz = 0;");
+    if (bx || by || bz) {
+      line(ind, "if (inc) {");
+      block_coords(ind + 1, u);
+      line(ind, "}");
+    }
+  }
+  // cbx, cby, cbz of block bl by division
+  void block_coords(int ind, const std::vector<bool>& u) {
+    const bool by = u[7], bz = u[8];
+    line(ind, "const uint32_t qb = g1 ? 0u : udiv(bl, vin->mGx);");
+    line(ind, "cbx = bl - qb * vin->gx;");
+    if (by || bz) line(ind, "const uint32_t zb = (g1 || gz1) ? 0u : udiv(bl, vin->mGxy);");
+    if (by || bz) line(ind, "cby = qb - zb * vin->grid[1];");
+    if (bz) line(ind, "cbz = zb;");
+  }
+  void stepped_in(int ind, const std::vector<bool>& u) {
+    const bool tx = u[0], ty = u[1], tz = u[2], bx = u[6], by = u[7], bz = u[8];
+    line(ind, "if (!inc) { bl = udiv(g, vin->mT); tl = g - bl * vin->T; }");
+    if (tx || ty || tz) {
+      std::string t = "if (!fix_t && !b1) {";
+      if (tx || ty) t += " qtl = udiv(tl, vin->mBx);";
+      if (ty || tz) t += " ztl = bz1 ? 0u : udiv(tl, vin->mBxy);";
+      line(ind, t + " }");
+    }
+    if (tx) line(ind, "const int32_t s_tx = (int32_t)(tl - qtl * vin->Bx);");
+    if (ty) line(ind, "const int32_t s_ty = (int32_t)(qtl - ztl * vin->block[1]);");
+    if (tz) line(ind, "const int32_t s_tz = (int32_t)ztl;");
+    if (bx || by || bz) {
+      line(ind, "if (!inc) {");
+      block_coords(ind + 1, u);
+      line(ind, "}");
+    }
+    if (bx) line(ind, "const int32_t s_bx = (int32_t)cbx;");
+    if (by) line(ind, "const int32_t s_by = (int32_t)cby;");
+    if (bz) line(ind, "const int32_t s_bz = (int32_t)cbz;");
+    for (int k = 0; k < 3; k++) {
+      if (u[3 + k]) line(ind, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
+      if (u[9 + k]) line(ind, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)vin->grid[" + std::to_string(k) + "];");
+    }
+    for (int k = 0; k < 4; k++)
+      if (u[12 + k]) line(ind, std::string("const int32_t ") + sreg_name(12 + k) + " = vin->args[" + std::to_string(k) + "];");
+  }
+  void stepped_tail(int ind, const std::vector<bool>& u) {
+    const bool bx = u[6], by = u[7], bz = u[8];
+    line(ind, "tl += blockDim.x;");
+    std::string t = "if (tl >= vin->T) { tl -= vin->T; bl++;";
+    if (bz) t += " if (++cbx == vin->gx) { cbx = 0; if (++cby == vin->grid[1]) { cby = 0; cbz++; } }";
+    else if (by) t += " if (++cbx == vin->gx) { cbx = 0; if (++cby == vin->grid[1]) cby = 0; }";
+    else if (bx) t += " if (++cbx == vin->gx) cbx = 0;";
+    line(ind, t + " }");
   }
 
   void reg_decls(int ind, const std::vector<bool>& used) {
@@ -924,6 +992,9 @@ struct Gen {
       if (op.kept && op.opc == B_SREG) sreg_used[op.sreg] = true;
     }
     const std::string fn = "cufz_prog_" + std::to_string(index);
+    int n_sites_kept = 0;
+    for (const auto& op : ir.ops) n_sites_kept += op.kept && (op.opc == B_IF || op.opc == B_LOOP);
+    compact_ = n_sites_kept >= kCompactSites;
 
     // division faults: records of kind 2 (division), class DIV_ZERO, written
     // like access records (one atomicAdd per active-mask group)
@@ -984,7 +1055,7 @@ struct Gen {
     line(1, "const DevInput* vin = &s_in;");
     line(1, "const uint32_t* lim = vin->lim;");
     lim_decls(1);
-    thread_setup(1, sreg_used, false);
+    thread_setup(1, sreg_used);
     line(1, "uint32_t ordinal = 0, back = 0, fo = ~0u;");
     line(1, "(void)back;");
     reg_decls(1, used);
@@ -1015,18 +1086,19 @@ struct Gen {
     line(1, "(void)b1; (void)g1;");
     line(1, "uint32_t bl = 0, tl = 0;");
     line(1, "if (inc) { bl = udiv(g0 + threadIdx.x, vin->mT); tl = g0 + threadIdx.x - bl * vin->T; }");
+    stepped_pre(1, sreg_used);
     line(1, "#pragma unroll 1");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
-    thread_setup(2, sreg_used, true);
+    stepped_in(2, sreg_used);
     // dh = the thread's digest state, nv = its violations
-    line(2, "uint32_t dh = bl * 0x9E3779B1u + tl;");
+    line(2, "uint32_t dh = digest_start(bl, tl);");
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
     reg_decls(2, used);
     if (heap_ops) line(2, heap_decl);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
-    line(2, "if (dig) acc.digest += dh;");
+    line(2, "if (dig) acc.digest += digest_end(dh);");
     line(2, "if (nv) {");
     line(3, "acc.n_viol += nv;");
     line(3, "bool listed = false;");
@@ -1040,8 +1112,7 @@ struct Gen {
     line(4, "if (acc.first_key == ~0ull) acc.first_key = first_key_of(bl, tl, f);");
     line(3, "}");
     line(2, "}");
-    line(2, "tl += blockDim.x;");
-    line(2, "if (tl >= vin->T) { tl -= vin->T; bl++; }");
+    stepped_tail(2, sreg_used);
     line(1, "}");
     line(1, "__syncwarp();");
     line(1, "acc_flush(s_T, slot, acc);");

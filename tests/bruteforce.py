@@ -150,7 +150,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
 
     def run_thread(bl, tl, sregs):
         regs = [0] * max(P["n_regs"], 1)
-        t = dict(ordinal=0, prev=0, back=0, stop=False, h=(bl * 0x9E3779B1 + tl) & M32)
+        t = dict(ordinal=0, prev=0, back=0, stop=False,
+                 h=(bl * 0x9E3779B1 + tl + 0x7F4A7C15) & M32)
         trace = st["traces"].setdefault((bl, tl), [])
 
         def edge(site, out):
@@ -164,8 +165,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
             off = regs[a] * w
             bad = off < 0 or off + w > lens[buf]
             trace.append((site, regs[a]))
-            k = ((site * 0xC2B2AE3D) & M32) | 1
-            t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
+            k = ((site * 0xC2B2AE3D) & M32) | 3
+            t["h"] = (t["h"] * k + regs[a]) & M32
             st["n_accesses"] += 1
             val = 0
             if bad:
@@ -217,8 +218,8 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
         def hmem(is_st, d, a, hreg, w, site):
             off = regs[a] * w
             trace.append((site, regs[a]))
-            k = ((site * 0xC2B2AE3D) & M32) | 1
-            t["h"] = (((t["h"] ^ (regs[a] & M32)) * k) + 0x9E3779B9) & M32
+            k = ((site * 0xC2B2AE3D) & M32) | 3
+            t["h"] = (t["h"] * k + regs[a]) & M32
             st["n_accesses"] += 1
             h, blk, cls = regs[hreg], None, 0
             blk = block_of(h)
@@ -305,7 +306,7 @@ def evaluate(prog: bytes, inp: dict, redzone=256, budget=4096):
                 yield
             else:
                 run([s])
-        st["digest"] = (st["digest"] + t["h"]) & M64
+        st["digest"] = (st["digest"] + (t["h"] ^ (t["h"] >> 16))) & M64
 
     args = [s32(v) for v in inp["args"]]
     for bz in range(g[2]):

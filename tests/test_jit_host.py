@@ -169,10 +169,16 @@ def test_budget_stop_and_3d_shapes_match_oracle(tmp_path, host_objs, orc):
     ins = gen.c2_inputs(progs, per_program=2, seed=306, max_grid=2)
     exe = build(tmp_path, host_objs, progs)
     rng = gen.SplitMix64(308)
-    shaped = np.concatenate([ins, ins])
-    for x in shaped:
+    shaped = np.concatenate([ins, ins, ins])
+    # blocks of exactly the CTA's 256 threads and larger ones over 3D grids:
+    # the stepped block coordinates (x, the carry into y, then into z)
+    big = ((16, 16, 1), (8, 8, 4), (32, 16, 1), (16, 8, 4), (64, 4, 2))
+    for k, x in enumerate(shaped):
         x["grid"] = [rng.randint(1, 3), rng.randint(1, 3), rng.randint(1, 3)]
-        x["block"] = [rng.randint(1, 9), rng.randint(1, 6), rng.randint(1, 4)]
+        if k < 2 * len(ins):
+            x["block"] = [rng.randint(1, 9), rng.randint(1, 6), rng.randint(1, 4)]
+        else:
+            x["block"] = big[k % len(big)]
     got = run(tmp_path, exe, progs, shaped)
     ores, orecs, obms = orc.run_batch(progs, shaped, rec_cap=1 << 14, bitmaps=True)
     for k, (res, recs, bm) in enumerate(got):
