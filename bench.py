@@ -650,7 +650,7 @@ def measure_serving(args, rate, duration, plain, rank, world, local, pg):
     stream = gen.c5_stream(progs, corpus, len(arrivals), seed=29 + rank)
     warm_n = min(max(int(rate * 0.25), 64), len(stream))
     warm_arr = gen.poisson_arrivals(rate, 10.0, seed=5)[:warm_n]
-    flags = B.CF_KEEP_BITMAPS | (B.CF_PLAIN_LAUNCH if plain else 0)
+    flags = B.CF_KEEP_BITMAPS | B.CF_AUTO_RELEASE | (B.CF_PLAIN_LAUNCH if plain else 0)
     if args.path == "jit":
         flags |= B.CF_JIT
     tune_path = tune_file("c5")[0] if args.path == "jit" else None

@@ -257,6 +257,12 @@ typedef struct {
   uint32_t smem_bytes;
   uint32_t graph_failures;    /* batches that fell back to direct launches */
   int32_t last_cuda_error;    /* last CUDA error code seen by the runtime (0 = none) */
+  /* overlap of batches on the device (from their CUDA events, among the
+     last 256 retired batches): pairs whose device intervals intersect, and
+     the most batches running at one moment */
+  uint64_t overlapping_batch_pairs;
+  uint32_t max_concurrent_batches;
+  uint32_t reserved;
 } cufz_stats;
 
 /* Statistics of a loaded (or pruned) program. */
@@ -504,12 +510,27 @@ cufz_status cufz_compile_programs(cufz_ctx* ctx, char* log, uint32_t log_cap);
 cufz_status cufz_set_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t compiled);
 cufz_status cufz_get_program_path(cufz_ctx* ctx, uint32_t program_id, uint32_t* compiled);
 
+/* Lane mapping of a compiled program: the test threads each CUDA thread of
+ * the persistent kernel runs per iteration of the program's work-item loop
+ * (1, 2 or 4; consecutive iterations of a lane take test threads one CTA
+ * apart, so the mapping only interleaves their instructions).  Results do
+ * not depend on it.  The default is 1, or the autotune cache's choice; a
+ * change recompiles the module at the next submit.  CUFZ_E_INVALID_ARG for
+ * other values.  (The paper's runtime maps each GPU thread to one iteration
+ * of a loop over the block, Sec. 4.1, Listing 2; this is the GPU-side
+ * counterpart of unrolling that loop.) */
+cufz_status cufz_set_program_lanes(cufz_ctx* ctx, uint32_t program_id, uint32_t lanes);
+cufz_status cufz_get_program_lanes(cufz_ctx* ctx, uint32_t program_id, uint32_t* lanes);
+
 /* Autotuner: for every program in the sample, times the sample's inputs of
  * that program run compiled and interpreted (best of three each; the sample
  * is repeated up to 2^24 test threads, at most 2048 inputs, so that the
  * timing measures throughput rather than launch costs) and moves
  * the program off its load-time path only if the other is at least 25%
- * faster.  Needs an idle context; the sample's results are discarded.
+ * faster.  Then, for compiled programs of at most 24 kept ops, it times the
+ * lane mappings 2 and 4 the same way and keeps the fastest (a wider mapping
+ * must win by 3%).  The choices go to the autotune cache, if the config
+ * names one.  Needs an idle context; the sample's results are discarded.
  * *n_compiled receives the number of programs left on the compiled path. */
 cufz_status cufz_autotune(cufz_ctx* ctx, const cufz_input* sample, uint32_t n,
                           uint32_t* n_compiled);

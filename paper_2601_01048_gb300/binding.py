@@ -60,7 +60,9 @@ class cufz_stats(ctypes.Structure):
                 ("cta_threads", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
                 ("item_threads", ctypes.c_uint32), ("n_sms", ctypes.c_uint32),
                 ("max_slots", ctypes.c_uint32), ("smem_bytes", ctypes.c_uint32),
-                ("graph_failures", ctypes.c_uint32), ("last_cuda_error", ctypes.c_int32)]
+                ("graph_failures", ctypes.c_uint32), ("last_cuda_error", ctypes.c_int32),
+                ("overlapping_batch_pairs", ctypes.c_uint64),
+                ("max_concurrent_batches", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
 
 
 class cufz_prog_stats(ctypes.Structure):
@@ -85,6 +87,7 @@ EXPORTS = [
     "cufz_new_epoch", "cufz_release", "cufz_sync", "cufz_get_stats", "cufz_reset_stats",
     "cufz_int32_peak", "cufz_compile_programs", "cufz_program_cuda", "cufz_compile_check",
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
+    "cufz_set_program_lanes", "cufz_get_program_lanes",
     "cufz_unload_program", "cufz_verify_prune", "cufz_prex_check",
     "cufz_prex_plan", "cufz_mutate_inputs",
 ]
@@ -126,6 +129,8 @@ def lib():
                 "cufz_run_noalloc": (i32, [vp, sz, vp, u32, u32, u32, vp, u32, vp, vp, vp]),
                 "cufz_set_program_path": (i32, [vp, u32, u32]),
                 "cufz_get_program_path": (i32, [vp, u32, P(u32)]),
+                "cufz_set_program_lanes": (i32, [vp, u32, u32]),
+                "cufz_get_program_lanes": (i32, [vp, u32, P(u32)]),
                 "cufz_autotune": (i32, [vp, vp, u32, P(u32)]),
                 "cufz_unload_program": (i32, [vp, u32]),
                 "cufz_verify_prune": (i32, [vp, u32, vp, u32, P(u32)]),
@@ -369,6 +374,16 @@ def cufz_get_program_path(ctx, program_id: int) -> bool:
     v = ctypes.c_uint32(0)
     _check(lib().cufz_get_program_path(ctx, program_id, ctypes.byref(v)), "cufz_get_program_path")
     return bool(v.value)
+
+
+def cufz_set_program_lanes(ctx, program_id: int, lanes: int) -> None:
+    _check(lib().cufz_set_program_lanes(ctx, program_id, lanes), "cufz_set_program_lanes")
+
+
+def cufz_get_program_lanes(ctx, program_id: int) -> int:
+    v = ctypes.c_uint32(0)
+    _check(lib().cufz_get_program_lanes(ctx, program_id, ctypes.byref(v)), "cufz_get_program_lanes")
+    return int(v.value)
 
 
 def cufz_autotune(ctx, sample: np.ndarray) -> int:

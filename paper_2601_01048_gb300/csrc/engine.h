@@ -78,9 +78,12 @@ constexpr uint32_t kJitMinCtasDefault = 3;
 
 // The compiled path's module source: the included programs' functions (from
 // jit_source), the dispatcher and the kernels.
+// lanes[k] is program k's lane mapping: test threads per lane per
+// iteration of its work-item loop (1, 2 or 4; 1 where absent).
 std::string jit_module_source(const std::vector<std::string>& prog_src,
                               const std::vector<uint8_t>& include, bool plain_kernel,
-                              uint32_t min_ctas, uint32_t cta_threads);
+                              uint32_t min_ctas, uint32_t cta_threads,
+                              const std::vector<uint8_t>& lanes);
 
 // CUDA source of one program's work-item function `cufz_prog_<index>` for
 // the compiled path (see jit_kernel.cuh).

@@ -171,7 +171,7 @@ __device__ __forceinline__ void run_warp(const EngineTables& T, const DevInput* 
           const uint32_t buf = op.b;
           const uint32_t lw = op.x;
           const uint32_t w = 1u << lw;
-          const int64_t off = (int64_t)idx << lw;
+          const int64_t off = (int64_t)idx * (int64_t)w;
           const int64_t len = in->len[buf];
           const bool viol = act && (idx < 0 || off + (int64_t)w > len);
           if (act) {

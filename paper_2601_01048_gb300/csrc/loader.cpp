@@ -504,6 +504,11 @@ namespace {
 
 // Programs with at least this many kept branch sites get compact code.
 constexpr int kCompactSites = 24;
+// Programs of at most this many kept ops read their launch constants and
+// arguments once per work item, before the loop over the lane's test
+// threads; larger ones read them inside it (from the CTA's shared copy of
+// the input), which keeps them out of registers the program needs.
+constexpr int kHoistMaxOps = 24;
 
 struct Gen {
   const Ir& ir;
@@ -518,6 +523,7 @@ struct Gen {
   // enough for the instruction caches (a branch-heavy program's warps
   // diverge and walk most of its code).
   bool compact_ = false;
+  bool hoist_ = false;  // launch constants and arguments read before the loop
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -643,7 +649,7 @@ struct Gen {
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
     const bool loads_value = o2.opc == B_LD && !o2.value_dead && !shared;
     if (rec_ || loads_value)
-      line(ind + 1, "const int64_t off = (int64_t)ix << " + std::to_string(lw) + ";");
+      line(ind + 1, "const int64_t off = (int64_t)ix * " + std::to_string(1 << lw) + ";");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
     if (rec_) {
@@ -910,6 +916,10 @@ struct Gen {
   void stepped_pre(int ind, const std::vector<bool>& u) {
     const bool tx = u[0], ty = u[1], tz = u[2], bx = u[6], by = u[7], bz = u[8];
     line(ind, "const bool fix_t = inc && vin->T == blockDim.x;");
+    if (hoist_) {
+      launch_consts(ind, u);
+      line(ind, "const uint32_t T_ = vin->T, gx_ = vin->gx, gy_ = vin->grid[1];");
+    }
     line(ind, "const bool bz1 = vin->block[2] == 1u, gz1 = vin->grid[2] == 1u;");
     line(ind, "(void)fix_t; (void)bz1; (void)gz1;");
     if (tx || ty) line(ind, "uint32_t qtl = 0;");
@@ -958,6 +968,10 @@ struct Gen {
     if (bx) line(ind, "const int32_t s_bx = (int32_t)cbx;");
     if (by) line(ind, "const int32_t s_by = (int32_t)cby;");
     if (bz) line(ind, "const int32_t s_bz = (int32_t)cbz;");
+    if (!hoist_) launch_consts(ind, u);
+  }
+  // the used launch dimensions and arguments
+  void launch_consts(int ind, const std::vector<bool>& u) {
     for (int k = 0; k < 3; k++) {
       if (u[3 + k]) line(ind, std::string("const int32_t ") + sreg_name(3 + k) + " = (int32_t)vin->block[" + std::to_string(k) + "];");
       if (u[9 + k]) line(ind, std::string("const int32_t ") + sreg_name(9 + k) + " = (int32_t)vin->grid[" + std::to_string(k) + "];");
@@ -967,12 +981,15 @@ struct Gen {
   }
   void stepped_tail(int ind, const std::vector<bool>& u) {
     const bool bx = u[6], by = u[7], bz = u[8];
+    const std::string T = hoist_ ? "T_" : "vin->T", gx = hoist_ ? "gx_" : "vin->gx",
+                      gy = hoist_ ? "gy_" : "vin->grid[1]";
     line(ind, "tl += blockDim.x;");
-    std::string t = "if (tl >= vin->T) { tl -= vin->T; bl++;";
-    if (bz) t += " if (++cbx == vin->gx) { cbx = 0; if (++cby == vin->grid[1]) { cby = 0; cbz++; } }";
-    else if (by) t += " if (++cbx == vin->gx) { cbx = 0; if (++cby == vin->grid[1]) cby = 0; }";
-    else if (bx) t += " if (++cbx == vin->gx) cbx = 0;";
+    std::string t = "if (tl >= " + T + ") { tl -= " + T + "; bl++;";
+    if (bz) t += " if (++cbx == " + gx + ") { cbx = 0; if (++cby == " + gy + ") { cby = 0; cbz++; } }";
+    else if (by) t += " if (++cbx == " + gx + ") { cbx = 0; if (++cby == " + gy + ") cby = 0; }";
+    else if (bx) t += " if (++cbx == " + gx + ") cbx = 0;";
     line(ind, t + " }");
+    if (hoist_) line(ind, "(void)gx_; (void)gy_;");
   }
 
   void reg_decls(int ind, const std::vector<bool>& used) {
@@ -995,6 +1012,9 @@ struct Gen {
     int n_sites_kept = 0;
     for (const auto& op : ir.ops) n_sites_kept += op.kept && (op.opc == B_IF || op.opc == B_LOOP);
     compact_ = n_sites_kept >= kCompactSites;
+    int n_kept = 0;
+    for (const auto& op : ir.ops) n_kept += op.kept && op.opc != B_NOP;
+    hoist_ = n_kept <= kHoistMaxOps;
 
     // division faults: records of kind 2 (division), class DIV_ZERO, written
     // like access records (one atomicAdd per active-mask group)
@@ -1065,9 +1085,16 @@ struct Gen {
     line(1, "return fo;");
     line(0, "}");
 
-    // count function: a work item
+    // count function: a work item.  Its loop over the lane's test threads
+    // is unrolled CUFZ_LANES_<index> times (1 unless the module defines it):
+    // the lane mapping, k test threads per lane per iteration, which the
+    // autotuner chooses for short programs.
     rec_ = false;
     has_loop = false;
+    const std::string lanes = "CUFZ_LANES_" + std::to_string(index);
+    line(0, "#ifndef " + lanes);
+    line(0, "#define " + lanes + " 1");
+    line(0, "#endif");
     line(0, "__device__ __noinline__ void " + fn + "(uint32_t g0, uint32_t g_end) {");
     line(1, "const uint32_t slot = s_in.slot;");
     line(1, "LaneAcc acc;");
@@ -1087,7 +1114,8 @@ struct Gen {
     line(1, "uint32_t bl = 0, tl = 0;");
     line(1, "if (inc) { bl = udiv(g0 + threadIdx.x, vin->mT); tl = g0 + threadIdx.x - bl * vin->T; }");
     stepped_pre(1, sreg_used);
-    line(1, "#pragma unroll 1");
+    line(1, "constexpr int lanes_k = " + lanes + ";");
+    line(1, "#pragma unroll lanes_k");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
     stepped_in(2, sreg_used);
     // dh = the thread's digest state, nv = its violations
@@ -1127,13 +1155,18 @@ struct Gen {
 // are register-allocated together with the kernel that calls them.
 std::string jit_module_source(const std::vector<std::string>& prog_src,
                               const std::vector<uint8_t>& include, bool plain_kernel,
-                              uint32_t min_ctas, uint32_t cta_threads) {
+                              uint32_t min_ctas, uint32_t cta_threads,
+                              const std::vector<uint8_t>& lanes) {
   // the persistent kernel's launch bounds follow the context's CTA size;
   // at most 2048 resident threads per SM
   min_ctas = std::max(1u, std::min(min_ctas ? min_ctas : kJitMinCtasDefault, 2048u / cta_threads));
   std::string src = "#define CUFZ_JIT_MIN_CTAS " + std::to_string(min_ctas) +
-                    "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) +
-                    "\n#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
+                    "\n#define CUFZ_JIT_CTA_THREADS " + std::to_string(cta_threads) + "\n";
+  // each program's lane mapping (test threads per lane per loop iteration)
+  for (size_t k = 0; k < prog_src.size() && k < lanes.size(); k++)
+    if (include[k] && lanes[k] > 1)
+      src += "#define CUFZ_LANES_" + std::to_string(k) + " " + std::to_string(lanes[k]) + "\n";
+  src += "#include \"jit_kernel.cuh\"\nnamespace cufz {\n";
   for (size_t k = 0; k < prog_src.size(); k++)
     if (include[k]) src += prog_src[k];
   src += "static __device__ bool jit_run(uint32_t prog, uint32_t g0, uint32_t g_end) {\n"

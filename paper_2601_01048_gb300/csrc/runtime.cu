@@ -13,6 +13,7 @@
 #include <nvrtc.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <cstdio>
@@ -40,6 +41,11 @@ constexpr int64_t kWaitLimitUs = 120ll * 1000 * 1000;  // longest host-side wait
 constexpr double kAutotuneMargin = 1.25;  // the other path must be 25% faster
 constexpr uint64_t kAutotuneMinThreads = 1ull << 24;  // test threads timed per program and path
 constexpr size_t kAutotuneMaxInputs = 2048;
+// Lane mappings the autotuner tries (test threads per lane per iteration of
+// a compiled program's work-item loop), for programs of at most this many
+// kept ops; a wider mapping must be 3% faster to be kept.
+constexpr uint32_t kLanesMaxOps = 24;
+constexpr double kLanesMargin = 1.03;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
 
@@ -97,7 +103,9 @@ struct cufz_ctx {
   std::vector<uint64_t> prog_key;                          // autotune-cache key of each program
   std::vector<std::vector<uint8_t>> prog_bytes;            // each program as loaded (unpruned)
   std::string tune_path;                                   // autotune cache file, if any
-  std::unordered_map<uint64_t, uint8_t> tune_cache;        // key -> compiled (1) or interpreted (0)
+  // key -> the autotuner's choice: bit 0 compiled (1) or interpreted (0),
+  // bits 1..3 the lane mapping (test threads per lane per loop iteration)
+  std::unordered_map<uint64_t, uint8_t> tune_cache;
   std::vector<std::pair<uint32_t, uint32_t>> prog_free;    // unloaded program-area ranges
   uint32_t max_regs = 1, max_prog_bytes = 16;
   uint32_t max_slots = 0;
@@ -121,6 +129,11 @@ struct cufz_ctx {
   uint32_t* d_scratch_word = nullptr;
   cudaStream_t copy_stream = nullptr;
   cufz_stats stats{};
+  // device intervals (ms after ev_ref) of the last retired batches, for the
+  // overlap statistics: recorded when the stats are reset
+  cudaEvent_t ev_ref = nullptr;
+  bool ref_recorded = false;
+  std::deque<std::pair<float, float>> recent;
   // compiled path
   std::vector<std::string> prog_src;  // CUDA source of each program's item function
   cudaLibrary_t jit_lib = nullptr;
@@ -128,6 +141,8 @@ struct cufz_ctx {
   uint32_t jit_progs = 0;             // programs in the loaded module
   std::vector<uint8_t> prog_compiled; // per program: run compiled (1) or interpreted (0)
   std::vector<uint8_t> prog_in_module; // per program: its code is in the loaded module
+  std::vector<uint8_t> prog_lanes;     // per program: lane mapping (1, 2 or 4)
+  std::vector<uint8_t> lanes_in_module; // the lane mappings the loaded module was built with
   uint32_t jit_ctas_per_sm = 0;
   std::string jit_log;
 };
@@ -173,11 +188,34 @@ void lane_reset_graph(Lane& L) {
 }
 
 // Accounts the finished batch of a lane (timing) and marks it free.
+// Overlap of a retired batch's device interval [a, b) with the recent
+// ones: pairs that intersect, and the most intervals that share a moment.
+void note_interval(cufz_ctx* c, float a, float b) {
+  constexpr size_t kRecent = 256;
+  for (const auto& r : c->recent)
+    if (r.first < b && a < r.second) c->stats.overlapping_batch_pairs++;
+  c->recent.emplace_back(a, b);
+  if (c->recent.size() > kRecent) c->recent.pop_front();
+  // the most intervals containing one of the recent start points
+  uint32_t most = 0;
+  for (const auto& p : c->recent) {
+    uint32_t k = 0;
+    for (const auto& r : c->recent) k += (r.first <= p.first && p.first < r.second) ? 1u : 0u;
+    most = std::max(most, k);
+  }
+  c->stats.max_concurrent_batches = std::max(c->stats.max_concurrent_batches, most);
+}
+
 void lane_retire(cufz_ctx* c, Lane& L) {
   if (!L.busy) return;
   if (L.timed) {
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, L.ev_start, L.ev_end) == cudaSuccess) c->stats.kernel_ms += ms;
+    float a = 0.f, b = 0.f;
+    if (c->ref_recorded && cudaEventElapsedTime(&a, c->ev_ref, L.ev_start) == cudaSuccess &&
+        cudaEventElapsedTime(&b, c->ev_ref, L.ev_end) == cudaSuccess)
+      note_interval(c, a, b);
+    cudaGetLastError();
   }
   L.busy = false;
 }
@@ -285,9 +323,11 @@ std::unordered_map<std::string, std::vector<char>> g_jit_cache;  // module sourc
 cufz_status jit_build_image(const std::vector<std::string>& prog_src,
                             const std::vector<uint8_t>& include, bool plain_kernel,
                             uint32_t min_ctas, uint32_t cta_threads, bool fast,
-                            std::vector<char>* image, std::string* log) {
-  const std::string src = jit_module_source(prog_src, include, plain_kernel, min_ctas, cta_threads) +
-                          (fast ? "//fast\n" : "");
+                            const std::vector<uint8_t>& lanes, std::vector<char>* image,
+                            std::string* log) {
+  const std::string src =
+      jit_module_source(prog_src, include, plain_kernel, min_ctas, cta_threads, lanes) +
+      (fast ? "//fast\n" : "");
   {
     std::lock_guard<std::mutex> g(g_jit_cache_mu);
     auto it = g_jit_cache.find(src);
@@ -309,8 +349,10 @@ cufz_status jit_build_image(const std::vector<std::string>& prog_src,
 // persistent and plain kernels of the compiled path come from it.
 bool jit_current(const cufz_ctx* c) {
   if (!c->jit_lib || c->prog_in_module.size() != c->progs.size()) return false;
+  if (c->lanes_in_module.size() != c->progs.size()) return false;
   for (size_t k = 0; k < c->progs.size(); k++)
-    if (c->prog_compiled[k] && !c->prog_in_module[k]) return false;
+    if (c->prog_compiled[k] && (!c->prog_in_module[k] || c->lanes_in_module[k] != c->prog_lanes[k]))
+      return false;
   return true;
 }
 
@@ -320,8 +362,8 @@ cufz_status jit_compile(cufz_ctx* c) {
   const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
   std::vector<uint8_t> include = c->prog_compiled;
   cufz_status cs = jit_build_image(c->prog_src, include, plain, c->cfg.jit_min_ctas,
-                                   c->shape.cta_threads, (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &cubin,
-                                   &c->jit_log);
+                                   c->shape.cta_threads, (c->cfg.flags & CUFZ_CF_JIT_FAST_COMPILE) != 0,
+                                   c->prog_lanes, &cubin, &c->jit_log);
   if (cs != CUFZ_OK) return cs;
   // wait for work that may still run on the old module
   for (uint32_t k = 0; k < c->n_lanes; k++) {
@@ -347,6 +389,7 @@ cufz_status jit_compile(cufz_ctx* c) {
   c->jit_ctas_per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
   c->jit_progs = (uint32_t)c->progs.size();
   c->prog_in_module = include;
+  c->lanes_in_module = c->prog_lanes;
   return CUFZ_OK;
 }
 
@@ -458,8 +501,9 @@ void build_dev_input(cufz_ctx* c, const cufz_input& in, uint32_t slot, DevInput*
   d->prog_bytes = P.blob_bytes;
 }
 
-// Autotune cache: one "key path" line per program, the key a 64-bit FNV-1a
-// hash of the program's bytes and of the kernel shape it was tuned for.
+// Autotune cache: one "key path lanes" line per program, the key a 64-bit
+// FNV-1a hash of the program's bytes and of the kernel shape it was tuned
+// for (files of the first version hold "key path" lines: lanes 1).
 uint64_t tune_key(const cufz_ctx* c, const void* bytes, size_t n) {
   uint64_t h = 0xCBF29CE484222325ull;
   auto mix = [&](uint8_t b) { h = (h ^ b) * 0x100000001B3ull; };
@@ -471,15 +515,28 @@ uint64_t tune_key(const cufz_ctx* c, const void* bytes, size_t n) {
   return h;
 }
 
+bool lanes_ok(uint32_t k) { return k == 1 || k == 2 || k == 4; }
+uint8_t tune_value(bool compiled, uint32_t lanes) {
+  return (uint8_t)((compiled ? 1u : 0u) | (lanes << 1));
+}
+uint32_t tune_lanes(uint8_t v) { return lanes_ok(v >> 1) ? (uint32_t)(v >> 1) : 1u; }
+
 void tune_cache_read(cufz_ctx* c) {
   if (c->tune_path.empty()) return;
   FILE* f = fopen(c->tune_path.c_str(), "r");
   if (!f) return;  // no cache yet
   char line[128];
-  if (fgets(line, sizeof line, f) && strncmp(line, "cufz-autotune 1", 15) == 0) {
+  if (fgets(line, sizeof line, f)) {
+    const bool v1 = strncmp(line, "cufz-autotune 1", 15) == 0;
+    const bool v2 = strncmp(line, "cufz-autotune 2", 15) == 0;
     unsigned long long key = 0;
-    unsigned path = 0;
-    while (fscanf(f, "%16llx %u", &key, &path) == 2) c->tune_cache[(uint64_t)key] = path ? 1 : 0;
+    unsigned path = 0, lanes = 1;
+    while ((v1 || v2) && fgets(line, sizeof line, f)) {
+      lanes = 1;
+      const int got = sscanf(line, "%16llx %u %u", &key, &path, &lanes);
+      if (got < 2) break;
+      c->tune_cache[(uint64_t)key] = tune_value(path != 0, lanes_ok(lanes) ? lanes : 1u);
+    }
   }
   fclose(f);
 }
@@ -491,9 +548,10 @@ bool tune_cache_write(const cufz_ctx* c) {
   const std::string tmp = c->tune_path + ".tmp";
   FILE* f = fopen(tmp.c_str(), "w");
   if (!f) return false;
-  bool ok = fprintf(f, "cufz-autotune 1\n") > 0;
+  bool ok = fprintf(f, "cufz-autotune 2\n") > 0;
   for (const auto& kv : c->tune_cache)
-    ok = ok && fprintf(f, "%016llx %u\n", (unsigned long long)kv.first, (unsigned)kv.second) > 0;
+    ok = ok && fprintf(f, "%016llx %u %u\n", (unsigned long long)kv.first, kv.second & 1u,
+                       (unsigned)tune_lanes(kv.second)) > 0;
   ok = (fclose(f) == 0) && ok;
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
 }
@@ -641,6 +699,9 @@ cufz_status cufz_create(const cufz_config* cfg_in, cufz_ctx** out) {
     if (e == cudaSuccess) e = cudaHostAlloc(reinterpret_cast<void**>(&L.h_stage), L.cap, cudaHostAllocDefault);
   }
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&c->ev_ref);
+  if (e == cudaSuccess) e = cudaEventRecord(c->ev_ref, c->copy_stream);
+  c->ref_recorded = e == cudaSuccess;
   // clear the tables on the caller's stream
   if (e == cudaSuccess) e = cudaMemsetAsync(c->T.union_map, 0, kBitmapBytes, s0);
   if (e == cudaSuccess) e = cudaMemsetAsync(c->T.union_snap, 0, kBitmapBytes, s0);
@@ -687,6 +748,7 @@ cufz_status cufz_destroy(cufz_ctx* c) {
       if (L.h_stage) cudaFreeHost(L.h_stage);
     }
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->ev_ref) cudaEventDestroy(c->ev_ref);
     if (c->jit_lib) cudaLibraryUnload(c->jit_lib);
     if (c->done_h) cudaFreeHost(c->done_h);
     for (auto& p : c->progs) free_program(&p);
@@ -766,7 +828,8 @@ cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune,
   *program_id = id;
   const uint64_t key = tune_key(c, bytes, nbytes);
   const auto cached = c->tune_cache.find(key);
-  const uint8_t path0 = path >= 0 ? (uint8_t)path : cached == c->tune_cache.end() ? 1 : cached->second;
+  const uint8_t path0 = path >= 0 ? (uint8_t)path : cached == c->tune_cache.end() ? 1 : (cached->second & 1u);
+  const uint8_t lanes0 = cached == c->tune_cache.end() ? 1 : (uint8_t)tune_lanes(cached->second);
   std::vector<uint8_t> original(static_cast<const uint8_t*>(bytes), static_cast<const uint8_t*>(bytes) + nbytes);
   // default path: compiled (measured faster than the interpreter on every
   // workload family here, branch-heavy ones included); the autotuner
@@ -774,6 +837,7 @@ cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune,
   if (id == c->progs.size()) {
     c->prog_src.push_back(fsrc);
     c->prog_compiled.push_back(path0);
+    c->prog_lanes.push_back(lanes0);
     c->progs.push_back(P);
     c->prog_off.push_back(off);
     c->prog_live.push_back(1);
@@ -782,6 +846,7 @@ cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune,
   } else {
     c->prog_src[id] = fsrc;
     c->prog_compiled[id] = path0;
+    c->prog_lanes[id] = lanes0;
     c->progs[id] = P;
     c->prog_off[id] = off;
     c->prog_live[id] = 1;
@@ -1194,7 +1259,8 @@ cufz_status cufz_compile_check(const void* const* progs, const size_t* sizes, ui
   std::string lg;
   cufz_status st = jit_build_image(srcs, std::vector<uint8_t>(n, 1),
                                    (flags & CUFZ_CF_PLAIN_LAUNCH) != 0, 0, 256,
-                                   (flags & CUFZ_CF_JIT_FAST_COMPILE) != 0, &image, &lg);
+                                   (flags & CUFZ_CF_JIT_FAST_COMPILE) != 0,
+                                   std::vector<uint8_t>(n, 1), &image, &lg);
   if (log && log_cap) {
     size_t m = std::min<size_t>(lg.size(), log_cap - 1);
     memcpy(log, lg.data(), m);
@@ -1214,6 +1280,22 @@ cufz_status cufz_compile_programs(cufz_ctx* c, char* log, uint32_t log_cap) {
     log[n] = 0;
   }
   return st;
+}
+
+cufz_status cufz_set_program_lanes(cufz_ctx* c, uint32_t program_id, uint32_t lanes) {
+  if (!c || !lanes_ok(lanes)) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+  c->prog_lanes[program_id] = (uint8_t)lanes;
+  return CUFZ_OK;
+}
+
+cufz_status cufz_get_program_lanes(cufz_ctx* c, uint32_t program_id, uint32_t* lanes) {
+  if (!c || !lanes) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+  *lanes = c->prog_lanes[program_id];
+  return CUFZ_OK;
 }
 
 cufz_status cufz_set_program_path(cufz_ctx* c, uint32_t program_id, uint32_t compiled) {
@@ -1443,6 +1525,7 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   cufz_get_stats(c, &saved);
   std::unordered_map<uint32_t, std::vector<cufz_input>> by_prog;
   for (uint32_t i = 0; i < n; i++) by_prog[sample[i].program_id].push_back(sample[i]);
+  std::unordered_map<uint32_t, std::array<double, 3>> lanes_ms;  // compiled: ms at 1, 2, 4 lanes
   // a few small inputs measure launch and finalize costs, not the paths:
   // repeat each program's sample until it fills the GPU many times over
   for (auto& kv : by_prog) {
@@ -1474,7 +1557,47 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
     const uint32_t other = 1u - dflt;
     const uint32_t chosen = best[other] * kAutotuneMargin < best[dflt] ? other : dflt;
     cufz_set_program_path(c, p, chosen);
-    c->tune_cache[c->prog_key[p]] = (uint8_t)chosen;
+    c->prog_lanes[p] = 1;
+    c->tune_cache[c->prog_key[p]] = tune_value(chosen != 0, 1);
+    if (chosen) lanes_ms[p][0] = best[1];
+  }
+  // Lane mapping of short compiled programs: their sample again with 2 and
+  // 4 test threads per lane per loop iteration.  The module for these runs
+  // holds only the short programs (the others are set aside, not run).
+  std::vector<uint32_t> small;
+  for (auto& kv : lanes_ms)
+    if (c->progs[kv.first].stats.n_ops_kept <= kLanesMaxOps) small.push_back(kv.first);
+  if (!small.empty()) {
+    std::vector<uint8_t> paths = c->prog_compiled;
+    for (auto& b : c->prog_compiled) b = 0;
+    for (uint32_t p : small) c->prog_compiled[p] = 1;
+    const uint32_t ks[2] = {2, 4};
+    for (int ki = 0; ki < 2; ki++) {
+      for (uint32_t p : small) c->prog_lanes[p] = (uint8_t)ks[ki];
+      for (uint32_t p : small) {
+        double b = 1e30;
+        for (int rep = 0; rep < 3; rep++) {
+          double ms = 0;
+          cufz_status st = autotune_run(c, by_prog[p].data(), (uint32_t)by_prog[p].size(), &ms);
+          if (st != CUFZ_OK) {
+            c->prog_compiled = paths;
+            return st;
+          }
+          b = std::min(b, ms);
+        }
+        lanes_ms[p][1 + ki] = b;
+      }
+    }
+    c->prog_compiled = paths;
+    for (uint32_t p : small) {
+      const std::array<double, 3>& t = lanes_ms[p];
+      uint32_t k = 1;
+      double tk = t[0];
+      if (t[1] * kLanesMargin < tk) k = 2, tk = t[1];
+      if (t[2] * kLanesMargin < tk) k = 4;
+      c->prog_lanes[p] = (uint8_t)k;
+      c->tune_cache[c->prog_key[p]] = tune_value(true, k);
+    }
   }
   std::lock_guard<std::mutex> g(c->mu);
   c->stats = saved;
@@ -1504,6 +1627,8 @@ cufz_status cufz_reset_stats(cufz_ctx* c) {
   c->stats.n_sms = keep.n_sms;
   c->stats.max_slots = keep.max_slots;
   c->stats.smem_bytes = keep.smem_bytes;
+  c->recent.clear();
+  c->ref_recorded = cudaEventRecord(c->ev_ref, c->copy_stream) == cudaSuccess;
   return CUFZ_OK;
 }
 

@@ -23,15 +23,23 @@ def serve_open_loop(engine: "B.Engine", inputs: np.ndarray, arrivals_s: np.ndarr
     """Runs `inputs` (arrival times `arrivals_s`, seconds from start, sorted)
     through `engine`.  Results of inputs whose index is in `keep` are held
     (records and bitmaps fetched, then released); others are released as
-    soon as they are polled.  Returns (results in input order, latency in
-    seconds per input, {index: (records, bitmap)} for `keep`, wall seconds)."""
+    soon as they are polled (by the context itself when it was created with
+    CUFZ_CF_AUTO_RELEASE and nothing is kept).  Returns (results in input
+    order, latency in seconds per input, {index: (records, bitmap)} for
+    `keep`, wall seconds).
+
+    The per-result host work is done on whole poll batches: tickets are
+    handed out in submission order, one per input, so an input's index is
+    its ticket minus the first ticket of the stream."""
     inputs = np.ascontiguousarray(inputs, dtype=INPUT_DTYPE)
     n = len(inputs)
     keep = keep or set()
+    cfg = getattr(engine, "cfg", None)
+    auto = bool(getattr(cfg, "flags", 0) & B.CF_AUTO_RELEASE) and not keep
     results = np.zeros(n, B.RESULT_DTYPE)
     latency = np.full(n, np.nan)
     kept = {}
-    ticket_idx: dict[int, int] = {}
+    t_first = None
     pos = 0
     done = 0
     t0 = time.perf_counter()
@@ -41,22 +49,25 @@ def serve_open_loop(engine: "B.Engine", inputs: np.ndarray, arrivals_s: np.ndarr
         due = int(np.searchsorted(arrivals_s, now, side="right"))
         if pos < due:
             st, acc, first = B.cufz_submit_inputs(engine.ctx, inputs[pos:due])
-            for k in range(acc):
-                ticket_idx[first + k] = pos + k
+            if acc:
+                if t_first is None:
+                    t_first = first - pos
+                elif first - pos != t_first:
+                    raise B.CufzError(B.E_INVALID_ARG, "serve_open_loop: tickets out of order")
             pos += acc
         out = B.cufz_poll_results(engine.ctx, poll_max, 0)
         if len(out):
             t_done = time.perf_counter() - t0
-            for r in out:
-                t = int(r["ticket"])
-                i = ticket_idx.pop(t)
-                results[i] = r
-                latency[i] = t_done - arrivals_s[i]
-                if i in keep:
-                    recs = B.cufz_get_records(engine.ctx, t, int(r["n_records"]))
-                    bm = B.cufz_get_bitmap(engine.ctx, t)
-                    kept[i] = (recs, bm)
-                B.cufz_release(engine.ctx, t)
+            idx = out["ticket"].astype(np.int64) - t_first
+            results[idx] = out
+            latency[idx] = t_done - arrivals_s[idx]
+            if not auto:
+                for t, i in zip(out["ticket"].tolist(), idx.tolist()):
+                    if i in keep:
+                        recs = B.cufz_get_records(engine.ctx, t, int(results[i]["n_records"]))
+                        bm = B.cufz_get_bitmap(engine.ctx, t)
+                        kept[i] = (recs, bm)
+                    B.cufz_release(engine.ctx, t)
             done += len(out)
         elif pos >= due:
             # nothing to submit or collect: wait a little (next arrival or 50 us)

@@ -340,3 +340,39 @@ def test_mixed_paths_and_autotune(B, orc):
         runs.append(E.run(inputs))
     for dres, drecs, dbms in runs:
         compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, cap)
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_lane_mappings(B, orc, lanes):
+    """Each lane mapping (test threads per lane per loop iteration of the
+    compiled program), forced for every program: configuration 1 and 3
+    programs over launch shapes of every kind (blocks smaller than, equal
+    to and larger than the CTA, 1D-3D), a few random programs, and a budget
+    that stops threads inside loops, bit-exact with the oracle."""
+    progs = [gen.c1_program()] + gen.c3_programs()[:4] + gen.c2_programs()[:3]
+    c1 = gen.c1_inputs(40, seed=71)
+    c3 = gen.c3_inputs(64, seed=72, max_blocks=64)
+    c3["program_id"] = 1 + c3["program_id"] % 4
+    c2 = gen.c2_inputs(progs[5:], per_program=6, seed=73, max_grid=6)
+    c2["program_id"] += 5
+    ins = np.concatenate([c1, c3, c2])
+    rng = gen.SplitMix64(74)
+    for x in ins[-12:]:
+        x["grid"] = [rng.randint(1, 4), rng.randint(1, 4), rng.randint(1, 3)]
+        x["block"] = [(8, 8, 4), (16, 16, 1), (32, 8, 2), (5, 7, 3)][rng.below(4)]
+    for budget in (4096, 9):
+        with B.Engine(record_cap=1 << 15, max_slots=512, iter_budget=budget,
+                      flags=B.CF_KEEP_BITMAPS | B.CF_JIT) as E:
+            for p in progs:
+                E.load(p)
+            for p in range(len(progs)):
+                B.cufz_set_program_lanes(E.ctx, p, lanes)
+                assert B.cufz_get_program_lanes(E.ctx, p) == lanes
+            dres, drecs, dbms = E.run(ins)
+        o = orc.opts(iter_budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, o, rec_cap=1 << 15, bitmaps=True)
+        compare(B, orc, ins, dres, drecs, dbms, ores, orecs, obms, 1 << 15)
+    with B.Engine(flags=B.CF_JIT) as E:
+        E.load(progs[0])
+        with pytest.raises(B.CufzError):
+            B.cufz_set_program_lanes(E.ctx, 0, 3)

@@ -115,8 +115,10 @@ def _tune_key(prog: bytes, cta_threads: int, jit_min_ctas: int, flags: int) -> i
 
 
 def test_autotune_cache(B, orc, tmp_path):
-    """A cache file's choices apply at load in a new context, results stay
-    exact on the cached paths, and cufz_autotune rewrites the file."""
+    """A cache file's choices (a first-version file: paths only) apply at
+    load in a new context, results stay exact on the cached paths, and
+    cufz_autotune rewrites the file in the current version: per program its
+    path and lane mapping, which a new context applies at load."""
     progs = [gen.c3_programs()[k] for k in (0, 1, 2)]
     cache = tmp_path / "tune.txt"
     keys = [_tune_key(p, 256, 0, B.CF_JIT) for p in progs]
@@ -133,9 +135,19 @@ def test_autotune_cache(B, orc, tmp_path):
     for k in range(len(ins)):
         assert int(dres[k]["digest"]) == int(ores[k]["digest"]) and np.array_equal(dbms[k], obms[k])
     lines = cache.read_text().split("\n")
-    assert lines[0] == "cufz-autotune 1"
-    got = {int(a, 16): int(b) for a, b in (l.split() for l in lines[1:] if l)}
-    assert set(keys) <= set(got) and all(v in (0, 1) for v in got.values())
+    assert lines[0] == "cufz-autotune 2"
+    got = {int(a, 16): (int(b), int(c)) for a, b, c in (l.split() for l in lines[1:] if l)}
+    assert set(keys) <= set(got)
+    assert all(p in (0, 1) and k in (1, 2, 4) and (p or k == 1) for p, k in got.values())
+    # a forced choice written by hand is what a new context loads
+    cache.write_text("cufz-autotune 2\n" + "".join(f"{k:016x} 1 {l}\n" for k, l in zip(keys, (1, 2, 4))))
+    with B.Engine(max_slots=64, flags=B.CF_KEEP_BITMAPS | B.CF_JIT, autotune_cache=str(cache)) as E:
+        for p in progs:
+            E.load(p)
+        assert [B.cufz_get_program_lanes(E.ctx, k) for k in range(3)] == [1, 2, 4]
+        dres, _, dbms = E.run(ins)
+    for k in range(len(ins)):
+        assert int(dres[k]["digest"]) == int(ores[k]["digest"]) and np.array_equal(dbms[k], obms[k])
 
 
 @pytest.mark.parametrize("path", [0, 64])

@@ -214,7 +214,8 @@ def test_abi_rejects_missing_arguments():
         "cufz_submit_inputs": (None, 0, ref(u32), ref(u64)),
         "cufz_poll_results": (None, 0, ref(u32), 0), "cufz_get_records": (1, None, 0, ref(u32)),
         "cufz_autotune": (None, 0, ref(u32)), "cufz_verify_prune": (0, None, 0, ref(u32)),
-        "cufz_get_stats": (None,),
+        "cufz_get_stats": (None,), "cufz_set_program_lanes": (0, 1),
+        "cufz_get_program_lanes": (0, ref(u32)),
     }
     for name, args in null_ctx.items():
         assert getattr(L, name)(None, *args) == B.E_INVALID_ARG, name

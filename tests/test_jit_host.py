@@ -27,7 +27,7 @@ from paper_2601_01048_gb300 import build_ext, bytecode as bc, gen
 
 CSRC = os.path.join(os.path.dirname(build_ext.__file__), "csrc")
 SHIM = os.path.join(os.path.dirname(os.path.abspath(__file__)), "host_emulation")
-SAN = ["-fsanitize=address,undefined", "-fno-sanitize=shift-base", "-fno-sanitize-recover=all"]
+SAN = ["-fsanitize=address,undefined", "-fno-sanitize-recover=all"]
 RESULT = np.dtype([("status", "<i4"), ("flags", "<u4"), ("n_accesses", "<u8"),
                    ("n_violations", "<u8"), ("first_key", "<u8"), ("digest", "<u8"),
                    ("n_branch", "<u8"), ("n_ops", "<u8"), ("n_threads", "<u8"),

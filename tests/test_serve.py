@@ -17,8 +17,10 @@ class FakeEngine:
     """Admits up to `slots` inputs; each completes `service_s` after it was
     admitted (never, if service_s is None)."""
 
-    def __init__(self, slots, service_s):
+    def __init__(self, slots, service_s, auto_release=False):
+        import types
         self.ctx = object()
+        self.cfg = types.SimpleNamespace(flags=B.CF_AUTO_RELEASE if auto_release else 0)
         self.slots, self.service_s = slots, service_s
         self.next_ticket = 1
         self.running = {}       # ticket -> (due time, user_tag)
@@ -47,7 +49,8 @@ class FakeEngine:
         out = np.zeros(len(done), B.RESULT_DTYPE)
         for r, t in zip(out, done):
             r["ticket"], r["user_tag"], r["n_records"] = t, self.running.pop(t)[1], 2
-            self.polled.add(t)
+            if not self.cfg.flags & B.CF_AUTO_RELEASE:
+                self.polled.add(t)                            # else released by the poll
         return out
 
     def _held(self, t):
@@ -68,8 +71,8 @@ class FakeEngine:
 
 @pytest.fixture
 def fake(monkeypatch):
-    def make(slots, service_s):
-        f = FakeEngine(slots, service_s)
+    def make(slots, service_s, auto_release=False):
+        f = FakeEngine(slots, service_s, auto_release)
         monkeypatch.setattr(B, "cufz_submit_inputs", f.submit)
         monkeypatch.setattr(B, "cufz_poll_results", f.poll)
         monkeypatch.setattr(B, "cufz_get_records", f.records)
@@ -116,3 +119,14 @@ def test_stuck_engine_times_out(fake):
     with pytest.raises(B.CufzError) as ei:
         serve.serve_open_loop(f, inputs(3), np.zeros(3), timeout_s=0.2)
     assert ei.value.status == B.E_TIMEOUT and time.perf_counter() - t0 < 5
+
+
+def test_auto_release_context(fake):
+    """A context that releases results when they are polled: every input
+    completes, in input order, and the loop releases nothing itself (a
+    release of an auto-released ticket would be a read after release)."""
+    f = fake(slots=4, service_s=0.001, auto_release=True)
+    x = inputs(40)
+    res, lat, kept, _ = serve.serve_open_loop(f, x, np.linspace(0.0, 0.02, 40))
+    assert res["user_tag"].tolist() == list(range(100, 140)) and not kept
+    assert not np.isnan(lat).any() and not f.running and not f.polled
