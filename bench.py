@@ -380,6 +380,14 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
         sample = np.concatenate([inputs[inputs["program_id"] == p][:8]
                                  for p in np.unique(inputs["program_id"])])
         tuned = autotune_or_load(B, E, wl_key, sample, len(progs))
+    lanes = None
+    if tune_path:
+        # the autotuner's lane mappings: compiled programs per test threads per lane
+        lanes = {}
+        for p in range(len(progs)):
+            if B.cufz_get_program_path(E.ctx, p):
+                k = str(B.cufz_get_program_lanes(E.ctx, p))
+                lanes[k] = lanes.get(k, 0) + 1
     n_batches = (n_all + per_step - 1) // per_step
     batches = [inputs[(k * per_step) % n_all: (k * per_step) % n_all + per_step]
                for k in range(n_batches)]
@@ -476,6 +484,7 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
             "cta_threads": int(st.cta_threads),
             "jit_min_ctas": args.jit_min_ctas or 3,
             "programs_compiled": tuned,
+            "lane_mapping": lanes,
             "ctas_per_sm": int(st.ctas_per_sm),
             "item_threads": int(st.item_threads),
             "record_cap": cap,
@@ -534,6 +543,7 @@ def sub_of(line):
         "ms_per_step": line["ms_per_step"], "steps": line["steps"], "warmup": line["warmup"],
         "inputs_per_step": line["config"]["inputs_per_step"],
         "programs_compiled": line["config"]["programs_compiled"],
+        "lane_mapping": line["config"]["lane_mapping"],
         "roofline": {"bound": r["bound"], "achieved": r["achieved"], "peak": r["peak"],
                      "unit": r["unit"], "frac": r["frac"],
                      "frac_folded_heads_uncredited": r["frac_folded_heads_uncredited"]},
