@@ -75,28 +75,32 @@ def _code_only(text: str) -> str:
     return "\n".join(" ".join(l.split()) for l in "".join(out).split("\n") if l.strip())
 
 
-def kernel_key(programs, cta_threads: int = 256, min_ctas: int = 3) -> str:
+def kernel_key(programs, cta_threads: int = 256, min_ctas: int = 3, lanes=None) -> str:
     """Hash of the compiled module a workload runs: device headers, the
-    emitted code of each program, the module's launch shape."""
+    emitted code of each program, each program's lane mapping (all 1 when
+    not given), the module's launch shape."""
     from paper_2601_01048_gb300 import binding as B
 
     h = hashlib.sha256()
     for name in TRAFFIC_HEADERS:
         with open(os.path.join(ROOT, "paper_2601_01048_gb300", "csrc", name), encoding="utf-8") as f:
             h.update(_code_only(f.read()).encode())
-    for p in programs:
+    for k, p in enumerate(programs):
         h.update(_code_only(B.cufz_program_cuda(p)).encode())
+        if lanes and lanes[k] != 1:
+            h.update(f"lanes[{k}]={lanes[k]}".encode())
     h.update(f"cta_threads={cta_threads} min_ctas={min_ctas}".encode())
     return h.hexdigest()[:16]
 
 
-def measured_traffic(args, programs, per_step: int, n_all: int):
-    """DRAM bytes per launch if captured for this workload and this kernel."""
-    entry = TRAFFIC_BYTES.get(args.workload)
+def measured_traffic(args, wl_key, programs, per_step: int, n_all: int, key: str):
+    """DRAM bytes per launch if captured for this workload and this kernel
+    (its key as measure_engine computed it)."""
+    entry = TRAFFIC_BYTES.get(wl_key)
     if (entry is None or per_step != n_all or args.plain or args.path != "jit"
             or args.cta_threads not in (0, 256) or args.jit_min_ctas not in (0, 3)):
         return None
-    return entry[1] if entry[0] == kernel_key(programs) else None
+    return entry[1] if entry[0] == key else None
 
 
 # algorithmic integer ops per checked access and per branch evaluation
@@ -130,6 +134,9 @@ def parse_args():
                     help="keep the load-time path choice (for profiling a single launch)")
     ap.add_argument("--item-threads", type=int, default=0)
     ap.add_argument("--ctas-per-sm", type=int, default=0, help="persistent CTAs per SM (0: occupancy)")
+    ap.add_argument("--tune-file", default="",
+                    help="autotune cache file: tuned into when absent, loaded (no tuning) when "
+                         "present, so that a later run (a profiler's) gets the same kernels")
     ap.add_argument("--no-sub", action="store_true",
                     help="default run: leave out the other configurations' sub-records")
     return ap.parse_args()
@@ -366,7 +373,11 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
         flags |= B.CF_PREX
     if args.path == "jit":
         flags |= B.CF_JIT | (B.CF_JIT_FAST_COMPILE if args.jit_fast_compile else 0)
-    tune_path = tune_file(wl_key)[0] if args.path == "jit" and not args.no_autotune else None
+    tune_path = None
+    if args.path == "jit" and not args.no_autotune:
+        tune_path = args.tune_file or tune_file(wl_key)[0]
+        if args.tune_file and os.path.exists(args.tune_file):
+            TUNED.add(wl_key)                       # its choices load with the programs
     E = B.Engine(device=local, max_slots=per_step, record_cap=cap, flags=flags,
                  cta_threads=cta, item_threads=args.item_threads, n_lanes=2,
                  jit_min_ctas=args.jit_min_ctas, ctas_per_sm=args.ctas_per_sm,
@@ -381,12 +392,13 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
                                  for p in np.unique(inputs["program_id"])])
         tuned = autotune_or_load(B, E, wl_key, sample, len(progs))
     lanes = None
+    prog_lanes = [B.cufz_get_program_lanes(E.ctx, p) for p in range(len(progs))]
     if tune_path:
         # the autotuner's lane mappings: compiled programs per test threads per lane
         lanes = {}
         for p in range(len(progs)):
             if B.cufz_get_program_path(E.ctx, p):
-                k = str(B.cufz_get_program_lanes(E.ctx, p))
+                k = str(prog_lanes[p])
                 lanes[k] = lanes.get(k, 0) + 1
     n_batches = (n_all + per_step - 1) // per_step
     batches = [inputs[(k * per_step) % n_all: (k * per_step) % n_all + per_step]
@@ -461,6 +473,7 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
     alg_ops_folded = alg_ops - OPS_PER_BRANCH * tot["folded"]
     achieved = alg_ops / kernel_s if kernel_s > 0 else 0.0
     s = max(steps, 1)
+    key = kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3, prog_lanes)
     return {
         "metric": METRIC,
         "value": acc_all / kernel_s_max if kernel_s_max > 0 else 0.0,
@@ -509,8 +522,8 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
             "peak": peak_ops / 1e12,
             "unit": "Tops/s (int32 lane-ops)",
             "frac": achieved / peak_ops,
-            "traffic": None if plain else measured_traffic(args, progs, per_step, n_all),
-            "kernel_key": kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3),
+            "traffic": None if plain else measured_traffic(args, wl_key, progs, per_step, n_all, key),
+            "kernel_key": key,
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
             "alg_ops_per_step": alg_ops // s,
             "loop_heads_folded_per_step": tot["folded"] // s,

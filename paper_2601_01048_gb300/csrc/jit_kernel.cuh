@@ -165,9 +165,18 @@ static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t of
   return lw == 0 ? (int32_t)((word >> (8u * ((uint32_t)off & 3u))) & 0xFFu) : (int32_t)word;
 }
 
-// jit_content as one shared out-of-line copy (compact code).
-static __device__ __noinline__ int32_t jit_content_out(uint32_t seedx, int64_t off, uint32_t lw) {
-  return jit_content(seedx, off, lw);
+// The same content for an in-bounds index ix of width 2^lw, from the 32-bit
+// index: word (off >> 2) mod 2^32 is ix << (lw - 2) for lw >= 2 and ix >> 2
+// for bytes (off = ix * 2^lw < 2^48), so no 64-bit offset is formed.
+static __device__ __forceinline__ int32_t jit_content_ix(uint32_t seedx, int32_t ix, uint32_t lw) {
+  const uint32_t u = (uint32_t)ix;
+  if (lw == 0) return (int32_t)((mix32(seedx ^ (u >> 2)) >> (8u * (u & 3u))) & 0xFFu);
+  return (int32_t)mix32(seedx ^ (u << (lw - 2u)));
+}
+
+// jit_content_ix as one shared out-of-line copy (compact code).
+static __device__ __noinline__ int32_t jit_content_out(uint32_t seedx, int32_t ix, uint32_t lw) {
+  return jit_content_ix(seedx, ix, lw);
 }
 
 

@@ -647,9 +647,7 @@ struct Gen {
     line(ind, "{");
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
-    const bool loads_value = o2.opc == B_LD && !o2.value_dead && !shared;
-    if (rec_ || loads_value)
-      line(ind + 1, "const int64_t off = (int64_t)ix * " + std::to_string(1 << lw) + ";");
+    if (rec_) line(ind + 1, "const int64_t off = (int64_t)ix * " + std::to_string(1 << lw) + ";");
     uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
                     ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
     if (rec_) {
@@ -667,8 +665,11 @@ struct Gen {
         line(ind + 1, r(o2.dst) + " = 0;");
       } else {
         uint32_t seedx = ir.seed ^ ((uint32_t)o2.buf * 0x9E3779B9u);
-        line(ind + 1, r(o2.dst) + " = viol ? 0 : " + (compact_ ? "jit_content_out(" : "jit_content(") +
-                          hex32(seedx) + ", off, " + std::to_string(lw) + "u);");
+        // the record function has the 64-bit offset; the count function
+        // derives the word from the 32-bit index
+        const std::string fnc = rec_ ? "jit_content(" : compact_ ? "jit_content_out(" : "jit_content_ix(";
+        line(ind + 1, r(o2.dst) + " = viol ? 0 : " + fnc + hex32(seedx) + (rec_ ? ", off, " : ", ix, ") +
+                          std::to_string(lw) + "u);");
       }
     }
     if (rec_) line(ind + 1, "ordinal++;");
