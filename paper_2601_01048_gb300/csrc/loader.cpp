@@ -524,6 +524,15 @@ struct Gen {
   // diverge and walk most of its code).
   bool compact_ = false;
   bool hoist_ = false;  // launch constants and arguments read before the loop
+  // Path mode, for compact programs without loops and with at most 64 branch
+  // sites: each site runs at most once per test thread and sites run in
+  // program order, so a thread's edges follow from which sites it evaluated
+  // and their outcomes.  Sites only set bits in two 64-bit masks (as 32-bit
+  // halves pe0/pe1, po0/po1), and one shared out-of-line call per thread
+  // (jit_cover_path) replays the edges; the counts of a run are one add to a
+  // packed per-thread counter (n_ops, accesses and branches of a loop-free
+  // thread are bounded by the program: 12, 12 and 8 bits).
+  bool path_ = false;
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -609,6 +618,11 @@ struct Gen {
     int q = pc;
     while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
     const bool ends_at_if = q < end && ir.ops[q].opc == B_IF && ir.ops[q].kept;
+    if (path_) {
+      const uint32_t packed = (uint32_t)k | ((uint32_t)m << 12) | ((ends_at_if ? 1u : 0u) << 24);
+      if (packed) line(ind, "pk += " + hex32(packed) + ";");
+      return;
+    }
     if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
     if (m) line(ind, "acc.n_acc += " + std::to_string(m) + "u;");
     if (ends_at_if) line(ind, "acc.n_branch += 1u;");
@@ -618,6 +632,10 @@ struct Gen {
   // heads); an IF's evaluation is counted with the run that ends at it.
   void cover(int ind, int site, const std::string& cond, bool count) {
     if (rec_) return;
+    if (path_) {  // the site's evaluation bit; the outcome bit is set in the taken arm
+      line(ind, "pe" + std::to_string(site >> 5) + " |= " + hex32(1u << (site & 31)) + ";");
+      return;
+    }
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
                   "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1;" +
@@ -802,6 +820,8 @@ struct Gen {
         line(ind + 1, "const bool " + c + " = " + r(o2.a) + " != 0;");
         cover(ind + 1, o2.site, c, false);
         line(ind + 1, "if (" + c + ") {");
+        if (path_ && !rec_)
+          line(ind + 2, "po" + std::to_string(o2.site >> 5) + " |= " + hex32(1u << (o2.site & 31)) + ";");
         range(ind + 2, pc + 1, o2.else_pc >= 0 ? o2.else_pc : o2.end_pc);
         if (o2.else_pc >= 0) {
           line(ind + 1, "} else {");
@@ -1013,6 +1033,17 @@ struct Gen {
     int n_sites_kept = 0;
     for (const auto& op : ir.ops) n_sites_kept += op.kept && (op.opc == B_IF || op.opc == B_LOOP);
     compact_ = n_sites_kept >= kCompactSites;
+    bool loops = false;
+    for (const auto& op : ir.ops) loops |= op.kept && op.opc == B_LOOP;
+    path_ = compact_ && !loops && ir.n_sites <= 64;
+    if (path_) {
+      // the LOC table the path replay reads: loc0 | loc1 << 16 per site
+      std::string t = "static __device__ const uint32_t " + fn + "_loc[" +
+                      std::to_string(std::max(ir.n_sites, 1)) + "] = {";
+      for (int s = 0; s < ir.n_sites; s++)
+        t += (s ? ", " : "") + hex32((uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16));
+      line(0, t + (ir.n_sites ? "};" : "0u};"));
+    }
     int n_kept = 0;
     for (const auto& op : ir.ops) n_kept += op.kept && op.opc != B_NOP;
     hoist_ = n_kept <= kHoistMaxOps;
@@ -1123,10 +1154,15 @@ struct Gen {
     line(2, "uint32_t dh = digest_start(bl, tl);");
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
+    if (path_) line(2, "uint32_t pe0 = 0, pe1 = 0, po0 = 0, po1 = 0, pk = 0;");
     reg_decls(2, used);
     if (heap_ops) line(2, heap_decl);
     range(2, 0, (int)ir.ops.size());
     if (has_loop) line(1, "cufz_done:");
+    if (path_) {
+      line(2, "acc.n_ops += pk & 0xFFFu; acc.n_acc += (pk >> 12) & 0xFFFu; acc.n_branch += pk >> 24;");
+      line(2, "jit_cover_path(slot, pe0, pe1, po0, po1, " + fn + "_loc);");
+    }
     line(2, "if (dig) acc.digest += digest_end(dh);");
     line(2, "if (nv) {");
     line(3, "acc.n_viol += nv;");
