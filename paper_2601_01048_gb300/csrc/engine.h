@@ -65,6 +65,10 @@ struct LoadedProgram {
   uint32_t n_bufs = 0;
   uint32_t shared_mask = 0;
   std::shared_ptr<const PrexInfo> prex;  // the program as given, for the PREX check
+  // runs only in the block-serial form (compiled path; see prepare_barriers),
+  // for launches of at most kBlkMaxThreads threads per block and
+  // kBlkSharedBytes bytes of shared buffers
+  bool block_serial = false;
 };
 
 // Decodes and validates program bytes; fills `out` (device blob built with or

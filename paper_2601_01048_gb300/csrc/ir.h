@@ -40,6 +40,8 @@ struct IrOp {
   int trip = -1;       // hidden trip vreg (LOOP, ENDLOOP)
   bool kept = true;
   bool value_dead = false;
+  bool value_live = false;  // ST of a block-serial program to a shared buffer: the
+                            // stored value (register b) is performed, so a use
   int sreg = -1;       // SREG id (format level)
   int buf = -1;
   int width = 0;
@@ -52,6 +54,9 @@ struct Ir {
   std::vector<uint16_t> loc0, loc1;
   std::vector<IrOp> ops;
   int nv = 0;  // vreg count (kTripBase + loops)
+  // performed shared stores whose barriers must stay: each test block's
+  // threads run in order, phase by phase (see prepare_barriers)
+  bool block_serial = false;
 };
 
 // Decodes and validates program bytes; false on any violation of the format.
@@ -64,6 +69,16 @@ bool decode(const uint8_t* p, size_t n, Ir* ir);
 // were not performed and its barriers were gone.  True for programs whose
 // shared stores are not performed.
 bool barriers_eliminable(const Ir& ir);
+
+// BarrierElimination where it applies; otherwise the program runs in the
+// block-serial form (the compiled path's block functions: one CUDA thread
+// runs a test block's threads in thread order, phase by phase between the
+// BARs, with its shared stores performed; Sec. 4.1's collapsing transform,
+// where a block becomes a loop over its threads that barriers split, run per
+// GPU lane).  Sets ir->block_serial and marks the shared stores whose value
+// is a use.  False for such programs with divisions or heap operations,
+// which no engine runs that way.
+bool prepare_barriers(Ir* ir);
 
 // A program's decoded form as given (unpruned) for PREX, which looks at
 // every access.

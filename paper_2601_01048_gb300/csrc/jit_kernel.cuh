@@ -184,6 +184,21 @@ static __device__ __forceinline__ void jit_loop_cover(uint32_t slot, uint32_t& p
   prev = exited ? (lf >> 1) : p_exit;
 }
 
+// A performed shared store of width w at p (in bounds): the value's four
+// bytes little-endian, then zero bytes for widths 8 and 16.
+static __device__ __forceinline__ void blk_store(uint8_t* p, int32_t v, uint32_t w) {
+  const uint32_t u = (uint32_t)v;
+#pragma unroll 1
+  for (uint32_t k = 0; k < w; k++) p[k] = k < 4u ? (uint8_t)(u >> (8u * k)) : (uint8_t)0;
+}
+
+// A shared load of width w at p (in bounds): the byte, or the 32-bit word.
+static __device__ __forceinline__ int32_t blk_load(const uint8_t* p, uint32_t w) {
+  if (w == 1u) return (int32_t)p[0];
+  return (int32_t)((uint32_t)p[0] | ((uint32_t)p[1] << 8) | ((uint32_t)p[2] << 16) |
+                   ((uint32_t)p[3] << 24));
+}
+
 // Seeded content of a global buffer (seedx = program seed ^ buf * 0x9E3779B9).
 static __device__ __forceinline__ int32_t jit_content(uint32_t seedx, int64_t off, uint32_t lw) {
   const uint32_t word = mix32(seedx ^ (uint32_t)(off >> 2));

@@ -27,6 +27,13 @@ constexpr int kMaxOps = 2048;       // ops of a program as given
 constexpr int kMaxDevOps = 4096;    // device ops (kept ops + END)
 constexpr int kMaxPhysRegs = 128;   // device registers per test thread
 constexpr int kMaxPrograms = 256;
+// Block-serial programs (performed shared stores whose barriers stay): one
+// CUDA thread runs a whole test block, so a block's threads, their state
+// between phases and its shared bytes live in that thread's local memory.
+constexpr uint32_t kBlkMaxThreads = 64;   // threads per block
+constexpr uint32_t kBlkSharedBytes = 1024; // bytes of all shared buffers of a block
+constexpr uint32_t kBlkMaxSaved = 32;     // registers live across a barrier
+
 constexpr int kBitmapBytes = 65536;
 constexpr int kEdgeCount = 65536;
 constexpr int kHashSlots = 2048;    // per-CTA edge hash table (power of two)

@@ -245,7 +245,10 @@ void uses_defs(const IrOp& o, bool device_ir, int* U, int* nu, int* D, int* nd) 
       U[(*nu)++] = o.a;
       if (!(device_ir && o.value_dead)) D[(*nd)++] = o.dst;
       break;
-    case B_ST: U[(*nu)++] = o.a; break;
+    case B_ST:
+      U[(*nu)++] = o.a;
+      if (o.value_live) U[(*nu)++] = o.b;
+      break;
     case B_HALLOC: U[(*nu)++] = o.a; D[(*nd)++] = o.dst; break;
     case B_HFREE: U[(*nu)++] = o.a; break;
     case B_HLD:  // the handle and the index decide the check; the value reads 0
@@ -389,7 +392,7 @@ void propagate_sregs(Ir* ir) {
       if (o.a == r) o.a = pseudo;
       if (o.c == r) o.c = pseudo;
       if (o.b == r && o.opc != B_ST) o.b = pseudo;
-      if (o.opc == B_ST && o.b == r) o.b = -1;
+      if (o.opc == B_ST && o.b == r) o.b = o.value_live ? pseudo : -1;
     }
     def.kept = false;
   }
@@ -484,6 +487,16 @@ bool barriers_eliminable(const Ir& ir) {
   return true;
 }
 
+bool prepare_barriers(Ir* ir) {
+  if (barriers_eliminable(*ir)) return true;
+  for (const IrOp& o : ir->ops)
+    if (o.opc == B_DIV || o.opc == B_REM || is_heap_op(o.opc)) return false;
+  ir->block_serial = true;
+  for (IrOp& o : ir->ops)
+    if (o.opc == B_ST && ((ir->shared_mask >> o.buf) & 1u)) o.value_live = true;
+  return true;
+}
+
 
 // ------------------------------------------------------------ code generator
 // Emits two __device__ functions for program `index`, both with the pruned
@@ -533,6 +546,12 @@ struct Gen {
   // packed per-thread counter (n_ops, accesses and branches of a loop-free
   // thread are bounded by the program: 12, 12 and 8 bits).
   bool path_ = false;
+  // Block-serial function (a program whose performed shared stores need
+  // their barriers): accesses perform shared stores and loads in the block's
+  // bytes and write their records at once; a budget stop ends the thread's
+  // part of the current phase (stop_code_ and its label).
+  bool blk_ = false;
+  std::string stop_code_ = "acc.budget_hit = true; goto cufz_done;";
   bool has_loop = false;
 
   void line(int ind, const std::string& t) {
@@ -662,6 +681,10 @@ struct Gen {
   void access(int ind, const IrOp& o2) {
     int lw = log2w(o2.width);
     bool shared = (ir.shared_mask >> o2.buf) & 1u;
+    if (blk_) {
+      block_access(ind, o2, lw, shared);
+      return;
+    }
     line(ind, "{");
     line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
     line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
@@ -691,6 +714,39 @@ struct Gen {
       }
     }
     if (rec_) line(ind + 1, "ordinal++;");
+    line(ind, "}");
+  }
+
+  // An access of the block-serial function: the check, the digest, the
+  // record written at once, and the shared bytes stored or read in bounds
+  // (little-endian; a store of width 8 or 16 writes the 32-bit value and
+  // zero bytes, a load of width > 1 reads the 32-bit word at the offset).
+  void block_access(int ind, const IrOp& o2, int lw, bool shared) {
+    line(ind, "{");
+    line(ind + 1, "const int32_t ix = " + r(o2.a) + ";");
+    line(ind + 1, "const bool viol = (uint32_t)ix >= " + lim_name(o2.buf, lw) + ";");
+    line(ind + 1, "const int64_t off = (int64_t)ix * " + std::to_string(1 << lw) + ";");
+    line(ind + 1, "if (dig) dh = access_step(dh, " + hex32(((uint32_t)o2.site * 0xC2B2AE3Du) | 3u) + ", ix);");
+    const uint32_t what = (uint32_t)o2.site | ((uint32_t)o2.buf << 16) |
+                          ((o2.opc == B_ST ? 1u : 0u) << 20) | ((uint32_t)lw << 24);
+    line(ind + 1, "if (viol) {");
+    line(ind + 2, "acc.n_viol++;");
+    line(ind + 2, "const unsigned long long fk = first_key_of(bl, tl, ordinal);");
+    line(ind + 2, "if (fk < acc.first_key) acc.first_key = fk;");
+    line(ind + 2, "if (!rec_full) rec_full = jit_record(bl, tl, ordinal, " + hex32(what) + ", off);");
+    line(ind + 1, "}");
+    const std::string at = "shb + SB" + std::to_string(o2.buf) + " + (uint32_t)off";
+    if (o2.opc == B_ST && shared && o2.value_live)
+      line(ind + 1, "if (!viol) blk_store(" + at + ", " + r(o2.b) + ", " + std::to_string(1 << lw) + "u);");
+    if (o2.opc == B_LD && !o2.value_dead) {
+      if (shared)
+        line(ind + 1, r(o2.dst) + " = viol ? 0 : blk_load(" + at + ", " + std::to_string(1 << lw) + "u);");
+      else
+        line(ind + 1, r(o2.dst) + " = viol ? 0 : jit_content_ix(" +
+                          hex32(ir.seed ^ ((uint32_t)o2.buf * 0x9E3779B9u)) + ", ix, " +
+                          std::to_string(lw) + "u);");
+    }
+    line(ind + 1, "ordinal++;");
     line(ind, "}");
   }
 
@@ -862,7 +918,7 @@ struct Gen {
         if (m) line(ind + 1, "acc.n_acc += " + std::to_string(m) + "u * " + it + ";");
         line(ind + 1, "back += " + it + ";");
         line(ind + 1, "jit_loop_cover(slot, prev, acc, " + it + ", !" + stop + ", " + lt + ", " + lf + ");");
-        line(ind + 1, "if (" + stop + ") { acc.budget_hit = true; goto cufz_done; }");
+        line(ind + 1, "if (" + stop + ") { " + stop_code_ + " }");
         line(ind, "}");
         pc = o2.end_pc + 1;
         run_counts(ind, pc, end);
@@ -883,7 +939,7 @@ struct Gen {
         line(ind + 2, "if (!" + c + ") break;");
         range(ind + 2, pc + 1, o2.end_pc);
         line(ind + 2, rec_ ? "if (++back > budget) goto cufz_done;"
-                           : "if (++back > budget) { acc.budget_hit = true; goto cufz_done; }");
+                           : "if (++back > budget) { " + stop_code_ + " }");
         line(ind + 2, r(o2.dst) + "++;");
         line(ind + 1, "}");
         line(ind, "}");
@@ -1020,6 +1076,123 @@ struct Gen {
     if (!decl.empty()) line(ind, decl + ";");
   }
 
+  // The block-serial function cufz_prog_<index>(g0, g_end) of a program whose
+  // performed shared stores need their barriers (prepare_barriers): its work
+  // items are whole test blocks; each CUDA thread takes one block at a time
+  // and runs its threads in thread_lin order through the first phase (the
+  // ops up to the first BAR), then all of them through the next phase, and
+  // so on, as the oracle does.  Between phases a thread keeps its registers
+  // live across the barriers, ordinal, prev, back-edges and digest state in
+  // local arrays; the block's shared buffers are one local byte array (all
+  // zero at the block's start) in which in-bounds shared stores are
+  // performed and shared loads read.  A thread stopped by the budget runs no
+  // later phase.  Records are written at each violation.
+  bool too_many_saved_ = false;
+  void emit_block_serial(const std::vector<bool>& used, const std::vector<bool>& u,
+                         const std::string& fn) {
+    blk_ = true;
+    compact_ = path_ = hoist_ = false;
+    // registers live at a barrier: the state a thread carries between phases
+    Liveness Lv = liveness(ir, false);
+    std::vector<int> saved;
+    std::vector<int> bars;
+    for (int pc = 0; pc < (int)ir.ops.size(); pc++)
+      if (ir.ops[pc].opc == B_BAR) bars.push_back(pc);
+    for (int v = 0; v < kSregBase; v++) {
+      bool live = false;
+      for (int pc : bars) live |= Lv.in[pc].get(v);
+      if (live) saved.push_back(v);
+    }
+    if ((uint32_t)saved.size() > kBlkMaxSaved) {
+      too_many_saved_ = true;
+      return;
+    }
+    const int ns = std::max((int)saved.size(), 1);
+    const std::string NS = std::to_string(ns);
+    line(0, "__device__ __noinline__ void " + fn + "(uint32_t g0, uint32_t g_end) {");
+    line(1, "const uint32_t slot = s_in.slot;");
+    line(1, "LaneAcc acc;");
+    line(1, "acc_init(acc);");
+    line(1, "const uint32_t budget = s_T.iter_budget;");
+    line(1, std::string("constexpr bool dig = ") + (digest_ ? "true;" : "false;"));
+    line(1, "const DevInput* vin = &s_in;");
+    line(1, "const uint32_t* lim = s_in.lim;");
+    lim_decls(1);
+    // offsets of the shared buffers in the block's bytes
+    std::string sb = "0u";
+    for (int k = 0; k < ir.n_bufs; k++)
+      if ((ir.shared_mask >> k) & 1u) {
+        line(1, "const uint32_t SB" + std::to_string(k) + " = " + sb + ";");
+        sb = "SB" + std::to_string(k) + " + (uint32_t)vin->len[" + std::to_string(k) + "]";
+      }
+    line(1, "const uint32_t sb_total = " + sb + ";");
+    line(1, "const uint32_t T = vin->T;");
+    line(1, "const uint32_t b_first = udiv(g0, vin->mT), b_end = udiv(g_end, vin->mT);");
+    line(1, "bool rec_full = false;");
+    line(1, "#pragma unroll 1");
+    line(1, "for (uint32_t bl = b_first + threadIdx.x; bl < b_end; bl += blockDim.x) {");
+    // block coordinates
+    if (u[6] || u[7]) line(2, "const uint32_t qbl = udiv(bl, vin->mGx);");
+    if (u[7] || u[8]) line(2, "const uint32_t zbl = udiv(bl, vin->mGxy);");
+    if (u[6]) line(2, "const int32_t s_bx = (int32_t)(bl - qbl * vin->gx);");
+    if (u[7]) line(2, "const int32_t s_by = (int32_t)(qbl - zbl * vin->grid[1]);");
+    if (u[8]) line(2, "const int32_t s_bz = (int32_t)zbl;");
+    launch_consts(2, u);
+    line(2, "uint8_t shb[" + std::to_string(kBlkSharedBytes) + "];");
+    line(2, "for (uint32_t i = 0; i < sb_total; i++) shb[i] = 0;");
+    line(2, "int32_t sv[" + std::to_string(kBlkMaxThreads) + "][" + NS + "];");
+    line(2, "uint32_t s_ord[" + std::to_string(kBlkMaxThreads) + "], s_prev[" +
+                std::to_string(kBlkMaxThreads) + "], s_back[" + std::to_string(kBlkMaxThreads) +
+                "], s_dh[" + std::to_string(kBlkMaxThreads) + "];");
+    line(2, "uint8_t s_stop[" + std::to_string(kBlkMaxThreads) + "];");
+    line(2, "#pragma unroll 1");
+    line(2, "for (uint32_t t = 0; t < T; t++) {");
+    line(3, "s_ord[t] = 0; s_prev[t] = 0; s_back[t] = 0; s_dh[t] = digest_start(bl, t); s_stop[t] = 0;");
+    line(3, "for (int j = 0; j < " + NS + "; j++) sv[t][j] = 0;");
+    line(2, "}");
+    // phases
+    std::vector<std::pair<int, int>> phases;
+    int begin = 0;
+    for (int pc : bars) {
+      phases.emplace_back(begin, pc);
+      begin = pc + 1;
+    }
+    phases.emplace_back(begin, (int)ir.ops.size());
+    for (size_t p = 0; p < phases.size(); p++) {
+      const std::string label = "blk_stop_" + std::to_string(p);
+      stop_code_ = "acc.budget_hit = true; s_stop[tl] = 1; goto " + label + ";";
+      line(2, "// phase " + std::to_string(p));
+      line(2, "#pragma unroll 1");
+      line(2, "for (uint32_t tl = 0; tl < T; tl++) {");
+      line(3, "if (s_stop[tl]) continue;");
+      if (u[0] || u[1]) line(3, "const uint32_t qtl = udiv(tl, vin->mBx);");
+      if (u[1] || u[2]) line(3, "const uint32_t ztl = udiv(tl, vin->mBxy);");
+      if (u[0]) line(3, "const int32_t s_tx = (int32_t)(tl - qtl * vin->Bx);");
+      if (u[1]) line(3, "const int32_t s_ty = (int32_t)(qtl - ztl * vin->block[1]);");
+      if (u[2]) line(3, "const int32_t s_tz = (int32_t)ztl;");
+      line(3, "uint32_t ordinal = s_ord[tl], prev = s_prev[tl], back = s_back[tl], dh = s_dh[tl];");
+      line(3, "(void)prev; (void)back; (void)dh;");
+      reg_decls(3, used);
+      for (size_t j = 0; j < saved.size(); j++)
+        line(3, r(saved[j]) + " = sv[tl][" + std::to_string(j) + "];");
+      has_loop = false;
+      range(3, phases[p].first, phases[p].second);
+      if (has_loop) line(2, label + ":");
+      for (size_t j = 0; j < saved.size(); j++)
+        line(3, "sv[tl][" + std::to_string(j) + "] = " + r(saved[j]) + ";");
+      line(3, "s_ord[tl] = ordinal; s_prev[tl] = prev; s_back[tl] = back; s_dh[tl] = dh;");
+      line(2, "}");
+    }
+    line(2, "#pragma unroll 1");
+    line(2, "for (uint32_t t = 0; t < T; t++)");
+    line(3, "if (dig) acc.digest += digest_end(s_dh[t]);");
+    line(1, "}");
+    line(1, "__syncwarp();");
+    line(1, "acc_flush(s_T, slot, acc);");
+    line(0, "}");
+    blk_ = false;
+  }
+
   void emit() {
     std::vector<bool> used(ir.nv, false), sreg_used(16, false);
     int U[4], D[4], nu, nd;
@@ -1030,6 +1203,10 @@ struct Gen {
       if (op.kept && op.opc == B_SREG) sreg_used[op.sreg] = true;
     }
     const std::string fn = "cufz_prog_" + std::to_string(index);
+    if (ir.block_serial) {
+      emit_block_serial(used, sreg_used, fn);
+      return;
+    }
     int n_sites_kept = 0;
     for (const auto& op : ir.ops) n_sites_kept += op.kept && (op.opc == B_IF || op.opc == B_LOOP);
     compact_ = n_sites_kept >= kCompactSites;
@@ -1222,7 +1399,7 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
                        uint32_t index, std::string* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
-  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
+  if (!prepare_barriers(&ir)) return CUFZ_E_UNSUPPORTED;
   if (do_prune) {
     prune(&ir);
   } else {
@@ -1235,7 +1412,7 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
   Gen g{ir, *out, (int)index};
   g.digest_ = digest;
   g.emit();
-  return CUFZ_OK;
+  return g.too_many_saved_ ? CUFZ_E_UNSUPPORTED : CUFZ_OK;
 }
 
 
@@ -1304,7 +1481,7 @@ void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask,
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
-  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
+  if (!prepare_barriers(&ir)) return CUFZ_E_UNSUPPORTED;
   auto prex = std::make_shared<PrexInfo>();
   prex->ir = ir;
   int n_in = (int)ir.ops.size();
@@ -1470,6 +1647,7 @@ cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, Loaded
   out->n_bufs = (uint32_t)ir.n_bufs;
   out->shared_mask = ir.shared_mask;
   out->prex = std::move(prex);
+  out->block_serial = ir.block_serial;
   fill_stats(ir, n_in, n_regs, &out->stats);
   return CUFZ_OK;
 }
@@ -1495,7 +1673,7 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
   if ((!out && out_cap) || !out_bytes) return CUFZ_E_INVALID_ARG;
   Ir ir;
   if (!decode((const uint8_t*)bytes, nbytes, &ir)) return CUFZ_E_INVALID_PROGRAM;
-  if (!barriers_eliminable(ir)) return CUFZ_E_UNSUPPORTED;
+  if (!prepare_barriers(&ir)) return CUFZ_E_UNSUPPORTED;
   int n_in = (int)ir.ops.size();
   prune(&ir);
   std::vector<int> map;
@@ -1504,8 +1682,9 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
   if (n_regs > 255) return CUFZ_E_INVALID_PROGRAM;
   std::vector<uint8_t> v;
   std::vector<IrOp> kept;
+  // a block-serial program keeps its barriers (they order its stores)
   for (const auto& o : ir.ops)
-    if (o.kept && o.opc != B_NOP) kept.push_back(o);
+    if ((o.kept && o.opc != B_NOP) || (ir.block_serial && o.opc == B_BAR)) kept.push_back(o);
   if (kept.empty()) {  // the format needs one op
     IrOp nop;
     nop.opc = B_NOP;
@@ -1517,7 +1696,7 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
   v.push_back((uint8_t)std::max(n_regs, 1));
   v.push_back((uint8_t)ir.n_bufs);
   v.push_back((uint8_t)ir.n_sites);
-  v.push_back((uint8_t)ir.flags);  // the flag stays; the barriers are gone
+  v.push_back((uint8_t)ir.flags);  // the flag stays; eliminated barriers are gone
   put16(v, (uint16_t)ir.shared_mask);
   put16(v, 0);
   put32(v, ir.seed);
@@ -1546,7 +1725,9 @@ extern "C" cufz_status cufz_prune_program(const void* bytes, size_t nbytes, void
         case B_DIV:
         case B_REM: d = R(o.dst); a = o.value_dead ? 0 : R(o.a); b = R(o.b); break;
         case B_LD: d = R(o.dst); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
-        case B_ST: d = R(o.a); a = R(o.a); b = (uint8_t)o.buf; imm = o.width; break;
+        case B_ST:  // a stored value that is not performed is dropped (the index stands in)
+          d = o.value_live ? R(o.b) : R(o.a); a = R(o.a); b = (uint8_t)o.buf; imm = o.width;
+          break;
         case B_HALLOC: d = R(o.dst); a = R(o.a); break;
         case B_HFREE: a = R(o.a); break;
         case B_HLD: d = R(o.dst); a = R(o.a); b = R(o.b); imm = o.width; break;

@@ -83,6 +83,7 @@ extern "C" cufz_status cufz_run_noalloc(const void* program, size_t nbytes,
   // a valid program's loaded form is at most about 34 KB (2,048 ops of 16
   // bytes, header, LOC table, zero list), so this only guards the limit
   if (P.blob_bytes > kMaxProgBytes) return CUFZ_E_NOMEM;
+  if (P.block_serial) return CUFZ_E_UNSUPPORTED;  // runs only compiled, in a context
 
   cufz_result r0;
   memset(&r0, 0, sizeof(r0));

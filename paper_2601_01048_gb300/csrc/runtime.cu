@@ -556,6 +556,16 @@ bool tune_cache_write(const cufz_ctx* c) {
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
 }
 
+// A launch the block-serial form runs: a block of at most kBlkMaxThreads
+// threads, and shared buffers of at most kBlkSharedBytes bytes together.
+bool block_serial_fits(const LoadedProgram& P, const cufz_input& x) {
+  const uint64_t T = (uint64_t)x.block[0] * x.block[1] * x.block[2];
+  uint64_t sh = 0;
+  for (uint32_t k = 0; k < P.n_bufs; k++)
+    if ((P.shared_mask >> k) & 1u) sh += x.buf_len[k];
+  return T <= kBlkMaxThreads && sh <= kBlkSharedBytes;
+}
+
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
@@ -789,6 +799,12 @@ cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune,
   LoadedProgram P;
   cufz_status st = load_program(bytes, nbytes, prune, &P);
   if (st != CUFZ_OK) return st;
+  // a program in the block-serial form runs only compiled
+  if (P.block_serial && (!use_jit(c) || path == 0)) {
+    free_program(&P);
+    return CUFZ_E_UNSUPPORTED;
+  }
+  if (P.block_serial) path = 1;
   // program-area space: the first unloaded range that fits, else the end
   const uint32_t need = (uint32_t)align_up(P.blob_bytes, 16);
   uint32_t off = 0;
@@ -910,6 +926,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
       const LoadedProgram& P = c->progs[x.program_id];
       for (uint32_t k = 0; k < P.n_bufs; k++)
         if (x.buf_len[k] >= (1ull << 48)) status = CUFZ_ST_LIMIT;
+      if (P.block_serial && status == CUFZ_ST_OK && !block_serial_fits(P, x)) status = CUFZ_ST_LIMIT;
     }
     uint64_t ticket = c->next_ticket;
     if (status != CUFZ_ST_OK) {
@@ -977,11 +994,18 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     auto compiled = [&](uint32_t prog) { return use_jit(c) && c->prog_compiled[prog]; };
     uint64_t want[2] = {0, 0};
     planned.resize(n_dev);
+    // an input's item size: a multiple of its block size for block-serial
+    // programs (their items are whole test blocks)
+    auto item_of = [&](const DevInput* d) -> uint32_t {
+      if (!c->progs[d->prog].block_serial) return item;
+      return std::max<uint32_t>(d->T, item / d->T * d->T);
+    };
     for (uint32_t i = 0; i < n_dev; i++) {
       DevInput* d = &dins[i];
+      const uint32_t it = item_of(d);
       d->n_items = plain ? (uint32_t)(d->n_threads / d->T)
                  : !planned[i].empty() ? (uint32_t)planned[i].size()  // one item per planned thread
-                                       : (uint32_t)((d->n_threads + item - 1) / item);
+                                       : (uint32_t)((d->n_threads + it - 1) / it);
       if (!plain) want[compiled(d->prog) ? 0 : 1] += d->n_items;
     }
     if (want[0] + want[1] > c->lane_max_items) {
@@ -1009,9 +1033,10 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
             w.g0 = planned[i][k];
             w.count = 1;
           } else {
-            w.g0 = k * item;
-            uint64_t rem = d->n_threads - (uint64_t)k * item;
-            w.count = (uint32_t)std::min<uint64_t>(rem, item);
+            const uint32_t it = item_of(d);
+            w.g0 = k * it;
+            uint64_t rem = d->n_threads - (uint64_t)k * it;
+            w.count = (uint32_t)std::min<uint64_t>(rem, it);
           }
           w.pad = 0;
         }
@@ -1302,6 +1327,7 @@ cufz_status cufz_set_program_path(cufz_ctx* c, uint32_t program_id, uint32_t com
   if (!c) return CUFZ_E_INVALID_ARG;
   std::lock_guard<std::mutex> g(c->mu);
   if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
+  if (!compiled && c->progs[program_id].block_serial) return CUFZ_E_UNSUPPORTED;
   c->prog_compiled[program_id] = compiled ? 1 : 0;
   return CUFZ_OK;
 }
@@ -1409,14 +1435,17 @@ cufz_status cufz_verify_prune(cufz_ctx* c, uint32_t program_id, const cufz_input
   if (!c || (!inputs && n) || !n_mismatch) return CUFZ_E_INVALID_ARG;
   *n_mismatch = 0;
   std::vector<uint8_t> bytes;
+  bool serial = false;
   {
     std::lock_guard<std::mutex> g(c->mu);
     if (program_id >= c->progs.size() || !c->prog_live[program_id]) return CUFZ_E_NOT_FOUND;
     if (!c->inflight.empty() || !c->ready.empty()) return CUFZ_E_BUSY;
     bytes = c->prog_bytes[program_id];
+    serial = c->progs[program_id].block_serial;
   }
   uint32_t full = 0;
-  cufz_status st = load_into(c, bytes.data(), bytes.size(), false, 0, &full, nullptr);
+  // the unpruned program on the interpreter (block-serial programs: compiled)
+  cufz_status st = load_into(c, bytes.data(), bytes.size(), false, serial ? 1 : 0, &full, nullptr);
   if (st != CUFZ_OK) return st;
   std::vector<cufz_input> a(inputs, inputs + n), b(inputs, inputs + n);
   for (auto& x : a) x.program_id = program_id;
@@ -1543,6 +1572,7 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
   for (auto& kv : by_prog) {
     const uint32_t p = kv.first;
     if (p >= c->progs.size() || !c->prog_live[p]) continue;
+    if (c->progs[p].block_serial) continue;  // compiled only
     const uint32_t dflt = before[p];
     double best[2] = {1e30, 1e30};
     for (int rep = 0; rep < 3; rep++)

@@ -380,22 +380,29 @@ def test_barrier_elimination_keeps_every_check(orc, which):
 
 def test_barriers_stay_where_shared_values_reach_checks(orc):
     """Where a value read from a shared buffer reaches an index or a branch,
-    BarrierElimination does not apply: the library refuses to prune, compile
-    or plan such a program (CUFZ_E_UNSUPPORTED, no PREX plan), and the
-    oracle shows why: without its barriers and stores its checks change."""
+    BarrierElimination does not apply, and the oracle shows why: without its
+    barriers and stores the program's checks change.  Such a program takes
+    the block-serial form: pruning keeps its barriers and the values its
+    shared stores write (MathElimination with those values as uses), and
+    the oracle gives the pruned program the same results; it compiles, and
+    PREX plans nothing for it."""
     differs = 0
     for which in range(16):
         prog = gen.barrier_program(which, live=True)
         assert B.cufz_validate_program(prog) == 0 and orc.validate(prog) == 0
-        with pytest.raises(B.CufzError) as e:
-            B.cufz_prune_program(prog)
-        assert e.value.status == B.E_UNSUPPORTED
+        pruned, st = B.cufz_prune_program(prog)
+        assert orc.validate(pruned) == 0
+        assert [o[0] for o in bc.ops_of(pruned)].count(bc.BAR) == \
+            [o[0] for o in bc.ops_of(prog)].count(bc.BAR)
+        assert bc.decode_header(pruned)["flags"] == bc.PF_SHARED_STORES
         ins = gen.barrier_inputs(4, n_programs=1, seed=700 + which)
+        for o in (orc.opts(), orc.opts(iter_budget=2)):
+            assert _same_results(orc, prog, pruned, ins, o)
         assert all(B.cufz_prex_plan(prog, x) is None and not B.cufz_prex_check(prog, x)
                    for x in ins)
         differs += not _same_results(orc, prog, _without_barriers(prog), ins, orc.opts())
-    st, log, _ = B.cufz_compile_check([gen.barrier_program(0, live=True)])
-    assert st == B.E_UNSUPPORTED
+    st, log, _ = B.cufz_compile_check(gen.barrier_programs(live=True))
+    assert st == 0, log
     assert differs >= 8
 
 

@@ -344,3 +344,32 @@ def test_barrier_programs_match_oracle(tmp_path, host_objs, orc, flags):
             assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
             assert np.array_equal(bm, obms[i]), (budget, i)
         assert sum(int(o["n_violations"]) for o in ores) > 0
+
+
+@pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
+def test_block_serial_barrier_programs_match_oracle(tmp_path, host_objs, orc, flags):
+    """Programs whose performed shared stores reach checks, so their
+    barriers must stay: the block-serial functions (a block's threads in
+    thread order, phase by phase, stores performed in the block's bytes)
+    equal the oracle's phased execution in every result, records included,
+    pruned (stored shared values kept) and unpruned, and under a budget that
+    stops threads inside loops, which then run no later phase."""
+    progs = gen.barrier_programs(live=True)
+    ins = gen.barrier_inputs(64, seed=331)
+    exe = build(tmp_path, host_objs, progs, flags)
+    for budget in (4096, 2):
+        got = run(tmp_path, exe, progs, ins, budget=budget)
+        ores, orecs, obms = orc.run_batch(progs, ins, orc.opts(iter_budget=budget),
+                                          rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, flags, budget)
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records", "n_threads"):
+                assert int(res[f]) == int(o[f]), (budget, i, f)
+            assert int(res["n_ops"]) == ops[i], (budget, i)
+            assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
+            assert np.array_equal(bm, obms[i]), (budget, i)
+        if budget == 2:
+            assert any(int(o["flags"]) & 1 for o in ores)
