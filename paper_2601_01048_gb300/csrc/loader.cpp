@@ -708,7 +708,9 @@ struct Gen {
         uint32_t seedx = ir.seed ^ ((uint32_t)o2.buf * 0x9E3779B9u);
         // the record function has the 64-bit offset; the count function
         // derives the word from the 32-bit index
-        const std::string fnc = rec_ ? "jit_content(" : compact_ ? "jit_content_out(" : "jit_content_ix(";
+        // (inline in path mode: measured faster there than one shared copy)
+        const std::string fnc =
+            rec_ ? "jit_content(" : (compact_ && !path_) ? "jit_content_out(" : "jit_content_ix(";
         line(ind + 1, r(o2.dst) + " = viol ? 0 : " + fnc + hex32(seedx) + (rec_ ? ", off, " : ", ix, ") +
                           std::to_string(lw) + "u);");
       }
