@@ -176,7 +176,9 @@ typedef struct {
   uint32_t n_lanes;      /* batches that may overlap on the device (1..8) */
   uint32_t ctas_per_sm;  /* persistent CTAs per SM (0 = from occupancy) */
   uint32_t jit_min_ctas; /* compiled path: CTAs per SM its registers must allow (0 = 3) */
-  uint32_t reserved;
+  uint32_t lane_items;   /* work items a batch's staging memory holds (0 = 2^20); the
+                            arena grows with it (cufz_arena_bytes) and admission stops
+                            where a batch's items would exceed it */
   const char* autotune_cache; /* NULL, or a file that keeps the autotuner's
                                  per-program choices across contexts and
                                  processes (read at create, applied at load,
@@ -440,12 +442,15 @@ cufz_status cufz_verify_prune(cufz_ctx* ctx, uint32_t program_id, const cufz_inp
  * fuzzer-provided input; Sec. 4.1: every thread of every block, here on
  * the GPU), with every access checked (the ASan checks of Sec. 4) and
  * edges counted (Sec. 2.1, the AFL trampolines after branches).
- * Admits a prefix of in[0..n) while slots are free; each admitted input gets
- * ticket first_ticket + i.  Inputs with an invalid launch configuration,
- * beyond the limits or naming no program are admitted and complete at once
- * with their status, without device work.  Returns CUFZ_E_BUSY (with
- * *n_accepted < n) when it ran out of slots; the caller polls and resubmits
- * the rest.  The admitted inputs run as one batch: one persistent launch
+ * Admits a prefix of in[0..n) while slots are free and while the batch's
+ * staging memory holds the admitted inputs' work items (admission by
+ * memory: a large grid takes more of it); each admitted input gets ticket
+ * first_ticket + i.  Inputs with an invalid launch configuration, beyond
+ * the limits (an input whose work items exceed a batch's staging memory on
+ * their own included) or naming no program are admitted and complete at
+ * once with their status, without device work.  Returns CUFZ_E_BUSY (with
+ * *n_accepted < n) when it ran out of slots or staging memory; the caller
+ * polls and resubmits the rest.  The admitted inputs run as one batch: one persistent launch
  * (through a CUDA graph unless CUFZ_CF_NO_GRAPH), or one launch per input
  * with CUFZ_CF_PLAIN_LAUNCH.  Batches of successive calls overlap on the
  * device. */

@@ -49,7 +49,7 @@ class cufz_config(ctypes.Structure):
                 ("iter_budget", ctypes.c_uint32), ("max_threads", ctypes.c_uint64),
                 ("item_threads", ctypes.c_uint32), ("cta_threads", ctypes.c_uint32),
                 ("n_lanes", ctypes.c_uint32), ("ctas_per_sm", ctypes.c_uint32),
-                ("jit_min_ctas", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("jit_min_ctas", ctypes.c_uint32), ("lane_items", ctypes.c_uint32),
                 ("autotune_cache", ctypes.c_char_p)]
 
 
@@ -412,7 +412,7 @@ class Engine:
                  record_cap: int = 4096, flags: int = CF_KEEP_BITMAPS, redzone: int = 256,
                  iter_budget: int = 4096, max_threads: int = 1 << 31, cta_threads: int = 256,
                  item_threads: int = 0, n_lanes: int = 4, ctas_per_sm: int = 0,
-                 jit_min_ctas: int = 0, autotune_cache: str | None = None):
+                 jit_min_ctas: int = 0, autotune_cache: str | None = None, lane_items: int = 0):
         import torch
 
         if not torch.cuda.is_available():
@@ -430,6 +430,7 @@ class Engine:
         cfg.n_lanes = n_lanes
         cfg.ctas_per_sm = ctas_per_sm
         cfg.jit_min_ctas = jit_min_ctas
+        cfg.lane_items = lane_items
         self._tune_path = autotune_cache.encode() if autotune_cache else None
         cfg.autotune_cache = self._tune_path
         cfg.max_slots = max_slots

@@ -161,7 +161,7 @@ uint64_t fixed_bytes(const cufz_config& c, uint32_t n_slots, uint32_t* max_input
                      uint32_t* max_items) {
   uint32_t lanes = std::max(1u, std::min(c.n_lanes, kMaxLanes));
   *max_inputs = std::max(1u, std::min(n_slots, 16384u));
-  *max_items = 1u << 20;
+  *max_items = c.lane_items ? std::min(c.lane_items, 1u << 24) : 1u << 20;
   return kProgAreaBytes + 2ull * kBitmapBytes + lanes * lane_bytes(*max_inputs, *max_items) + 4096;
 }
 
@@ -566,6 +566,19 @@ bool block_serial_fits(const LoadedProgram& P, const cufz_input& x) {
   return T <= kBlkMaxThreads && sh <= kBlkSharedBytes;
 }
 
+// The status an input completes with at once (anything but OK), or OK
+// when it needs device work.
+int32_t input_status(const cufz_ctx* c, const cufz_input& x) {
+  if (x.program_id >= c->progs.size() || !c->prog_live[x.program_id]) return CUFZ_ST_BAD_PROGRAM;
+  if (launch_rejected(x)) return CUFZ_ST_INVALID_CONFIG;
+  if (!launch_within(x, c->cfg.max_threads, nullptr)) return CUFZ_ST_LIMIT;
+  const LoadedProgram& P = c->progs[x.program_id];
+  for (uint32_t k = 0; k < P.n_bufs; k++)
+    if (x.buf_len[k] >= (1ull << 48)) return CUFZ_ST_LIMIT;
+  if (P.block_serial && !block_serial_fits(P, x)) return CUFZ_ST_LIMIT;
+  return CUFZ_ST_OK;
+}
+
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
   uint32_t cta = c->shape.cta_threads;
@@ -910,23 +923,61 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
   BatchHdr* hdr_i = reinterpret_cast<BatchHdr*>(L->h_stage + sizeof(BatchHdr));
   DevInput* dins = reinterpret_cast<DevInput*>(L->h_stage + 2 * sizeof(BatchHdr));
   uint32_t n_dev = 0;
-  uint64_t batch_threads = 0;
   const bool prex_on = (c->cfg.flags & CUFZ_CF_PREX) != 0 && !plain;
   std::vector<std::vector<uint32_t>> planned;  // per device input under PREX: its threads
   std::vector<uint32_t> dev_slots;
   uint32_t accepted = 0;
   bool busy = false;
+  // The batch's work-item size, fixed before admission from the inputs the
+  // lane could take; admission then also stops where the lane's staging
+  // memory for work items runs out (a prefix is admitted, the rest gets
+  // CUFZ_E_BUSY), so inputs are admitted by memory as well as by slots.
+  uint64_t est_threads = 0;
+  {
+    const uint64_t room = std::min<uint64_t>(c->free_slots.size(), c->lane_max_inputs);
+    uint64_t k = 0;
+    for (uint32_t i = 0; i < n && k < room; i++) {
+      uint64_t nt = 0;
+      if (input_status(c, in[i]) == CUFZ_ST_OK && launch_within(in[i], ~0ull, &nt)) {
+        est_threads += nt;
+        k++;
+      }
+    }
+  }
+  const uint32_t item = choose_item_threads(c, est_threads);
+  // an input's item size: a multiple of its block size for block-serial
+  // programs (their items are whole test blocks)
+  auto item_of = [&](uint32_t prog, uint32_t T) -> uint32_t {
+    if (!c->progs[prog].block_serial) return item;
+    return std::max<uint32_t>(T, item / T * T);
+  };
+  uint64_t items_taken = 0;
   for (uint32_t i = 0; i < n; i++) {
     const cufz_input& x = in[i];
-    int32_t status = CUFZ_ST_OK;
-    if (x.program_id >= c->progs.size() || !c->prog_live[x.program_id]) status = CUFZ_ST_BAD_PROGRAM;
-    else if (launch_rejected(x)) status = CUFZ_ST_INVALID_CONFIG;
-    else {
-      if (!launch_within(x, c->cfg.max_threads, nullptr)) status = CUFZ_ST_LIMIT;
-      const LoadedProgram& P = c->progs[x.program_id];
-      for (uint32_t k = 0; k < P.n_bufs; k++)
-        if (x.buf_len[k] >= (1ull << 48)) status = CUFZ_ST_LIMIT;
-      if (P.block_serial && status == CUFZ_ST_OK && !block_serial_fits(P, x)) status = CUFZ_ST_LIMIT;
+    int32_t status = input_status(c, x);
+    std::vector<uint32_t> plan;
+    bool part = false;
+    uint64_t need = 0;  // work items of this input
+    if (status == CUFZ_ST_OK) {
+      if (c->free_slots.empty() || n_dev >= c->lane_max_inputs) {
+        busy = true;
+        break;
+      }
+      part = prex_on && c->progs[x.program_id].prex &&
+             prex_plan(*c->progs[x.program_id].prex, x, c->T.iter_budget, &plan) &&
+             plan.size() <= CUFZ_PREX_MAX_PLAN;
+      uint64_t nt = 0;
+      launch_within(x, ~0ull, &nt);
+      const uint32_t T = x.block[0] * x.block[1] * x.block[2];
+      const uint64_t it = item_of(x.program_id, T);
+      need = plain ? 0 : part ? plan.size() : (nt + it - 1) / it;
+      if (items_taken + need > c->lane_max_items) {
+        if (n_dev > 0) {
+          busy = true;
+          break;
+        }
+        status = CUFZ_ST_LIMIT;  // more work items than a lane holds, even alone
+      }
     }
     uint64_t ticket = c->next_ticket;
     if (status != CUFZ_ST_OK) {
@@ -962,19 +1013,16 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     sh.lane = lane_idx;
     sh.prog = x.program_id;
     sh.partial = false;
-    std::vector<uint32_t> plan;
-    if (prex_on && c->progs[x.program_id].prex &&
-        prex_plan(*c->progs[x.program_id].prex, x, c->T.iter_budget, &plan) &&
-        plan.size() <= CUFZ_PREX_MAX_PLAN) {
+    if (part) {
       // these threads decide the verdict: run only them
       planned.resize(n_dev + 1);
       planned[n_dev] = std::move(plan);
       d->n_threads = planned[n_dev].size();
       sh.partial = true;
     }
+    items_taken += need;
     c->ticket_slot[ticket] = s;
     dev_slots.push_back(s);
-    batch_threads += d->n_threads;
     n_dev++;
     c->next_ticket++;
     accepted++;
@@ -985,7 +1033,6 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     // work items: one list per path, each grouped by program (stable), so
     // CTAs running at the same time mostly run the same program
     uint8_t* items_base = reinterpret_cast<uint8_t*>(dins) + (uint64_t)n_dev * sizeof(DevInput);
-    uint32_t item = choose_item_threads(c, batch_threads);
     c->stats.item_threads = item;
     std::vector<uint32_t> order(n_dev);
     for (uint32_t i = 0; i < n_dev; i++) order[i] = i;
@@ -994,30 +1041,15 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
     auto compiled = [&](uint32_t prog) { return use_jit(c) && c->prog_compiled[prog]; };
     uint64_t want[2] = {0, 0};
     planned.resize(n_dev);
-    // an input's item size: a multiple of its block size for block-serial
-    // programs (their items are whole test blocks)
-    auto item_of = [&](const DevInput* d) -> uint32_t {
-      if (!c->progs[d->prog].block_serial) return item;
-      return std::max<uint32_t>(d->T, item / d->T * d->T);
-    };
     for (uint32_t i = 0; i < n_dev; i++) {
       DevInput* d = &dins[i];
-      const uint32_t it = item_of(d);
+      const uint32_t it = item_of(d->prog, d->T);
       d->n_items = plain ? (uint32_t)(d->n_threads / d->T)
                  : !planned[i].empty() ? (uint32_t)planned[i].size()  // one item per planned thread
                                        : (uint32_t)((d->n_threads + it - 1) / it);
       if (!plain) want[compiled(d->prog) ? 0 : 1] += d->n_items;
     }
-    if (want[0] + want[1] > c->lane_max_items) {
-      // roll back every device input of this call: more work items than a lane holds
-      for (uint32_t s : dev_slots) {
-        c->ticket_slot.erase(c->slots[s].ticket);
-        c->slots[s].state = 0;
-        c->free_slots.push_back(s);
-      }
-      *n_accepted = 0;
-      return CUFZ_E_NOMEM;
-    }
+    // (admission kept want[0] + want[1] within the lane's lane_max_items)
     WorkItem* lists[2] = {reinterpret_cast<WorkItem*>(items_base),
                           reinterpret_cast<WorkItem*>(items_base) + want[0]};
     uint32_t counts[2] = {0, 0};
@@ -1033,7 +1065,7 @@ cufz_status cufz_submit_inputs(cufz_ctx* c, const cufz_input* in, uint32_t n, ui
             w.g0 = planned[i][k];
             w.count = 1;
           } else {
-            const uint32_t it = item_of(d);
+            const uint32_t it = item_of(d->prog, d->T);
             w.g0 = k * it;
             uint64_t rem = d->n_threads - (uint64_t)k * it;
             w.count = (uint32_t)std::min<uint64_t>(rem, it);

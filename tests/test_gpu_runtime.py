@@ -169,3 +169,43 @@ def test_verify_prune(B, path):
         with pytest.raises(B.CufzError) as ei:
             B.cufz_verify_prune(E.ctx, 9, c2[:1])
         assert ei.value.status == B.E_NOT_FOUND
+
+
+def test_admission_by_staging_memory(B, orc):
+    """A batch admits inputs while its staging memory holds their work
+    items: with room for 64 items of 2,048 test threads, a submit of inputs
+    of 8 items each admits 8 of them and answers BUSY; resubmitting the rest
+    as slots and lanes free up runs every input, and each equals the oracle.
+    An input whose items exceed that memory on their own completes as
+    LIMIT."""
+    prog = gen.c1_program()
+    ins = gen.c1_inputs(20, seed=51)
+    for x in ins:
+        x["grid"] = [128, 1, 1]                       # 16,384 threads: 8 items
+    big = gen.make_inputs(1)
+    gen.set_input(big[0], 0, (2048, 1, 1), (128, 1, 1), (0, 100), (400, 400, 400, 400))  # 128 items
+    with B.Engine(max_slots=64, n_lanes=1, item_threads=2048, lane_items=64,
+                  flags=B.CF_KEEP_BITMAPS | B.CF_AUTO_RELEASE) as E:
+        E.load(prog)
+        st, acc, first = B.cufz_submit_inputs(E.ctx, ins)
+        assert st == B.E_BUSY and acc == 8, (st, acc)
+        B.cufz_sync(E.ctx)
+        out = list(B.cufz_poll_results(E.ctx, 64, 0))
+        pos = acc
+        while pos < len(ins):
+            st, acc, _ = B.cufz_submit_inputs(E.ctx, ins[pos:])
+            assert acc > 0
+            pos += acc
+            B.cufz_sync(E.ctx)
+            out += list(B.cufz_poll_results(E.ctx, 64, 0))
+        st, acc, _ = B.cufz_submit_inputs(E.ctx, big)
+        assert acc == 1
+        B.cufz_sync(E.ctx)
+        lim = B.cufz_poll_results(E.ctx, 4, 0)
+    assert [int(r["status"]) for r in lim] == [B.ST_LIMIT]
+    res = sorted(out, key=lambda r: int(r["ticket"]))
+    assert len(res) == len(ins)
+    ores, _, _ = orc.run_batch([prog], ins)
+    for k in range(len(ins)):
+        for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch"):
+            assert int(res[k][f]) == int(ores[k][f]), (k, f)
