@@ -116,7 +116,7 @@ def parse_args():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2",
                     choices=["c1", "c2", "c3", "c4", "c5", "affine", "guard2d", "div", "heap",
-                             "barrier"])
+                             "barrier", "barrier_live"])
     ap.add_argument("--prex", action="store_true",
                     help="partial representative execution: inputs with a PREX plan run only its threads")
     ap.add_argument("--rate", type=float, default=50000.0, help="c5: offered inputs/s")
@@ -172,6 +172,11 @@ def workload(name: str, rank: int = 0):
         return ("heap: 8192 inputs over 16 programs on the per-thread device heap (use after "
                 "free, double and invalid frees, heap bounds), blocks of 16x2, grids up to 4096 "
                 "blocks", gen.heap_programs(), gen.heap_inputs(8192, max_blocks=4096), 4096)
+    if name == "barrier_live":
+        return ("barrier_live: 8192 inputs over 16 programs whose performed shared stores reach "
+                "checks (barriers kept; the block-serial form), blocks of 16-32 threads, grids "
+                "up to 4096 blocks", gen.barrier_programs(live=True),
+                gen.barrier_inputs(8192, max_blocks=4096), 4096)
     if name == "barrier":
         return ("barrier: 8192 inputs over 16 programs with performed shared stores in 2-4 "
                 "barrier phases that BarrierElimination removes, blocks of 16-32 threads, grids "

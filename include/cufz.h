@@ -534,8 +534,12 @@ cufz_status cufz_get_program_lanes(cufz_ctx* ctx, uint32_t program_id, uint32_t*
  * the program off its load-time path only if the other is at least 25%
  * faster.  Then, for compiled programs of at most 24 kept ops, it times the
  * lane mappings 2 and 4 the same way and keeps the fastest (a wider mapping
- * must win by 3%).  The choices go to the autotune cache, if the config
- * names one.  Needs an idle context; the sample's results are discarded.
+ * must win by 3%).  Last, unless the config fixes item_threads, it times
+ * the whole sample (an equal share of each program's, at most 4096 inputs)
+ * with work items of the size heuristic's choice and of 4096, 16384, 65536
+ * and 262144 test threads, and keeps the fastest (3% margin) for the set of
+ * programs loaded (reported in cufz_stats.item_threads once a batch ran).
+ * The choices go to the autotune cache, if the config names one.  Needs an idle context; the sample's results are discarded.
  * *n_compiled receives the number of programs left on the compiled path. */
 cufz_status cufz_autotune(cufz_ctx* ctx, const cufz_input* sample, uint32_t n,
                           uint32_t* n_compiled);

@@ -45,6 +45,8 @@ constexpr size_t kAutotuneMaxInputs = 2048;
 // a compiled program's work-item loop), for programs of at most this many
 // kept ops; a wider mapping must be 3% faster to be kept.
 constexpr uint32_t kLanesMaxOps = 24;
+// Inputs of the sample the work-item size is timed on.
+constexpr size_t kAutotuneItemInputs = 4096;
 constexpr double kLanesMargin = 1.03;
 
 uint64_t align_up(uint64_t x, uint64_t a) { return (x + a - 1) / a * a; }
@@ -106,6 +108,10 @@ struct cufz_ctx {
   // key -> the autotuner's choice: bit 0 compiled (1) or interpreted (0),
   // bits 1..3 the lane mapping (test threads per lane per loop iteration)
   std::unordered_map<uint64_t, uint8_t> tune_cache;
+  // the autotuner's work-item size per set of loaded programs (key: the sum
+  // of their cache keys), and the one in force (0: the size heuristic)
+  std::unordered_map<uint64_t, uint32_t> tune_items;
+  uint32_t tuned_item = 0;
   std::vector<std::pair<uint32_t, uint32_t>> prog_free;    // unloaded program-area ranges
   uint32_t max_regs = 1, max_prog_bytes = 16;
   uint32_t max_slots = 0;
@@ -516,6 +522,21 @@ uint64_t tune_key(const cufz_ctx* c, const void* bytes, size_t n) {
 }
 
 bool lanes_ok(uint32_t k) { return k == 1 || k == 2 || k == 4; }
+
+// The key of the loaded program set for the work-item size: the sum of the
+// live programs' cache keys (independent of load order).
+uint64_t workload_key(const cufz_ctx* c) {
+  uint64_t k = 0;
+  for (size_t p = 0; p < c->progs.size(); p++)
+    if (c->prog_live[p]) k += c->prog_key[p];
+  return k;
+}
+
+// Applies the cached work-item size of the loaded program set, if any.
+void apply_tuned_item(cufz_ctx* c) {
+  const auto it = c->tune_items.find(workload_key(c));
+  c->tuned_item = it == c->tune_items.end() ? 0u : it->second;
+}
 uint8_t tune_value(bool compiled, uint32_t lanes) {
   return (uint8_t)((compiled ? 1u : 0u) | (lanes << 1));
 }
@@ -533,6 +554,11 @@ void tune_cache_read(cufz_ctx* c) {
     unsigned path = 0, lanes = 1;
     while ((v1 || v2) && fgets(line, sizeof line, f)) {
       lanes = 1;
+      unsigned items = 0;
+      if (sscanf(line, "item %16llx %u", &key, &items) == 2) {
+        if (items && items % 32 == 0) c->tune_items[(uint64_t)key] = items;
+        continue;
+      }
       const int got = sscanf(line, "%16llx %u %u", &key, &path, &lanes);
       if (got < 2) break;
       c->tune_cache[(uint64_t)key] = tune_value(path != 0, lanes_ok(lanes) ? lanes : 1u);
@@ -552,6 +578,8 @@ bool tune_cache_write(const cufz_ctx* c) {
   for (const auto& kv : c->tune_cache)
     ok = ok && fprintf(f, "%016llx %u %u\n", (unsigned long long)kv.first, kv.second & 1u,
                        (unsigned)tune_lanes(kv.second)) > 0;
+  for (const auto& kv : c->tune_items)
+    ok = ok && fprintf(f, "item %016llx %u\n", (unsigned long long)kv.first, kv.second) > 0;
   ok = (fclose(f) == 0) && ok;
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
 }
@@ -581,6 +609,7 @@ int32_t input_status(const cufz_ctx* c, const cufz_input& x) {
 
 uint32_t choose_item_threads(cufz_ctx* c, uint64_t batch_threads) {
   if (c->cfg.item_threads) return c->cfg.item_threads;
+  if (c->tuned_item) return c->tuned_item;
   uint32_t cta = c->shape.cta_threads;
   uint64_t target = batch_threads / (8ull * std::max(std::max(interp_ctas(c), jit_ctas(c)), 1u));
   uint64_t lo = 2ull * cta, hi = 256ull * cta;
@@ -885,6 +914,7 @@ cufz_status load_into(cufz_ctx* c, const void* bytes, size_t nbytes, bool prune,
   }
   c->shape.max_regs = std::max(c->shape.max_regs, P.hdr.n_regs);
   c->shape.max_prog_bytes = std::max(c->shape.max_prog_bytes, (uint32_t)align_up(P.blob_bytes, 16));
+  apply_tuned_item(c);
   return ensure_smem(c);
 }
 
@@ -1377,6 +1407,7 @@ cufz_status cufz_unload_program(cufz_ctx* c, uint32_t program_id) {
   c->prog_live[program_id] = 0;
   c->prog_compiled[program_id] = 0;
   c->prog_src[program_id].clear();
+  apply_tuned_item(c);
   return CUFZ_OK;
 }
 
@@ -1660,6 +1691,46 @@ cufz_status cufz_autotune(cufz_ctx* c, const cufz_input* sample, uint32_t n, uin
       c->prog_lanes[p] = (uint8_t)k;
       c->tune_cache[c->prog_key[p]] = tune_value(true, k);
     }
+  }
+  // The work-item size (test threads a CTA takes at a time, so how many
+  // inputs a CTA serves): the whole sample, an equal share of every
+  // program's and at most 4096 inputs, timed at a few sizes; a size other
+  // than the heuristic's must be 3% faster.  Kept for this set of programs.
+  if (!c->cfg.item_threads && !by_prog.empty()) {
+    std::vector<cufz_input> all;
+    for (size_t k = 0; all.size() < kAutotuneItemInputs; k++) {
+      bool more = false;
+      for (auto& kv : by_prog)
+        if (k < kv.second.size() && all.size() < kAutotuneItemInputs) {
+          all.push_back(kv.second[k]);
+          more = true;
+        }
+      if (!more) break;
+    }
+    const uint32_t cands[] = {0u, 4096u, 16384u, 65536u, 262144u};
+    double base = 1e30, best_ms = 1e30;
+    uint32_t best = 0;
+    for (uint32_t cand : cands) {
+      c->tuned_item = cand;
+      double b = 1e30;
+      for (int rep = 0; rep < 2; rep++) {
+        double ms = 0;
+        cufz_status st = autotune_run(c, all.data(), (uint32_t)all.size(), &ms);
+        if (st != CUFZ_OK) {
+          apply_tuned_item(c);
+          return st;
+        }
+        b = std::min(b, ms);
+      }
+      if (cand == 0) base = b;
+      if (b < best_ms) best_ms = b, best = cand;
+    }
+    if (best && best_ms * kLanesMargin >= base) best = 0;
+    c->tuned_item = best;
+    if (best)
+      c->tune_items[workload_key(c)] = best;
+    else
+      c->tune_items.erase(workload_key(c));
   }
   std::lock_guard<std::mutex> g(c->mu);
   c->stats = saved;
