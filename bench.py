@@ -45,8 +45,9 @@ LANES_PER_SM = 128
 # workload's programs, with the module's launch shape.  Once the kernel
 # changes the figure no longer applies and is reported as null.
 TRAFFIC_HEADERS = ("jit_kernel.cuh", "jit_launch.cuh", "device_common.cuh", "layout.h")
-TRAFFIC_BYTES: dict[str, tuple[str, int]] = {
-    "c2": ("87b412013a63f0b3", 58_376_448 + 1_471_800_576),
+TRAFFIC_BYTES: dict[str, tuple[str, int, str]] = {
+    "c2": ("b67b6284fa2ef920", 55_926_016 + 1_496_278_016,
+           "lane mapping {1: 28, 2: 3, 4: 1}, item_threads 65536"),
 }
 
 
@@ -93,14 +94,17 @@ def kernel_key(programs, cta_threads: int = 256, min_ctas: int = 3, lanes=None) 
     return h.hexdigest()[:16]
 
 
-def measured_traffic(args, wl_key, programs, per_step: int, n_all: int, key: str):
-    """DRAM bytes per launch if captured for this workload and this kernel
-    (its key as measure_engine computed it)."""
+def measured_traffic(args, wl_key, per_step: int, n_all: int, code_key: str):
+    """DRAM bytes per launch if captured for this workload and this code (the
+    kernel key without the lane mapping: a mapping and an item size decide
+    which lane runs which test thread, while the bytes a launch reads and
+    writes are its inputs, bitmaps, records and results), with the settings
+    of the capture."""
     entry = TRAFFIC_BYTES.get(wl_key)
     if (entry is None or per_step != n_all or args.plain or args.path != "jit"
             or args.cta_threads not in (0, 256) or args.jit_min_ctas not in (0, 3)):
-        return None
-    return entry[1] if entry[0] == key else None
+        return None, None
+    return (entry[1], entry[2]) if entry[0] == code_key else (None, None)
 
 
 # algorithmic integer ops per checked access and per branch evaluation
@@ -120,6 +124,7 @@ def parse_args():
     ap.add_argument("--prex", action="store_true",
                     help="partial representative execution: inputs with a PREX plan run only its threads")
     ap.add_argument("--rate", type=float, default=50000.0, help="c5: offered inputs/s")
+    ap.add_argument("--lanes", type=int, default=4, help="c5: batches that may overlap (1-8)")
     ap.add_argument("--duration", type=float, default=2.0, help="c5: seconds of arrivals")
     ap.add_argument("--inputs-per-step", type=int, default=0, help="0: the whole workload")
     ap.add_argument("--plain", action="store_true", help="one kernel launch per input")
@@ -479,6 +484,9 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
     achieved = alg_ops / kernel_s if kernel_s > 0 else 0.0
     s = max(steps, 1)
     key = kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3, prog_lanes)
+    code_key = kernel_key(progs, int(st.cta_threads), args.jit_min_ctas or 3)
+    traffic, traffic_with = ((None, None) if plain else
+                             measured_traffic(args, wl_key, per_step, n_all, code_key))
     return {
         "metric": METRIC,
         "value": acc_all / kernel_s_max if kernel_s_max > 0 else 0.0,
@@ -527,8 +535,10 @@ def measure_engine(args, wl_key, plain, steps, warmup, per_step_arg, rank, world
             "peak": peak_ops / 1e12,
             "unit": "Tops/s (int32 lane-ops)",
             "frac": achieved / peak_ops,
-            "traffic": None if plain else measured_traffic(args, wl_key, progs, per_step, n_all, key),
+            "traffic": traffic,
+            "traffic_captured_with": traffic_with,
             "kernel_key": key,
+            "code_key": code_key,
             "peak_source": f"{n_sm} SMs x 128 int32 lanes/clk x {sm_max:.0f} MHz (derived)",
             "alg_ops_per_step": alg_ops // s,
             "loop_heads_folded_per_step": tot["folded"] // s,
@@ -682,7 +692,7 @@ def measure_serving(args, rate, duration, plain, rank, world, local, pg):
     if args.path == "jit":
         flags |= B.CF_JIT
     tune_path = tune_file("c5")[0] if args.path == "jit" else None
-    E = B.Engine(device=local, max_slots=4096, record_cap=1024, flags=flags, n_lanes=4,
+    E = B.Engine(device=local, max_slots=4096, record_cap=1024, flags=flags, n_lanes=args.lanes,
                  cta_threads=args.cta_threads, autotune_cache=tune_path)
     for p in progs:
         E.load(p)
@@ -711,7 +721,7 @@ def measure_serving(args, rate, duration, plain, rank, world, local, pg):
                                "32 random 2D, 16 branch-heavy), mutated inputs",
                    "offered_rate": rate, "duration_s": duration, "inputs": len(stream),
                    "path": "plain one launch per input" if plain else
-                           "persistent kernels in CUDA graphs, 4 overlapping lanes",
+                           f"persistent kernels in CUDA graphs, {args.lanes} overlapping lanes",
                    "programs_compiled": tuned, "parallelism": f"replicas x{world}"},
         "inputs_per_s": len(stream) / wall,
         "latency_ms": {"p50": 1e3 * float(np.nanpercentile(lat, 50)),
