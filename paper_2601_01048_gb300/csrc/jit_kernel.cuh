@@ -132,6 +132,12 @@ static __device__ __forceinline__ void jit_cover(uint32_t slot, uint32_t e) {
   if (!edge_saturated(s_hash, e)) jit_cover_lane(slot, e);
 }
 
+// jit_cover for an edge whose word w and bit b in the saturated-edge bitmap
+// are known (e >> 5 and 1 << (e & 31), constants of the emitted code).
+static __device__ __forceinline__ void jit_cover_k(uint32_t slot, uint32_t e, uint32_t w, uint32_t b) {
+  if (!(s_hash[kHashSlots + w] & b)) jit_cover_lane(slot, e);
+}
+
 // jit_cover as one shared out-of-line copy, for programs compiled to compact
 // code (many branch sites): a call at each site instead of the inline test.
 static __device__ __noinline__ void jit_cover_out(uint32_t slot, uint32_t e) { jit_cover(slot, e); }
@@ -161,9 +167,91 @@ static __device__ __noinline__ void jit_cover_path(uint32_t slot, uint32_t e0, u
   }
 }
 
+// Path counting (path-mode programs).  In a loop-free program a thread's
+// edges follow from its path: the sites it evaluates and their outcomes.
+// The outcome bits po (bit s: site s took its then-arm) fix the path alone:
+// which site comes after site s is a function of s and its outcome (the
+// program's structure), so the sites evaluated need no bits of their own.
+// walk[s].x = LOC[s][0] | LOC[s][1] << 16 and walk[s].y = next[s][0] |
+// next[s][1] << 8, the site evaluated after s for each outcome (>= 64: none).
+// A thread adds its path to a per-CTA table of paths and counts; after its
+// work item the CTA replays each distinct path once, adding its count to
+// every edge of the path, so threads on one path share one replay.  A path
+// that finds no room in the table is replayed by its thread at once.
+#ifndef CUFZ_PATH_SLOTS_LOG2
+#define CUFZ_PATH_SLOTS_LOG2 11
+#endif
+constexpr uint32_t kPathSlots = 1u << CUFZ_PATH_SLOTS_LOG2;
+constexpr int kPathProbes = kPathSlots < 8u ? (int)kPathSlots : 8;
+static __shared__ unsigned long long s_pkey[kPathSlots];  // path + 1, 0 = empty
+static __shared__ uint32_t s_pcnt[kPathSlots];
+
 // n hits of edge e at once (n may differ between lanes, and be 0).
 static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
   if (n != 0 && !edge_saturated(s_hash, e)) jit_cover_slow(slot, e, n);
+}
+
+// The edges of path (po1:po0), m threads on it, starting at site s.  One
+// shared out-of-line copy.
+static __device__ __noinline__ void jit_path_walk(uint32_t slot, uint32_t po0, uint32_t po1,
+                                                  uint32_t m, const uint2* __restrict__ walk,
+                                                  uint32_t s) {
+  uint32_t prev = 0;
+#pragma unroll 1
+  while (s < 64u) {
+    const uint2 w = walk[s];
+    const uint32_t o = ((s < 32u ? po0 : po1) >> (s & 31u)) & 1u;
+    const uint32_t cur = o ? (w.x >> 16) : (w.x & 0xFFFFu);
+    jit_cover_n(slot, (cur ^ prev) & 0xFFFFu, m);
+    prev = cur >> 1;
+    s = o ? (w.y >> 8) & 0xFFu : w.y & 0xFFu;
+  }
+}
+
+// Empties the CTA's path table; every thread of the CTA calls it.
+static __device__ __forceinline__ void jit_path_clear() {
+  for (uint32_t i = threadIdx.x; i < kPathSlots; i += blockDim.x) {
+    s_pkey[i] = 0ull;
+    s_pcnt[i] = 0u;
+  }
+  __syncthreads();
+}
+
+// Counts one thread on path (po1:po0) in the CTA's table; false when the
+// path found no room (within kPathProbes slots of its home).
+static __device__ __forceinline__ bool jit_path_count(uint32_t po0, uint32_t po1) {
+  const unsigned long long key = (((unsigned long long)po1 << 32) | po0) + 1ull;
+  if (key == 0ull) return false;  // every one of 64 sites taken: no key left for it
+  uint32_t h = ((po0 * 0x9E3779B1u) ^ (po1 * 0x85EBCA77u)) >> (32 - CUFZ_PATH_SLOTS_LOG2);
+#pragma unroll 1
+  for (int p = 0; p < kPathProbes; p++) {
+    unsigned long long k = s_pkey[h];
+    if (k == 0ull) {
+      k = atomicCAS(&s_pkey[h], 0ull, key);
+      if (k == 0ull) k = key;
+    }
+    if (k == key) {
+      atomicAdd(&s_pcnt[h], 1u);
+      return true;
+    }
+    h = (h + 1u) & (kPathSlots - 1u);
+  }
+  return false;
+}
+
+// Replays every path of the table with its count; every thread of the CTA
+// calls it, after its last thread of the work item.
+static __device__ __noinline__ void jit_path_flush(uint32_t slot, const uint2* __restrict__ walk,
+                                                   uint32_t first) {
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kPathSlots; i += blockDim.x) {
+    const unsigned long long k = s_pkey[i];
+    if (k) {
+      const unsigned long long po = k - 1ull;
+      jit_path_walk(slot, (uint32_t)po, (uint32_t)(po >> 32), s_pcnt[i], walk, first);
+    }
+  }
+  __syncthreads();
 }
 
 // Edges of the head evaluations of one execution of a loop whose body has no

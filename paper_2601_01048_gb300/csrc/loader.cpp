@@ -16,6 +16,7 @@
 #include <cstring>
 #include <cstdio>
 #include <string>
+#include <array>
 #include <vector>
 
 #include "checked_ops.h"
@@ -517,6 +518,9 @@ namespace {
 
 // Programs with at least this many kept branch sites get compact code.
 constexpr int kCompactSites = 24;
+// Path-mode programs count their threads' paths per CTA and replay each
+// distinct path once per work item (jit_path_count, jit_path_flush).
+constexpr bool kPathCounting = true;
 // Programs of at most this many kept ops read their launch constants and
 // arguments once per work item, before the loop over the lane's test
 // threads; larger ones read them inside it (from the CTA's shared copy of
@@ -553,6 +557,22 @@ struct Gen {
   bool blk_ = false;
   std::string stop_code_ = "acc.budget_hit = true; goto cufz_done;";
   bool has_loop = false;
+  // The AFL state prev where the code being emitted runs, when the
+  // generator knows it (count function, not in path mode): kp_ with value
+  // pv_, else the run-time variable prev holds it.  After a branch site each
+  // successor knows it (LOC[site][outcome] >> 1), so a site's edge is a
+  // choice between two constants wherever the site before it is known,
+  // and prev is written only where paths with different values join (the
+  // end of an IF, a loop head).
+  bool sp_ = false;
+  bool kp_ = false;
+  uint32_t pv_ = 0;
+
+  // Makes the run-time variable hold prev (at a join or a loop head).
+  void materialize(int ind) {
+    if (sp_ && kp_) line(ind, "prev = " + hex32(pv_) + ";");
+    kp_ = false;
+  }
 
   void line(int ind, const std::string& t) {
     o.append((size_t)ind * 2, ' ');
@@ -652,14 +672,33 @@ struct Gen {
   void cover(int ind, int site, const std::string& cond, bool count) {
     if (rec_) return;
     if (path_) {  // the site's evaluation bit; the outcome bit is set in the taken arm
+      if (kPathCounting) return;  // the walk derives the evaluated sites from the outcomes
       line(ind, "pe" + std::to_string(site >> 5) + " |= " + hex32(1u << (site & 31)) + ";");
       return;
     }
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
-    line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
-                  "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1;" +
-                  (count ? " acc.n_branch++;" : "") +
-                  (compact_ ? " jit_cover_out(slot, e); }" : " jit_cover(slot, e); }"));
+    const std::string upd = std::string(count ? " acc.n_branch++;" : "") +
+                            (compact_ ? " jit_cover_out(slot, e); }" : " jit_cover(slot, e); }");
+    if (!sp_) {
+      line(ind, "{ const uint32_t cur = (" + cond + ") ? " + hex32(l1) + " : " + hex32(l0) +
+                    "; const uint32_t e = (cur ^ prev) & 0xFFFFu; prev = cur >> 1;" + upd);
+      return;
+    }
+    // prev is not written here: the caller sets what each successor knows
+    if (kp_ && !compact_) {
+      // both edges are constants: so are their words and bits in the
+      // saturated-edge bitmap
+      const uint32_t e1 = (l1 ^ pv_) & 0xFFFFu, e0 = (l0 ^ pv_) & 0xFFFFu;
+      line(ind, "{ const uint32_t e = (" + cond + ") ? " + hex32(e1) + " : " + hex32(e0) + ";" +
+                    (count ? " acc.n_branch++;" : "") + " jit_cover_k(slot, e, (" + cond + ") ? " +
+                    std::to_string(e1 >> 5) + "u : " + std::to_string(e0 >> 5) + "u, (" + cond +
+                    ") ? " + hex32(1u << (e1 & 31)) + " : " + hex32(1u << (e0 & 31)) + "); }");
+    } else if (kp_)
+      line(ind, "{ const uint32_t e = (" + cond + ") ? " + hex32((l1 ^ pv_) & 0xFFFFu) + " : " +
+                    hex32((l0 ^ pv_) & 0xFFFFu) + ";" + upd);
+    else
+      line(ind, "{ const uint32_t e = ((" + cond + " ? " + hex32(l1) + " : " + hex32(l0) +
+                    ") ^ prev) & 0xFFFFu;" + upd);
   }
 
   // index limits are read once per function call into constants (a
@@ -880,12 +919,28 @@ struct Gen {
         line(ind + 1, "if (" + c + ") {");
         if (path_ && !rec_)
           line(ind + 2, "po" + std::to_string(o2.site >> 5) + " |= " + hex32(1u << (o2.site & 31)) + ";");
+        kp_ = true;
+        pv_ = ir.loc1[o2.site] >> 1;
         range(ind + 2, pc + 1, o2.else_pc >= 0 ? o2.else_pc : o2.end_pc);
+        const bool kt = kp_;
+        const uint32_t vt = pv_;
+        kp_ = true;
+        pv_ = ir.loc0[o2.site] >> 1;
         if (o2.else_pc >= 0) {
           line(ind + 1, "} else {");
           range(ind + 2, o2.else_pc + 1, o2.end_pc);
         }
         line(ind + 1, "}");
+        if (sp_) {
+          // the join: prev stays known if both paths agree on a constant
+          if (kt && kp_ && vt != pv_)
+            line(ind + 1, "prev = " + c + " ? " + hex32(vt) + " : " + hex32(pv_) + ";");
+          else if (kt && !kp_)
+            line(ind + 1, "if (" + c + ") prev = " + hex32(vt) + ";");
+          else if (!kt && kp_)
+            line(ind + 1, "if (!" + c + ") prev = " + hex32(pv_) + ";");
+          kp_ = kt && kp_ && vt == pv_;
+        }
         line(ind, "}");
         pc = o2.end_pc + 1;
         run_counts(ind, pc, end);
@@ -919,9 +974,18 @@ struct Gen {
         if (k) line(ind + 1, "acc.n_ops += " + std::to_string(k) + "u * " + it + ";");
         if (m) line(ind + 1, "acc.n_acc += " + std::to_string(m) + "u * " + it + ";");
         line(ind + 1, "back += " + it + ";");
-        line(ind + 1, "jit_loop_cover(slot, prev, acc, " + it + ", !" + stop + ", " + lt + ", " + lf + ");");
+        if (sp_ && kp_) {
+          // the entering prev is a constant: the loop's edges fold to constants
+          line(ind + 1, "{ uint32_t pin = " + hex32(pv_) + "; jit_loop_cover(slot, pin, acc, " + it +
+                            ", !" + stop + ", " + lt + ", " + lf + "); }");
+        } else {
+          line(ind + 1, "jit_loop_cover(slot, prev, acc, " + it + ", !" + stop + ", " + lt + ", " + lf + ");");
+        }
         line(ind + 1, "if (" + stop + ") { " + stop_code_ + " }");
         line(ind, "}");
+        // a loop that did not stop the thread left through its exit edge
+        kp_ = true;
+        pv_ = ir.loc0[o2.site] >> 1;
         pc = o2.end_pc + 1;
         run_counts(ind, pc, end);
         continue;
@@ -934,17 +998,23 @@ struct Gen {
         line(ind + 1, "const int32_t " + t + " = " + n + " < 0 ? 0 : (" + n + " > " +
                           std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + " : " + n + ");");
         line(ind + 1, r(o2.dst) + " = 0;");
+        materialize(ind + 1);  // the head is reached from the entry and the back-edge
         line(ind + 1, "#pragma unroll 1");
         line(ind + 1, "for (;;) {");
         line(ind + 2, "const bool " + c + " = " + r(o2.dst) + " < " + t + ";");
         cover(ind + 2, o2.site, c, true);
         line(ind + 2, "if (!" + c + ") break;");
+        kp_ = true;
+        pv_ = ir.loc1[o2.site] >> 1;
         range(ind + 2, pc + 1, o2.end_pc);
+        materialize(ind + 2);
         line(ind + 2, rec_ ? "if (++back > budget) goto cufz_done;"
                            : "if (++back > budget) { " + stop_code_ + " }");
         line(ind + 2, r(o2.dst) + "++;");
         line(ind + 1, "}");
         line(ind, "}");
+        kp_ = true;
+        pv_ = ir.loc0[o2.site] >> 1;
         pc = o2.end_pc + 1;
         run_counts(ind, pc, end);
         continue;
@@ -1215,13 +1285,24 @@ struct Gen {
     bool loops = false;
     for (const auto& op : ir.ops) loops |= op.kept && op.opc == B_LOOP;
     path_ = compact_ && !loops && ir.n_sites <= 64;
-    if (path_) {
+    if (path_ && !kPathCounting) {
       // the LOC table the path replay reads: loc0 | loc1 << 16 per site
       std::string t = "static __device__ const uint32_t " + fn + "_loc[" +
                       std::to_string(std::max(ir.n_sites, 1)) + "] = {";
       for (int s = 0; s < ir.n_sites; s++)
         t += (s ? ", " : "") + hex32((uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16));
       line(0, t + (ir.n_sites ? "};" : "0u};"));
+    }
+    if (path_ && kPathCounting) {
+      // the walk table: LOC pair and the next site for each outcome
+      path_next();
+      std::string t = "static __device__ const uint2 " + fn + "_walk[" +
+                      std::to_string(std::max(ir.n_sites, 1)) + "] = {";
+      for (int s = 0; s < ir.n_sites; s++)
+        t += std::string(s ? ", " : "") + "{" +
+             hex32((uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16)) + ", " +
+             hex32((uint32_t)next_[s][0] | ((uint32_t)next_[s][1] << 8)) + "}";
+      line(0, t + (ir.n_sites ? "};" : "{0u, 0u}};"));
     }
     int n_kept = 0;
     for (const auto& op : ir.ops) n_kept += op.kept && op.opc != B_NOP;
@@ -1325,6 +1406,7 @@ struct Gen {
     line(1, "uint32_t bl = 0, tl = 0;");
     line(1, "if (inc) { bl = udiv(g0 + threadIdx.x, vin->mT); tl = g0 + threadIdx.x - bl * vin->T; }");
     stepped_pre(1, sreg_used);
+    if (path_ && kPathCounting) line(1, "jit_path_clear();");
     line(1, "constexpr int lanes_k = " + lanes + ";");
     line(1, "#pragma unroll lanes_k");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
@@ -1334,13 +1416,22 @@ struct Gen {
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
     if (path_) line(2, "uint32_t pe0 = 0, pe1 = 0, po0 = 0, po1 = 0, pk = 0;");
+    if (path_) line(2, "(void)pe0; (void)pe1;");
     reg_decls(2, used);
     if (heap_ops) line(2, heap_decl);
+    sp_ = !path_;  // prev is 0 at each test thread's start
+    kp_ = true;
+    pv_ = 0;
     range(2, 0, (int)ir.ops.size());
+    sp_ = kp_ = false;
     if (has_loop) line(1, "cufz_done:");
     if (path_) {
       line(2, "acc.n_ops += pk & 0xFFFu; acc.n_acc += (pk >> 12) & 0xFFFu; acc.n_branch += pk >> 24;");
-      line(2, "jit_cover_path(slot, pe0, pe1, po0, po1, " + fn + "_loc);");
+      if (kPathCounting)
+        line(2, "if (!jit_path_count(po0, po1)) jit_path_walk(slot, po0, po1, 1u, " + fn + "_walk, " +
+                    std::to_string(first_site_) + "u);");
+      else
+        line(2, "jit_cover_path(slot, pe0, pe1, po0, po1, " + fn + "_loc);");
     }
     line(2, "if (dig) acc.digest += digest_end(dh);");
     line(2, "if (nv) {");
@@ -1358,9 +1449,47 @@ struct Gen {
     line(2, "}");
     stepped_tail(2, sreg_used);
     line(1, "}");
+    if (path_ && kPathCounting)
+      line(1, "jit_path_flush(slot, " + fn + "_walk, " + std::to_string(first_site_) + "u);");
     line(1, "__syncwarp();");
     line(1, "acc_flush(s_T, slot, acc);");
     line(0, "}");
+  }
+
+  // The walk of a loop-free program's sites: next_[s][o], the site
+  // evaluated after site s when its outcome is o (255: none), and
+  // first_site_, the first site a thread evaluates.  Control flow is
+  // structured, so what follows an IF statement is fixed: the first site of
+  // the arm taken, else the first site after the IF, else what follows the
+  // enclosing arm.
+  std::vector<std::array<uint8_t, 2>> next_;
+  int first_site_ = 255;
+  int first_in(int pc, int end, int cont) const {
+    for (; pc < end; pc++)
+      if (ir.ops[pc].kept && ir.ops[pc].opc == B_IF) return ir.ops[pc].site;
+    return cont;
+  }
+  void walk_range(int pc, int end, int cont) {
+    while (pc < end) {
+      const IrOp& o2 = ir.ops[pc];
+      if (!o2.kept || o2.opc != B_IF) {
+        pc++;
+        continue;
+      }
+      const int after = first_in(o2.end_pc + 1, end, cont);
+      const int then_end = o2.else_pc >= 0 ? o2.else_pc : o2.end_pc;
+      next_[o2.site][1] = (uint8_t)first_in(pc + 1, then_end, after);
+      next_[o2.site][0] = (uint8_t)(o2.else_pc >= 0 ? first_in(o2.else_pc + 1, o2.end_pc, after) : after);
+      walk_range(pc + 1, then_end, after);
+      if (o2.else_pc >= 0) walk_range(o2.else_pc + 1, o2.end_pc, after);
+      pc = o2.end_pc + 1;
+    }
+  }
+  void path_next() {
+    next_.assign(std::max(ir.n_sites, 1), {255, 255});
+    const int n = (int)ir.ops.size();
+    first_site_ = first_in(0, n, 255);
+    walk_range(0, n, 255);
   }
 };
 

@@ -27,6 +27,9 @@ static const shim_dim3 blockIdx = {0, 0, 0};
 static const shim_dim3 blockDim = {1, 1, 1};
 static const shim_dim3 gridDim = {1, 1, 1};
 
+struct uint2 {
+  unsigned x, y;
+};
 struct uint4 {
   unsigned x, y, z, w;
 };

@@ -64,9 +64,10 @@ def host_objs(tmp_path_factory):
     return objs
 
 
-def build(tmp_path, objs, progs, flags=0):
+def build(tmp_path, objs, progs, flags=0, defines=()):
     """One host executable running `progs` (their emitted functions as the
-    device's module would hold them, program k as cufz_prog_k)."""
+    device's module would hold them, program k as cufz_prog_k), compiled with
+    the given preprocessor definitions."""
     srcs = [B.cufz_program_cuda(p, flags).replace("cufz_prog_0", f"cufz_prog_{k}")
             for k, p in enumerate(progs)]
     cases = "".join(f"    case {k}: cufz_prog_{k}(g0, g_end); return true;\n"
@@ -79,8 +80,9 @@ def build(tmp_path, objs, progs, flags=0):
     src = tmp_path / "module_host.cpp"
     src.write_text(tu)
     exe = str(tmp_path / "module_host")
-    r = subprocess.run([_gxx(), "-std=c++17", "-O1", *SAN, "-w", "-I", SHIM, "-I", CSRC,
-                        str(src), *objs, "-o", exe], capture_output=True, text=True)
+    r = subprocess.run([_gxx(), "-std=c++17", "-O1", *SAN, "-w", *[f"-D{d}" for d in defines],
+                        "-I", SHIM, "-I", CSRC, str(src), *objs, "-o", exe],
+                       capture_output=True, text=True)
     assert r.returncode == 0, r.stderr[-4000:]
     return exe
 
@@ -256,6 +258,42 @@ def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
             assert int(res["flags"]) & 1 == int(o["flags"]) & 1, (budget, i)
             assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (budget, i)
             assert np.array_equal(bm, obms[i]), (budget, i)
+
+
+@pytest.mark.parametrize("table_log2", [11, 1])
+def test_path_counting_matches_oracle(tmp_path, host_objs, orc, table_log2):
+    """Branch-heavy loop-free programs run in path mode: each thread counts
+    its path (its sites' outcomes) in the CTA's path table, and each distinct
+    path's edges are replayed once per work item with its count.  Pruned and
+    unpruned, and on bit-flipped variants of the programs.  With a table of
+    two slots most paths find no room, and their threads replay them at
+    once."""
+    rng = gen.SplitMix64(0x9ED1)
+    progs = gen.c4_programs()[:6]
+    k = 0
+    while len(progs) < 12:
+        p = bytearray(gen.c4_program(700 + k))
+        k += 1
+        for _ in range(1 + rng.below(3)):
+            j = 32 + rng.below(len(p) - 32)
+            p[j] ^= 1 << rng.below(8)
+        if B.cufz_validate_program(bytes(p)) == 0 and orc.validate(bytes(p)) == 0:
+            progs.append(bytes(p))
+    ins = gen.c4_inputs(36, n_programs=len(progs), seed=309, max_blocks=2)
+    for flags in (0, B.CF_NO_PRUNE):
+        exe = build(tmp_path, host_objs, progs, flags,
+                    defines=(f"CUFZ_PATH_SLOTS_LOG2={table_log2}",))
+        got = run(tmp_path, exe, progs, ins)
+        ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
+        ops = engine_ops(orc, progs, ins, flags)
+        for i, (res, recs, bm) in enumerate(got):
+            o = ores[i]
+            for f in ("status", "n_accesses", "n_violations", "first_key", "digest", "n_branch",
+                      "n_edges", "n_records"):
+                assert int(res[f]) == int(o[f]), (flags, i, f)
+            assert int(res["n_ops"]) == ops[i], (flags, i)
+            assert record_set(recs) == record_set(orecs[i][: int(o["n_records"])]), (flags, i)
+            assert np.array_equal(bm, obms[i]), (flags, i)
 
 
 @pytest.mark.parametrize("flags", [0, B.CF_NO_PRUNE])
