@@ -120,7 +120,7 @@ def parse_args():
     ap.add_argument("--impl", default="engine", choices=["engine", "reference"])
     ap.add_argument("--workload", default="c2",
                     choices=["c1", "c2", "c3", "c4", "c5", "affine", "guard2d", "div", "heap",
-                             "barrier", "barrier_live"])
+                             "barrier", "barrier_live", "campaign"])
     ap.add_argument("--prex", action="store_true",
                     help="partial representative execution: inputs with a PREX plan run only its threads")
     ap.add_argument("--rate", type=float, default=50000.0, help="c5: offered inputs/s")
@@ -751,11 +751,78 @@ def run_serving(args, rank, world, local, pg):
         print(json.dumps(line), flush=True)
 
 
+def run_campaign(args, rank, world, local, pg):
+    """The fuzzing campaign over the serving workload's 64 programs: rounds
+    per second with the queue on the host (one device batch per round, a
+    host round trip between rounds) and on the device (every step of a round
+    in kernels, rounds enqueued back to back), at several round sizes."""
+    import torch
+
+    from paper_2601_01048_gb300 import binding as B
+    from paper_2601_01048_gb300 import gen
+    from paper_2601_01048_gb300.fuzz import Campaign, DeviceCampaign, EngineExecutor
+
+    torch.cuda.set_device(local)
+    progs = gen.c5_programs()
+    seeds = gen.c5_corpus(progs, per_program=2, max_blocks=64)
+    n_bufs = gen.program_bufs(progs)
+    rows = []
+    clocks = ClockSampler(local)
+    clocks.start()
+    for batch in (64, 256, 1024, 4096):
+        rounds = max(4, min(64, 65536 // batch))
+        row = {"batch": batch, "rounds": rounds}
+        for kind in ("host", "device"):
+            E = B.Engine(device=local, max_slots=max(batch, len(seeds)), record_cap=64,
+                         flags=B.CF_JIT, iter_budget=4096)
+            for p in progs:
+                E.load(p)
+            if kind == "host":
+                c = Campaign(EngineExecutor(E), n_bufs, seeds, seed=1 + rank, batch=batch)
+                c.run_round()                              # warm-up round
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                for _ in range(rounds):
+                    c.run_round()
+                dt = time.perf_counter() - t0
+                corpus = len(c.corpus)
+            else:
+                d = DeviceCampaign(E, seeds, seed=1 + rank, batch=batch)
+                d.run(1)
+                d.sync()                                   # warm-up round
+                t0 = time.perf_counter()
+                d.run(rounds)
+                d.sync()
+                dt = time.perf_counter() - t0
+                corpus = d.counters().corpus
+                d.close()
+            E.close()
+            row[kind] = {"rounds_per_s": rounds / dt, "execs_per_s": rounds * batch / dt,
+                         "ms_per_round": 1e3 * dt / rounds, "corpus_after": corpus}
+        row["device_over_host"] = row["device"]["rounds_per_s"] / row["host"]["rounds_per_s"]
+        rows.append(row)
+    clk = clocks.stop()
+    if rank == 0:
+        top = rows[-1]
+        print(json.dumps({
+            "metric": "fuzz inputs/sec", "value": top["device"]["execs_per_s"], "unit": "inputs/s",
+            "n_gpus": world, "steps": top["rounds"], "warmup": 1,
+            "ms_per_step": top["device"]["ms_per_round"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic (seeded programs, seed corpus, mutated children)",
+            "config": {"workload": "campaign: coverage-guided rounds over the serving workload's 64 "
+                                   "programs, host queue vs device-resident queue",
+                       "parallelism": f"replicas x{world}"},
+            "rows": rows, "clocks": clk}), flush=True)
+
+
 def main():
     args = parse_args()
     rank, world, local, pg = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "campaign":
+        run_campaign(args, rank, world, local, pg)
     elif args.workload == "c5":
         run_serving(args, rank, world, local, pg)
     else:

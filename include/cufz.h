@@ -267,6 +267,116 @@ typedef struct {
   uint32_t reserved;
 } cufz_stats;
 
+/* ------------------------------------------------ device fuzzing campaign
+ * AFL++'s coverage-guided loop (Sec. 2.1, Fig. 1; the harness of Sec. 4)
+ * with its queue, corpus and bug buckets resident on the device.  A round
+ * takes `batch` parents from the corpus, favoured entries first (those that
+ * brought new coverage), least picked first, then the lowest index, round
+ * robin; mutates a copy of each (cufz_mutate_children's streams, round r,
+ * child j); runs the children on the context's compiled kernel; adds the
+ * children flagged CUFZ_FL_NEW_COV to the corpus as favoured entries, in
+ * child order; files every violating child under the key (program_id,
+ * site, cls) of its first stored violation record (the least block, thread
+ * and ordinal); keeps the children flagged CUFZ_FL_BUDGET and NEW_COV as
+ * unique hangs; and renews the union's epoch snapshot.  Every step is a
+ * kernel; a round is one launch of a CUDA graph, and no round waits for the
+ * host.  (The host campaign in the Python package, fuzz.Campaign, follows
+ * the same rules, one device batch per round.) */
+typedef struct cufz_campaign cufz_campaign;
+
+typedef struct {
+  uint32_t batch;        /* children per round, 1..8192 (the context needs as
+                            many free slots) */
+  uint32_t corpus_cap;   /* corpus entries kept, 1..16384; later entries with
+                            new coverage are counted as dropped */
+  uint32_t bucket_cap;   /* bug bucket table size, a power of two, 16..2^20 */
+  uint32_t hang_cap;     /* unique hangs kept, 1..2^20 */
+  uint32_t item_threads; /* work-item size (0: the context's configured or
+                            autotuned size, else 64 x its CTA threads) */
+  uint32_t max_items;    /* work items per round, <= 2^24 (0: 64 per child); a child
+                            whose items would pass it, counting the children
+                            admitted before it in child order, completes as
+                            CUFZ_ST_LIMIT */
+  uint64_t seed;         /* of the children's mutation streams */
+} cufz_campaign_config;
+
+typedef struct {
+  uint64_t key;      /* program_id << 32 | site << 8 | cls of the first
+                        stored violation (site 0xFFFF, cls 0xFF: none stored) */
+  uint64_t first;    /* round << 32 | child index of its first child */
+  uint32_t hits;     /* violating children filed under it */
+  uint32_t pad;
+  cufz_input input;  /* that first child */
+} cufz_bucket;
+
+typedef struct {
+  uint64_t rounds, executed, violating, hang_execs, new_coverage;
+  uint32_t corpus, buckets, hangs;
+  uint32_t corpus_dropped, buckets_dropped, hangs_dropped;
+  uint32_t limit_children; /* children refused by max_items */
+  uint32_t cycles_done;    /* least pick count in the corpus (queue cycles) */
+} cufz_campaign_stats;
+
+/* Device bytes a campaign of this configuration needs (0 for an invalid
+ * configuration). */
+uint64_t cufz_campaign_bytes(const cufz_campaign_config* cfg);
+
+/* Creates a campaign over a context created with CUFZ_CF_JIT (not
+ * CUFZ_CF_PLAIN_LAUNCH), in caller-owned device memory dev_mem (256-byte
+ * aligned, cufz_campaign_bytes large; the caller frees it after
+ * cufz_campaign_destroy).  Runs the n_seeds seeds once through the context
+ * (AFL's dry run: the union then holds their coverage) and starts a new
+ * epoch; the seeds become the corpus, favoured, picked 0 times.  Then
+ * reserves `batch` of the context's slots and sets every loaded program to
+ * the compiled path.  While a campaign exists the context's compiled module
+ * stays as it is: loading or unloading programs or changing their paths or
+ * lane mappings makes submits that would rebuild it, and cufz_destroy,
+ * return CUFZ_E_BUSY.  CUFZ_E_INVALID_ARG for a bad configuration, memory
+ * or seed count (1..corpus_cap); CUFZ_E_BUSY without batch free slots;
+ * CUFZ_E_UNSUPPORTED for a context without the compiled path. */
+cufz_status cufz_campaign_create(cufz_ctx* ctx, const cufz_campaign_config* cfg, void* dev_mem,
+                                 uint64_t dev_bytes, const cufz_input* seeds, uint32_t n_seeds,
+                                 cufz_campaign** out);
+
+/* Enqueues `rounds` rounds on the campaign's stream and returns; they run
+ * one after another with no host involvement.  CUFZ_E_BUSY if the
+ * context's module changed since the campaign was created. */
+cufz_status cufz_campaign_run(cufz_campaign* camp, uint32_t rounds);
+
+/* Waits for the enqueued rounds (timeout_us < 0: up to 120 s);
+ * CUFZ_E_TIMEOUT if they are still running. */
+cufz_status cufz_campaign_sync(cufz_campaign* camp, int32_t timeout_us);
+
+/* Counters of the campaign (after its enqueued rounds). */
+cufz_status cufz_campaign_get_stats(cufz_campaign* camp, cufz_campaign_stats* out);
+
+/* The corpus in entry order: up to cap inputs (out may be NULL), their
+ * favoured flags and pick counts (either may be NULL); *n = corpus size. */
+cufz_status cufz_campaign_corpus(cufz_campaign* camp, cufz_input* out, uint8_t* favoured,
+                                 uint32_t* picks, uint32_t cap, uint32_t* n);
+
+/* The bug buckets, sorted by key: up to cap of them; *n = their number. */
+cufz_status cufz_campaign_buckets(cufz_campaign* camp, cufz_bucket* out, uint32_t cap, uint32_t* n);
+
+/* The unique hangs in the order they were found, with their rounds. */
+cufz_status cufz_campaign_hangs(cufz_campaign* camp, cufz_input* out, uint64_t* rounds, uint32_t cap,
+                                uint32_t* n);
+
+/* Restores a saved campaign into one just created with the saved corpus as
+ * its seeds (whose dry run rebuilt the union): the entries' favoured flags
+ * and pick counts (n_corpus = the corpus size), the buckets, the unique
+ * hangs and the counters (rounds, executed, violating, hang_execs,
+ * new_coverage and the dropped and refused counts).  Afterwards the
+ * campaign continues as the saved one would have. */
+cufz_status cufz_campaign_restore(cufz_campaign* camp, const uint8_t* favoured, const uint32_t* picks,
+                                  uint32_t n_corpus, const cufz_bucket* buckets, uint32_t n_buckets,
+                                  const cufz_input* hangs, const uint64_t* hang_rounds, uint32_t n_hangs,
+                                  const cufz_campaign_stats* counters);
+
+/* Waits for the enqueued rounds, returns the slots to the context and frees
+ * the campaign's host resources (not dev_mem). */
+cufz_status cufz_campaign_destroy(cufz_campaign* camp);
+
 /* Statistics of a loaded (or pruned) program. */
 typedef struct {
   uint32_t n_ops_in;     /* ops of the program as given */
@@ -382,6 +492,16 @@ cufz_status cufz_prex_plan(const void* bytes, size_t nbytes, const cufz_input* i
  * n_bufs entry above 9 (and then nothing is changed). */
 cufz_status cufz_mutate_inputs(cufz_input* inputs, uint32_t n, const uint8_t* n_bufs,
                                uint32_t n_programs, uint64_t* rng_state);
+
+/* The mutator of the device fuzzing campaign below, on the host: mutates
+ * inputs[j] with the draws of cufz_mutate_inputs from the SplitMix64 state
+ * seed + ((round << 32) | j) * 0xD1B54A32D192ED03, one stream per child, so
+ * the children of a round are mutated independently of one another (the
+ * campaign's kernel mutates them in parallel from the same states).  The
+ * host campaign uses it to follow the device campaign exactly.
+ * CUFZ_E_INVALID_ARG as for cufz_mutate_inputs.  Host-only. */
+cufz_status cufz_mutate_children(cufz_input* inputs, uint32_t n, const uint8_t* n_bufs,
+                                 uint32_t n_programs, uint64_t seed, uint64_t round);
 
 /* Human-readable name of a status code (the error classes of Sec. 2.3.1 and
  * Sec. 2.3.2 that the engine reports, and the context's own errors). */

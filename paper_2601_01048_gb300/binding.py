@@ -71,6 +71,27 @@ class cufz_prog_stats(ctypes.Structure):
         "n_branch_sites", "n_loads_value_dead", "reserved")]
 
 
+class cufz_campaign_config(ctypes.Structure):
+    _fields_ = [("batch", ctypes.c_uint32), ("corpus_cap", ctypes.c_uint32),
+                ("bucket_cap", ctypes.c_uint32), ("hang_cap", ctypes.c_uint32),
+                ("item_threads", ctypes.c_uint32), ("max_items", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class cufz_campaign_stats(ctypes.Structure):
+    _fields_ = [("rounds", ctypes.c_uint64), ("executed", ctypes.c_uint64),
+                ("violating", ctypes.c_uint64), ("hang_execs", ctypes.c_uint64),
+                ("new_coverage", ctypes.c_uint64)] + [
+        (n, ctypes.c_uint32) for n in ("corpus", "buckets", "hangs", "corpus_dropped",
+                                       "buckets_dropped", "hangs_dropped", "limit_children",
+                                       "cycles_done")]
+
+
+BUCKET_DTYPE = np.dtype([("key", "<u8"), ("first", "<u8"), ("hits", "<u4"), ("pad", "<u4"),
+                         ("input", INPUT_DTYPE)])
+assert BUCKET_DTYPE.itemsize == 152
+
+
 class CufzError(RuntimeError):
     def __init__(self, status: int, what: str = ""):
         self.status = status
@@ -89,7 +110,10 @@ EXPORTS = [
     "cufz_run_noalloc", "cufz_set_program_path", "cufz_get_program_path", "cufz_autotune",
     "cufz_set_program_lanes", "cufz_get_program_lanes",
     "cufz_unload_program", "cufz_verify_prune", "cufz_prex_check",
-    "cufz_prex_plan", "cufz_mutate_inputs",
+    "cufz_prex_plan", "cufz_mutate_inputs", "cufz_mutate_children", "cufz_campaign_bytes",
+    "cufz_campaign_create", "cufz_campaign_run", "cufz_campaign_sync", "cufz_campaign_get_stats",
+    "cufz_campaign_corpus", "cufz_campaign_buckets", "cufz_campaign_hangs",
+    "cufz_campaign_restore", "cufz_campaign_destroy",
 ]
 
 
@@ -137,6 +161,18 @@ def lib():
                 "cufz_prex_check": (i32, [vp, sz, vp, u32, P(u32)]),
                 "cufz_prex_plan": (i32, [vp, sz, vp, u32, P(u32), u32, P(u32)]),
                 "cufz_mutate_inputs": (i32, [vp, u32, vp, u32, P(u64)]),
+                "cufz_mutate_children": (i32, [vp, u32, vp, u32, u64, u64]),
+                "cufz_campaign_bytes": (u64, [P(cufz_campaign_config)]),
+                "cufz_campaign_create": (i32, [vp, P(cufz_campaign_config), vp, u64, vp, u32, P(vp)]),
+                "cufz_campaign_run": (i32, [vp, u32]),
+                "cufz_campaign_sync": (i32, [vp, i32]),
+                "cufz_campaign_get_stats": (i32, [vp, P(cufz_campaign_stats)]),
+                "cufz_campaign_corpus": (i32, [vp, vp, vp, vp, u32, P(u32)]),
+                "cufz_campaign_buckets": (i32, [vp, vp, u32, P(u32)]),
+                "cufz_campaign_hangs": (i32, [vp, vp, vp, u32, P(u32)]),
+                "cufz_campaign_restore": (i32, [vp, vp, vp, u32, vp, u32, vp, vp, u32,
+                                                P(cufz_campaign_stats)]),
+                "cufz_campaign_destroy": (i32, [vp]),
             }
             for name, (res, args) in sig.items():
                 f = getattr(L, name)
@@ -245,6 +281,94 @@ def cufz_mutate_inputs(inputs: np.ndarray, n_bufs, rng_state: int) -> int:
     _check(lib().cufz_mutate_inputs(inputs.ctypes.data, len(inputs), nb.ctypes.data, len(nb),
                                     ctypes.byref(st)), "cufz_mutate_inputs")
     return st.value
+
+
+def cufz_mutate_children(inputs: np.ndarray, n_bufs, seed: int, round_: int) -> None:
+    """Mutates child j of round `round_` in place from its own stream (the
+    device campaign's draws)."""
+    if inputs.dtype != INPUT_DTYPE or not inputs.flags["C_CONTIGUOUS"]:
+        raise CufzError(E_INVALID_ARG, "cufz_mutate_children")
+    nb = np.ascontiguousarray(n_bufs, dtype=np.uint8)
+    _check(lib().cufz_mutate_children(inputs.ctypes.data, len(inputs), nb.ctypes.data, len(nb),
+                                      seed & (2**64 - 1), round_), "cufz_mutate_children")
+
+
+def cufz_campaign_bytes(cfg: cufz_campaign_config) -> int:
+    return int(lib().cufz_campaign_bytes(ctypes.byref(cfg)))
+
+
+def cufz_campaign_create(ctx, cfg: cufz_campaign_config, dev_mem: int, dev_bytes: int,
+                         seeds: np.ndarray):
+    seeds = np.ascontiguousarray(seeds, dtype=INPUT_DTYPE)
+    out = ctypes.c_void_p()
+    _check(lib().cufz_campaign_create(ctx, ctypes.byref(cfg), ctypes.c_void_p(dev_mem), dev_bytes,
+                                      seeds.ctypes.data, len(seeds), ctypes.byref(out)),
+           "cufz_campaign_create")
+    return out
+
+
+def cufz_campaign_run(camp, rounds: int) -> None:
+    _check(lib().cufz_campaign_run(camp, rounds), "cufz_campaign_run")
+
+
+def cufz_campaign_sync(camp, timeout_us: int = -1) -> None:
+    _check(lib().cufz_campaign_sync(camp, timeout_us), "cufz_campaign_sync")
+
+
+def cufz_campaign_get_stats(camp) -> cufz_campaign_stats:
+    s = cufz_campaign_stats()
+    _check(lib().cufz_campaign_get_stats(camp, ctypes.byref(s)), "cufz_campaign_get_stats")
+    return s
+
+
+def cufz_campaign_corpus(camp):
+    """(inputs, favoured flags, pick counts) of the device corpus."""
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_campaign_corpus(camp, None, None, None, 0, ctypes.byref(n)),
+           "cufz_campaign_corpus")
+    k = int(n.value)
+    inp = np.zeros(k, INPUT_DTYPE)
+    fav = np.zeros(k, np.uint8)
+    picks = np.zeros(k, np.uint32)
+    _check(lib().cufz_campaign_corpus(camp, inp.ctypes.data, fav.ctypes.data, picks.ctypes.data, k,
+                                      ctypes.byref(n)), "cufz_campaign_corpus")
+    return inp, fav.astype(bool), picks
+
+
+def cufz_campaign_buckets(camp) -> np.ndarray:
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_campaign_buckets(camp, None, 0, ctypes.byref(n)), "cufz_campaign_buckets")
+    out = np.zeros(int(n.value), BUCKET_DTYPE)
+    _check(lib().cufz_campaign_buckets(camp, out.ctypes.data, len(out), ctypes.byref(n)),
+           "cufz_campaign_buckets")
+    return out
+
+
+def cufz_campaign_hangs(camp):
+    n = ctypes.c_uint32(0)
+    _check(lib().cufz_campaign_hangs(camp, None, None, 0, ctypes.byref(n)), "cufz_campaign_hangs")
+    k = int(n.value)
+    inp = np.zeros(k, INPUT_DTYPE)
+    rounds = np.zeros(k, np.uint64)
+    _check(lib().cufz_campaign_hangs(camp, inp.ctypes.data, rounds.ctypes.data, k, ctypes.byref(n)),
+           "cufz_campaign_hangs")
+    return inp, rounds
+
+
+def cufz_campaign_restore(camp, favoured, picks, buckets: np.ndarray, hangs: np.ndarray,
+                          hang_rounds, counters: cufz_campaign_stats) -> None:
+    fav = np.ascontiguousarray(favoured, dtype=np.uint8)
+    pk = np.ascontiguousarray(picks, dtype=np.uint32)
+    bk = np.ascontiguousarray(buckets, dtype=BUCKET_DTYPE)
+    hg = np.ascontiguousarray(hangs, dtype=INPUT_DTYPE)
+    hr = np.ascontiguousarray(hang_rounds, dtype=np.uint64)
+    _check(lib().cufz_campaign_restore(camp, fav.ctypes.data, pk.ctypes.data, len(fav),
+                                       bk.ctypes.data, len(bk), hg.ctypes.data, hr.ctypes.data,
+                                       len(hg), ctypes.byref(counters)), "cufz_campaign_restore")
+
+
+def cufz_campaign_destroy(camp) -> None:
+    _check(lib().cufz_campaign_destroy(camp), "cufz_campaign_destroy")
 
 
 def cufz_verify_prune(ctx, program_id: int, inputs: np.ndarray) -> int:

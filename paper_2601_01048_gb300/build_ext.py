@@ -14,13 +14,13 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libcufz.so")
-SOURCES = ["engine.cu", "runtime.cu", "loader.cpp", "prex.cpp", "mutate.cpp", "noalloc.cu"]
+SOURCES = ["engine.cu", "runtime.cu", "loader.cpp", "prex.cpp", "mutate.cpp", "noalloc.cu", "campaign.cu"]
 # device headers handed to the runtime compiler for the compiled path, under
 # the names the sources include them by
 JIT_HEADERS = [("jit_kernel.cuh", "jit_kernel.cuh"), ("jit_launch.cuh", "jit_launch.cuh"),
                ("device_common.cuh", "device_common.cuh"), ("layout.h", "layout.h"),
                ("../../include/cufz.h", os.path.join("..", "..", "include", "cufz.h"))]
-HEADERS = ["engine.h", "ir.h", "interp_kernel.cuh", "checked_ops.h"] + [h[1] for h in JIT_HEADERS]
+HEADERS = ["engine.h", "ir.h", "interp_kernel.cuh", "checked_ops.h", "input_build.h", "mutate.h"] + [h[1] for h in JIT_HEADERS]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-Wall",
          "--expt-relaxed-constexpr"]

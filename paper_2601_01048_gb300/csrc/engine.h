@@ -12,6 +12,7 @@
 #include <string>
 #include <vector>
 
+#include "input_build.h"
 #include "layout.h"
 
 namespace cufz {
@@ -38,24 +39,8 @@ bool prex_plan(const PrexInfo& p, const cufz_input& in, uint32_t iter_budget,
                std::vector<uint32_t>* threads);
 
 // ---------------------------------------------------------------- inputs
-// Launch shapes CUDA would refuse (a zero dimension, more than 1024 threads
-// per block, block.z > 64, grid.x > 2^31 - 1, grid.y or grid.z > 65535):
-// such inputs complete as CUFZ_ST_INVALID_CONFIG without running.
-bool launch_rejected(const cufz_input& in);
-
-// Whether a launch CUDA accepts has at most max_threads test threads; if so
-// their number goes to *n_threads (when not null).  The block count is
-// compared with max_threads / (threads per block) before any product, so a
-// grid whose thread count would wrap 64 bits is refused, not wrapped.
-bool launch_within(const cufz_input& in, uint64_t max_threads, uint64_t* n_threads);
-
-// The part of a DevInput that follows from the input and its program: launch
-// shape, division magics, arguments, buffer lengths, redzone-separated
-// virtual bases (per space: base_0 = R, base_k+1 = align256(base_k + len_k
-// + R)) and per-width index limits.  Zeroes the rest (slot, program
-// placement, items, ticket, sequence), which the caller sets.
-void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
-                    DevInput* d);
+// launch_rejected, launch_within, fill_dev_input, block_serial_fits: see
+// input_build.h (host and device code).
 
 struct LoadedProgram {
   DevProgHdr hdr;
@@ -119,9 +104,33 @@ cudaError_t persistent_occupancy(uint32_t cta_threads, uint32_t smem_bytes, int*
 cudaError_t persistent_func_attributes(cudaFuncAttributes* out);
 cudaError_t set_kernel_smem(uint32_t smem_bytes);
 
-// unsigned division helpers shared by host (magic computation) and device
-__host__ __device__ inline uint64_t div_magic(uint32_t d) {
-  return d <= 1 ? 0ull : (~0ull / d) + 1ull;
-}
+// ---------------------------------------------------------------- campaign
+// What the device fuzzing campaign (campaign.cu) takes from a context: the
+// tables and compiled kernel its rounds launch, the launch limits, a table
+// of the loaded programs (4 words each: bit 0 loaded, bits 8..15 buffers,
+// bits 16..24 shared mask, bit 31 block-serial; blob offset; blob bytes; 0)
+// and the slots reserved for its children.
+struct CampaignEnv {
+  int device = 0;
+  EngineTables T{};
+  const void* jit_kernel = nullptr;
+  uint32_t jit_ctas = 0, cta_threads = 0;
+  uint32_t item_threads = 0;
+  uint64_t max_threads = 0;
+  uint32_t redzone = 0;
+  uint32_t n_programs = 0;
+  std::vector<uint32_t> progs;
+  std::vector<uint32_t> slots;
+  uint64_t module_gen = 0;
+};
+
+// Reserves n_slots free slots for a campaign, sets every loaded program to
+// the compiled path and builds the module if needed.  While a campaign is
+// attached the module is not rebuilt: a change of programs, paths or lane
+// mappings makes later submits return CUFZ_E_BUSY until it detaches.
+cufz_status campaign_attach(cufz_ctx* c, uint32_t n_slots, uint32_t item_threads, CampaignEnv* env);
+void campaign_detach(cufz_ctx* c, const std::vector<uint32_t>& slots);
+// Whether the context still runs the module the campaign captured.
+bool campaign_env_current(cufz_ctx* c, const CampaignEnv& env);
 
 }  // namespace cufz

@@ -168,16 +168,20 @@ static __device__ __noinline__ void jit_cover_path(uint32_t slot, uint32_t e0, u
 }
 
 // Path counting (path-mode programs).  In a loop-free program a thread's
-// edges follow from its path: the sites it evaluates and their outcomes.
-// The outcome bits po (bit s: site s took its then-arm) fix the path alone:
-// which site comes after site s is a function of s and its outcome (the
-// program's structure), so the sites evaluated need no bits of their own.
-// walk[s].x = LOC[s][0] | LOC[s][1] << 16 and walk[s].y = next[s][0] |
-// next[s][1] << 8, the site evaluated after s for each outcome (>= 64: none).
+// edges and its counts of ops, accesses and branch evaluations follow from
+// its path: the sites it evaluates and their outcomes.  The outcome bits po
+// (bit s: site s took its then-arm) fix the path alone: which site comes
+// after site s is a function of s and its outcome (the program's
+// structure), so the sites evaluated need no bits of their own.  walk[s] =
+// {LOC[s][0] | LOC[s][1] << 16, next[s][0] | next[s][1] << 8, seg[s][0],
+// seg[s][1]}: for each outcome the site evaluated next (>= 64: none) and the
+// counts a thread adds up to that evaluation (ops | accesses << 12 | branch
+// evaluations << 24); a thread's counts start at the program's `init`.
 // A thread adds its path to a per-CTA table of paths and counts; after its
 // work item the CTA replays each distinct path once, adding its count to
-// every edge of the path, so threads on one path share one replay.  A path
-// that finds no room in the table is replayed by its thread at once.
+// every edge of the path and its counts times that count, so threads on one
+// path share one replay.  A path that finds no room in the table is replayed
+// by its thread at once.
 #ifndef CUFZ_PATH_SLOTS_LOG2
 #define CUFZ_PATH_SLOTS_LOG2 11
 #endif
@@ -186,26 +190,40 @@ constexpr int kPathProbes = kPathSlots < 8u ? (int)kPathSlots : 8;
 static __shared__ unsigned long long s_pkey[kPathSlots];  // path + 1, 0 = empty
 static __shared__ uint32_t s_pcnt[kPathSlots];
 
+// Counts of one or more threads: executed ops, accesses, branch evaluations.
+struct PathCounts {
+  uint32_t ops, acc, branch;
+};
+
 // n hits of edge e at once (n may differ between lanes, and be 0).
 static __device__ __forceinline__ void jit_cover_n(uint32_t slot, uint32_t e, uint32_t n) {
   if (n != 0 && !edge_saturated(s_hash, e)) jit_cover_slow(slot, e, n);
 }
 
-// The edges of path (po1:po0), m threads on it, starting at site s.  One
-// shared out-of-line copy.
-static __device__ __noinline__ void jit_path_walk(uint32_t slot, uint32_t po0, uint32_t po1,
-                                                  uint32_t m, const uint2* __restrict__ walk,
-                                                  uint32_t s) {
-  uint32_t prev = 0;
+// The edges of path (po1:po0), m threads on it, starting at site s; returns
+// the path's packed counts (one thread's).  One shared out-of-line copy.
+static __device__ __noinline__ uint32_t jit_path_walk(uint32_t slot, uint32_t po0, uint32_t po1,
+                                                      uint32_t m, const uint4* __restrict__ walk,
+                                                      uint32_t s, uint32_t init) {
+  uint32_t prev = 0, cnt = init;
 #pragma unroll 1
   while (s < 64u) {
-    const uint2 w = walk[s];
+    const uint4 w = walk[s];
     const uint32_t o = ((s < 32u ? po0 : po1) >> (s & 31u)) & 1u;
     const uint32_t cur = o ? (w.x >> 16) : (w.x & 0xFFFFu);
     jit_cover_n(slot, (cur ^ prev) & 0xFFFFu, m);
     prev = cur >> 1;
+    cnt += o ? w.w : w.z;
     s = o ? (w.y >> 8) & 0xFFu : w.y & 0xFFu;
   }
+  return cnt;
+}
+
+// Adds m threads of packed counts c.
+static __device__ __forceinline__ void path_counts_add(PathCounts& t, uint32_t c, uint32_t m) {
+  t.ops += m * (c & 0xFFFu);
+  t.acc += m * ((c >> 12) & 0xFFFu);
+  t.branch += m * (c >> 24);
 }
 
 // Empties the CTA's path table; every thread of the CTA calls it.
@@ -239,19 +257,23 @@ static __device__ __forceinline__ bool jit_path_count(uint32_t po0, uint32_t po1
   return false;
 }
 
-// Replays every path of the table with its count; every thread of the CTA
+// Replays every path of the table with its count and returns the counts of
+// the threads on the paths this CTA thread replayed; every thread of the CTA
 // calls it, after its last thread of the work item.
-static __device__ __noinline__ void jit_path_flush(uint32_t slot, const uint2* __restrict__ walk,
-                                                   uint32_t first) {
+static __device__ __noinline__ PathCounts jit_path_flush(uint32_t slot, const uint4* __restrict__ walk,
+                                                         uint32_t first, uint32_t init) {
+  PathCounts t{0u, 0u, 0u};
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kPathSlots; i += blockDim.x) {
     const unsigned long long k = s_pkey[i];
     if (k) {
       const unsigned long long po = k - 1ull;
-      jit_path_walk(slot, (uint32_t)po, (uint32_t)(po >> 32), s_pcnt[i], walk, first);
+      const uint32_t m = s_pcnt[i];
+      path_counts_add(t, jit_path_walk(slot, (uint32_t)po, (uint32_t)(po >> 32), m, walk, first, init), m);
     }
   }
   __syncthreads();
+  return t;
 }
 
 // Edges of the head evaluations of one execution of a loop whose body has no

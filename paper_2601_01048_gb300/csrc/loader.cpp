@@ -658,6 +658,7 @@ struct Gen {
     while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
     const bool ends_at_if = q < end && ir.ops[q].opc == B_IF && ir.ops[q].kept;
     if (path_) {
+      if (kPathCounting) return;  // the walk adds the path's counts (seg_)
       const uint32_t packed = (uint32_t)k | ((uint32_t)m << 12) | ((ends_at_if ? 1u : 0u) << 24);
       if (packed) line(ind, "pk += " + hex32(packed) + ";");
       return;
@@ -1294,15 +1295,17 @@ struct Gen {
       line(0, t + (ir.n_sites ? "};" : "0u};"));
     }
     if (path_ && kPathCounting) {
-      // the walk table: LOC pair and the next site for each outcome
+      // the walk table: LOC pair, the next site and the counts up to it for
+      // each outcome
       path_next();
-      std::string t = "static __device__ const uint2 " + fn + "_walk[" +
+      std::string t = "static __device__ const uint4 " + fn + "_walk[" +
                       std::to_string(std::max(ir.n_sites, 1)) + "] = {";
       for (int s = 0; s < ir.n_sites; s++)
         t += std::string(s ? ", " : "") + "{" +
              hex32((uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16)) + ", " +
-             hex32((uint32_t)next_[s][0] | ((uint32_t)next_[s][1] << 8)) + "}";
-      line(0, t + (ir.n_sites ? "};" : "{0u, 0u}};"));
+             hex32((uint32_t)next_[s][0] | ((uint32_t)next_[s][1] << 8)) + ", " +
+             hex32(seg_[s][0]) + ", " + hex32(seg_[s][1]) + "}";
+      line(0, t + (ir.n_sites ? "};" : "{0u, 0u, 0u, 0u}};"));
     }
     int n_kept = 0;
     for (const auto& op : ir.ops) n_kept += op.kept && op.opc != B_NOP;
@@ -1426,12 +1429,16 @@ struct Gen {
     sp_ = kp_ = false;
     if (has_loop) line(1, "cufz_done:");
     if (path_) {
-      line(2, "acc.n_ops += pk & 0xFFFu; acc.n_acc += (pk >> 12) & 0xFFFu; acc.n_branch += pk >> 24;");
-      if (kPathCounting)
-        line(2, "if (!jit_path_count(po0, po1)) jit_path_walk(slot, po0, po1, 1u, " + fn + "_walk, " +
-                    std::to_string(first_site_) + "u);");
-      else
+      if (kPathCounting) {
+        line(2, "if (!jit_path_count(po0, po1)) {");
+        line(3, "const uint32_t pc_ = jit_path_walk(slot, po0, po1, 1u, " + fn + "_walk, " +
+                    std::to_string(first_site_) + "u, " + hex32(init_) + ");");
+        line(3, "acc.n_ops += pc_ & 0xFFFu; acc.n_acc += (pc_ >> 12) & 0xFFFu; acc.n_branch += pc_ >> 24;");
+        line(2, "}");
+      } else {
+        line(2, "acc.n_ops += pk & 0xFFFu; acc.n_acc += (pk >> 12) & 0xFFFu; acc.n_branch += pk >> 24;");
         line(2, "jit_cover_path(slot, pe0, pe1, po0, po1, " + fn + "_loc);");
+      }
     }
     line(2, "if (dig) acc.digest += digest_end(dh);");
     line(2, "if (nv) {");
@@ -1449,8 +1456,13 @@ struct Gen {
     line(2, "}");
     stepped_tail(2, sreg_used);
     line(1, "}");
-    if (path_ && kPathCounting)
-      line(1, "jit_path_flush(slot, " + fn + "_walk, " + std::to_string(first_site_) + "u);");
+    if (path_ && kPathCounting) {
+      line(1, "{");
+      line(2, "const PathCounts t_ = jit_path_flush(slot, " + fn + "_walk, " +
+                  std::to_string(first_site_) + "u, " + hex32(init_) + ");");
+      line(2, "acc.n_ops += t_.ops; acc.n_acc += t_.acc; acc.n_branch += t_.branch;");
+      line(1, "}");
+    }
     line(1, "__syncwarp();");
     line(1, "acc_flush(s_T, slot, acc);");
     line(0, "}");
@@ -1462,24 +1474,42 @@ struct Gen {
   // structured, so what follows an IF statement is fixed: the first site of
   // the arm taken, else the first site after the IF, else what follows the
   // enclosing arm.
+  // seg_[s][o] packs the counts (ops | accesses << 12 | branch evaluations
+  // << 24) of the runs a thread executes from outcome o at site s to its
+  // next site evaluation (that evaluation included), init_ those before its
+  // first: the counts run_counts adds at each run, summed along a path.
   std::vector<std::array<uint8_t, 2>> next_;
+  std::vector<std::array<uint32_t, 2>> seg_;
   int first_site_ = 255;
-  int first_in(int pc, int end, int cont) const {
-    for (; pc < end; pc++)
-      if (ir.ops[pc].kept && ir.ops[pc].opc == B_IF) return ir.ops[pc].site;
-    return cont;
+  uint32_t init_ = 0;
+  struct To {
+    uint32_t cnt;
+    int site;
+  };
+  // From the start of a run at pc in [pc, end) to the next site evaluation:
+  // the first IF of the range, else what follows the range (cont).
+  To to_site(int pc, int end, To cont) const {
+    int q = pc;
+    while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
+    const bool at_if = q < end && ir.ops[q].opc == B_IF && ir.ops[q].kept;
+    const uint32_t c = (uint32_t)run_ops(pc, end) | ((uint32_t)run_acc(pc, end) << 12) |
+                       ((at_if ? 1u : 0u) << 24);
+    if (at_if) return {c, ir.ops[q].site};
+    return {c + cont.cnt, cont.site};
   }
-  void walk_range(int pc, int end, int cont) {
+  void walk_range(int pc, int end, To cont) {
     while (pc < end) {
       const IrOp& o2 = ir.ops[pc];
       if (!o2.kept || o2.opc != B_IF) {
         pc++;
         continue;
       }
-      const int after = first_in(o2.end_pc + 1, end, cont);
+      const To after = to_site(o2.end_pc + 1, end, cont);
       const int then_end = o2.else_pc >= 0 ? o2.else_pc : o2.end_pc;
-      next_[o2.site][1] = (uint8_t)first_in(pc + 1, then_end, after);
-      next_[o2.site][0] = (uint8_t)(o2.else_pc >= 0 ? first_in(o2.else_pc + 1, o2.end_pc, after) : after);
+      const To t1 = to_site(pc + 1, then_end, after);
+      const To t0 = o2.else_pc >= 0 ? to_site(o2.else_pc + 1, o2.end_pc, after) : after;
+      next_[o2.site] = {(uint8_t)t0.site, (uint8_t)t1.site};
+      seg_[o2.site] = {t0.cnt, t1.cnt};
       walk_range(pc + 1, then_end, after);
       if (o2.else_pc >= 0) walk_range(o2.else_pc + 1, o2.end_pc, after);
       pc = o2.end_pc + 1;
@@ -1487,9 +1517,12 @@ struct Gen {
   }
   void path_next() {
     next_.assign(std::max(ir.n_sites, 1), {255, 255});
+    seg_.assign(std::max(ir.n_sites, 1), {0u, 0u});
     const int n = (int)ir.ops.size();
-    first_site_ = first_in(0, n, 255);
-    walk_range(0, n, 255);
+    const To start = to_site(0, n, To{0u, 255});
+    first_site_ = start.site;
+    init_ = start.cnt;
+    walk_range(0, n, To{0u, 255});
   }
 };
 
@@ -1549,65 +1582,6 @@ cufz_status jit_source(const void* bytes, size_t nbytes, bool do_prune, bool dig
 
 
 // ---------------------------------------------------------------- public
-
-bool launch_rejected(const cufz_input& in) {
-  const uint32_t* g = in.grid;
-  const uint32_t* b = in.block;
-  if (!g[0] || !g[1] || !g[2] || !b[0] || !b[1] || !b[2]) return true;
-  if (b[0] > 1024 || b[1] > 1024 || b[2] > 64) return true;
-  if ((uint64_t)b[0] * b[1] * b[2] > 1024) return true;
-  return g[0] > 0x7FFFFFFFu || g[1] > 65535 || g[2] > 65535;
-}
-
-bool launch_within(const cufz_input& in, uint64_t max_threads, uint64_t* n_threads) {
-  // blocks < 2^31 * 2^16 * 2^16 = 2^63 fits 64 bits; the product with the
-  // block size (<= 1024) is formed only once it cannot exceed max_threads
-  const uint64_t T = (uint64_t)in.block[0] * in.block[1] * in.block[2];
-  const uint64_t nb = (uint64_t)in.grid[0] * in.grid[1] * in.grid[2];
-  if (T == 0 || nb > max_threads / T) return false;
-  if (n_threads) *n_threads = nb * T;
-  return true;
-}
-
-void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
-                    DevInput* d) {
-  memset(d, 0, sizeof(*d));
-  for (int k = 0; k < 3; k++) {
-    d->grid[k] = in.grid[k];
-    d->block[k] = in.block[k];
-  }
-  for (int k = 0; k < 4; k++) d->args[k] = in.args[k];
-  const uint32_t Bx = in.block[0], By = in.block[1], Bz = in.block[2];
-  d->T = Bx * By * Bz;
-  // callers pass inputs that launch_within() accepted; anything larger would
-  // wrap, so it is stored as 0 threads rather than as a wrapped count
-  uint64_t nt = 0;
-  d->n_threads = launch_within(in, ~0ull, &nt) ? nt : 0;
-  d->mT = div_magic(d->T);
-  d->Bx = Bx;
-  d->mBx = div_magic(Bx);
-  d->Bxy = Bx * By;
-  d->mBxy = div_magic(d->Bxy);
-  d->gx = in.grid[0];
-  d->mGx = div_magic(in.grid[0]);
-  d->gxy = (uint32_t)((uint64_t)in.grid[0] * in.grid[1]);
-  d->mGxy = div_magic(d->gxy);
-  const int64_t R = (int64_t)redzone;
-  int64_t next[2] = {R, R};
-  for (uint32_t k = 0; k < n_bufs; k++) {
-    const int sp = (shared_mask >> k) & 1;
-    d->len[k] = (int64_t)in.buf_len[k];
-    d->base[k] = next[sp];
-    next[sp] = (next[sp] + d->len[k] + R + 255) & ~(int64_t)255;
-    for (uint32_t lw = 0; lw < 5; lw++) {
-      const uint64_t n = in.buf_len[k] >> lw;
-      d->lim[k * 5 + lw] = n < 0x80000000ull ? (uint32_t)n : 0x80000000u;
-    }
-  }
-  d->shared_mask = shared_mask;
-  d->n_bufs = n_bufs;
-  d->user_tag = in.user_tag;
-}
 
 cufz_status load_program(const void* bytes, size_t nbytes, bool do_prune, LoadedProgram* out) {
   Ir ir;

@@ -151,6 +151,8 @@ struct cufz_ctx {
   std::vector<uint8_t> lanes_in_module; // the lane mappings the loaded module was built with
   uint32_t jit_ctas_per_sm = 0;
   std::string jit_log;
+  uint64_t module_gen = 0;   // compiled modules loaded so far
+  uint32_t campaigns = 0;    // device campaigns attached
 };
 
 namespace {
@@ -364,6 +366,7 @@ bool jit_current(const cufz_ctx* c) {
 
 cufz_status jit_compile(cufz_ctx* c) {
   if (jit_current(c)) return CUFZ_OK;
+  if (c->campaigns) return CUFZ_E_BUSY;  // a campaign's captured rounds run this module
   std::vector<char> cubin;
   const bool plain = (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH) != 0;
   std::vector<uint8_t> include = c->prog_compiled;
@@ -394,6 +397,7 @@ cufz_status jit_compile(cufz_ctx* c) {
   }
   c->jit_ctas_per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
   c->jit_progs = (uint32_t)c->progs.size();
+  c->module_gen++;
   c->prog_in_module = include;
   c->lanes_in_module = c->prog_lanes;
   return CUFZ_OK;
@@ -584,16 +588,6 @@ bool tune_cache_write(const cufz_ctx* c) {
   return ok && rename(tmp.c_str(), c->tune_path.c_str()) == 0;
 }
 
-// A launch the block-serial form runs: a block of at most kBlkMaxThreads
-// threads, and shared buffers of at most kBlkSharedBytes bytes together.
-bool block_serial_fits(const LoadedProgram& P, const cufz_input& x) {
-  const uint64_t T = (uint64_t)x.block[0] * x.block[1] * x.block[2];
-  uint64_t sh = 0;
-  for (uint32_t k = 0; k < P.n_bufs; k++)
-    if ((P.shared_mask >> k) & 1u) sh += x.buf_len[k];
-  return T <= kBlkMaxThreads && sh <= kBlkSharedBytes;
-}
-
 // The status an input completes with at once (anything but OK), or OK
 // when it needs device work.
 int32_t input_status(const cufz_ctx* c, const cufz_input& x) {
@@ -603,7 +597,7 @@ int32_t input_status(const cufz_ctx* c, const cufz_input& x) {
   const LoadedProgram& P = c->progs[x.program_id];
   for (uint32_t k = 0; k < P.n_bufs; k++)
     if (x.buf_len[k] >= (1ull << 48)) return CUFZ_ST_LIMIT;
-  if (P.block_serial && !block_serial_fits(P, x)) return CUFZ_ST_LIMIT;
+  if (P.block_serial && !block_serial_fits(P.n_bufs, P.shared_mask, x)) return CUFZ_ST_LIMIT;
   return CUFZ_ST_OK;
 }
 
@@ -788,6 +782,7 @@ cufz_status cufz_destroy(cufz_ctx* c) {
   if (!c) return CUFZ_E_INVALID_ARG;
   {
     std::lock_guard<std::mutex> g(c->mu);
+    if (c->campaigns) return CUFZ_E_BUSY;  // destroy the campaigns first
     uint64_t t0 = now_us();
     for (uint32_t k = 0; k < c->n_lanes; k++) {
       Lane& L = c->lanes[k];
@@ -1802,3 +1797,69 @@ cufz_status cufz_int32_peak(int32_t device, void* stream, double* lane_ops_per_s
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- campaign
+namespace cufz {
+
+cufz_status campaign_attach(cufz_ctx* c, uint32_t n_slots, uint32_t item_threads, CampaignEnv* env) {
+  if (!c || !env || !n_slots) return CUFZ_E_INVALID_ARG;
+  std::lock_guard<std::mutex> g(c->mu);
+  if (!use_jit(c) || (c->cfg.flags & CUFZ_CF_PLAIN_LAUNCH)) return CUFZ_E_UNSUPPORTED;
+  harvest(c);
+  if (c->free_slots.size() < n_slots) return CUFZ_E_BUSY;
+  // a campaign runs every loaded program compiled
+  for (size_t k = 0; k < c->progs.size(); k++)
+    if (c->prog_live[k]) c->prog_compiled[k] = 1;
+  const cufz_status st = jit_compile(c);
+  if (st != CUFZ_OK) return st;
+  if (!c->jit_persist) return CUFZ_E_CUDA;
+  env->device = c->device;
+  env->T = c->T;
+  env->jit_kernel = reinterpret_cast<const void*>(c->jit_persist);
+  env->jit_ctas = jit_ctas(c);
+  env->cta_threads = c->shape.cta_threads;
+  env->item_threads = item_threads ? item_threads
+                    : c->cfg.item_threads ? c->cfg.item_threads
+                    : c->tuned_item ? c->tuned_item
+                                    : 64u * c->shape.cta_threads;
+  env->max_threads = c->cfg.max_threads;
+  env->redzone = c->cfg.redzone;
+  env->n_programs = (uint32_t)c->progs.size();
+  env->progs.assign(c->progs.size() * 4, 0u);
+  for (size_t k = 0; k < c->progs.size(); k++) {
+    const LoadedProgram& P = c->progs[k];
+    if (!c->prog_live[k]) continue;
+    env->progs[k * 4] = 1u | (P.n_bufs << 8) | ((P.shared_mask & 0x1FFu) << 16) |
+                        (P.block_serial ? 1u << 31 : 0u);
+    env->progs[k * 4 + 1] = c->prog_off[k];
+    env->progs[k * 4 + 2] = P.blob_bytes;
+  }
+  env->slots.clear();
+  for (uint32_t k = 0; k < n_slots; k++) {
+    const uint32_t s = c->free_slots.back();
+    c->free_slots.pop_back();
+    c->slots[s].state = 3;  // held by a campaign
+    env->slots.push_back(s);
+  }
+  env->module_gen = c->module_gen;
+  c->campaigns++;
+  return CUFZ_OK;
+}
+
+void campaign_detach(cufz_ctx* c, const std::vector<uint32_t>& slots) {
+  if (!c) return;
+  std::lock_guard<std::mutex> g(c->mu);
+  for (uint32_t s : slots) {
+    c->slots[s].state = 0;
+    c->free_slots.push_back(s);
+  }
+  if (c->campaigns) c->campaigns--;
+}
+
+bool campaign_env_current(cufz_ctx* c, const CampaignEnv& env) {
+  std::lock_guard<std::mutex> g(c->mu);
+  return c->module_gen == env.module_gen &&
+         reinterpret_cast<const void*>(c->jit_persist) == env.jit_kernel;
+}
+
+}  // namespace cufz

@@ -944,6 +944,12 @@ class Mutator:
                 rec["buf_len"][b] = v
 
 
+def child_stream(seed: int, round_: int, j: int) -> int:
+    """SplitMix64 state of child j's mutation stream in round `round_` of a
+    campaign (one stream per child)."""
+    return (seed + (((round_ << 32) | j) * 0xD1B54A32D192ED03)) & MASK64
+
+
 def c5_programs() -> list[bytes]:
     """64 resident programs: 16 of config 3's family, 32 random (config 2
     generator with fresh seeds), 16 branch-heavy (config 4 generator)."""

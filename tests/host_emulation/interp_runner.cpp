@@ -6,7 +6,7 @@
 // CTA pulls in turn, and the CTA that completes an input's last item
 // finalizes it (bitmap, union, result), as on the device.  Programs are
 // loaded with the library's load_program and inputs built with its
-// fill_dev_input (loader.cpp, linked in).
+// fill_dev_input (input_build.h).
 //
 // Job file (little-endian u32 unless noted): n_programs, record_cap,
 // redzone, iter_budget, item_threads, flags (CUFZ_CF_NO_PRUNE,
@@ -25,10 +25,7 @@ thread_local shim_dim3 threadIdx = {0, 0, 0};
 ShimWarp g_shim_warp;
 std::mutex g_shim_atomic;
 
-namespace cufz {
-void fill_dev_input(const cufz_input& in, uint32_t n_bufs, uint32_t shared_mask, uint32_t redzone,
-                    DevInput* d);
-}
+#include "input_build.h"  // the library's own fill_dev_input
 extern "C" int shim_load_blob(const void* bytes, size_t nbytes, int prune, uint8_t** blob,
                               uint32_t* blob_bytes, uint32_t* n_regs, uint32_t* n_bufs,
                               uint32_t* shared_mask);

@@ -188,3 +188,49 @@ def test_command_line_reports_checkpoints_and_resumes(tmp_path, capsys):
               executor_factory=fake)
     last = json.loads(capsys.readouterr().out.splitlines()[-1])
     assert last["rounds"] == 7 and last["execs_done"] == 224
+
+
+def test_child_streams_draw_like_the_generator_mutator():
+    """cufz_mutate_children mutates child j of round r with gen.Mutator's
+    draws from the state child_stream(seed, r, j): the stream of each child
+    is its own, so the device campaign's kernel gives the same children."""
+    rng = gen.SplitMix64(17)
+    n_bufs = [rng.below(10) for _ in range(12)]
+    x = gen.make_inputs(700)
+    for k in range(len(x)):
+        gen.set_input(x[k], rng.below(12), (rng.randint(1, 9), 1, 1), (32, 1, 1),
+                      [rng.randint(-2**31, 2**31 - 1) for _ in range(4)],
+                      [rng.randint(0, 1 << 40) for _ in range(9)])
+    for seed, rnd in ((0xF022, 0), (0xF022, 5), (2**64 - 3, 2**31 + 7)):
+        a, b = x.copy(), x.copy()
+        for j in range(len(a)):
+            m = gen.Mutator(0)
+            m.rng.state = gen.child_stream(seed, rnd, j)
+            m.mutate(a[j], n_bufs[int(a[j]["program_id"])])
+        B.cufz_mutate_children(b, n_bufs, seed, rnd)
+        assert np.array_equal(a.view(np.uint8), b.view(np.uint8))
+        assert (a != x).all()
+    # streams differ between rounds and children
+    a, b = x[:64].copy(), x[:64].copy()
+    B.cufz_mutate_children(a, n_bufs, 1, 0)
+    B.cufz_mutate_children(b, n_bufs, 1, 1)
+    assert (a != b).any()
+
+
+def test_corpus_and_hang_caps():
+    """Entries with new coverage beyond corpus_cap, and unique hangs beyond
+    hang_cap, are counted as dropped; the round is otherwise the same as
+    without caps (same children, same order)."""
+    ex_a, ex_b = FakeExecutor(), FakeExecutor()
+    a = Campaign(ex_a, [3, 3], seeds(), seed=9, batch=64)
+    b = Campaign(ex_b, [3, 3], seeds(), seed=9, batch=64, corpus_cap=9, hang_cap=1)
+    a.run_round()
+    b.run_round()
+    assert len(a.corpus) > 9 and len(a.hangs) > 1          # the caps matter here
+    assert np.array_equal(b.corpus, a.corpus[:9])
+    assert b.corpus_dropped == len(a.corpus) - 9
+    assert len(b.hangs) == 1 and b.hangs[0]["input"].tobytes() == a.hangs[0]["input"].tobytes()
+    assert b.hangs_dropped == len(a.hangs) - 1
+    assert b.n_hangs == a.n_hangs and b.n_new_coverage == a.n_new_coverage
+    s = b.stats()
+    assert s["corpus_count"] == 9 and s["corpus_dropped"] == b.corpus_dropped
