@@ -183,7 +183,7 @@ static __device__ __noinline__ void jit_cover_path(uint32_t slot, uint32_t e0, u
 // path share one replay.  A path that finds no room in the table is replayed
 // by its thread at once.
 #ifndef CUFZ_PATH_SLOTS_LOG2
-#define CUFZ_PATH_SLOTS_LOG2 11
+#define CUFZ_PATH_SLOTS_LOG2 12
 #endif
 constexpr uint32_t kPathSlots = 1u << CUFZ_PATH_SLOTS_LOG2;
 constexpr int kPathProbes = kPathSlots < 8u ? (int)kPathSlots : 8;

@@ -260,7 +260,7 @@ def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
             assert np.array_equal(bm, obms[i]), (budget, i)
 
 
-@pytest.mark.parametrize("table_log2", [11, 1])
+@pytest.mark.parametrize("table_log2", [12, 1])
 def test_path_counting_matches_oracle(tmp_path, host_objs, orc, table_log2):
     """Branch-heavy loop-free programs run in path mode: each thread counts
     its path (its sites' outcomes) in the CTA's path table, and each distinct
