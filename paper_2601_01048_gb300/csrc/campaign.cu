@@ -544,9 +544,10 @@ cufz_status camp_capture(cufz_campaign* c) {
       at<WorkItem>(c, c->L.items));
   EngineTables T = c->env.T;
   BatchHdr* B = at<BatchHdr>(c, c->L.batch);
-  void* args[] = {&T, &B};
+  uint32_t paths = c->env.jit_smem ? 1u : 0u;
+  void* args[] = {&T, &B, &paths};
   cudaError_t e1 = cudaLaunchKernel(c->env.jit_kernel, dim3(c->env.jit_ctas), dim3(c->env.cta_threads),
-                                    args, 0, c->stream);
+                                    args, c->env.jit_smem, c->stream);
   camp_file<<<1, kCampThreads, 0, c->stream>>>(
       H, at<cufz_input>(c, c->L.corpus), at<uint32_t>(c, c->L.fav), at<uint32_t>(c, c->L.picks),
       at<cufz_input>(c, c->L.kids), at<int32_t>(c, c->L.kid_status), at<uint32_t>(c, c->L.kid_slot), T,

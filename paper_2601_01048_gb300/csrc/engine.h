@@ -61,6 +61,11 @@ struct LoadedProgram {
 cufz_status load_program(const void* bytes, size_t nbytes, bool prune, LoadedProgram* out);
 void free_program(LoadedProgram* p);
 
+// Dynamic shared memory of a persistent compiled-kernel launch whose module
+// holds path-mode programs: the path table (4096 slots of 12 bytes; the
+// kPathTableBytes of jit_kernel.cuh).
+constexpr uint32_t kJitPathTableBytes = 4096u * 12u;
+
 // Resident CTAs per SM the compiled kernel's registers must allow when the
 // config leaves it open: 3 x 256 threads gives it 85 registers a thread.
 constexpr uint32_t kJitMinCtasDefault = 3;
@@ -122,6 +127,7 @@ struct CampaignEnv {
   std::vector<uint32_t> progs;
   std::vector<uint32_t> slots;
   uint64_t module_gen = 0;
+  uint32_t jit_smem = 0;  // the persistent kernel's dynamic shared memory (path table)
 };
 
 // Reserves n_slots free slots for a campaign, sets every loaded program to

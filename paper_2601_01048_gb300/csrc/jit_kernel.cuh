@@ -181,14 +181,24 @@ static __device__ __noinline__ void jit_cover_path(uint32_t slot, uint32_t e0, u
 // work item the CTA replays each distinct path once, adding its count to
 // every edge of the path and its counts times that count, so threads on one
 // path share one replay.  A path that finds no room in the table is replayed
-// by its thread at once.
+// by its thread at once.  The table is the launch's dynamic shared memory
+// (kPathTableBytes): the persistent kernel gets it when its module holds
+// path-mode programs; the plain kernel (a CTA per test block) does not, and
+// there every thread replays its own path (s_paths = 0).
 #ifndef CUFZ_PATH_SLOTS_LOG2
 #define CUFZ_PATH_SLOTS_LOG2 12
 #endif
 constexpr uint32_t kPathSlots = 1u << CUFZ_PATH_SLOTS_LOG2;
+constexpr uint32_t kPathTableBytes = kPathSlots * 12u;
 constexpr int kPathProbes = kPathSlots < 8u ? (int)kPathSlots : 8;
-static __shared__ unsigned long long s_pkey[kPathSlots];  // path + 1, 0 = empty
-static __shared__ uint32_t s_pcnt[kPathSlots];
+extern __shared__ __align__(16) unsigned char s_dyn[];
+static __shared__ uint32_t s_paths;  // the CTA has a path table
+static __device__ __forceinline__ unsigned long long* path_keys() {
+  return reinterpret_cast<unsigned long long*>(s_dyn);  // path + 1, 0 = empty
+}
+static __device__ __forceinline__ uint32_t* path_counts() {
+  return reinterpret_cast<uint32_t*>(s_dyn + kPathSlots * 8u);
+}
 
 // Counts of one or more threads: executed ops, accesses, branch evaluations.
 struct PathCounts {
@@ -211,7 +221,10 @@ static __device__ __noinline__ uint32_t jit_path_walk(uint32_t slot, uint32_t po
     const uint4 w = walk[s];
     const uint32_t o = ((s < 32u ? po0 : po1) >> (s & 31u)) & 1u;
     const uint32_t cur = o ? (w.x >> 16) : (w.x & 0xFFFFu);
-    jit_cover_n(slot, (cur ^ prev) & 0xFFFFu, m);
+    if (m == 1u)  // one thread's path: a lane's own hit, no warp merging
+      jit_cover(slot, (cur ^ prev) & 0xFFFFu);
+    else
+      jit_cover_n(slot, (cur ^ prev) & 0xFFFFu, m);
     prev = cur >> 1;
     cnt += o ? w.w : w.z;
     s = o ? (w.y >> 8) & 0xFFu : w.y & 0xFFu;
@@ -226,30 +239,37 @@ static __device__ __forceinline__ void path_counts_add(PathCounts& t, uint32_t c
   t.branch += m * (c >> 24);
 }
 
-// Empties the CTA's path table; every thread of the CTA calls it.
+// Empties the CTA's path table, if it has one; every thread of the CTA
+// calls it.
 static __device__ __forceinline__ void jit_path_clear() {
+  if (!s_paths) return;
+  unsigned long long* keys = path_keys();
+  uint32_t* cnt = path_counts();
   for (uint32_t i = threadIdx.x; i < kPathSlots; i += blockDim.x) {
-    s_pkey[i] = 0ull;
-    s_pcnt[i] = 0u;
+    keys[i] = 0ull;
+    cnt[i] = 0u;
   }
   __syncthreads();
 }
 
 // Counts one thread on path (po1:po0) in the CTA's table; false when the
-// path found no room (within kPathProbes slots of its home).
+// CTA has no table or the path found no room (within kPathProbes slots of
+// its home).
 static __device__ __forceinline__ bool jit_path_count(uint32_t po0, uint32_t po1) {
   const unsigned long long key = (((unsigned long long)po1 << 32) | po0) + 1ull;
-  if (key == 0ull) return false;  // every one of 64 sites taken: no key left for it
+  if (!s_paths || key == 0ull) return false;  // key 0: every one of 64 sites taken
+  unsigned long long* keys = path_keys();
+  uint32_t* cnt = path_counts();
   uint32_t h = ((po0 * 0x9E3779B1u) ^ (po1 * 0x85EBCA77u)) >> (32 - CUFZ_PATH_SLOTS_LOG2);
 #pragma unroll 1
   for (int p = 0; p < kPathProbes; p++) {
-    unsigned long long k = s_pkey[h];
+    unsigned long long k = keys[h];
     if (k == 0ull) {
-      k = atomicCAS(&s_pkey[h], 0ull, key);
+      k = atomicCAS(&keys[h], 0ull, key);
       if (k == 0ull) k = key;
     }
     if (k == key) {
-      atomicAdd(&s_pcnt[h], 1u);
+      atomicAdd(&cnt[h], 1u);
       return true;
     }
     h = (h + 1u) & (kPathSlots - 1u);
@@ -263,12 +283,15 @@ static __device__ __forceinline__ bool jit_path_count(uint32_t po0, uint32_t po1
 static __device__ __noinline__ PathCounts jit_path_flush(uint32_t slot, const uint4* __restrict__ walk,
                                                          uint32_t first, uint32_t init) {
   PathCounts t{0u, 0u, 0u};
+  if (!s_paths) return t;
+  const unsigned long long* keys = path_keys();
+  const uint32_t* cnt = path_counts();
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kPathSlots; i += blockDim.x) {
-    const unsigned long long k = s_pkey[i];
+    const unsigned long long k = keys[i];
     if (k) {
       const unsigned long long po = k - 1ull;
-      const uint32_t m = s_pcnt[i];
+      const uint32_t m = cnt[i];
       path_counts_add(t, jit_path_walk(slot, (uint32_t)po, (uint32_t)(po >> 32), m, walk, first, init), m);
     }
   }

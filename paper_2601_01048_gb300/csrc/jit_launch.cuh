@@ -21,9 +21,12 @@ static __device__ __forceinline__ void jit_stage_tables(const cufz::EngineTables
 }
 
 // Persistent: CTAs pull work items from the batch until it is drained.
+// paths: the launch gives the CTA a path table (kPathTableBytes of dynamic
+// shared memory).
 extern "C" __global__ void __launch_bounds__(CUFZ_JIT_CTA_THREADS, CUFZ_JIT_MIN_CTAS)
-    cufz_jit_persistent(cufz::EngineTables T, cufz::BatchHdr* batch) {
+    cufz_jit_persistent(cufz::EngineTables T, cufz::BatchHdr* batch, uint32_t paths) {
   using namespace cufz;
+  if (threadIdx.x == 0) s_paths = paths;
   jit_stage_tables(T);
   run_items<true, false>(s_T, batch, 0u, 0u, 0u, s_hash, nullptr, &s_in,
                          [&](const DevInput* in, uint32_t g0, uint32_t cnt, bool) -> bool {
@@ -37,6 +40,7 @@ extern "C" __global__ void __launch_bounds__(1024) cufz_jit_plain(cufz::EngineTa
                                                                   cufz::BatchHdr* batch,
                                                                   uint32_t input) {
   using namespace cufz;
+  if (threadIdx.x == 0) s_paths = 0u;  // no path table: threads replay their own paths
   jit_stage_tables(T);
   run_items<false, false>(s_T, batch, input, 0u, 0u, s_hash, nullptr, &s_in,
                           [&](const DevInput* in, uint32_t g0, uint32_t cnt, bool) -> bool {

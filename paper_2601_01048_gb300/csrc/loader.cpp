@@ -965,7 +965,7 @@ struct Gen {
                           std::to_string(o2.imm) + " ? " + std::to_string(o2.imm) + "u : (uint32_t)" + n + ");");
         line(ind + 1, "const bool " + stop + " = " + t + " > budget - back;");
         line(ind + 1, "const uint32_t " + it + " = " + stop + " ? budget - back + 1u : " + t + ";");
-        line(ind + 1, "#pragma unroll 2");
+        line(ind + 1, "#pragma unroll 4");
         line(ind + 1, "for (" + r(o2.dst) + " = 0; (uint32_t)" + r(o2.dst) + " < " + it + "; " + r(o2.dst) + "++) {");
         no_counts_ = true;
         range(ind + 2, pc + 1, o2.end_pc);

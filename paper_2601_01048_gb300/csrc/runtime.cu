@@ -152,6 +152,7 @@ struct cufz_ctx {
   uint32_t jit_ctas_per_sm = 0;
   std::string jit_log;
   uint64_t module_gen = 0;   // compiled modules loaded so far
+  uint32_t jit_smem = 0;     // dynamic shared memory of persistent launches (path table)
   uint32_t campaigns = 0;    // device campaigns attached
 };
 
@@ -387,16 +388,24 @@ cufz_status jit_compile(cufz_ctx* c) {
                                       nullptr, 0);
   if (e == cudaSuccess) e = cudaLibraryGetKernel(&c->jit_persist, c->jit_lib, "cufz_jit_persistent");
   if (e == cudaSuccess && plain) e = cudaLibraryGetKernel(&c->jit_plain, c->jit_lib, "cufz_jit_plain");
+  // a module with path-mode programs gives persistent CTAs a path table
+  uint32_t smem = 0;
+  for (size_t k = 0; k < c->prog_src.size(); k++)
+    if (include[k] && c->prog_src[k].find("jit_path_count(") != std::string::npos) smem = kJitPathTableBytes;
+  if (e == cudaSuccess && smem)
+    e = cudaFuncSetAttribute(reinterpret_cast<const void*>(c->jit_persist),
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int occ = 0;
   if (e == cudaSuccess)
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        &occ, reinterpret_cast<const void*>(c->jit_persist), (int)c->shape.cta_threads, 0);
+        &occ, reinterpret_cast<const void*>(c->jit_persist), (int)c->shape.cta_threads, smem);
   if (e != cudaSuccess || occ < 1) {
     cudaGetLastError();
     return CUFZ_E_CUDA;
   }
   c->jit_ctas_per_sm = c->cfg.ctas_per_sm ? std::min<uint32_t>(c->cfg.ctas_per_sm, occ) : (uint32_t)occ;
   c->jit_progs = (uint32_t)c->progs.size();
+  c->jit_smem = smem;
   c->module_gen++;
   c->prog_in_module = include;
   c->lanes_in_module = c->prog_lanes;
@@ -406,9 +415,10 @@ cufz_status jit_compile(cufz_ctx* c) {
 cudaError_t launch_jit_persistent(cufz_ctx* c, const BatchHdr* d_batch, uint32_t ctas, cudaStream_t st) {
   EngineTables T = c->T;
   BatchHdr* b = const_cast<BatchHdr*>(d_batch);
-  void* args[] = {&T, &b};
+  uint32_t paths = c->jit_smem ? 1u : 0u;
+  void* args[] = {&T, &b, &paths};
   return cudaLaunchKernel(reinterpret_cast<const void*>(c->jit_persist), dim3(ctas), dim3(c->shape.cta_threads),
-                          args, 0, st);
+                          args, c->jit_smem, st);
 }
 
 cudaError_t launch_jit_plain(cufz_ctx* c, const BatchHdr* d_batch, uint32_t input, uint32_t blocks,
@@ -1842,6 +1852,7 @@ cufz_status campaign_attach(cufz_ctx* c, uint32_t n_slots, uint32_t item_threads
     env->slots.push_back(s);
   }
   env->module_gen = c->module_gen;
+  env->jit_smem = c->jit_smem;
   c->campaigns++;
   return CUFZ_OK;
 }

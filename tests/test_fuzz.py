@@ -234,3 +234,29 @@ def test_corpus_and_hang_caps():
     assert b.n_hangs == a.n_hangs and b.n_new_coverage == a.n_new_coverage
     s = b.stats()
     assert s["corpus_count"] == 9 and s["corpus_dropped"] == b.corpus_dropped
+
+
+def test_campaign_config_limits():
+    """cufz_campaign_bytes sizes valid configurations and gives 0 for
+    invalid ones (batch 1..8192, corpus 1..16384, bucket table a power of
+    two in 16..2^20, hang cap 1..2^20, item capacity up to 2^24); creating a
+    campaign without a context is refused before anything runs."""
+    def cfg(**kw):
+        base = dict(batch=1024, corpus_cap=4096, bucket_cap=1024, hang_cap=256, item_threads=0,
+                    max_items=0, seed=1)
+        base.update(kw)
+        return B.cufz_campaign_config(**base)
+
+    small = B.cufz_campaign_bytes(cfg())
+    assert small > 0 and small % 256 == 0
+    assert B.cufz_campaign_bytes(cfg(corpus_cap=16384)) > small
+    assert B.cufz_campaign_bytes(cfg(batch=8192)) > small
+    for bad in (dict(batch=0), dict(batch=8193), dict(corpus_cap=0), dict(corpus_cap=16385),
+                dict(bucket_cap=1000), dict(bucket_cap=8), dict(hang_cap=0),
+                dict(max_items=(1 << 24) + 1)):
+        assert B.cufz_campaign_bytes(cfg(**bad)) == 0, bad
+    try:
+        B.cufz_campaign_create(None, cfg(), 0, small, seeds(2))
+        raise AssertionError("created a campaign without a context")
+    except B.CufzError as e:
+        assert e.status == B.E_INVALID_ARG

@@ -166,13 +166,16 @@ def test_c3_ragged_blocks(B, orc, path):
 
 @pytest.mark.parametrize("path", PATHS)
 def test_c4_branch_heavy(B, orc, path):
+    """Branch-heavy programs: on the compiled path the persistent kernel
+    counts paths in its CTAs' path tables, and the plain kernel (no table)
+    replays each thread's path."""
     progs = gen.c4_programs()
     inputs = gen.c4_inputs(256, seed=4, max_blocks=12)
-    dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs, cap=1 << 13,
-                                                       orc_cap=1 << 16,
-                                                       flags=B.CF_KEEP_BITMAPS | path)
-    compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, 1 << 13)
-    assert int(dres["n_edges"].max()) > 50
+    for flags in (B.CF_KEEP_BITMAPS | path, B.CF_KEEP_BITMAPS | B.CF_PLAIN_LAUNCH | path):
+        dres, drecs, dbms, ores, orecs, obms, _ = run_both(B, orc, progs, inputs, cap=1 << 13,
+                                                           orc_cap=1 << 16, flags=flags)
+        compare(B, orc, inputs, dres, drecs, dbms, ores, orecs, obms, 1 << 13)
+        assert int(dres["n_edges"].max()) > 50
 
 
 @pytest.mark.parametrize("path", PATHS)

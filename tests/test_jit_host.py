@@ -260,14 +260,15 @@ def test_mutated_programs_match_oracle(tmp_path, host_objs, orc):
             assert np.array_equal(bm, obms[i]), (budget, i)
 
 
-@pytest.mark.parametrize("table_log2", [12, 1])
+@pytest.mark.parametrize("table_log2", [12, 1, 0])
 def test_path_counting_matches_oracle(tmp_path, host_objs, orc, table_log2):
     """Branch-heavy loop-free programs run in path mode: each thread counts
     its path (its sites' outcomes) in the CTA's path table, and each distinct
     path's edges are replayed once per work item with its count.  Pruned and
     unpruned, and on bit-flipped variants of the programs.  With a table of
     two slots most paths find no room, and their threads replay them at
-    once."""
+    once; without a table (table_log2 0: the plain kernel's CTAs) every
+    thread replays its own path."""
     rng = gen.SplitMix64(0x9ED1)
     progs = gen.c4_programs()[:6]
     k = 0
@@ -282,7 +283,8 @@ def test_path_counting_matches_oracle(tmp_path, host_objs, orc, table_log2):
     ins = gen.c4_inputs(36, n_programs=len(progs), seed=309, max_blocks=2)
     for flags in (0, B.CF_NO_PRUNE):
         exe = build(tmp_path, host_objs, progs, flags,
-                    defines=(f"CUFZ_PATH_SLOTS_LOG2={table_log2}",))
+                    defines=(f"CUFZ_PATH_SLOTS_LOG2={table_log2}",) if table_log2
+                    else ("CUFZ_SHIM_NO_PATH_TABLE",))
         got = run(tmp_path, exe, progs, ins)
         ores, orecs, obms = orc.run_batch(progs, ins, rec_cap=1 << 14, bitmaps=True)
         ops = engine_ops(orc, progs, ins, flags)
