@@ -332,8 +332,10 @@ uint64_t cufz_campaign_bytes(const cufz_campaign_config* cfg);
  * stays as it is: loading or unloading programs or changing their paths or
  * lane mappings makes submits that would rebuild it, and cufz_destroy,
  * return CUFZ_E_BUSY.  CUFZ_E_INVALID_ARG for a bad configuration, memory
- * or seed count (1..corpus_cap); CUFZ_E_BUSY without batch free slots;
- * CUFZ_E_UNSUPPORTED for a context without the compiled path. */
+ * or seed count (1..corpus_cap), checked before anything runs; CUFZ_E_BUSY
+ * without batch free slots; CUFZ_E_UNSUPPORTED for a context without the
+ * compiled path.  These last two are found after the dry run, so the
+ * context's union then holds the seeds' coverage. */
 cufz_status cufz_campaign_create(cufz_ctx* ctx, const cufz_campaign_config* cfg, void* dev_mem,
                                  uint64_t dev_bytes, const cufz_input* seeds, uint32_t n_seeds,
                                  cufz_campaign** out);
@@ -367,7 +369,9 @@ cufz_status cufz_campaign_hangs(cufz_campaign* camp, cufz_input* out, uint64_t* 
  * and pick counts (n_corpus = the corpus size), the buckets, the unique
  * hangs and the counters (rounds, executed, violating, hang_execs,
  * new_coverage and the dropped and refused counts).  Afterwards the
- * campaign continues as the saved one would have. */
+ * campaign continues as the saved one would have.  CUFZ_E_INVALID_ARG when
+ * n_corpus is not the corpus size, or for more hangs than hang_cap or more
+ * buckets than half of bucket_cap (the table keeps room to probe). */
 cufz_status cufz_campaign_restore(cufz_campaign* camp, const uint8_t* favoured, const uint32_t* picks,
                                   uint32_t n_corpus, const cufz_bucket* buckets, uint32_t n_buckets,
                                   const cufz_input* hangs, const uint64_t* hang_rounds, uint32_t n_hangs,
