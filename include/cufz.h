@@ -331,7 +331,9 @@ uint64_t cufz_campaign_bytes(const cufz_campaign_config* cfg);
  * the compiled path.  While a campaign exists the context's compiled module
  * stays as it is: loading or unloading programs or changing their paths or
  * lane mappings makes submits that would rebuild it, and cufz_destroy,
- * return CUFZ_E_BUSY.  CUFZ_E_INVALID_ARG for a bad configuration, memory
+ * return CUFZ_E_BUSY.  The context may run other inputs meanwhile (on its
+ * other slots); they share its union, and each campaign round renews the
+ * union's epoch snapshot.  CUFZ_E_INVALID_ARG for a bad configuration, memory
  * or seed count (1..corpus_cap), checked before anything runs; CUFZ_E_BUSY
  * without batch free slots; CUFZ_E_UNSUPPORTED for a context without the
  * compiled path.  These last two are found after the dry run, so the

@@ -260,10 +260,13 @@ class DeviceCampaign:
 
     def __init__(self, engine, seeds: np.ndarray, seed: int = 0xF022, batch: int = 1024,
                  corpus_cap: int = 16384, bucket_cap: int = 4096, hang_cap: int = 4096,
-                 item_threads: int = 0, max_items: int = 0):
+                 item_threads: int = 0, max_items: int = 0, n_bufs: list[int] | None = None):
+        """n_bufs (each program's buffer count) is kept for checkpoints, which
+        the host campaign can then resume."""
         import torch
 
         self.engine = engine
+        self.n_bufs = list(n_bufs) if n_bufs is not None else None
         self.cfg = B.cufz_campaign_config(batch=batch, corpus_cap=corpus_cap, bucket_cap=bucket_cap,
                                           hang_cap=hang_cap, item_threads=item_threads,
                                           max_items=max_items, seed=int(seed) & (2**64 - 1))
@@ -329,7 +332,7 @@ class DeviceCampaign:
         bk = self.buckets()
         hg = self.hangs()
         keys = sorted(bk)
-        n_bufs = getattr(self, "n_bufs", None)
+        n_bufs = self.n_bufs
         np.savez(path, corpus=inp, favoured=fav, picks=picks.astype(np.int64),
                  bucket_keys=np.array(keys, dtype=np.int64).reshape(-1, 3),
                  bucket_inputs=np.array([bk[k]["input"] for k in keys], dtype=INPUT_DTYPE),
@@ -368,8 +371,7 @@ class DeviceCampaign:
         B.cufz_campaign_restore(c.camp, z["favoured"], z["picks"], bk, z["hang_inputs"],
                                 z["hang_rounds"], cnt)
         c.seconds = float(z["seconds"][0])
-        if len(z["n_bufs"]):
-            c.n_bufs = [int(v) for v in z["n_bufs"]]
+        c.n_bufs = [int(v) for v in z["n_bufs"]] if len(z["n_bufs"]) else None
         return c
 
     def close(self) -> None:
@@ -427,7 +429,8 @@ def main(argv=None, executor_factory=None) -> int:
             if args.resume:
                 c = DeviceCampaign.resume(args.resume, ex.engine)
             else:
-                c = DeviceCampaign(ex.engine, c5_corpus(progs), seed=args.seed, batch=args.batch)
+                c = DeviceCampaign(ex.engine, c5_corpus(progs), seed=args.seed, batch=args.batch,
+                                   n_bufs=n_bufs)
             c.n_bufs = n_bufs
             done = 0
             try:

@@ -132,9 +132,9 @@ def test_device_campaign_checkpoint_and_resume(B, tmp_path):
     progs, seeds, n_bufs = _workload()
     path = str(tmp_path / "dev")
     with _engine(B, progs) as E1:
-        a = DeviceCampaign(E1, seeds, seed=77, batch=128, corpus_cap=200, bucket_cap=256)
+        a = DeviceCampaign(E1, seeds, seed=77, batch=128, corpus_cap=200, bucket_cap=256,
+                           n_bufs=n_bufs)
         try:
-            a.n_bufs = n_bufs
             a.run(2)
             a.checkpoint(path)
             a.run(3)
