@@ -142,31 +142,6 @@ static __device__ __forceinline__ void jit_cover_k(uint32_t slot, uint32_t e, ui
 // code (many branch sites): a call at each site instead of the inline test.
 static __device__ __noinline__ void jit_cover_out(uint32_t slot, uint32_t e) { jit_cover(slot, e); }
 
-// The edges of one test thread of a loop-free program, from the sites it
-// evaluated (bit s of e1:e0) and their outcomes (bit s of o1:o0): in a
-// loop-free program each site runs at most once and sites run in program
-// order, so ascending site order is the order of evaluation, and prev
-// starts at 0.  loc[s] = loc0 | loc1 << 16.  One shared out-of-line copy.
-static __device__ __noinline__ void jit_cover_path(uint32_t slot, uint32_t e0, uint32_t e1,
-                                                   uint32_t o0, uint32_t o1,
-                                                   const uint32_t* __restrict__ loc) {
-  uint32_t prev = 0;
-#pragma unroll 1
-  for (uint32_t h = 0; h < 2; h++) {
-    uint32_t e = h ? e1 : e0;
-    const uint32_t o = h ? o1 : o0;
-#pragma unroll 1
-    while (e) {
-      const uint32_t b = (uint32_t)__ffs(e) - 1u;
-      e &= e - 1u;
-      const uint32_t lv = loc[h * 32u + b];
-      const uint32_t cur = ((o >> b) & 1u) ? (lv >> 16) : (lv & 0xFFFFu);
-      jit_cover(slot, (cur ^ prev) & 0xFFFFu);
-      prev = cur >> 1;
-    }
-  }
-}
-
 // Path counting (path-mode programs).  In a loop-free program a thread's
 // edges and its counts of ops, accesses and branch evaluations follow from
 // its path: the sites it evaluates and their outcomes.  The outcome bits po

@@ -518,9 +518,6 @@ namespace {
 
 // Programs with at least this many kept branch sites get compact code.
 constexpr int kCompactSites = 24;
-// Path-mode programs count their threads' paths per CTA and replay each
-// distinct path once per work item (jit_path_count, jit_path_flush).
-constexpr bool kPathCounting = true;
 // Programs of at most this many kept ops read their launch constants and
 // arguments once per work item, before the loop over the lane's test
 // threads; larger ones read them inside it (from the CTA's shared copy of
@@ -543,12 +540,14 @@ struct Gen {
   bool hoist_ = false;  // launch constants and arguments read before the loop
   // Path mode, for compact programs without loops and with at most 64 branch
   // sites: each site runs at most once per test thread and sites run in
-  // program order, so a thread's edges follow from which sites it evaluated
-  // and their outcomes.  Sites only set bits in two 64-bit masks (as 32-bit
-  // halves pe0/pe1, po0/po1), and one shared out-of-line call per thread
-  // (jit_cover_path) replays the edges; the counts of a run are one add to a
-  // packed per-thread counter (n_ops, accesses and branches of a loop-free
-  // thread are bounded by the program: 12, 12 and 8 bits).
+  // program order, so a thread's edges and counts follow from its path, which
+  // its sites' outcome bits fix (po0/po1, the two halves of a 64-bit mask,
+  // set in taken arms).  At its end a thread counts its path in the CTA's
+  // path table (jit_path_count); after the work item the CTA replays each
+  // distinct path once through the program's walk table (jit_path_flush),
+  // adding the path's count to its edges and counts.  A loop-free thread's
+  // ops, accesses and branch evaluations are bounded by the program (12, 12
+  // and 8 bits of the walk table's packed counts).
   bool path_ = false;
   // Block-serial function (a program whose performed shared stores need
   // their barriers): accesses perform shared stores and loads in the block's
@@ -657,12 +656,7 @@ struct Gen {
     int q = pc;
     while (q < end && ir.ops[q].opc != B_IF && ir.ops[q].opc != B_LOOP) q++;
     const bool ends_at_if = q < end && ir.ops[q].opc == B_IF && ir.ops[q].kept;
-    if (path_) {
-      if (kPathCounting) return;  // the walk adds the path's counts (seg_)
-      const uint32_t packed = (uint32_t)k | ((uint32_t)m << 12) | ((ends_at_if ? 1u : 0u) << 24);
-      if (packed) line(ind, "pk += " + hex32(packed) + ";");
-      return;
-    }
+    if (path_) return;  // the walk adds the path's counts (seg_)
     if (k) line(ind, "acc.n_ops += " + std::to_string(k) + "u;");
     if (m) line(ind, "acc.n_acc += " + std::to_string(m) + "u;");
     if (ends_at_if) line(ind, "acc.n_branch += 1u;");
@@ -672,11 +666,7 @@ struct Gen {
   // heads); an IF's evaluation is counted with the run that ends at it.
   void cover(int ind, int site, const std::string& cond, bool count) {
     if (rec_) return;
-    if (path_) {  // the site's evaluation bit; the outcome bit is set in the taken arm
-      if (kPathCounting) return;  // the walk derives the evaluated sites from the outcomes
-      line(ind, "pe" + std::to_string(site >> 5) + " |= " + hex32(1u << (site & 31)) + ";");
-      return;
-    }
+    if (path_) return;  // the outcome bit is set in the taken arm; the walk does the rest
     uint32_t l0 = ir.loc0[site], l1 = ir.loc1[site];
     const std::string upd = std::string(count ? " acc.n_branch++;" : "") +
                             (compact_ ? " jit_cover_out(slot, e); }" : " jit_cover(slot, e); }");
@@ -1286,15 +1276,7 @@ struct Gen {
     bool loops = false;
     for (const auto& op : ir.ops) loops |= op.kept && op.opc == B_LOOP;
     path_ = compact_ && !loops && ir.n_sites <= 64;
-    if (path_ && !kPathCounting) {
-      // the LOC table the path replay reads: loc0 | loc1 << 16 per site
-      std::string t = "static __device__ const uint32_t " + fn + "_loc[" +
-                      std::to_string(std::max(ir.n_sites, 1)) + "] = {";
-      for (int s = 0; s < ir.n_sites; s++)
-        t += (s ? ", " : "") + hex32((uint32_t)ir.loc0[s] | ((uint32_t)ir.loc1[s] << 16));
-      line(0, t + (ir.n_sites ? "};" : "0u};"));
-    }
-    if (path_ && kPathCounting) {
+    if (path_) {
       // the walk table: LOC pair, the next site and the counts up to it for
       // each outcome
       path_next();
@@ -1409,7 +1391,7 @@ struct Gen {
     line(1, "uint32_t bl = 0, tl = 0;");
     line(1, "if (inc) { bl = udiv(g0 + threadIdx.x, vin->mT); tl = g0 + threadIdx.x - bl * vin->T; }");
     stepped_pre(1, sreg_used);
-    if (path_ && kPathCounting) line(1, "jit_path_clear();");
+    if (path_) line(1, "jit_path_clear();");
     line(1, "constexpr int lanes_k = " + lanes + ";");
     line(1, "#pragma unroll lanes_k");
     line(1, "for (uint32_t g = g0 + threadIdx.x; g < g_end; g += blockDim.x) {");
@@ -1418,8 +1400,7 @@ struct Gen {
     line(2, "uint32_t dh = digest_start(bl, tl);");
     line(2, "uint32_t prev = 0, back = 0, nv = 0;");
     line(2, "(void)prev; (void)back; (void)dh;");
-    if (path_) line(2, "uint32_t pe0 = 0, pe1 = 0, po0 = 0, po1 = 0, pk = 0;");
-    if (path_) line(2, "(void)pe0; (void)pe1;");
+    if (path_) line(2, "uint32_t po0 = 0, po1 = 0;");
     reg_decls(2, used);
     if (heap_ops) line(2, heap_decl);
     sp_ = !path_;  // prev is 0 at each test thread's start
@@ -1429,16 +1410,11 @@ struct Gen {
     sp_ = kp_ = false;
     if (has_loop) line(1, "cufz_done:");
     if (path_) {
-      if (kPathCounting) {
-        line(2, "if (!jit_path_count(po0, po1)) {");
-        line(3, "const uint32_t pc_ = jit_path_walk(slot, po0, po1, 1u, " + fn + "_walk, " +
-                    std::to_string(first_site_) + "u, " + hex32(init_) + ");");
-        line(3, "acc.n_ops += pc_ & 0xFFFu; acc.n_acc += (pc_ >> 12) & 0xFFFu; acc.n_branch += pc_ >> 24;");
-        line(2, "}");
-      } else {
-        line(2, "acc.n_ops += pk & 0xFFFu; acc.n_acc += (pk >> 12) & 0xFFFu; acc.n_branch += pk >> 24;");
-        line(2, "jit_cover_path(slot, pe0, pe1, po0, po1, " + fn + "_loc);");
-      }
+      line(2, "if (!jit_path_count(po0, po1)) {");
+      line(3, "const uint32_t pc_ = jit_path_walk(slot, po0, po1, 1u, " + fn + "_walk, " +
+                  std::to_string(first_site_) + "u, " + hex32(init_) + ");");
+      line(3, "acc.n_ops += pc_ & 0xFFFu; acc.n_acc += (pc_ >> 12) & 0xFFFu; acc.n_branch += pc_ >> 24;");
+      line(2, "}");
     }
     line(2, "if (dig) acc.digest += digest_end(dh);");
     line(2, "if (nv) {");
@@ -1456,7 +1432,7 @@ struct Gen {
     line(2, "}");
     stepped_tail(2, sreg_used);
     line(1, "}");
-    if (path_ && kPathCounting) {
+    if (path_) {
       line(1, "{");
       line(2, "const PathCounts t_ = jit_path_flush(slot, " + fn + "_walk, " +
                   std::to_string(first_site_) + "u, " + hex32(init_) + ");");
