@@ -628,6 +628,11 @@ def run_engine(args, rank, world, local, pg):
                                       pg)
                 out.append(serving_sub(rec))
             subs["c5" + ("_plain" if plain else "")] = out
+        rows, clk = measure_campaign(local, rank, (1024,), max_rounds=16)
+        subs["campaign"] = {"metric": "fuzz inputs/sec", "unit": "inputs/s", "rows": rows,
+                            "clocks": clk,
+                            "workload": "coverage-guided rounds over the serving workload's 64 "
+                                        "programs, host queue vs device-resident queue"}
         line["sub"] = subs
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -751,11 +756,12 @@ def run_serving(args, rank, world, local, pg):
         print(json.dumps(line), flush=True)
 
 
-def run_campaign(args, rank, world, local, pg):
+def measure_campaign(local, rank, batches, max_rounds=64):
     """The fuzzing campaign over the serving workload's 64 programs: rounds
     per second with the queue on the host (one device batch per round, a
     host round trip between rounds) and on the device (every step of a round
-    in kernels, rounds enqueued back to back), at several round sizes."""
+    in kernels, rounds enqueued back to back), at the given round sizes.
+    Returns (rows, clocks record)."""
     import torch
 
     from paper_2601_01048_gb300 import binding as B
@@ -769,8 +775,8 @@ def run_campaign(args, rank, world, local, pg):
     rows = []
     clocks = ClockSampler(local)
     clocks.start()
-    for batch in (64, 256, 1024, 4096):
-        rounds = max(4, min(64, 65536 // batch))
+    for batch in batches:
+        rounds = max(4, min(max_rounds, 65536 // batch))
         row = {"batch": batch, "rounds": rounds}
         for kind in ("host", "device"):
             E = B.Engine(device=local, max_slots=max(batch, len(seeds)), record_cap=64,
@@ -801,7 +807,13 @@ def run_campaign(args, rank, world, local, pg):
                          "ms_per_round": 1e3 * dt / rounds, "corpus_after": corpus}
         row["device_over_host"] = row["device"]["rounds_per_s"] / row["host"]["rounds_per_s"]
         rows.append(row)
-    clk = clocks.stop()
+    return rows, clocks.stop()
+
+
+def run_campaign(args, rank, world, local, pg):
+    """Fuzz inputs per second of the campaign, host queue against device
+    queue, at 64 to 4,096 children per round."""
+    rows, clk = measure_campaign(local, rank, (64, 256, 1024, 4096))
     if rank == 0:
         top = rows[-1]
         print(json.dumps({
