@@ -305,6 +305,7 @@ static __device__ __forceinline__ void run_items(const EngineTables& T, BatchHdr
   const uint32_t n_items = kPersistent ? batch->n_items : 1u;
 
   for (uint32_t i = threadIdx.x; i < kHashSlots + kSatWords; i += blockDim.x) hash[i] = 0;
+  if (threadIdx.x == 0) s_skip = 0;  // only the interpreter's staging sets it
   uint32_t cur_input = 0xFFFFFFFFu, cur_prog = 0xFFFFFFFFu;
   bool first = true;
 
@@ -332,19 +333,21 @@ static __device__ __forceinline__ void run_items(const EngineTables& T, BatchHdr
       uint32_t* dst = reinterpret_cast<uint32_t*>(sin);
       for (uint32_t i = threadIdx.x; i < sizeof(DevInput) / 4; i += blockDim.x) dst[i] = src[i];
       __syncthreads();
-      if (threadIdx.x == 0) s_skip = (kStageProg && sin->prog_bytes > max_prog_bytes) ? 1u : 0u;
-      __syncthreads();
-      if (kStageProg && !s_skip && sin->prog_off != cur_prog) {
-        const uint4* ps = reinterpret_cast<const uint4*>(T.progs + sin->prog_off);
-        uint4* pd = reinterpret_cast<uint4*>(sprog);
-        for (uint32_t i = threadIdx.x; i < sin->prog_bytes / 16; i += blockDim.x) pd[i] = ps[i];
-        cur_prog = sin->prog_off;
+      if (kStageProg) {  // the interpreter stages the input's program too
+        if (threadIdx.x == 0) s_skip = sin->prog_bytes > max_prog_bytes ? 1u : 0u;
+        __syncthreads();
+        if (!s_skip && sin->prog_off != cur_prog) {
+          const uint4* ps = reinterpret_cast<const uint4*>(T.progs + sin->prog_off);
+          uint4* pd = reinterpret_cast<uint4*>(sprog);
+          for (uint32_t i = threadIdx.x; i < sin->prog_bytes / 16; i += blockDim.x) pd[i] = ps[i];
+          cur_prog = sin->prog_off;
+        }
+        __syncthreads();
+        if (!s_skip && threadIdx.x == 0 &&
+            reinterpret_cast<const DevProgHdr*>(sprog)->n_regs > max_regs)
+          s_skip = 1;
+        __syncthreads();
       }
-      __syncthreads();
-      if (kStageProg && !s_skip && threadIdx.x == 0 &&
-          reinterpret_cast<const DevProgHdr*>(sprog)->n_regs > max_regs)
-        s_skip = 1;
-      __syncthreads();
       cur_input = in_idx;
     }
     const bool ran = run(sin, g0, cnt, s_skip != 0);

@@ -260,3 +260,21 @@ def test_campaign_config_limits():
         raise AssertionError("created a campaign without a context")
     except B.CufzError as e:
         assert e.status == B.E_INVALID_ARG
+
+
+def test_first_record_is_the_least_key():
+    """A bucket's key comes from the stored record of least (block, thread,
+    ordinal), whatever order the records were stored in."""
+    from paper_2601_01048_gb300.fuzz import first_record
+
+    recs = np.zeros(5, B.VIOLATION_DTYPE)
+    keys = [(3, 0, 1), (1, 7, 4), (1, 2, 9), (1, 2, 3), (2, 0, 0)]
+    for r, (b, t, o) in zip(recs, keys):
+        r["block_lin"], r["thread_lin"], r["ordinal"], r["site"] = b, t, o, 100 * b + 10 * t + o
+    rng = gen.SplitMix64(5)
+    for _ in range(8):
+        perm = [int(v) for v in np.argsort([rng.next() for _ in range(5)])]
+        f = first_record(recs[perm])
+        assert (int(f["block_lin"]), int(f["thread_lin"]), int(f["ordinal"])) == (1, 2, 3)
+        assert int(f["site"]) == 123
+    assert first_record(recs[:0]) is None and first_record(None) is None
