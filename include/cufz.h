@@ -271,8 +271,8 @@ typedef struct {
  * AFL++'s coverage-guided loop (Sec. 2.1, Fig. 1; the harness of Sec. 4)
  * with its queue, corpus and bug buckets resident on the device.  A round
  * takes `batch` parents from the corpus, favoured entries first (those that
- * brought new coverage), least picked first, then the lowest index, round
- * robin; mutates a copy of each (cufz_mutate_children's streams, round r,
+ * brought new coverage and have not been picked since), least picked first,
+ * then the lowest index, round robin; mutates a copy of each (cufz_mutate_children's streams, round r,
  * child j); runs the children on the context's compiled kernel; adds the
  * children flagged CUFZ_FL_NEW_COV to the corpus as favoured entries, in
  * child order; files every violating child under the key (program_id,
@@ -302,7 +302,10 @@ typedef struct {
 
 typedef struct {
   uint64_t key;      /* program_id << 32 | site << 8 | cls of the first
-                        stored violation (site 0xFFFF, cls 0xFF: none stored) */
+                        stored violation (site 0xFFFF, cls 0xFF: none stored);
+                        for a child whose violations overflowed the record
+                        area, which records were stored, and so the key, can
+                        depend on the order its threads finished */
   uint64_t first;    /* round << 32 | child index of its first child */
   uint32_t hits;     /* violating children filed under it */
   uint32_t pad;
