@@ -167,3 +167,33 @@ def test_device_campaign_checkpoint_and_resume(B, tmp_path):
         assert np.array_equal(h.corpus.view(np.uint8), a_corpus[0].view(np.uint8))
         assert sorted(h.buckets) == sorted(a_buckets)
         assert np.array_equal(E3.union(), union_a)
+
+
+def test_device_campaign_on_every_program_kind(B):
+    """Division, heap and block-serial barrier programs (whole test blocks
+    per work item, the block-serial launch limits) in a device campaign:
+    it reaches the host campaign's corpus, buckets, hangs, counters and
+    union."""
+    from paper_2601_01048_gb300.fuzz import DeviceCampaign
+
+    progs = gen.div_programs(4) + gen.heap_programs(4) + gen.barrier_programs(4, live=True)
+    seeds = np.concatenate([gen.div_inputs(8, n_programs=4, seed=91),
+                            gen.heap_inputs(8, n_programs=4, seed=92),
+                            gen.barrier_inputs(8, n_programs=4, seed=93)])
+    seeds["program_id"][8:16] += 4
+    seeds["program_id"][16:] += 8
+    n_bufs = gen.program_bufs(progs)
+    with _engine(B, progs) as E1:
+        host = Campaign(_NoOverflow(E1), n_bufs, seeds, seed=0xB0B, batch=96, corpus_cap=100)
+        for _ in range(4):
+            host.run_round()
+        union_host = E1.union()
+    assert host.n_new_coverage > 0 and host.buckets
+    with _engine(B, progs) as E2:
+        dev = DeviceCampaign(E2, seeds, seed=0xB0B, batch=96, corpus_cap=100, bucket_cap=256)
+        try:
+            dev.run(4)
+            _same_campaign(host, dev)
+            assert np.array_equal(E2.union(), union_host)
+        finally:
+            dev.close()
