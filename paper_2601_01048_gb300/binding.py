@@ -620,7 +620,9 @@ class Engine:
                 res[i] = r
                 t = int(r["ticket"])
                 if records:
-                    recs[i] = cufz_get_records(self.ctx, t, int(r["n_records"]))
+                    nr = int(r["n_records"])
+                    recs[i] = (cufz_get_records(self.ctx, t, nr) if nr
+                               else np.zeros(0, VIOLATION_DTYPE))
                 if bitmaps:
                     bms[i] = cufz_get_bitmap(self.ctx, t)
                 if release:
